@@ -1,0 +1,447 @@
+#!/usr/bin/env python
+"""Benchmark of the slimLS hot path on one GB300 (or N replicas).
+
+Metric: sampled rows/s (ell rows per step) of the chosen form on the
+256x256 / 180-view / 363-bin workload (r = 5, lambda = 1e-3), next to the
+plain float64 form on the same seeds, plus time-to-accuracy of both.
+
+  chosen form: float32 projector/residual/scatter, float64 Gram, float32 tiled
+               Cholesky + float64-residual refinement, one CUDA graph per step
+  plain form:  float64 everywhere, float64 tiled Cholesky, per-kernel launches
+
+Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
+stream the library launches on, with a 256 MiB write between steps to flush
+L2 (129 MB).  Per-phase times come from the library's own event records
+inside the same timed steps.  One JSON line on rank 0.
+
+`--impl reference` times the FP64 CPU oracle (the reference arm) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "sampled rows/s & time to 1e-2 rel. error: plain FP64 vs chosen form, 1 GB300"
+FP32_LANES_PER_SM = 128
+FP64_FMA_PER_SM_CLK = 2          # measured: 1.19 TFLOP/s FP64 FMA at 152 SMs
+NUM_SMS = 152
+MAX_SM_MHZ = 2070.0
+
+
+def workload_of(name):
+    cfg = {"precision-256": workloads.C2, "plain-64": workloads.C1}[name]
+    desc = (f"{cfg.name}: {cfg.N}x{cfg.N} image (n={cfg.n}), {cfg.n_views} views x {cfg.det} bins "
+            f"(m={cfg.m}), one view per block (ell={cfg.ell}), r={cfg.r}, lambda={cfg.lam:g}, "
+            f"seed {cfg.seed}, 10 random ellipses, 1% noise")
+    return cfg, desc
+
+
+# --------------------------------------------------------------------------- CPU oracle leg
+def cpu_leg(args):
+    """Times the FP64 oracle (single BLAS thread); prints one JSON object."""
+    from oracle import joseph, slim as oslim
+    cfg, _ = workload_of(args.workload)
+    g = joseph.Geometry(cfg.N, cfg.n_views, cfg.det)
+    x_true, e = workloads.tomo_inputs_2d(cfg)
+    A = joseph.full_matrix(g)
+    b = workloads.add_noise(A @ x_true, e, cfg.noise)
+    src = oslim.tomo_source(g, b)
+    sched = oslim.view_schedule(g, cfg.seed, 10 ** 9)
+    runner = oslim.run(src, sched, cfg.r, cfg.lam)
+    for _ in range(args.cpu_warmup):
+        next(runner)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        next(runner)
+        steps += 1
+        el = time.perf_counter() - t0
+        if (args.cpu_steps and steps >= args.cpu_steps) or (not args.cpu_steps and el >= args.cpu_seconds):
+            break
+    el = time.perf_counter() - t0
+    print(json.dumps({"rows_per_s": cfg.ell * steps / el, "steps": steps, "seconds": el,
+                      "warmup": args.cpu_warmup}))
+
+
+def run_cpu_leg(args, steps=0, warmup=None):
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", "--workload", args.workload,
+           "--cpu-seconds", str(args.cpu_seconds), "--cpu-steps", str(steps),
+           "--cpu-warmup", str(args.r_warm if warmup is None else warmup)]
+    res = subprocess.run(cmd, capture_output=True, text=True, env=env)
+    if res.returncode != 0:
+        raise RuntimeError("cpu leg failed:\n" + res.stderr[-2000:])
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+# --------------------------------------------------------------------------- GPU helpers
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index):
+        self.dev = dev_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def make_b(sl, cfg, x_true, e):
+    """b = A x_true + noise, with A x_true from the library's projector (float64)."""
+    import torch
+    s = sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.ell, cfg.r, cfg.lam, cfg.seed)
+    xt = torch.tensor(x_true, dtype=torch.float64, device="cuda")
+    y = torch.zeros(cfg.m, dtype=torch.float64, device="cuda")
+    s.project(xt, y)
+    torch.cuda.synchronize()
+    clean = y.cpu().numpy()
+    s.close()
+    return workloads.add_noise(clean, e, cfg.noise)
+
+
+def make_form(sl, cfg, form, seed):
+    if form == "chosen":
+        return sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.ell, cfg.r, cfg.lam, seed,
+                       precision=sl.SLIM_PREC_FP32, solver=sl.SLIM_SOLVE_MIXED, refine_iters=2,
+                       use_graph=True)
+    return sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.ell, cfg.r, cfg.lam, seed,
+                   precision=sl.SLIM_PREC_FP64, solver=sl.SLIM_SOLVE_FP64, use_graph=False)
+
+
+def timed_steps(s, K, W, flush, stream, snapshot_every=0, snap_dtype=None, accum_last=0):
+    """Run W untimed then K timed steps; returns (ms per step list, phase-ms sums, snapshots)."""
+    import torch
+    s.set_stream(stream.cuda_stream)
+    s.set_timing(True)
+    for i in range(W):
+        flush.fill_(i)
+        s.step(1)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    per = []
+    phases = None
+    snaps = []
+    xs = None
+    xbuf = torch.empty(s.n, dtype=snap_dtype or torch.float64, device="cuda") if (
+        snapshot_every or accum_last) else None
+    for i in range(K):
+        flush.fill_(i + W)
+        e0.record(stream)
+        s.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        per.append(e0.elapsed_time(e1))
+        ph, _ = s.get_timing()
+        phases = ph if phases is None else {k: phases[k] + ph[k] for k in ph}
+        if snapshot_every and (i + 1) % snapshot_every == 0:
+            s.get_x(xbuf)
+            snaps.append((i + 1, float(sum(per)), xbuf.double().clone()))
+        if accum_last and i >= K - accum_last:
+            s.get_x(xbuf)
+            xs = xbuf.double().clone() if xs is None else xs + xbuf.double()
+    s.set_timing(False)
+    return per, phases, snaps, xs
+
+
+def chol_flops(p):
+    return p ** 3 / 3.0
+
+
+def roofline_of(phases_ms, K, p, ell, N, form, clocks_mhz):
+    """Roofline of the dominant phase (largest share of step time)."""
+    tot = {k: v / K for k, v in phases_ms.items()}
+    dom = max(tot, key=tot.get)
+    t = tot[dom] * 1e-3
+    if dom in ("factor",):
+        flops = chol_flops(p)
+        if form == "chosen":
+            peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+            note = "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"
+        else:
+            peak = NUM_SMS * FP64_FMA_PER_SM_CLK * 2 * MAX_SM_MHZ * 1e6 / 1e12
+            note = "FP64 FMA: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz"
+        ach = flops / t / 1e12
+        return {"kernel": "chol_factor_kernel", "phase": dom, "bound": "alu", "achieved": ach,
+                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "algorithmic": f"p^3/3 = {flops:.4g} flop per launch (p = {p})",
+                "peak_source": note, "share_of_step": tot[dom] / sum(tot.values())}
+    if dom == "solve":
+        # triangular solves + refinement residuals: bytes of L (read twice per solve) and G
+        es = 4 if form == "chosen" else 8
+        solves = 3 if form == "chosen" else 1
+        byts = solves * 2 * (p * p / 2) * es + (2 * p * p * 8 if form == "chosen" else 0)
+        ach = byts / t / 1e9
+        peak = 6797.2
+        return {"kernel": "chol_fwd/bwd_kernel", "phase": dom, "bound": "hbm", "achieved": ach,
+                "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                "algorithmic": f"{byts:.4g} bytes per step", "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                "share_of_step": tot[dom] / sum(tot.values())}
+    byts = {"forward_residual": ell * 2 * N * (4 + 12), "gram_update": (ell * 6) * 2 * N * 12,
+            "scatter": ell * 6 * 2 * N * 20, "form_k": p * p * 12}.get(dom, 0)
+    ach = byts / t / 1e9
+    return {"kernel": dom, "phase": dom, "bound": "hbm", "achieved": ach, "peak": 6797.2,
+            "unit": "GB/s", "frac": ach / 6797.2, "traffic": None,
+            "algorithmic": f"{byts} bytes per step", "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+            "share_of_step": tot[dom] / sum(tot.values())}
+
+
+def traffic_from_profiles(kernel):
+    """dram bytes per launch recorded by the committed ncu summary, if the kernel
+    sources have not changed since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1912_07962_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_1912_07962_gb300", "csrc", f), "rb").read())
+    if rec.get("csrc_sha256") != h.hexdigest():
+        return None
+    return rec.get("kernels", {}).get(kernel)
+
+
+def tta_block(sl, cfg, b, flush, stream, epochs, thresholds):
+    """Time to relative error thresholds vs the reference iterate."""
+    import torch
+    M = cfg.n_views
+    steps = epochs * M
+    every = max(1, M // 10)
+    out = {}
+    res = {}
+    x_ref = None
+    for form in ("plain", "chosen"):
+        s = make_form(sl, cfg, form, cfg.seed)
+        s.set_data(b if form == "plain" else b.astype(np.float32))
+        per, _, snaps, xs = timed_steps(s, steps, 0, flush, stream, snapshot_every=every,
+                                        snap_dtype=torch.float64 if form == "plain" else torch.float32,
+                                        accum_last=M if form == "plain" else 0)
+        if form == "plain":
+            x_ref = xs / M
+        res[form] = (per, snaps)
+        s.close()
+    nref = float(torch.linalg.norm(x_ref))
+    for form, (per, snaps) in res.items():
+        errs = [(k, ms, float(torch.linalg.norm(x - x_ref)) / nref) for k, ms, x in snaps]
+        first = {}
+        for th in thresholds:
+            hit = next(((k, ms) for k, ms, e in errs if e <= th), None)
+            first[str(th)] = None if hit is None else {"steps": hit[0], "seconds": hit[1] * 1e-3}
+        kmin, msmin, emin = min(errs, key=lambda t: t[2])
+        out[form] = {"first_below": first, "min_err": emin, "min_err_step": kmin,
+                     "seconds_to_min_err": msmin * 1e-3, "seconds_total": sum(per) * 1e-3,
+                     "steps_total": len(per)}
+    out["reference"] = (f"mean of the float64 GPU iterates over epoch {epochs} "
+                        f"(steps {(epochs - 1) * M + 1}..{epochs * M}), same seed")
+    out["eval_every_steps"] = every
+    return out
+
+
+def e2e_block(sl, cfg, b, K, W):
+    """Same metric through the C ABI with host buffers: each step copies b from
+    pinned host memory, steps, and reads x back to pinned host memory."""
+    import torch
+    s = make_form(sl, cfg, "chosen", cfg.seed)
+    bh = torch.tensor(b.astype(np.float32)).pin_memory()
+    xh = torch.empty(cfg.n, dtype=torch.float32).pin_memory()
+    s.set_data(bh)
+    for _ in range(W):
+        s.set_data(bh)
+        s.step(1)
+        s.get_x(xh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        s.set_data(bh)
+        s.step(1)
+        s.get_x(xh)
+    el = time.perf_counter() - t0
+    s.close()
+    return {"value": cfg.ell * K / el, "unit": "rows/s", "h2d_bytes_per_step": 4 * cfg.m,
+            "d2h_bytes_per_step": 4 * cfg.n, "seconds": el, "steps": K}
+
+
+def main_gpu(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1912_07962_gb300 import build as slbuild
+    slbuild.build()
+    from paper_1912_07962_gb300 import slim as sl
+
+    cfg, desc = workload_of(args.workload)
+    seed = cfg.seed + 1000 * rank      # independent replicas
+    x_true = workloads.phantom_2d(cfg.N, seed, cfg.n_ellipses)
+    e = workloads.noise_direction(cfg.m, seed)
+    b = make_b(sl, cfg, x_true, e)
+    stream = torch.cuda.Stream()          # the library and the timing events share it
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # plain float64 form
+    sp = make_form(sl, cfg, "plain", seed)
+    sp.set_data(b)
+    per_p, ph_p, _, _ = timed_steps(sp, args.plain_steps, args.warmup, flush, stream)
+    sp.close()
+
+    # chosen form: the headline timed region
+    sc = make_form(sl, cfg, "chosen", seed)
+    sc.set_data(b.astype(np.float32))
+    clk = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    per_c, ph_c, _, _ = timed_steps(sc, args.steps, args.warmup, flush, stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    kernels = sc.kernels_per_step()
+    sc.close()
+    t_c = sum(per_c) * 1e-3
+    t_p = sum(per_p) * 1e-3
+    if world > 1:
+        tt = torch.tensor([t_c], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_c = float(tt)
+    rows_c = cfg.ell * args.steps * world / t_c
+    rows_p = cfg.ell * args.plain_steps / t_p
+
+    rl = roofline_of(ph_c, args.steps, cfg.p, cfg.ell, cfg.N, "chosen", clocks.get("sm_mhz"))
+    rl["traffic"] = traffic_from_profiles(rl["kernel"])
+    rl_p = roofline_of(ph_p, args.plain_steps, cfg.p, cfg.ell, cfg.N, "plain", None)
+
+    tta = None
+    if args.tta_epochs > 0 and rank == 0:
+        tta = tta_block(sl, cfg, b, flush, stream, args.tta_epochs,
+                        [0.5, 0.2, 0.1, 0.05, 0.02, 0.01])
+    e2e = e2e_block(sl, cfg, b, args.steps, args.warmup) if rank == 0 else None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        leg = run_cpu_leg(args)
+        cpu = {"value": leg["rows_per_s"], "unit": "rows/s", "cores": 1, "kind": "oracle",
+               "sample": (f"{leg['steps']} oracle steps of this workload after {leg['warmup']} "
+                          f"untimed warm-up steps, {leg['seconds']:.1f} s, one BLAS thread")}
+    if world > 1:
+        torch.distributed.barrier()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": rows_c, "unit": "rows/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_c / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": desc, "form": "chosen: float32 projector/residual/scatter, "
+                   "float64 Gram, float32 tiled Cholesky + 2 float64-residual refinements, "
+                   "one CUDA graph per step",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "plain": {"rows_per_s": rows_p, "ms_per_step": t_p / args.plain_steps * 1e3,
+                  "steps": args.plain_steps, "dtype": "f64",
+                  "phases_ms": {k: v / args.plain_steps for k, v in ph_p.items()},
+                  "roofline": rl_p},
+        "speedup_vs_plain": rows_c / (rows_p * world),
+        "phases_ms": {k: v / args.steps for k, v in ph_c.items()},
+        "roofline": rl, "tta": tta, "e2e": e2e, "cpu_baseline": cpu,
+        "gpu_launches": kernels * args.steps, "kernels_per_step": kernels, "clocks": clocks,
+    }
+    print(json.dumps(line))
+
+
+def main_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg, desc = workload_of(args.workload)
+    leg = run_cpu_leg(args, steps=args.steps, warmup=max(args.warmup, 0))
+    v = leg["rows_per_s"]
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "rows/s", "n_gpus": world,
+        "steps": leg["steps"], "warmup": args.warmup, "ms_per_step": leg["seconds"] / leg["steps"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": desc, "form": "FP64 CPU oracle (numpy/scipy)",
+                                        "parallelism": "single process"},
+        "cpu_baseline": {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{leg['steps']} oracle steps after {args.warmup} warm-up steps, "
+                                   f"one BLAS thread"},
+        "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=6)
+    ap.add_argument("--plain-steps", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="precision-256", choices=["precision-256", "plain-64"])
+    ap.add_argument("--tta-epochs", type=int, default=20)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-steps", type=int, default=0)
+    ap.add_argument("--cpu-warmup", type=int, default=6)
+    ap.add_argument("--cpu-leg", action="store_true")
+    args = ap.parse_args()
+    args.r_warm = workload_of(args.workload)[0].r + 1
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.cpu_leg:
+        cpu_leg(args)
+    elif args.impl == "reference":
+        main_reference(args)
+    else:
+        main_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

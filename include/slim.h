@@ -1,0 +1,214 @@
+/*
+ * slim.h -- C ABI of the GB300 slimLS library (libslim.so).
+ *
+ * The sampled limited-memory row-action method for least squares
+ * (Chung, Chung, Slagel, Tenorio, arXiv:1912.07962), Sec. 1, Eq. (ram)/(B_k):
+ *
+ *     x_k = x_{k-1} - eta * B_k A_k^T (A_k x_{k-1} - b_k),
+ *     B_k = (lambda_k I + M_k^T M_k)^{-1},   M_k = [A_{k-r}; ...; A_k],
+ *
+ * with C_k = I and lambda_k = 1/alpha_k.  A is a parallel-beam tomography
+ * forward model (Sec. 4.3) whose rows are generated on the device by a Joseph
+ * ray-driven projector; it is never stored (Sec. 4.2: blocks are function
+ * evaluations).  A block A_k is one projection view (the tomography blocks of
+ * Sec. 4.3), drawn i.i.d. uniformly (Sec. 1, the sampling W_k).
+ *
+ * Each step runs on the device, in the context's CUDA stream:
+ *   1. sample tau_k (counter-based SplitMix64; no host round trip);
+ *   2. r_k = A_k x_{k-1} - b_k, storing the block's rows in a ring of r+1 slots;
+ *   3. G = M_k M_k^T, updating only the new block's rows and columns;
+ *   4. (lambda_k I + G) z = [0;...;r_k;...;0] by a tiled Cholesky factorisation
+ *      (Sec. 2's Sherman-Woodbury identity turns the n x n solve of Eq. (B_k)
+ *      into this p x p one, p = (r+1) * ell);
+ *   5. x -= eta * M_k^T z.
+ *
+ * Conventions
+ *   - Every call returns a slim_status; the library never aborts and never
+ *     traps the device.  Device-side failures (a non-positive pivot, a bounded
+ *     wait that ran out) are recorded in a device status word and returned
+ *     by the next synchronising call (slim_sync, slim_get_x, slim_run, ...).
+ *   - Pointers are host pointers unless an `on_device` flag says otherwise or
+ *     the argument is documented as a device pointer.  All inputs are copied;
+ *     the caller keeps ownership of its buffers.
+ *   - dtype: SLIM_F32 = 0 (float), SLIM_F64 = 1 (double).
+ *   - Image layout: x[iy*N + ix] (2D).  Data layout: b[view*det_u + bin]
+ *     (view-major).  Ray id = view*det_u + bin.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef SLIM_H_
+#define SLIM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct slim_ctx slim_ctx;
+
+typedef enum {
+  SLIM_OK = 0,
+  SLIM_EINVAL = 1,   /* an argument is out of range or inconsistent */
+  SLIM_ENOMEM = 2,   /* a device or host allocation failed */
+  SLIM_ECUDA = 3,    /* a CUDA runtime call failed (message in slim_last_error) */
+  SLIM_ENOTPD = 4,   /* lambda_k I + G is not positive definite (Cholesky pivot <= 0) */
+  SLIM_ETIMEOUT = 5, /* a bounded device-side wait ran out; results are invalid */
+  SLIM_ESTATE = 6,   /* call order: e.g. a step before slim_set_data */
+  SLIM_ENOTSUP = 7   /* a valid but unsupported combination of options */
+} slim_status;
+
+enum { SLIM_F32 = 0, SLIM_F64 = 1 };
+enum { SLIM_PREC_FP64 = 0, SLIM_PREC_FP32 = 1 };
+enum { SLIM_SOLVE_FP64 = 0, SLIM_SOLVE_MIXED = 1 };
+enum { SLIM_BLOCKS_VIEWS = 0 };
+
+/* Parallel-beam geometry (Sec. 4.3; Joseph rows defined in the library docs).
+ *   dim        2 (only 2D is supported by this version)
+ *   n_side     N, image is N x N (n = N^2 unknowns)
+ *   n_views    A_v projection angles
+ *   det_u      D detector bins per view, unit spacing, centred
+ *   det_v      1 in 2D
+ *   angles     host array [n_views] of radians, or NULL for theta_a = a*pi/A_v
+ *   a_mode     0: rows generated on the fly (matrix-free); no other value yet
+ *   precision  SLIM_PREC_FP64: x, b, residual and scatter in float64;
+ *              SLIM_PREC_FP32: x, b, residual and scatter in float32 with float32
+ *              accumulation.  The Gram matrix is float64 in both. */
+typedef struct {
+  int dim;
+  int n_side;
+  int n_views;
+  int det_u;
+  int det_v;
+  const double* angles;
+  int a_mode;
+  int precision;
+} slim_geometry;
+
+/* Block sampling (Sec. 1: W_k i.i.d. uniform over M selectors).
+ *   kind   SLIM_BLOCKS_VIEWS: one view per block, M = n_views, drawn uniformly
+ *          with replacement; ell must equal det_u
+ *   ell    rows per block
+ *   seed   generator seed; step k draws view bounded(draw(seed, 2, k-1), A_v) */
+typedef struct {
+  int kind;
+  int ell;
+  unsigned long long seed;
+  int reserved;
+} slim_blocks;
+
+/* Step options.
+ *   eta           extra step size multiplying s_k (1 = Eq. (ram))
+ *   ramp          1: lambda_k = lambda*(r+1)/k for k <= r+1 (the damping ramp of Sec. 4.2)
+ *   solver        SLIM_SOLVE_FP64: float64 tiled Cholesky and triangular solves;
+ *                 SLIM_SOLVE_MIXED: float32 tiled Cholesky of the same float64
+ *                 matrix, then `refine_iters` rounds of iterative refinement whose
+ *                 residual (lambda_k I + G) z is computed in float64
+ *   refine_iters  refinement rounds for SLIM_SOLVE_MIXED (0..16)
+ *   use_graph     1: capture one step as a CUDA graph at the first slim_step and
+ *                 replay it (one graph launch per step) */
+typedef struct {
+  double eta;
+  int ramp;
+  int solver;
+  int refine_iters;
+  int use_graph;
+} slim_step_opts;
+
+/* Create a context: validates the arguments and allocates all device state
+ * (x, b, the ring of r+1 blocks, G and its factor).  r is the memory of
+ * Eq. (B_k) (M_k holds r+1 blocks), lambda > 0 the damping 1/alpha.
+ * `step` may be NULL (eta 1, no ramp, FP64 solver, no graph).
+ * On success *out owns the context; release it with slim_destroy. */
+slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, int r,
+                        double lambda, const slim_step_opts* step, slim_ctx** out);
+
+/* Release every resource of the context (NULL is a no-op). */
+void slim_destroy(slim_ctx* ctx);
+
+/* Human-readable text of the last error on this context (never NULL). */
+const char* slim_last_error(const slim_ctx* ctx);
+
+/* Run subsequent work on `cuda_stream` (a cudaStream_t; NULL = the context's own). */
+slim_status slim_set_stream(slim_ctx* ctx, void* cuda_stream);
+
+/* b (Eq. inverseproblem), m = n_views*det_u values, copied (converted to the
+ * context precision).  Must precede slim_step. */
+slim_status slim_set_data(slim_ctx* ctx, const void* b, size_t m, int dtype, int on_device);
+
+/* x_0 (default 0), n values, copied.  Does not change the step counter. */
+slim_status slim_set_x(slim_ctx* ctx, const void* x, size_t n, int dtype, int on_device);
+
+/* Copy the current iterate into the caller's buffer (synchronises; returns
+ * any device-side error recorded since the last synchronising call). */
+slim_status slim_get_x(slim_ctx* ctx, void* x, size_t n, int dtype, int on_device);
+
+/* Enqueue nsteps iterations of Eq. (ram) on the context stream (asynchronous). */
+slim_status slim_step(slim_ctx* ctx, int nsteps);
+
+/* Per-phase timing (tracing).  With on = 1 every step records CUDA events at
+ * its phase boundaries (also inside a captured graph); slim_get_timing then
+ * returns the device milliseconds of the last step's phases, in order:
+ * sample, forward+residual, Gram update, K = lambda I + G, factorisation,
+ * triangular solves (with refinement), scatter (nphase <= 7).  *kernels
+ * receives the number of kernels one step launches.  SLIM_ESTATE if timing
+ * is off and phase_ms is not NULL. */
+slim_status slim_set_timing(slim_ctx* ctx, int on);
+slim_status slim_get_timing(slim_ctx* ctx, double* phase_ms, int nphase, int* kernels);
+
+/* Wait for queued work and return the device status. */
+slim_status slim_sync(slim_ctx* ctx);
+
+/* Reference iterate for slim_run's error metric ||x - x_ref|| / ||x_ref||
+ * (host or device array of n values).  NULL clears it. */
+slim_status slim_set_ref(slim_ctx* ctx, const void* x_ref, size_t n, int dtype, int on_device);
+
+/* Step until the relative error to the reference is <= tol (checked every
+ * eval_every steps) or max_steps steps were taken.  Reports steps taken,
+ * device seconds spent stepping (CUDA events; error evaluation excluded) and
+ * the last evaluated error (-1 if no reference is set). */
+slim_status slim_run(slim_ctx* ctx, long long max_steps, double tol, int eval_every,
+                     long long* steps_done, double* seconds, double* final_err);
+
+/* Number of steps taken so far (k). */
+slim_status slim_get_iter(const slim_ctx* ctx, long long* k);
+
+/* Jump to the state after k steps: the memory is rebuilt from the sampled
+ * blocks tau_{max(1,k-r)}..tau_k and the current x is kept.  Used by
+ * slim_restore and to align the device with an externally computed iterate. */
+slim_status slim_set_iter(slim_ctx* ctx, long long k);
+
+/* Checkpoint: k and x.  With buf == NULL, *len receives the size needed. */
+slim_status slim_checkpoint(slim_ctx* ctx, void* buf, size_t* len);
+slim_status slim_restore(slim_ctx* ctx, const void* buf, size_t len);
+
+/* Memory of the last step, for inspection: ray ids of the ring (p ints, -1
+ * for empty slots), the Gram matrix G = M_k M_k^T in ring order (p*p doubles,
+ * row-major) and the last solution z (p doubles).  Host pointers; any may be NULL. */
+slim_status slim_get_memory(slim_ctx* ctx, int* ray_ids, double* G, double* z);
+
+/* Sizes: n unknowns, m rows, p = (r+1)*ell. */
+slim_status slim_get_sizes(const slim_ctx* ctx, long long* n, long long* m, int* p);
+
+/* Forward projection y = A_S x for the rays listed in ray_ids (device array of
+ * count ints; NULL = all m rays in order).  x and y are device arrays of the
+ * context precision.  Enqueued on the context stream. */
+slim_status slim_project(slim_ctx* ctx, const int* ray_ids, int count, const void* x, void* y);
+
+/* Back projection x += A_S^T y for the listed rays (device arrays as above). */
+slim_status slim_backproject(slim_ctx* ctx, const int* ray_ids, int count, const void* y,
+                             void* x);
+
+/* Damped Gram solve (lambda I + G) z = rhs for a symmetric positive definite
+ * G (the inner solve of the Woodbury form of Eq. (B_k)).  G: device array
+ * p*p doubles, row-major, lower triangle read; rhs, z: device arrays of p
+ * doubles.  Float64 tiled Cholesky and triangular solves.  Allocates its
+ * factor storage on each call and synchronises `cuda_stream` before returning.
+ * Returns SLIM_ENOTPD on a non-positive pivot. */
+slim_status slim_damped_solve(const double* G, int p, double lambda, const double* rhs,
+                              double* z, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLIM_H_ */

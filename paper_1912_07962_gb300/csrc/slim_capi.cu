@@ -1,0 +1,789 @@
+// C ABI of libslim.so: context management and the step driver.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/slim.h"
+#include "slim_chol.cuh"
+#include "slim_kernels.cuh"
+
+using namespace slim;
+
+struct slim_ctx {
+  // configuration
+  int N = 0, n_views = 0, D = 0;
+  long long n = 0, m = 0;
+  int precision = SLIM_PREC_FP64, solver = SLIM_SOLVE_FP64, refine_iters = 2, use_graph = 0;
+  int ramp = 0, r = 0, nslots = 1, ell = 0, p = 0, P = 0, taps = 0, nb = 32;
+  double lam = 0.0, eta = 1.0;
+  unsigned long long seed = 0;
+  std::vector<ViewGeom> h_views;
+  // device state
+  ViewGeom* d_views = nullptr;
+  StepInfo* d_info = nullptr;
+  long long* d_done = nullptr;
+  int* d_status = nullptr;
+  void* d_x = nullptr;
+  void* d_b = nullptr;
+  int* d_ring_ids = nullptr;
+  int* d_ring_pix = nullptr;
+  double* d_ring_w = nullptr;
+  int* d_map_ray = nullptr;
+  double* d_map_w = nullptr;
+  double* d_G = nullptr;
+  void* d_L = nullptr;
+  double* d_rhs = nullptr;
+  double* d_z = nullptr;
+  double* d_dz = nullptr;
+  double* d_res = nullptr;
+  double* d_ref = nullptr;
+  double* d_err = nullptr;
+  CholPlan plan;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  bool has_data = false;
+  long long h_k = 0;
+  int num_sms = 0;
+  bool timing = false;
+  bool capturing = false;
+  cudaEvent_t ev[8] = {};
+  std::string err;
+};
+
+namespace {
+
+size_t elem(int precision) { return precision == SLIM_PREC_FP32 ? sizeof(float) : sizeof(double); }
+
+slim_status fail(slim_ctx* c, slim_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+slim_status cuda_fail(slim_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  if (c) c->err = m;
+  return e == cudaErrorMemoryAllocation ? SLIM_ENOMEM : SLIM_ECUDA;
+}
+
+#define CK(call, where)                                    \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+  } while (0)
+
+template <typename TI, typename TO>
+__global__ void convert_kernel(const TI* in, TO* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (TO)in[i];
+}
+
+// Copy n values of dtype `src_dtype` (host or device) into a device array of
+// precision `dst_prec`, converting if needed.
+cudaError_t copy_in(void* dst, int dst_f32, const void* src, int src_dtype, int on_device,
+                    long long n, cudaStream_t s) {
+  const bool same = (src_dtype == SLIM_F32) == (dst_f32 != 0);
+  const size_t sb = src_dtype == SLIM_F32 ? 4 : 8;
+  if (same)
+    return cudaMemcpyAsync(dst, src, n * sb, on_device ? cudaMemcpyDeviceToDevice
+                                                       : cudaMemcpyHostToDevice, s);
+  const void* dsrc = src;
+  void* tmp = nullptr;
+  cudaError_t e;
+  if (!on_device) {
+    if ((e = cudaMallocAsync(&tmp, n * sb, s)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(tmp, src, n * sb, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+    dsrc = tmp;
+  }
+  int grid = (int)std::min<long long>((n + 255) / 256, 4096);
+  if (grid < 1) grid = 1;
+  if (src_dtype == SLIM_F32)
+    convert_kernel<float, double><<<grid, 256, 0, s>>>((const float*)dsrc, (double*)dst, n);
+  else
+    convert_kernel<double, float><<<grid, 256, 0, s>>>((const double*)dsrc, (float*)dst, n);
+  e = cudaGetLastError();
+  if (tmp) cudaFreeAsync(tmp, s);
+  return e;
+}
+
+cudaError_t copy_out(void* dst, int dst_dtype, int on_device, const void* src, int src_f32,
+                     long long n, cudaStream_t s) {
+  const bool same = (dst_dtype == SLIM_F32) == (src_f32 != 0);
+  const size_t db = dst_dtype == SLIM_F32 ? 4 : 8;
+  if (same) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, n * db, on_device ? cudaMemcpyDeviceToDevice
+                                                                : cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+  }
+  void* ddst = dst;
+  void* tmp = nullptr;
+  cudaError_t e;
+  if (!on_device) {
+    if ((e = cudaMallocAsync(&tmp, n * db, s)) != cudaSuccess) return e;
+    ddst = tmp;
+  }
+  int grid = (int)std::min<long long>((n + 255) / 256, 4096);
+  if (grid < 1) grid = 1;
+  if (src_f32)
+    convert_kernel<float, double><<<grid, 256, 0, s>>>((const float*)src, (double*)ddst, n);
+  else
+    convert_kernel<double, float><<<grid, 256, 0, s>>>((const double*)src, (float*)ddst, n);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (tmp) {
+    if ((e = cudaMemcpyAsync(dst, tmp, n * db, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    cudaFreeAsync(tmp, s);
+  }
+  return cudaStreamSynchronize(s);
+}
+
+template <typename T>
+StepArgs<T> make_args(slim_ctx* c) {
+  StepArgs<T> a;
+  a.info = c->d_info;
+  a.done = c->d_done;
+  a.views = c->d_views;
+  a.N = c->N;
+  a.D = c->D;
+  a.n_views = c->n_views;
+  a.n = c->n;
+  a.m = c->m;
+  a.ell = c->ell;
+  a.nslots = c->nslots;
+  a.r = c->r;
+  a.P = c->P;
+  a.p = c->p;
+  a.taps = c->taps;
+  a.seed = c->seed;
+  a.lam = c->lam;
+  a.eta = c->eta;
+  a.ramp = c->ramp;
+  a.ring_ids = c->d_ring_ids;
+  a.ring_pix = c->d_ring_pix;
+  a.ring_w = c->d_ring_w;
+  a.map_ray = c->d_map_ray;
+  a.map_w = c->d_map_w;
+  a.G = c->d_G;
+  a.rhs = c->d_rhs;
+  a.z = c->d_z;
+  a.x = (T*)c->d_x;
+  a.b = (const T*)c->d_b;
+  a.status = c->d_status;
+  return a;
+}
+
+// Phase boundaries recorded when timing is on (event i closes phase i-1).
+enum { kPhSample = 1, kPhForward, kPhGram, kPhFormK, kPhFactor, kPhSolve, kPhScatter };
+
+// External event records stay real event records inside a captured graph, so
+// they can be timed with cudaEventElapsedTime after each replay.
+cudaError_t mark(slim_ctx* c, int i) {
+  if (!c->timing) return cudaSuccess;
+  if (c->capturing) return cudaEventRecordWithFlags(c->ev[i], c->stream, cudaEventRecordExternal);
+  return cudaEventRecord(c->ev[i], c->stream);
+}
+
+// Kernels one step launches (sample, forward, Gram, K, factor, 2 per solve,
+// 2 per refinement round, scatter).
+int kernels_per_step(const slim_ctx* c) {
+  int solves = c->solver == SLIM_SOLVE_MIXED ? 1 + c->refine_iters : 1;
+  int refine = c->solver == SLIM_SOLVE_MIXED ? 2 * c->refine_iters : 0;
+  return 5 + 2 * solves + refine + 1;
+}
+
+// The damped solve (lambda_k I + G) z = rhs: float64 tiled Cholesky, or a
+// float32 factor refined with float64 residuals.
+cudaError_t enqueue_solve(slim_ctx* c) {
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  if (c->solver == SLIM_SOLVE_FP64) {
+    if ((e = launch_form_k<double>(c->d_info, c->d_G, (double*)c->d_L, c->P, s)) != cudaSuccess)
+      return e;
+    if ((e = mark(c, kPhFormK)) != cudaSuccess) return e;
+    if ((e = chol_factor(c->plan, c->d_L, c->d_status, s)) != cudaSuccess) return e;
+    if ((e = mark(c, kPhFactor)) != cudaSuccess) return e;
+    return chol_solve(c->plan, c->d_L, c->d_rhs, c->d_z, c->d_status, s);
+  }
+  if ((e = launch_form_k<float>(c->d_info, c->d_G, (float*)c->d_L, c->P, s)) != cudaSuccess)
+    return e;
+  if ((e = mark(c, kPhFormK)) != cudaSuccess) return e;
+  if ((e = chol_factor(c->plan, c->d_L, c->d_status, s)) != cudaSuccess) return e;
+  if ((e = mark(c, kPhFactor)) != cudaSuccess) return e;
+  if ((e = chol_solve(c->plan, c->d_L, c->d_rhs, c->d_z, c->d_status, s)) != cudaSuccess) return e;
+  for (int it = 0; it < c->refine_iters; ++it) {
+    if ((e = launch_refine_residual(c->d_info, c->d_G, c->d_z, c->d_rhs, c->d_res, c->P, s)) !=
+        cudaSuccess)
+      return e;
+    if ((e = chol_solve(c->plan, c->d_L, c->d_res, c->d_dz, c->d_status, s)) != cudaSuccess)
+      return e;
+    if ((e = launch_axpy(c->d_z, c->d_dz, c->P, s)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t enqueue_step_t(slim_ctx* c) {
+  StepArgs<T> a = make_args<T>(c);
+  cudaError_t e;
+  if ((e = mark(c, 0)) != cudaSuccess) return e;
+  if ((e = launch_sample<T>(a, c->stream)) != cudaSuccess) return e;
+  if ((e = mark(c, kPhSample)) != cudaSuccess) return e;
+  if ((e = launch_forward_residual<T>(a, c->stream)) != cudaSuccess) return e;
+  if ((e = mark(c, kPhForward)) != cudaSuccess) return e;
+  if ((e = launch_gram_update<T>(a, c->stream)) != cudaSuccess) return e;
+  if ((e = mark(c, kPhGram)) != cudaSuccess) return e;
+  if ((e = enqueue_solve(c)) != cudaSuccess) return e;
+  if ((e = mark(c, kPhSolve)) != cudaSuccess) return e;
+  if ((e = launch_scatter<T>(a, c->stream)) != cudaSuccess) return e;
+  return mark(c, kPhScatter);
+}
+
+cudaError_t enqueue_step(slim_ctx* c) {
+  return c->precision == SLIM_PREC_FP32 ? enqueue_step_t<float>(c) : enqueue_step_t<double>(c);
+}
+
+// Rebuild the memory for the state after k steps (no change to x).
+template <typename T>
+cudaError_t rebuild_t(slim_ctx* c, long long k) {
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(c->d_ring_ids, 0xFF, (size_t)c->p * sizeof(int), s)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemsetAsync(c->d_G, 0, (size_t)c->P * c->P * sizeof(double), s)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemsetAsync(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int), s)) != cudaSuccess)
+    return e;
+  StepArgs<T> a = make_args<T>(c);
+  long long j0 = k - c->r;
+  if (j0 < 1) j0 = 1;
+  for (long long j = j0; j <= k; ++j) {
+    long long done = j - 1;
+    if ((e = cudaMemcpyAsync(c->d_done, &done, sizeof(done), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;   // `done` is a host local
+    if ((e = launch_sample<T>(a, s)) != cudaSuccess) return e;
+    if ((e = launch_forward_residual<T>(a, s)) != cudaSuccess) return e;
+    if ((e = launch_gram_update<T>(a, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int), s)) !=
+        cudaSuccess)
+      return e;
+  }
+  long long done = k;
+  if ((e = cudaMemcpyAsync(c->d_done, &done, sizeof(done), cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return e;
+  return cudaStreamSynchronize(s);
+}
+
+slim_status read_status(slim_ctx* c) {
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "status");
+  if (st != 0) {
+    int zero = 0;
+    cudaMemcpy(c->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    switch (st) {
+      case SLIM_ENOTPD: return fail(c, SLIM_ENOTPD, "lambda_k I + G is not positive definite");
+      case SLIM_ETIMEOUT: return fail(c, SLIM_ETIMEOUT, "a bounded device wait ran out");
+      case SLIM_EINVAL:
+        return fail(c, SLIM_EINVAL, "a pixel is tapped by more than two rays of one view");
+      default: return fail(c, (slim_status)st, "device error");
+    }
+  }
+  return SLIM_OK;
+}
+
+void free_all(slim_ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  void* ptrs[] = {c->d_views, c->d_info, c->d_done, c->d_status, c->d_x, c->d_b,
+                  c->d_ring_ids, c->d_ring_pix, c->d_ring_w, c->d_map_ray, c->d_map_w,
+                  c->d_G, c->d_L, c->d_rhs, c->d_z, c->d_dz, c->d_res, c->d_ref, c->d_err};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  chol_plan_destroy(&c->plan);
+  for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+void drop_graph(slim_ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, int r, double lambda,
+                        const slim_step_opts* step, slim_ctx** out) {
+  if (!out) return SLIM_EINVAL;
+  *out = nullptr;
+  if (!geom || !blocks) return SLIM_EINVAL;
+  if (geom->dim != 2 || geom->det_v != 1) return SLIM_ENOTSUP;
+  if (geom->a_mode != 0) return SLIM_ENOTSUP;
+  if (geom->n_side < 2 || geom->n_side > 16384 || geom->n_views < 1 || geom->det_u < 1)
+    return SLIM_EINVAL;
+  if (geom->precision != SLIM_PREC_FP64 && geom->precision != SLIM_PREC_FP32) return SLIM_EINVAL;
+  if (blocks->kind != SLIM_BLOCKS_VIEWS) return SLIM_ENOTSUP;
+  if (blocks->ell != geom->det_u) return SLIM_EINVAL;
+  if (r < 0 || !(lambda > 0.0) || !std::isfinite(lambda)) return SLIM_EINVAL;
+  slim_ctx* c = new (std::nothrow) slim_ctx();
+  if (!c) return SLIM_ENOMEM;
+  c->N = geom->n_side;
+  c->n_views = geom->n_views;
+  c->D = geom->det_u;
+  c->n = (long long)c->N * c->N;
+  c->m = (long long)c->n_views * c->D;
+  c->precision = geom->precision;
+  c->r = r;
+  c->nslots = r + 1;
+  c->ell = blocks->ell;
+  c->seed = blocks->seed;
+  c->lam = lambda;
+  c->p = c->nslots * c->ell;
+  c->taps = 2 * c->N;
+  if (step) {
+    c->eta = step->eta;
+    c->ramp = step->ramp;
+    c->solver = step->solver;
+    c->refine_iters = step->refine_iters;
+    c->use_graph = step->use_graph;
+    if (!(c->eta > 0.0) || (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED) ||
+        c->refine_iters < 0 || c->refine_iters > 16) {
+      delete c;
+      return SLIM_EINVAL;
+    }
+  }
+  if (c->m > 0x7fffffffLL || c->n > 0x7fffffffLL || (long long)c->p * c->p > (1LL << 33)) {
+    delete c;
+    return SLIM_EINVAL;
+  }
+  c->nb = c->solver == SLIM_SOLVE_FP64 ? 32 : 64;
+  c->P = (c->p + c->nb - 1) / c->nb * c->nb;
+  // geometry tables: host libm cos/sin, row-stepping iff |cos| >= |sin|
+  c->h_views.resize(c->n_views);
+  for (int a = 0; a < c->n_views; ++a) {
+    double th = geom->angles ? geom->angles[a] : a * M_PI / c->n_views;
+    ViewGeom v;
+    v.co = std::cos(th);
+    v.si = std::sin(th);
+    v.row_step = std::fabs(v.co) >= std::fabs(v.si) ? 1 : 0;
+    v.rc = 1.0 / (v.row_step ? v.co : v.si);
+    v.ia = std::fabs(v.rc);
+    v.pad_ = 0;
+    c->h_views[a] = v;
+  }
+  slim_status st = SLIM_OK;
+  auto chk = [&](cudaError_t e, const char* w) {
+    if (e != cudaSuccess && st == SLIM_OK) st = cuda_fail(c, e, w);
+    return e == cudaSuccess;
+  };
+  int dev = 0;
+  chk(cudaGetDevice(&dev), "cudaGetDevice");
+  chk(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
+  if (st == SLIM_OK && chk(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream"))
+    c->own_stream = true;
+  const size_t es = elem(c->precision);
+  const size_t fs = c->solver == SLIM_SOLVE_FP64 ? sizeof(double) : sizeof(float);
+  struct { void** p; size_t bytes; } allocs[] = {
+      {(void**)&c->d_views, c->h_views.size() * sizeof(ViewGeom)},
+      {(void**)&c->d_info, sizeof(StepInfo)},
+      {(void**)&c->d_done, sizeof(long long)},
+      {(void**)&c->d_status, sizeof(int)},
+      {&c->d_x, (size_t)c->n * es},
+      {&c->d_b, (size_t)c->m * es},
+      {(void**)&c->d_ring_ids, (size_t)c->p * sizeof(int)},
+      {(void**)&c->d_ring_pix, (size_t)c->p * c->taps * sizeof(int)},
+      {(void**)&c->d_ring_w, (size_t)c->p * c->taps * sizeof(double)},
+      {(void**)&c->d_map_ray, 2 * (size_t)c->n * sizeof(int)},
+      {(void**)&c->d_map_w, 2 * (size_t)c->n * sizeof(double)},
+      {(void**)&c->d_G, (size_t)c->P * c->P * sizeof(double)},
+      {&c->d_L, (size_t)c->P * c->P * fs},
+      {(void**)&c->d_rhs, (size_t)c->P * sizeof(double)},
+      {(void**)&c->d_z, (size_t)c->P * sizeof(double)},
+      {(void**)&c->d_dz, (size_t)c->P * sizeof(double)},
+      {(void**)&c->d_res, (size_t)c->P * sizeof(double)},
+      {(void**)&c->d_err, 2 * sizeof(double)},
+  };
+  for (auto& al : allocs)
+    if (st == SLIM_OK) chk(cudaMalloc(al.p, al.bytes), "cudaMalloc");
+  if (st == SLIM_OK) {
+    chk(cudaMemcpy(c->d_views, c->h_views.data(), c->h_views.size() * sizeof(ViewGeom),
+                   cudaMemcpyHostToDevice), "views");
+    chk(cudaMemset(c->d_done, 0, sizeof(long long)), "memset");
+    chk(cudaMemset(c->d_status, 0, sizeof(int)), "memset");
+    chk(cudaMemset(c->d_x, 0, (size_t)c->n * es), "memset");
+    chk(cudaMemset(c->d_b, 0, (size_t)c->m * es), "memset");
+    chk(cudaMemset(c->d_ring_ids, 0xFF, (size_t)c->p * sizeof(int)), "memset");
+    chk(cudaMemset(c->d_ring_pix, 0xFF, (size_t)c->p * c->taps * sizeof(int)), "memset");
+    chk(cudaMemset(c->d_ring_w, 0, (size_t)c->p * c->taps * sizeof(double)), "memset");
+    chk(cudaMemset(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int)), "memset");
+    chk(cudaMemset(c->d_G, 0, (size_t)c->P * c->P * sizeof(double)), "memset");
+    chk(cudaMemset(c->d_L, 0, (size_t)c->P * c->P * fs), "memset");
+    chk(cudaMemset(c->d_z, 0, (size_t)c->P * sizeof(double)), "memset");
+    chk(chol_plan_create(&c->plan, c->P, c->nb, c->solver == SLIM_SOLVE_MIXED ? 1 : 0, c->num_sms),
+        "chol plan");
+    size_t gsmem = 8 * (size_t)c->ell * sizeof(double);
+    if (gsmem > 200 * 1024) st = fail(c, SLIM_ENOTSUP, "ell too large for the Gram kernel");
+  }
+  if (st != SLIM_OK) {
+    std::string msg = c->err;
+    free_all(c);
+    delete c;
+    fprintf(stderr, "slim_create: %s\n", msg.c_str());
+    return st;
+  }
+  *out = c;
+  return SLIM_OK;
+}
+
+void slim_destroy(slim_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+const char* slim_last_error(const slim_ctx* c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+slim_status slim_set_stream(slim_ctx* c, void* stream) {
+  if (!c) return SLIM_EINVAL;
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  c->own_stream = false;
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream");
+    c->own_stream = true;
+  }
+  drop_graph(c);
+  return SLIM_OK;
+}
+
+slim_status slim_set_timing(slim_ctx* c, int on) {
+  if (!c) return SLIM_EINVAL;
+  if (on && !c->ev[0])
+    for (cudaEvent_t& e : c->ev) CK(cudaEventCreate(&e), "event");
+  if ((on != 0) != c->timing) {
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    drop_graph(c);   // the captured step changes with the event records
+  }
+  c->timing = on != 0;
+  return SLIM_OK;
+}
+
+slim_status slim_get_timing(slim_ctx* c, double* phase_ms, int nphase, int* kernels) {
+  if (!c) return SLIM_EINVAL;
+  if (kernels) *kernels = kernels_per_step(c);
+  if (!phase_ms) return SLIM_OK;
+  if (!c->timing || nphase < 1 || nphase > 7) return fail(c, SLIM_ESTATE, "timing is off");
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  for (int i = 0; i < nphase; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]), "elapsed");
+    phase_ms[i] = ms;
+  }
+  return SLIM_OK;
+}
+
+slim_status slim_set_data(slim_ctx* c, const void* b, size_t m, int dtype, int on_device) {
+  if (!c || !b || (long long)m != c->m || (dtype != SLIM_F32 && dtype != SLIM_F64))
+    return fail(c, SLIM_EINVAL, "set_data: bad arguments");
+  CK(copy_in(c->d_b, c->precision == SLIM_PREC_FP32, b, dtype, on_device, c->m, c->stream),
+     "set_data");
+  CK(cudaStreamSynchronize(c->stream), "set_data");
+  c->has_data = true;
+  return SLIM_OK;
+}
+
+slim_status slim_set_x(slim_ctx* c, const void* x, size_t n, int dtype, int on_device) {
+  if (!c || !x || (long long)n != c->n || (dtype != SLIM_F32 && dtype != SLIM_F64))
+    return fail(c, SLIM_EINVAL, "set_x: bad arguments");
+  CK(copy_in(c->d_x, c->precision == SLIM_PREC_FP32, x, dtype, on_device, c->n, c->stream),
+     "set_x");
+  CK(cudaStreamSynchronize(c->stream), "set_x");
+  return SLIM_OK;
+}
+
+slim_status slim_get_x(slim_ctx* c, void* x, size_t n, int dtype, int on_device) {
+  if (!c || !x || (long long)n != c->n || (dtype != SLIM_F32 && dtype != SLIM_F64))
+    return fail(c, SLIM_EINVAL, "get_x: bad arguments");
+  CK(copy_out(x, dtype, on_device, c->d_x, c->precision == SLIM_PREC_FP32, c->n, c->stream),
+     "get_x");
+  return read_status(c);
+}
+
+slim_status slim_step(slim_ctx* c, int nsteps) {
+  if (!c || nsteps < 0) return fail(c, SLIM_EINVAL, "step: bad arguments");
+  if (!c->has_data) return fail(c, SLIM_ESTATE, "step before slim_set_data");
+  if (c->use_graph) {
+    if (!c->graph_exec) {
+      CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
+      c->capturing = true;
+      cudaError_t e = enqueue_step(c);
+      c->capturing = false;
+      cudaGraph_t g = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+      if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, e, "capture step");
+      }
+      CK(e2, "end capture");
+      c->graph = g;
+      CK(cudaGraphInstantiate(&c->graph_exec, g, 0), "instantiate");
+    }
+    for (int i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(c->graph_exec, c->stream), "graph launch");
+  } else {
+    for (int i = 0; i < nsteps; ++i) CK(enqueue_step(c), "step");
+  }
+  c->h_k += nsteps;
+  return SLIM_OK;
+}
+
+slim_status slim_sync(slim_ctx* c) {
+  if (!c) return SLIM_EINVAL;
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  return read_status(c);
+}
+
+slim_status slim_set_ref(slim_ctx* c, const void* x_ref, size_t n, int dtype, int on_device) {
+  if (!c) return SLIM_EINVAL;
+  if (!x_ref) {
+    if (c->d_ref) cudaFree(c->d_ref);
+    c->d_ref = nullptr;
+    return SLIM_OK;
+  }
+  if ((long long)n != c->n || (dtype != SLIM_F32 && dtype != SLIM_F64))
+    return fail(c, SLIM_EINVAL, "set_ref: bad arguments");
+  if (!c->d_ref) CK(cudaMalloc(&c->d_ref, (size_t)c->n * sizeof(double)), "set_ref");
+  CK(copy_in(c->d_ref, 0, x_ref, dtype, on_device, c->n, c->stream), "set_ref");
+  CK(cudaStreamSynchronize(c->stream), "set_ref");
+  return SLIM_OK;
+}
+
+static slim_status eval_err(slim_ctx* c, double* err) {
+  CK(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(double), c->stream), "err");
+  if (c->precision == SLIM_PREC_FP32)
+    CK(launch_rel_err<float>((const float*)c->d_x, c->d_ref, c->n, c->d_err, c->stream), "err");
+  else
+    CK(launch_rel_err<double>((const double*)c->d_x, c->d_ref, c->n, c->d_err, c->stream), "err");
+  double h[2];
+  CK(cudaMemcpyAsync(h, c->d_err, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "err");
+  CK(cudaStreamSynchronize(c->stream), "err");
+  *err = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+  return SLIM_OK;
+}
+
+slim_status slim_run(slim_ctx* c, long long max_steps, double tol, int eval_every,
+                     long long* steps_done, double* seconds, double* final_err) {
+  if (!c || max_steps < 0 || eval_every < 1) return fail(c, SLIM_EINVAL, "run: bad arguments");
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "event");
+  CK(cudaEventCreate(&e1), "event");
+  long long done = 0;
+  double total_ms = 0.0, err = -1.0;
+  slim_status st = SLIM_OK;
+  while (done < max_steps) {
+    int nb = (int)std::min<long long>(eval_every, max_steps - done);
+    cudaEventRecord(e0, c->stream);
+    if ((st = slim_step(c, nb)) != SLIM_OK) break;
+    cudaEventRecord(e1, c->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) { st = cuda_fail(c, e, "run"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    total_ms += ms;
+    done += nb;
+    if ((st = read_status(c)) != SLIM_OK) break;
+    if (c->d_ref) {
+      if ((st = eval_err(c, &err)) != SLIM_OK) break;
+      if (err <= tol) break;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (steps_done) *steps_done = done;
+  if (seconds) *seconds = total_ms * 1e-3;
+  if (final_err) *final_err = err;
+  return st;
+}
+
+slim_status slim_get_iter(const slim_ctx* c, long long* k) {
+  if (!c || !k) return SLIM_EINVAL;
+  *k = c->h_k;
+  return SLIM_OK;
+}
+
+slim_status slim_set_iter(slim_ctx* c, long long k) {
+  if (!c || k < 0) return fail(c, SLIM_EINVAL, "set_iter: bad arguments");
+  cudaError_t e = c->precision == SLIM_PREC_FP32 ? rebuild_t<float>(c, k) : rebuild_t<double>(c, k);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set_iter");
+  c->h_k = k;
+  return read_status(c);
+}
+
+namespace {
+struct CkptHeader {
+  char magic[8];
+  long long k, n;
+  int precision, version;
+};
+}  // namespace
+
+slim_status slim_checkpoint(slim_ctx* c, void* buf, size_t* len) {
+  if (!c || !len) return SLIM_EINVAL;
+  size_t need = sizeof(CkptHeader) + (size_t)c->n * elem(c->precision);
+  if (!buf) {
+    *len = need;
+    return SLIM_OK;
+  }
+  if (*len < need) return fail(c, SLIM_EINVAL, "checkpoint buffer too small");
+  CkptHeader h;
+  memcpy(h.magic, "SLIMCKP1", 8);
+  h.k = c->h_k;
+  h.n = c->n;
+  h.precision = c->precision;
+  h.version = 1;
+  memcpy(buf, &h, sizeof(h));
+  CK(cudaMemcpyAsync((char*)buf + sizeof(h), c->d_x, (size_t)c->n * elem(c->precision),
+                     cudaMemcpyDeviceToHost, c->stream), "checkpoint");
+  CK(cudaStreamSynchronize(c->stream), "checkpoint");
+  *len = need;
+  return read_status(c);
+}
+
+slim_status slim_restore(slim_ctx* c, const void* buf, size_t len) {
+  if (!c || !buf || len < sizeof(CkptHeader)) return fail(c, SLIM_EINVAL, "restore: bad buffer");
+  CkptHeader h;
+  memcpy(&h, buf, sizeof(h));
+  if (memcmp(h.magic, "SLIMCKP1", 8) != 0 || h.version != 1 || h.n != c->n ||
+      h.precision != c->precision || h.k < 0 ||
+      len != sizeof(CkptHeader) + (size_t)c->n * elem(c->precision))
+    return fail(c, SLIM_EINVAL, "restore: checkpoint does not match this context");
+  CK(cudaMemcpyAsync(c->d_x, (const char*)buf + sizeof(h), (size_t)c->n * elem(c->precision),
+                     cudaMemcpyHostToDevice, c->stream), "restore");
+  return slim_set_iter(c, h.k);
+}
+
+slim_status slim_get_memory(slim_ctx* c, int* ids, double* G, double* z) {
+  if (!c) return SLIM_EINVAL;
+  CK(cudaStreamSynchronize(c->stream), "get_memory");
+  if (ids) CK(cudaMemcpy(ids, c->d_ring_ids, (size_t)c->p * sizeof(int), cudaMemcpyDeviceToHost),
+              "get_memory");
+  if (G) CK(cudaMemcpy2D(G, (size_t)c->p * sizeof(double), c->d_G, (size_t)c->P * sizeof(double),
+                         (size_t)c->p * sizeof(double), c->p, cudaMemcpyDeviceToHost),
+            "get_memory");
+  if (z) CK(cudaMemcpy(z, c->d_z, (size_t)c->p * sizeof(double), cudaMemcpyDeviceToHost),
+            "get_memory");
+  return read_status(c);
+}
+
+slim_status slim_get_sizes(const slim_ctx* c, long long* n, long long* m, int* p) {
+  if (!c) return SLIM_EINVAL;
+  if (n) *n = c->n;
+  if (m) *m = c->m;
+  if (p) *p = c->p;
+  return SLIM_OK;
+}
+
+slim_status slim_project(slim_ctx* c, const int* ids, int count, const void* x, void* y) {
+  if (!c || !x || !y) return fail(c, SLIM_EINVAL, "project: bad arguments");
+  if (!ids) count = (int)c->m;
+  if (count < 0) return fail(c, SLIM_EINVAL, "project: bad count");
+  if (c->precision == SLIM_PREC_FP32)
+    CK(launch_project<float>(c->d_views, c->N, c->D, ids, count, (const float*)x, (float*)y,
+                             c->stream), "project");
+  else
+    CK(launch_project<double>(c->d_views, c->N, c->D, ids, count, (const double*)x, (double*)y,
+                              c->stream), "project");
+  return SLIM_OK;
+}
+
+slim_status slim_backproject(slim_ctx* c, const int* ids, int count, const void* y, void* x) {
+  if (!c || !x || !y) return fail(c, SLIM_EINVAL, "backproject: bad arguments");
+  if (!ids) count = (int)c->m;
+  if (count < 0) return fail(c, SLIM_EINVAL, "backproject: bad count");
+  if (c->precision == SLIM_PREC_FP32)
+    CK(launch_backproject<float>(c->d_views, c->N, c->D, ids, count, (const float*)y, (float*)x,
+                                 c->stream), "backproject");
+  else
+    CK(launch_backproject<double>(c->d_views, c->N, c->D, ids, count, (const double*)y,
+                                  (double*)x, c->stream), "backproject");
+  return SLIM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+__global__ void damped_form_kernel(const double* G, int p, double lam, double* L, int P) {
+  long long total = (long long)P * P;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(idx / P), j = (int)(idx % P);
+    double v = 0.0;
+    if (i < p && j < p) v = G[(size_t)i * p + j] + (i == j ? lam : 0.0);
+    else if (i == j) v = 1.0;
+    L[idx] = v;
+  }
+}
+}  // namespace
+
+extern "C" slim_status slim_damped_solve(const double* G, int p, double lambda, const double* rhs,
+                                         double* z, void* stream) {
+  if (!G || !rhs || !z || p <= 0 || p > 65536 || !(lambda >= 0.0)) return SLIM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = 32;
+  const int P = (p + nb - 1) / nb * nb;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SLIM_ECUDA;
+  CholPlan plan;
+  double *L = nullptr, *v = nullptr, *out = nullptr;
+  int* status = nullptr;
+  slim_status st = SLIM_OK;
+  cudaError_t e = chol_plan_create(&plan, P, nb, 0, sms);
+  if (e == cudaSuccess) e = cudaMalloc(&L, (size_t)P * P * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&v, (size_t)P * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&out, (size_t)P * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, (size_t)P * sizeof(double), s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(v, rhs, (size_t)p * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) {
+    int grid = (int)std::min<long long>(((long long)P * P + 255) / 256, 152LL * 16);
+    damped_form_kernel<<<grid, 256, 0, s>>>(G, p, lambda, L, P);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = chol_factor(plan, L, status, s);
+  if (e == cudaSuccess) e = chol_solve(plan, L, v, out, status, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(z, out, (size_t)p * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  int hs = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? SLIM_ENOMEM : SLIM_ECUDA;
+  else if (hs != 0) st = (slim_status)hs;
+  cudaFree(L);
+  cudaFree(v);
+  cudaFree(out);
+  cudaFree(status);
+  chol_plan_destroy(&plan);
+  return st;
+}

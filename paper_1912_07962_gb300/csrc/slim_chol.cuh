@@ -1,0 +1,49 @@
+// Tiled Cholesky factorisation and triangular solves of the damped Gram
+// matrix K = lambda_k I + M_k M_k^T (the p x p system that the Woodbury form
+// of Eq. (B_k) leaves to solve each step).
+#pragma once
+#include <cstdint>
+#include <vector>
+#include <cuda_runtime.h>
+
+namespace slim {
+
+// One task of the right-looking tiled factorisation.
+//   kPotrf (k):      factor diagonal tile (k,k) and form its inverse
+//   kTrsm  (i,k):    L_ik = A_ik L_kk^{-T}
+//   kUpd   (i,m,k):  A_im -= L_ik L_mk^T   (update from panel k)
+struct CholTask {
+  uint16_t type, i, m, k;
+};
+enum : uint16_t { kPotrf = 0, kTrsm = 1, kUpd = 2 };
+
+// Task list in a dependency-compatible order: every task depends only on
+// tasks earlier in the list, so CTAs that claim tasks through an atomic
+// ticket always make progress.
+std::vector<CholTask> build_chol_tasks(int T);
+
+struct CholPlan {
+  int P = 0;          // padded order (multiple of NB)
+  int T = 0;          // tiles per side
+  int nb = 0;         // tile size
+  int is_f32 = 0;     // factor precision
+  int ntasks = 0;
+  CholTask* d_tasks = nullptr;   // device task list
+  int* d_sync = nullptr;         // [T*T tile counters | T fwd flags | T bwd flags | 4 tickets]
+  void* d_winv = nullptr;        // T inverse diagonal tiles, NB*NB each (factor precision)
+  void* d_y = nullptr;           // forward-solve intermediate, P values (factor precision)
+  int grid = 0;                  // persistent CTAs for the factorisation
+};
+
+// Allocate / free the plan for order P (multiple of nb).
+cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_sms);
+void chol_plan_destroy(CholPlan* plan);
+
+// Factor L (P x P row-major, lower triangle holds K on entry, L on exit) in
+// the factor precision; then solve L L^T z = v (float64 vectors of length P).
+// Errors are recorded in *status (SLIM_ENOTPD, SLIM_ETIMEOUT).
+cudaError_t chol_factor(const CholPlan& plan, void* L, int* status, cudaStream_t s);
+cudaError_t chol_solve(const CholPlan& plan, const void* L, const double* v, double* z,
+                       int* status, cudaStream_t s);
+
+}  // namespace slim

@@ -1,0 +1,262 @@
+"""ctypes binding of libslim.so with the names of the C ABI (include/slim.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Device arrays are passed as torch CUDA tensors (their data_ptr()), host arrays
+as numpy arrays or CPU tensors.  Loading fails loudly when the library is
+missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libslim.so")
+
+SLIM_OK, SLIM_EINVAL, SLIM_ENOMEM, SLIM_ECUDA, SLIM_ENOTPD, SLIM_ETIMEOUT, SLIM_ESTATE, \
+    SLIM_ENOTSUP = range(8)
+STATUS_NAMES = ["SLIM_OK", "SLIM_EINVAL", "SLIM_ENOMEM", "SLIM_ECUDA", "SLIM_ENOTPD",
+                "SLIM_ETIMEOUT", "SLIM_ESTATE", "SLIM_ENOTSUP"]
+SLIM_F32, SLIM_F64 = 0, 1
+SLIM_PREC_FP64, SLIM_PREC_FP32 = 0, 1
+SLIM_SOLVE_FP64, SLIM_SOLVE_MIXED = 0, 1
+SLIM_BLOCKS_VIEWS = 0
+
+# every function the header declares (checked by the CPU test suite)
+EXPORTS = [
+    "slim_create", "slim_destroy", "slim_last_error", "slim_set_stream", "slim_set_data",
+    "slim_set_x", "slim_get_x", "slim_step", "slim_sync", "slim_set_ref", "slim_run",
+    "slim_get_iter", "slim_set_iter", "slim_checkpoint", "slim_restore", "slim_get_memory",
+    "slim_get_sizes", "slim_project", "slim_backproject", "slim_damped_solve",
+    "slim_set_timing", "slim_get_timing",
+]
+PHASES = ["sample", "forward_residual", "gram_update", "form_k", "factor", "solve", "scatter"]
+
+
+class slim_geometry(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_side", C.c_int), ("n_views", C.c_int),
+                ("det_u", C.c_int), ("det_v", C.c_int), ("angles", C.POINTER(C.c_double)),
+                ("a_mode", C.c_int), ("precision", C.c_int)]
+
+
+class slim_blocks(C.Structure):
+    _fields_ = [("kind", C.c_int), ("ell", C.c_int), ("seed", C.c_ulonglong),
+                ("reserved", C.c_int)]
+
+
+class slim_step_opts(C.Structure):
+    _fields_ = [("eta", C.c_double), ("ramp", C.c_int), ("solver", C.c_int),
+                ("refine_iters", C.c_int), ("use_graph", C.c_int)]
+
+
+class SlimError(RuntimeError):
+    def __init__(self, code, msg):
+        self.code = code
+        name = STATUS_NAMES[code] if 0 <= code < len(STATUS_NAMES) else str(code)
+        super().__init__(f"{name}: {msg}")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libslim.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libslim.so not built ({path}); run paper_1912_07962_gb300.build")
+    lib = C.CDLL(path)
+    P, VP, I, SZ, D, LL = C.POINTER, C.c_void_p, C.c_int, C.c_size_t, C.c_double, C.c_longlong
+    sig = {
+        "slim_create": ([P(slim_geometry), P(slim_blocks), I, D, P(slim_step_opts), P(VP)], I),
+        "slim_destroy": ([VP], None),
+        "slim_last_error": ([VP], C.c_char_p),
+        "slim_set_stream": ([VP, VP], I),
+        "slim_set_data": ([VP, VP, SZ, I, I], I),
+        "slim_set_x": ([VP, VP, SZ, I, I], I),
+        "slim_get_x": ([VP, VP, SZ, I, I], I),
+        "slim_step": ([VP, I], I),
+        "slim_sync": ([VP], I),
+        "slim_set_ref": ([VP, VP, SZ, I, I], I),
+        "slim_run": ([VP, LL, D, I, P(LL), P(D), P(D)], I),
+        "slim_get_iter": ([VP, P(LL)], I),
+        "slim_set_iter": ([VP, LL], I),
+        "slim_checkpoint": ([VP, VP, P(SZ)], I),
+        "slim_restore": ([VP, VP, SZ], I),
+        "slim_get_memory": ([VP, VP, VP, VP], I),
+        "slim_get_sizes": ([VP, P(LL), P(LL), P(I)], I),
+        "slim_project": ([VP, VP, I, VP, VP], I),
+        "slim_backproject": ([VP, VP, I, VP, VP], I),
+        "slim_damped_solve": ([VP, I, D, VP, VP, VP], I),
+        "slim_set_timing": ([VP, I], I),
+        "slim_get_timing": ([VP, P(D), I, P(I)], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """(pointer, on_device, dtype code, element count) of a torch tensor or numpy array."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        code = {torch.float32: SLIM_F32, torch.float64: SLIM_F64}.get(a.dtype)
+        if code is None:
+            raise ValueError(f"unsupported dtype {a.dtype}")
+        return C.c_void_p(a.data_ptr()), int(a.is_cuda), code, a.numel()
+    a = np.ascontiguousarray(a)
+    code = {np.dtype(np.float32): SLIM_F32, np.dtype(np.float64): SLIM_F64}.get(a.dtype)
+    if code is None:
+        raise ValueError(f"unsupported dtype {a.dtype}")
+    return C.c_void_p(a.ctypes.data), 0, code, a.size
+
+
+class Slim:
+    """One slimLS problem on the GPU (owns a slim_ctx)."""
+
+    def __init__(self, N, n_views, det, ell, r, lam, seed, precision=SLIM_PREC_FP64,
+                 solver=SLIM_SOLVE_FP64, refine_iters=2, eta=1.0, ramp=False, use_graph=False,
+                 angles=None):
+        lib = load()
+        self._lib = lib
+        self._angles = None
+        g = slim_geometry(2, N, n_views, det, 1, None, 0, precision)
+        if angles is not None:
+            self._angles = np.ascontiguousarray(angles, dtype=np.float64)
+            g.angles = self._angles.ctypes.data_as(C.POINTER(C.c_double))
+        blk = slim_blocks(SLIM_BLOCKS_VIEWS, ell, seed, 0)
+        opts = slim_step_opts(eta, int(ramp), solver, refine_iters, int(use_graph))
+        h = C.c_void_p()
+        st = lib.slim_create(C.byref(g), C.byref(blk), r, lam, C.byref(opts), C.byref(h))
+        if st != SLIM_OK:
+            raise SlimError(st, "slim_create failed")
+        self.h = h
+        self.precision = precision
+        self.N, self.n, self.m = N, N * N, n_views * det
+        n, m, p = C.c_longlong(), C.c_longlong(), C.c_int()
+        lib.slim_get_sizes(h, C.byref(n), C.byref(m), C.byref(p))
+        self.p = p.value
+
+    def _check(self, st):
+        if st != SLIM_OK:
+            raise SlimError(st, self._lib.slim_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.slim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_data(self, b):
+        p, dev, code, cnt = _ptr(b)
+        self._check(self._lib.slim_set_data(self.h, p, cnt, code, dev))
+
+    def set_x(self, x):
+        p, dev, code, cnt = _ptr(x)
+        self._check(self._lib.slim_set_x(self.h, p, cnt, code, dev))
+
+    def get_x(self, out=None, dtype=np.float64):
+        if out is None:
+            out = np.empty(self.n, dtype=dtype)
+        p, dev, code, cnt = _ptr(out)
+        self._check(self._lib.slim_get_x(self.h, p, cnt, code, dev))
+        return out
+
+    def step(self, nsteps=1):
+        self._check(self._lib.slim_step(self.h, nsteps))
+
+    def sync(self):
+        self._check(self._lib.slim_sync(self.h))
+
+    def set_stream(self, stream_ptr):
+        self._check(self._lib.slim_set_stream(self.h, C.c_void_p(stream_ptr)))
+
+    def set_ref(self, x_ref):
+        if x_ref is None:
+            self._check(self._lib.slim_set_ref(self.h, None, 0, 0, 0))
+            return
+        p, dev, code, cnt = _ptr(x_ref)
+        self._check(self._lib.slim_set_ref(self.h, p, cnt, code, dev))
+
+    def run(self, max_steps, tol=0.0, eval_every=1):
+        k, sec, err = C.c_longlong(), C.c_double(), C.c_double()
+        self._check(self._lib.slim_run(self.h, max_steps, tol, eval_every, C.byref(k),
+                                       C.byref(sec), C.byref(err)))
+        return k.value, sec.value, err.value
+
+    def set_timing(self, on=True):
+        self._check(self._lib.slim_set_timing(self.h, int(on)))
+
+    def get_timing(self):
+        """(per-phase ms of the last step as a dict, kernels per step)."""
+        ms = (C.c_double * len(PHASES))()
+        k = C.c_int()
+        self._check(self._lib.slim_get_timing(self.h, ms, len(PHASES), C.byref(k)))
+        return dict(zip(PHASES, list(ms))), k.value
+
+    def kernels_per_step(self):
+        k = C.c_int()
+        self._check(self._lib.slim_get_timing(self.h, None, 0, C.byref(k)))
+        return k.value
+
+    def get_iter(self):
+        k = C.c_longlong()
+        self._check(self._lib.slim_get_iter(self.h, C.byref(k)))
+        return k.value
+
+    def set_iter(self, k):
+        self._check(self._lib.slim_set_iter(self.h, k))
+
+    def checkpoint(self) -> bytes:
+        ln = C.c_size_t()
+        self._check(self._lib.slim_checkpoint(self.h, None, C.byref(ln)))
+        buf = C.create_string_buffer(ln.value)
+        self._check(self._lib.slim_checkpoint(self.h, buf, C.byref(ln)))
+        return buf.raw[:ln.value]
+
+    def restore(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        self._check(self._lib.slim_restore(self.h, buf, len(blob)))
+
+    def get_memory(self):
+        ids = np.empty(self.p, dtype=np.int32)
+        G = np.empty((self.p, self.p), dtype=np.float64)
+        z = np.empty(self.p, dtype=np.float64)
+        self._check(self._lib.slim_get_memory(self.h, ids.ctypes.data, G.ctypes.data,
+                                              z.ctypes.data))
+        return ids, G, z
+
+    def project(self, x, y, ray_ids=None):
+        ids = C.c_void_p(ray_ids.data_ptr()) if ray_ids is not None else None
+        cnt = ray_ids.numel() if ray_ids is not None else 0
+        self._check(self._lib.slim_project(self.h, ids, cnt, C.c_void_p(x.data_ptr()),
+                                           C.c_void_p(y.data_ptr())))
+
+    def backproject(self, y, x, ray_ids=None):
+        ids = C.c_void_p(ray_ids.data_ptr()) if ray_ids is not None else None
+        cnt = ray_ids.numel() if ray_ids is not None else 0
+        self._check(self._lib.slim_backproject(self.h, ids, cnt, C.c_void_p(y.data_ptr()),
+                                               C.c_void_p(x.data_ptr())))
+
+
+def damped_solve(G, lam, rhs, z, stream_ptr=0):
+    """(lam I + G) z = rhs on the device (torch float64 CUDA tensors)."""
+    lib = load()
+    p = rhs.numel()
+    st = lib.slim_damped_solve(C.c_void_p(G.data_ptr()), p, lam, C.c_void_p(rhs.data_ptr()),
+                               C.c_void_p(z.data_ptr()), C.c_void_p(stream_ptr))
+    if st != SLIM_OK:
+        raise SlimError(st, "slim_damped_solve failed")

@@ -1,0 +1,295 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (per-step relative error ||x_gpu - x_oracle|| / ||x_oracle||):
+  float64 mode (x, residual, scatter, Gram, Cholesky all float64): 1e-12
+  float32 mode (float32 x/residual/scatter, float64 Gram, float32 factor with
+  float64-residual refinement): 1e-5
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import joseph, slim as oslim
+
+from _common import oracle_step_from, rel, tomo_problem
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sl():
+    from paper_1912_07962_gb300 import build, slim
+    build.build()
+    return slim
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return tomo_problem(workloads.C1)
+
+
+@pytest.fixture(scope="module")
+def c2():
+    return tomo_problem(workloads.C2)
+
+
+def _make(sl, cfg, precision=0, solver=0, **kw):
+    return sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.det, cfg.r, cfg.lam, cfg.seed,
+                   precision=precision, solver=solver, **kw)
+
+
+# ---------------------------------------------------------------- projector
+@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 2e-6)])
+def test_projector_full_and_subset(sl, c1, precision, tol):
+    g, A, x_true, b = c1
+    s = _make(sl, workloads.C1, precision=precision)
+    dt = torch.float64 if precision == 0 else torch.float32
+    x = torch.tensor(np.random.default_rng(0).standard_normal(g.n), dtype=dt, device="cuda")
+    y = torch.zeros(g.m, dtype=dt, device="cuda")
+    s.project(x, y)
+    want = A @ x.double().cpu().numpy()
+    got = y.double().cpu().numpy()
+    scale = np.abs(A) @ np.abs(x.double().cpu().numpy()) + 1e-30
+    assert np.max(np.abs(got - want) / scale) < tol
+    ids = torch.tensor(np.random.default_rng(1).integers(0, g.m, 37), dtype=torch.int32,
+                       device="cuda")
+    ys = torch.zeros(37, dtype=dt, device="cuda")
+    s.project(x, ys, ids)
+    assert np.allclose(ys.double().cpu().numpy(), got[ids.cpu().numpy()], rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 2e-6)])
+def test_backprojector(sl, c1, precision, tol):
+    g, A, _, _ = c1
+    s = _make(sl, workloads.C1, precision=precision)
+    dt = torch.float64 if precision == 0 else torch.float32
+    yv = np.random.default_rng(2).standard_normal(g.m)
+    y = torch.tensor(yv, dtype=dt, device="cuda")
+    x = torch.zeros(g.n, dtype=dt, device="cuda")
+    s.backproject(y, x)
+    want = A.T @ y.double().cpu().numpy()
+    scale = np.abs(A.T) @ np.abs(y.double().cpu().numpy()) + 1e-30
+    assert np.max(np.abs(x.double().cpu().numpy() - want) / scale) < tol
+
+
+# ---------------------------------------------------------------- damped Gram solve
+@pytest.mark.parametrize("p,lam", [(364, 1e-2), (250, 1e-3), (1000, 1e-1), (17, 1.0)])
+def test_damped_solve(sl, p, lam):
+    rs = np.random.default_rng(p)
+    B = rs.standard_normal((p, p + 20)) / np.sqrt(p)
+    G = B @ B.T
+    rhs = rs.standard_normal(p)
+    want = np.linalg.solve(lam * np.eye(p) + G, rhs)
+    Gt = torch.tensor(G, device="cuda")
+    rt = torch.tensor(rhs, device="cuda")
+    zt = torch.zeros(p, dtype=torch.float64, device="cuda")
+    sl.damped_solve(Gt, lam, rt, zt)
+    torch.cuda.synchronize()
+    assert rel(zt.cpu().numpy(), want) < 1e-11
+
+
+def test_damped_solve_reports_not_positive_definite(sl):
+    p = 70
+    G = -np.eye(p)
+    Gt = torch.tensor(G, device="cuda")
+    rt = torch.ones(p, dtype=torch.float64, device="cuda")
+    zt = torch.zeros(p, dtype=torch.float64, device="cuda")
+    with pytest.raises(sl.SlimError) as ei:
+        sl.damped_solve(Gt, 0.0, rt, zt)
+    assert ei.value.code == sl.SLIM_ENOTPD
+
+
+# ---------------------------------------------------------------- full steps, float64
+def _oracle_traj(g, b, cfg, steps, r=None, lam=None, ramp=False, eta=1.0):
+    src = oslim.tomo_source(g, b)
+    r = cfg.r if r is None else r
+    lam = cfg.lam if lam is None else lam
+    sched = list(oslim.view_schedule(g, cfg.seed, steps))
+    return [x for _, x, _ in oslim.run(src, sched, r, lam, ramp=ramp, eta=eta)]
+
+
+def test_trajectory_fp64_first_steps(sl, c1):
+    cfg = workloads.C1
+    g, A, _, b = c1
+    traj = _oracle_traj(g, b, cfg, cfg.r + 3)
+    s = _make(sl, cfg)
+    s.set_data(b)
+    for k, xo in enumerate(traj, start=1):
+        s.step(1)
+        assert rel(s.get_x(), xo) < TOL64, k
+
+
+def test_single_step_fp64_every_step_of_first_epoch(sl, c1):
+    cfg = workloads.C1
+    g, A, _, b = c1
+    src = oslim.tomo_source(g, b)
+    s = _make(sl, cfg)
+    s.set_data(b)
+    x_prev = np.zeros(g.n)
+    worst = 0.0
+    for k in range(1, cfg.n_views + 1):
+        xo, _ = oracle_step_from(g, src, cfg.seed, k, cfg.r, cfg.lam, x_prev)
+        s.set_x(x_prev)
+        s.set_iter(k - 1)
+        s.step(1)
+        e = rel(s.get_x(), xo)
+        worst = max(worst, e)
+        x_prev = xo
+    assert worst < TOL64
+
+
+def test_memory_and_gram_match_oracle(sl, c1):
+    cfg = workloads.C1
+    g, A, _, b = c1
+    s = _make(sl, cfg)
+    s.set_data(b)
+    k = 7
+    s.step(k)
+    ids, G, z = s.get_memory()
+    want_ids = np.full(s.p, -1)
+    for kk in range(max(1, k - cfg.r), k + 1):
+        slot = (kk - 1) % (cfg.r + 1)
+        want_ids[slot * cfg.det:(slot + 1) * cfg.det] = oslim.view_block_ids(g, cfg.seed, kk)
+    assert np.array_equal(ids, want_ids)
+    M = joseph.rows(g, want_ids)
+    Go = (M @ M.T).toarray()
+    assert np.max(np.abs(G - Go)) <= 1e-13 * np.max(np.abs(Go))
+
+
+@pytest.mark.parametrize("r,ramp,eta", [(0, False, 1.0), (2, True, 0.7), (5, False, 1.0)])
+def test_variants_tiny_ragged(sl, r, ramp, eta):
+    # N=24, 18 views x 35 bins: p = (r+1)*35 is not a multiple of the tile size
+    cfg = workloads.Tomo2D("tiny", N=24, n_views=18, det=35, ell=35, r=r, lam=3e-2, seed=9)
+    g, A, _, b = tomo_problem(cfg)
+    traj = _oracle_traj(g, b, cfg, 10, ramp=ramp, eta=eta)
+    s = sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.det, r, cfg.lam, cfg.seed, eta=eta, ramp=ramp)
+    s.set_data(b)
+    for k, xo in enumerate(traj, start=1):
+        s.step(1)
+        assert rel(s.get_x(), xo) < TOL64, k
+
+
+def test_graph_replay_matches_eager(sl, c1):
+    cfg = workloads.C1
+    g, A, _, b = c1
+    s1 = _make(sl, cfg)
+    s2 = _make(sl, cfg, use_graph=True)
+    for s in (s1, s2):
+        s.set_data(b)
+        s.step(9)
+    assert rel(s2.get_x(), s1.get_x()) < 1e-13
+
+
+def test_checkpoint_restore_resumes(sl, c1):
+    cfg = workloads.C1
+    g, A, _, b = c1
+    s1 = _make(sl, cfg)
+    s1.set_data(b)
+    s1.step(10)
+    blob = s1.checkpoint()
+    s1.step(6)
+    s2 = _make(sl, cfg)
+    s2.set_data(b)
+    s2.restore(blob)
+    assert s2.get_iter() == 10
+    s2.step(6)
+    assert rel(s2.get_x(), s1.get_x()) < TOL64
+    with pytest.raises(sl.SlimError):
+        s2.restore(blob[:-8])
+
+
+def test_step_before_data_is_a_state_error(sl):
+    cfg = workloads.C1
+    s = _make(sl, cfg)
+    with pytest.raises(sl.SlimError) as ei:
+        s.step(1)
+    assert ei.value.code == sl.SLIM_ESTATE
+
+
+# ---------------------------------------------------------------- float32 mode
+def _single_step_fp32(sl, cfg, prob, ks, **kw):
+    g, A, _, b = prob
+    src = oslim.tomo_source(g, b)
+    s = _make(sl, cfg, precision=1, solver=1, **kw)
+    s.set_data(b)
+    worst = 0.0
+    x_prev = np.zeros(g.n)
+    for k in range(1, max(ks) + 1):
+        xo, _ = oracle_step_from(g, src, cfg.seed, k, cfg.r, cfg.lam, x_prev)
+        if k in ks:
+            s.set_x(x_prev.astype(np.float32))
+            s.set_iter(k - 1)
+            s.step(1)
+            xg = s.get_x()
+            x32 = x_prev.astype(np.float32).astype(np.float64)
+            xo32, _ = oracle_step_from(g, src, cfg.seed, k, cfg.r, cfg.lam, x32)
+            worst = max(worst, rel(xg, xo32))
+        x_prev = xo
+    return worst
+
+
+def test_single_step_fp32_mixed_c1(sl, c1):
+    cfg = workloads.C1
+    assert _single_step_fp32(sl, cfg, c1, set(range(1, cfg.n_views + 1))) < TOL32
+
+
+def test_single_step_fp32_mixed_c2_sampled(sl, c2):
+    cfg = workloads.C2
+    assert _single_step_fp32(sl, cfg, c2, {1, 2, 6, 7, 13}) < TOL32
+
+
+def test_bench_configuration_c2_graph_sampled_steps(sl, c2):
+    # the launch configuration the bench times: float32 form, mixed solve, CUDA graph
+    cfg = workloads.C2
+    g, A, _, b = c2
+    src = oslim.tomo_source(g, b)
+    s = _make(sl, cfg, precision=1, solver=1, use_graph=True)
+    s.set_data(b.astype(np.float32))
+    worst = 0.0
+    for k in range(1, 16):
+        x_prev = s.get_x()
+        s.step(1)
+        if k in (1, 6, 7, 15):
+            xo, _ = oracle_step_from(g, src, cfg.seed, k, cfg.r, cfg.lam,
+                                     x_prev.astype(np.float32).astype(np.float64))
+            worst = max(worst, rel(s.get_x(), xo))
+    assert worst < TOL32
+
+
+def _kappa_tol(g, mem, lam, x_prev, x_k):
+    """max(1e-12, 0.1 * kappa(lambda I + G) * u * ||s|| / ||x_k||): two backward-stable
+    float64 solves of the damped Gram system may differ by up to about kappa * u in
+    z, hence in s = M^T z; the tolerance sits a decade below that first-order bound."""
+    import scipy.linalg as sla
+    M = joseph.rows(g, np.concatenate([ids for _, _, ids in mem]))
+    K = (M @ M.T).toarray() + lam * np.eye(M.shape[0])
+    p = K.shape[0]
+    lo = sla.eigvalsh(K, subset_by_index=[0, 0])[0]
+    hi = sla.eigvalsh(K, subset_by_index=[p - 1, p - 1])[0]
+    u = 2.0 ** -53
+    s_rel = np.linalg.norm(x_k - x_prev) / np.linalg.norm(x_k)
+    return max(TOL64, 0.1 * (hi / lo) * u * s_rel), hi / lo
+
+
+def test_plain_fp64_c2_single_steps(sl, c2):
+    # the 256x256 workload: kappa(lambda I + G) = 1.5e6 once the memory is full
+    cfg = workloads.C2
+    g, A, _, b = c2
+    src = oslim.tomo_source(g, b)
+    s = _make(sl, cfg)
+    s.set_data(b)
+    x_prev = np.zeros(g.n)
+    for k in range(1, 21):
+        xo, mem = oracle_step_from(g, src, cfg.seed, k, cfg.r, cfg.lam, x_prev)
+        if k in (1, 2, 6, 7, 20):
+            s.set_x(x_prev)
+            s.set_iter(k - 1)
+            s.step(1)
+            tol, kappa = _kappa_tol(g, mem, cfg.lam, x_prev, xo)
+            assert rel(s.get_x(), xo) < tol, (k, kappa, tol)
+        x_prev = xo
