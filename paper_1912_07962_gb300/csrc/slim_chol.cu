@@ -116,27 +116,56 @@ __device__ void tile_gemm_nt(T* out, const T* C, int ldC, const T* A, int ldA, c
 // Factor the NB x NB diagonal tile at Lkk in place (lower triangle) and write
 // its inverse (lower, zeros above) to W.  Non-positive pivots set SLIM_ENOTPD
 // and are replaced by 1 so the factorisation still completes without NaNs.
+//
+// Right-looking elimination on the unscaled Schur complements,
+//   S[i][q] -= (S[i][c] / d_c) S[q][c]   for c < q <= i,
+// with the tile held in registers (thread (ty,tx) owns rows ty+16u, columns
+// tx+16v) and column c broadcast through a double-buffered shared column, so
+// each column costs one barrier.
 template <typename T, int NB>
 __device__ void tile_potrf(T* Lkk, int ld, T* W, T* S, T* Ls, int* status) {
   constexpr int LD = NB + 1;
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < NB * NB; idx += kThreads) {
-    int r = idx / NB, c = idx % NB;
-    S[r * LD + c] = ldcg(Lkk + (size_t)r * ld + c);
-  }
-  // right-looking elimination on the unscaled Schur complements:
-  // S[i][q] -= S[i][c] S[q][c] / d_c for c < q <= i
+  constexpr int TM = NB / 16;
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  T* colbuf = Ls;   // 2 x NB, reused before Ls receives the scaled factor
+  T a[TM][TM];
+#pragma unroll
+  for (int u = 0; u < TM; ++u)
+#pragma unroll
+    for (int v = 0; v < TM; ++v) a[u][v] = ldcg(Lkk + (size_t)(ty + 16 * u) * ld + tx + 16 * v);
+  for (int i = tid; i < NB; i += kThreads) colbuf[i] = ldcg(Lkk + (size_t)i * ld);
+  __syncthreads();
   for (int c = 0; c < NB; ++c) {
-    __syncthreads();
-    T d = S[c * LD + c];
+    const T* col = colbuf + (c & 1) * NB;
+    T d = col[c];
     if (!(d > T(0))) d = T(1);
     const T inv_d = T(1) / d;
-    const int w = NB - c - 1;
-    for (int idx = tid; idx < w * w; idx += kThreads) {
-      int i = c + 1 + idx / w, q = c + 1 + idx % w;
-      if (q <= i) S[i * LD + q] -= S[i * LD + c] * S[q * LD + c] * inv_d;
+    T cr[TM], cq[TM];
+#pragma unroll
+    for (int u = 0; u < TM; ++u) cr[u] = col[ty + 16 * u] * inv_d;
+#pragma unroll
+    for (int v = 0; v < TM; ++v) cq[v] = col[tx + 16 * v];
+#pragma unroll
+    for (int u = 0; u < TM; ++u)
+#pragma unroll
+      for (int v = 0; v < TM; ++v) {
+        const int row = ty + 16 * u, cl = tx + 16 * v;
+        if (cl > c && cl <= row) a[u][v] -= cr[u] * cq[v];
+      }
+    if (c + 1 < NB) {
+      T* nxt = colbuf + ((c + 1) & 1) * NB;
+#pragma unroll
+      for (int v = 0; v < TM; ++v)
+        if (tx + 16 * v == c + 1)
+#pragma unroll
+          for (int u = 0; u < TM; ++u) nxt[ty + 16 * u] = a[u][v];
     }
+    __syncthreads();
   }
+#pragma unroll
+  for (int u = 0; u < TM; ++u)
+#pragma unroll
+    for (int v = 0; v < TM; ++v) S[(ty + 16 * u) * LD + tx + 16 * v] = a[u][v];
   __syncthreads();
   // scale the columns: L[c][c] = sqrt(d_c), L[i][c] = S[i][c] / sqrt(d_c)
   for (int idx = tid; idx < NB * NB; idx += kThreads) {
@@ -217,48 +246,59 @@ __global__ void __launch_bounds__(kThreads) chol_factor_kernel(T* L, int P, int 
   }
 }
 
-// out[r] = sign * sum_c M[r][c] v[c] (+ acc[r] if accumulate), one NB x NB tile;
-// rows split over TPR lanes.  v and acc in shared memory.
+// Row-split GEMV pieces: thread (r = tid/TPR, sub = tid%TPR) owns columns
+// sub*CPT .. sub*CPT+CPT-1 of row r.  Tiles are loaded into registers before
+// the wait for the vector they multiply, hiding the L2 latency of the tile.
 template <typename T, int NB>
-__device__ void tile_gemv(const T* M, int ld, const T* v, T* acc, T sign) {
-  constexpr int TPR = kThreads / NB;
-  constexpr int CPT = NB / TPR;
-  const int r = threadIdx.x / TPR, sub = threadIdx.x % TPR;
-  T s = T(0);
-#pragma unroll 4
-  for (int q = 0; q < CPT; ++q) {
-    int c = sub * CPT + q;
-    s += ldcg(M + (size_t)r * ld + c) * v[c];
-  }
+struct RowPart {
+  static constexpr int TPR = kThreads / NB;
+  static constexpr int CPT = NB / TPR;
+  T v[CPT];
+  __device__ void load(const T* M, int ld) {
+    const int r = threadIdx.x / TPR, sub = threadIdx.x % TPR;
 #pragma unroll
-  for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
-  __syncthreads();
-  if (sub == 0) acc[r] += sign * s;
-  __syncthreads();
-}
+    for (int q = 0; q < CPT; ++q) v[q] = ldcg(M + (size_t)r * ld + sub * CPT + q);
+  }
+  // acc[r] += sign * (M v)[r]
+  __device__ void apply(const T* vec, T* acc, T sign) const {
+    const int r = threadIdx.x / TPR, sub = threadIdx.x % TPR;
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) s += v[q] * vec[sub * CPT + q];
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
+    if (sub == 0) acc[r] += sign * s;
+  }
+};
 
-// out[a] += sign * sum_c M[c][a] v[c]  (transposed tile), partial sums in `part`.
+// Column-split transposed GEMV: thread (a = tid%NB, ch = tid/NB) owns rows
+// ch*RPC .. ch*RPC+RPC-1 of column a; partial sums meet in shared memory.
 template <typename T, int NB>
-__device__ void tile_gemv_t(const T* M, int ld, const T* v, T* acc, T sign, T* part) {
-  constexpr int CH = kThreads / NB;
-  constexpr int RPC = NB / CH;
-  const int a = threadIdx.x % NB, ch = threadIdx.x / NB;
-  T s = T(0);
-#pragma unroll 4
-  for (int q = 0; q < RPC; ++q) {
-    int c = ch * RPC + q;
-    s += ldcg(M + (size_t)c * ld + a) * v[c];
-  }
-  part[ch * NB + a] = s;
-  __syncthreads();
-  if (threadIdx.x < NB) {
-    T t = T(0);
+struct ColPart {
+  static constexpr int CH = kThreads / NB;
+  static constexpr int RPC = NB / CH;
+  T v[RPC];
+  __device__ void load(const T* M, int ld) {
+    const int a = threadIdx.x % NB, ch = threadIdx.x / NB;
 #pragma unroll
-    for (int c = 0; c < CH; ++c) t += part[c * NB + threadIdx.x];
-    acc[threadIdx.x] += sign * t;
+    for (int q = 0; q < RPC; ++q) v[q] = ldcg(M + (size_t)(ch * RPC + q) * ld + a);
   }
-  __syncthreads();
-}
+  // acc[a] += sign * (M^T vec)[a]; `part` holds kThreads partial sums
+  __device__ void apply(const T* vec, T* acc, T sign, T* part) const {
+    const int a = threadIdx.x % NB, ch = threadIdx.x / NB;
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < RPC; ++q) s += v[q] * vec[ch * RPC + q];
+    part[ch * NB + a] = s;
+    __syncthreads();
+    if (threadIdx.x < NB) {
+      T t = T(0);
+#pragma unroll
+      for (int c = 0; c < CH; ++c) t += part[c * NB + threadIdx.x];
+      acc[threadIdx.x] += sign * t;
+    }
+  }
+};
 
 template <typename T, int NB>
 __global__ void __launch_bounds__(kThreads) chol_fwd_kernel(const T* L, int P, int Tt,
@@ -273,17 +313,21 @@ __global__ void __launch_bounds__(kThreads) chol_fwd_kernel(const T* L, int P, i
     const int i = s_task;
     __syncthreads();
     if (i >= Tt) return;
+    RowPart<T, NB> wpart, lpart;
+    wpart.load(winv + (size_t)i * NB * NB, NB);
     if (threadIdx.x < NB) acc[threadIdx.x] = (T)v[i * NB + threadIdx.x];
-    __syncthreads();
     for (int j = 0; j < i; ++j) {
+      lpart.load(L + (size_t)i * NB * P + (size_t)j * NB, P);
       if (!cta_wait(&fflag[j], 1, abort_flag, status, &s_ok)) return;
       if (threadIdx.x < NB) vec[threadIdx.x] = ldcg(y + j * NB + threadIdx.x);
       __syncthreads();
-      tile_gemv<T, NB>(L + (size_t)i * NB * P + (size_t)j * NB, P, vec, acc, T(-1));
+      lpart.apply(vec, acc, T(-1));
+      __syncthreads();
     }
     if (threadIdx.x < NB) out[threadIdx.x] = T(0);
     __syncthreads();
-    tile_gemv<T, NB>(winv + (size_t)i * NB * NB, NB, acc, out, T(1));
+    wpart.apply(acc, out, T(1));
+    __syncthreads();
     if (threadIdx.x < NB) stcg(y + i * NB + threadIdx.x, out[threadIdx.x]);
     cta_publish(&fflag[i]);
   }
@@ -304,17 +348,21 @@ __global__ void __launch_bounds__(kThreads) chol_bwd_kernel(const T* L, int P, i
     __syncthreads();
     if (t >= Tt) return;
     const int i = Tt - 1 - t;
+    ColPart<T, NB> wpart, lpart;
+    wpart.load(winv + (size_t)i * NB * NB, NB);
     if (threadIdx.x < NB) acc[threadIdx.x] = ldcg(y + i * NB + threadIdx.x);
-    __syncthreads();
     for (int j = Tt - 1; j > i; --j) {
+      lpart.load(L + (size_t)j * NB * P + (size_t)i * NB, P);
       if (!cta_wait(&bflag[j], 1, abort_flag, status, &s_ok)) return;
       if (threadIdx.x < NB) vec[threadIdx.x] = ldcg(zt + j * NB + threadIdx.x);
       __syncthreads();
-      tile_gemv_t<T, NB>(L + (size_t)j * NB * P + (size_t)i * NB, P, vec, acc, T(-1), part);
+      lpart.apply(vec, acc, T(-1), part);
+      __syncthreads();
     }
     if (threadIdx.x < NB) out[threadIdx.x] = T(0);
     __syncthreads();
-    tile_gemv_t<T, NB>(winv + (size_t)i * NB * NB, NB, acc, out, T(1), part);
+    wpart.apply(acc, out, T(1), part);
+    __syncthreads();
     if (threadIdx.x < NB) {
       stcg(zt + i * NB + threadIdx.x, out[threadIdx.x]);
       z[i * NB + threadIdx.x] = (double)out[threadIdx.x];
@@ -358,12 +406,19 @@ cudaError_t launch_solve(const CholPlan& p, const void* L, const double* v, doub
 }  // namespace
 
 std::vector<CholTask> build_chol_tasks(int T) {
+  // Right-looking order with a lookahead of one panel: after panel k's update
+  // of column k+1, panel k+1 is factored (POTRF, TRSM) before panel k's
+  // remaining trailing updates, so the next diagonal factorisation can start
+  // while those updates are still running.
   std::vector<CholTask> t;
-  for (int k = 0; k < T; ++k) {
-    t.push_back({kPotrf, (uint16_t)k, (uint16_t)k, (uint16_t)k});
-    for (int i = k + 1; i < T; ++i) t.push_back({kTrsm, (uint16_t)i, (uint16_t)k, (uint16_t)k});
-    // updates from panel k; column k+1 first so the next panel can start early
-    for (int m = k + 1; m < T; ++m)
+  t.push_back({kPotrf, 0, 0, 0});
+  for (int i = 1; i < T; ++i) t.push_back({kTrsm, (uint16_t)i, 0, 0});
+  for (int k = 0; k + 1 < T; ++k) {
+    const int n1 = k + 1;
+    for (int i = n1; i < T; ++i) t.push_back({kUpd, (uint16_t)i, (uint16_t)n1, (uint16_t)k});
+    t.push_back({kPotrf, (uint16_t)n1, (uint16_t)n1, (uint16_t)n1});
+    for (int i = n1 + 1; i < T; ++i) t.push_back({kTrsm, (uint16_t)i, (uint16_t)n1, (uint16_t)n1});
+    for (int m = k + 2; m < T; ++m)
       for (int i = m; i < T; ++i) t.push_back({kUpd, (uint16_t)i, (uint16_t)m, (uint16_t)k});
   }
   return t;
