@@ -208,6 +208,28 @@ slim_status slim_backproject(slim_ctx* ctx, const int* ray_ids, int count, const
 slim_status slim_damped_solve(const double* G, int p, double lambda, const double* rhs,
                               double* z, void* cuda_stream);
 
+/* Largest order p accepted by slim_damped_solve_noalloc. */
+#define SLIM_NOALLOC_MAX_P 1024
+
+/* The damped Gram solve of slim_damped_solve without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they solve -- an application whose device
+ * memory is wholly reserved by its own pool allocator (as under a framework's
+ * caching allocator), or a latency-critical loop that must not call
+ * cudaMalloc/cudaFree, which synchronise the device.
+ *
+ * Same arguments, arithmetic (float64 tiled Cholesky and triangular solves)
+ * and results as slim_damped_solve, for p <= SLIM_NOALLOC_MAX_P; larger p is
+ * rejected with SLIM_EINVAL (use slim_damped_solve).  The caller passes G,
+ * rhs and z as device arrays.  All scratch lives in one static device array of
+ * about 8.7 MB that every GPU which loads the library keeps until the process
+ * exits.  The first call on a device resolves that array's address for the
+ * current device (a one-time set-up).  Calls share the array: calls that
+ * overlap on the GPU (different streams or host threads at the same time)
+ * race and give wrong results.  Each call synchronises `cuda_stream`. */
+slim_status slim_damped_solve_noalloc(const double* G, int p, double lambda, const double* rhs,
+                                      double* z, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

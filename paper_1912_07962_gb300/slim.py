@@ -30,8 +30,9 @@ EXPORTS = [
     "slim_set_x", "slim_get_x", "slim_step", "slim_sync", "slim_set_ref", "slim_run",
     "slim_get_iter", "slim_set_iter", "slim_checkpoint", "slim_restore", "slim_get_memory",
     "slim_get_sizes", "slim_project", "slim_backproject", "slim_damped_solve",
-    "slim_set_timing", "slim_get_timing",
+    "slim_set_timing", "slim_get_timing", "slim_damped_solve_noalloc",
 ]
+NOALLOC_MAX_P = 1024
 PHASES = ["sample", "forward_residual", "gram_update", "form_k", "factor", "solve", "scatter"]
 
 
@@ -93,6 +94,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "slim_damped_solve": ([VP, I, D, VP, VP, VP], I),
         "slim_set_timing": ([VP, I], I),
         "slim_get_timing": ([VP, P(D), I, P(I)], I),
+        "slim_damped_solve_noalloc": ([VP, I, D, VP, VP, VP], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -260,3 +262,15 @@ def damped_solve(G, lam, rhs, z, stream_ptr=0):
                                C.c_void_p(z.data_ptr()), C.c_void_p(stream_ptr))
     if st != SLIM_OK:
         raise SlimError(st, "slim_damped_solve failed")
+
+
+def damped_solve_noalloc(G, lam, rhs, z, stream_ptr=0):
+    """(lam I + G) z = rhs without device allocation (p <= NOALLOC_MAX_P); torch
+    float64 CUDA tensors.  Scratch is a static device array shared by all calls."""
+    lib = load()
+    p = rhs.numel()
+    st = lib.slim_damped_solve_noalloc(C.c_void_p(G.data_ptr()), p, lam,
+                                       C.c_void_p(rhs.data_ptr()), C.c_void_p(z.data_ptr()),
+                                       C.c_void_p(stream_ptr))
+    if st != SLIM_OK:
+        raise SlimError(st, "slim_damped_solve_noalloc failed")
