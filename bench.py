@@ -363,7 +363,7 @@ def main_gpu(args):
     if args.tta_epochs > 0 and rank == 0:
         tta = tta_block(sl, cfg, b, flush, stream, args.tta_epochs,
                         [0.5, 0.2, 0.1, 0.05, 0.02, 0.01])
-    e2e = e2e_block(sl, cfg, b, args.steps, args.warmup) if rank == 0 else None
+    e2e = e2e_block(sl, cfg, b, args.steps, args.warmup) if rank == 0 and not args.no_e2e else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         leg = run_cpu_leg(args)
@@ -427,6 +427,7 @@ def main():
     ap.add_argument("--workload", default="precision-256", choices=["precision-256", "plain-64"])
     ap.add_argument("--tta-epochs", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-steps", type=int, default=0)
     ap.add_argument("--cpu-warmup", type=int, default=6)

@@ -32,35 +32,47 @@ __device__ __forceinline__ void red_release_add(int* p, int v) {
   asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// CTA-wide bounded wait until *flag >= target.  Returns false if the wait ran
-// out or another CTA asked everyone to stop.
-__device__ bool cta_wait(const int* flag, int target, int* abort_flag, int* status, int* s_ok) {
-  if (threadIdx.x == 0) {
+// CTA-wide bounded wait until f[q] >= t[q] for q < nf (nf <= 3), the flags
+// polled in parallel by threads 0..nf-1.  Returns false if a wait ran out or
+// another CTA asked everyone to stop.
+__device__ bool cta_wait(const int* f0, int t0, const int* f1, int t1, const int* f2, int t2,
+                         int nf, int* abort_flag, int* status, int* s_ok3) {
+  const int tid = threadIdx.x;
+  if (tid < 3) {
     int ok = 1;
-    unsigned it = 0;
-    while (ld_acquire(flag) < target) {
-      if (ld_acquire(abort_flag)) { ok = 0; break; }
-      if (++it > kSpinLimit) {
-        set_status(status, SLIM_ETIMEOUT);
-        atomicExch(abort_flag, 1);
-        ok = 0;
-        break;
+    if (tid < nf) {
+      const int* f = tid == 0 ? f0 : (tid == 1 ? f1 : f2);
+      const int tg = tid == 0 ? t0 : (tid == 1 ? t1 : t2);
+      unsigned it = 0;
+      while (ld_acquire(f) < tg) {
+        if (ld_acquire(abort_flag)) { ok = 0; break; }
+        if (++it > kSpinLimit) {
+          set_status(status, SLIM_ETIMEOUT);
+          atomicExch(abort_flag, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
       }
-      __nanosleep(40);
+      __threadfence();
     }
-    *s_ok = ok;
+    s_ok3[tid] = ok;
   }
   __syncthreads();
-  int ok = *s_ok;
+  const int ok = s_ok3[0] & s_ok3[1] & s_ok3[2];
   __syncthreads();
   return ok != 0;
 }
 
-__device__ __forceinline__ void cta_publish(int* flag) {
+__device__ bool cta_wait(const int* flag, int target, int* abort_flag, int* status, int* s_ok3) {
+  return cta_wait(flag, target, flag, 0, flag, 0, 1, abort_flag, status, s_ok3);
+}
+
+__device__ __forceinline__ void cta_publish(int* flag, int add = 1) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    red_release_add(flag, 1);
+    red_release_add(flag, add);
   }
 }
 
@@ -69,12 +81,31 @@ __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
 template <typename T>
 __device__ __forceinline__ void stcg(T* p, T v) { __stcg(p, v); }
 
+// Load TM consecutive values from (16-byte aligned) shared memory.
+template <typename T, int TM>
+__device__ __forceinline__ void lds_vec(T (&v)[TM], const T* p) {
+  if constexpr (sizeof(T) == 4 && TM == 4) {
+    float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (sizeof(T) == 8 && TM == 2) {
+    double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int a = 0; a < TM; ++a) v[a] = p[a];
+  }
+}
+
+__host__ __device__ constexpr int gemm_ld(int nb) { return nb + 4; }   // padded row of a staged tile
+
 // out = beta*C + sign * A B^T for NB x NB tiles (row-major, leading dimension
-// ldA/ldB/ldC).  A and B are staged transposed (k-major) in shared memory.
+// ldA/ldB/ldC).  A and B are staged transposed (k-major) in shared memory;
+// thread (ty,tx) owns the TM x TM block at rows ty*TM.., columns tx*TM.., so
+// each k step reads two contiguous vectors from shared memory.
 template <typename T, int NB>
 __device__ void tile_gemm_nt(T* out, const T* C, int ldC, const T* A, int ldA, const T* B, int ldB,
                              bool beta, T sign, T* As, T* Bs) {
-  constexpr int LD = NB + 1;
+  constexpr int LD = gemm_ld(NB);
   constexpr int TM = NB / 16;
   const int tid = threadIdx.x;
   for (int idx = tid; idx < NB * NB; idx += kThreads) {
@@ -89,13 +120,11 @@ __device__ void tile_gemm_nt(T* out, const T* C, int ldC, const T* A, int ldA, c
   for (int a = 0; a < TM; ++a)
 #pragma unroll
     for (int b = 0; b < TM; ++b) acc[a][b] = T(0);
-#pragma unroll 4
+#pragma unroll 8
   for (int q = 0; q < NB; ++q) {
     T av[TM], bv[TM];
-#pragma unroll
-    for (int a = 0; a < TM; ++a) av[a] = As[q * LD + ty + 16 * a];
-#pragma unroll
-    for (int b = 0; b < TM; ++b) bv[b] = Bs[q * LD + tx + 16 * b];
+    lds_vec<T, TM>(av, As + q * LD + ty * TM);
+    lds_vec<T, TM>(bv, Bs + q * LD + tx * TM);
 #pragma unroll
     for (int a = 0; a < TM; ++a)
 #pragma unroll
@@ -105,7 +134,7 @@ __device__ void tile_gemm_nt(T* out, const T* C, int ldC, const T* A, int ldA, c
   for (int a = 0; a < TM; ++a)
 #pragma unroll
     for (int b = 0; b < TM; ++b) {
-      int r = ty + 16 * a, c = tx + 16 * b;
+      const int r = ty * TM + a, c = tx * TM + b;
       T v = sign * acc[a][b];
       if (beta) v += ldcg(C + (size_t)r * ldC + c);
       stcg(out + (size_t)r * ldC + c, v);
@@ -212,37 +241,75 @@ __global__ void __launch_bounds__(kThreads) chol_factor_kernel(T* L, int P, int 
                                                                int* status, int* abort_flag) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* As = reinterpret_cast<T*>(smem_raw);
-  T* Bs = As + NB * (NB + 1);
-  __shared__ int s_task, s_ok;
+  T* Bs = As + NB * gemm_ld(NB);
+  __shared__ int s_task, s_ok3[3];
+  __shared__ CholTask s_desc;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    const int t = atomicAdd(ticket, 1);
+    s_task = t;
+    if (t < ntasks) s_desc = tasks[t];
+  }
+  __syncthreads();
   for (;;) {
-    if (threadIdx.x == 0) s_task = atomicAdd(ticket, 1);
-    __syncthreads();
     const int t = s_task;
-    __syncthreads();
     if (t >= ntasks) return;
-    const CholTask tk = tasks[t];
+    const CholTask tk = s_desc;
+    // thread 32 claims the next ticket while the CTA works on this one; the
+    // claimed task is started only after this one finishes, which keeps the
+    // claim order a valid execution order
+    int next = 0;
+    if (tid == 32) next = atomicAdd(ticket, 1);
+    __syncthreads();
     const int i = tk.i, m = tk.m, k = tk.k;
-    T* tile_im = L + (size_t)i * NB * P + (size_t)m * NB;
+    bool ok = true;
     if (tk.type == kUpd) {
-      if (!cta_wait(&cnt[i * Tt + k], k + 1, abort_flag, status, &s_ok)) return;
-      if (!cta_wait(&cnt[m * Tt + k], k + 1, abort_flag, status, &s_ok)) return;
-      if (!cta_wait(&cnt[i * Tt + m], k, abort_flag, status, &s_ok)) return;
-      const T* Lik = L + (size_t)i * NB * P + (size_t)k * NB;
-      const T* Lmk = L + (size_t)m * NB * P + (size_t)k * NB;
-      tile_gemm_nt<T, NB>(tile_im, tile_im, P, Lik, P, Lmk, P, true, T(-1), As, Bs);
-      cta_publish(&cnt[i * Tt + m]);
+      ok = cta_wait(&cnt[i * Tt + k], k + 1, &cnt[m * Tt + k], k + 1, &cnt[i * Tt + m], k, 3,
+                    abort_flag, status, s_ok3);
+      if (ok) {
+        T* tile_im = L + (size_t)i * NB * P + (size_t)m * NB;
+        const T* Lik = L + (size_t)i * NB * P + (size_t)k * NB;
+        const T* Lmk = L + (size_t)m * NB * P + (size_t)k * NB;
+        tile_gemm_nt<T, NB>(tile_im, tile_im, P, Lik, P, Lmk, P, true, T(-1), As, Bs);
+        cta_publish(&cnt[i * Tt + m]);
+      }
     } else if (tk.type == kTrsm) {
-      if (!cta_wait(&cnt[m * Tt + m], m + 1, abort_flag, status, &s_ok)) return;
-      if (!cta_wait(&cnt[i * Tt + m], m, abort_flag, status, &s_ok)) return;
-      const T* Wm = winv + (size_t)m * NB * NB;
-      tile_gemm_nt<T, NB>(tile_im, nullptr, P, tile_im, P, Wm, NB, false, T(1), As, Bs);
-      cta_publish(&cnt[i * Tt + m]);
+      ok = cta_wait(&cnt[m * Tt + m], m + 1, &cnt[i * Tt + m], m, nullptr, 0, 2, abort_flag,
+                    status, s_ok3);
+      if (ok) {
+        T* tile_im = L + (size_t)i * NB * P + (size_t)m * NB;
+        tile_gemm_nt<T, NB>(tile_im, nullptr, P, tile_im, P, winv + (size_t)m * NB * NB, NB, false,
+                            T(1), As, Bs);
+        cta_publish(&cnt[i * Tt + m]);
+      }
+    } else if (tk.type == kPanel) {
+      // i = k+1: TRSM(k+1,k), SYRK into (k+1,k+1), POTRF(k+1)
+      ok = cta_wait(&cnt[k * Tt + k], k + 1, &cnt[i * Tt + k], k, &cnt[i * Tt + i], k, 3,
+                    abort_flag, status, s_ok3);
+      if (ok) {
+        T* t_ik = L + (size_t)i * NB * P + (size_t)k * NB;
+        T* t_ii = L + (size_t)i * NB * P + (size_t)i * NB;
+        tile_gemm_nt<T, NB>(t_ik, nullptr, P, t_ik, P, winv + (size_t)k * NB * NB, NB, false,
+                            T(1), As, Bs);
+        cta_publish(&cnt[i * Tt + k]);
+        tile_gemm_nt<T, NB>(t_ii, t_ii, P, t_ik, P, t_ik, P, true, T(-1), As, Bs);
+        tile_potrf<T, NB>(t_ii, P, winv + (size_t)i * NB * NB, As, Bs, status);
+        cta_publish(&cnt[i * Tt + i], 2);
+      }
     } else {
-      if (!cta_wait(&cnt[k * Tt + k], k, abort_flag, status, &s_ok)) return;
-      T* Lkk = L + (size_t)k * NB * P + (size_t)k * NB;
-      tile_potrf<T, NB>(Lkk, P, winv + (size_t)k * NB * NB, As, Bs, status);
-      cta_publish(&cnt[k * Tt + k]);
+      ok = cta_wait(&cnt[k * Tt + k], k, abort_flag, status, s_ok3);
+      if (ok) {
+        T* Lkk = L + (size_t)k * NB * P + (size_t)k * NB;
+        tile_potrf<T, NB>(Lkk, P, winv + (size_t)k * NB * NB, As, Bs, status);
+        cta_publish(&cnt[k * Tt + k]);
+      }
     }
+    __syncthreads();
+    if (tid == 32) {
+      s_task = ok ? next : ntasks;
+      if (ok && next < ntasks) s_desc = tasks[next];
+    }
+    __syncthreads();
   }
 }
 
@@ -306,7 +373,7 @@ __global__ void __launch_bounds__(kThreads) chol_fwd_kernel(const T* L, int P, i
                                                             int* fflag, int* ticket, int* status,
                                                             int* abort_flag) {
   __shared__ T acc[NB], vec[NB], out[NB];
-  __shared__ int s_task, s_ok;
+  __shared__ int s_task, s_ok3[3];
   for (;;) {
     if (threadIdx.x == 0) s_task = atomicAdd(ticket, 1);
     __syncthreads();
@@ -318,7 +385,7 @@ __global__ void __launch_bounds__(kThreads) chol_fwd_kernel(const T* L, int P, i
     if (threadIdx.x < NB) acc[threadIdx.x] = (T)v[i * NB + threadIdx.x];
     for (int j = 0; j < i; ++j) {
       lpart.load(L + (size_t)i * NB * P + (size_t)j * NB, P);
-      if (!cta_wait(&fflag[j], 1, abort_flag, status, &s_ok)) return;
+      if (!cta_wait(&fflag[j], 1, abort_flag, status, s_ok3)) return;
       if (threadIdx.x < NB) vec[threadIdx.x] = ldcg(y + j * NB + threadIdx.x);
       __syncthreads();
       lpart.apply(vec, acc, T(-1));
@@ -340,7 +407,7 @@ __global__ void __launch_bounds__(kThreads) chol_bwd_kernel(const T* L, int P, i
                                                             int* status, int* abort_flag) {
   __shared__ T acc[NB], vec[NB], out[NB];
   __shared__ T part[kThreads];
-  __shared__ int s_task, s_ok;
+  __shared__ int s_task, s_ok3[3];
   for (;;) {
     if (threadIdx.x == 0) s_task = atomicAdd(ticket, 1);
     __syncthreads();
@@ -353,7 +420,7 @@ __global__ void __launch_bounds__(kThreads) chol_bwd_kernel(const T* L, int P, i
     if (threadIdx.x < NB) acc[threadIdx.x] = ldcg(y + i * NB + threadIdx.x);
     for (int j = Tt - 1; j > i; --j) {
       lpart.load(L + (size_t)j * NB * P + (size_t)i * NB, P);
-      if (!cta_wait(&bflag[j], 1, abort_flag, status, &s_ok)) return;
+      if (!cta_wait(&bflag[j], 1, abort_flag, status, s_ok3)) return;
       if (threadIdx.x < NB) vec[threadIdx.x] = ldcg(zt + j * NB + threadIdx.x);
       __syncthreads();
       lpart.apply(vec, acc, T(-1), part);
@@ -372,7 +439,7 @@ __global__ void __launch_bounds__(kThreads) chol_bwd_kernel(const T* L, int P, i
 }
 
 template <typename T, int NB>
-size_t factor_smem() { return 2 * NB * (NB + 1) * sizeof(T); }
+size_t factor_smem() { return 2 * NB * gemm_ld(NB) * sizeof(T); }
 
 template <typename T, int NB>
 cudaError_t launch_factor(const CholPlan& p, void* L, int* status, cudaStream_t s) {
@@ -406,18 +473,18 @@ cudaError_t launch_solve(const CholPlan& p, const void* L, const double* v, doub
 }  // namespace
 
 std::vector<CholTask> build_chol_tasks(int T) {
-  // Right-looking order with a lookahead of one panel: after panel k's update
-  // of column k+1, panel k+1 is factored (POTRF, TRSM) before panel k's
-  // remaining trailing updates, so the next diagonal factorisation can start
-  // while those updates are still running.
+  // Right-looking order with a lookahead of one panel.  The critical path of
+  // panel k+1 (TRSM of tile (k+1,k), its update of the diagonal tile, and the
+  // diagonal factorisation) is one task placed right after panel k's, ahead of
+  // panel k's remaining trailing updates.
   std::vector<CholTask> t;
   t.push_back({kPotrf, 0, 0, 0});
-  for (int i = 1; i < T; ++i) t.push_back({kTrsm, (uint16_t)i, 0, 0});
+  for (int i = 2; i < T; ++i) t.push_back({kTrsm, (uint16_t)i, 0, 0});
   for (int k = 0; k + 1 < T; ++k) {
     const int n1 = k + 1;
-    for (int i = n1; i < T; ++i) t.push_back({kUpd, (uint16_t)i, (uint16_t)n1, (uint16_t)k});
-    t.push_back({kPotrf, (uint16_t)n1, (uint16_t)n1, (uint16_t)n1});
-    for (int i = n1 + 1; i < T; ++i) t.push_back({kTrsm, (uint16_t)i, (uint16_t)n1, (uint16_t)n1});
+    t.push_back({kPanel, (uint16_t)n1, (uint16_t)n1, (uint16_t)k});
+    for (int i = n1 + 1; i < T; ++i) t.push_back({kUpd, (uint16_t)i, (uint16_t)n1, (uint16_t)k});
+    for (int i = n1 + 2; i < T; ++i) t.push_back({kTrsm, (uint16_t)i, (uint16_t)n1, (uint16_t)n1});
     for (int m = k + 2; m < T; ++m)
       for (int i = m; i < T; ++i) t.push_back({kUpd, (uint16_t)i, (uint16_t)m, (uint16_t)k});
   }

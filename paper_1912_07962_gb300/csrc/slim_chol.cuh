@@ -12,10 +12,13 @@ namespace slim {
 //   kPotrf (k):      factor diagonal tile (k,k) and form its inverse
 //   kTrsm  (i,k):    L_ik = A_ik L_kk^{-T}
 //   kUpd   (i,m,k):  A_im -= L_ik L_mk^T   (update from panel k)
+//   kPanel (k+1,k):  the critical path of one panel in one task:
+//                    TRSM(k+1,k), then A_{k+1,k+1} -= L_{k+1,k} L_{k+1,k}^T,
+//                    then POTRF(k+1)
 struct CholTask {
   uint16_t type, i, m, k;
 };
-enum : uint16_t { kPotrf = 0, kTrsm = 1, kUpd = 2 };
+enum : uint16_t { kPotrf = 0, kTrsm = 1, kUpd = 2, kPanel = 3 };
 
 // Task list in a dependency-compatible order: every task depends only on
 // tasks earlier in the list, so CTAs that claim tasks through an atomic
