@@ -13,6 +13,8 @@
 // The solves chain diagonal blocks the same way: CTA i of the forward solve
 // subtracts L_ij y_j as each y_j is published, then applies L_ii^{-1}; the
 // backward solve runs the transposed chain from the last block.
+#include <type_traits>
+
 #include "slim_chol.cuh"
 #include "slim_device.cuh"
 
@@ -97,6 +99,8 @@ __device__ __forceinline__ void lds_vec(T (&v)[TM], const T* p) {
 }
 
 __host__ __device__ constexpr int gemm_ld(int nb) { return nb + 4; }   // padded row of a staged tile
+// scratch of the blocked tile inverse, placed after the two staged tiles
+__host__ __device__ constexpr int potrf_tmp_elems(int nb) { return (nb / 16 - 1) * 256; }
 
 // out = beta*C + sign * A B^T for NB x NB tiles (row-major, leading dimension
 // ldA/ldB/ldC).  A and B are staged transposed (k-major) in shared memory;
@@ -108,10 +112,27 @@ __device__ void tile_gemm_nt(T* out, const T* C, int ldC, const T* A, int ldA, c
   constexpr int LD = gemm_ld(NB);
   constexpr int TM = NB / 16;
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < NB * NB; idx += kThreads) {
-    int r = idx / NB, q = idx % NB;
-    As[q * LD + r] = ldcg(A + (size_t)r * ldA + q);
-    Bs[q * LD + r] = ldcg(B + (size_t)r * ldB + q);
+  // stage with 16-byte loads, all of a thread's loads in flight at once
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int EV = 16 / sizeof(T);               // values per vector
+  constexpr int NV = NB * NB / EV / kThreads;      // vectors per thread per tile
+  V va[NV], vb[NV];
+#pragma unroll
+  for (int t = 0; t < NV; ++t) {
+    const int idx = (tid + t * kThreads) * EV, r = idx / NB, q = idx % NB;
+    va[t] = __ldcg(reinterpret_cast<const V*>(A + (size_t)r * ldA + q));
+    vb[t] = __ldcg(reinterpret_cast<const V*>(B + (size_t)r * ldB + q));
+  }
+#pragma unroll
+  for (int t = 0; t < NV; ++t) {
+    const int idx = (tid + t * kThreads) * EV, r = idx / NB, q = idx % NB;
+    const T* ea = reinterpret_cast<const T*>(&va[t]);
+    const T* eb = reinterpret_cast<const T*>(&vb[t]);
+#pragma unroll
+    for (int e = 0; e < EV; ++e) {
+      As[(q + e) * LD + r] = ea[e];
+      Bs[(q + e) * LD + r] = eb[e];
+    }
   }
   __syncthreads();
   const int ty = tid / 16, tx = tid % 16;
@@ -148,46 +169,75 @@ __device__ void tile_gemm_nt(T* out, const T* C, int ldC, const T* A, int ldA, c
 //
 // Right-looking elimination on the unscaled Schur complements,
 //   S[i][q] -= (S[i][c] / d_c) S[q][c]   for c < q <= i,
-// with the tile held in registers (thread (ty,tx) owns rows ty+16u, columns
-// tx+16v) and column c broadcast through a double-buffered shared column, so
-// each column costs one barrier.
+// with the tile in registers (thread (ty,tx) owns rows ty+16u, columns
+// tx+16v) and column c broadcast through a double-buffered shared column: one
+// barrier per column.  The column's owners publish it as soon as it is final.
+// float: every thread forms 1/d_c itself (correctly rounded reciprocal), and
+// the update runs unpredicated (rows/columns <= c get zero multipliers; the
+// upper triangle receives values that are never read).  double: the narrow
+// float64 pipe makes per-thread reciprocals costly, so the owner of the next
+// pivot divides once and shares 1/d with the column, and only lower-triangle
+// entries are updated.
+// The inverse is blocked in 16 x 16 blocks: diagonal blocks in parallel, then
+// one block diagonal at a time, W_ij = -W_ii (sum_{k=j}^{i-1} L_ik W_kj).
 template <typename T, int NB>
 __device__ void tile_potrf(T* Lkk, int ld, T* W, T* S, T* Ls, int* status) {
   constexpr int LD = NB + 1;
   constexpr int TM = NB / 16;
+  constexpr bool kF64 = sizeof(T) == 8;
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
-  T* colbuf = Ls;   // 2 x NB, reused before Ls receives the scaled factor
+  // shared layout (S and Ls hold NB*(NB+4) values each, followed by
+  // potrf_tmp_elems(NB) values of scratch):
+  //   S:  the tile, NB x LD, then sqrt(d_c) and 1/sqrt(d_c) (2*NB)
+  //   Ls: the double-buffered column (2*(NB+1), the last entry 1/d for
+  //       float64) during the elimination, then the inverse W (NB x LD)
+  T* colbuf = Ls;
+  T* sd = S + NB * LD;
+  T* rsd = sd + NB;
   T a[TM][TM];
 #pragma unroll
   for (int u = 0; u < TM; ++u)
 #pragma unroll
     for (int v = 0; v < TM; ++v) a[u][v] = ldcg(Lkk + (size_t)(ty + 16 * u) * ld + tx + 16 * v);
   for (int i = tid; i < NB; i += kThreads) colbuf[i] = ldcg(Lkk + (size_t)i * ld);
+  if (kF64 && tid == 0) {
+    const T d0 = ldcg(Lkk);
+    colbuf[NB] = d0 > T(0) ? T(1) / d0 : T(1);
+  }
   __syncthreads();
   for (int c = 0; c < NB; ++c) {
-    const T* col = colbuf + (c & 1) * NB;
-    T d = col[c];
-    if (!(d > T(0))) d = T(1);
-    const T inv_d = T(1) / d;
+    const T* col = colbuf + (c & 1) * (NB + 1);
+    T inv_d;
+    if constexpr (kF64) {
+      inv_d = col[NB];
+    } else {
+      const T d = col[c];
+      inv_d = d > T(0) ? __frcp_rn(d) : T(1);
+    }
     T cr[TM], cq[TM];
 #pragma unroll
-    for (int u = 0; u < TM; ++u) cr[u] = col[ty + 16 * u] * inv_d;
+    for (int u = 0; u < TM; ++u) cr[u] = (ty + 16 * u > c) ? col[ty + 16 * u] * inv_d : T(0);
 #pragma unroll
-    for (int v = 0; v < TM; ++v) cq[v] = col[tx + 16 * v];
+    for (int v = 0; v < TM; ++v) cq[v] = (tx + 16 * v > c) ? col[tx + 16 * v] : T(0);
+    T* nxt = colbuf + ((c + 1) & 1) * (NB + 1);
 #pragma unroll
-    for (int u = 0; u < TM; ++u)
+    for (int v = 0; v < TM; ++v) {
+      const int cl = tx + 16 * v;
 #pragma unroll
-      for (int v = 0; v < TM; ++v) {
-        const int row = ty + 16 * u, cl = tx + 16 * v;
-        if (cl > c && cl <= row) a[u][v] -= cr[u] * cq[v];
+      for (int u = 0; u < TM; ++u) {
+        if constexpr (kF64) {
+          if (cl > c && cl <= ty + 16 * u) a[u][v] -= cr[u] * cq[v];
+        } else {
+          a[u][v] -= cr[u] * cq[v];
+        }
       }
-    if (c + 1 < NB) {
-      T* nxt = colbuf + ((c + 1) & 1) * NB;
+      if (cl == c + 1) {
 #pragma unroll
-      for (int v = 0; v < TM; ++v)
-        if (tx + 16 * v == c + 1)
-#pragma unroll
-          for (int u = 0; u < TM; ++u) nxt[ty + 16 * u] = a[u][v];
+        for (int u = 0; u < TM; ++u) {
+          nxt[ty + 16 * u] = a[u][v];
+          if (kF64 && ty + 16 * u == c + 1) nxt[NB] = a[u][v] > T(0) ? T(1) / a[u][v] : T(1);
+        }
+      }
     }
     __syncthreads();
   }
@@ -196,46 +246,81 @@ __device__ void tile_potrf(T* Lkk, int ld, T* W, T* S, T* Ls, int* status) {
 #pragma unroll
     for (int v = 0; v < TM; ++v) S[(ty + 16 * u) * LD + tx + 16 * v] = a[u][v];
   __syncthreads();
-  // scale the columns: L[c][c] = sqrt(d_c), L[i][c] = S[i][c] / sqrt(d_c)
-  for (int idx = tid; idx < NB * NB; idx += kThreads) {
-    int i = idx / NB, c = idx % NB;
-    T d = S[c * LD + c];
+  if (tid < NB) {
+    T d = S[tid * LD + tid];
     if (!(d > T(0))) {
-      if (i == c) set_status(status, SLIM_ENOTPD);
+      set_status(status, SLIM_ENOTPD);
       d = T(1);
     }
-    T sd = sqrt(d);
-    T v = (i == c) ? sd : (i > c ? S[i * LD + c] / sd : T(0));
-    Ls[i * LD + c] = v;
+    const T r = sqrt(d);
+    sd[tid] = r;
+    rsd[tid] = T(1) / r;
   }
   __syncthreads();
-  // inverse of the lower-triangular tile, one column per group of TPC lanes:
-  // W[j][j] = 1/L[j][j];  W[i][j] = -(sum_{q=j}^{i-1} L[i][q] W[q][j]) / L[i][i]
-  constexpr int TPC = kThreads / NB;
-  const int j = tid / TPC, sub = tid % TPC;
-  for (int i = 0; i < NB; ++i) {
-    T s = T(0);
-    if (i > j)
-      for (int q = j + sub; q < i; q += TPC) s += Ls[i * LD + q] * S[q * LD + j];
-    // every lane takes part in the reduction (groups of one warp differ in branch)
-#pragma unroll
-    for (int o = TPC / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPC);
-    T v = (i < j) ? T(0) : (i == j ? T(1) / Ls[j * LD + j] : -s / Ls[i * LD + i]);
-    __syncwarp();
-    if (sub == 0) S[i * LD + j] = v;   // S now holds W column by column
-    __syncwarp();
-  }
-  __syncthreads();
+  // scale the columns: L[c][c] = sqrt(d_c), L[i][c] = S[i][c] / sqrt(d_c)
   for (int idx = tid; idx < NB * NB; idx += kThreads) {
-    int r = idx / NB, c = idx % NB;
-    stcg(Lkk + (size_t)r * ld + c, Ls[r * LD + c]);
-    stcg(W + (size_t)r * NB + c, S[r * LD + c]);
+    const int i = idx / NB, c = idx % NB;
+    S[i * LD + c] = (i == c) ? sd[c] : (i > c ? S[i * LD + c] * rsd[c] : T(0));
+  }
+  __syncthreads();
+  constexpr int NBLK = NB / 16;
+  constexpr int TPB = kThreads / NBLK;      // threads per diagonal block
+  constexpr int TPC = TPB / 16;             // threads per column of a block
+  T* Wt = Ls;
+  for (int idx = tid; idx < NB * NB; idx += kThreads) {
+    const int i = idx / NB, c = idx % NB;
+    if (i / 16 != c / 16 || i < c) Wt[i * LD + c] = T(0);
+  }
+  {
+    const int blk = tid / TPB, jl = (tid % TPB) / TPC, sub = tid % TPC;
+    const int base = blk * 16, j = base + jl;
+    for (int il = 0; il < 16; ++il) {
+      const int i = base + il;
+      T sacc = T(0);
+      if (il > jl)
+        for (int q = j + sub; q < i; q += TPC) sacc += S[i * LD + q] * Wt[q * LD + j];
+#pragma unroll
+      for (int o = TPC / 2; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o, TPC);
+      __syncwarp();
+      if (sub == 0 && il >= jl) Wt[i * LD + j] = (il == jl) ? rsd[j] : -sacc * rsd[i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  T* Tmp = Ls + NB * gemm_ld(NB);   // sum_k L_ik W_kj, 16 x 16 per block of a diagonal
+  for (int d = 1; d < NBLK; ++d) {
+    const int nblk = NBLK - d;          // blocks (i, i-d) on this diagonal
+    for (int idx = tid; idx < nblk * 256; idx += kThreads) {
+      const int bi = idx / 256, e = idx % 256, r = e / 16, c = e % 16;
+      const int i = bi + d, j = bi;
+      T acc = T(0);
+      for (int k = j; k < i; ++k)
+#pragma unroll 4
+        for (int q = 0; q < 16; ++q)
+          acc += S[(i * 16 + r) * LD + k * 16 + q] * Wt[(k * 16 + q) * LD + j * 16 + c];
+      Tmp[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nblk * 256; idx += kThreads) {
+      const int bi = idx / 256, e = idx % 256, r = e / 16, c = e % 16;
+      const int i = bi + d, j = bi;
+      T acc = T(0);
+#pragma unroll 4
+      for (int q = 0; q < 16; ++q) acc += Wt[(i * 16 + r) * LD + i * 16 + q] * Tmp[bi * 256 + q * 16 + c];
+      Wt[(i * 16 + r) * LD + j * 16 + c] = -acc;
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < NB * NB; idx += kThreads) {
+    const int r = idx / NB, c = idx % NB;
+    stcg(Lkk + (size_t)r * ld + c, S[r * LD + c]);
+    stcg(W + (size_t)r * NB + c, Wt[r * LD + c]);
   }
   __syncthreads();
 }
 
 template <typename T, int NB>
-__global__ void __launch_bounds__(kThreads) chol_factor_kernel(T* L, int P, int Tt,
+__global__ void __launch_bounds__(kThreads, 2) chol_factor_kernel(T* L, int P, int Tt,
                                                                const CholTask* tasks, int ntasks,
                                                                int* cnt, int* ticket, T* winv,
                                                                int* status, int* abort_flag) {
@@ -439,7 +524,7 @@ __global__ void __launch_bounds__(kThreads) chol_bwd_kernel(const T* L, int P, i
 }
 
 template <typename T, int NB>
-size_t factor_smem() { return 2 * NB * gemm_ld(NB) * sizeof(T); }
+size_t factor_smem() { return (2 * NB * gemm_ld(NB) + potrf_tmp_elems(NB)) * sizeof(T); }
 
 template <typename T, int NB>
 cudaError_t launch_factor(const CholPlan& p, void* L, int* status, cudaStream_t s) {
