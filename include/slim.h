@@ -70,7 +70,13 @@ enum { SLIM_BLOCKS_VIEWS = 0 };
  *   det_u      D detector bins per view, unit spacing, centred
  *   det_v      1 in 2D
  *   angles     host array [n_views] of radians, or NULL for theta_a = a*pi/A_v
- *   a_mode     0: rows generated on the fly (matrix-free); no other value yet
+ *   a_mode     0: rows generated on the fly by the projector (matrix-free);
+ *              1: all of A built once on the device and stored as CSR (plus a
+ *                 CSC copy) with float32 values; 2: the same with bfloat16
+ *                 values (Sec. 4.2: blocks may be stored when A fits in memory).
+ *                 The step then reads its rows from the stored matrix, and the
+ *                 method runs on that (rounded) A: residual, Gram and scatter
+ *                 all use the stored values.
  *   precision  SLIM_PREC_FP64: x, b, residual and scatter in float64;
  *              SLIM_PREC_FP32: x, b, residual and scatter in float32 with float32
  *              accumulation.  The Gram matrix is float64 in both. */
@@ -187,15 +193,22 @@ slim_status slim_restore(slim_ctx* ctx, const void* buf, size_t len);
  * row-major) and the last solution z (p doubles).  Host pointers; any may be NULL. */
 slim_status slim_get_memory(slim_ctx* ctx, int* ray_ids, double* G, double* z);
 
+/* The stored matrix of a context with a_mode 1 or 2: *nnz, and (if not NULL)
+ * row_ptr [m+1], col [nnz] and the values as float32 [nnz] (host buffers).
+ * SLIM_ESTATE for a matrix-free context. */
+slim_status slim_get_csr(slim_ctx* ctx, long long* nnz, int* row_ptr, int* col, float* val);
+
 /* Sizes: n unknowns, m rows, p = (r+1)*ell. */
 slim_status slim_get_sizes(const slim_ctx* ctx, long long* n, long long* m, int* p);
 
 /* Forward projection y = A_S x for the rays listed in ray_ids (device array of
  * count ints; NULL = all m rays in order).  x and y are device arrays of the
- * context precision.  Enqueued on the context stream. */
+ * context precision.  Enqueued on the context stream.  With a stored matrix
+ * this streams the CSR (the full pass is an HBM-bound SpMV). */
 slim_status slim_project(slim_ctx* ctx, const int* ray_ids, int count, const void* x, void* y);
 
-/* Back projection x += A_S^T y for the listed rays (device arrays as above). */
+/* Back projection x += A_S^T y for the listed rays (device arrays as above).
+ * With a stored matrix and ray_ids == NULL this streams the CSC copy. */
 slim_status slim_backproject(slim_ctx* ctx, const int* ray_ids, int count, const void* y,
                              void* x);
 

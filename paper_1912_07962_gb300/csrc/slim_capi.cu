@@ -16,6 +16,8 @@ struct slim_ctx {
   int N = 0, n_views = 0, D = 0;
   long long n = 0, m = 0;
   int precision = SLIM_PREC_FP64, solver = SLIM_SOLVE_FP64, refine_iters = 2, use_graph = 0;
+  int a_mode = 0;                 // 0 rows from the projector, 1/2 stored float32/bfloat16 rows
+  CsrStore csr;
   int ramp = 0, r = 0, nslots = 1, ell = 0, p = 0, P = 0, taps = 0, nb = 32;
   double lam = 0.0, eta = 1.0;
   unsigned long long seed = 0;
@@ -174,6 +176,10 @@ StepArgs<T> make_args(slim_ctx* c) {
   a.x = (T*)c->d_x;
   a.b = (const T*)c->d_b;
   a.status = c->d_status;
+  a.csr_ptr = c->a_mode ? c->csr.row_ptr : nullptr;
+  a.csr_col = c->a_mode ? c->csr.col : nullptr;
+  a.csr_val = c->a_mode ? c->csr.val : nullptr;
+  a.csr_bf16 = c->csr.bf16;
   return a;
 }
 
@@ -309,6 +315,7 @@ void free_all(slim_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   chol_plan_destroy(&c->plan);
+  free_csr(&c->csr);
   for (cudaEvent_t e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -331,7 +338,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
   *out = nullptr;
   if (!geom || !blocks) return SLIM_EINVAL;
   if (geom->dim != 2 || geom->det_v != 1) return SLIM_ENOTSUP;
-  if (geom->a_mode != 0) return SLIM_ENOTSUP;
+  if (geom->a_mode < 0 || geom->a_mode > 2) return SLIM_EINVAL;
   if (geom->n_side < 2 || geom->n_side > 16384 || geom->n_views < 1 || geom->det_u < 1)
     return SLIM_EINVAL;
   if (geom->precision != SLIM_PREC_FP64 && geom->precision != SLIM_PREC_FP32) return SLIM_EINVAL;
@@ -346,6 +353,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
   c->n = (long long)c->N * c->N;
   c->m = (long long)c->n_views * c->D;
   c->precision = geom->precision;
+  c->a_mode = geom->a_mode;
   c->r = r;
   c->nslots = r + 1;
   c->ell = blocks->ell;
@@ -434,6 +442,9 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     chk(cudaMemset(c->d_z, 0, (size_t)c->P * sizeof(double)), "memset");
     chk(chol_plan_create(&c->plan, c->P, c->nb, c->solver == SLIM_SOLVE_MIXED ? 1 : 0, c->num_sms),
         "chol plan");
+    if (st == SLIM_OK && c->a_mode != 0)
+      chk(build_csr(c->d_views, c->N, c->D, c->m, c->n, c->a_mode == 2, &c->csr, c->stream),
+          "stored matrix");
     size_t gsmem = 8 * (size_t)c->ell * sizeof(double);
     if (gsmem > 200 * 1024) st = fail(c, SLIM_ENOTSUP, "ell too large for the Gram kernel");
   }
@@ -693,6 +704,33 @@ slim_status slim_get_memory(slim_ctx* c, int* ids, double* G, double* z) {
   return read_status(c);
 }
 
+slim_status slim_get_csr(slim_ctx* c, long long* nnz, int* row_ptr, int* col, float* val) {
+  if (!c || !nnz) return SLIM_EINVAL;
+  if (!c->a_mode) return fail(c, SLIM_ESTATE, "the context stores no matrix");
+  *nnz = c->csr.nnz;
+  CK(cudaStreamSynchronize(c->stream), "get_csr");
+  if (row_ptr)
+    CK(cudaMemcpy(row_ptr, c->csr.row_ptr, (size_t)(c->m + 1) * sizeof(int), cudaMemcpyDeviceToHost),
+       "get_csr");
+  if (col)
+    CK(cudaMemcpy(col, c->csr.col, (size_t)c->csr.nnz * sizeof(int), cudaMemcpyDeviceToHost),
+       "get_csr");
+  if (val) {
+    if (c->csr.bf16) {
+      std::vector<uint16_t> raw((size_t)c->csr.nnz);
+      CK(cudaMemcpy(raw.data(), c->csr.val, raw.size() * 2, cudaMemcpyDeviceToHost), "get_csr");
+      for (size_t e = 0; e < raw.size(); ++e) {
+        uint32_t bits = (uint32_t)raw[e] << 16;
+        memcpy(&val[e], &bits, 4);
+      }
+    } else {
+      CK(cudaMemcpy(val, c->csr.val, (size_t)c->csr.nnz * sizeof(float), cudaMemcpyDeviceToHost),
+         "get_csr");
+    }
+  }
+  return SLIM_OK;
+}
+
 slim_status slim_get_sizes(const slim_ctx* c, long long* n, long long* m, int* p) {
   if (!c) return SLIM_EINVAL;
   if (n) *n = c->n;
@@ -705,6 +743,15 @@ slim_status slim_project(slim_ctx* c, const int* ids, int count, const void* x, 
   if (!c || !x || !y) return fail(c, SLIM_EINVAL, "project: bad arguments");
   if (!ids) count = (int)c->m;
   if (count < 0) return fail(c, SLIM_EINVAL, "project: bad count");
+  if (c->a_mode) {
+    if (c->precision == SLIM_PREC_FP32)
+      CK(launch_csr_project<float>(c->csr, ids, count, (const float*)x, (float*)y, c->stream),
+         "project");
+    else
+      CK(launch_csr_project<double>(c->csr, ids, count, (const double*)x, (double*)y, c->stream),
+         "project");
+    return SLIM_OK;
+  }
   if (c->precision == SLIM_PREC_FP32)
     CK(launch_project<float>(c->d_views, c->N, c->D, ids, count, (const float*)x, (float*)y,
                              c->stream), "project");
@@ -718,6 +765,15 @@ slim_status slim_backproject(slim_ctx* c, const int* ids, int count, const void*
   if (!c || !x || !y) return fail(c, SLIM_EINVAL, "backproject: bad arguments");
   if (!ids) count = (int)c->m;
   if (count < 0) return fail(c, SLIM_EINVAL, "backproject: bad count");
+  if (c->a_mode) {
+    if (c->precision == SLIM_PREC_FP32)
+      CK(launch_csr_backproject<float>(c->csr, c->n, ids, count, (const float*)y, (float*)x,
+                                       c->stream), "backproject");
+    else
+      CK(launch_csr_backproject<double>(c->csr, c->n, ids, count, (const double*)y, (double*)x,
+                                        c->stream), "backproject");
+    return SLIM_OK;
+  }
   if (c->precision == SLIM_PREC_FP32)
     CK(launch_backproject<float>(c->d_views, c->N, c->D, ids, count, (const float*)y, (float*)x,
                                  c->stream), "backproject");

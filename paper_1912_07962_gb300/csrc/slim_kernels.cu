@@ -1,4 +1,7 @@
 // Per-step kernels of the slimLS iteration (Eq. (ram) with the Woodbury form of Eq. (B_k)).
+#include <algorithm>
+#include <cuda_bf16.h>
+
 #include "slim_kernels.cuh"
 
 namespace slim {
@@ -84,6 +87,364 @@ __global__ void __launch_bounds__(kCta) forward_residual_kernel(StepArgs<T> a) {
   if (lane == 0) a.rhs[q] = (double)(acc - a.b[ray]);
 }
 
+__device__ __forceinline__ float csr_value(const void* val, int bf16, long long e) {
+  return bf16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(val)[e])
+              : reinterpret_cast<const float*>(val)[e];
+}
+
+// Step 2 with stored rows: the new block's rows come from the CSR instead of
+// the projector.  Ring taps take the stored values (as float64); map slots are
+// claimed in order (a pixel is in at most two rows of one view).
+template <typename T>
+__global__ void __launch_bounds__(kCta) csr_forward_residual_kernel(StepArgs<T> a) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= a.ell) return;
+  const int q = a.info->slot * a.ell + w;
+  const int ray = a.ring_ids[q];
+  const int e0 = a.csr_ptr[ray], len = a.csr_ptr[ray + 1] - e0;
+  int* rp = a.ring_pix + (size_t)q * a.taps;
+  double* rw = a.ring_w + (size_t)q * a.taps;
+  const long long n = a.n;
+  T acc = T(0);
+  for (int t = lane; t < a.taps; t += 32) {
+    if (t >= len) {
+      rp[t] = -1;
+      rw[t] = 0.0;
+      continue;
+    }
+    const int pix = a.csr_col[e0 + t];
+    const double wv = (double)csr_value(a.csr_val, a.csr_bf16, e0 + t);
+    rp[t] = pix;
+    rw[t] = wv;
+    acc += (T)wv * a.x[pix];
+    if (atomicCAS(&a.map_ray[pix], -1, w) == -1) {
+      a.map_w[pix] = wv;
+    } else if (atomicCAS(&a.map_ray[n + pix], -1, w) == -1) {
+      a.map_w[n + pix] = wv;
+    } else {
+      set_status(a.status, SLIM_EINVAL);
+    }
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) a.rhs[q] = (double)(acc - a.b[ray]);
+}
+
+// ---------------------------------------------------------------------------
+// Building the stored matrix
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCta) csr_count_kernel(const ViewGeom* views, int N, int D,
+                                                         long long m, int* counts) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= m) return;
+  const int ray = (int)w, view = ray / D, d = ray - view * D;
+  const ViewGeom v = views[view];
+  const double cc = 0.5 * (double)(N - 1), t = (double)d - 0.5 * (double)(D - 1);
+  int cnt = 0;
+  for (int s = lane; s < N; s += 32) {
+    Tap2 tp = joseph_step(v, t, cc, s);
+    cnt += (tp.wa != 0.0 && inplane_pixel(v.row_step, N, s, tp.minor0) >= 0);
+    cnt += (tp.wb != 0.0 && inplane_pixel(v.row_step, N, s, tp.minor0 + 1) >= 0);
+  }
+  cnt = warp_sum(cnt);
+  if (lane == 0) counts[ray] = cnt;
+}
+
+// Exclusive scan of n counts into ptr[0..n] by one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) scan_kernel(const int* counts, int* ptr, long long n,
+                                                    long long* total) {
+  __shared__ long long part[1024];
+  const int tid = threadIdx.x;
+  const long long chunk = (n + 1023) / 1024;
+  const long long lo = tid * chunk, hi = min(n, lo + chunk);
+  long long sum = 0;
+  for (long long i = lo; i < hi; ++i) sum += counts[i];
+  part[tid] = sum;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    long long v = tid >= off ? part[tid - off] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  long long run = part[tid] - sum;   // exclusive prefix of this chunk
+  for (long long i = lo; i < hi; ++i) {
+    ptr[i] = (int)run;
+    run += counts[i];
+  }
+  if (tid == 1023) {
+    ptr[n] = (int)part[1023];
+    *total = part[1023];
+  }
+}
+
+// Fill the CSR rows in march order (tap a then tap b per step), as the oracle does.
+__global__ void __launch_bounds__(kCta) csr_fill_kernel(const ViewGeom* views, int N, int D,
+                                                        long long m, const int* row_ptr, int* col,
+                                                        void* val, int bf16) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= m) return;
+  const int ray = (int)w, view = ray / D, d = ray - view * D;
+  const ViewGeom v = views[view];
+  const double cc = 0.5 * (double)(N - 1), t = (double)d - 0.5 * (double)(D - 1);
+  int pos = row_ptr[ray];
+  for (int s0 = 0; s0 < N; s0 += 32) {
+    const int s = s0 + lane;
+    int pa = -1, pb = -1;
+    double wa = 0.0, wb = 0.0;
+    if (s < N) {
+      Tap2 tp = joseph_step(v, t, cc, s);
+      if (tp.wa != 0.0) pa = inplane_pixel(v.row_step, N, s, tp.minor0);
+      if (tp.wb != 0.0) pb = inplane_pixel(v.row_step, N, s, tp.minor0 + 1);
+      wa = tp.wa;
+      wb = tp.wb;
+    }
+    const int c = (pa >= 0) + (pb >= 0);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    int e = pos + incl - c;
+    if (pa >= 0) {
+      col[e] = pa;
+      if (bf16) reinterpret_cast<__nv_bfloat16*>(val)[e] = __float2bfloat16_rn((float)wa);
+      else reinterpret_cast<float*>(val)[e] = (float)wa;
+      ++e;
+    }
+    if (pb >= 0) {
+      col[e] = pb;
+      if (bf16) reinterpret_cast<__nv_bfloat16*>(val)[e] = __float2bfloat16_rn((float)wb);
+      else reinterpret_cast<float*>(val)[e] = (float)wb;
+    }
+    pos += __shfl_sync(0xffffffffu, incl, 31);
+  }
+}
+
+__global__ void csc_count_kernel(const int* col, long long nnz, int* ccount) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nnz;
+       e += (long long)gridDim.x * blockDim.x)
+    atomicAdd(&ccount[col[e]], 1);
+}
+
+__global__ void __launch_bounds__(kCta) csc_fill_kernel(long long m, const int* row_ptr,
+                                                        const int* col, const void* val, int bf16,
+                                                        int* cursor, int* crow, void* cval) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= m) return;
+  for (int e = row_ptr[w] + lane; e < row_ptr[w + 1]; e += 32) {
+    const int j = col[e];
+    const int pos = atomicAdd(&cursor[j], 1);
+    crow[pos] = (int)w;
+    if (bf16) reinterpret_cast<__nv_bfloat16*>(cval)[pos] = reinterpret_cast<const __nv_bfloat16*>(val)[e];
+    else reinterpret_cast<float*>(cval)[pos] = reinterpret_cast<const float*>(val)[e];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Full passes over the stored matrix (HBM streams of the index and value
+// arrays; x or y gathers stay in L2).  One warp per output row (column for
+// the transpose); lanes read consecutive entries; streaming loads bypass L1.
+// ---------------------------------------------------------------------------
+template <typename T, bool BF16>
+__global__ void __launch_bounds__(kCta) spmv_kernel(const int* __restrict__ ptr,
+                                                    const int* __restrict__ idx,
+                                                    const void* __restrict__ val,
+                                                    const int* __restrict__ rows, long long count,
+                                                    const T* __restrict__ x, T* __restrict__ y,
+                                                    int accumulate) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  // the CTA's consecutive rows take their pointers from one coalesced load
+  __shared__ int sptr[kWarpsPerCta + 1];
+  if (!rows) {
+    const long long row0 = (long long)blockIdx.x * kWarpsPerCta;
+    if (threadIdx.x <= kWarpsPerCta && row0 + threadIdx.x <= count)
+      sptr[threadIdx.x] = __ldg(ptr + row0 + threadIdx.x);
+    __syncthreads();
+  }
+  if (w >= count) return;
+  const int r = rows ? rows[w] : (int)w;
+  const int e0 = rows ? __ldg(ptr + r) : sptr[wib];
+  const int e1 = rows ? __ldg(ptr + r + 1) : sptr[wib + 1];
+  // each lane takes 4 consecutive entries per chunk from a 4-aligned base, so
+  // index and value loads are 16-byte (8-byte for bfloat16) vectors; entries
+  // outside [e0, e1) are masked.  The loads of up to kBatch chunks are issued
+  // before any dependent gather of x, to keep enough bytes in flight.
+  constexpr int kBatch = 4;
+  T acc = T(0);
+  for (int base0 = (e0 & ~3) + 4 * lane; base0 - 4 * lane < e1; base0 += 128 * kBatch) {
+    int4 j4[kBatch];
+    float v[kBatch][4];
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      const int base = base0 + 128 * b;
+      if (base < e1) {
+        j4[b] = __ldcs(reinterpret_cast<const int4*>(idx + base));
+        if constexpr (BF16) {
+          const uint2 raw = __ldcs(reinterpret_cast<const uint2*>(
+              reinterpret_cast<const unsigned short*>(val) + base));
+          v[b][0] = __uint_as_float(raw.x << 16);
+          v[b][1] = __uint_as_float(raw.x & 0xffff0000u);
+          v[b][2] = __uint_as_float(raw.y << 16);
+          v[b][3] = __uint_as_float(raw.y & 0xffff0000u);
+        } else {
+          const float4 f =
+              __ldcs(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(val) + base));
+          v[b][0] = f.x; v[b][1] = f.y; v[b][2] = f.z; v[b][3] = f.w;
+        }
+      } else {
+        j4[b] = make_int4(0, 0, 0, 0);
+        v[b][0] = v[b][1] = v[b][2] = v[b][3] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      const int base = base0 + 128 * b;
+      const int jj[4] = {j4[b].x, j4[b].y, j4[b].z, j4[b].w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int e = base + t;
+        if (e >= e0 && e < e1) acc += (T)v[b][t] * __ldg(x + jj[t]);
+      }
+    }
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) y[w] = accumulate ? y[w] + acc : acc;
+}
+
+// Sort each CSC column by row id (one warp per column, rank sort in shared
+// memory; a ray taps a pixel at most once, so row ids in a column are distinct).
+constexpr int kSortCap = 1024;   // longest column handled (2 x views)
+__global__ void __launch_bounds__(128) csc_sort_kernel(const int* col_ptr, int* row, void* cval,
+                                                       int bf16, long long n) {
+  __shared__ int srow[4][kSortCap];
+  __shared__ unsigned int sval[4][kSortCap];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long j = (long long)blockIdx.x * 4 + wib;
+  if (j >= n) return;
+  const int e0 = col_ptr[j], len = col_ptr[j + 1] - e0;
+  if (len > kSortCap) return;
+  for (int i = lane; i < len; i += 32) {
+    srow[wib][i] = row[e0 + i];
+    sval[wib][i] = bf16 ? (unsigned int)reinterpret_cast<const unsigned short*>(cval)[e0 + i]
+                        : __float_as_uint(reinterpret_cast<const float*>(cval)[e0 + i]);
+  }
+  __syncwarp();
+  for (int i = lane; i < len; i += 32) {
+    const int key = srow[wib][i];
+    int rank = 0;
+    for (int k = 0; k < len; ++k) rank += srow[wib][k] < key;
+    row[e0 + rank] = key;
+    if (bf16) reinterpret_cast<unsigned short*>(cval)[e0 + rank] = (unsigned short)sval[wib][i];
+    else reinterpret_cast<float*>(cval)[e0 + rank] = __uint_as_float(sval[wib][i]);
+  }
+}
+
+// Slice lengths (longest line of each 32-line slice) and the SELL fill.
+__global__ void sell_len_kernel(const int* ptr, long long lines, int* slen) {
+  const long long sidx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long slices = (lines + 31) / 32;
+  if (sidx >= slices) return;
+  int mx = 0;
+  for (int l = 0; l < 32; ++l) {
+    const long long r = sidx * 32 + l;
+    if (r < lines) mx = max(mx, ptr[r + 1] - ptr[r]);
+  }
+  slen[sidx] = 32 * mx;
+}
+
+__global__ void __launch_bounds__(kCta) sell_fill_kernel(const int* ptr, const int* idx,
+                                                         const void* val, int bf16, long long lines,
+                                                         const int* slice_ptr, int* sidx,
+                                                         void* sval) {
+  const long long s = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long slices = (lines + 31) / 32;
+  if (s >= slices) return;
+  const long long r = s * 32 + lane;
+  const int e0 = r < lines ? ptr[r] : 0, len = r < lines ? ptr[r + 1] - e0 : 0;
+  const int depth = (slice_ptr[s + 1] - slice_ptr[s]) / 32;
+  for (int k = 0; k < depth; ++k) {
+    const long long o = slice_ptr[s] + 32LL * k + lane;
+    const bool ok = k < len;
+    sidx[o] = ok ? idx[e0 + k] : 0;
+    if (bf16) reinterpret_cast<unsigned short*>(sval)[o] =
+        ok ? reinterpret_cast<const unsigned short*>(val)[e0 + k] : (unsigned short)0;
+    else reinterpret_cast<float*>(sval)[o] = ok ? reinterpret_cast<const float*>(val)[e0 + k] : 0.f;
+  }
+}
+
+// Full pass over a SELL-32 copy: one slice per CTA of 4 warps; lane l owns
+// line l of the slice and warp w takes entries k = w, w+4, ...; loads are
+// 128-byte coalesced and the gathers of 32 adjacent rays (pixels) at the same
+// step hit neighbouring addresses.
+template <typename T, bool BF16>
+__global__ void __launch_bounds__(128) sell_spmv_kernel(const int* __restrict__ slice_ptr,
+                                                        const int* __restrict__ idx,
+                                                        const void* __restrict__ val,
+                                                        long long lines, const T* __restrict__ x,
+                                                        T* __restrict__ y, int accumulate) {
+  __shared__ T part[4][32];
+  const long long s = blockIdx.x;
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int o0 = __ldg(slice_ptr + s), depth = (__ldg(slice_ptr + s + 1) - o0) / 32;
+  T acc = T(0);
+  int k = wib;
+#pragma unroll 1
+  for (; k + 12 < depth; k += 16) {
+    int j[4];
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long o = o0 + 32LL * (k + 4 * u) + lane;
+      j[u] = __ldcs(idx + o);
+      if constexpr (BF16) v[u] = __uint_as_float(((unsigned)__ldcs(reinterpret_cast<const unsigned short*>(val) + o)) << 16);
+      else v[u] = __ldcs(reinterpret_cast<const float*>(val) + o);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc += (T)v[u] * __ldg(x + j[u]);
+  }
+  for (; k < depth; k += 4) {
+    const long long o = o0 + 32LL * k + lane;
+    const int jj = __ldcs(idx + o);
+    float vv;
+    if constexpr (BF16) vv = __uint_as_float(((unsigned)__ldcs(reinterpret_cast<const unsigned short*>(val) + o)) << 16);
+    else vv = __ldcs(reinterpret_cast<const float*>(val) + o);
+    acc += (T)vv * __ldg(x + jj);
+  }
+  part[wib][lane] = acc;
+  __syncthreads();
+  if (wib == 0) {
+    const long long r = s * 32 + lane;
+    const T t = part[0][lane] + part[1][lane] + part[2][lane] + part[3][lane];
+    if (r < lines) y[r] = accumulate ? y[r] + t : t;
+  }
+}
+
+// x += A_rows^T y through the stored rows (atomics), for a ray subset.
+template <typename T, bool BF16>
+__global__ void __launch_bounds__(kCta) csr_scatter_kernel(const int* ptr, const int* idx,
+                                                           const void* val, const int* rows,
+                                                           int count, const T* y, T* x) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= count) return;
+  const int r = rows[w];
+  const T yv = y[w];
+  for (int e = ptr[r] + lane; e < ptr[r + 1]; e += 32) {
+    float v;
+    if constexpr (BF16) {
+      v = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(val)[e]);
+    } else {
+      v = reinterpret_cast<const float*>(val)[e];
+    }
+    atomicAdd(&x[idx[e]], (T)v * yv);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Step 3: incremental Gram update.  For every ring row q (each retained ray,
 // the new block included) accumulate A_k a_q^T over a_q's stored taps through
@@ -143,7 +504,10 @@ __global__ void __launch_bounds__(kCta) scatter_kernel(StepArgs<T> a) {
     int pix = rp[t];
     if (pix < 0) continue;
     if (c != T(0)) atomicAdd(&a.x[pix], c * (T)rw[t]);
-    if (is_new) a.map_ray[(t & 1) * n + pix] = -1;
+    if (is_new) {
+      a.map_ray[pix] = -1;
+      a.map_ray[n + pix] = -1;
+    }
   }
 }
 
@@ -247,7 +611,159 @@ cudaError_t launch_sample(const StepArgs<T>& a, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_forward_residual(const StepArgs<T>& a, cudaStream_t s) {
-  forward_residual_kernel<T><<<cdiv(a.ell, kWarpsPerCta), kCta, 0, s>>>(a);
+  if (a.csr_ptr)
+    csr_forward_residual_kernel<T><<<cdiv(a.ell, kWarpsPerCta), kCta, 0, s>>>(a);
+  else
+    forward_residual_kernel<T><<<cdiv(a.ell, kWarpsPerCta), kCta, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// SELL-32 copy of a CSR-like (ptr, idx, val) matrix with `lines` lines;
+// `scratch` holds at least (lines+31)/32 + 1 ints.
+cudaError_t build_sell(const int* ptr, const int* idx, const void* val, int bf16, long long lines,
+                       int* scratch, long long* d_total, Sell* out, cudaStream_t s) {
+  const size_t vs = bf16 ? 2 : 4;
+  const long long slices = (lines + 31) / 32;
+  cudaError_t e;
+  out->lines = lines;
+  if ((e = cudaMalloc(&out->slice_ptr, (size_t)(slices + 1) * sizeof(int))) != cudaSuccess) return e;
+  sell_len_kernel<<<cdiv(slices, 256), 256, 0, s>>>(ptr, lines, scratch);
+  scan_kernel<<<1, 1024, 0, s>>>(scratch, out->slice_ptr, slices, d_total);
+  long long stored = 0;
+  if ((e = cudaMemcpyAsync(&stored, d_total, sizeof(stored), cudaMemcpyDeviceToHost, s)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  if (stored >= (1LL << 31)) return cudaErrorInvalidValue;
+  out->stored = stored;
+  if ((e = cudaMalloc(&out->idx, (size_t)stored * sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&out->val, (size_t)stored * vs)) != cudaSuccess) return e;
+  sell_fill_kernel<<<cdiv(slices, kWarpsPerCta), kCta, 0, s>>>(ptr, idx, val, bf16, lines,
+                                                               out->slice_ptr, out->idx, out->val);
+  return cudaGetLastError();
+}
+
+void free_sell(Sell* a) {
+  if (a->slice_ptr) cudaFree(a->slice_ptr);
+  if (a->idx) cudaFree(a->idx);
+  if (a->val) cudaFree(a->val);
+  *a = Sell{};
+}
+
+cudaError_t build_csr(const ViewGeom* views, int N, int D, long long m, long long n, int bf16,
+                      CsrStore* st, cudaStream_t s) {
+  *st = CsrStore{};
+  st->bf16 = bf16;
+  const size_t vs = bf16 ? 2 : 4;
+  int* counts = nullptr;
+  long long* d_total = nullptr;
+  cudaError_t e;
+  if ((e = cudaMalloc(&counts, (size_t)(std::max(m, n) + 1) * sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&d_total, sizeof(long long))) != cudaSuccess) { cudaFree(counts); return e; }
+  auto done = [&](cudaError_t err) { cudaFree(counts); cudaFree(d_total); return err; };
+  if ((e = cudaMalloc(&st->row_ptr, (size_t)(m + 1) * sizeof(int))) != cudaSuccess) return done(e);
+  csr_count_kernel<<<cdiv(m, kWarpsPerCta), kCta, 0, s>>>(views, N, D, m, counts);
+  scan_kernel<<<1, 1024, 0, s>>>(counts, st->row_ptr, m, d_total);
+  if ((e = cudaGetLastError()) != cudaSuccess) return done(e);
+  long long nnz = 0;
+  if ((e = cudaMemcpyAsync(&nnz, d_total, sizeof(nnz), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return done(e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return done(e);
+  if (nnz >= (1LL << 31)) return done(cudaErrorInvalidValue);
+  st->nnz = nnz;
+  // a row of at most 2N - 3 entries lies in one aligned window of 2N entries
+  st->max_row = 2 * N;
+  // arrays padded by 4 entries: vector loads start at a 4-aligned index <= the
+  // last entry and read up to 3 entries past it (masked out)
+  const size_t pad = 4;
+  if ((e = cudaMalloc(&st->col, ((size_t)nnz + pad) * sizeof(int))) != cudaSuccess) return done(e);
+  if ((e = cudaMalloc(&st->val, ((size_t)nnz + pad) * vs)) != cudaSuccess) return done(e);
+  csr_fill_kernel<<<cdiv(m, kWarpsPerCta), kCta, 0, s>>>(views, N, D, m, st->row_ptr, st->col,
+                                                         st->val, bf16);
+  // CSC copy: counts per pixel, scan, fill by atomic cursors
+  if ((e = cudaMalloc(&st->col_ptr, (size_t)(n + 1) * sizeof(int))) != cudaSuccess) return done(e);
+  if ((e = cudaMalloc(&st->row, ((size_t)nnz + pad) * sizeof(int))) != cudaSuccess) return done(e);
+  if ((e = cudaMalloc(&st->cval, ((size_t)nnz + pad) * vs)) != cudaSuccess) return done(e);
+  // the padding is read (then masked), so give it defined contents
+  if ((e = cudaMemsetAsync(st->col + nnz, 0, pad * sizeof(int), s)) != cudaSuccess) return done(e);
+  if ((e = cudaMemsetAsync(st->row + nnz, 0, pad * sizeof(int), s)) != cudaSuccess) return done(e);
+  if ((e = cudaMemsetAsync((char*)st->val + nnz * vs, 0, pad * vs, s)) != cudaSuccess) return done(e);
+  if ((e = cudaMemsetAsync((char*)st->cval + nnz * vs, 0, pad * vs, s)) != cudaSuccess) return done(e);
+  if ((e = cudaMemsetAsync(counts, 0, (size_t)(n + 1) * sizeof(int), s)) != cudaSuccess) return done(e);
+  csc_count_kernel<<<152 * 8, 256, 0, s>>>(st->col, nnz, counts);
+  // a pixel is tapped at most twice per view, so a column has at most 2 A_v entries
+  st->max_col = 2 * (int)(m / D);
+  scan_kernel<<<1, 1024, 0, s>>>(counts, st->col_ptr, n, d_total);
+  if ((e = cudaMemcpyAsync(counts, st->col_ptr, (size_t)n * sizeof(int), cudaMemcpyDeviceToDevice,
+                           s)) != cudaSuccess)
+    return done(e);
+  csc_fill_kernel<<<cdiv(m, kWarpsPerCta), kCta, 0, s>>>(m, st->row_ptr, st->col, st->val, bf16,
+                                                         counts, st->row, st->cval);
+  if (st->max_col > kSortCap) return done(cudaErrorInvalidValue);
+  csc_sort_kernel<<<cdiv(n, 4), 128, 0, s>>>(st->col_ptr, st->row, st->cval, bf16, n);
+  if ((e = cudaGetLastError()) != cudaSuccess) return done(e);
+  if ((e = build_sell(st->col_ptr, st->row, st->cval, bf16, n, counts, d_total, &st->cols32, s)) !=
+      cudaSuccess)
+    return done(e);
+  return done(cudaStreamSynchronize(s));
+}
+
+void free_csr(CsrStore* st) {
+  free_sell(&st->cols32);
+  void* ptrs[] = {st->row_ptr, st->col, st->val, st->col_ptr, st->row, st->cval};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  *st = CsrStore{};
+}
+
+template <typename T, bool BF16>
+void launch_spmv(const int* ptr, const int* idx, const void* val, const int* rows,
+                 long long count, const T* x, T* y, int accumulate, int /*max_len*/,
+                 cudaStream_t s) {
+  spmv_kernel<T, BF16><<<cdiv(count, kWarpsPerCta), kCta, 0, s>>>(ptr, idx, val, rows, count, x, y,
+                                                                  accumulate);
+}
+
+template <typename T>
+cudaError_t launch_csr_project(const CsrStore& a, const int* ids, int count, const T* x, T* y,
+                               cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (!ids) {
+    // rays entering the image at different rows misalign a sliced layout, so
+    // the forward pass streams the CSR one warp per ray
+    if (a.bf16) launch_spmv<T, true>(a.row_ptr, a.col, a.val, nullptr, count, x, y, 0, a.max_row, s);
+    else launch_spmv<T, false>(a.row_ptr, a.col, a.val, nullptr, count, x, y, 0, a.max_row, s);
+    return cudaGetLastError();
+  }
+  if (a.bf16)
+    spmv_kernel<T, true><<<cdiv(count, kWarpsPerCta), kCta, 0, s>>>(a.row_ptr, a.col, a.val, ids,
+                                                                      count, x, y, 0);
+  else
+    spmv_kernel<T, false><<<cdiv(count, kWarpsPerCta), kCta, 0, s>>>(a.row_ptr, a.col, a.val, ids,
+                                                                       count, x, y, 0);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_csr_backproject(const CsrStore& a, long long n, const int* ids, int count,
+                                   const T* y, T* x, cudaStream_t s) {
+  if (!ids) {
+    // x += A^T y: lines of A^T are pixels (the SELL copy of the CSC)
+    const Sell& q = a.cols32;
+    const long long slices = (q.lines + 31) / 32;
+    if (a.bf16)
+      sell_spmv_kernel<T, true><<<(int)slices, 128, 0, s>>>(q.slice_ptr, q.idx, q.val, q.lines, y, x, 1);
+    else
+      sell_spmv_kernel<T, false><<<(int)slices, 128, 0, s>>>(q.slice_ptr, q.idx, q.val, q.lines, y, x, 1);
+    return cudaGetLastError();
+  }
+  if (count <= 0) return cudaSuccess;
+  if (a.bf16)
+    csr_scatter_kernel<T, true><<<cdiv(count, kWarpsPerCta), kCta, 0, s>>>(a.row_ptr, a.col, a.val,
+                                                                            ids, count, y, x);
+  else
+    csr_scatter_kernel<T, false><<<cdiv(count, kWarpsPerCta), kCta, 0, s>>>(a.row_ptr, a.col,
+                                                                             a.val, ids, count, y, x);
   return cudaGetLastError();
 }
 
@@ -313,6 +829,10 @@ cudaError_t launch_rel_err(const T* x, const double* ref, long long n, double* o
 }
 
 #define SLIM_INSTANTIATE(T)                                                                     \
+  template cudaError_t launch_csr_project<T>(const CsrStore&, const int*, int, const T*, T*,     \
+                                             cudaStream_t);                                     \
+  template cudaError_t launch_csr_backproject<T>(const CsrStore&, long long, const int*, int,    \
+                                                 const T*, T*, cudaStream_t);                   \
   template cudaError_t launch_sample<T>(const StepArgs<T>&, cudaStream_t);                    \
   template cudaError_t launch_forward_residual<T>(const StepArgs<T>&, cudaStream_t);          \
   template cudaError_t launch_gram_update<T>(const StepArgs<T>&, cudaStream_t);               \

@@ -30,7 +30,55 @@ struct StepArgs {
   T* x;                    // [n]
   const T* b;              // [m]
   int* status;
+  // stored rows of A (a_mode 1: float32 values, 2: bfloat16 values); null if
+  // the rows are generated by the projector
+  const int* csr_ptr;      // [m+1]
+  const int* csr_col;      // [nnz]
+  const void* csr_val;     // [nnz]
+  int csr_bf16;
 };
+
+// Sliced ELLPACK with slices of 32 lines (SELL-32): line l of slice s has its
+// entry k at slice_ptr[s] + 32 k + (l mod 32); short lines are padded with
+// index 0 and value 0.
+struct Sell {
+  long long lines = 0;      // rows (or columns) covered
+  long long stored = 0;     // entries including padding
+  int* slice_ptr = nullptr; // [slices+1] offsets of the slices
+  int* idx = nullptr;       // [stored]
+  void* val = nullptr;      // [stored]
+};
+
+// Stored A: CSR by rays and a CSC copy by pixels, values float32 or bfloat16.
+struct CsrStore {
+  long long nnz = 0;
+  int bf16 = 0;
+  int max_row = 0;          // bound on the entries of a row (2N)
+  int max_col = 0;          // bound on the entries of a column (2 A_v)
+  int* row_ptr = nullptr;   // [m+1]
+  int* col = nullptr;       // [nnz]
+  void* val = nullptr;      // [nnz]
+  int* col_ptr = nullptr;   // [n+1]
+  int* row = nullptr;       // [nnz]
+  void* cval = nullptr;     // [nnz]
+  // SELL-32 copy of the CSC for the transposed full pass: slices of 32
+  // consecutive pixels, each pixel's entries in ray order
+  Sell cols32;
+};
+
+// Build the stored rows of all m rays from the projector (values rounded to
+// float32 or bfloat16), and the CSC copy.  Allocates the arrays in `st`.
+cudaError_t build_csr(const ViewGeom* views, int N, int D, long long m, long long n, int bf16,
+                      CsrStore* st, cudaStream_t s);
+void free_csr(CsrStore* st);
+
+// y[i] = A_{ids[i]} x over stored rows (ids == nullptr: all m rows), and
+// x += A^T y over all rows using the CSC copy (ids == nullptr) or the rows.
+template <typename T> cudaError_t launch_csr_project(const CsrStore& a, const int* ids, int count,
+                                                     const T* x, T* y, cudaStream_t s);
+template <typename T> cudaError_t launch_csr_backproject(const CsrStore& a, long long n,
+                                                         const int* ids, int count, const T* y,
+                                                         T* x, cudaStream_t s);
 
 template <typename T> cudaError_t launch_sample(const StepArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_forward_residual(const StepArgs<T>& a, cudaStream_t s);

@@ -30,8 +30,9 @@ EXPORTS = [
     "slim_set_x", "slim_get_x", "slim_step", "slim_sync", "slim_set_ref", "slim_run",
     "slim_get_iter", "slim_set_iter", "slim_checkpoint", "slim_restore", "slim_get_memory",
     "slim_get_sizes", "slim_project", "slim_backproject", "slim_damped_solve",
-    "slim_set_timing", "slim_get_timing", "slim_damped_solve_noalloc",
+    "slim_set_timing", "slim_get_timing", "slim_damped_solve_noalloc", "slim_get_csr",
 ]
+A_MATRIX_FREE, A_CSR_F32, A_CSR_BF16 = 0, 1, 2
 NOALLOC_MAX_P = 1024
 PHASES = ["sample", "forward_residual", "gram_update", "form_k", "factor", "solve", "scatter"]
 
@@ -95,6 +96,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "slim_set_timing": ([VP, I], I),
         "slim_get_timing": ([VP, P(D), I, P(I)], I),
         "slim_damped_solve_noalloc": ([VP, I, D, VP, VP, VP], I),
+        "slim_get_csr": ([VP, P(LL), VP, VP, VP], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -126,11 +128,11 @@ class Slim:
 
     def __init__(self, N, n_views, det, ell, r, lam, seed, precision=SLIM_PREC_FP64,
                  solver=SLIM_SOLVE_FP64, refine_iters=2, eta=1.0, ramp=False, use_graph=False,
-                 angles=None):
+                 angles=None, a_mode=A_MATRIX_FREE):
         lib = load()
         self._lib = lib
         self._angles = None
-        g = slim_geometry(2, N, n_views, det, 1, None, 0, precision)
+        g = slim_geometry(2, N, n_views, det, 1, None, a_mode, precision)
         if angles is not None:
             self._angles = np.ascontiguousarray(angles, dtype=np.float64)
             g.angles = self._angles.ctypes.data_as(C.POINTER(C.c_double))
@@ -240,6 +242,17 @@ class Slim:
         self._check(self._lib.slim_get_memory(self.h, ids.ctypes.data, G.ctypes.data,
                                               z.ctypes.data))
         return ids, G, z
+
+    def get_csr(self):
+        """(row_ptr, col, values as float32) of the stored matrix."""
+        nnz = C.c_longlong()
+        self._check(self._lib.slim_get_csr(self.h, C.byref(nnz), None, None, None))
+        rp = np.empty(self.m + 1, dtype=np.int32)
+        col = np.empty(nnz.value, dtype=np.int32)
+        val = np.empty(nnz.value, dtype=np.float32)
+        self._check(self._lib.slim_get_csr(self.h, C.byref(nnz), rp.ctypes.data, col.ctypes.data,
+                                           val.ctypes.data))
+        return rp, col, val
 
     def project(self, x, y, ray_ids=None):
         ids = C.c_void_p(ray_ids.data_ptr()) if ray_ids is not None else None
