@@ -231,18 +231,18 @@ def roofline_of(phases_ms, K, p, ell, N, form, clocks_mhz):
 
 
 def traffic_from_profiles(kernel):
-    """dram bytes per launch recorded by the committed ncu summary, if the kernel
-    sources have not changed since."""
+    """dram bytes per launch recorded from an ncu capture (profiles/traffic.json), or
+    None when the kernel's sources changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path))
-    h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1912_07962_gb300", "csrc"))):
-        h.update(open(os.path.join(ROOT, "paper_1912_07962_gb300", "csrc", f), "rb").read())
-    if rec.get("csrc_sha256") != h.hexdigest():
+    rec = json.load(open(path)).get("kernels", {}).get(kernel)
+    if not rec:
         return None
-    return rec.get("kernels", {}).get(kernel)
+    h = hashlib.sha256()
+    for f in rec["sources"]:
+        h.update(open(os.path.join(ROOT, "paper_1912_07962_gb300", "csrc", f), "rb").read())
+    return rec["bytes"] if h.hexdigest() == rec["sha256"] else None
 
 
 def tta_block(sl, cfg, b, flush, stream, epochs, thresholds):
