@@ -61,14 +61,17 @@ typedef enum {
 enum { SLIM_F32 = 0, SLIM_F64 = 1 };
 enum { SLIM_PREC_FP64 = 0, SLIM_PREC_FP32 = 1 };
 enum { SLIM_SOLVE_FP64 = 0, SLIM_SOLVE_MIXED = 1 };
-enum { SLIM_BLOCKS_VIEWS = 0 };
+enum { SLIM_BLOCKS_VIEWS = 0, SLIM_BLOCKS_RAYS = 1, SLIM_BLOCKS_STREAM = 2 };
 
 /* Parallel-beam geometry (Sec. 4.3; Joseph rows defined in the library docs).
- *   dim        2 (only 2D is supported by this version)
- *   n_side     N, image is N x N (n = N^2 unknowns)
+ *   dim        2 (image N x N) or 3 (volume N x N x N, x[(iz*N + iy)*N + ix],
+ *              views rotating about z)
+ *   n_side     N
  *   n_views    A_v projection angles
- *   det_u      D detector bins per view, unit spacing, centred
- *   det_v      1 in 2D
+ *   det_u      D detector bins per view row, unit spacing, centred
+ *   det_v      1 in 2D; in 3D the detector rows, which must equal N: row v
+ *              then lies in z-slice v, rays of different slices share no voxel
+ *              and the Gram matrix is block diagonal by slice
  *   angles     host array [n_views] of radians, or NULL for theta_a = a*pi/A_v
  *   a_mode     0: rows generated on the fly by the projector (matrix-free);
  *              1: all of A built once on the device and stored as CSR (plus a
@@ -92,15 +95,22 @@ typedef struct {
 } slim_geometry;
 
 /* Block sampling (Sec. 1: W_k i.i.d. uniform over M selectors).
- *   kind   SLIM_BLOCKS_VIEWS: one view per block, M = n_views, drawn uniformly
- *          with replacement; ell must equal det_u
+ *   kind   SLIM_BLOCKS_VIEWS (2D): one view per block, M = n_views, drawn
+ *          uniformly with replacement; ell must equal det_u.  Step k draws view
+ *          bounded(draw(seed, 2, k-1), A_v).
+ *          SLIM_BLOCKS_RAYS: ell rays, each uniform over all m rays.
+ *          SLIM_BLOCKS_STREAM (streaming data, Sec. 4.3): views arrive in angle
+ *          order, view v from step steps_per_view*v + 1; each of the ell rays is
+ *          uniform over the rays of the views that have arrived.  Ray i of step
+ *          k is bounded(draw(seed, 3, (k-1)*ell + i), available rays).
  *   ell    rows per block
- *   seed   generator seed; step k draws view bounded(draw(seed, 2, k-1), A_v) */
+ *   seed   generator seed
+ *   steps_per_view  SLIM_BLOCKS_STREAM only */
 typedef struct {
   int kind;
   int ell;
   unsigned long long seed;
-  int reserved;
+  int steps_per_view;
 } slim_blocks;
 
 /* Step options.

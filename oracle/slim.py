@@ -144,6 +144,16 @@ def random_ray_schedule(seed: int, ell: int, n_avail: int, steps: int, k0: int =
         yield np.array(rng.random_rays(seed, k, ell, n_avail), dtype=np.int64)
 
 
+def streaming_ray_schedule(seed: int, ell: int, n_views: int, rays_per_view: int,
+                           steps_per_view: int, steps: int, k0: int = 1):
+    """Streaming data (Sec. 4.3, 3D streaming): views arrive in angle order, view v
+    from step steps_per_view * v + 1 on; step k draws ell rays uniformly from the
+    views that have arrived."""
+    for k in range(k0, k0 + steps):
+        arrived = min(n_views, (k - 1) // steps_per_view + 1)
+        yield np.array(rng.random_rays(seed, k, ell, arrived * rays_per_view), dtype=np.int64)
+
+
 def contiguous_block_ids(i: int, ell: int) -> np.ndarray:
     """Sec. 4.1's selectors W^(i): rows ell*i .. ell*i + ell - 1 (0-based i)."""
     return np.arange(ell * i, ell * (i + 1))

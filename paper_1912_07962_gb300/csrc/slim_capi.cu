@@ -8,6 +8,7 @@
 #include "../../include/slim.h"
 #include "slim_chol.cuh"
 #include "slim_kernels.cuh"
+#include "slim_rays.cuh"
 
 using namespace slim;
 
@@ -18,6 +19,10 @@ struct slim_ctx {
   int precision = SLIM_PREC_FP64, solver = SLIM_SOLVE_FP64, refine_iters = 2, use_graph = 0;
   int a_mode = 0;                 // 0 rows from the projector, 1/2 stored float32/bfloat16 rows
   CsrStore csr;
+  int dim = 2, Dv = 1, kind = SLIM_BLOCKS_VIEWS, steps_per_view = 1;
+  int S = 0, cap = 0;             // 3D: slices and the largest slice block solved
+  int* d_slice_cnt = nullptr;
+  int* d_slice_rows = nullptr;
   int ramp = 0, r = 0, nslots = 1, ell = 0, p = 0, P = 0, taps = 0, nb = 32;
   double lam = 0.0, eta = 1.0;
   unsigned long long seed = 0;
@@ -183,6 +188,43 @@ StepArgs<T> make_args(slim_ctx* c) {
   return a;
 }
 
+RayArgs make_ray_args(slim_ctx* c) {
+  RayArgs a;
+  a.info = c->d_info;
+  a.done = c->d_done;
+  a.views = c->d_views;
+  a.N = c->N;
+  a.Du = c->D;
+  a.Dv = c->Dv;
+  a.n_views = c->n_views;
+  a.dim = c->dim;
+  a.n = c->n;
+  a.m = c->m;
+  a.ell = c->ell;
+  a.nslots = c->nslots;
+  a.r = c->r;
+  a.p = c->p;
+  a.taps = c->taps;
+  a.kind = c->kind;
+  a.steps_per_view = c->steps_per_view;
+  a.seed = c->seed;
+  a.lam = c->lam;
+  a.ramp = c->ramp;
+  a.ring_ids = c->d_ring_ids;
+  a.ring_pix = c->d_ring_pix;
+  a.ring_w = c->d_ring_w;
+  a.rhs = c->d_rhs;
+  a.z = c->d_z;
+  a.status = c->d_status;
+  a.G = c->d_G;
+  a.P = c->P;
+  a.S = c->S;
+  a.cap = c->cap;
+  a.slice_cnt = c->d_slice_cnt;
+  a.slice_rows = c->d_slice_rows;
+  return a;
+}
+
 // Phase boundaries recorded when timing is on (event i closes phase i-1).
 enum { kPhSample = 1, kPhForward, kPhGram, kPhFormK, kPhFactor, kPhSolve, kPhScatter };
 
@@ -197,6 +239,7 @@ cudaError_t mark(slim_ctx* c, int i) {
 // Kernels one step launches (sample, forward, Gram, K, factor, 2 per solve,
 // 2 per refinement round, scatter).
 int kernels_per_step(const slim_ctx* c) {
+  if (c->dim == 3) return 6;   // sample, march, collect, slice Gram, slice solve, scatter
   int solves = c->solver == SLIM_SOLVE_MIXED ? 1 + c->refine_iters : 1;
   int refine = c->solver == SLIM_SOLVE_MIXED ? 2 * c->refine_iters : 0;
   return 5 + 2 * solves + refine + 1;
@@ -232,8 +275,39 @@ cudaError_t enqueue_solve(slim_ctx* c) {
   return cudaSuccess;
 }
 
+// A step with random-ray blocks: 2D forms the dense Gram from pair overlaps
+// and uses the tiled solve; 3D solves slice by slice.
+template <typename T>
+cudaError_t enqueue_ray_step_t(slim_ctx* c) {
+  RayArgs ra = make_ray_args(c);
+  StepArgs<T> a = make_args<T>(c);
+  a.map_ray = nullptr;
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  if ((e = mark(c, 0)) != cudaSuccess) return e;
+  if ((e = launch_sample_rays<T>(ra, s)) != cudaSuccess) return e;
+  if ((e = mark(c, kPhSample)) != cudaSuccess) return e;
+  if ((e = launch_forward_rays<T>(ra, (T*)c->d_x, (const T*)c->d_b, s)) != cudaSuccess) return e;
+  if ((e = mark(c, kPhForward)) != cudaSuccess) return e;
+  if (c->dim == 2) {
+    if ((e = launch_gram_pairs(ra, s)) != cudaSuccess) return e;
+    if ((e = mark(c, kPhGram)) != cudaSuccess) return e;
+    if ((e = enqueue_solve(c)) != cudaSuccess) return e;
+  } else {
+    if ((e = launch_slice_collect(ra, s)) != cudaSuccess) return e;
+    if ((e = mark(c, kPhGram)) != cudaSuccess) return e;
+    if ((e = mark(c, kPhFormK)) != cudaSuccess) return e;
+    if ((e = launch_slice_solve(ra, s)) != cudaSuccess) return e;
+    if ((e = mark(c, kPhFactor)) != cudaSuccess) return e;
+  }
+  if ((e = mark(c, kPhSolve)) != cudaSuccess) return e;
+  if ((e = launch_scatter<T>(a, s)) != cudaSuccess) return e;
+  return mark(c, kPhScatter);
+}
+
 template <typename T>
 cudaError_t enqueue_step_t(slim_ctx* c) {
+  if (c->kind != SLIM_BLOCKS_VIEWS) return enqueue_ray_step_t<T>(c);
   StepArgs<T> a = make_args<T>(c);
   cudaError_t e;
   if ((e = mark(c, 0)) != cudaSuccess) return e;
@@ -262,7 +336,8 @@ cudaError_t rebuild_t(slim_ctx* c, long long k) {
     return e;
   if ((e = cudaMemsetAsync(c->d_G, 0, (size_t)c->P * c->P * sizeof(double), s)) != cudaSuccess)
     return e;
-  if ((e = cudaMemsetAsync(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int), s)) != cudaSuccess)
+  if (c->d_map_ray &&
+      (e = cudaMemsetAsync(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int), s)) != cudaSuccess)
     return e;
   StepArgs<T> a = make_args<T>(c);
   long long j0 = k - c->r;
@@ -273,6 +348,14 @@ cudaError_t rebuild_t(slim_ctx* c, long long k) {
         cudaSuccess)
       return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;   // `done` is a host local
+    if (c->kind != SLIM_BLOCKS_VIEWS) {
+      RayArgs ra = make_ray_args(c);
+      if ((e = launch_sample_rays<T>(ra, s)) != cudaSuccess) return e;
+      if ((e = launch_forward_rays<T>(ra, (T*)c->d_x, (const T*)c->d_b, s)) != cudaSuccess) return e;
+      e = c->dim == 2 ? launch_gram_pairs(ra, s) : launch_slice_collect(ra, s);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     if ((e = launch_sample<T>(a, s)) != cudaSuccess) return e;
     if ((e = launch_forward_residual<T>(a, s)) != cudaSuccess) return e;
     if ((e = launch_gram_update<T>(a, s)) != cudaSuccess) return e;
@@ -309,7 +392,7 @@ slim_status read_status(slim_ctx* c) {
 void free_all(slim_ctx* c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
-  void* ptrs[] = {c->d_views, c->d_info, c->d_done, c->d_status, c->d_x, c->d_b,
+  void* ptrs[] = {c->d_slice_cnt, c->d_slice_rows, c->d_views, c->d_info, c->d_done, c->d_status, c->d_x, c->d_b,
                   c->d_ring_ids, c->d_ring_pix, c->d_ring_w, c->d_map_ray, c->d_map_w,
                   c->d_G, c->d_L, c->d_rhs, c->d_z, c->d_dz, c->d_res, c->d_ref, c->d_err};
   for (void* p : ptrs)
@@ -337,21 +420,32 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
   if (!out) return SLIM_EINVAL;
   *out = nullptr;
   if (!geom || !blocks) return SLIM_EINVAL;
-  if (geom->dim != 2 || geom->det_v != 1) return SLIM_ENOTSUP;
+  if (geom->dim != 2 && geom->dim != 3) return SLIM_EINVAL;
+  if (geom->dim == 2 && geom->det_v != 1) return SLIM_EINVAL;
+  if (geom->dim == 3 && geom->det_v != geom->n_side) return SLIM_ENOTSUP;
   if (geom->a_mode < 0 || geom->a_mode > 2) return SLIM_EINVAL;
   if (geom->n_side < 2 || geom->n_side > 16384 || geom->n_views < 1 || geom->det_u < 1)
     return SLIM_EINVAL;
   if (geom->precision != SLIM_PREC_FP64 && geom->precision != SLIM_PREC_FP32) return SLIM_EINVAL;
-  if (blocks->kind != SLIM_BLOCKS_VIEWS) return SLIM_ENOTSUP;
-  if (blocks->ell != geom->det_u) return SLIM_EINVAL;
+  if (blocks->kind < SLIM_BLOCKS_VIEWS || blocks->kind > SLIM_BLOCKS_STREAM) return SLIM_EINVAL;
+  if (blocks->kind == SLIM_BLOCKS_VIEWS && (geom->dim != 2 || blocks->ell != geom->det_u))
+    return SLIM_EINVAL;
+  if (blocks->kind != SLIM_BLOCKS_VIEWS && geom->a_mode != 0) return SLIM_ENOTSUP;
+  if (geom->dim == 3 && blocks->kind == SLIM_BLOCKS_VIEWS) return SLIM_ENOTSUP;
+  if (blocks->kind == SLIM_BLOCKS_STREAM && blocks->steps_per_view < 1) return SLIM_EINVAL;
+  if (blocks->ell < 1) return SLIM_EINVAL;
   if (r < 0 || !(lambda > 0.0) || !std::isfinite(lambda)) return SLIM_EINVAL;
   slim_ctx* c = new (std::nothrow) slim_ctx();
   if (!c) return SLIM_ENOMEM;
   c->N = geom->n_side;
   c->n_views = geom->n_views;
   c->D = geom->det_u;
-  c->n = (long long)c->N * c->N;
-  c->m = (long long)c->n_views * c->D;
+  c->Dv = geom->det_v;
+  c->dim = geom->dim;
+  c->kind = blocks->kind;
+  c->steps_per_view = blocks->kind == SLIM_BLOCKS_STREAM ? blocks->steps_per_view : 1;
+  c->n = c->dim == 3 ? (long long)c->N * c->N * c->N : (long long)c->N * c->N;
+  c->m = (long long)c->n_views * c->D * c->Dv;
   c->precision = geom->precision;
   c->a_mode = geom->a_mode;
   c->r = r;
@@ -373,12 +467,20 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       return SLIM_EINVAL;
     }
   }
-  if (c->m > 0x7fffffffLL || c->n > 0x7fffffffLL || (long long)c->p * c->p > (1LL << 33)) {
+  if (c->m > 0x7fffffffLL || c->n > 0x7fffffffLL || (long long)c->p * c->p > (1LL << 33) ||
+      c->ell > c->m) {
     delete c;
     return SLIM_EINVAL;
   }
   c->nb = c->solver == SLIM_SOLVE_FP64 ? 32 : 64;
   c->P = (c->p + c->nb - 1) / c->nb * c->nb;
+  const bool dense_solve = c->dim == 2;             // tiled Cholesky of the full p x p system
+  const bool use_map = c->kind == SLIM_BLOCKS_VIEWS;
+  if (c->dim == 3) {
+    c->P = c->p;      // G stored p x p; the solve runs slice by slice
+    c->S = c->N;
+    c->cap = 96;
+  }
   // geometry tables: host libm cos/sin, row-stepping iff |cos| >= |sin|
   c->h_views.resize(c->n_views);
   for (int a = 0; a < c->n_views; ++a) {
@@ -414,10 +516,12 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       {(void**)&c->d_ring_ids, (size_t)c->p * sizeof(int)},
       {(void**)&c->d_ring_pix, (size_t)c->p * c->taps * sizeof(int)},
       {(void**)&c->d_ring_w, (size_t)c->p * c->taps * sizeof(double)},
-      {(void**)&c->d_map_ray, 2 * (size_t)c->n * sizeof(int)},
-      {(void**)&c->d_map_w, 2 * (size_t)c->n * sizeof(double)},
+      {(void**)&c->d_map_ray, use_map ? 2 * (size_t)c->n * sizeof(int) : 0},
+      {(void**)&c->d_map_w, use_map ? 2 * (size_t)c->n * sizeof(double) : 0},
       {(void**)&c->d_G, (size_t)c->P * c->P * sizeof(double)},
-      {&c->d_L, (size_t)c->P * c->P * fs},
+      {&c->d_L, dense_solve ? (size_t)c->P * c->P * fs : 0},
+      {(void**)&c->d_slice_cnt, (size_t)c->S * sizeof(int)},
+      {(void**)&c->d_slice_rows, (size_t)c->S * c->cap * sizeof(int)},
       {(void**)&c->d_rhs, (size_t)c->P * sizeof(double)},
       {(void**)&c->d_z, (size_t)c->P * sizeof(double)},
       {(void**)&c->d_dz, (size_t)c->P * sizeof(double)},
@@ -425,7 +529,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       {(void**)&c->d_err, 2 * sizeof(double)},
   };
   for (auto& al : allocs)
-    if (st == SLIM_OK) chk(cudaMalloc(al.p, al.bytes), "cudaMalloc");
+    if (st == SLIM_OK && al.bytes > 0) chk(cudaMalloc(al.p, al.bytes), "cudaMalloc");
   if (st == SLIM_OK) {
     chk(cudaMemcpy(c->d_views, c->h_views.data(), c->h_views.size() * sizeof(ViewGeom),
                    cudaMemcpyHostToDevice), "views");
@@ -436,12 +540,15 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     chk(cudaMemset(c->d_ring_ids, 0xFF, (size_t)c->p * sizeof(int)), "memset");
     chk(cudaMemset(c->d_ring_pix, 0xFF, (size_t)c->p * c->taps * sizeof(int)), "memset");
     chk(cudaMemset(c->d_ring_w, 0, (size_t)c->p * c->taps * sizeof(double)), "memset");
-    chk(cudaMemset(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int)), "memset");
+    if (use_map) chk(cudaMemset(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int)), "memset");
     chk(cudaMemset(c->d_G, 0, (size_t)c->P * c->P * sizeof(double)), "memset");
-    chk(cudaMemset(c->d_L, 0, (size_t)c->P * c->P * fs), "memset");
+    if (dense_solve) chk(cudaMemset(c->d_L, 0, (size_t)c->P * c->P * fs), "memset");
     chk(cudaMemset(c->d_z, 0, (size_t)c->P * sizeof(double)), "memset");
-    chk(chol_plan_create(&c->plan, c->P, c->nb, c->solver == SLIM_SOLVE_MIXED ? 1 : 0, c->num_sms),
-        "chol plan");
+    if (dense_solve)
+      chk(chol_plan_create(&c->plan, c->P, c->nb, c->solver == SLIM_SOLVE_MIXED ? 1 : 0,
+                           c->num_sms), "chol plan");
+    else
+      chk(prepare_slice_solve(c->cap), "slice solve");
     if (st == SLIM_OK && c->a_mode != 0)
       chk(build_csr(c->d_views, c->N, c->D, c->m, c->n, c->a_mode == 2, &c->csr, c->stream),
           "stored matrix");
@@ -743,6 +850,15 @@ slim_status slim_project(slim_ctx* c, const int* ids, int count, const void* x, 
   if (!c || !x || !y) return fail(c, SLIM_EINVAL, "project: bad arguments");
   if (!ids) count = (int)c->m;
   if (count < 0) return fail(c, SLIM_EINVAL, "project: bad count");
+  if (c->dim == 3) {
+    if (c->precision == SLIM_PREC_FP32)
+      CK(launch_project_rays<float>(c->d_views, c->N, c->D, c->Dv, ids, count, (const float*)x,
+                                    (float*)y, c->stream), "project");
+    else
+      CK(launch_project_rays<double>(c->d_views, c->N, c->D, c->Dv, ids, count, (const double*)x,
+                                     (double*)y, c->stream), "project");
+    return SLIM_OK;
+  }
   if (c->a_mode) {
     if (c->precision == SLIM_PREC_FP32)
       CK(launch_csr_project<float>(c->csr, ids, count, (const float*)x, (float*)y, c->stream),
@@ -765,6 +881,7 @@ slim_status slim_backproject(slim_ctx* c, const int* ids, int count, const void*
   if (!c || !x || !y) return fail(c, SLIM_EINVAL, "backproject: bad arguments");
   if (!ids) count = (int)c->m;
   if (count < 0) return fail(c, SLIM_EINVAL, "backproject: bad count");
+  if (c->dim == 3) return fail(c, SLIM_ENOTSUP, "backproject: 2D only");
   if (c->a_mode) {
     if (c->precision == SLIM_PREC_FP32)
       CK(launch_csr_backproject<float>(c->csr, c->n, ids, count, (const float*)y, (float*)x,

@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(kCta) scatter_kernel(StepArgs<T> a) {
     int pix = rp[t];
     if (pix < 0) continue;
     if (c != T(0)) atomicAdd(&a.x[pix], c * (T)rw[t]);
-    if (is_new) {
+    if (is_new && a.map_ray) {
       a.map_ray[pix] = -1;
       a.map_ray[n + pix] = -1;
     }

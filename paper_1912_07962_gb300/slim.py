@@ -22,7 +22,7 @@ STATUS_NAMES = ["SLIM_OK", "SLIM_EINVAL", "SLIM_ENOMEM", "SLIM_ECUDA", "SLIM_ENO
 SLIM_F32, SLIM_F64 = 0, 1
 SLIM_PREC_FP64, SLIM_PREC_FP32 = 0, 1
 SLIM_SOLVE_FP64, SLIM_SOLVE_MIXED = 0, 1
-SLIM_BLOCKS_VIEWS = 0
+SLIM_BLOCKS_VIEWS, SLIM_BLOCKS_RAYS, SLIM_BLOCKS_STREAM = 0, 1, 2
 
 # every function the header declares (checked by the CPU test suite)
 EXPORTS = [
@@ -45,7 +45,7 @@ class slim_geometry(C.Structure):
 
 class slim_blocks(C.Structure):
     _fields_ = [("kind", C.c_int), ("ell", C.c_int), ("seed", C.c_ulonglong),
-                ("reserved", C.c_int)]
+                ("steps_per_view", C.c_int)]
 
 
 class slim_step_opts(C.Structure):
@@ -128,15 +128,16 @@ class Slim:
 
     def __init__(self, N, n_views, det, ell, r, lam, seed, precision=SLIM_PREC_FP64,
                  solver=SLIM_SOLVE_FP64, refine_iters=2, eta=1.0, ramp=False, use_graph=False,
-                 angles=None, a_mode=A_MATRIX_FREE):
+                 angles=None, a_mode=A_MATRIX_FREE, dim=2, det_v=1, kind=SLIM_BLOCKS_VIEWS,
+                 steps_per_view=1):
         lib = load()
         self._lib = lib
         self._angles = None
-        g = slim_geometry(2, N, n_views, det, 1, None, a_mode, precision)
+        g = slim_geometry(dim, N, n_views, det, det_v, None, a_mode, precision)
         if angles is not None:
             self._angles = np.ascontiguousarray(angles, dtype=np.float64)
             g.angles = self._angles.ctypes.data_as(C.POINTER(C.c_double))
-        blk = slim_blocks(SLIM_BLOCKS_VIEWS, ell, seed, 0)
+        blk = slim_blocks(kind, ell, seed, steps_per_view)
         opts = slim_step_opts(eta, int(ramp), solver, refine_iters, int(use_graph))
         h = C.c_void_p()
         st = lib.slim_create(C.byref(g), C.byref(blk), r, lam, C.byref(opts), C.byref(h))
@@ -144,7 +145,7 @@ class Slim:
             raise SlimError(st, "slim_create failed")
         self.h = h
         self.precision = precision
-        self.N, self.n, self.m = N, N * N, n_views * det
+        self.N, self.n, self.m = N, N ** dim, n_views * det * det_v
         n, m, p = C.c_longlong(), C.c_longlong(), C.c_int()
         lib.slim_get_sizes(h, C.byref(n), C.byref(m), C.byref(p))
         self.p = p.value
