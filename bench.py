@@ -324,6 +324,49 @@ def csr_block(sl, cfg, flush, stream, reps=20):
     return out
 
 
+def stream3d_block(sl, flush, stream, K, W, steps_per_view=46):
+    """The 3D streaming form at 256^3: float32 volume, random rays from the views
+    that have arrived, float64 per-slice solves, one CUDA graph per step."""
+    import torch
+    cfg = workloads.C4
+    x_true = workloads.phantom_3d(cfg.N, cfg.seed, cfg.n_ellipsoids, dtype=np.float32)
+    s = sl.Slim(cfg.N, cfg.n_views, cfg.det_u, cfg.ell, cfg.r, cfg.lam, cfg.seed,
+                precision=sl.SLIM_PREC_FP32, dim=3, det_v=cfg.det_v, kind=sl.SLIM_BLOCKS_STREAM,
+                steps_per_view=steps_per_view, use_graph=True)
+    xt = torch.tensor(x_true, device="cuda")
+    y = torch.zeros(cfg.m, dtype=torch.float32, device="cuda")
+    s.project(xt, y)
+    torch.cuda.synchronize()
+    e = torch.tensor(workloads.noise_direction(cfg.m, cfg.seed), dtype=torch.float32, device="cuda")
+    b = y + cfg.noise * torch.linalg.norm(y) * e / torch.linalg.norm(e)
+    del xt, e, y
+    s.set_data(b)
+    per, ph, _, _ = timed_steps(s, K, W, flush, stream)
+    s.close()
+    t = sum(per) * 1e-3
+    phases = {k: v / K for k, v in ph.items()}
+    names = {"sample": "sample", "forward_residual": "ray march + residual",
+             "gram_update": "slice lists + same-slice Gram pairs", "factor": "per-slice float64 solves",
+             "scatter": "scatter into the volume"}
+    dom = max(phases, key=phases.get)
+    # algorithmic bytes of the ray march and the scatter (2 taps per step, N steps per ray)
+    taps_new = cfg.ell * 2 * cfg.N
+    taps_all = (cfg.r + 1) * cfg.ell * 2 * cfg.N
+    alg = {"forward_residual": taps_new * (4 + 4 + 8),       # x gather + ring index + weight
+           "scatter": taps_all * (4 + 8 + 8)}                 # ring index + weight + x RMW
+    rl = None
+    if dom in alg:
+        gbs = alg[dom] / (phases[dom] * 1e-3) / 1e9
+        rl = {"phase": dom, "bound": "hbm", "achieved": gbs, "peak": 6797.2, "unit": "GB/s",
+              "frac": gbs / 6797.2, "algorithmic": f"{alg[dom]} bytes per step"}
+    return {"workload": f"{cfg.name}: {cfg.N}^3 volume, {cfg.n_views} views x {cfg.det_v}x{cfg.det_u} "
+                        f"detector (m={cfg.m}), ell={cfg.ell} random rays from arrived views "
+                        f"(one view every {steps_per_view} steps), r={cfg.r}, lambda={cfg.lam:g}",
+            "rows_per_s": cfg.ell * K / t, "ms_per_step": t / K * 1e3, "steps": K, "warmup": W,
+            "phases_ms": {names.get(k, k): v for k, v in phases.items()}, "dominant": names.get(dom, dom),
+            "roofline": rl}
+
+
 def e2e_block(sl, cfg, b, K, W):
     """Same metric through the C ABI with host buffers: each step copies b from
     pinned host memory, steps, and reads x back to pinned host memory."""
@@ -408,6 +451,7 @@ def main_gpu(args):
                         [0.5, 0.2, 0.1, 0.05, 0.02, 0.01])
     e2e = e2e_block(sl, cfg, b, args.steps, args.warmup) if rank == 0 and not args.no_e2e else None
     csr_pass = csr_block(sl, cfg, flush, stream) if rank == 0 and not args.no_csr else None
+    s3d = stream3d_block(sl, flush, stream, args.steps, args.warmup) if rank == 0 and not args.no_3d else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         leg = run_cpu_leg(args)
@@ -434,7 +478,8 @@ def main_gpu(args):
                   "roofline": rl_p},
         "speedup_vs_plain": rows_c / (rows_p * world),
         "phases_ms": {k: v / args.steps for k, v in ph_c.items()},
-        "roofline": rl, "csr_full_pass": csr_pass, "tta": tta, "e2e": e2e, "cpu_baseline": cpu,
+        "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "tta": tta, "e2e": e2e,
+        "cpu_baseline": cpu,
         "gpu_launches": kernels * args.steps, "kernels_per_step": kernels, "clocks": clocks,
     }
     print(json.dumps(line))
@@ -473,6 +518,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-csr", action="store_true")
+    ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-steps", type=int, default=0)
     ap.add_argument("--cpu-warmup", type=int, default=6)

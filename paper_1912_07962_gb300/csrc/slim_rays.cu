@@ -35,24 +35,28 @@ __device__ __forceinline__ bool overlap_window(const ViewGeom& gi, const RayDesc
   lo = 0;
   hi = N - 1;
   if (ri.view == rj.view) return fabs(ri.t - rj.t) <= 1.0;
-  const double det = gi.co * gj.si - gi.si * gj.co;   // sin(theta_j - theta_i)
-  if (fabs(det) < 1e-9) return true;
-  const double cc = 0.5 * (double)(N - 1);
-  const double px = (ri.t * gj.si - gi.si * rj.t) / det;
-  const double py = (gi.co * rj.t - ri.t * gj.co) / det;
-  const double sc = (gi.row_step ? py : px) + cc;
-  const double half = 3.0 / fabs(det) + 2.0;
-  const double l = floor(sc - half), h = ceil(sc + half);
-  if (h < 0.0 || l > (double)(N - 1)) return false;
-  lo = l < 0.0 ? 0 : (int)l;
-  hi = h > (double)(N - 1) ? N - 1 : (int)h;
+  // bounds only: float32 suffices given the margin of 2 steps
+  const float ci = (float)gi.co, si = (float)gi.si, cj = (float)gj.co, sj = (float)gj.si;
+  const float ti = (float)ri.t, tj = (float)rj.t;
+  const float det = ci * sj - si * cj;   // sin(theta_j - theta_i)
+  if (fabsf(det) < 1e-5f) return true;
+  const float rdet = 1.0f / det;
+  const float cc = 0.5f * (float)(N - 1);
+  const float sc = (gi.row_step ? (ci * tj - ti * cj) : (ti * sj - si * tj)) * rdet + cc;
+  const float half = 3.0f * fabsf(rdet) + 2.0f;
+  const float l = floorf(sc - half), h = ceilf(sc + half);
+  if (h < 0.0f || l > (float)(N - 1)) return false;
+  lo = l < 0.0f ? 0 : (int)l;
+  hi = h > (float)(N - 1) ? N - 1 : (int)h;
   return lo <= hi;
 }
 
 // sum_pixels a_i(pix) a_j(pix) for two rays in the same slice, read from the
 // stored taps: tap 2s / 2s+1 of a ray are its two taps at step s, so ray j's
-// taps at a pixel are at the step of ray j that covers the pixel.
-__device__ double pair_overlap(const RayArgs& a, int qi, int qj) {
+// taps at a pixel are at the step of ray j that covers the pixel.  The steps
+// of the window are split over `lanes` threads starting at `lane` (the caller
+// reduces the partial sums).
+__device__ double pair_overlap(const RayArgs& a, int qi, int qj, int lane = 0, int lanes = 1) {
   const int rayi = a.ring_ids[qi], rayj = a.ring_ids[qj];
   if (rayi < 0 || rayj < 0) return 0.0;
   const RayDesc ri = decode_ray(rayi, a.Du, a.Dv), rj = decode_ray(rayj, a.Du, a.Dv);
@@ -66,7 +70,7 @@ __device__ double pair_overlap(const RayArgs& a, int qi, int qj) {
   const double* wj = a.ring_w + (size_t)qj * a.taps;
   const long long plane = (long long)a.N * a.N;
   double acc = 0.0;
-  for (int s = lo; s <= hi; ++s) {
+  for (int s = lo + lane; s <= hi; s += lanes) {
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int pix = pi[2 * s + e];
@@ -154,120 +158,161 @@ __global__ void __launch_bounds__(kCta) forward_rays_kernel(RayArgs a, const T* 
   if (lane == 0) a.rhs[q] = (double)(acc - b[ray]);
 }
 
-// 2D: one thread per (new ray i, ring row q): G[new_i][q] = G[q][new_i].
-// The ray with the smaller ring index is the one marched, so both threads of
-// a pair inside the new block compute the same value.
-__global__ void gram_pairs_kernel(RayArgs a) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// 2D: one warp per (new ray i, ring row q): G[new_i][q] = G[q][new_i]; the
+// lanes split the overlap window (windows of near-parallel rays span the image).
+// The ray with the smaller ring index is the one marched, so both warps of a
+// pair inside the new block compute the same value.
+__global__ void __launch_bounds__(kCta) gram_pairs_kernel(RayArgs a) {
+  const long long idx = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (idx >= (long long)a.ell * a.p) return;
   const int i = (int)(idx / a.p), q = (int)(idx % a.p);
   const int qi = a.info->slot * a.ell + i;
-  const double v = pair_overlap(a, min(qi, q), max(qi, q));
-  a.G[(size_t)qi * a.P + q] = v;
-  a.G[(size_t)q * a.P + qi] = v;
-}
-
-// 3D: one warp per slice lists the ring rows whose ray lies in it (ring order).
-__global__ void slice_collect_kernel(RayArgs a) {
-  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (s >= a.S) return;
-  int cnt = 0;
-  for (int q0 = 0; q0 < a.p; q0 += 32) {
-    const int q = q0 + lane;
-    bool hit = false;
-    if (q < a.p) {
-      const int ray = a.ring_ids[q];
-      hit = ray >= 0 && decode_ray(ray, a.Du, a.Dv).slice == s;
-    }
-    const unsigned mask = __ballot_sync(0xffffffffu, hit);
-    const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
-    if (hit && pos < a.cap) a.slice_rows[(size_t)s * a.cap + pos] = q;
-    cnt += __popc(mask);
-  }
+  double v = pair_overlap(a, min(qi, q), max(qi, q), lane, 32);
+  v = warp_sum(v);
   if (lane == 0) {
-    a.slice_cnt[s] = cnt;
-    if (cnt > a.cap) set_status(a.status, SLIM_ENOTSUP);
+    a.G[(size_t)qi * a.P + q] = v;
+    a.G[(size_t)q * a.P + qi] = v;
   }
 }
 
-// 3D: per slice, G entries between the new block's rays and the slice's rays.
-__global__ void slice_gram_kernel(RayArgs a) {
+// 3D: bucket the ring rows by z-slice (one thread per row; the order inside
+// a bucket is fixed afterwards by slice_gram_kernel, which sorts it).
+__global__ void slice_fill_kernel(RayArgs a) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.p) return;
+  const int ray = a.ring_ids[q];
+  if (ray < 0) return;
+  const int s = decode_ray(ray, a.Du, a.Dv).slice;
+  const int pos = atomicAdd(&a.slice_cnt[s], 1);
+  if (pos < a.cap) a.slice_rows[(size_t)s * a.cap + pos] = q;
+}
+
+// 3D: per slice, G entries between the new block's rays and the slice's rays;
+// one warp per pair, lanes splitting the overlap window.  The slice's rows and
+// the positions of its new rows are staged in shared memory first, so warps
+// walk only the (new, member) pairs.
+constexpr int kSliceCapMax = 128;
+__global__ void __launch_bounds__(kCta) slice_gram_kernel(RayArgs a) {
+  __shared__ int srows[kSliceCapMax], snew[kSliceCapMax];
+  __shared__ int s_nnew;
+  __shared__ int sraw[kSliceCapMax];
   const int s = blockIdx.x;
-  const int n = min(a.slice_cnt[s], a.cap);
-  const int* rows = a.slice_rows + (size_t)s * a.cap;
+  const int cnt = a.slice_cnt[s];
+  const int n = min(cnt, a.cap);
   const int slot = a.info->slot;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int u = idx / n, v = idx % n;
-    const int qu = rows[u], qv = rows[v];
-    // pairs with row u new; a pair of two new rows only once (v >= u)
-    if (qu / a.ell != slot || (qv / a.ell == slot && v < u)) continue;
-    const double g = pair_overlap(a, min(qu, qv), max(qu, qv));
-    a.G[(size_t)qu * a.p + qv] = g;
-    a.G[(size_t)qv * a.p + qu] = g;
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0 && cnt > a.cap) set_status(a.status, SLIM_ENOTSUP);
+  for (int u = threadIdx.x; u < n; u += blockDim.x) sraw[u] = a.slice_rows[(size_t)s * a.cap + u];
+  __syncthreads();
+  // ring order inside the slice (ring rows are distinct): rank sort
+  for (int u = threadIdx.x; u < n; u += blockDim.x) {
+    const int key = sraw[u];
+    int rank = 0;
+    for (int v = 0; v < n; ++v) rank += sraw[v] < key;
+    srows[rank] = key;
+  }
+  __syncthreads();
+  for (int u = threadIdx.x; u < n; u += blockDim.x) a.slice_rows[(size_t)s * a.cap + u] = srows[u];
+  if (wib == 0) {
+    int cnt = 0;
+    for (int u0 = 0; u0 < n; u0 += 32) {
+      const int u = u0 + lane;
+      const bool isnew = u < n && srows[u] / a.ell == slot;
+      const unsigned mask = __ballot_sync(0xffffffffu, isnew);
+      if (isnew) snew[cnt + __popc(mask & ((1u << lane) - 1u))] = u;
+      cnt += __popc(mask);
+    }
+    if (lane == 0) s_nnew = cnt;
+  }
+  __syncthreads();
+  const int total = s_nnew * n;
+  for (int t = wib; t < total; t += kWarpsPerCta) {
+    const int u = snew[t / n], v = t % n;
+    const int qu = srows[u], qv = srows[v];
+    if (qv / a.ell == slot && v < u) continue;    // a pair of two new rows only once
+    double g = pair_overlap(a, min(qu, qv), max(qu, qv), lane, 32);
+    g = warp_sum(g);
+    if (lane == 0) {
+      a.G[(size_t)qu * a.p + qv] = g;
+      a.G[(size_t)qv * a.p + qu] = g;
+    }
   }
 }
 
-// 3D: per slice, K_s = lambda_k I + G_s from the stored Gram, float64
-// Cholesky in shared memory, then the solves with the right-hand side
-// restricted to the slice (residuals of the new block's rows, 0 elsewhere).
-__global__ void slice_solve_kernel(RayArgs a) {
+// 1/sqrt(d) in float64 from a float seed and two Newton steps (a handful of
+// float64 operations; the library square root and division are long
+// sequences on the float64 pipe).  d <= 0 is reported and replaced by 1.
+__device__ __forceinline__ double rsqrt_pivot(double d, int* status) {
+  if (!(d > 0.0)) {
+    set_status(status, SLIM_ENOTPD);
+    d = 1.0;
+  }
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double r = (double)rsqrtf((float)d);
+  const double h = 0.5 * d;
+  r = r * fma(-h * r, r, 1.5);
+  r = r * fma(-h * r, r, 1.5);
+  return r;
+}
+
+// 3D: one CTA of 4 warps per slice: K_s = lambda_k I + G_s from the stored
+// Gram, float64 Cholesky in shared memory (one pivot reciprocal per column,
+// rows of the trailing update split over 4 threads each), then L y = e and
+// L^T z = y with e the residuals of the slice's new rows.
+constexpr int kSolveThreads = 128;
+__global__ void __launch_bounds__(kSolveThreads) slice_solve_kernel(RayArgs a) {
   extern __shared__ double smem[];
-  const int s = blockIdx.x, tid = threadIdx.x;
+  const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
   const int n = min(a.slice_cnt[s], a.cap);
   if (n == 0) return;
   const int ld = a.cap + 1;
   double* K = smem;                 // cap x ld
   double* y = K + (size_t)a.cap * ld;
-  __shared__ double s_inv;
+  double* rdiag = y + a.cap;        // 1/L[c][c]
   const int* rows = a.slice_rows + (size_t)s * a.cap;
   const double lam = a.info->lam_k;
-  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+  for (int idx = tid; idx < n * n; idx += kSolveThreads) {
     const int u = idx / n, v = idx % n;
-    K[u * ld + v] = a.G[(size_t)rows[u] * a.p + rows[v]] + (u == v ? lam : 0.0);
+    if (v <= u) K[u * ld + v] = a.G[(size_t)rows[u] * a.p + rows[v]] + (u == v ? lam : 0.0);
   }
-  for (int u = tid; u < n; u += blockDim.x) y[u] = a.rhs[rows[u]];
+  for (int u = tid; u < n; u += kSolveThreads) y[u] = a.rhs[rows[u]];
   __syncthreads();
   for (int c = 0; c < n; ++c) {
     if (tid == 0) {
-      double d = K[c * ld + c];
-      if (!(d > 0.0)) {
-        set_status(a.status, SLIM_ENOTPD);
-        d = 1.0;
-      }
-      const double sd = sqrt(d);
-      K[c * ld + c] = sd;
-      s_inv = 1.0 / sd;
+      const double d = K[c * ld + c];
+      const double inv = rsqrt_pivot(d, a.status);
+      K[c * ld + c] = d > 0.0 ? d * inv : 1.0;   // sqrt(d) = d / sqrt(d)
+      rdiag[c] = inv;
     }
     __syncthreads();
-    const double inv = s_inv;
-    for (int i = c + 1 + tid; i < n; i += blockDim.x) K[i * ld + c] *= inv;
+    const double inv = rdiag[c];
+    for (int i = c + 1 + tid; i < n; i += kSolveThreads) K[i * ld + c] *= inv;
     __syncthreads();
-    const int w = n - c - 1;
-    for (int idx = tid; idx < w * w; idx += blockDim.x) {
-      const int i = c + 1 + idx / w, j = c + 1 + idx % w;
-      if (j <= i) K[i * ld + j] -= K[i * ld + c] * K[j * ld + c];
+    for (int i = c + 1 + (tid >> 2); i < n; i += kSolveThreads / 4) {
+      const double lic = K[i * ld + c];
+      for (int j = c + 1 + (tid & 3); j <= i; j += 4) K[i * ld + j] -= lic * K[j * ld + c];
     }
     __syncthreads();
   }
-  // L y = e, then L^T z = y, by one warp
   if (tid < 32) {
     for (int i = 0; i < n; ++i) {
       double t = 0.0;
-      for (int j = tid; j < i; j += 32) t += K[i * ld + j] * y[j];
+      for (int j = lane; j < i; j += 32) t += K[i * ld + j] * y[j];
       t = warp_sum(t);
-      if (tid == 0) y[i] = (y[i] - t) / K[i * ld + i];
+      if (lane == 0) y[i] = (y[i] - t) * rdiag[i];
       __syncwarp();
     }
     for (int i = n - 1; i >= 0; --i) {
       double t = 0.0;
-      for (int j = i + 1 + tid; j < n; j += 32) t += K[j * ld + i] * y[j];
+      for (int j = i + 1 + lane; j < n; j += 32) t += K[j * ld + i] * y[j];
       t = warp_sum(t);
-      if (tid == 0) y[i] = (y[i] - t) / K[i * ld + i];
+      if (lane == 0) y[i] = (y[i] - t) * rdiag[i];
       __syncwarp();
     }
   }
   __syncthreads();
-  for (int u = tid; u < n; u += blockDim.x) a.z[rows[u]] = y[u];
+  for (int u = tid; u < n; u += kSolveThreads) a.z[rows[u]] = y[u];
 }
 
 template <typename T>
@@ -310,19 +355,21 @@ cudaError_t launch_forward_rays(const RayArgs& a, T* x, const T* b, cudaStream_t
 
 cudaError_t launch_gram_pairs(const RayArgs& a, cudaStream_t s) {
   const long long total = (long long)a.ell * a.p;
-  gram_pairs_kernel<<<cdiv(total, 256), 256, 0, s>>>(a);
+  gram_pairs_kernel<<<cdiv(total, kWarpsPerCta), kCta, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_slice_collect(const RayArgs& a, cudaStream_t s) {
-  slice_collect_kernel<<<cdiv(a.S, kWarpsPerCta), kCta, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaMemsetAsync(a.slice_cnt, 0, (size_t)a.S * sizeof(int), s);
   if (e != cudaSuccess) return e;
-  slice_gram_kernel<<<a.S, 256, 0, s>>>(a);
+  slice_fill_kernel<<<cdiv(a.p, 256), 256, 0, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  slice_gram_kernel<<<a.S, kCta, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-size_t slice_solve_smem(int cap) { return ((size_t)cap * (cap + 1) + cap) * sizeof(double); }
+size_t slice_solve_smem(int cap) { return ((size_t)cap * (cap + 1) + 2 * (size_t)cap) * sizeof(double); }
 
 cudaError_t prepare_slice_solve(int cap) {
   return cudaFuncSetAttribute(slice_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -330,7 +377,7 @@ cudaError_t prepare_slice_solve(int cap) {
 }
 
 cudaError_t launch_slice_solve(const RayArgs& a, cudaStream_t s) {
-  slice_solve_kernel<<<a.S, 256, slice_solve_smem(a.cap), s>>>(a);
+  slice_solve_kernel<<<a.S, kSolveThreads, slice_solve_smem(a.cap), s>>>(a);
   return cudaGetLastError();
 }
 
