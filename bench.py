@@ -367,6 +367,60 @@ def stream3d_block(sl, flush, stream, K, W, steps_per_view=46):
             "roofline": rl}
 
 
+def batch_block(sl, flush, stream, K, W, count=96):
+    """Many uneven 2D problems (random-ray blocks) advancing together: one CUDA
+    graph per batch step with a parallel branch per problem, tile size and CTAs
+    per SM chosen by the autotuner per size class."""
+    import torch
+    cfgs = workloads.batch_mix(count)
+    t0 = time.perf_counter()
+    specs, choices = [], {}
+    for c in cfgs:
+        sp = dict(N=c.N, n_views=c.n_views, det=c.det, ell=c.ell, r=c.r, lam=c.lam, seed=c.seed,
+                  kind=sl.SLIM_BLOCKS_RAYS, precision=sl.SLIM_PREC_FP32, solver=sl.SLIM_SOLVE_MIXED)
+        tile, cps, _ = sl.autotune(sp, steps=3)
+        sp.update(tile=tile, ctas_per_sm=cps)
+        choices[f"{tile}x{cps}"] = choices.get(f"{tile}x{cps}", 0) + 1
+        specs.append(sp)
+    tune_s = time.perf_counter() - t0
+    bt = sl.SlimBatch(specs)
+    for c, pb in zip(cfgs, bt.problems):
+        xt = torch.tensor(workloads.phantom_2d(c.N, c.seed, c.n_ellipses), dtype=torch.float32,
+                          device="cuda")
+        y = torch.zeros(c.m, dtype=torch.float32, device="cuda")
+        pb.project(xt, y)
+        e = torch.tensor(workloads.noise_direction(c.m, c.seed), dtype=torch.float32, device="cuda")
+        pb.set_data(y + c.noise * torch.linalg.norm(y) * e / torch.linalg.norm(e))
+    torch.cuda.synchronize()
+    bt.set_stream(stream.cuda_stream)
+    for i in range(W):
+        flush.fill_(i)
+        bt.step(1)
+    bt.sync()
+    per = []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        for i in range(K):
+            flush.fill_(i)
+            ev[0].record(stream)
+            bt.step(1)
+            ev[1].record(stream)
+            ev[1].synchronize()
+            per.append(ev[0].elapsed_time(ev[1]))
+    bt.sync()
+    bt.close()
+    rows = sum(c.ell for c in cfgs)
+    t = sum(per) * 1e-3
+    flops = sum(chol_flops((c.r + 1) * c.ell) for c in cfgs)
+    return {"workload": f"{count} uneven 2D problems: N in {{128..512}}, views U{{90..360}}, "
+                        f"bins ceil(sqrt2 N), ell U{{128..512}} random rays, r U{{2..8}}, "
+                        f"lambda log-U[1e-4,1e-2]; float32 x, mixed solve",
+            "rows_per_s": rows * K / t, "ms_per_step": t / K * 1e3, "rows_per_step": rows,
+            "steps": K, "warmup": W, "factor_flops_per_step": flops,
+            "factor_tflops_if_all_time": flops / (t / K) / 1e12,
+            "autotune": {"choices_tile_x_ctas": choices, "seconds": tune_s}}
+
+
 def e2e_block(sl, cfg, b, K, W):
     """Same metric through the C ABI with host buffers: each step copies b from
     pinned host memory, steps, and reads x back to pinned host memory."""
@@ -452,6 +506,8 @@ def main_gpu(args):
     e2e = e2e_block(sl, cfg, b, args.steps, args.warmup) if rank == 0 and not args.no_e2e else None
     csr_pass = csr_block(sl, cfg, flush, stream) if rank == 0 and not args.no_csr else None
     s3d = stream3d_block(sl, flush, stream, args.steps, args.warmup) if rank == 0 and not args.no_3d else None
+    batch = (batch_block(sl, flush, stream, args.batch_steps, max(3, args.warmup))
+             if rank == 0 and args.batch_steps > 0 else None)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         leg = run_cpu_leg(args)
@@ -478,7 +534,7 @@ def main_gpu(args):
                   "roofline": rl_p},
         "speedup_vs_plain": rows_c / (rows_p * world),
         "phases_ms": {k: v / args.steps for k, v in ph_c.items()},
-        "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "tta": tta, "e2e": e2e,
+        "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "batched": batch, "tta": tta, "e2e": e2e,
         "cpu_baseline": cpu,
         "gpu_launches": kernels * args.steps, "kernels_per_step": kernels, "clocks": clocks,
     }
@@ -519,6 +575,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-csr", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=5,
+                    help="timed steps of the 96-problem batched block (0: skip it)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-steps", type=int, default=0)
     ap.add_argument("--cpu-warmup", type=int, default=6)

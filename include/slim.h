@@ -122,13 +122,19 @@ typedef struct {
  *                 residual (lambda_k I + G) z is computed in float64
  *   refine_iters  refinement rounds for SLIM_SOLVE_MIXED (0..16)
  *   use_graph     1: capture one step as a CUDA graph at the first slim_step and
- *                 replay it (one graph launch per step) */
+ *                 replay it (one graph launch per step)
+ *   tile          tile size of the tiled Cholesky: 32 or 64, 0 = default (64 for
+ *                 the float32 factor, 32 for float64)
+ *   ctas_per_sm   resident CTAs per SM of the persistent factorisation (1..4,
+ *                 0 = default 2) */
 typedef struct {
   double eta;
   int ramp;
   int solver;
   int refine_iters;
   int use_graph;
+  int tile;
+  int ctas_per_sm;
 } slim_step_opts;
 
 /* Create a context: validates the arguments and allocates all device state
@@ -230,6 +236,38 @@ slim_status slim_backproject(slim_ctx* ctx, const int* ray_ids, int count, const
  * Returns SLIM_ENOTPD on a non-positive pivot. */
 slim_status slim_damped_solve(const double* G, int p, double lambda, const double* rhs,
                               double* z, void* cuda_stream);
+
+/* Autotuner: time the factorisation tile size and CTAs per SM for a problem's
+ * size class (geometry, blocks, r, lambda as for slim_create; `base` gives the
+ * other step options) over `steps` steps each, and return the fastest options
+ * in *best (and its time per step in *best_ms).  A size class is the
+ * dimension, block kind, precisions and the Gram order p = (r+1) ell rounded
+ * up to a multiple of 512.  Results are cached per size class for the life of
+ * the process; with the environment variable
+ * SLIM_AUTOTUNE_CACHE naming a file, also across processes.  Allocates and
+ * frees temporary contexts.  For 3D problems (per-slice solves) *best = *base.
+ * Neither the tuner nor the batched form below has a counterpart in the
+ * paper: they schedule many problems of the kind Sec. 4 solves one at a time. */
+slim_status slim_autotune(const slim_geometry* geom, const slim_blocks* blocks, int r,
+                          double lambda, const slim_step_opts* base, int steps,
+                          slim_step_opts* best, double* best_ms);
+
+/* Batched form: many independent problems of uneven sizes advance together.
+ * slim_batch_create makes one context per problem (arrays of `count` entries;
+ * `steps` may be NULL for defaults).  slim_batch_step captures, at its first
+ * call, every problem's step as a parallel branch of one CUDA graph and then
+ * replays that graph: one graph launch advances every problem by one step.
+ * slim_batch_ctx returns problem i's context for set_data / get_x / ...
+ * (owned by the batch; do not destroy it). */
+typedef struct slim_batch slim_batch;
+slim_status slim_batch_create(int count, const slim_geometry* geoms, const slim_blocks* blocks,
+                              const int* r, const double* lambda, const slim_step_opts* steps,
+                              slim_batch** out);
+slim_status slim_batch_ctx(slim_batch* batch, int i, slim_ctx** ctx);
+slim_status slim_batch_step(slim_batch* batch, int nsteps);
+slim_status slim_batch_sync(slim_batch* batch);
+slim_status slim_batch_set_stream(slim_batch* batch, void* cuda_stream);
+void slim_batch_destroy(slim_batch* batch);
 
 /* Largest order p accepted by slim_damped_solve_noalloc. */
 #define SLIM_NOALLOC_MAX_P 1024

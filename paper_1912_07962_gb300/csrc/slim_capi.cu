@@ -1,5 +1,6 @@
 // C ABI of libslim.so: context management and the step driver.
 #include <cmath>
+#include <tuple>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -24,6 +25,7 @@ struct slim_ctx {
   int* d_slice_cnt = nullptr;
   int* d_slice_rows = nullptr;
   int ramp = 0, r = 0, nslots = 1, ell = 0, p = 0, P = 0, taps = 0, nb = 32;
+  int tile = 0, ctas_per_sm = 2;
   double lam = 0.0, eta = 1.0;
   unsigned long long seed = 0;
   std::vector<ViewGeom> h_views;
@@ -461,8 +463,11 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     c->solver = step->solver;
     c->refine_iters = step->refine_iters;
     c->use_graph = step->use_graph;
+    c->tile = step->tile;
+    c->ctas_per_sm = step->ctas_per_sm ? step->ctas_per_sm : 2;
     if (!(c->eta > 0.0) || (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED) ||
-        c->refine_iters < 0 || c->refine_iters > 16) {
+        c->refine_iters < 0 || c->refine_iters > 16 || (c->tile != 0 && c->tile != 32 && c->tile != 64) ||
+        c->ctas_per_sm < 1 || c->ctas_per_sm > 4) {
       delete c;
       return SLIM_EINVAL;
     }
@@ -472,7 +477,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     delete c;
     return SLIM_EINVAL;
   }
-  c->nb = c->solver == SLIM_SOLVE_FP64 ? 32 : 64;
+  c->nb = c->tile ? c->tile : (c->solver == SLIM_SOLVE_FP64 ? 32 : 64);
   c->P = (c->p + c->nb - 1) / c->nb * c->nb;
   const bool dense_solve = c->dim == 2;             // tiled Cholesky of the full p x p system
   const bool use_map = c->kind == SLIM_BLOCKS_VIEWS;
@@ -546,7 +551,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     chk(cudaMemset(c->d_z, 0, (size_t)c->P * sizeof(double)), "memset");
     if (dense_solve)
       chk(chol_plan_create(&c->plan, c->P, c->nb, c->solver == SLIM_SOLVE_MIXED ? 1 : 0,
-                           c->num_sms), "chol plan");
+                           c->num_sms, c->ctas_per_sm), "chol plan");
     else
       chk(prepare_slice_solve(c->cap), "slice solve");
     if (st == SLIM_OK && c->a_mode != 0)
@@ -958,5 +963,276 @@ extern "C" slim_status slim_damped_solve(const double* G, int p, double lambda, 
   cudaFree(out);
   cudaFree(status);
   chol_plan_destroy(&plan);
+  return st;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner and batched form
+// ---------------------------------------------------------------------------
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+
+namespace {
+
+// size class: dimension, block kind, precisions and the order p of the Gram
+// system rounded up to a multiple of 512 (the choice depends on p alone)
+struct TuneKey {
+  int dim, kind, precision, solver, pclass;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dim, kind, precision, solver, pclass) <
+           std::tie(o.dim, o.kind, o.precision, o.solver, o.pclass);
+  }
+  std::string str() const {
+    std::ostringstream os;
+    os << dim << ' ' << kind << ' ' << precision << ' ' << solver << ' ' << pclass;
+    return os.str();
+  }
+};
+struct TuneVal {
+  int tile, ctas;
+  double ms;
+};
+std::map<TuneKey, TuneVal> g_tune;
+std::mutex g_tune_mu;
+
+void load_tune_file() {
+  const char* path = std::getenv("SLIM_AUTOTUNE_CACHE");
+  if (!path) return;
+  std::ifstream f(path);
+  TuneKey k;
+  TuneVal v;
+  while (f >> k.dim >> k.kind >> k.precision >> k.solver >> k.pclass >> v.tile >> v.ctas >> v.ms)
+    g_tune[k] = v;
+}
+
+void save_tune_entry(const TuneKey& k, const TuneVal& v) {
+  const char* path = std::getenv("SLIM_AUTOTUNE_CACHE");
+  if (!path) return;
+  std::ofstream f(path, std::ios::app);
+  f << k.str() << ' ' << v.tile << ' ' << v.ctas << ' ' << v.ms << '\n';
+}
+
+}  // namespace
+
+extern "C" slim_status slim_autotune(const slim_geometry* geom, const slim_blocks* blocks, int r,
+                                     double lambda, const slim_step_opts* base, int steps,
+                                     slim_step_opts* best, double* best_ms) {
+  if (!geom || !blocks || !best || steps < 1) return SLIM_EINVAL;
+  slim_step_opts b0 = base ? *base : slim_step_opts{1.0, 0, SLIM_SOLVE_FP64, 2, 0, 0, 0};
+  *best = b0;
+  if (geom->dim == 3) {   // per-slice solves: nothing to tune here
+    if (best_ms) *best_ms = 0.0;
+    return SLIM_OK;
+  }
+  const int p = (r + 1) * blocks->ell;
+  TuneKey key{geom->dim, blocks->kind, geom->precision, b0.solver, (p + 511) / 512};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    static bool loaded = false;
+    if (!loaded) {
+      load_tune_file();
+      loaded = true;
+    }
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      best->tile = it->second.tile;
+      best->ctas_per_sm = it->second.ctas;
+      if (best_ms) *best_ms = it->second.ms;
+      return SLIM_OK;
+    }
+  }
+  const int tiles[2] = {32, 64};
+  const int ctas[3] = {1, 2, 3};
+  TuneVal bestv{0, 0, 1e30};
+  std::vector<double> b((size_t)geom->n_views * geom->det_u * geom->det_v, 0.0);
+  for (int t : tiles) {
+    for (int cps : ctas) {
+      slim_step_opts o = b0;
+      o.tile = t;
+      o.ctas_per_sm = cps;
+      o.use_graph = 1;
+      slim_ctx* c = nullptr;
+      if (slim_create(geom, blocks, r, lambda, &o, &c) != SLIM_OK) continue;
+      double ms = 1e30;
+      if (slim_set_data(c, b.data(), b.size(), SLIM_F64, 0) == SLIM_OK &&
+          slim_step(c, r + 1) == SLIM_OK && slim_sync(c) == SLIM_OK) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, c->stream);
+        slim_step(c, steps);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float f = 0.f;
+        cudaEventElapsedTime(&f, e0, e1);
+        if (slim_sync(c) == SLIM_OK) ms = f / steps;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+      }
+      slim_destroy(c);
+      if (ms < bestv.ms) bestv = TuneVal{t, cps, ms};
+    }
+  }
+  if (bestv.tile == 0) return SLIM_ECUDA;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = bestv;
+    save_tune_entry(key, bestv);
+  }
+  best->tile = bestv.tile;
+  best->ctas_per_sm = bestv.ctas;
+  if (best_ms) *best_ms = bestv.ms;
+  return SLIM_OK;
+}
+
+struct slim_batch {
+  std::vector<slim_ctx*> ctx;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+void batch_drop_graph(slim_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+}  // namespace
+
+extern "C" void slim_batch_destroy(slim_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  for (slim_ctx* c : b->ctx) slim_destroy(c);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+extern "C" slim_status slim_batch_create(int count, const slim_geometry* geoms,
+                                         const slim_blocks* blocks, const int* r,
+                                         const double* lambda, const slim_step_opts* steps,
+                                         slim_batch** out) {
+  if (!out || count < 1 || !geoms || !blocks || !r || !lambda) return SLIM_EINVAL;
+  *out = nullptr;
+  slim_batch* b = new (std::nothrow) slim_batch();
+  if (!b) return SLIM_ENOMEM;
+  for (int i = 0; i < count; ++i) {
+    slim_ctx* c = nullptr;
+    slim_status st = slim_create(&geoms[i], &blocks[i], r[i], lambda[i], steps ? &steps[i] : nullptr,
+                                 &c);
+    if (st != SLIM_OK) {
+      slim_batch_destroy(b);
+      return st;
+    }
+    c->use_graph = 0;   // the batch captures the steps itself
+    b->ctx.push_back(c);
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      slim_batch_destroy(b);
+      return SLIM_ECUDA;
+    }
+    b->join.push_back(e);
+  }
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    slim_batch_destroy(b);
+    return SLIM_ECUDA;
+  }
+  b->own_stream = true;
+  *out = b;
+  return SLIM_OK;
+}
+
+extern "C" slim_status slim_batch_ctx(slim_batch* b, int i, slim_ctx** ctx) {
+  if (!b || !ctx || i < 0 || i >= (int)b->ctx.size()) return SLIM_EINVAL;
+  *ctx = b->ctx[i];
+  return SLIM_OK;
+}
+
+extern "C" slim_status slim_batch_set_stream(slim_batch* b, void* stream) {
+  if (!b) return SLIM_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return SLIM_ECUDA;
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  b->own_stream = false;
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return SLIM_ECUDA;
+    b->own_stream = true;
+  }
+  batch_drop_graph(b);
+  return SLIM_OK;
+}
+
+extern "C" slim_status slim_batch_step(slim_batch* b, int nsteps) {
+  if (!b || nsteps < 0) return SLIM_EINVAL;
+  for (slim_ctx* c : b->ctx)
+    if (!c->has_data) return SLIM_ESTATE;
+  if (!b->exec) {
+    // fork every problem's stream off the batch stream, capture one step on
+    // each, join them back: one graph with a parallel branch per problem
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return SLIM_ECUDA;
+    cudaError_t e = cudaEventRecord(b->fork, b->stream);
+    for (size_t i = 0; i < b->ctx.size() && e == cudaSuccess; ++i) {
+      slim_ctx* c = b->ctx[i];
+      e = cudaStreamWaitEvent(c->stream, b->fork, 0);
+      if (e == cudaSuccess) {
+        c->capturing = true;
+        e = enqueue_step(c);
+        c->capturing = false;
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(b->join[i], c->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return SLIM_ECUDA;
+    }
+    b->graph = g;
+    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+      batch_drop_graph(b);
+      return SLIM_ECUDA;
+    }
+  }
+  // order the graph after work already queued on each problem's own stream
+  // (set_data, set_x, ...), and later work there after the graph
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    if (cudaEventRecord(b->join[i], b->ctx[i]->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(b->stream, b->join[i], 0) != cudaSuccess)
+      return SLIM_ECUDA;
+  }
+  for (int i = 0; i < nsteps; ++i)
+    if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return SLIM_ECUDA;
+  if (cudaEventRecord(b->fork, b->stream) != cudaSuccess) return SLIM_ECUDA;
+  for (slim_ctx* c : b->ctx) {
+    if (cudaStreamWaitEvent(c->stream, b->fork, 0) != cudaSuccess) return SLIM_ECUDA;
+    c->h_k += nsteps;
+  }
+  return SLIM_OK;
+}
+
+extern "C" slim_status slim_batch_sync(slim_batch* b) {
+  if (!b) return SLIM_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return SLIM_ECUDA;
+  slim_status st = SLIM_OK;
+  for (slim_ctx* c : b->ctx) {
+    slim_status s2 = read_status(c);
+    if (st == SLIM_OK) st = s2;
+  }
   return st;
 }

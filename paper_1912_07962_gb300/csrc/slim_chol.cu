@@ -576,7 +576,8 @@ std::vector<CholTask> build_chol_tasks(int T) {
   return t;
 }
 
-cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_sms) {
+cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_sms,
+                             int ctas_per_sm) {
   *plan = CholPlan{};
   if (P % nb) return cudaErrorInvalidValue;
   plan->P = P;
@@ -596,7 +597,7 @@ cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_
   if ((e = cudaMemset(plan->d_sync, 0, nsync * sizeof(int))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&plan->d_winv, (size_t)plan->T * nb * nb * es)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&plan->d_y, 2 * (size_t)P * es)) != cudaSuccess) return e;
-  plan->grid = 2 * num_sms;
+  plan->grid = ctas_per_sm * num_sms;
   // opt in to the shared memory the factor kernel needs
   if (is_f32) {
     if (nb == 64)

@@ -39,7 +39,8 @@ struct CholPlan {
 };
 
 // Allocate / free the plan for order P (multiple of nb).
-cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_sms);
+cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_sms,
+                             int ctas_per_sm = 2);
 void chol_plan_destroy(CholPlan* plan);
 
 // Factor L (P x P row-major, lower triangle holds K on entry, L on exit) in

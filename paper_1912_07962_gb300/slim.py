@@ -31,6 +31,8 @@ EXPORTS = [
     "slim_get_iter", "slim_set_iter", "slim_checkpoint", "slim_restore", "slim_get_memory",
     "slim_get_sizes", "slim_project", "slim_backproject", "slim_damped_solve",
     "slim_set_timing", "slim_get_timing", "slim_damped_solve_noalloc", "slim_get_csr",
+    "slim_autotune", "slim_batch_create", "slim_batch_ctx", "slim_batch_step", "slim_batch_sync",
+    "slim_batch_set_stream", "slim_batch_destroy",
 ]
 A_MATRIX_FREE, A_CSR_F32, A_CSR_BF16 = 0, 1, 2
 NOALLOC_MAX_P = 1024
@@ -50,7 +52,8 @@ class slim_blocks(C.Structure):
 
 class slim_step_opts(C.Structure):
     _fields_ = [("eta", C.c_double), ("ramp", C.c_int), ("solver", C.c_int),
-                ("refine_iters", C.c_int), ("use_graph", C.c_int)]
+                ("refine_iters", C.c_int), ("use_graph", C.c_int), ("tile", C.c_int),
+                ("ctas_per_sm", C.c_int)]
 
 
 class SlimError(RuntimeError):
@@ -97,6 +100,15 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "slim_get_timing": ([VP, P(D), I, P(I)], I),
         "slim_damped_solve_noalloc": ([VP, I, D, VP, VP, VP], I),
         "slim_get_csr": ([VP, P(LL), VP, VP, VP], I),
+        "slim_autotune": ([P(slim_geometry), P(slim_blocks), I, D, P(slim_step_opts), I,
+                           P(slim_step_opts), P(D)], I),
+        "slim_batch_create": ([I, P(slim_geometry), P(slim_blocks), P(I), P(D),
+                               P(slim_step_opts), P(VP)], I),
+        "slim_batch_ctx": ([VP, I, P(VP)], I),
+        "slim_batch_step": ([VP, I], I),
+        "slim_batch_sync": ([VP], I),
+        "slim_batch_set_stream": ([VP, VP], I),
+        "slim_batch_destroy": ([VP], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -129,16 +141,25 @@ class Slim:
     def __init__(self, N, n_views, det, ell, r, lam, seed, precision=SLIM_PREC_FP64,
                  solver=SLIM_SOLVE_FP64, refine_iters=2, eta=1.0, ramp=False, use_graph=False,
                  angles=None, a_mode=A_MATRIX_FREE, dim=2, det_v=1, kind=SLIM_BLOCKS_VIEWS,
-                 steps_per_view=1):
+                 steps_per_view=1, tile=0, ctas_per_sm=0, _handle=None):
         lib = load()
         self._lib = lib
         self._angles = None
+        self._owned = _handle is None
+        self.precision = precision
+        self.N, self.n, self.m = N, N ** dim, n_views * det * det_v
+        if _handle is not None:      # a context owned by a batch
+            self.h = _handle
+            n_, m_, p_ = C.c_longlong(), C.c_longlong(), C.c_int()
+            lib.slim_get_sizes(self.h, C.byref(n_), C.byref(m_), C.byref(p_))
+            self.p = p_.value
+            return
         g = slim_geometry(dim, N, n_views, det, det_v, None, a_mode, precision)
         if angles is not None:
             self._angles = np.ascontiguousarray(angles, dtype=np.float64)
             g.angles = self._angles.ctypes.data_as(C.POINTER(C.c_double))
         blk = slim_blocks(kind, ell, seed, steps_per_view)
-        opts = slim_step_opts(eta, int(ramp), solver, refine_iters, int(use_graph))
+        opts = slim_step_opts(eta, int(ramp), solver, refine_iters, int(use_graph), tile, ctas_per_sm)
         h = C.c_void_p()
         st = lib.slim_create(C.byref(g), C.byref(blk), r, lam, C.byref(opts), C.byref(h))
         if st != SLIM_OK:
@@ -155,9 +176,9 @@ class Slim:
             raise SlimError(st, self._lib.slim_last_error(self.h).decode())
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self, "_owned", True):
             self._lib.slim_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -288,3 +309,85 @@ def damped_solve_noalloc(G, lam, rhs, z, stream_ptr=0):
                                        C.c_void_p(stream_ptr))
     if st != SLIM_OK:
         raise SlimError(st, "slim_damped_solve_noalloc failed")
+
+
+def problem_structs(specs):
+    """ctypes arrays (geometry, blocks, r, lambda, step options) for a list of
+    dicts with keys N, n_views, det, ell, r, lam, seed and optional precision,
+    solver, kind, use_graph, tile, ctas_per_sm, refine_iters."""
+    n = len(specs)
+    G = (slim_geometry * n)()
+    B = (slim_blocks * n)()
+    R = (C.c_int * n)()
+    L = (C.c_double * n)()
+    S = (slim_step_opts * n)()
+    for i, sp in enumerate(specs):
+        G[i] = slim_geometry(2, sp["N"], sp["n_views"], sp["det"], 1, None, 0, sp.get("precision", 0))
+        B[i] = slim_blocks(sp.get("kind", SLIM_BLOCKS_RAYS), sp["ell"], sp["seed"], 1)
+        R[i] = sp["r"]
+        L[i] = sp["lam"]
+        S[i] = slim_step_opts(1.0, 0, sp.get("solver", 0), sp.get("refine_iters", 2), 0,
+                              sp.get("tile", 0), sp.get("ctas_per_sm", 0))
+    return G, B, R, L, S
+
+
+def autotune(spec, steps=3):
+    """Best (tile, ctas_per_sm) for a problem spec (dict as in problem_structs)."""
+    lib = load()
+    G, B, R, L, S = problem_structs([spec])
+    best = slim_step_opts()
+    ms = C.c_double()
+    st = lib.slim_autotune(C.byref(G[0]), C.byref(B[0]), R[0], L[0], C.byref(S[0]), steps,
+                           C.byref(best), C.byref(ms))
+    if st != SLIM_OK:
+        raise SlimError(st, "slim_autotune failed")
+    return best.tile, best.ctas_per_sm, ms.value
+
+
+class SlimBatch:
+    """Many independent problems advancing together (one CUDA graph launch per step)."""
+
+    def __init__(self, specs):
+        lib = load()
+        self._lib = lib
+        G, B, R, L, S = problem_structs(specs)
+        self._keep = (G, B, R, L, S)
+        h = C.c_void_p()
+        st = lib.slim_batch_create(len(specs), G, B, R, L, S, C.byref(h))
+        if st != SLIM_OK:
+            raise SlimError(st, "slim_batch_create failed")
+        self.h = h
+        self.problems = []
+        for i, sp in enumerate(specs):
+            ch = C.c_void_p()
+            lib.slim_batch_ctx(h, i, C.byref(ch))
+            self.problems.append(Slim(sp["N"], sp["n_views"], sp["det"], sp["ell"], sp["r"], sp["lam"],
+                                      sp["seed"], precision=sp.get("precision", 0), _handle=ch))
+
+    def step(self, nsteps=1):
+        st = self._lib.slim_batch_step(self.h, nsteps)
+        if st != SLIM_OK:
+            raise SlimError(st, "slim_batch_step failed")
+
+    def sync(self):
+        st = self._lib.slim_batch_sync(self.h)
+        if st != SLIM_OK:
+            raise SlimError(st, "slim_batch_sync failed")
+
+    def set_stream(self, stream_ptr):
+        st = self._lib.slim_batch_set_stream(self.h, C.c_void_p(stream_ptr))
+        if st != SLIM_OK:
+            raise SlimError(st, "slim_batch_set_stream failed")
+
+    def close(self):
+        if getattr(self, "h", None):
+            for pb in self.problems:
+                pb.h = None
+            self._lib.slim_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
