@@ -143,11 +143,11 @@ def make_b(sl, cfg, x_true, e):
     return workloads.add_noise(clean, e, cfg.noise)
 
 
-def make_form(sl, cfg, form, seed):
+def make_form(sl, cfg, form, seed, lookahead=0, ctas_per_sm=0):
     if form == "chosen":
         return sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.ell, cfg.r, cfg.lam, seed,
                        precision=sl.SLIM_PREC_FP32, solver=sl.SLIM_SOLVE_MIXED, refine_iters=2,
-                       use_graph=True)
+                       use_graph=True, lookahead=lookahead, ctas_per_sm=ctas_per_sm)
     return sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.ell, cfg.r, cfg.lam, seed,
                    precision=sl.SLIM_PREC_FP64, solver=sl.SLIM_SOLVE_FP64, use_graph=False)
 
@@ -186,6 +186,40 @@ def timed_steps(s, K, W, flush, stream, snapshot_every=0, snap_dtype=None, accum
             xs = xbuf.double().clone() if xs is None else xs + xbuf.double()
     s.set_timing(False)
     return per, phases, snaps, xs
+
+
+def timed_region(s, K, W, flush, stream, snapshot_every=0, snap_dtype=None):
+    """Pipelined form: W untimed steps, then K steps timed as one region on the
+    caller's stream (events recorded after every step, no synchronisation, the
+    L2 flush between steps inside the region).  The factorisation launches and
+    iterate chains of the region are timed by the library's launch log.
+    Returns (ms per step list, launch log, snapshots)."""
+    import torch
+    s.set_stream(stream.cuda_stream)
+    s.set_timing(True)
+    for i in range(W):
+        flush.fill_(i)
+        s.step(1)
+    s.sync()
+    s.launch_log()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    snaps = []
+    evs[0].record(stream)
+    for i in range(K):
+        flush.fill_(i + W)
+        s.step(1)
+        evs[i + 1].record(stream)
+        if snapshot_every and (i + 1) % snapshot_every == 0:
+            xb = torch.empty(s.n, dtype=snap_dtype or torch.float32, device="cuda")
+            s.get_x(xb)
+            snaps.append((i + 1, xb))
+    evs[-1].synchronize()
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(K)]
+    f_ms, x_ms, n = s.launch_log()
+    s.set_timing(False)
+    cum = np.cumsum(per)
+    snaps = [(k, float(cum[k - 1]), x.double()) for k, x in snaps]
+    return per, {"factor_launch_ms": f_ms, "iterate_chain_ms": x_ms, "chains": n}, snaps
 
 
 def chol_flops(p):
@@ -245,7 +279,7 @@ def traffic_from_profiles(kernel):
     return rec["bytes"] if h.hexdigest() == rec["sha256"] else None
 
 
-def tta_block(sl, cfg, b, flush, stream, epochs, thresholds):
+def tta_block(sl, cfg, b, flush, stream, epochs, thresholds, lookahead=0):
     """Time to relative error thresholds vs the reference iterate."""
     import torch
     M = cfg.n_views
@@ -255,11 +289,14 @@ def tta_block(sl, cfg, b, flush, stream, epochs, thresholds):
     res = {}
     x_ref = None
     for form in ("plain", "chosen"):
-        s = make_form(sl, cfg, form, cfg.seed)
+        s = make_form(sl, cfg, form, cfg.seed, lookahead=lookahead if form == "chosen" else 0)
         s.set_data(b if form == "plain" else b.astype(np.float32))
-        per, _, snaps, xs = timed_steps(s, steps, 0, flush, stream, snapshot_every=every,
-                                        snap_dtype=torch.float64 if form == "plain" else torch.float32,
-                                        accum_last=M if form == "plain" else 0)
+        if form == "chosen" and lookahead:
+            per, _, snaps = timed_region(s, steps, 0, flush, stream, snapshot_every=every)
+        else:
+            per, _, snaps, xs = timed_steps(s, steps, 0, flush, stream, snapshot_every=every,
+                                            snap_dtype=torch.float64 if form == "plain" else torch.float32,
+                                            accum_last=M if form == "plain" else 0)
         if form == "plain":
             x_ref = xs / M
         res[form] = (per, snaps)
@@ -421,11 +458,11 @@ def batch_block(sl, flush, stream, K, W, count=96):
             "autotune": {"choices_tile_x_ctas": choices, "seconds": tune_s}}
 
 
-def e2e_block(sl, cfg, b, K, W):
+def e2e_block(sl, cfg, b, K, W, lookahead=0):
     """Same metric through the C ABI with host buffers: each step copies b from
     pinned host memory, steps, and reads x back to pinned host memory."""
     import torch
-    s = make_form(sl, cfg, "chosen", cfg.seed)
+    s = make_form(sl, cfg, "chosen", cfg.seed, lookahead=lookahead)
     bh = torch.tensor(b.astype(np.float32)).pin_memory()
     xh = torch.empty(cfg.n, dtype=torch.float32).pin_memory()
     s.set_data(bh)
@@ -474,17 +511,26 @@ def main_gpu(args):
     sp.close()
 
     # chosen form: the headline timed region
-    sc = make_form(sl, cfg, "chosen", seed)
+    sc = make_form(sl, cfg, "chosen", seed, lookahead=args.lookahead,
+                   ctas_per_sm=args.factor_ctas_per_sm)
     sc.set_data(b.astype(np.float32))
     clk = ClockSampler(local)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clk.start()
-    per_c, ph_c, _, _ = timed_steps(sc, args.steps, args.warmup, flush, stream)
+    launch_log = None
+    if args.lookahead:
+        per_c, launch_log, _ = timed_region(sc, args.steps, args.warmup, flush, stream)
+    else:
+        per_c, ph_c, _, _ = timed_steps(sc, args.steps, args.warmup, flush, stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
     kernels = sc.kernels_per_step()
+    if args.lookahead:
+        # phase breakdown from a short synchronous pass (one step at a time)
+        _, ph_c, _, _ = timed_steps(sc, 5, 0, flush, stream)
+        ph_c = {k: v * args.steps / 5 for k, v in ph_c.items()}
     sc.close()
     t_c = sum(per_c) * 1e-3
     t_p = sum(per_p) * 1e-3
@@ -495,15 +541,33 @@ def main_gpu(args):
     rows_c = cfg.ell * args.steps * world / t_c
     rows_p = cfg.ell * args.plain_steps / t_p
 
-    rl = roofline_of(ph_c, args.steps, cfg.p, cfg.ell, cfg.N, "chosen", clocks.get("sm_mhz"))
+    if launch_log:
+        # pipelined: the factorisation is the kernel with the most device time
+        # per step; its launches are timed live over the timed region
+        f_s = launch_log["factor_launch_ms"] * 1e-3
+        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+        ach = chol_flops(cfg.p) / f_s / 1e12
+        rl = {"kernel": "chol_factor_kernel", "phase": "factor", "bound": "alu", "achieved": ach,
+              "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+              "algorithmic": f"p^3/3 = {chol_flops(cfg.p):.4g} flop per launch (p = {cfg.p})",
+              "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
+              "launch_ms": launch_log["factor_launch_ms"],
+              "iterate_chain_ms": launch_log["iterate_chain_ms"],
+              "launches_timed": launch_log["chains"],
+              "note": (f"factorisations run up to {args.lookahead} steps ahead of the iterate "
+                       "chain, overlapping one another and it; launch_ms is the mean duration "
+                       "of one factorisation launch inside the timed region")}
+    else:
+        rl = roofline_of(ph_c, args.steps, cfg.p, cfg.ell, cfg.N, "chosen", clocks.get("sm_mhz"))
     rl["traffic"] = traffic_from_profiles(rl["kernel"])
     rl_p = roofline_of(ph_p, args.plain_steps, cfg.p, cfg.ell, cfg.N, "plain", None)
 
     tta = None
     if args.tta_epochs > 0 and rank == 0:
         tta = tta_block(sl, cfg, b, flush, stream, args.tta_epochs,
-                        [0.5, 0.2, 0.1, 0.05, 0.02, 0.01])
-    e2e = e2e_block(sl, cfg, b, args.steps, args.warmup) if rank == 0 and not args.no_e2e else None
+                        [0.5, 0.2, 0.1, 0.05, 0.02, 0.01], lookahead=args.lookahead)
+    e2e = (e2e_block(sl, cfg, b, args.steps, args.warmup, lookahead=args.lookahead)
+           if rank == 0 and not args.no_e2e else None)
     csr_pass = csr_block(sl, cfg, flush, stream) if rank == 0 and not args.no_csr else None
     s3d = stream3d_block(sl, flush, stream, args.steps, args.warmup) if rank == 0 and not args.no_3d else None
     batch = (batch_block(sl, flush, stream, args.batch_steps, max(3, args.warmup))
@@ -525,7 +589,13 @@ def main_gpu(args):
         "data": "synthetic",
         "config": {"workload": desc, "form": "chosen: float32 projector/residual/scatter, "
                    "float64 Gram, float32 tiled Cholesky + 2 float64-residual refinements, "
-                   "one CUDA graph per step",
+                   + (f"geometry and factorisation pipelined {args.lookahead} steps ahead of "
+                      "the iterate chain (CUDA graphs on three kinds of stream)"
+                      if args.lookahead else "one CUDA graph per step"),
+                   "lookahead": args.lookahead,
+                   "timing": ("one region of K back-to-back steps (pipelined steady state; "
+                              "the flush writes are inside the region)" if args.lookahead else
+                              "each step bracketed by events and synchronised"),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "plain": {"rows_per_s": rows_p, "ms_per_step": t_p / args.plain_steps * 1e3,
@@ -534,6 +604,9 @@ def main_gpu(args):
                   "roofline": rl_p},
         "speedup_vs_plain": rows_c / (rows_p * world),
         "phases_ms": {k: v / args.steps for k, v in ph_c.items()},
+        "phases_note": ("one step at a time (synchronous pass); the pipelined region overlaps "
+                        "the geometry phases with the iterate chain" if args.lookahead else
+                        "per step, inside the timed region"),
         "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "batched": batch, "tta": tta, "e2e": e2e,
         "cpu_baseline": cpu,
         "gpu_launches": kernels * args.steps, "kernels_per_step": kernels, "clocks": clocks,
@@ -575,6 +648,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-csr", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--factor-ctas-per-sm", type=int, default=0,
+                    help="persistent factorisation CTAs per SM (0: library default)")
+    ap.add_argument("--lookahead", type=int, default=3,
+                    help="steps the geometry chain runs ahead in the chosen form (0: one chain)")
     ap.add_argument("--batch-steps", type=int, default=5,
                     help="timed steps of the 96-problem batched block (0: skip it)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -126,7 +126,18 @@ typedef struct {
  *   tile          tile size of the tiled Cholesky: 32 or 64, 0 = default (64 for
  *                 the float32 factor, 32 for float64)
  *   ctas_per_sm   resident CTAs per SM of the persistent factorisation (1..4,
- *                 0 = default 2) */
+ *                 0 = default: 2, or 1 with lookahead, where the D factorisations
+ *                 in flight share these CTAs, num_SMs * ctas_per_sm / D each)
+ *   lookahead     0: each step runs as one chain.  D = 1..3 (view blocks, 2D,
+ *                 rows from the projector): the matrix lambda_k I + M_k M_k^T of
+ *                 Eq. (B_k) depends only on the blocks drawn, so the chain that
+ *                 draws tau_j, adds its Gram rows and factors K_j runs up to D
+ *                 steps ahead of the chain that updates x, on streams of its
+ *                 own.  The iterates are the same; slim_step returns with the
+ *                 update of x enqueued on the context's stream and the
+ *                 geometry of up to D later steps in flight on internal
+ *                 streams (slim_sync waits for those too).  Uses graphs
+ *                 whatever use_graph says. */
 typedef struct {
   double eta;
   int ramp;
@@ -135,6 +146,7 @@ typedef struct {
   int use_graph;
   int tile;
   int ctas_per_sm;
+  int lookahead;
 } slim_step_opts;
 
 /* Create a context: validates the arguments and allocates all device state
@@ -236,6 +248,14 @@ slim_status slim_backproject(slim_ctx* ctx, const int* ray_ids, int count, const
  * Returns SLIM_ENOTPD on a non-positive pivot. */
 slim_status slim_damped_solve(const double* G, int p, double lambda, const double* rhs,
                               double* z, void* cuda_stream);
+
+/* Launch log of the pipelined form (lookahead > 0, timing on): every
+ * factorisation launch and every iterate chain is bracketed by events without
+ * any synchronisation, so a pipelined run can be timed as it runs.  Returns
+ * their mean durations in ms since the previous call (at most the last 512 of
+ * each) and the number of iterate chains.  Synchronises the context. */
+slim_status slim_get_launch_log(slim_ctx* ctx, double* factor_ms, double* iterate_ms,
+                                long long* count);
 
 /* Autotuner: time the factorisation tile size and CTAs per SM for a problem's
  * size class (geometry, blocks, r, lambda as for slim_create; `base` gives the

@@ -16,7 +16,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libslim.so")
-SOURCES = ["slim_capi.cu", "slim_kernels.cu", "slim_chol.cu", "slim_noalloc.cu", "slim_rays.cu"]
+SOURCES = [
+    "slim_capi.cu", "slim_kernels.cu", "slim_chol.cu", "slim_noalloc.cu", "slim_rays.cu",
+    "slim_lookahead.cu",
+]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -9,9 +9,12 @@
 #include "../../include/slim.h"
 #include "slim_chol.cuh"
 #include "slim_kernels.cuh"
+#include "slim_lookahead.cuh"
 #include "slim_rays.cuh"
 
 using namespace slim;
+
+constexpr int kMaxBuf = 4;   // lookahead D <= 3: D+1 factor buffers
 
 struct slim_ctx {
   // configuration
@@ -60,6 +63,22 @@ struct slim_ctx {
   bool timing = false;
   bool capturing = false;
   cudaEvent_t ev[8] = {};
+  // pipelined form (lookahead D > 0): geometry chain D steps ahead
+  int lookahead = 0, eslots = 0, Pe = 0, nbuf = 1;
+  long long h_g = 0;                 // geometry steps enqueued
+  long long* d_gdone = nullptr;      // geometry steps prepared (device)
+  StepInfo* d_info_buf = nullptr;    // [nbuf]
+  int* d_ext = nullptr;              // [nbuf * P] ring index -> extended row
+  void* d_Lb[kMaxBuf] = {};
+  CholPlan planb[kMaxBuf];
+  cudaStream_t xs = nullptr, gs = nullptr, fs[kMaxBuf] = {};
+  cudaGraphExec_t g1_exec[kMaxBuf] = {}, g2_exec[kMaxBuf] = {}, gx_exec[kMaxBuf] = {};
+  cudaEvent_t ev_user = nullptr, ev_g1 = nullptr, ev_g2[kMaxBuf] = {}, ev_x[kMaxBuf] = {};
+  cudaEvent_t la_ev[10] = {};
+  // launch log (timing on): event pairs around factor and iterate launches
+  static constexpr int kLog = 512;
+  std::vector<cudaEvent_t> log_f, log_x;   // 2*kLog each
+  long long log_nf = 0, log_nx = 0, log_f0 = 0, log_x0 = 0;
   std::string err;
 };
 
@@ -242,6 +261,13 @@ cudaError_t mark(slim_ctx* c, int i) {
 // 2 per refinement round, scatter).
 int kernels_per_step(const slim_ctx* c) {
   if (c->dim == 3) return 6;   // sample, march, collect, slice Gram, slice solve, scatter
+  if (c->lookahead) {
+    // geometry: sample, taps, Gram, map clear, ring map, K, factor; iterate:
+    // residual, 2 per solve, 2 per refinement round, scatter
+    int solves = c->solver == SLIM_SOLVE_MIXED ? 1 + c->refine_iters : 1;
+    int refine = c->solver == SLIM_SOLVE_MIXED ? 2 * c->refine_iters : 0;
+    return 7 + 1 + 2 * solves + refine + 1;
+  }
   int solves = c->solver == SLIM_SOLVE_MIXED ? 1 + c->refine_iters : 1;
   int refine = c->solver == SLIM_SOLVE_MIXED ? 2 * c->refine_iters : 0;
   return 5 + 2 * solves + refine + 1;
@@ -404,6 +430,28 @@ void free_all(slim_ctx* c) {
   for (cudaEvent_t e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  // pipelined form
+  for (cudaEvent_t e : c->log_f) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->log_x) cudaEventDestroy(e);
+  for (int b = 0; b < kMaxBuf; ++b) {
+    if (c->g1_exec[b]) cudaGraphExecDestroy(c->g1_exec[b]);
+    if (c->g2_exec[b]) cudaGraphExecDestroy(c->g2_exec[b]);
+    if (c->gx_exec[b]) cudaGraphExecDestroy(c->gx_exec[b]);
+    if (c->d_Lb[b]) cudaFree(c->d_Lb[b]);
+    chol_plan_destroy(&c->planb[b]);
+    if (c->ev_g2[b]) cudaEventDestroy(c->ev_g2[b]);
+    if (c->ev_x[b]) cudaEventDestroy(c->ev_x[b]);
+    if (c->fs[b]) cudaStreamDestroy(c->fs[b]);
+  }
+  for (cudaEvent_t e : c->la_ev)
+    if (e) cudaEventDestroy(e);
+  if (c->ev_user) cudaEventDestroy(c->ev_user);
+  if (c->ev_g1) cudaEventDestroy(c->ev_g1);
+  if (c->xs) cudaStreamDestroy(c->xs);
+  if (c->gs) cudaStreamDestroy(c->gs);
+  if (c->d_gdone) cudaFree(c->d_gdone);
+  if (c->d_info_buf) cudaFree(c->d_info_buf);
+  if (c->d_ext) cudaFree(c->d_ext);
 }
 
 void drop_graph(slim_ctx* c) {
@@ -411,6 +459,244 @@ void drop_graph(slim_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   c->graph_exec = nullptr;
   c->graph = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined form: three kinds of graph, replayed on internal streams
+//   geometry (one graph, stream gs): draw tau_j, march its taps, Gram rows,
+//     clear the pixel map;
+//   factor (graph b, stream fs[b]): ring map and K_j into buffer b = j mod (D+1),
+//     tiled factorisation;
+//   iterate (graph b, high-priority stream xs): residual, solve with buffer b,
+//     refinement, scatter.
+// Events order them: geometry j waits for the iterate chain j-D-1 (the last
+// reader of its tap slot, Gram rows and buffer); factor j waits for geometry
+// j; iterate k waits for the caller's stream and for factor k.
+// ---------------------------------------------------------------------------
+template <typename T>
+LaArgs<T> make_la_args(slim_ctx* c) {
+  LaArgs<T> a;
+  a.views = c->d_views;
+  a.N = c->N;
+  a.D = c->D;
+  a.n_views = c->n_views;
+  a.n = c->n;
+  a.m = c->m;
+  a.ell = c->ell;
+  a.r = c->r;
+  a.nslots = c->nslots;
+  a.eslots = c->eslots;
+  a.p = c->p;
+  a.P = c->P;
+  a.Pe = c->Pe;
+  a.taps = c->taps;
+  a.seed = c->seed;
+  a.lam = c->lam;
+  a.eta = c->eta;
+  a.ramp = c->ramp;
+  a.gdone = c->d_gdone;
+  a.info_buf = c->d_info_buf;
+  a.nbuf = c->nbuf;
+  a.ring_ids = c->d_ring_ids;
+  a.ring_pix = c->d_ring_pix;
+  a.ring_w = c->d_ring_w;
+  a.map_ray = c->d_map_ray;
+  a.map_w = c->d_map_w;
+  a.G = c->d_G;
+  a.rhs = c->d_rhs;
+  a.z = c->d_z;
+  a.x = (T*)c->d_x;
+  a.b = (const T*)c->d_b;
+  a.status = c->d_status;
+  return a;
+}
+
+cudaError_t la_mark(slim_ctx* c, int i, cudaStream_t s) {
+  if (!c->timing) return cudaSuccess;
+  return cudaEventRecordWithFlags(c->la_ev[i], s, cudaEventRecordExternal);
+}
+
+template <typename T>
+cudaError_t la_enqueue_geometry(slim_ctx* c, int b, cudaStream_t s) {
+  LaArgs<T> a = make_la_args<T>(c);
+  int* ext = c->d_ext + (size_t)b * c->P;
+  const StepInfo* info = c->d_info_buf + b;
+  cudaError_t e;
+  if ((e = la_mark(c, 0, s)) != cudaSuccess) return e;
+  if ((e = la_launch_sample<T>(a, s)) != cudaSuccess) return e;
+  if ((e = la_launch_taps<T>(a, s)) != cudaSuccess) return e;
+  if ((e = la_mark(c, 1, s)) != cudaSuccess) return e;
+  if ((e = la_launch_gram<T>(a, s)) != cudaSuccess) return e;
+  if ((e = la_launch_map_clear<T>(a, s)) != cudaSuccess) return e;
+  if ((e = la_mark(c, 2, s)) != cudaSuccess) return e;
+  if ((e = la_launch_ext_map(info, c->ell, c->nslots, c->eslots, c->p, c->P, ext, s)) !=
+      cudaSuccess)
+    return e;
+  if (c->solver == SLIM_SOLVE_MIXED)
+    e = la_launch_form<float>(info, ext, c->d_G, c->Pe, (float*)c->d_Lb[b], c->P, s);
+  else
+    e = la_launch_form<double>(info, ext, c->d_G, c->Pe, (double*)c->d_Lb[b], c->P, s);
+  if (e != cudaSuccess) return e;
+  return la_mark(c, 3, s);
+}
+
+cudaError_t la_enqueue_factor(slim_ctx* c, int b, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = la_mark(c, 4, s)) != cudaSuccess) return e;
+  if ((e = chol_factor(c->planb[b], c->d_Lb[b], c->d_status, s)) != cudaSuccess) return e;
+  return la_mark(c, 5, s);
+}
+
+template <typename T>
+cudaError_t la_enqueue_iterate(slim_ctx* c, int b, cudaStream_t s) {
+  LaArgs<T> a = make_la_args<T>(c);
+  const int* ext = c->d_ext + (size_t)b * c->P;
+  const StepInfo* info = c->d_info_buf + b;
+  cudaError_t e;
+  if ((e = la_mark(c, 6, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(c->d_rhs, 0, (size_t)c->P * sizeof(double), s)) != cudaSuccess) return e;
+  if ((e = la_launch_residual<T>(a, info, s)) != cudaSuccess) return e;
+  if ((e = la_mark(c, 7, s)) != cudaSuccess) return e;
+  if ((e = chol_solve(c->planb[b], c->d_Lb[b], c->d_rhs, c->d_z, c->d_status, s)) != cudaSuccess)
+    return e;
+  if (c->solver == SLIM_SOLVE_MIXED) {
+    for (int it = 0; it < c->refine_iters; ++it) {
+      if ((e = la_launch_refine(info, ext, c->d_G, c->Pe, c->d_z, c->d_rhs, c->d_res, c->P, s)) !=
+          cudaSuccess)
+        return e;
+      if ((e = chol_solve(c->planb[b], c->d_Lb[b], c->d_res, c->d_dz, c->d_status, s)) !=
+          cudaSuccess)
+        return e;
+      if ((e = launch_axpy(c->d_z, c->d_dz, c->P, s)) != cudaSuccess) return e;
+    }
+  }
+  if ((e = la_mark(c, 8, s)) != cudaSuccess) return e;
+  if ((e = la_launch_scatter<T>(a, ext, s)) != cudaSuccess) return e;
+  return la_mark(c, 9, s);
+}
+
+// Capture `body` on stream s into an instantiated graph.
+template <typename F>
+cudaError_t la_capture(cudaStream_t s, cudaGraphExec_t* exec, F body) {
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t eb = body();
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(s, &g);
+  if (eb != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return eb != cudaSuccess ? eb : e;
+  }
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+void la_drop_graphs(slim_ctx* c) {
+  for (int b = 0; b < kMaxBuf; ++b) {
+    if (c->g1_exec[b]) cudaGraphExecDestroy(c->g1_exec[b]);
+    c->g1_exec[b] = nullptr;
+    if (c->g2_exec[b]) cudaGraphExecDestroy(c->g2_exec[b]);
+    if (c->gx_exec[b]) cudaGraphExecDestroy(c->gx_exec[b]);
+    c->g2_exec[b] = nullptr;
+    c->gx_exec[b] = nullptr;
+  }
+}
+
+cudaError_t la_build_graphs(slim_ctx* c) {
+  const bool f32 = c->precision == SLIM_PREC_FP32;
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < c->nbuf && e == cudaSuccess; ++b) {
+    e = la_capture(c->gs, &c->g1_exec[b], [&] {
+      return f32 ? la_enqueue_geometry<float>(c, b, c->gs) : la_enqueue_geometry<double>(c, b, c->gs);
+    });
+    if (e == cudaSuccess)
+      e = la_capture(c->fs[b], &c->g2_exec[b], [&] { return la_enqueue_factor(c, b, c->fs[b]); });
+    if (e == cudaSuccess)
+      e = la_capture(c->xs, &c->gx_exec[b], [&] {
+        return f32 ? la_enqueue_iterate<float>(c, b, c->xs) : la_enqueue_iterate<double>(c, b, c->xs);
+      });
+  }
+  return e;
+}
+
+cudaError_t la_sync_all(slim_ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->gs);
+  for (int b = 0; b < c->nbuf && e == cudaSuccess; ++b) e = cudaStreamSynchronize(c->fs[b]);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->xs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e;
+}
+
+// Enqueue steps h_k+1 .. h_k+nsteps.
+cudaError_t la_step(slim_ctx* c, int nsteps) {
+  cudaError_t e = cudaSuccess;
+  if (!c->g1_exec[0] && (e = la_build_graphs(c)) != cudaSuccess) return e;
+  const bool log = c->timing && !c->log_f.empty();
+  for (int t = 0; t < nsteps; ++t) {
+    const long long k = c->h_k + 1;
+    while (c->h_g < k + c->lookahead) {
+      const long long j = ++c->h_g;
+      const int b = (int)(j % c->nbuf);
+      if ((e = cudaStreamWaitEvent(c->gs, c->ev_x[b], 0)) != cudaSuccess) return e;
+      if ((e = cudaGraphLaunch(c->g1_exec[b], c->gs)) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(c->ev_g1, c->gs)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(c->fs[b], c->ev_g1, 0)) != cudaSuccess) return e;
+      const int li = (int)(c->log_nf % slim_ctx::kLog);
+      if (log && (e = cudaEventRecord(c->log_f[2 * li], c->fs[b])) != cudaSuccess) return e;
+      if ((e = cudaGraphLaunch(c->g2_exec[b], c->fs[b])) != cudaSuccess) return e;
+      if (log) {
+        if ((e = cudaEventRecord(c->log_f[2 * li + 1], c->fs[b])) != cudaSuccess) return e;
+        ++c->log_nf;
+      }
+      if ((e = cudaEventRecord(c->ev_g2[b], c->fs[b])) != cudaSuccess) return e;
+    }
+    const int b = (int)(k % c->nbuf);
+    if ((e = cudaEventRecord(c->ev_user, c->stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c->xs, c->ev_user, 0)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c->xs, c->ev_g2[b], 0)) != cudaSuccess) return e;
+    const int lx = (int)(c->log_nx % slim_ctx::kLog);
+    if (log && (e = cudaEventRecord(c->log_x[2 * lx], c->xs)) != cudaSuccess) return e;
+    if ((e = cudaGraphLaunch(c->gx_exec[b], c->xs)) != cudaSuccess) return e;
+    if (log) {
+      if ((e = cudaEventRecord(c->log_x[2 * lx + 1], c->xs)) != cudaSuccess) return e;
+      ++c->log_nx;
+    }
+    if ((e = cudaEventRecord(c->ev_x[b], c->xs)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c->stream, c->ev_x[b], 0)) != cudaSuccess) return e;
+    c->h_k = k;
+  }
+  return e;
+}
+
+// Rebuild the tap ring and the Gram rows of the window of step k (x unchanged).
+cudaError_t la_rebuild(slim_ctx* c, long long k) {
+  cudaError_t e = la_sync_all(c);
+  if (e != cudaSuccess) return e;
+  if (!c->g1_exec[0] && (e = la_build_graphs(c)) != cudaSuccess) return e;
+  for (long long j = std::max<long long>(1, k - c->r); j <= k; ++j) {
+    long long done = j - 1;
+    if ((e = cudaMemcpy(c->d_gdone, &done, sizeof(done), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return e;
+    if ((e = cudaGraphLaunch(c->g1_exec[j % c->nbuf], c->gs)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(c->gs)) != cudaSuccess) return e;
+  }
+  long long done = k;
+  if ((e = cudaMemcpy(c->d_gdone, &done, sizeof(done), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
+  c->h_g = k;
+  c->h_k = k;
+  return cudaSuccess;
+}
+
+// Ring index q of step k -> extended row (host copy of the device map).
+int la_ext_host(const slim_ctx* c, long long k, int q) {
+  if (q >= c->p) return -1;
+  const int s = q / c->ell;
+  const long long blk = k - (((k - 1 - s) % c->nslots) + c->nslots) % c->nslots;
+  if (blk < 1) return -1;
+  return (int)((blk - 1) % c->eslots) * c->ell + q % c->ell;
 }
 
 }  // namespace
@@ -464,16 +750,28 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     c->refine_iters = step->refine_iters;
     c->use_graph = step->use_graph;
     c->tile = step->tile;
-    c->ctas_per_sm = step->ctas_per_sm ? step->ctas_per_sm : 2;
+    c->lookahead = step->lookahead;
+    c->ctas_per_sm = step->ctas_per_sm ? step->ctas_per_sm : (c->lookahead ? 1 : 2);
     if (!(c->eta > 0.0) || (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED) ||
         c->refine_iters < 0 || c->refine_iters > 16 || (c->tile != 0 && c->tile != 32 && c->tile != 64) ||
-        c->ctas_per_sm < 1 || c->ctas_per_sm > 4) {
+        c->ctas_per_sm < 1 || c->ctas_per_sm > 4 || c->lookahead < 0 ||
+        c->lookahead > kMaxBuf - 1) {
       delete c;
       return SLIM_EINVAL;
     }
+    if (c->lookahead && (c->kind != SLIM_BLOCKS_VIEWS || c->dim != 2 || c->a_mode != 0)) {
+      delete c;
+      return SLIM_ENOTSUP;
+    }
   }
+  if (c->lookahead) {
+    c->eslots = c->nslots + c->lookahead;
+    c->Pe = c->eslots * c->ell;
+    c->nbuf = c->lookahead + 1;
+  }
+  const bool la = c->lookahead > 0;
   if (c->m > 0x7fffffffLL || c->n > 0x7fffffffLL || (long long)c->p * c->p > (1LL << 33) ||
-      c->ell > c->m) {
+      (long long)c->Pe * c->Pe > (1LL << 33) || c->ell > c->m) {
     delete c;
     return SLIM_EINVAL;
   }
@@ -509,6 +807,22 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
   chk(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
   if (st == SLIM_OK && chk(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream"))
     c->own_stream = true;
+  if (la && st == SLIM_OK) {
+    // the iterate chain outranks the geometry chains running ahead of it
+    int least = 0, greatest = 0;
+    chk(cudaDeviceGetStreamPriorityRange(&least, &greatest), "priorities");
+    chk(cudaStreamCreateWithPriority(&c->xs, cudaStreamNonBlocking, greatest), "stream");
+    chk(cudaStreamCreateWithPriority(&c->gs, cudaStreamNonBlocking, least), "stream");
+    for (int b = 0; b < c->nbuf; ++b) {
+      chk(cudaStreamCreateWithPriority(&c->fs[b], cudaStreamNonBlocking, least), "stream");
+      chk(cudaEventCreateWithFlags(&c->ev_g2[b], cudaEventDisableTiming), "event");
+      chk(cudaEventCreateWithFlags(&c->ev_x[b], cudaEventDisableTiming), "event");
+    }
+    chk(cudaEventCreateWithFlags(&c->ev_user, cudaEventDisableTiming), "event");
+    chk(cudaEventCreateWithFlags(&c->ev_g1, cudaEventDisableTiming), "event");
+  }
+  const int ring_rows = la ? c->Pe : c->p;
+  const size_t g_elems = la ? (size_t)c->Pe * c->Pe : (size_t)c->P * c->P;
   const size_t es = elem(c->precision);
   const size_t fs = c->solver == SLIM_SOLVE_FP64 ? sizeof(double) : sizeof(float);
   struct { void** p; size_t bytes; } allocs[] = {
@@ -518,13 +832,20 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       {(void**)&c->d_status, sizeof(int)},
       {&c->d_x, (size_t)c->n * es},
       {&c->d_b, (size_t)c->m * es},
-      {(void**)&c->d_ring_ids, (size_t)c->p * sizeof(int)},
-      {(void**)&c->d_ring_pix, (size_t)c->p * c->taps * sizeof(int)},
-      {(void**)&c->d_ring_w, (size_t)c->p * c->taps * sizeof(double)},
+      {(void**)&c->d_ring_ids, (size_t)ring_rows * sizeof(int)},
+      {(void**)&c->d_ring_pix, (size_t)ring_rows * c->taps * sizeof(int)},
+      {(void**)&c->d_ring_w, (size_t)ring_rows * c->taps * sizeof(double)},
       {(void**)&c->d_map_ray, use_map ? 2 * (size_t)c->n * sizeof(int) : 0},
       {(void**)&c->d_map_w, use_map ? 2 * (size_t)c->n * sizeof(double) : 0},
-      {(void**)&c->d_G, (size_t)c->P * c->P * sizeof(double)},
-      {&c->d_L, dense_solve ? (size_t)c->P * c->P * fs : 0},
+      {(void**)&c->d_G, g_elems * sizeof(double)},
+      {&c->d_L, dense_solve && !la ? (size_t)c->P * c->P * fs : 0},
+      {&c->d_Lb[0], la ? (size_t)c->P * c->P * fs : 0},
+      {&c->d_Lb[1], la ? (size_t)c->P * c->P * fs : 0},
+      {&c->d_Lb[2], la && c->nbuf > 2 ? (size_t)c->P * c->P * fs : 0},
+      {&c->d_Lb[3], la && c->nbuf > 3 ? (size_t)c->P * c->P * fs : 0},
+      {(void**)&c->d_gdone, la ? sizeof(long long) : 0},
+      {(void**)&c->d_info_buf, la ? c->nbuf * sizeof(StepInfo) : 0},
+      {(void**)&c->d_ext, la ? (size_t)c->nbuf * c->P * sizeof(int) : 0},
       {(void**)&c->d_slice_cnt, (size_t)c->S * sizeof(int)},
       {(void**)&c->d_slice_rows, (size_t)c->S * c->cap * sizeof(int)},
       {(void**)&c->d_rhs, (size_t)c->P * sizeof(double)},
@@ -542,14 +863,25 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     chk(cudaMemset(c->d_status, 0, sizeof(int)), "memset");
     chk(cudaMemset(c->d_x, 0, (size_t)c->n * es), "memset");
     chk(cudaMemset(c->d_b, 0, (size_t)c->m * es), "memset");
-    chk(cudaMemset(c->d_ring_ids, 0xFF, (size_t)c->p * sizeof(int)), "memset");
-    chk(cudaMemset(c->d_ring_pix, 0xFF, (size_t)c->p * c->taps * sizeof(int)), "memset");
-    chk(cudaMemset(c->d_ring_w, 0, (size_t)c->p * c->taps * sizeof(double)), "memset");
+    chk(cudaMemset(c->d_ring_ids, 0xFF, (size_t)ring_rows * sizeof(int)), "memset");
+    chk(cudaMemset(c->d_ring_pix, 0xFF, (size_t)ring_rows * c->taps * sizeof(int)), "memset");
+    chk(cudaMemset(c->d_ring_w, 0, (size_t)ring_rows * c->taps * sizeof(double)), "memset");
     if (use_map) chk(cudaMemset(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int)), "memset");
-    chk(cudaMemset(c->d_G, 0, (size_t)c->P * c->P * sizeof(double)), "memset");
-    if (dense_solve) chk(cudaMemset(c->d_L, 0, (size_t)c->P * c->P * fs), "memset");
+    chk(cudaMemset(c->d_G, 0, g_elems * sizeof(double)), "memset");
+    if (dense_solve && !la) chk(cudaMemset(c->d_L, 0, (size_t)c->P * c->P * fs), "memset");
     chk(cudaMemset(c->d_z, 0, (size_t)c->P * sizeof(double)), "memset");
-    if (dense_solve)
+    if (la) {
+      chk(cudaMemset(c->d_gdone, 0, sizeof(long long)), "memset");
+      chk(cudaMemset(c->d_info_buf, 0, c->nbuf * sizeof(StepInfo)), "memset");
+      // up to D factorisations run at once next to the iterate chain: together
+      // they take ctas_per_sm CTAs per SM, leaving room for the iterate kernels
+      const int fgrid = std::max(16, c->num_sms * c->ctas_per_sm / c->lookahead);
+      for (int b = 0; b < c->nbuf; ++b) {
+        chk(cudaMemset(c->d_Lb[b], 0, (size_t)c->P * c->P * fs), "memset");
+        chk(chol_plan_create(&c->planb[b], c->P, c->nb, c->solver == SLIM_SOLVE_MIXED ? 1 : 0,
+                             fgrid, 1), "chol plan");
+      }
+    } else if (dense_solve)
       chk(chol_plan_create(&c->plan, c->P, c->nb, c->solver == SLIM_SOLVE_MIXED ? 1 : 0,
                            c->num_sms, c->ctas_per_sm), "chol plan");
     else
@@ -573,6 +905,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
 
 void slim_destroy(slim_ctx* c) {
   if (!c) return;
+  if (c->lookahead && c->xs) la_sync_all(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_all(c);
   delete c;
@@ -602,9 +935,20 @@ slim_status slim_set_timing(slim_ctx* c, int on) {
   if (!c) return SLIM_EINVAL;
   if (on && !c->ev[0])
     for (cudaEvent_t& e : c->ev) CK(cudaEventCreate(&e), "event");
+  if (on && c->lookahead && !c->la_ev[0]) {
+    for (cudaEvent_t& e : c->la_ev) CK(cudaEventCreate(&e), "event");
+    c->log_f.assign(2 * slim_ctx::kLog, nullptr);
+    c->log_x.assign(2 * slim_ctx::kLog, nullptr);
+    for (cudaEvent_t& e : c->log_f) CK(cudaEventCreate(&e), "event");
+    for (cudaEvent_t& e : c->log_x) CK(cudaEventCreate(&e), "event");
+  }
   if ((on != 0) != c->timing) {
     CK(cudaStreamSynchronize(c->stream), "sync");
     drop_graph(c);   // the captured step changes with the event records
+    if (c->lookahead) {
+      CK(la_sync_all(c), "sync");
+      la_drop_graphs(c);
+    }
   }
   c->timing = on != 0;
   return SLIM_OK;
@@ -615,12 +959,51 @@ slim_status slim_get_timing(slim_ctx* c, double* phase_ms, int nphase, int* kern
   if (kernels) *kernels = kernels_per_step(c);
   if (!phase_ms) return SLIM_OK;
   if (!c->timing || nphase < 1 || nphase > 7) return fail(c, SLIM_ESTATE, "timing is off");
+  if (c->lookahead) {
+    // sample+taps, residual, Gram, K, factor, solve, scatter: each from its own
+    // pair of events (the geometry phases are those of the latest prepared step)
+    CK(la_sync_all(c), "sync");
+    const int pairs[7][2] = {{0, 1}, {6, 7}, {1, 2}, {2, 3}, {4, 5}, {7, 8}, {8, 9}};
+    for (int i = 0; i < nphase; ++i) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, c->la_ev[pairs[i][0]], c->la_ev[pairs[i][1]]), "elapsed");
+      phase_ms[i] = ms;
+    }
+    return SLIM_OK;
+  }
   CK(cudaStreamSynchronize(c->stream), "sync");
   for (int i = 0; i < nphase; ++i) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]), "elapsed");
     phase_ms[i] = ms;
   }
+  return SLIM_OK;
+}
+
+slim_status slim_get_launch_log(slim_ctx* c, double* factor_ms, double* iterate_ms,
+                                long long* count) {
+  if (!c) return SLIM_EINVAL;
+  if (!c->lookahead || !c->timing || c->log_f.empty())
+    return fail(c, SLIM_ESTATE, "launch log: pipelined form with timing on only");
+  CK(la_sync_all(c), "sync");
+  auto mean = [&](std::vector<cudaEvent_t>& ev, long long n0, long long n1, double* out) {
+    const long long first = std::max(n0, n1 - slim_ctx::kLog);
+    double sum = 0.0;
+    for (long long i = first; i < n1; ++i) {
+      const int li = (int)(i % slim_ctx::kLog);
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[2 * li], ev[2 * li + 1]) != cudaSuccess) return false;
+      sum += ms;
+    }
+    if (out) *out = n1 > first ? sum / (double)(n1 - first) : 0.0;
+    return true;
+  };
+  if (!mean(c->log_f, c->log_f0, c->log_nf, factor_ms) ||
+      !mean(c->log_x, c->log_x0, c->log_nx, iterate_ms))
+    return cuda_fail(c, cudaGetLastError(), "launch log");
+  if (count) *count = c->log_nx - c->log_x0;
+  c->log_f0 = c->log_nf;
+  c->log_x0 = c->log_nx;
   return SLIM_OK;
 }
 
@@ -654,6 +1037,10 @@ slim_status slim_get_x(slim_ctx* c, void* x, size_t n, int dtype, int on_device)
 slim_status slim_step(slim_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return fail(c, SLIM_EINVAL, "step: bad arguments");
   if (!c->has_data) return fail(c, SLIM_ESTATE, "step before slim_set_data");
+  if (c->lookahead) {
+    CK(la_step(c, nsteps), "pipelined step");
+    return SLIM_OK;
+  }
   if (c->use_graph) {
     if (!c->graph_exec) {
       CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
@@ -680,6 +1067,7 @@ slim_status slim_step(slim_ctx* c, int nsteps) {
 
 slim_status slim_sync(slim_ctx* c) {
   if (!c) return SLIM_EINVAL;
+  if (c->lookahead) CK(la_sync_all(c), "sync");
   CK(cudaStreamSynchronize(c->stream), "sync");
   return read_status(c);
 }
@@ -754,7 +1142,8 @@ slim_status slim_get_iter(const slim_ctx* c, long long* k) {
 
 slim_status slim_set_iter(slim_ctx* c, long long k) {
   if (!c || k < 0) return fail(c, SLIM_EINVAL, "set_iter: bad arguments");
-  cudaError_t e = c->precision == SLIM_PREC_FP32 ? rebuild_t<float>(c, k) : rebuild_t<double>(c, k);
+  cudaError_t e = c->lookahead ? la_rebuild(c, k)
+                 : c->precision == SLIM_PREC_FP32 ? rebuild_t<float>(c, k) : rebuild_t<double>(c, k);
   if (e != cudaSuccess) return cuda_fail(c, e, "set_iter");
   c->h_k = k;
   return read_status(c);
@@ -806,6 +1195,33 @@ slim_status slim_restore(slim_ctx* c, const void* buf, size_t len) {
 slim_status slim_get_memory(slim_ctx* c, int* ids, double* G, double* z) {
   if (!c) return SLIM_EINVAL;
   CK(cudaStreamSynchronize(c->stream), "get_memory");
+  if (c->lookahead) {
+    // gather the window of step h_k from the extended ring into ring order
+    CK(la_sync_all(c), "get_memory");
+    std::vector<int> ext(c->p);
+    for (int q = 0; q < c->p; ++q) ext[q] = la_ext_host(c, c->h_k, q);
+    if (ids) {
+      std::vector<int> all((size_t)c->Pe);
+      CK(cudaMemcpy(all.data(), c->d_ring_ids, all.size() * sizeof(int), cudaMemcpyDeviceToHost),
+         "get_memory");
+      for (int q = 0; q < c->p; ++q) ids[q] = ext[q] >= 0 ? all[ext[q]] : -1;
+    }
+    if (G) {
+      std::vector<double> row((size_t)c->Pe);
+      for (int i = 0; i < c->p; ++i) {
+        if (ext[i] < 0) {
+          for (int j = 0; j < c->p; ++j) G[(size_t)i * c->p + j] = 0.0;
+          continue;
+        }
+        CK(cudaMemcpy(row.data(), c->d_G + (size_t)ext[i] * c->Pe, row.size() * sizeof(double),
+                      cudaMemcpyDeviceToHost), "get_memory");
+        for (int j = 0; j < c->p; ++j) G[(size_t)i * c->p + j] = ext[j] >= 0 ? row[ext[j]] : 0.0;
+      }
+    }
+    if (z) CK(cudaMemcpy(z, c->d_z, (size_t)c->p * sizeof(double), cudaMemcpyDeviceToHost),
+              "get_memory");
+    return read_status(c);
+  }
   if (ids) CK(cudaMemcpy(ids, c->d_ring_ids, (size_t)c->p * sizeof(int), cudaMemcpyDeviceToHost),
               "get_memory");
   if (G) CK(cudaMemcpy2D(G, (size_t)c->p * sizeof(double), c->d_G, (size_t)c->P * sizeof(double),
@@ -1021,7 +1437,7 @@ extern "C" slim_status slim_autotune(const slim_geometry* geom, const slim_block
                                      double lambda, const slim_step_opts* base, int steps,
                                      slim_step_opts* best, double* best_ms) {
   if (!geom || !blocks || !best || steps < 1) return SLIM_EINVAL;
-  slim_step_opts b0 = base ? *base : slim_step_opts{1.0, 0, SLIM_SOLVE_FP64, 2, 0, 0, 0};
+  slim_step_opts b0 = base ? *base : slim_step_opts{1.0, 0, SLIM_SOLVE_FP64, 2, 0, 0, 0, 0};
   *best = b0;
   if (geom->dim == 3) {   // per-slice solves: nothing to tune here
     if (best_ms) *best_ms = 0.0;
@@ -1134,6 +1550,11 @@ extern "C" slim_status slim_batch_create(int count, const slim_geometry* geoms,
     if (st != SLIM_OK) {
       slim_batch_destroy(b);
       return st;
+    }
+    if (c->lookahead) {   // a batch captures one plain chain per problem
+      slim_destroy(c);
+      slim_batch_destroy(b);
+      return SLIM_ENOTSUP;
     }
     c->use_graph = 0;   // the batch captures the steps itself
     b->ctx.push_back(c);

@@ -99,44 +99,113 @@ __device__ __forceinline__ void lds_vec(T (&v)[TM], const T* p) {
 }
 
 __host__ __device__ constexpr int gemm_ld(int nb) { return nb + 4; }   // padded row of a staged tile
-// scratch of the blocked tile inverse, placed after the two staged tiles
-__host__ __device__ constexpr int potrf_tmp_elems(int nb) { return (nb / 16 - 1) * 256; }
+constexpr int kPanelLd = 20;   // 16 panel columns + pad, 16-byte rows
 
-// out = beta*C + sign * A B^T for NB x NB tiles (row-major, leading dimension
-// ldA/ldB/ldC).  A and B are staged transposed (k-major) in shared memory;
-// thread (ty,tx) owns the TM x TM block at rows ty*TM.., columns tx*TM.., so
-// each k step reads two contiguous vectors from shared memory.
+// A factorisation CTA holds three NB x gemm_ld(NB) tiles in shared memory:
+//   As, Bs  GEMM operands staged transposed (k-major)
+//   S       a tile staged as is: the GEMM's C operand, or the diagonal tile
+// The diagonal factorisation reuses Bs for the inverse and As for the
+// factored panel and the partial sums of the inverse.
+template <typename T>
+__host__ __device__ constexpr size_t factor_smem_bytes(int nb) {
+  return (size_t)3 * nb * gemm_ld(nb) * sizeof(T);
+}
+
+template <typename T>
+using vec16_t = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+
+// One NB x NB tile (row-major, leading dimension ld) in registers, in EV x EV
+// blocks (EV values per 16 bytes): block b covers rows (b / (NB/EV))*EV..,
+// columns (b % (NB/EV))*EV..; a row's blocks are read by consecutive threads.
 template <typename T, int NB>
-__device__ void tile_gemm_nt(T* out, const T* C, int ldC, const T* A, int ldA, const T* B, int ldB,
-                             bool beta, T sign, T* As, T* Bs) {
-  constexpr int LD = gemm_ld(NB);
-  constexpr int TM = NB / 16;
-  const int tid = threadIdx.x;
-  // stage with 16-byte loads, all of a thread's loads in flight at once
-  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-  constexpr int EV = 16 / sizeof(T);               // values per vector
-  constexpr int NV = NB * NB / EV / kThreads;      // vectors per thread per tile
-  V va[NV], vb[NV];
+struct TileRegs {
+  using V = vec16_t<T>;
+  static constexpr int EV = 16 / sizeof(T);
+  static constexpr int QB = NB / EV;                            // blocks per row
+  static constexpr int NBLKS = QB * QB;
+  static constexpr int BPT = (NBLKS + kThreads - 1) / kThreads;  // blocks per thread
+  V v[BPT][EV];
+  __device__ void load(const T* A, int ld) {
 #pragma unroll
-  for (int t = 0; t < NV; ++t) {
-    const int idx = (tid + t * kThreads) * EV, r = idx / NB, q = idx % NB;
-    va[t] = __ldcg(reinterpret_cast<const V*>(A + (size_t)r * ldA + q));
-    vb[t] = __ldcg(reinterpret_cast<const V*>(B + (size_t)r * ldB + q));
+    for (int t = 0; t < BPT; ++t) {
+      const int b = threadIdx.x + t * kThreads;
+      if (b < NBLKS) {
+        const int rq = b / QB, qq = b % QB;
+#pragma unroll
+        for (int e = 0; e < EV; ++e)
+          v[t][e] = __ldcg(reinterpret_cast<const V*>(A + (size_t)(rq * EV + e) * ld + qq * EV));
+      }
+    }
   }
+  // As[q][r] = A[r][q]: each EV x EV block transposed in registers
+  __device__ void store_t(T* As) const {
+    constexpr int LD = gemm_ld(NB);
 #pragma unroll
-  for (int t = 0; t < NV; ++t) {
-    const int idx = (tid + t * kThreads) * EV, r = idx / NB, q = idx % NB;
-    const T* ea = reinterpret_cast<const T*>(&va[t]);
-    const T* eb = reinterpret_cast<const T*>(&vb[t]);
+    for (int t = 0; t < BPT; ++t) {
+      const int b = threadIdx.x + t * kThreads;
+      if (b < NBLKS) {
+        const int rq = b / QB, qq = b % QB;
 #pragma unroll
-    for (int e = 0; e < EV; ++e) {
-      As[(q + e) * LD + r] = ea[e];
-      Bs[(q + e) * LD + r] = eb[e];
+        for (int e = 0; e < EV; ++e) {
+          V o;
+          T* po = reinterpret_cast<T*>(&o);
+#pragma unroll
+          for (int f = 0; f < EV; ++f) po[f] = reinterpret_cast<const T*>(&v[t][f])[e];
+          *reinterpret_cast<V*>(As + (size_t)(qq * EV + e) * LD + rq * EV) = o;
+        }
+      }
+    }
+  }
+  __device__ void store_n(T* S) const {
+    constexpr int LD = gemm_ld(NB);
+#pragma unroll
+    for (int t = 0; t < BPT; ++t) {
+      const int b = threadIdx.x + t * kThreads;
+      if (b < NBLKS) {
+        const int rq = b / QB, qq = b % QB;
+#pragma unroll
+        for (int e = 0; e < EV; ++e)
+          *reinterpret_cast<V*>(S + (size_t)(rq * EV + e) * LD + qq * EV) = v[t][e];
+      }
+    }
+  }
+};
+
+// Stage A and B transposed into As, Bs and (if C) C as is into S, then
+// barrier.  With one block per thread all loads are in flight together;
+// larger tiles are staged one after another to bound the registers.
+template <typename T, int NB>
+__device__ void stage_tiles(const T* A, int lda, const T* B, int ldb, const T* C, int ldc, T* As,
+                            T* Bs, T* S) {
+  if constexpr (TileRegs<T, NB>::BPT == 1) {
+    TileRegs<T, NB> ra, rb, rc;
+    ra.load(A, lda);
+    rb.load(B, ldb);
+    if (C) rc.load(C, ldc);
+    ra.store_t(As);
+    rb.store_t(Bs);
+    if (C) rc.store_n(S);
+  } else {
+    TileRegs<T, NB> rt;
+    rt.load(A, lda);
+    rt.store_t(As);
+    rt.load(B, ldb);
+    rt.store_t(Bs);
+    if (C) {
+      rt.load(C, ldc);
+      rt.store_n(S);
     }
   }
   __syncthreads();
-  const int ty = tid / 16, tx = tid % 16;
-  T acc[TM][TM];
+}
+
+// acc = (A B^T) for the thread's TM x TM block: thread (ty,tx) owns rows
+// ty*TM.., columns tx*TM..; each k step reads two contiguous vectors.
+template <typename T, int NB>
+__device__ __forceinline__ void gemm_core(const T* As, const T* Bs, T (&acc)[NB / 16][NB / 16]) {
+  constexpr int LD = gemm_ld(NB);
+  constexpr int TM = NB / 16;
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
 #pragma unroll
   for (int a = 0; a < TM; ++a)
 #pragma unroll
@@ -151,20 +220,121 @@ __device__ void tile_gemm_nt(T* out, const T* C, int ldC, const T* A, int ldA, c
 #pragma unroll
       for (int b = 0; b < TM; ++b) acc[a][b] += av[a] * bv[b];
   }
+}
+
+// 16-byte streaming store of EV values.
+template <typename T>
+__device__ __forceinline__ void st_vec16(T* p, const T (&v)[16 / sizeof(T)]) {
+  if constexpr (sizeof(T) == 4)
+    __stcg(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+  else
+    __stcg(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
+}
+
+// Store a thread's TM values of row r (columns tx*TM..) to global memory.
+template <typename T, int TM>
+__device__ __forceinline__ void st_row(T* p, const T (&v)[TM]) {
+  if constexpr (TM * sizeof(T) == 16) {
+    st_vec16<T>(p, v);
+  } else {
 #pragma unroll
-  for (int a = 0; a < TM; ++a)
+    for (int b = 0; b < TM; ++b) stcg(p + b, v[b]);
+  }
+}
+
+// out = sign * A B^T (+ C if C): the TRSM (B = inverse diagonal tile) and the
+// trailing update (C = the tile itself, sign -1) of the tiled algorithm.
+template <typename T, int NB>
+__device__ __noinline__ void task_gemm(T* out, int ldo, const T* A, int lda, const T* B, int ldb, const T* C,
+                          T sign, T* As, T* Bs, T* S) {
+  constexpr int LD = gemm_ld(NB);
+  constexpr int TM = NB / 16;
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  stage_tiles<T, NB>(A, lda, B, ldb, C, ldo, As, Bs, S);
+  T acc[TM][TM];
+  gemm_core<T, NB>(As, Bs, acc);
 #pragma unroll
-    for (int b = 0; b < TM; ++b) {
-      const int r = ty * TM + a, c = tx * TM + b;
-      T v = sign * acc[a][b];
-      if (beta) v += ldcg(C + (size_t)r * ldC + c);
-      stcg(out + (size_t)r * ldC + c, v);
-    }
+  for (int a = 0; a < TM; ++a) {
+    const int r = ty * TM + a;
+    T o[TM];
+#pragma unroll
+    for (int b = 0; b < TM; ++b) o[b] = sign * acc[a][b] + (C ? S[r * LD + tx * TM + b] : T(0));
+    st_row<T, TM>(out + (size_t)r * ldo + tx * TM, o);
+  }
   __syncthreads();
 }
 
-// Factor the NB x NB diagonal tile at Lkk in place (lower triangle) and write
-// its inverse (lower, zeros above) to W.  Non-positive pivots set SLIM_ENOTPD
+template <typename T>
+__device__ __forceinline__ void pivot(T d, T& s, T& rs, int* status) {
+  if (!(d > T(0))) {
+    set_status(status, SLIM_ENOTPD);
+    d = T(1);
+  }
+  if constexpr (sizeof(T) == 4) {
+    // hardware reciprocal square root (a few ulp): the float32 factor only
+    // preconditions the float64-residual refinement
+    rs = rsqrtf(d);
+    s = d * rs;
+  } else {
+    rs = rsqrt_pivot(d, status);
+    s = d * rs;
+  }
+}
+
+// One warp: factor the 16 x 16 block D (lower triangle, leading dimension
+// ld) in place and write its inverse X (lower, zeros above).  Lane l holds
+// row l in registers; step c broadcasts the pivot and column c by shuffles
+// (right-looking: a_lj -= l_lc l_jc for c < j <= l).  Then lane l forms
+// column l of the inverse by forward substitution,
+//   X_il = -(sum_{q=l}^{i-1} L_iq X_ql) / L_ii,  X_ll = 1 / L_ll.
+// Lanes 16..31 mirror lanes 0..15.
+template <typename T>
+__device__ __noinline__ void diag_block(T* D, int ld, T* X, int ldx, int* status) {
+  const int lane = threadIdx.x & 31, l = lane & 15;
+  T a[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) a[j] = (j <= l) ? D[l * ld + j] : T(0);
+  T my_rs = T(0);   // 1 / L_ll
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const T d = __shfl_sync(0xffffffffu, a[c], c);
+    T s, rs;
+    pivot(d, s, rs, status);
+    if (l == c) my_rs = rs;
+    const T lc = (l > c) ? a[c] * rs : T(0);
+    a[c] = (l == c) ? s : lc;
+#pragma unroll
+    for (int j = c + 1; j < 16; ++j) {
+      const T bj = __shfl_sync(0xffffffffu, lc, j);
+      if (l >= j) a[j] -= lc * bj;
+    }
+  }
+  if (lane < 16) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j <= l) D[l * ld + j] = a[j];
+  }
+  __syncwarp();
+  // rows of L are read back from shared memory (one broadcast load each)
+  T x[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const T rs_i = __shfl_sync(0xffffffffu, my_rs, i);
+    T sum = T(0);
+#pragma unroll
+    for (int q = 0; q < i; ++q) sum += D[i * ld + q] * x[q];
+    x[i] = (i == l) ? rs_i : (i > l ? -sum * rs_i : T(0));
+  }
+  if (lane < 16) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) X[i * ldx + l] = x[i];
+  }
+  __syncwarp();
+}
+
+// Float64 tile factorisation: factor the NB x NB tile In (lower triangle,
+// leading dimension ld_in; read once at the start) into Lkk and write its
+// inverse (lower, zeros above) to W.  Non-positive pivots set SLIM_ENOTPD
 // and are replaced by 1 so the factorisation still completes without NaNs.
 //
 // Right-looking elimination on the unscaled Schur complements,
@@ -181,13 +351,14 @@ __device__ void tile_gemm_nt(T* out, const T* C, int ldC, const T* A, int ldA, c
 // The inverse is blocked in 16 x 16 blocks: diagonal blocks in parallel, then
 // one block diagonal at a time, W_ij = -W_ii (sum_{k=j}^{i-1} L_ik W_kj).
 template <typename T, int NB>
-__device__ void tile_potrf(T* Lkk, int ld, T* W, T* S, T* Ls, int* status) {
+__device__ void potrf_elim(const T* In, int ld_in, T* Lkk, int ld, T* W, T* S, T* Ls,
+                           int* status) {
   constexpr int LD = NB + 1;
   constexpr int TM = NB / 16;
   constexpr bool kF64 = sizeof(T) == 8;
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
-  // shared layout (S and Ls hold NB*(NB+4) values each, followed by
-  // potrf_tmp_elems(NB) values of scratch):
+  // shared layout (S and Ls hold NB*(NB+4) values each; the scratch of the
+  // inverse follows Ls and may overlap In, which is no longer read then):
   //   S:  the tile, NB x LD, then sqrt(d_c) and 1/sqrt(d_c) (2*NB)
   //   Ls: the double-buffered column (2*(NB+1), the last entry 1/d for
   //       float64) during the elimination, then the inverse W (NB x LD)
@@ -198,10 +369,10 @@ __device__ void tile_potrf(T* Lkk, int ld, T* W, T* S, T* Ls, int* status) {
 #pragma unroll
   for (int u = 0; u < TM; ++u)
 #pragma unroll
-    for (int v = 0; v < TM; ++v) a[u][v] = ldcg(Lkk + (size_t)(ty + 16 * u) * ld + tx + 16 * v);
-  for (int i = tid; i < NB; i += kThreads) colbuf[i] = ldcg(Lkk + (size_t)i * ld);
+    for (int v = 0; v < TM; ++v) a[u][v] = In[(ty + 16 * u) * ld_in + tx + 16 * v];
+  for (int i = tid; i < NB; i += kThreads) colbuf[i] = In[i * ld_in];
   if (kF64 && tid == 0) {
-    const T d0 = ldcg(Lkk);
+    const T d0 = In[0];
     colbuf[NB] = d0 > T(0) ? T(1) / d0 : T(1);
   }
   __syncthreads();
@@ -319,6 +490,191 @@ __device__ void tile_potrf(T* Lkk, int ld, T* W, T* S, T* Ls, int* status) {
   __syncthreads();
 }
 
+// Factor the diagonal tile held in S (lower triangle of K_kk after its
+// updates) and write L_kk (zeros above the diagonal) to Lg and its inverse
+// to Wg.  Blocked by 16 columns: warp 0 factors and inverts the 16 x 16
+// diagonal block, the CTA forms the panel below it, L_P = S_P D^{-T}, and
+// updates the trailing lower triangle, S -= L_P L_P^T (three barriers per
+// panel).  Then the off-diagonal blocks of the inverse, one block diagonal
+// at a time: W_ij = -W_ii sum_{k=j}^{i-1} L_ik W_kj.
+// Non-positive pivots set SLIM_ENOTPD and are replaced by 1, so the
+// factorisation still completes without NaNs.
+template <typename T, int NB>
+__device__ void potrf_smem(T* S, T* Wt, T* Pn, T* Tmp, T* Lg, int ld, T* Wg, int* status) {
+  constexpr int LD = gemm_ld(NB);
+  constexpr int LP = kPanelLd;
+  constexpr int NBLK = NB / 16;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int ty = tid / 16, tx = tid % 16;
+  for (int idx = tid; idx < NB * NB; idx += kThreads) {
+    const int i = idx / NB, c = idx % NB;
+    if (i / 16 < c / 16) Wt[i * LD + c] = T(0);
+  }
+  for (int pb = 0; pb < NBLK; ++pb) {
+    const int c0 = 16 * pb;
+    if (warp == 0) diag_block<T>(S + c0 * LD + c0, LD, Wt + c0 * LD + c0, LD, status);
+    __syncthreads();
+    const int rows = NB - c0 - 16;
+    if (rows == 0) break;
+    for (int idx = tid; idx < rows * 16; idx += kThreads) {
+      const int r = c0 + 16 + idx / 16, c = idx % 16;
+      const T* sr = S + r * LD + c0;
+      const T* dc = Wt + (c0 + c) * LD + c0;   // row c of D^{-1}, zeros above the diagonal
+      T acc = T(0);
+#pragma unroll
+      for (int q = 0; q < 16; q += 16 / sizeof(T)) {
+        constexpr int EV = 16 / sizeof(T);
+        T sv[EV], dv[EV];
+        lds_vec<T, EV>(sv, sr + q);
+        lds_vec<T, EV>(dv, dc + q);
+#pragma unroll
+        for (int e = 0; e < EV; ++e) acc += sv[e] * dv[e];
+      }
+      Pn[r * LP + c] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < NBLK; ++u) {
+      const int r = ty + 16 * u;
+      if (r < c0 + 16) continue;
+#pragma unroll
+      for (int v = 0; v < NBLK; ++v) {
+        const int c = tx + 16 * v;
+        if (c < c0 + 16 || c > r) continue;
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < 16; q += 16 / sizeof(T)) {
+          constexpr int EV = 16 / sizeof(T);
+          T pr[EV], pc[EV];
+          lds_vec<T, EV>(pr, Pn + r * LP + q);
+          lds_vec<T, EV>(pc, Pn + c * LP + q);
+#pragma unroll
+          for (int e = 0; e < EV; ++e) acc += pr[e] * pc[e];
+        }
+        S[r * LD + c] -= acc;
+      }
+    }
+    for (int idx = tid; idx < rows * 16; idx += kThreads) {
+      const int r = c0 + 16 + idx / 16, c = idx % 16;
+      S[r * LD + c0 + c] = Pn[r * LP + c];
+    }
+    __syncthreads();
+  }
+  constexpr int EVI = 16 / sizeof(T);
+#pragma unroll
+  for (int d = 1; d < NBLK; ++d) {
+    const int nblk = NBLK - d;   // blocks (i, i-d) on this block diagonal
+    for (int idx = tid; idx < nblk * 256; idx += kThreads) {
+      const int bi = idx / 256, e = idx % 256, r = e / 16, c = e % 16;
+      const int i = bi + d, j = bi;
+      T acc = T(0);
+#pragma unroll
+      for (int kk = 0; kk < d; ++kk) {
+        const int k = j + kk;
+#pragma unroll
+        for (int q = 0; q < 16; q += EVI) {
+          T sv[EVI];
+          lds_vec<T, EVI>(sv, S + (i * 16 + r) * LD + k * 16 + q);
+#pragma unroll
+          for (int f = 0; f < EVI; ++f) acc += sv[f] * Wt[(k * 16 + q + f) * LD + j * 16 + c];
+        }
+      }
+      Tmp[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nblk * 256; idx += kThreads) {
+      const int bi = idx / 256, e = idx % 256, r = e / 16, c = e % 16;
+      const int i = bi + d;
+      T acc = T(0);
+#pragma unroll
+      for (int q = 0; q < 16; q += EVI) {
+        T wv[EVI];
+        lds_vec<T, EVI>(wv, Wt + (i * 16 + r) * LD + i * 16 + q);
+#pragma unroll
+        for (int f = 0; f < EVI; ++f) acc += wv[f] * Tmp[bi * 256 + (q + f) * 16 + c];
+      }
+      Wt[(i * 16 + r) * LD + bi * 16 + c] = -acc;
+    }
+    __syncthreads();
+  }
+  constexpr int EV = 16 / sizeof(T);
+  for (int idx = tid; idx < NB * NB / EV; idx += kThreads) {
+    const int r = idx / (NB / EV), c = (idx % (NB / EV)) * EV;
+    T lo[EV], wo[EV];
+#pragma unroll
+    for (int e = 0; e < EV; ++e) {
+      lo[e] = (c + e <= r) ? S[r * LD + c + e] : T(0);
+      wo[e] = Wt[r * LD + c + e];
+    }
+    st_vec16(Lg + (size_t)r * ld + c, lo);
+    st_vec16(Wg + (size_t)r * NB + c, wo);
+  }
+  __syncthreads();
+}
+
+// Factor the diagonal tile staged in S (float32: blocked by 16 columns;
+// float64: CTA-wide elimination, where the narrow float64 pipe makes one
+// warp's serial 16 x 16 factorisations slow).
+template <typename T, int NB>
+__device__ __forceinline__ void potrf_tile(T* S, T* As, T* Bs, T* Lg, int ld, T* Wg, int* status) {
+  if constexpr (sizeof(T) == 8)
+    potrf_elim<T, NB>(S, gemm_ld(NB), Lg, ld, Wg, As, Bs, status);
+  else
+    potrf_smem<T, NB>(S, Bs, As, As + NB * kPanelLd, Lg, ld, Wg, status);
+}
+
+// The critical path of panel k in one task (i = k+1): L_ik = A_ik W_k^T
+// (published at once for the trailing updates), then A_ii -= L_ik L_ik^T with
+// L_ik kept in shared memory, then the factorisation of tile (i,i).
+template <typename T, int NB>
+__device__ __noinline__ void task_panel(T* t_ik, T* t_ii, int P, const T* w_k, T* w_i, int* flag_ik, T* As,
+                           T* Bs, T* S, int* status) {
+  constexpr int LD = gemm_ld(NB);
+  constexpr int TM = NB / 16;
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  stage_tiles<T, NB>(t_ik, P, w_k, NB, t_ii, P, As, Bs, S);
+  T acc[TM][TM];
+  gemm_core<T, NB>(As, Bs, acc);
+  __syncthreads();   // every thread is done reading As
+#pragma unroll
+  for (int a = 0; a < TM; ++a) st_row<T, TM>(t_ik + (size_t)(ty * TM + a) * P + tx * TM, acc[a]);
+  // As[c][r] = X[r][c]: the thread's TM rows of column c are contiguous
+#pragma unroll
+  for (int b = 0; b < TM; ++b) {
+    T col[TM];
+#pragma unroll
+    for (int a = 0; a < TM; ++a) col[a] = acc[a][b];
+    if constexpr (TM * sizeof(T) == 16) {
+      vec16_t<T> o;
+      T* po = reinterpret_cast<T*>(&o);
+#pragma unroll
+      for (int a = 0; a < TM; ++a) po[a] = col[a];
+      *reinterpret_cast<vec16_t<T>*>(As + (tx * TM + b) * LD + ty * TM) = o;
+    } else {
+#pragma unroll
+      for (int a = 0; a < TM; ++a) As[(tx * TM + b) * LD + ty * TM + a] = col[a];
+    }
+  }
+  cta_publish(flag_ik);
+  gemm_core<T, NB>(As, As, acc);
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TM; ++b) S[(ty * TM + a) * LD + tx * TM + b] -= acc[a][b];
+  __syncthreads();
+  potrf_tile<T, NB>(S, As, Bs, t_ii, P, w_i, status);
+}
+
+// Factor diagonal tile (k,k) when nothing precedes it (k = 0).
+template <typename T, int NB>
+__device__ __noinline__ void task_potrf(T* Lkk, int P, T* w_k, T* As, T* Bs, T* S, int* status) {
+  TileRegs<T, NB> rc;
+  rc.load(Lkk, P);
+  rc.store_n(S);
+  __syncthreads();
+  potrf_tile<T, NB>(S, As, Bs, Lkk, P, w_k, status);
+}
+
 template <typename T, int NB>
 __global__ void __launch_bounds__(kThreads, 2) chol_factor_kernel(T* L, int P, int Tt,
                                                                const CholTask* tasks, int ntasks,
@@ -327,6 +683,7 @@ __global__ void __launch_bounds__(kThreads, 2) chol_factor_kernel(T* L, int P, i
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* As = reinterpret_cast<T*>(smem_raw);
   T* Bs = As + NB * gemm_ld(NB);
+  T* S = Bs + NB * gemm_ld(NB);
   __shared__ int s_task, s_ok3[3];
   __shared__ CholTask s_desc;
   const int tid = threadIdx.x;
@@ -355,7 +712,7 @@ __global__ void __launch_bounds__(kThreads, 2) chol_factor_kernel(T* L, int P, i
         T* tile_im = L + (size_t)i * NB * P + (size_t)m * NB;
         const T* Lik = L + (size_t)i * NB * P + (size_t)k * NB;
         const T* Lmk = L + (size_t)m * NB * P + (size_t)k * NB;
-        tile_gemm_nt<T, NB>(tile_im, tile_im, P, Lik, P, Lmk, P, true, T(-1), As, Bs);
+        task_gemm<T, NB>(tile_im, P, Lik, P, Lmk, P, tile_im, T(-1), As, Bs, S);
         cta_publish(&cnt[i * Tt + m]);
       }
     } else if (tk.type == kTrsm) {
@@ -363,29 +720,24 @@ __global__ void __launch_bounds__(kThreads, 2) chol_factor_kernel(T* L, int P, i
                     status, s_ok3);
       if (ok) {
         T* tile_im = L + (size_t)i * NB * P + (size_t)m * NB;
-        tile_gemm_nt<T, NB>(tile_im, nullptr, P, tile_im, P, winv + (size_t)m * NB * NB, NB, false,
-                            T(1), As, Bs);
+        task_gemm<T, NB>(tile_im, P, tile_im, P, winv + (size_t)m * NB * NB, NB, nullptr, T(1),
+                         As, Bs, S);
         cta_publish(&cnt[i * Tt + m]);
       }
     } else if (tk.type == kPanel) {
-      // i = k+1: TRSM(k+1,k), SYRK into (k+1,k+1), POTRF(k+1)
       ok = cta_wait(&cnt[k * Tt + k], k + 1, &cnt[i * Tt + k], k, &cnt[i * Tt + i], k, 3,
                     abort_flag, status, s_ok3);
       if (ok) {
-        T* t_ik = L + (size_t)i * NB * P + (size_t)k * NB;
-        T* t_ii = L + (size_t)i * NB * P + (size_t)i * NB;
-        tile_gemm_nt<T, NB>(t_ik, nullptr, P, t_ik, P, winv + (size_t)k * NB * NB, NB, false,
-                            T(1), As, Bs);
-        cta_publish(&cnt[i * Tt + k]);
-        tile_gemm_nt<T, NB>(t_ii, t_ii, P, t_ik, P, t_ik, P, true, T(-1), As, Bs);
-        tile_potrf<T, NB>(t_ii, P, winv + (size_t)i * NB * NB, As, Bs, status);
+        task_panel<T, NB>(L + (size_t)i * NB * P + (size_t)k * NB,
+                          L + (size_t)i * NB * P + (size_t)i * NB, P, winv + (size_t)k * NB * NB,
+                          winv + (size_t)i * NB * NB, &cnt[i * Tt + k], As, Bs, S, status);
         cta_publish(&cnt[i * Tt + i], 2);
       }
     } else {
       ok = cta_wait(&cnt[k * Tt + k], k, abort_flag, status, s_ok3);
       if (ok) {
-        T* Lkk = L + (size_t)k * NB * P + (size_t)k * NB;
-        tile_potrf<T, NB>(Lkk, P, winv + (size_t)k * NB * NB, As, Bs, status);
+        task_potrf<T, NB>(L + (size_t)k * NB * P + (size_t)k * NB, P, winv + (size_t)k * NB * NB,
+                          As, Bs, S, status);
         cta_publish(&cnt[k * Tt + k]);
       }
     }
@@ -524,7 +876,7 @@ __global__ void __launch_bounds__(kThreads) chol_bwd_kernel(const T* L, int P, i
 }
 
 template <typename T, int NB>
-size_t factor_smem() { return (2 * NB * gemm_ld(NB) + potrf_tmp_elems(NB)) * sizeof(T); }
+size_t factor_smem() { return factor_smem_bytes<T>(NB); }
 
 template <typename T, int NB>
 cudaError_t launch_factor(const CholPlan& p, void* L, int* status, cudaStream_t s) {

@@ -88,6 +88,25 @@ __device__ __forceinline__ void set_status(int* status, int code) {
   atomicCAS(status, 0, code);
 }
 
+// 1/sqrt(d) in float64 from a float seed refined by two Newton-Raphson steps
+// r <- r (3/2 - d r^2 / 2) (each roughly doubles the correct bits, about
+// 22 -> 44 -> the float64 precision);
+// a handful of float64 operations where the library square root and division
+// are long sequences on the float64 pipe.  d <= 0 is reported as SLIM_ENOTPD
+// and replaced by 1; magnitudes outside the float range take the slow path.
+__device__ __forceinline__ double rsqrt_pivot(double d, int* status) {
+  if (!(d > 0.0)) {
+    set_status(status, SLIM_ENOTPD);
+    d = 1.0;
+  }
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double r = (double)rsqrtf((float)d);
+  const double h = 0.5 * d;
+  r = r * fma(-h * r, r, 1.5);
+  r = r * fma(-h * r, r, 1.5);
+  return r;
+}
+
 // Per-step values computed on the device by the sampler.
 struct StepInfo {
   long long k;      // 1-based index of the step being taken

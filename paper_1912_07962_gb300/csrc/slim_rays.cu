@@ -240,21 +240,6 @@ __global__ void __launch_bounds__(kCta) slice_gram_kernel(RayArgs a) {
   }
 }
 
-// 1/sqrt(d) in float64 from a float seed and two Newton steps (a handful of
-// float64 operations; the library square root and division are long
-// sequences on the float64 pipe).  d <= 0 is reported and replaced by 1.
-__device__ __forceinline__ double rsqrt_pivot(double d, int* status) {
-  if (!(d > 0.0)) {
-    set_status(status, SLIM_ENOTPD);
-    d = 1.0;
-  }
-  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-  double r = (double)rsqrtf((float)d);
-  const double h = 0.5 * d;
-  r = r * fma(-h * r, r, 1.5);
-  r = r * fma(-h * r, r, 1.5);
-  return r;
-}
 
 // 3D: one CTA of 4 warps per slice: K_s = lambda_k I + G_s from the stored
 // Gram, float64 Cholesky in shared memory (one pivot reciprocal per column,

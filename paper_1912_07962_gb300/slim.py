@@ -32,7 +32,7 @@ EXPORTS = [
     "slim_get_sizes", "slim_project", "slim_backproject", "slim_damped_solve",
     "slim_set_timing", "slim_get_timing", "slim_damped_solve_noalloc", "slim_get_csr",
     "slim_autotune", "slim_batch_create", "slim_batch_ctx", "slim_batch_step", "slim_batch_sync",
-    "slim_batch_set_stream", "slim_batch_destroy",
+    "slim_batch_set_stream", "slim_batch_destroy", "slim_get_launch_log",
 ]
 A_MATRIX_FREE, A_CSR_F32, A_CSR_BF16 = 0, 1, 2
 NOALLOC_MAX_P = 1024
@@ -53,7 +53,7 @@ class slim_blocks(C.Structure):
 class slim_step_opts(C.Structure):
     _fields_ = [("eta", C.c_double), ("ramp", C.c_int), ("solver", C.c_int),
                 ("refine_iters", C.c_int), ("use_graph", C.c_int), ("tile", C.c_int),
-                ("ctas_per_sm", C.c_int)]
+                ("ctas_per_sm", C.c_int), ("lookahead", C.c_int)]
 
 
 class SlimError(RuntimeError):
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "slim_batch_sync": ([VP], I),
         "slim_batch_set_stream": ([VP, VP], I),
         "slim_batch_destroy": ([VP], None),
+        "slim_get_launch_log": ([VP, P(D), P(D), P(LL)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -141,7 +142,7 @@ class Slim:
     def __init__(self, N, n_views, det, ell, r, lam, seed, precision=SLIM_PREC_FP64,
                  solver=SLIM_SOLVE_FP64, refine_iters=2, eta=1.0, ramp=False, use_graph=False,
                  angles=None, a_mode=A_MATRIX_FREE, dim=2, det_v=1, kind=SLIM_BLOCKS_VIEWS,
-                 steps_per_view=1, tile=0, ctas_per_sm=0, _handle=None):
+                 steps_per_view=1, tile=0, ctas_per_sm=0, lookahead=0, _handle=None):
         lib = load()
         self._lib = lib
         self._angles = None
@@ -159,7 +160,8 @@ class Slim:
             self._angles = np.ascontiguousarray(angles, dtype=np.float64)
             g.angles = self._angles.ctypes.data_as(C.POINTER(C.c_double))
         blk = slim_blocks(kind, ell, seed, steps_per_view)
-        opts = slim_step_opts(eta, int(ramp), solver, refine_iters, int(use_graph), tile, ctas_per_sm)
+        opts = slim_step_opts(eta, int(ramp), solver, refine_iters, int(use_graph), tile, ctas_per_sm,
+                              lookahead)
         h = C.c_void_p()
         st = lib.slim_create(C.byref(g), C.byref(blk), r, lam, C.byref(opts), C.byref(h))
         if st != SLIM_OK:
@@ -232,6 +234,13 @@ class Slim:
         k = C.c_int()
         self._check(self._lib.slim_get_timing(self.h, ms, len(PHASES), C.byref(k)))
         return dict(zip(PHASES, list(ms))), k.value
+
+    def launch_log(self):
+        """(mean factorisation ms, mean iterate-chain ms, iterate chains) since the
+        previous call; pipelined form with timing on."""
+        f, x, n = C.c_double(), C.c_double(), C.c_longlong()
+        self._check(self._lib.slim_get_launch_log(self.h, C.byref(f), C.byref(x), C.byref(n)))
+        return f.value, x.value, n.value
 
     def kernels_per_step(self):
         k = C.c_int()
@@ -327,7 +336,7 @@ def problem_structs(specs):
         R[i] = sp["r"]
         L[i] = sp["lam"]
         S[i] = slim_step_opts(1.0, 0, sp.get("solver", 0), sp.get("refine_iters", 2), 0,
-                              sp.get("tile", 0), sp.get("ctas_per_sm", 0))
+                              sp.get("tile", 0), sp.get("ctas_per_sm", 0), sp.get("lookahead", 0))
     return G, B, R, L, S
 
 

@@ -130,3 +130,23 @@ def test_bad_tile_rejected(sl):
         sl.Slim(32, 20, 47, 47, 2, 1e-2, 1, tile=48)
     with pytest.raises(sl.SlimError):
         sl.Slim(32, 20, 47, 47, 2, 1e-2, 1, ctas_per_sm=5)
+
+
+@pytest.mark.parametrize("solver,tile,cps", [(0, 32, 1), (0, 64, 3), (1, 32, 2), (1, 64, 1)])
+def test_tile_variants_single_step(sl, solver, tile, cps):
+    """Each factor precision x tile size, several tiles and a ragged tail."""
+    N, V, D, ell, r, lam, seed = 40, 30, 57, 57, 5, 1e-2, 21   # p = 342
+    g = joseph.Geometry(N, V, D)
+    b = workloads.add_noise(joseph.full_matrix(g) @ workloads.phantom_2d(N, seed, 5),
+                            workloads.noise_direction(g.m, seed), 0.01)
+    sched = list(oslim.view_schedule(g, seed, 8))
+    traj = [x for _, x, _ in oslim.run(oslim.tomo_source(g, b), sched, r, lam)]
+    s = sl.Slim(N, V, D, ell, r, lam, seed, precision=sl.SLIM_PREC_FP64, solver=solver, tile=tile,
+                ctas_per_sm=cps)
+    s.set_data(b)
+    s.step(7)
+    s.set_x(traj[6])
+    s.step(1)
+    tol = 1e-12 if solver == 0 else 1e-9
+    assert rel(s.get_x(), traj[7]) < tol
+    s.close()
