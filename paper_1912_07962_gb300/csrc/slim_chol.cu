@@ -15,6 +15,8 @@
 // backward solve runs the transposed chain from the last block.
 #include <type_traits>
 
+#include <cooperative_groups.h>
+
 #include "slim_chol.cuh"
 #include "slim_device.cuh"
 
@@ -875,6 +877,280 @@ __global__ void __launch_bounds__(kThreads) chol_bwd_kernel(const T* L, int P, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// Both triangular solves of L L^T z = v in one thread-block cluster.
+//
+// Tile row i belongs to CTA i mod C.  Every CTA keeps the whole of y (and
+// then z) in its shared memory: the owner of a tile row broadcasts its C-block
+// of y into all CTAs of the cluster (distributed shared memory) and then sets
+// a per-row flag in each of them with a cluster-scope release; the others
+// poll their own flag.  While waiting for row j-1, a CTA has already folded
+// rows < j-1 into its accumulator, so each link of the chain costs one
+// NB x NB matrix-vector product and one broadcast.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
+__device__ __forceinline__ int ld_acquire_cluster(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cluster.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_cluster(int* p, int v) {
+  asm volatile("st.release.cluster.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+
+// CTA-wide bounded wait for a flag in this CTA's shared memory.
+__device__ bool cluster_wait(const int* flag, int* abort_flag, int* status, int* s_ok) {
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned it = 0;
+    while (ld_acquire_cluster(flag) == 0) {
+      if (++it > kSpinLimit) {
+        set_status(status, SLIM_ETIMEOUT);
+        atomicExch(abort_flag, 1);
+        ok = 0;
+        break;
+      }
+      if ((it & 255u) == 0 && ld_acquire(abort_flag)) {
+        ok = 0;
+        break;
+      }
+      __nanosleep(16);
+    }
+    *s_ok = ok;
+  }
+  __syncthreads();
+  const int ok = *s_ok;
+  __syncthreads();
+  return ok != 0;
+}
+
+// Write the NB values of out[] into row block i of `vec` in every CTA of the
+// cluster, then raise flag[i] in each of them.
+template <typename T, int NB>
+__device__ void cluster_publish(cg::cluster_group& cl, int C, T* vec, int* flag, int i,
+                                const T* out) {
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < C * NB; idx += kThreads) {
+    const int d = idx / NB, e = idx % NB;
+    T* rv = cl.map_shared_rank(vec, d);
+    rv[i * NB + e] = out[e];
+  }
+  fence_cluster();
+  __syncthreads();
+  if (tid < C) st_release_cluster(cl.map_shared_rank(flag, tid) + i, 1);
+}
+
+// Bounded wait until flags [j0, j1) in this CTA's shared memory are all set.
+__device__ bool cluster_wait_range(const int* flag, int j0, int j1, int* abort_flag, int* status,
+                                   int* s_ok) {
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    for (int j = j0; ok && j < j1; ++j) {
+      unsigned it = 0;
+      while (ld_acquire_cluster(flag + j) == 0) {
+        if (++it > kSpinLimit) {
+          set_status(status, SLIM_ETIMEOUT);
+          atomicExch(abort_flag, 1);
+          ok = 0;
+          break;
+        }
+        if ((it & 255u) == 0 && ld_acquire(abort_flag)) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(16);
+      }
+    }
+    *s_ok = ok;
+  }
+  __syncthreads();
+  const int ok = *s_ok;
+  __syncthreads();
+  return ok != 0;
+}
+
+constexpr int kSolveBatch = 4;   // tiles folded per batch
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(kThreads) chol_solve_cluster_kernel(
+    const T* L, int P, int Tt, const T* winv, const double* v, double* z, int* status,
+    int* abort_flag) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* y = reinterpret_cast<T*>(smem_raw);     // [P] forward solution
+  T* zt = y + P;                              // [P] backward solution
+  int* fready = reinterpret_cast<int*>(zt + P);
+  int* bready = fready + Tt;
+  __shared__ T acc[NB], out[NB];
+  __shared__ T part[kThreads];
+  __shared__ int s_ok;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x;
+  for (int i = tid; i < Tt; i += kThreads) {
+    fready[i] = 0;
+    bready[i] = 0;
+  }
+  cl.sync();   // every CTA's flags are cleared before anyone publishes
+  bool ok = true;
+  // forward: y_i = W_i (v_i - sum_{j<i} L_ij y_j)
+  {
+    using RP = RowPart<T, NB>;
+    const int r = tid / RP::TPR, sub = tid % RP::TPR;
+    for (int i = rank; ok && i < Tt; i += C) {
+      RP wpart, lastp, bp[kSolveBatch];
+      wpart.load(winv + (size_t)i * NB * NB, NB);
+      if (i > 0) lastp.load(L + (size_t)i * NB * P + (size_t)(i - 1) * NB, P);
+      T s = T(0);
+      // tiles j < i-1: their blocks are (mostly) solved already; fold them in
+      // batches with all loads in flight
+      for (int j = 0; j + 1 < i; j += kSolveBatch) {
+        const int nj = min(kSolveBatch, i - 1 - j);
+#pragma unroll
+        for (int u = 0; u < kSolveBatch; ++u)
+          if (u < nj) bp[u].load(L + (size_t)i * NB * P + (size_t)(j + u) * NB, P);
+        if (!cluster_wait_range(fready, j, j + nj, abort_flag, status, &s_ok)) {
+          ok = false;
+          break;
+        }
+#pragma unroll
+        for (int u = 0; u < kSolveBatch; ++u)
+          if (u < nj)
+#pragma unroll
+            for (int q = 0; q < RP::CPT; ++q) s += bp[u].v[q] * y[(j + u) * NB + sub * RP::CPT + q];
+      }
+      if (!ok) break;
+      if (i > 0) {
+        if (!cluster_wait_range(fready, i - 1, i, abort_flag, status, &s_ok)) {
+          ok = false;
+          break;
+        }
+#pragma unroll
+        for (int q = 0; q < RP::CPT; ++q) s += lastp.v[q] * y[(i - 1) * NB + sub * RP::CPT + q];
+      }
+#pragma unroll
+      for (int o = RP::TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, RP::TPR);
+      if (sub == 0) acc[r] = (T)v[i * NB + r] - s;
+      if (tid < NB) out[tid] = T(0);
+      __syncthreads();
+      wpart.apply(acc, out, T(1));
+      __syncthreads();
+      cluster_publish<T, NB>(cl, C, y, fready, i, out);
+    }
+  }
+  // backward: z_i = W_i^T (y_i - sum_{j>i} L_ji^T z_j)
+  {
+    using CP = ColPart<T, NB>;
+    const int a = tid % NB, ch = tid / NB;
+    const int last = Tt - 1 - ((Tt - 1 - rank) % C + C) % C;   // largest i = rank (mod C)
+    for (int i = last; ok && i >= 0; i -= C) {
+      CP wpart, nextp, bp[kSolveBatch];
+      wpart.load(winv + (size_t)i * NB * NB, NB);
+      if (i + 1 < Tt) nextp.load(L + (size_t)(i + 1) * NB * P + (size_t)i * NB, P);
+      T s = T(0);
+      for (int j = Tt - 1; j > i + 1; j -= kSolveBatch) {
+        const int nj = min(kSolveBatch, j - i - 1);   // tiles j, j-1, .., j-nj+1
+#pragma unroll
+        for (int u = 0; u < kSolveBatch; ++u)
+          if (u < nj) bp[u].load(L + (size_t)(j - u) * NB * P + (size_t)i * NB, P);
+        if (!cluster_wait_range(bready, j - nj + 1, j + 1, abort_flag, status, &s_ok)) {
+          ok = false;
+          break;
+        }
+#pragma unroll
+        for (int u = 0; u < kSolveBatch; ++u)
+          if (u < nj)
+#pragma unroll
+            for (int q = 0; q < CP::RPC; ++q) s += bp[u].v[q] * zt[(j - u) * NB + ch * CP::RPC + q];
+      }
+      if (!ok) break;
+      if (i + 1 < Tt) {
+        if (!cluster_wait_range(bready, i + 1, i + 2, abort_flag, status, &s_ok)) {
+          ok = false;
+          break;
+        }
+#pragma unroll
+        for (int q = 0; q < CP::RPC; ++q) s += nextp.v[q] * zt[(i + 1) * NB + ch * CP::RPC + q];
+      }
+      part[ch * NB + a] = s;
+      __syncthreads();
+      if (tid < NB) {
+        T t = T(0);
+#pragma unroll
+        for (int c = 0; c < CP::CH; ++c) t += part[c * NB + tid];
+        acc[tid] = y[i * NB + tid] - t;
+        out[tid] = T(0);
+      }
+      __syncthreads();
+      wpart.apply(acc, out, T(1), part);
+      __syncthreads();
+      if (tid < NB) z[i * NB + tid] = (double)out[tid];
+      cluster_publish<T, NB>(cl, C, zt, bready, i, out);
+    }
+  }
+  cl.sync();   // no CTA leaves while others may still write into its shared memory
+}
+
+template <typename T>
+size_t solve_cluster_smem(int P, int Tt) { return 2 * (size_t)P * sizeof(T) + 2 * (size_t)Tt * sizeof(int); }
+
+// Largest cluster (16, else 8) that fits the solve, or 0 when none does.
+template <typename T, int NB>
+int pick_solve_cluster(int P, int Tt) {
+  constexpr int kMaxSmem = 200 * 1024;   // allowance set once for every plan
+  const size_t smem = solve_cluster_smem<T>(P, Tt);
+  if (smem > (size_t)kMaxSmem) return 0;
+  auto kern = chol_solve_cluster_kernel<T, NB>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const bool np = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                  cudaSuccess;
+  cudaGetLastError();
+  for (int C : {16, 8}) {
+    if (C > 8 && !np) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = C;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) return C;
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+template <typename T, int NB>
+cudaError_t launch_solve_cluster(const CholPlan& p, const void* L, const double* v, double* z,
+                                 int* status, cudaStream_t s) {
+  int* abort_flag = p.d_sync + p.T * p.T + 2 * p.T + 3;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p.cluster);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = solve_cluster_smem<T>(p.P, p.T);
+  cfg.stream = s;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = p.cluster;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, chol_solve_cluster_kernel<T, NB>, (const T*)L, p.P, p.T,
+                            (const T*)p.d_winv, v, z, status, abort_flag);
+}
+
 template <typename T, int NB>
 size_t factor_smem() { return factor_smem_bytes<T>(NB); }
 
@@ -950,6 +1226,12 @@ cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_
   if ((e = cudaMalloc(&plan->d_winv, (size_t)plan->T * nb * nb * es)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&plan->d_y, 2 * (size_t)P * es)) != cudaSuccess) return e;
   plan->grid = ctas_per_sm * num_sms;
+  if (is_f32)
+    plan->cluster = nb == 64 ? pick_solve_cluster<float, 64>(P, plan->T)
+                             : pick_solve_cluster<float, 32>(P, plan->T);
+  else
+    plan->cluster = nb == 64 ? pick_solve_cluster<double, 64>(P, plan->T)
+                             : pick_solve_cluster<double, 32>(P, plan->T);
   // opt in to the shared memory the factor kernel needs
   if (is_f32) {
     if (nb == 64)
@@ -994,6 +1276,12 @@ cudaError_t chol_factor(const CholPlan& p, void* L, int* status, cudaStream_t s)
 
 cudaError_t chol_solve(const CholPlan& p, const void* L, const double* v, double* z, int* status,
                        cudaStream_t s) {
+  if (p.cluster) {
+    if (p.is_f32) return p.nb == 64 ? launch_solve_cluster<float, 64>(p, L, v, z, status, s)
+                                    : launch_solve_cluster<float, 32>(p, L, v, z, status, s);
+    return p.nb == 64 ? launch_solve_cluster<double, 64>(p, L, v, z, status, s)
+                      : launch_solve_cluster<double, 32>(p, L, v, z, status, s);
+  }
   // reset the solve flags and tickets, keep the factor's abort flag
   int* fflag = p.d_sync + p.T * p.T;
   cudaError_t e = cudaMemsetAsync(fflag, 0, (2 * p.T + 3) * sizeof(int), s);

@@ -36,6 +36,7 @@ struct CholPlan {
   void* d_winv = nullptr;        // T inverse diagonal tiles, NB*NB each (factor precision)
   void* d_y = nullptr;           // forward-solve intermediate, P values (factor precision)
   int grid = 0;                  // persistent CTAs for the factorisation
+  int cluster = 0;               // CTAs of the cluster that runs both solves (0: chained CTAs)
 };
 
 // Allocate / free the plan for order P (multiple of nb).
