@@ -239,3 +239,28 @@ def batch_mix(count: int = 96, meta_seed: int = 3):
         out.append(Tomo2D(f"batch-{i}", N=N, n_views=views, det=det, ell=ell, r=r, lam=lam,
                           seed=1000 + i))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Warm-start network: initial weights and the train / held-out seeds
+# ---------------------------------------------------------------------------
+STREAM_NET = 5
+WARM_TRAIN_SEEDS = range(10000, 12000)     # 2000 training phantoms
+WARM_TEST_SEEDS = range(20000, 20200)      # 200 held-out phantoms
+
+
+def unet_init(seed: int, layers):
+    """Initial float32 weights of the warm-start U-Net: He-normal (standard
+    deviation sqrt(2 / fan_in)), zero biases.  `layers` is a list of
+    (name, weight shape, kind) in the network's order; kind "tconv" has its
+    output channels second and fan_in = in_channels * 4."""
+    g = _gen(seed, STREAM_NET)
+    out = {}
+    for name, shape, kind in layers:
+        if kind == "tconv":
+            fan_in, nb = shape[0] * shape[2] * shape[3], shape[1]
+        else:
+            fan_in, nb = int(np.prod(shape[1:])), shape[0]
+        w = (g.standard_normal(shape) * math.sqrt(2.0 / fan_in)).astype(np.float32)
+        out[name] = (w, np.zeros(nb, dtype=np.float32))
+    return out
