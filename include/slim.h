@@ -289,6 +289,51 @@ slim_status slim_batch_sync(slim_batch* batch);
 slim_status slim_batch_set_stream(slim_batch* batch, void* cuda_stream);
 void slim_batch_destroy(slim_batch* batch);
 
+/* ---------------------------------------------------------------------------
+ * Learned initial guess (not in the paper, which starts from x_0 = 0, Sec. 4).
+ *
+ * A U-Net maps the scaled back-projection s_in A^T b (one N x N channel) to
+ * x_0 / s_out: three encoder levels of two 3x3 convolutions + ReLU (32, 64,
+ * 128 channels) each followed by 2x2 max-pooling, a 256-channel bottom of two
+ * 3x3 convolutions + ReLU, three decoder levels of a 2x2 stride-2 transposed
+ * convolution, concatenation [upsampled; encoder output of that level] and
+ * two 3x3 convolutions + ReLU (128, 64, 32 channels), then a 1x1 convolution
+ * to one channel (1,925,025 parameters).  The forward pass uses the float32
+ * master weights rounded to bfloat16 (biases unrounded), with float32
+ * activations and accumulation; training minimises the mean squared error
+ * with Adam (beta 0.9 / 0.999, eps 1e-8) on the float32 master copy.
+ *
+ * Parameters are one float32 array in layer order, each layer's weights then
+ * its bias: convolutions [out][in][3][3], transposed convolutions
+ * [in][out][2][2], the final [1][32].  Tensors passed to forward / train are
+ * device arrays of n images of H x W float32 (image-major).
+ * ------------------------------------------------------------------------- */
+typedef struct slim_unet slim_unet;
+slim_status slim_unet_param_count(long long* count);
+/* H, W multiples of 8; max_batch images per call.  Parameters start at zero. */
+slim_status slim_unet_create(int H, int W, int max_batch, slim_unet** out);
+void slim_unet_destroy(slim_unet* net);
+/* Host float32 parameters in; resets the Adam state. */
+slim_status slim_unet_set_params(slim_unet* net, const float* params, long long count);
+slim_status slim_unet_get_params(slim_unet* net, float* params, long long count);
+/* Gradients of the last slim_unet_train_step (host float32). */
+slim_status slim_unet_get_grads(slim_unet* net, float* grads, long long count);
+/* y = U-Net(x) for n images; asynchronous on `cuda_stream`. */
+slim_status slim_unet_forward(slim_unet* net, const float* x, float* y, int n, void* cuda_stream);
+/* One step: forward, loss = mean (y - target)^2, backward, Adam with rate lr.
+ * *loss (if not NULL) receives the loss; the call then synchronises. */
+slim_status slim_unet_train_step(slim_unet* net, const float* x, const float* target, int n,
+                                 float lr, double* loss, void* cuda_stream);
+/* Warm start of a 2D context: x_0 = s_out * U-Net(s_in * A^T b) with the
+ * context's data b (N x N network).  If ||A x_0 - b|| >= ||b|| the network's
+ * guess is worse than zero and x is set to 0 instead.  *used = 1 when x_0
+ * was kept; *ratio = ||A x_0 - b|| / ||b||.  Synchronises. */
+slim_status slim_warm_start(slim_ctx* ctx, slim_unet* net, double s_in, double s_out, int* used,
+                            double* ratio);
+/* Back-projection A^T b of the context's data into a device float32 array
+ * x[n] (the network's input before scaling).  Synchronises. */
+slim_status slim_backproject_data(slim_ctx* ctx, float* x);
+
 /* Largest order p accepted by slim_damped_solve_noalloc. */
 #define SLIM_NOALLOC_MAX_P 1024
 

@@ -10,6 +10,7 @@
 #include "slim_chol.cuh"
 #include "slim_kernels.cuh"
 #include "slim_lookahead.cuh"
+#include "slim_unet.cuh"
 #include "slim_rays.cuh"
 
 using namespace slim;
@@ -1230,6 +1231,150 @@ slim_status slim_get_memory(slim_ctx* c, int* ids, double* G, double* z) {
   if (z) CK(cudaMemcpy(z, c->d_z, (size_t)c->p * sizeof(double), cudaMemcpyDeviceToHost),
             "get_memory");
   return read_status(c);
+}
+
+}  // extern "C"
+
+namespace {
+// out[0] += sum (r_i - b_i)^2, out[1] += sum b_i^2
+template <typename T>
+__global__ void resid_norms_kernel(const T* r, const T* b, long long m, double* out) {
+  double e = 0.0, q = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double d = (double)r[i] - (double)b[i];
+    e += d * d;
+    q += (double)b[i] * (double)b[i];
+  }
+  e = warp_sum(e);
+  q = warp_sum(q);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out[0], e);
+    atomicAdd(&out[1], q);
+  }
+}
+
+// A^T b of the context's data into a device array of precision T (zeroed first).
+template <typename T>
+cudaError_t backproject_data_t(slim_ctx* c, T* x) {
+  cudaError_t e = cudaMemsetAsync(x, 0, (size_t)c->n * sizeof(T), c->stream);
+  if (e != cudaSuccess) return e;
+  if (c->a_mode)
+    return launch_csr_backproject<T>(c->csr, c->n, nullptr, (int)c->m, (const T*)c->d_b, x, c->stream);
+  return launch_backproject<T>(c->d_views, c->N, c->D, nullptr, (int)c->m, (const T*)c->d_b, x,
+                               c->stream);
+}
+
+template <typename T>
+slim_status warm_start_t(slim_ctx* c, slim_unet* net, double s_in, double s_out, int* used,
+                         double* ratio) {
+  const long long n = c->n, m = c->m;
+  T *atb = nullptr, *x0 = nullptr, *r = nullptr;
+  float *fin = nullptr, *fout = nullptr;
+  double* nrm = nullptr;
+  cudaStream_t s = c->stream;
+  slim_status st = SLIM_OK;
+  auto ck = [&](cudaError_t e, const char* w) {
+    if (e != cudaSuccess && st == SLIM_OK) st = cuda_fail(c, e, w);
+    return st == SLIM_OK;
+  };
+  const int grid = (int)std::min<long long>((n + 255) / 256, 4096);
+  if (ck(cudaMalloc(&atb, n * sizeof(T)), "warm start") && ck(cudaMalloc(&x0, n * sizeof(T)), "warm start") &&
+      ck(cudaMalloc(&r, m * sizeof(T)), "warm start") && ck(cudaMalloc(&fin, n * sizeof(float)), "warm start") &&
+      ck(cudaMalloc(&fout, n * sizeof(float)), "warm start") &&
+      ck(cudaMalloc(&nrm, 2 * sizeof(double)), "warm start") &&
+      ck(backproject_data_t<T>(c, atb), "back-projection")) {
+    if (sizeof(T) == 4) {
+      ck(unet_scale((const float*)atb, fin, n, (float)s_in, s), "scale");
+    } else {
+      convert_kernel<T, float><<<grid, 256, 0, s>>>(atb, fin, n);
+      ck(cudaGetLastError(), "convert");
+      ck(unet_scale(fin, fin, n, (float)s_in, s), "scale");
+    }
+    if (st == SLIM_OK && slim_unet_forward(net, fin, fout, 1, s) != SLIM_OK)
+      st = fail(c, SLIM_ECUDA, "warm start: network forward");
+    if (st == SLIM_OK) ck(unet_scale(fout, fout, n, (float)s_out, s), "scale");
+    if (st == SLIM_OK) {
+      if (sizeof(T) == 4) {
+        ck(cudaMemcpyAsync(x0, fout, n * sizeof(float), cudaMemcpyDeviceToDevice, s), "copy");
+      } else {
+        convert_kernel<float, T><<<grid, 256, 0, s>>>(fout, x0, n);
+        ck(cudaGetLastError(), "convert");
+      }
+    }
+    // residual of the guess against the data
+    if (st == SLIM_OK) {
+      if (c->a_mode)
+        ck(launch_csr_project<T>(c->csr, nullptr, (int)m, x0, r, s), "project");
+      else
+        ck(launch_project<T>(c->d_views, c->N, c->D, nullptr, (int)m, x0, r, s), "project");
+    }
+    double h[2] = {0.0, 0.0};
+    if (st == SLIM_OK && ck(cudaMemsetAsync(nrm, 0, 2 * sizeof(double), s), "norms")) {
+      resid_norms_kernel<T><<<(int)std::min<long long>((m + 255) / 256, 4096), 256, 0, s>>>(
+          r, (const T*)c->d_b, m, nrm);
+      ck(cudaGetLastError(), "norms");
+      ck(cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, s), "norms");
+      ck(cudaStreamSynchronize(s), "norms");
+    }
+    if (st == SLIM_OK) {
+      const double q = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
+      const bool keep = h[1] > 0 && q < 1.0;
+      if (ratio) *ratio = q;
+      if (used) *used = keep ? 1 : 0;
+      if (keep)
+        ck(cudaMemcpyAsync(c->d_x, x0, n * sizeof(T), cudaMemcpyDeviceToDevice, s), "set x");
+      else
+        ck(cudaMemsetAsync(c->d_x, 0, n * sizeof(T), s), "set x");
+      ck(cudaStreamSynchronize(s), "warm start");
+    }
+  }
+  cudaFree(atb);
+  cudaFree(x0);
+  cudaFree(r);
+  cudaFree(fin);
+  cudaFree(fout);
+  cudaFree(nrm);
+  return st;
+}
+}  // namespace
+
+extern "C" {
+
+slim_status slim_warm_start(slim_ctx* c, slim_unet* net, double s_in, double s_out, int* used,
+                            double* ratio) {
+  if (!c || !net || !(s_in > 0.0) || !(s_out > 0.0)) return fail(c, SLIM_EINVAL, "warm start: bad arguments");
+  if (c->dim != 2) return fail(c, SLIM_ENOTSUP, "warm start: 2D only");
+  if (unet_height(net) != c->N || unet_width(net) != c->N)
+    return fail(c, SLIM_EINVAL, "warm start: network size differs from the image");
+  if (!c->has_data) return fail(c, SLIM_ESTATE, "warm start before slim_set_data");
+  if (c->lookahead) CK(la_sync_all(c), "sync");
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  return c->precision == SLIM_PREC_FP32 ? warm_start_t<float>(c, net, s_in, s_out, used, ratio)
+                                        : warm_start_t<double>(c, net, s_in, s_out, used, ratio);
+}
+
+slim_status slim_backproject_data(slim_ctx* c, float* x) {
+  if (!c || !x) return SLIM_EINVAL;
+  if (c->dim != 2) return fail(c, SLIM_ENOTSUP, "back-projection of the data: 2D only");
+  if (!c->has_data) return fail(c, SLIM_ESTATE, "no data");
+  if (c->precision == SLIM_PREC_FP32) {
+    CK(backproject_data_t<float>(c, x), "back-projection");
+  } else {
+    double* tmp = nullptr;
+    CK(cudaMalloc(&tmp, (size_t)c->n * sizeof(double)), "back-projection");
+    cudaError_t e = backproject_data_t<double>(c, tmp);
+    if (e == cudaSuccess) {
+      const int grid = (int)std::min<long long>((c->n + 255) / 256, 4096);
+      convert_kernel<double, float><<<grid, 256, 0, c->stream>>>(tmp, x, c->n);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    CK(e, "back-projection");
+  }
+  CK(cudaStreamSynchronize(c->stream), "back-projection");
+  return SLIM_OK;
 }
 
 slim_status slim_get_csr(slim_ctx* c, long long* nnz, int* row_ptr, int* col, float* val) {

@@ -1,0 +1,716 @@
+// U-Net for the learned initial guess x_0 = f(A^T b): forward, backward and
+// Adam, all in hand-written kernels.  The paper starts from x_0 = 0 (Sec. 4);
+// the network is an extension of this library.
+//
+// Layout: activations are channel-major over the batch, C x (n*H*W) float32
+// ("CNHW"), so every layer is one GEMM:
+//   conv3x3    Y = W col(X) + b        col = im2col of X (K = 9 C_in rows)
+//              dW += dY col(X)^T,  dX = col2im(W^T dY)
+//   tconv2x2   Y4 = W^T X (rows (o,u,v)), scattered to the 2x upsampled grid
+//              dW += X dY4^T,  dX = W dY4   (dY4 gathered from dY)
+//   conv1x1    Y = W X + b
+// The decoder's concatenation [upsampled; skip] is one buffer whose lower
+// channel rows are written by the encoder directly.  Weights used by the
+// forward pass are the float32 master values rounded to bfloat16 (nearest
+// even); biases are used unrounded.  Accumulation is float32 throughout.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/slim.h"
+#include "slim_unet.cuh"
+
+namespace {
+
+constexpr int kT = 256;
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+inline int grid_for(long long n) { return (int)std::min<long long>(std::max<long long>(cdiv(n, kT), 1), 152LL * 32); }
+
+// ---------------------------------------------------------------------------
+// GEMM: C[m][n] (+)= sum_k op(A)[m][k] op(B)[k][n] (+ bias[m]) (ReLU)
+//   op(A)[m][k] = TA ? A[k*lda + m] : A[m*lda + k]
+//   op(B)[k][n] = TB ? B[n*ldb + k] : B[k*ldb + n]
+// BM x BN tile per CTA of 256 threads (4 x 4 outputs each), k in chunks of
+// 16 staged k-major in shared memory.  With gridDim.z > 1 the k range is
+// split and partial sums are added atomically into C (which holds the
+// accumulated value on entry).
+// ---------------------------------------------------------------------------
+constexpr int kBK = 16;
+
+template <bool TA, bool TB, int BM, int BN>
+__global__ void __launch_bounds__(kT) sgemm_kernel(int M, int N, int K, const float* __restrict__ A,
+                                                   int lda, const float* __restrict__ B, int ldb,
+                                                   float* C, int ldc, const float* __restrict__ bias,
+                                                   int relu, int accumulate, int kchunk) {
+  static_assert((BM / 4) * (BN / 4) == kT, "tile shape");
+  __shared__ __align__(16) float As[kBK][BM + 4];
+  __shared__ __align__(16) float Bs[kBK][BN + 4];
+  const int tid = threadIdx.x;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+  const int tm = tid / (BN / 4), tn = tid % (BN / 4);
+  float acc[4][4] = {};
+  for (int k0 = kbeg; k0 < kend; k0 += kBK) {
+    for (int idx = tid; idx < BM * kBK; idx += kT) {
+      int mm, kk;
+      if (TA) { mm = idx % BM; kk = idx / BM; } else { kk = idx % kBK; mm = idx / kBK; }
+      const int m = m0 + mm, k = k0 + kk;
+      float v = 0.f;
+      if (m < M && k < kend) v = TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
+      As[kk][mm] = v;
+    }
+    for (int idx = tid; idx < BN * kBK; idx += kT) {
+      int nn, kk;
+      if (TB) { kk = idx % kBK; nn = idx / kBK; } else { nn = idx % BN; kk = idx / BN; }
+      const int n = n0 + nn, k = k0 + kk;
+      float v = 0.f;
+      if (n < N && k < kend) v = TB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[kk][tm * 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tn * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+    }
+    __syncthreads();
+  }
+  const bool split = gridDim.z > 1;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + tm * 4 + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tn * 4 + j;
+      if (n >= N) continue;
+      float v = acc[i][j];
+      float* c = C + (size_t)m * ldc + n;
+      if (split) {
+        atomicAdd(c, v);
+      } else {
+        if (bias) v += bias[m];
+        if (accumulate) v += *c;
+        if (relu) v = fmaxf(v, 0.f);
+        *c = v;
+      }
+    }
+  }
+}
+
+template <bool TA, bool TB>
+cudaError_t gemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
+                 int ldc, const float* bias, bool relu, bool accumulate, int splits, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  splits = std::max(1, std::min(splits, cdiv(K, kBK)));
+  const int kchunk = cdiv(cdiv(K, splits), kBK) * kBK;
+  splits = cdiv(K, kchunk);
+  if (M <= 32) {
+    dim3 grid(cdiv(N, 128), cdiv(M, 32), splits);
+    sgemm_kernel<TA, TB, 32, 128><<<grid, kT, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias,
+                                                       relu, accumulate, kchunk);
+  } else {
+    dim3 grid(cdiv(N, 64), cdiv(M, 64), splits);
+    sgemm_kernel<TA, TB, 64, 64><<<grid, kT, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu,
+                                                     accumulate, kchunk);
+  }
+  return cudaGetLastError();
+}
+
+// Split-K factor for the weight gradients (long reductions over pixels).
+int wgrad_splits(int M, int N, int K) {
+  const long long tiles = (long long)cdiv(M, 64) * cdiv(N, 64);
+  const long long want = std::max<long long>(1, 152 * 4 / std::max<long long>(tiles, 1));
+  return (int)std::min<long long>(want, std::max(1, K / 1024));
+}
+
+// ---------------------------------------------------------------------------
+// Layout kernels
+// ---------------------------------------------------------------------------
+// col[(c*9 + u*3 + v) * P + p] = X[c][img, y+u-1, x+v-1] (zero outside)
+__global__ void im2col_kernel(const float* __restrict__ X, int C, int n, int H, int W, float* col) {
+  const long long P = (long long)n * H * W, total = 9LL * C * P;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long k = idx / P, p = idx % P;
+    const int c = (int)(k / 9), t = (int)(k % 9), u = t / 3, v = t % 3;
+    const int img = (int)(p / ((long long)H * W));
+    const int rem = (int)(p % ((long long)H * W));
+    const int y = rem / W + u - 1, x = rem % W + v - 1;
+    col[idx] = (y >= 0 && y < H && x >= 0 && x < W)
+                   ? X[(size_t)c * P + ((size_t)img * H + y) * W + x] : 0.f;
+  }
+}
+
+// dX[c][img, y, x] = sum_{u,v} dcol[(c*9+u*3+v)][img, y-u+1, x-v+1]
+__global__ void col2im_kernel(const float* __restrict__ dcol, int C, int n, int H, int W,
+                              float* dX) {
+  const long long P = (long long)n * H * W, total = (long long)C * P;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / P);
+    const long long p = idx % P;
+    const int img = (int)(p / ((long long)H * W));
+    const int rem = (int)(p % ((long long)H * W));
+    const int y = rem / W, x = rem % W;
+    float s = 0.f;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int yy = y - u + 1;
+      if (yy < 0 || yy >= H) continue;
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const int xx = x - v + 1;
+        if (xx < 0 || xx >= W) continue;
+        s += dcol[(size_t)(c * 9 + u * 3 + v) * P + ((size_t)img * H + yy) * W + xx];
+      }
+    }
+    dX[idx] = s;
+  }
+}
+
+// 2x2 max-pool: first maximum in row-major window order (arg in 0..3).
+__global__ void maxpool_kernel(const float* __restrict__ X, int C, int n, int H, int W, float* Y,
+                               unsigned char* arg) {
+  const int H2 = H / 2, W2 = W / 2;
+  const long long Q = (long long)n * H2 * W2, total = (long long)C * Q;
+  const long long P = (long long)n * H * W;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / Q);
+    const long long q = idx % Q;
+    const int img = (int)(q / ((long long)H2 * W2));
+    const int rem = (int)(q % ((long long)H2 * W2));
+    const int y = 2 * (rem / W2), x = 2 * (rem % W2);
+    const float* base = X + (size_t)c * P + ((size_t)img * H + y) * W + x;
+    const float v[4] = {base[0], base[1], base[W], base[W + 1]};
+    int a = 0;
+    for (int t = 1; t < 4; ++t)
+      if (v[t] > v[a]) a = t;
+    Y[idx] = v[a];
+    arg[idx] = (unsigned char)a;
+  }
+}
+
+// dX (holding the skip gradient) += the pooled gradient routed to its argmax.
+__global__ void maxpool_bwd_kernel(const float* __restrict__ dY, const unsigned char* arg, int C,
+                                   int n, int H, int W, float* dX) {
+  const int H2 = H / 2, W2 = W / 2;
+  const long long Q = (long long)n * H2 * W2, total = (long long)C * Q;
+  const long long P = (long long)n * H * W;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / Q);
+    const long long q = idx % Q;
+    const int img = (int)(q / ((long long)H2 * W2));
+    const int rem = (int)(q % ((long long)H2 * W2));
+    const int a = arg[idx];
+    const int y = 2 * (rem / W2) + a / 2, x = 2 * (rem % W2) + a % 2;
+    dX[(size_t)c * P + ((size_t)img * H + y) * W + x] += dY[idx];
+  }
+}
+
+// Y[o][img, 2y+u, 2x+v] = Y4[(o*4 + u*2 + v)][img, y, x] + b[o]
+__global__ void tconv_scatter_kernel(const float* __restrict__ Y4, const float* __restrict__ b,
+                                     int O, int n, int H, int W, float* Y) {
+  const long long Pin = (long long)n * H * W, total = 4LL * O * Pin;
+  const long long Pout = 4 * Pin;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / Pin);
+    const long long p = idx % Pin;
+    const int o = r / 4, u = (r % 4) / 2, v = r % 2;
+    const int img = (int)(p / ((long long)H * W));
+    const int rem = (int)(p % ((long long)H * W));
+    const int y = 2 * (rem / W) + u, x = 2 * (rem % W) + v;
+    Y[(size_t)o * Pout + ((size_t)img * 2 * H + y) * (2 * W) + x] = Y4[idx] + b[o];
+  }
+}
+
+__global__ void tconv_gather_kernel(const float* __restrict__ dY, int O, int n, int H, int W,
+                                    float* dY4) {
+  const long long Pin = (long long)n * H * W, total = 4LL * O * Pin;
+  const long long Pout = 4 * Pin;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / Pin);
+    const long long p = idx % Pin;
+    const int o = r / 4, u = (r % 4) / 2, v = r % 2;
+    const int img = (int)(p / ((long long)H * W));
+    const int rem = (int)(p % ((long long)H * W));
+    const int y = 2 * (rem / W) + u, x = 2 * (rem % W) + v;
+    dY4[idx] = dY[(size_t)o * Pout + ((size_t)img * 2 * H + y) * (2 * W) + x];
+  }
+}
+
+// db[c] += sum_p dY[c][p]   (one CTA per channel)
+__global__ void rowsum_kernel(const float* __restrict__ dY, long long P, float* db) {
+  const int c = blockIdx.x;
+  float s = 0.f;
+  for (long long p = threadIdx.x; p < P; p += blockDim.x) s += dY[(size_t)c * P + p];
+  __shared__ float red[kT];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) db[c] += red[0];
+}
+
+__global__ void relu_mask_kernel(float* d, const float* __restrict__ y, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    if (!(y[i] > 0.f)) d[i] = 0.f;
+}
+
+// grad = 2 (y - t) / count;  loss += sum (y - t)^2
+__global__ void mse_kernel(const float* __restrict__ y, const float* __restrict__ t, long long count,
+                           float* grad, double* loss) {
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float d = y[i] - t[i];
+    grad[i] = 2.f * d / (float)count;
+    s += (double)d * d;
+  }
+  __shared__ double red[kT];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(loss, red[0]);
+}
+
+// Adam (Kingma and Ba, 2015) on the float32 master copy; refreshes the
+// forward copy (bfloat16-rounded weights, unrounded biases).
+__global__ void adam_kernel(float* master, float* eff, const float* __restrict__ g, float* m,
+                            float* v, const unsigned char* __restrict__ is_w, long long count,
+                            float lr, float b1, float b2, float eps, float c1, float c2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float p = master[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    master[i] = p;
+    eff[i] = is_w[i] ? __bfloat162float(__float2bfloat16_rn(p)) : p;
+  }
+}
+
+__global__ void refresh_eff_kernel(const float* __restrict__ master, float* eff,
+                                   const unsigned char* __restrict__ is_w, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    eff[i] = is_w[i] ? __bfloat162float(__float2bfloat16_rn(master[i])) : master[i];
+}
+
+__global__ void scale_copy_kernel(const float* __restrict__ in, float* out, long long count,
+                                  float s) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = s * in[i];
+}
+
+// ---------------------------------------------------------------------------
+// The network
+// ---------------------------------------------------------------------------
+enum Kind { kConv = 0, kTconv = 1, kConv1 = 2 };
+struct LayerSpec {
+  const char* name;
+  int o, i, kind;   // conv: o x i x 3 x 3; tconv: i x o x 2 x 2 (in, out); conv1: o x i
+};
+// in the order of the oracle's parameter list
+const LayerSpec kLayers[] = {
+    {"enc1a", 32, 1, kConv},    {"enc1b", 32, 32, kConv},   {"enc2a", 64, 32, kConv},
+    {"enc2b", 64, 64, kConv},   {"enc3a", 128, 64, kConv},  {"enc3b", 128, 128, kConv},
+    {"bota", 256, 128, kConv},  {"botb", 256, 256, kConv},  {"up3", 128, 256, kTconv},
+    {"dec3a", 128, 256, kConv}, {"dec3b", 128, 128, kConv}, {"up2", 64, 128, kTconv},
+    {"dec2a", 64, 128, kConv},  {"dec2b", 64, 64, kConv},   {"up1", 32, 64, kTconv},
+    {"dec1a", 32, 64, kConv},   {"dec1b", 32, 32, kConv},   {"out", 1, 32, kConv1},
+};
+constexpr int kNumLayers = sizeof(kLayers) / sizeof(kLayers[0]);
+enum {
+  L_ENC1A, L_ENC1B, L_ENC2A, L_ENC2B, L_ENC3A, L_ENC3B, L_BOTA, L_BOTB, L_UP3, L_DEC3A, L_DEC3B,
+  L_UP2, L_DEC2A, L_DEC2B, L_UP1, L_DEC1A, L_DEC1B, L_OUT
+};
+
+long long weight_count(const LayerSpec& l) {
+  return l.kind == kConv ? 9LL * l.o * l.i : l.kind == kTconv ? 4LL * l.o * l.i : (long long)l.o * l.i;
+}
+
+}  // namespace
+
+struct slim_unet {
+  int H = 0, W = 0, max_n = 0;
+  long long nparams = 0;
+  long long woff[kNumLayers] = {}, boff[kNumLayers] = {};
+  float *master = nullptr, *eff = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+  unsigned char* is_w = nullptr;
+  long long t = 0;
+  // activations (channel-major over the batch) and their gradients
+  float *x = nullptr, *a1 = nullptr, *c1 = nullptr, *p1 = nullptr, *a2 = nullptr, *c2 = nullptr,
+        *p2 = nullptr, *a3 = nullptr, *c3 = nullptr, *p3 = nullptr, *ab = nullptr, *bt = nullptr,
+        *d3a = nullptr, *d3 = nullptr, *d2a = nullptr, *d2 = nullptr, *d1a = nullptr,
+        *d1 = nullptr, *y = nullptr;
+  float *ga1 = nullptr, *gc1 = nullptr, *gp1 = nullptr, *ga2 = nullptr, *gc2 = nullptr,
+        *gp2 = nullptr, *ga3 = nullptr, *gc3 = nullptr, *gp3 = nullptr, *gab = nullptr,
+        *gbt = nullptr, *gd3a = nullptr, *gd3 = nullptr, *gd2a = nullptr, *gd2 = nullptr,
+        *gd1a = nullptr, *gd1 = nullptr, *gy = nullptr;
+  unsigned char *arg1 = nullptr, *arg2 = nullptr, *arg3 = nullptr;
+  float *col = nullptr, *dcol = nullptr, *y4 = nullptr;
+  double* loss = nullptr;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+struct Net {
+  slim_unet* u;
+  int n;
+  cudaStream_t s;
+  long long P(int level) const {   // pixels at level 1..4
+    return (long long)n * (u->H >> (level - 1)) * (u->W >> (level - 1));
+  }
+  int h(int level) const { return u->H >> (level - 1); }
+  int w(int level) const { return u->W >> (level - 1); }
+  const float* W_(int l) const { return u->eff + u->woff[l]; }
+  const float* B_(int l) const { return u->eff + u->boff[l]; }
+  float* gW(int l) const { return u->grad + u->woff[l]; }
+  float* gB(int l) const { return u->grad + u->boff[l]; }
+
+  cudaError_t conv(int l, const float* X, int level, float* Y, bool relu) const {
+    const LayerSpec& L = kLayers[l];
+    const long long P_ = P(level);
+    im2col_kernel<<<grid_for(9LL * L.i * P_), kT, 0, s>>>(X, L.i, n, h(level), w(level), u->col);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return gemm<false, false>(L.o, (int)P_, 9 * L.i, W_(l), 9 * L.i, u->col, (int)P_, Y, (int)P_,
+                              B_(l), relu, false, 1, s);
+  }
+  // dY holds the gradient at the ReLU output; on return dX (if any) holds the
+  // gradient at the layer input.
+  cudaError_t conv_back(int l, const float* X, int level, const float* Yout, float* dY, float* dX) const {
+    const LayerSpec& L = kLayers[l];
+    const long long P_ = P(level);
+    const int K9 = 9 * L.i;
+    relu_mask_kernel<<<grid_for((long long)L.o * P_), kT, 0, s>>>(dY, Yout, (long long)L.o * P_);
+    im2col_kernel<<<grid_for((long long)K9 * P_), kT, 0, s>>>(X, L.i, n, h(level), w(level), u->col);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = gemm<false, true>(L.o, K9, (int)P_, dY, (int)P_, u->col, (int)P_, gW(l), K9, nullptr, false,
+                          true, wgrad_splits(L.o, K9, (int)P_), s);
+    if (e != cudaSuccess) return e;
+    rowsum_kernel<<<L.o, kT, 0, s>>>(dY, P_, gB(l));
+    if (!dX) return cudaGetLastError();
+    e = gemm<true, false>(K9, (int)P_, L.o, W_(l), K9, dY, (int)P_, u->dcol, (int)P_, nullptr, false,
+                          false, 1, s);
+    if (e != cudaSuccess) return e;
+    col2im_kernel<<<grid_for((long long)L.i * P_), kT, 0, s>>>(u->dcol, L.i, n, h(level), w(level), dX);
+    return cudaGetLastError();
+  }
+  // transposed conv from level `lin` (input) to lin-1
+  cudaError_t tconv(int l, const float* X, int lin, float* Y) const {
+    const LayerSpec& L = kLayers[l];
+    const long long Pin = P(lin);
+    cudaError_t e = gemm<true, false>(4 * L.o, (int)Pin, L.i, W_(l), 4 * L.o, X, (int)Pin, u->y4,
+                                      (int)Pin, nullptr, false, false, 1, s);
+    if (e != cudaSuccess) return e;
+    tconv_scatter_kernel<<<grid_for(4LL * L.o * Pin), kT, 0, s>>>(u->y4, B_(l), L.o, n, h(lin), w(lin), Y);
+    return cudaGetLastError();
+  }
+  cudaError_t tconv_back(int l, const float* X, int lin, const float* dY, float* dX) const {
+    const LayerSpec& L = kLayers[l];
+    const long long Pin = P(lin);
+    tconv_gather_kernel<<<grid_for(4LL * L.o * Pin), kT, 0, s>>>(dY, L.o, n, h(lin), w(lin), u->y4);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = gemm<false, true>(L.i, 4 * L.o, (int)Pin, X, (int)Pin, u->y4, (int)Pin, gW(l), 4 * L.o,
+                          nullptr, false, true, wgrad_splits(L.i, 4 * L.o, (int)Pin), s);
+    if (e != cudaSuccess) return e;
+    rowsum_kernel<<<L.o, kT, 0, s>>>(dY, 4 * Pin, gB(l));
+    return gemm<false, false>(L.i, (int)Pin, 4 * L.o, W_(l), 4 * L.o, u->y4, (int)Pin, dX, (int)Pin,
+                              nullptr, false, false, 1, s);
+  }
+  cudaError_t pool(const float* X, int level, float* Y, unsigned char* arg, int C) const {
+    maxpool_kernel<<<grid_for((long long)C * P(level + 1)), kT, 0, s>>>(X, C, n, h(level), w(level), Y, arg);
+    return cudaGetLastError();
+  }
+  cudaError_t pool_back(const float* dY, const unsigned char* arg, int level, float* dX, int C) const {
+    maxpool_bwd_kernel<<<grid_for((long long)C * P(level + 1)), kT, 0, s>>>(dY, arg, C, n, h(level),
+                                                                           w(level), dX);
+    return cudaGetLastError();
+  }
+
+  cudaError_t forward() const {
+    slim_unet& U = *u;
+    cudaError_t e;
+#define CKE(x) if ((e = (x)) != cudaSuccess) return e
+    // the encoder output of each level goes to the lower rows of its concat buffer
+    float* e1 = U.c1 + 32 * P(1);
+    float* e2 = U.c2 + 64 * P(2);
+    float* e3 = U.c3 + 128 * P(3);
+    CKE(conv(L_ENC1A, U.x, 1, U.a1, true));
+    CKE(conv(L_ENC1B, U.a1, 1, e1, true));
+    CKE(pool(e1, 1, U.p1, U.arg1, 32));
+    CKE(conv(L_ENC2A, U.p1, 2, U.a2, true));
+    CKE(conv(L_ENC2B, U.a2, 2, e2, true));
+    CKE(pool(e2, 2, U.p2, U.arg2, 64));
+    CKE(conv(L_ENC3A, U.p2, 3, U.a3, true));
+    CKE(conv(L_ENC3B, U.a3, 3, e3, true));
+    CKE(pool(e3, 3, U.p3, U.arg3, 128));
+    CKE(conv(L_BOTA, U.p3, 4, U.ab, true));
+    CKE(conv(L_BOTB, U.ab, 4, U.bt, true));
+    CKE(tconv(L_UP3, U.bt, 4, U.c3));
+    CKE(conv(L_DEC3A, U.c3, 3, U.d3a, true));
+    CKE(conv(L_DEC3B, U.d3a, 3, U.d3, true));
+    CKE(tconv(L_UP2, U.d3, 3, U.c2));
+    CKE(conv(L_DEC2A, U.c2, 2, U.d2a, true));
+    CKE(conv(L_DEC2B, U.d2a, 2, U.d2, true));
+    CKE(tconv(L_UP1, U.d2, 2, U.c1));
+    CKE(conv(L_DEC1A, U.c1, 1, U.d1a, true));
+    CKE(conv(L_DEC1B, U.d1a, 1, U.d1, true));
+    return gemm<false, false>(1, (int)P(1), 32, W_(L_OUT), 32, U.d1, (int)P(1), U.y, (int)P(1),
+                              B_(L_OUT), false, false, 1, s);
+  }
+
+  // Gradients of the loss whose gradient at y is in gy (grad buffer zeroed first).
+  cudaError_t backward() const {
+    slim_unet& U = *u;
+    cudaError_t e;
+    float* e1 = U.c1 + 32 * P(1);
+    float* e2 = U.c2 + 64 * P(2);
+    float* e3 = U.c3 + 128 * P(3);
+    float* ge1 = U.gc1 + 32 * P(1);
+    float* ge2 = U.gc2 + 64 * P(2);
+    float* ge3 = U.gc3 + 128 * P(3);
+    const int P1 = (int)P(1);
+    // output 1x1 conv
+    CKE((gemm<false, true>(1, 32, P1, U.gy, P1, U.d1, P1, gW(L_OUT), 32, nullptr, false, true,
+                           wgrad_splits(1, 32, P1), s)));
+    rowsum_kernel<<<1, kT, 0, s>>>(U.gy, P(1), gB(L_OUT));
+    CKE((gemm<true, false>(32, P1, 1, W_(L_OUT), 32, U.gy, P1, U.gd1, P1, nullptr, false, false, 1, s)));
+    // level 1 decoder
+    CKE(conv_back(L_DEC1B, U.d1a, 1, U.d1, U.gd1, U.gd1a));
+    CKE(conv_back(L_DEC1A, U.c1, 1, U.d1a, U.gd1a, U.gc1));
+    CKE(tconv_back(L_UP1, U.d2, 2, U.gc1, U.gd2));
+    CKE(conv_back(L_DEC2B, U.d2a, 2, U.d2, U.gd2, U.gd2a));
+    CKE(conv_back(L_DEC2A, U.c2, 2, U.d2a, U.gd2a, U.gc2));
+    CKE(tconv_back(L_UP2, U.d3, 3, U.gc2, U.gd3));
+    CKE(conv_back(L_DEC3B, U.d3a, 3, U.d3, U.gd3, U.gd3a));
+    CKE(conv_back(L_DEC3A, U.c3, 3, U.d3a, U.gd3a, U.gc3));
+    CKE(tconv_back(L_UP3, U.bt, 4, U.gc3, U.gbt));
+    CKE(conv_back(L_BOTB, U.ab, 4, U.bt, U.gbt, U.gab));
+    CKE(conv_back(L_BOTA, U.p3, 4, U.ab, U.gab, U.gp3));
+    // encoder: skip gradient (already in the concat gradient) + pooled gradient
+    CKE(pool_back(U.gp3, U.arg3, 3, ge3, 128));
+    CKE(conv_back(L_ENC3B, U.a3, 3, e3, ge3, U.ga3));
+    CKE(conv_back(L_ENC3A, U.p2, 3, U.a3, U.ga3, U.gp2));
+    CKE(pool_back(U.gp2, U.arg2, 2, ge2, 64));
+    CKE(conv_back(L_ENC2B, U.a2, 2, e2, ge2, U.ga2));
+    CKE(conv_back(L_ENC2A, U.p1, 2, U.a2, U.ga2, U.gp1));
+    CKE(pool_back(U.gp1, U.arg1, 1, ge1, 32));
+    CKE(conv_back(L_ENC1B, U.a1, 1, e1, ge1, U.ga1));
+    CKE(conv_back(L_ENC1A, U.x, 1, U.a1, U.ga1, nullptr));
+#undef CKE
+    return cudaSuccess;
+  }
+};
+
+void unet_free(slim_unet* u) {
+  for (void* p : u->allocs) cudaFree(p);
+  u->allocs.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+slim_status slim_unet_param_count(long long* count) {
+  if (!count) return SLIM_EINVAL;
+  long long c = 0;
+  for (const LayerSpec& l : kLayers) c += weight_count(l) + (l.kind == kTconv ? l.o : l.o);
+  *count = c;
+  return SLIM_OK;
+}
+
+slim_status slim_unet_create(int H, int W, int max_batch, slim_unet** out) {
+  if (!out) return SLIM_EINVAL;
+  *out = nullptr;
+  if (H < 8 || W < 8 || H % 8 || W % 8 || max_batch < 1 || (long long)H * W * max_batch > (1LL << 24))
+    return SLIM_EINVAL;
+  slim_unet* u = new (std::nothrow) slim_unet();
+  if (!u) return SLIM_ENOMEM;
+  u->H = H;
+  u->W = W;
+  u->max_n = max_batch;
+  long long off = 0;
+  for (int l = 0; l < kNumLayers; ++l) {
+    u->woff[l] = off;
+    off += weight_count(kLayers[l]);
+    u->boff[l] = off;
+    off += kLayers[l].o;
+  }
+  u->nparams = off;
+  const long long P1 = (long long)max_batch * H * W, P2 = P1 / 4, P3 = P1 / 16, P4 = P1 / 64;
+  bool ok = true;
+  auto fa = [&](float** p, long long count) {
+    if (!ok) return;
+    void* q = nullptr;
+    if (cudaMalloc(&q, (size_t)count * sizeof(float)) != cudaSuccess) { ok = false; return; }
+    u->allocs.push_back(q);
+    *p = (float*)q;
+  };
+  auto ba = [&](unsigned char** p, long long count) {
+    if (!ok) return;
+    void* q = nullptr;
+    if (cudaMalloc(&q, (size_t)count) != cudaSuccess) { ok = false; return; }
+    u->allocs.push_back(q);
+    *p = (unsigned char*)q;
+  };
+  fa(&u->master, off); fa(&u->eff, off); fa(&u->grad, off); fa(&u->m, off); fa(&u->v, off);
+  ba(&u->is_w, off);
+  fa(&u->x, P1); fa(&u->a1, 32 * P1); fa(&u->c1, 64 * P1); fa(&u->p1, 32 * P2);
+  fa(&u->a2, 64 * P2); fa(&u->c2, 128 * P2); fa(&u->p2, 64 * P3); fa(&u->a3, 128 * P3);
+  fa(&u->c3, 256 * P3); fa(&u->p3, 128 * P4); fa(&u->ab, 256 * P4); fa(&u->bt, 256 * P4);
+  fa(&u->d3a, 128 * P3); fa(&u->d3, 128 * P3); fa(&u->d2a, 64 * P2); fa(&u->d2, 64 * P2);
+  fa(&u->d1a, 32 * P1); fa(&u->d1, 32 * P1); fa(&u->y, P1);
+  fa(&u->ga1, 32 * P1); fa(&u->gc1, 64 * P1); fa(&u->gp1, 32 * P2); fa(&u->ga2, 64 * P2);
+  fa(&u->gc2, 128 * P2); fa(&u->gp2, 64 * P3); fa(&u->ga3, 128 * P3); fa(&u->gc3, 256 * P3);
+  fa(&u->gp3, 128 * P4); fa(&u->gab, 256 * P4); fa(&u->gbt, 256 * P4); fa(&u->gd3a, 128 * P3);
+  fa(&u->gd3, 128 * P3); fa(&u->gd2a, 64 * P2); fa(&u->gd2, 64 * P2); fa(&u->gd1a, 32 * P1);
+  fa(&u->gd1, 32 * P1); fa(&u->gy, P1);
+  ba(&u->arg1, 32 * P2); ba(&u->arg2, 64 * P3); ba(&u->arg3, 128 * P4);
+  // im2col buffers: the largest 9 C_in x P is dec1a's (64 channels at level 1;
+  // level 2 at most 128 channels on P1/4, level 3 256 on P1/16)
+  const long long colmax = std::max({9LL * 64 * P1, 9LL * 128 * P2, 9LL * 256 * P3, 9LL * 256 * P4});
+  fa(&u->col, colmax); fa(&u->dcol, colmax);
+  fa(&u->y4, 4LL * 128 * P4 * 4);   // largest 4*o*Pin: up3 512 x P4, up2 256 x P3, up1 128 x P2
+  {
+    long long y4 = std::max({4LL * 128 * P4, 4LL * 64 * P3, 4LL * 32 * P2});
+    if (ok && y4 > 4LL * 128 * P4 * 4) ok = false;
+  }
+  if (ok) {
+    void* q = nullptr;
+    ok = cudaMalloc(&q, sizeof(double)) == cudaSuccess;
+    if (ok) { u->allocs.push_back(q); u->loss = (double*)q; }
+  }
+  if (ok) {
+    std::vector<unsigned char> isw((size_t)off, 0);
+    for (int l = 0; l < kNumLayers; ++l)
+      std::fill(isw.begin() + u->woff[l], isw.begin() + u->boff[l], 1);
+    ok = cudaMemcpy(u->is_w, isw.data(), isw.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(u->master, 0, off * sizeof(float)) == cudaSuccess &&
+         cudaMemset(u->eff, 0, off * sizeof(float)) == cudaSuccess &&
+         cudaMemset(u->m, 0, off * sizeof(float)) == cudaSuccess &&
+         cudaMemset(u->v, 0, off * sizeof(float)) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    unet_free(u);
+    delete u;
+    return SLIM_ENOMEM;
+  }
+  *out = u;
+  return SLIM_OK;
+}
+
+void slim_unet_destroy(slim_unet* u) {
+  if (!u) return;
+  cudaDeviceSynchronize();
+  unet_free(u);
+  delete u;
+}
+
+slim_status slim_unet_set_params(slim_unet* u, const float* params, long long count) {
+  if (!u || !params || count != u->nparams) return SLIM_EINVAL;
+  if (cudaMemcpy(u->master, params, count * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(u->m, 0, count * sizeof(float)) != cudaSuccess ||
+      cudaMemset(u->v, 0, count * sizeof(float)) != cudaSuccess)
+    return SLIM_ECUDA;
+  refresh_eff_kernel<<<grid_for(count), kT>>>(u->master, u->eff, u->is_w, count);
+  u->t = 0;
+  return cudaDeviceSynchronize() == cudaSuccess ? SLIM_OK : SLIM_ECUDA;
+}
+
+slim_status slim_unet_get_params(slim_unet* u, float* params, long long count) {
+  if (!u || !params || count != u->nparams) return SLIM_EINVAL;
+  return cudaMemcpy(params, u->master, count * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess
+             ? SLIM_OK : SLIM_ECUDA;
+}
+
+slim_status slim_unet_get_grads(slim_unet* u, float* grads, long long count) {
+  if (!u || !grads || count != u->nparams) return SLIM_EINVAL;
+  return cudaMemcpy(grads, u->grad, count * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess
+             ? SLIM_OK : SLIM_ECUDA;
+}
+
+slim_status slim_unet_forward(slim_unet* u, const float* x, float* y, int n, void* stream) {
+  if (!u || !x || !y || n < 1 || n > u->max_n) return SLIM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long P1 = (long long)n * u->H * u->W;
+  Net net{u, n, s};
+  if (cudaMemcpyAsync(u->x, x, P1 * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return SLIM_ECUDA;
+  if (net.forward() != cudaSuccess) return SLIM_ECUDA;
+  if (cudaMemcpyAsync(y, u->y, P1 * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return SLIM_ECUDA;
+  return SLIM_OK;
+}
+
+slim_status slim_unet_train_step(slim_unet* u, const float* x, const float* target, int n, float lr,
+                                 double* loss, void* stream) {
+  if (!u || !x || !target || n < 1 || n > u->max_n || !(lr >= 0.f)) return SLIM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long P1 = (long long)n * u->H * u->W;
+  Net net{u, n, s};
+  if (cudaMemcpyAsync(u->x, x, P1 * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(u->grad, 0, u->nparams * sizeof(float), s) != cudaSuccess ||
+      cudaMemsetAsync(u->loss, 0, sizeof(double), s) != cudaSuccess)
+    return SLIM_ECUDA;
+  if (net.forward() != cudaSuccess) return SLIM_ECUDA;
+  mse_kernel<<<grid_for(P1), kT, 0, s>>>(u->y, target, P1, u->gy, u->loss);
+  if (cudaGetLastError() != cudaSuccess || net.backward() != cudaSuccess) return SLIM_ECUDA;
+  u->t += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - (float)std::pow(0.9, (double)u->t);
+  const float c2 = 1.f - (float)std::pow(0.999, (double)u->t);
+  adam_kernel<<<grid_for(u->nparams), kT, 0, s>>>(u->master, u->eff, u->grad, u->m, u->v, u->is_w,
+                                                  u->nparams, lr, b1, b2, 1e-8f, c1, c2);
+  if (cudaGetLastError() != cudaSuccess) return SLIM_ECUDA;
+  if (loss) {
+    double h = 0.0;
+    if (cudaMemcpyAsync(&h, u->loss, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return SLIM_ECUDA;
+    *loss = h / (double)P1;
+  }
+  return SLIM_OK;
+}
+
+}  // extern "C"
+
+namespace slim {
+int unet_height(const slim_unet* net) { return net->H; }
+int unet_width(const slim_unet* net) { return net->W; }
+
+// out = s * in (the warm start's input and output scaling).
+cudaError_t unet_scale(const float* in, float* out, long long count, float s, cudaStream_t st) {
+  scale_copy_kernel<<<grid_for(count), kT, 0, st>>>(in, out, count, s);
+  return cudaGetLastError();
+}
+}  // namespace slim

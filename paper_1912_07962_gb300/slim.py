@@ -33,6 +33,9 @@ EXPORTS = [
     "slim_set_timing", "slim_get_timing", "slim_damped_solve_noalloc", "slim_get_csr",
     "slim_autotune", "slim_batch_create", "slim_batch_ctx", "slim_batch_step", "slim_batch_sync",
     "slim_batch_set_stream", "slim_batch_destroy", "slim_get_launch_log",
+    "slim_unet_param_count", "slim_unet_create", "slim_unet_destroy", "slim_unet_set_params",
+    "slim_unet_get_params", "slim_unet_get_grads", "slim_unet_forward", "slim_unet_train_step",
+    "slim_warm_start", "slim_backproject_data",
 ]
 A_MATRIX_FREE, A_CSR_F32, A_CSR_BF16 = 0, 1, 2
 NOALLOC_MAX_P = 1024
@@ -110,6 +113,16 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "slim_batch_set_stream": ([VP, VP], I),
         "slim_batch_destroy": ([VP], None),
         "slim_get_launch_log": ([VP, P(D), P(D), P(LL)], I),
+        "slim_unet_param_count": ([P(LL)], I),
+        "slim_unet_create": ([I, I, I, P(VP)], I),
+        "slim_unet_destroy": ([VP], None),
+        "slim_unet_set_params": ([VP, VP, LL], I),
+        "slim_unet_get_params": ([VP, VP, LL], I),
+        "slim_unet_get_grads": ([VP, VP, LL], I),
+        "slim_unet_forward": ([VP, VP, VP, I, VP], I),
+        "slim_unet_train_step": ([VP, VP, VP, I, C.c_float, P(D), VP], I),
+        "slim_warm_start": ([VP, VP, D, D, P(I), P(D)], I),
+        "slim_backproject_data": ([VP, VP], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -234,6 +247,19 @@ class Slim:
         k = C.c_int()
         self._check(self._lib.slim_get_timing(self.h, ms, len(PHASES), C.byref(k)))
         return dict(zip(PHASES, list(ms))), k.value
+
+    def backproject_data(self, out):
+        """A^T b of the context's data into a float32 device tensor of n entries."""
+        self._check(self._lib.slim_backproject_data(self.h, C.c_void_p(out.data_ptr())))
+        return out
+
+    def warm_start(self, net, s_in, s_out):
+        """x_0 = s_out * net(s_in * A^T b), or 0 when its residual is not below ||b||.
+        Returns (used, ||A x_0 - b|| / ||b||)."""
+        used, ratio = C.c_int(), C.c_double()
+        self._check(self._lib.slim_warm_start(self.h, net.h, s_in, s_out, C.byref(used),
+                                              C.byref(ratio)))
+        return bool(used.value), ratio.value
 
     def launch_log(self):
         """(mean factorisation ms, mean iterate-chain ms, iterate chains) since the
@@ -400,3 +426,103 @@ class SlimBatch:
             self.close()
         except Exception:
             pass
+
+
+# Layers of the warm-start network in the C ABI's parameter order:
+# (name, weight shape, kind); convolution weights [out][in][3][3], transposed
+# convolutions [in][out][2][2], the final 1x1 [1][32]; each bias follows its weights.
+UNET_LAYERS = [
+    ("enc1a", (32, 1, 3, 3), "conv"), ("enc1b", (32, 32, 3, 3), "conv"),
+    ("enc2a", (64, 32, 3, 3), "conv"), ("enc2b", (64, 64, 3, 3), "conv"),
+    ("enc3a", (128, 64, 3, 3), "conv"), ("enc3b", (128, 128, 3, 3), "conv"),
+    ("bota", (256, 128, 3, 3), "conv"), ("botb", (256, 256, 3, 3), "conv"),
+    ("up3", (256, 128, 2, 2), "tconv"),
+    ("dec3a", (128, 256, 3, 3), "conv"), ("dec3b", (128, 128, 3, 3), "conv"),
+    ("up2", (128, 64, 2, 2), "tconv"),
+    ("dec2a", (64, 128, 3, 3), "conv"), ("dec2b", (64, 64, 3, 3), "conv"),
+    ("up1", (64, 32, 2, 2), "tconv"),
+    ("dec1a", (32, 64, 3, 3), "conv"), ("dec1b", (32, 32, 3, 3), "conv"),
+    ("out", (1, 32), "conv1x1"),
+]
+
+
+class UNet:
+    """The warm-start network (device weights, Adam state and buffers)."""
+
+    def __init__(self, H, W, max_batch=1):
+        lib = load()
+        self._lib = lib
+        h = C.c_void_p()
+        st = lib.slim_unet_create(H, W, max_batch, C.byref(h))
+        if st != SLIM_OK:
+            raise SlimError(st, "slim_unet_create failed")
+        self.h = h
+        self.H, self.W, self.max_batch = H, W, max_batch
+        n = C.c_longlong()
+        lib.slim_unet_param_count(C.byref(n))
+        self.nparams = n.value
+
+    def _chk(self, st, what):
+        if st != SLIM_OK:
+            raise SlimError(st, what + " failed")
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.nparams
+        self._chk(self._lib.slim_unet_set_params(self.h, a.ctypes.data_as(C.c_void_p), a.size),
+                  "slim_unet_set_params")
+
+    def get_params(self):
+        a = np.empty(self.nparams, dtype=np.float32)
+        self._chk(self._lib.slim_unet_get_params(self.h, a.ctypes.data_as(C.c_void_p), a.size),
+                  "slim_unet_get_params")
+        return a
+
+    def get_grads(self):
+        a = np.empty(self.nparams, dtype=np.float32)
+        self._chk(self._lib.slim_unet_get_grads(self.h, a.ctypes.data_as(C.c_void_p), a.size),
+                  "slim_unet_get_grads")
+        return a
+
+    def forward(self, x, y, stream_ptr=0):
+        """x, y: float32 device tensors of n*H*W entries."""
+        n = x.numel() // (self.H * self.W)
+        self._chk(self._lib.slim_unet_forward(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                              n, C.c_void_p(stream_ptr)), "slim_unet_forward")
+
+    def train_step(self, x, target, lr, stream_ptr=0):
+        n = x.numel() // (self.H * self.W)
+        loss = C.c_double()
+        self._chk(self._lib.slim_unet_train_step(self.h, C.c_void_p(x.data_ptr()),
+                                                 C.c_void_p(target.data_ptr()), n, C.c_float(lr),
+                                                 C.byref(loss), C.c_void_p(stream_ptr)),
+                  "slim_unet_train_step")
+        return loss.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.slim_unet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def flatten_params(params, layers=UNET_LAYERS):
+    """{name: (w, b)} -> one float32 array in the layer order of the C ABI."""
+    return np.concatenate([np.concatenate([np.asarray(params[name][0], np.float32).ravel(),
+                                           np.asarray(params[name][1], np.float32).ravel()])
+                           for name, _, _ in layers])
+
+
+def unflatten_params(flat, layers=UNET_LAYERS):
+    out, o = {}, 0
+    for name, shape, kind in layers:
+        nw = int(np.prod(shape))
+        nb = shape[1] if kind == "tconv" else shape[0]
+        out[name] = (flat[o:o + nw].reshape(shape), flat[o + nw:o + nw + nb])
+        o += nw + nb
+    return out
