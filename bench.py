@@ -376,6 +376,7 @@ def stream3d_block(sl, flush, stream, K, W, steps_per_view=46):
     torch.cuda.synchronize()
     e = torch.tensor(workloads.noise_direction(cfg.m, cfg.seed), dtype=torch.float32, device="cuda")
     b = y + cfg.noise * torch.linalg.norm(y) * e / torch.linalg.norm(e)
+    torch.cuda.synchronize()     # b is formed on torch's stream, copied on the context's
     del xt, e, y
     s.set_data(b)
     per, ph, _, _ = timed_steps(s, K, W, flush, stream)
@@ -426,8 +427,11 @@ def batch_block(sl, flush, stream, K, W, count=96):
                           device="cuda")
         y = torch.zeros(c.m, dtype=torch.float32, device="cuda")
         pb.project(xt, y)
+        torch.cuda.synchronize()     # y comes from the problem's stream, b is formed on torch's
         e = torch.tensor(workloads.noise_direction(c.m, c.seed), dtype=torch.float32, device="cuda")
-        pb.set_data(y + c.noise * torch.linalg.norm(y) * e / torch.linalg.norm(e))
+        bb = y + c.noise * torch.linalg.norm(y) * e / torch.linalg.norm(e)
+        torch.cuda.synchronize()
+        pb.set_data(bb)
     torch.cuda.synchronize()
     bt.set_stream(stream.cuda_stream)
     for i in range(W):
@@ -456,6 +460,62 @@ def batch_block(sl, flush, stream, K, W, count=96):
             "steps": K, "warmup": W, "factor_flops_per_step": flops,
             "factor_tflops_if_all_time": flops / (t / K) / 1e12,
             "autotune": {"choices_tile_x_ctas": choices, "seconds": tune_s}}
+
+
+def warm_start_block(args):
+    """Learned initial guess on the 256x256 workload: pairs from the method,
+    training of the U-Net in the library's kernels, held-out steps to relative
+    error thresholds against the method's own reconstruction."""
+    import torch
+    from paper_1912_07962_gb300 import slim as sl, warmstart as ws
+    cfg = workloads.C2
+    train = list(workloads.WARM_TRAIN_SEEDS)[:args.ws_train]
+    test = list(workloads.WARM_TEST_SEEDS)[:args.ws_test]
+    log = (lambda m: print(m, file=sys.stderr)) if args.ws_verbose else None
+    t0 = time.perf_counter()
+    X, Y, worst = ws.make_pairs(cfg, train, args.ws_target_epochs, torch, log=log)
+    t_pairs = time.perf_counter() - t0
+    s_in = ws.input_scale(X)
+    net = sl.UNet(cfg.N, cfg.N, max_batch=args.ws_batch)
+    net.set_params(sl.flatten_params(workloads.unet_init(0, sl.UNET_LAYERS)))
+    losses, t_train = ws.train(net, X, Y, s_in, args.ws_net_epochs, args.ws_batch, args.ws_lr, torch,
+                               log=log)
+    del X, Y
+    # inference time of one forward pass (256x256)
+    xin = torch.randn(cfg.n, device="cuda")
+    yout = torch.empty_like(xin)
+    cur = torch.cuda.current_stream()
+    for _ in range(3):
+        net.forward(xin, yout, cur.cuda_stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    for _ in range(10):
+        net.forward(xin, yout, cur.cuda_stream)
+    e1.record(cur)
+    e1.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / 10
+    thresholds = [0.5, 0.3, 0.2, 0.15, 0.1]
+    recs, t_ws = ws.evaluate(net, cfg, test, s_in, args.ws_eval_epochs, thresholds, torch, log=log)
+    net.close()
+    # each weight is used once per output pixel (conv) or per input pixel (tconv)
+    n1 = cfg.n
+    px = {"enc1a": n1, "enc1b": n1, "enc2a": n1 // 4, "enc2b": n1 // 4, "enc3a": n1 // 16,
+          "enc3b": n1 // 16, "bota": n1 // 64, "botb": n1 // 64, "up3": n1 // 64, "dec3a": n1 // 16,
+          "dec3b": n1 // 16, "up2": n1 // 16, "dec2a": n1 // 4, "dec2b": n1 // 4, "up1": n1 // 4,
+          "dec1a": n1, "dec1b": n1, "out": n1}
+    fwd_gflop = 2e-9 * sum(int(np.prod(shape)) * px[name] for name, shape, _ in sl.UNET_LAYERS)
+    return {"train_seeds": len(train), "test_seeds": len(test),
+            "target": f"chosen-form iterate after {args.ws_target_epochs} epochs from x0=0",
+            "error": "relative error to x_true (the phantom), checked every 6 steps",
+            "budget": f"{args.ws_eval_epochs} epochs per start",
+            "float64_check_max_rel_diff": worst, "pairs_seconds": t_pairs,
+            "net_epochs": args.ws_net_epochs, "batch": args.ws_batch, "lr": args.ws_lr,
+            "train_seconds": t_train, "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1],
+            "input_scale": s_in, "forward_ms": fwd_ms, "forward_gflop": fwd_gflop,
+            "forward_tflops": fwd_gflop / fwd_ms,
+            "warm_start_call_ms_median": t_ws * 1e3,
+            "steps_to_threshold": ws.summarize(recs, thresholds)}
 
 
 def e2e_block(sl, cfg, b, K, W, lookahead=0):
@@ -572,6 +632,7 @@ def main_gpu(args):
     s3d = stream3d_block(sl, flush, stream, args.steps, args.warmup) if rank == 0 and not args.no_3d else None
     batch = (batch_block(sl, flush, stream, args.batch_steps, max(3, args.warmup))
              if rank == 0 and args.batch_steps > 0 else None)
+    warm = warm_start_block(args) if rank == 0 and args.warm_start else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         leg = run_cpu_leg(args)
@@ -607,7 +668,7 @@ def main_gpu(args):
         "phases_note": ("one step at a time (synchronous pass); the pipelined region overlaps "
                         "the geometry phases with the iterate chain" if args.lookahead else
                         "per step, inside the timed region"),
-        "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "batched": batch, "tta": tta, "e2e": e2e,
+        "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "batched": batch, "warm_start": warm, "tta": tta, "e2e": e2e,
         "cpu_baseline": cpu,
         "gpu_launches": kernels * args.steps, "kernels_per_step": kernels, "clocks": clocks,
     }
@@ -648,6 +709,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-csr", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--warm-start", action="store_true",
+                    help="train and evaluate the learned initial guess (minutes of GPU time)")
+    ap.add_argument("--ws-train", type=int, default=256)
+    ap.add_argument("--ws-test", type=int, default=20)
+    ap.add_argument("--ws-target-epochs", type=int, default=2)
+    ap.add_argument("--ws-eval-epochs", type=int, default=4)
+    ap.add_argument("--ws-net-epochs", type=int, default=8)
+    ap.add_argument("--ws-batch", type=int, default=8)
+    ap.add_argument("--ws-lr", type=float, default=1e-3)
+    ap.add_argument("--ws-verbose", action="store_true")
     ap.add_argument("--factor-ctas-per-sm", type=int, default=0,
                     help="persistent factorisation CTAs per SM (0: library default)")
     ap.add_argument("--lookahead", type=int, default=3,

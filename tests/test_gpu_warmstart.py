@@ -1,0 +1,33 @@
+"""The warm-start experiment driver at a tiny size: pairs from the method,
+training, and the held-out evaluation run end to end."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+def test_driver_end_to_end():
+    from paper_1912_07962_gb300 import build, slim as sl, warmstart as ws
+    build.build()
+    cfg = dataclasses.replace(workloads.C1, N=32, n_views=24, det=47, ell=47, r=2, lam=1e-2)
+    X, Y, worst = ws.make_pairs(cfg, list(range(100, 116)), 2, torch, check_every=8)
+    assert X.shape == (16, 32 * 32) and torch.isfinite(Y).all()
+    assert worst < 1e-4                     # float32 chosen form vs float64 form after 2 epochs
+    s_in = ws.input_scale(X)
+    net = sl.UNet(32, 32, max_batch=4)
+    net.set_params(sl.flatten_params(workloads.unet_init(0, sl.UNET_LAYERS)))
+    losses, _ = ws.train(net, X, Y, s_in, 6, 4, 1e-3, torch)
+    assert losses[-1] < losses[0]
+    recs, _ = ws.evaluate(net, cfg, [200, 201], s_in, 3, [0.9, 0.5], torch, every=6)
+    summary = ws.summarize(recs, [0.9, 0.5])
+    assert summary["thresholds"]["0.9"]["reached_zero"] == 2   # the iteration reduces the error
+    assert summary["zero"]["err0"] == 1.0                      # from x_0 = 0 the error starts at 1
+    assert 0.0 < summary["zero"]["best"] < 0.9
+    assert 0.0 <= summary["used_fraction"] <= 1.0
+    net.close()
