@@ -881,76 +881,61 @@ __global__ void __launch_bounds__(kThreads) chol_bwd_kernel(const T* L, int P, i
 // Both triangular solves of L L^T z = v in one thread-block cluster.
 //
 // Tile row i belongs to CTA i mod C.  Every CTA keeps the whole of y (and
-// then z) in its shared memory: the owner of a tile row broadcasts its C-block
-// of y into all CTAs of the cluster (distributed shared memory) and then sets
-// a per-row flag in each of them with a cluster-scope release; the others
-// poll their own flag.  While waiting for row j-1, a CTA has already folded
-// rows < j-1 into its accumulator, so each link of the chain costs one
-// NB x NB matrix-vector product and one broadcast.
+// then z) in its shared memory.  The owner of a tile row sends its NB values
+// to every other CTA of the cluster with one bulk copy each (distributed
+// shared memory); the copy completes a per-row mbarrier in the receiving CTA,
+// on which that CTA waits.  While waiting for row j-1, a CTA has already
+// folded rows < j-1 into its accumulator (batches of tiles with all loads in
+// flight), so each link of the chain costs one NB x NB matrix-vector product
+// and one copy.  Every wait is bounded; before leaving, each CTA waits for all
+// copies addressed to it.
 // ---------------------------------------------------------------------------
 namespace cg = cooperative_groups;
 
-__device__ __forceinline__ int ld_acquire_cluster(const int* p) {
-  int v;
-  asm volatile("ld.acquire.cluster.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void st_release_cluster(int* p, int v) {
-  asm volatile("st.release.cluster.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void fence_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
-
-// CTA-wide bounded wait for a flag in this CTA's shared memory.
-__device__ bool cluster_wait(const int* flag, int* abort_flag, int* status, int* s_ok) {
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    unsigned it = 0;
-    while (ld_acquire_cluster(flag) == 0) {
-      if (++it > kSpinLimit) {
-        set_status(status, SLIM_ETIMEOUT);
-        atomicExch(abort_flag, 1);
-        ok = 0;
-        break;
-      }
-      if ((it & 255u) == 0 && ld_acquire(abort_flag)) {
-        ok = 0;
-        break;
-      }
-      __nanosleep(16);
-    }
-    *s_ok = ok;
-  }
-  __syncthreads();
-  const int ok = *s_ok;
-  __syncthreads();
-  return ok != 0;
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+// Copy `bytes` (multiple of 16, 16-byte aligned) from this CTA's shared memory
+// to the CTA whose addresses are dst / bar; the copy completes that CTA's mbarrier.
+__device__ __forceinline__ void bulk_copy_to(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst), "r"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
-// Write the NB values of out[] into row block i of `vec` in every CTA of the
-// cluster, then raise flag[i] in each of them.
-template <typename T, int NB>
-__device__ void cluster_publish(cg::cluster_group& cl, int C, T* vec, int* flag, int i,
-                                const T* out) {
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < C * NB; idx += kThreads) {
-    const int d = idx / NB, e = idx % NB;
-    T* rv = cl.map_shared_rank(vec, d);
-    rv[i * NB + e] = out[e];
-  }
-  fence_cluster();
-  __syncthreads();
-  if (tid < C) st_release_cluster(cl.map_shared_rank(flag, tid) + i, 1);
-}
+constexpr int kSolveBatch = 4;   // tiles folded per batch
 
-// Bounded wait until flags [j0, j1) in this CTA's shared memory are all set.
-__device__ bool cluster_wait_range(const int* flag, int j0, int j1, int* abort_flag, int* status,
-                                   int* s_ok) {
+// CTA-wide bounded wait until the rows [j0, j1) owned by other CTAs have
+// arrived (their mbarriers in this CTA completed).
+__device__ bool cluster_wait_rows(uint64_t* bars, int j0, int j1, int C, int rank, unsigned limit,
+                                  int* abort_flag, int* status, int* s_ok) {
   if (threadIdx.x == 0) {
     int ok = 1;
     for (int j = j0; ok && j < j1; ++j) {
+      if (j % C == rank) continue;
       unsigned it = 0;
-      while (ld_acquire_cluster(flag + j) == 0) {
-        if (++it > kSpinLimit) {
+      while (!mbar_try_wait(&bars[j], 0)) {
+        if (++it > limit) {
           set_status(status, SLIM_ETIMEOUT);
           atomicExch(abort_flag, 1);
           ok = 0;
@@ -960,7 +945,6 @@ __device__ bool cluster_wait_range(const int* flag, int j0, int j1, int* abort_f
           ok = 0;
           break;
         }
-        __nanosleep(16);
       }
     }
     *s_ok = ok;
@@ -971,130 +955,247 @@ __device__ bool cluster_wait_range(const int* flag, int j0, int j1, int* abort_f
   return ok != 0;
 }
 
-constexpr int kSolveBatch = 4;   // tiles folded per batch
+// Rows per super-row: with R = 2 a CTA solves 2 consecutive tile rows itself
+// and one handoff between CTAs covers both; measured on the 256x256 workload
+// it is slower than R = 1 (166 vs 133 us per float32 solve), so R = 1.
+template <typename T, int NB>
+__host__ __device__ constexpr int solve_rows() { return 1; }
 
 template <typename T, int NB>
 __global__ void __launch_bounds__(kThreads) chol_solve_cluster_kernel(
     const T* L, int P, int Tt, const T* winv, const double* v, double* z, int* status,
     int* abort_flag) {
+  constexpr int R = solve_rows<T, NB>();
+  static_assert(R == 1 || R == 2, "one intra-super-row tile per row");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* y = reinterpret_cast<T*>(smem_raw);     // [P] forward solution
   T* zt = y + P;                              // [P] backward solution
-  int* fready = reinterpret_cast<int*>(zt + P);
-  int* bready = fready + Tt;
-  __shared__ T acc[NB], out[NB];
+  const int ST = (Tt + R - 1) / R;            // super-rows
+  uint64_t* fbar = reinterpret_cast<uint64_t*>(zt + P);   // [ST] arrival of y super-rows
+  uint64_t* bbar = fbar + ST;                             // [ST] arrival of z super-rows
+  __shared__ T acc[R][NB], out[NB];
   __shared__ T part[kThreads];
   __shared__ int s_ok;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x;
-  for (int i = tid; i < Tt; i += kThreads) {
-    fready[i] = 0;
-    bready[i] = 0;
+  if (tid == 0) {
+    for (int q = 0; q < ST; ++q) {
+      mbar_init(&fbar[q], 1);
+      mbar_init(&bbar[q], 1);
+      if (q % C != rank) {   // super-rows sent by other CTAs
+        const uint32_t bytes = (uint32_t)(min(R, Tt - q * R) * NB * sizeof(T));
+        mbar_expect_tx(&fbar[q], bytes);
+        mbar_expect_tx(&bbar[q], bytes);
+      }
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  cl.sync();   // every CTA's flags are cleared before anyone publishes
+  cl.sync();   // every CTA's barriers exist before anyone sends
   bool ok = true;
   // forward: y_i = W_i (v_i - sum_{j<i} L_ij y_j)
   {
     using RP = RowPart<T, NB>;
     const int r = tid / RP::TPR, sub = tid % RP::TPR;
-    for (int i = rank; ok && i < Tt; i += C) {
-      RP wpart, lastp, bp[kSolveBatch];
-      wpart.load(winv + (size_t)i * NB * NB, NB);
-      if (i > 0) lastp.load(L + (size_t)i * NB * P + (size_t)(i - 1) * NB, P);
-      T s = T(0);
-      // tiles j < i-1: their blocks are (mostly) solved already; fold them in
-      // batches with all loads in flight
-      for (int j = 0; j + 1 < i; j += kSolveBatch) {
-        const int nj = min(kSolveBatch, i - 1 - j);
+    for (int sr = rank; ok && sr < ST; sr += C) {
+      const int i0 = sr * R, nr = min(R, Tt - i0), p0 = i0 - R;   // p0: previous super-row
+      T sacc[R];
 #pragma unroll
-        for (int u = 0; u < kSolveBatch; ++u)
-          if (u < nj) bp[u].load(L + (size_t)i * NB * P + (size_t)(j + u) * NB, P);
-        if (!cluster_wait_range(fready, j, j + nj, abort_flag, status, &s_ok)) {
+      for (int b = 0; b < R; ++b) sacc[b] = T(0);
+      // super-rows before the previous one: (mostly) arrived; batches of
+      // tiles for every row of the super-row, all loads in flight per batch
+      for (int j = 0; j < p0; j += kSolveBatch) {
+        const int nj = min(kSolveBatch, p0 - j);
+        RP bp[R][kSolveBatch];
+#pragma unroll
+        for (int b = 0; b < R; ++b)
+#pragma unroll
+          for (int u = 0; u < kSolveBatch; ++u)
+            if (b < nr && u < nj) bp[b][u].load(L + (size_t)(i0 + b) * NB * P + (size_t)(j + u) * NB, P);
+        if (!cluster_wait_rows(fbar, j / R, (j + nj - 1) / R + 1, C, rank, kSpinLimit, abort_flag,
+                               status, &s_ok)) {
           ok = false;
           break;
         }
 #pragma unroll
-        for (int u = 0; u < kSolveBatch; ++u)
-          if (u < nj)
+        for (int b = 0; b < R; ++b)
 #pragma unroll
-            for (int q = 0; q < RP::CPT; ++q) s += bp[u].v[q] * y[(j + u) * NB + sub * RP::CPT + q];
+          for (int u = 0; u < kSolveBatch; ++u)
+            if (b < nr && u < nj)
+#pragma unroll
+              for (int q = 0; q < RP::CPT; ++q)
+                sacc[b] += bp[b][u].v[q] * y[(j + u) * NB + sub * RP::CPT + q];
       }
       if (!ok) break;
-      if (i > 0) {
-        if (!cluster_wait_range(fready, i - 1, i, abort_flag, status, &s_ok)) {
+      // the previous super-row closes the chain link
+      RP wp[R], prevp[R][R], intra[R];
+#pragma unroll
+      for (int b = 0; b < R; ++b)
+        if (b < nr) {
+          wp[b].load(winv + (size_t)(i0 + b) * NB * NB, NB);
+#pragma unroll
+          for (int c = 0; c < R; ++c)
+            if (p0 >= 0) prevp[b][c].load(L + (size_t)(i0 + b) * NB * P + (size_t)(p0 + c) * NB, P);
+          if (b > 0) intra[b].load(L + (size_t)(i0 + b) * NB * P + (size_t)i0 * NB, P);
+        }
+      if (p0 >= 0) {
+        if (!cluster_wait_rows(fbar, sr - 1, sr, C, rank, kSpinLimit, abort_flag, status, &s_ok)) {
           ok = false;
           break;
         }
 #pragma unroll
-        for (int q = 0; q < RP::CPT; ++q) s += lastp.v[q] * y[(i - 1) * NB + sub * RP::CPT + q];
+        for (int b = 0; b < R; ++b)
+          if (b < nr)
+#pragma unroll
+            for (int c = 0; c < R; ++c)
+#pragma unroll
+              for (int q = 0; q < RP::CPT; ++q)
+                sacc[b] += prevp[b][c].v[q] * y[(p0 + c) * NB + sub * RP::CPT + q];
       }
 #pragma unroll
-      for (int o = RP::TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, RP::TPR);
-      if (sub == 0) acc[r] = (T)v[i * NB + r] - s;
-      if (tid < NB) out[tid] = T(0);
+      for (int b = 0; b < R; ++b) {
+#pragma unroll
+        for (int o = RP::TPR / 2; o > 0; o >>= 1) sacc[b] += __shfl_xor_sync(0xffffffffu, sacc[b], o, RP::TPR);
+        if (b < nr && sub == 0) acc[b][r] = (T)v[(i0 + b) * NB + r] - sacc[b];
+      }
+      // rows of the super-row in order (R <= 2: row i0+1 needs only y_{i0})
+#pragma unroll
+      for (int b = 0; b < R; ++b) {
+        if (b >= nr) break;
+        if (tid < NB) out[tid] = T(0);
+        __syncthreads();
+        if (b > 0) {
+          intra[b].apply(y + i0 * NB, acc[b], T(-1));
+          __syncthreads();
+        }
+        wp[b].apply(acc[b], out, T(1));
+        __syncthreads();
+        if (tid < NB) y[(i0 + b) * NB + tid] = out[tid];
+      }
+      // send the super-row to the other CTAs
+      if (tid < NB) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
-      wpart.apply(acc, out, T(1));
-      __syncthreads();
-      cluster_publish<T, NB>(cl, C, y, fready, i, out);
+      if (tid < C && tid != rank) {
+        const uint32_t src = smem_u32(y + i0 * NB);
+        bulk_copy_to(map_to_rank(src, tid), src, nr * NB * sizeof(T),
+                     map_to_rank(smem_u32(&fbar[sr]), tid));
+      }
     }
   }
   // backward: z_i = W_i^T (y_i - sum_{j>i} L_ji^T z_j)
   {
     using CP = ColPart<T, NB>;
     const int a = tid % NB, ch = tid / NB;
-    const int last = Tt - 1 - ((Tt - 1 - rank) % C + C) % C;   // largest i = rank (mod C)
-    for (int i = last; ok && i >= 0; i -= C) {
-      CP wpart, nextp, bp[kSolveBatch];
-      wpart.load(winv + (size_t)i * NB * NB, NB);
-      if (i + 1 < Tt) nextp.load(L + (size_t)(i + 1) * NB * P + (size_t)i * NB, P);
-      T s = T(0);
-      for (int j = Tt - 1; j > i + 1; j -= kSolveBatch) {
-        const int nj = min(kSolveBatch, j - i - 1);   // tiles j, j-1, .., j-nj+1
+    const int last = ST - 1 - ((ST - 1 - rank) % C + C) % C;   // largest super-row = rank (mod C)
+    for (int sr = last; ok && sr >= 0; sr -= C) {
+      const int i0 = sr * R, nr = min(R, Tt - i0);
+      const int n0 = i0 + R;                      // first row of the next super-row
+      const int n1 = min(Tt, n0 + R);             // end of the next super-row
+      T sacc[R];
 #pragma unroll
-        for (int u = 0; u < kSolveBatch; ++u)
-          if (u < nj) bp[u].load(L + (size_t)(j - u) * NB * P + (size_t)i * NB, P);
-        if (!cluster_wait_range(bready, j - nj + 1, j + 1, abort_flag, status, &s_ok)) {
+      for (int b = 0; b < R; ++b) sacc[b] = T(0);
+      // super-rows after the next one: tiles j >= n1, every row of the
+      // super-row per batch
+      for (int j = Tt - 1; j >= n1; j -= kSolveBatch) {
+        const int nj = min(kSolveBatch, j - n1 + 1);   // tiles j, j-1, .., j-nj+1
+        CP bp[R][kSolveBatch];
+#pragma unroll
+        for (int b = 0; b < R; ++b)
+#pragma unroll
+          for (int u = 0; u < kSolveBatch; ++u)
+            if (b < nr && u < nj) bp[b][u].load(L + (size_t)(j - u) * NB * P + (size_t)(i0 + b) * NB, P);
+        if (!cluster_wait_rows(bbar, (j - nj + 1) / R, j / R + 1, C, rank, kSpinLimit, abort_flag,
+                               status, &s_ok)) {
           ok = false;
           break;
         }
 #pragma unroll
-        for (int u = 0; u < kSolveBatch; ++u)
-          if (u < nj)
+        for (int b = 0; b < R; ++b)
 #pragma unroll
-            for (int q = 0; q < CP::RPC; ++q) s += bp[u].v[q] * zt[(j - u) * NB + ch * CP::RPC + q];
+          for (int u = 0; u < kSolveBatch; ++u)
+            if (b < nr && u < nj)
+#pragma unroll
+              for (int q = 0; q < CP::RPC; ++q)
+                sacc[b] += bp[b][u].v[q] * zt[(j - u) * NB + ch * CP::RPC + q];
       }
       if (!ok) break;
-      if (i + 1 < Tt) {
-        if (!cluster_wait_range(bready, i + 1, i + 2, abort_flag, status, &s_ok)) {
+      CP wp[R], nextp[R][R], intra[R];
+#pragma unroll
+      for (int b = 0; b < R; ++b)
+        if (b < nr) {
+          wp[b].load(winv + (size_t)(i0 + b) * NB * NB, NB);
+#pragma unroll
+          for (int c = 0; c < R; ++c)
+            if (n0 + c < n1) nextp[b][c].load(L + (size_t)(n0 + c) * NB * P + (size_t)(i0 + b) * NB, P);
+          if (b + 1 < nr) intra[b].load(L + (size_t)(i0 + R - 1) * NB * P + (size_t)(i0 + b) * NB, P);
+        }
+      if (n0 < Tt) {
+        if (!cluster_wait_rows(bbar, sr + 1, sr + 2, C, rank, kSpinLimit, abort_flag, status, &s_ok)) {
           ok = false;
           break;
         }
 #pragma unroll
-        for (int q = 0; q < CP::RPC; ++q) s += nextp.v[q] * zt[(i + 1) * NB + ch * CP::RPC + q];
-      }
-      part[ch * NB + a] = s;
-      __syncthreads();
-      if (tid < NB) {
-        T t = T(0);
+        for (int b = 0; b < R; ++b)
+          if (b < nr)
 #pragma unroll
-        for (int c = 0; c < CP::CH; ++c) t += part[c * NB + tid];
-        acc[tid] = y[i * NB + tid] - t;
-        out[tid] = T(0);
+            for (int c = 0; c < R; ++c)
+              if (n0 + c < n1)
+#pragma unroll
+                for (int q = 0; q < CP::RPC; ++q)
+                  sacc[b] += nextp[b][c].v[q] * zt[(n0 + c) * NB + ch * CP::RPC + q];
       }
+#pragma unroll
+      for (int b = 0; b < R; ++b) {
+        if (b >= nr) break;
+        part[ch * NB + a] = sacc[b];
+        __syncthreads();
+        if (tid < NB) {
+          T t = T(0);
+#pragma unroll
+          for (int c = 0; c < CP::CH; ++c) t += part[c * NB + tid];
+          acc[b][tid] = y[(i0 + b) * NB + tid] - t;
+        }
+        __syncthreads();
+      }
+      // rows of the super-row from the last (R <= 2: row i0 needs only z_{i0+1})
+#pragma unroll
+      for (int bb = R - 1; bb >= 0; --bb) {
+        if (bb >= nr) continue;
+        if (tid < NB) out[tid] = T(0);
+        __syncthreads();
+        if (bb + 1 < nr) {
+          intra[bb].apply(zt + (i0 + R - 1) * NB, acc[bb], T(-1), part);
+          __syncthreads();
+        }
+        wp[bb].apply(acc[bb], out, T(1), part);
+        __syncthreads();
+        if (tid < NB) {
+          zt[(i0 + bb) * NB + tid] = out[tid];
+          z[(i0 + bb) * NB + tid] = (double)out[tid];
+        }
+      }
+      if (tid < NB) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
-      wpart.apply(acc, out, T(1), part);
-      __syncthreads();
-      if (tid < NB) z[i * NB + tid] = (double)out[tid];
-      cluster_publish<T, NB>(cl, C, zt, bready, i, out);
+      if (tid < C && tid != rank) {
+        const uint32_t src = smem_u32(zt + i0 * NB);
+        bulk_copy_to(map_to_rank(src, tid), src, nr * NB * sizeof(T),
+                     map_to_rank(smem_u32(&bbar[sr]), tid));
+      }
     }
   }
-  cl.sync();   // no CTA leaves while others may still write into its shared memory
+  // wait for every copy addressed to this CTA before leaving (briefly when a
+  // wait already ran out: the rows still missing will not come)
+  const unsigned drain = ok ? kSpinLimit : (kSpinLimit >> 8);
+  cluster_wait_rows(fbar, 0, ST, C, rank, drain, abort_flag, status, &s_ok);
+  cluster_wait_rows(bbar, 0, ST, C, rank, drain, abort_flag, status, &s_ok);
+  cl.sync();   // no CTA leaves while others may still read its shared memory
 }
 
 template <typename T>
-size_t solve_cluster_smem(int P, int Tt) { return 2 * (size_t)P * sizeof(T) + 2 * (size_t)Tt * sizeof(int); }
+size_t solve_cluster_smem(int P, int Tt) {
+  return 2 * (size_t)P * sizeof(T) + 2 * (size_t)Tt * sizeof(uint64_t);   // Tt >= super-rows
+}
 
 // Largest cluster (16, else 8) that fits the solve, or 0 when none does.
 template <typename T, int NB>
