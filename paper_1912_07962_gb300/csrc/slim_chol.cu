@@ -760,10 +760,24 @@ struct RowPart {
   static constexpr int TPR = kThreads / NB;
   static constexpr int CPT = NB / TPR;
   T v[CPT];
+  // 16-byte loads (the rows of a tile start on 16-byte boundaries: ld and the
+  // tile offsets are multiples of 4 floats / 2 doubles)
   __device__ void load(const T* M, int ld) {
     const int r = threadIdx.x / TPR, sub = threadIdx.x % TPR;
+    const T* p = M + (size_t)r * ld + sub * CPT;
+    if constexpr ((CPT * sizeof(T)) % 16 == 0) {
+      constexpr int EV = 16 / sizeof(T);
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) v[q] = ldcg(M + (size_t)r * ld + sub * CPT + q);
+      for (int q = 0; q < CPT; q += EV) {
+        const vec16_t<T> t = __ldcg(reinterpret_cast<const vec16_t<T>*>(p + q));
+        const T* pt = reinterpret_cast<const T*>(&t);
+#pragma unroll
+        for (int e = 0; e < EV; ++e) v[q + e] = pt[e];
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) v[q] = ldcg(p + q);
+    }
   }
   // acc[r] += sign * (M v)[r]
   __device__ void apply(const T* vec, T* acc, T sign) const {
@@ -955,241 +969,209 @@ __device__ bool cluster_wait_rows(uint64_t* bars, int j0, int j1, int C, int ran
   return ok != 0;
 }
 
-// Rows per super-row: with R = 2 a CTA solves 2 consecutive tile rows itself
-// and one handoff between CTAs covers both; measured on the 256x256 workload
-// it is slower than R = 1 (166 vs 133 us per float32 solve), so R = 1.
+// Transposed GEMV piece: thread (a = tid%NB, ch = tid/NB) holds rows
+// ch*RPC .. ch*RPC+RPC-1 of column a of a tile (a warp reads whole rows of the
+// tile, coalesced); (M^T vec)[a] is the sum of the CH partial sums of column a.
 template <typename T, int NB>
-__host__ __device__ constexpr int solve_rows() { return 1; }
+struct TPart {
+  static constexpr int CH = kThreads / NB;
+  static constexpr int RPC = NB / CH;
+  T v[RPC];
+  __device__ void load(const T* M, int ld) {
+    const int a = threadIdx.x % NB, ch = threadIdx.x / NB;
+#pragma unroll
+    for (int q = 0; q < RPC; ++q) v[q] = ldcg(M + (size_t)(ch * RPC + q) * ld + a);
+  }
+  // partial sum of column a over this thread's rows of vec (shared memory)
+  __device__ T dot(const T* vec) const {
+    const int ch = threadIdx.x / NB;
+    T s = T(0);
+    constexpr int EV = (RPC * sizeof(T)) % 16 == 0 ? 16 / (int)sizeof(T) : 1;
+    T x[EV];
+#pragma unroll
+    for (int q = 0; q < RPC; q += EV) {
+      lds_vec<T, EV>(x, vec + ch * RPC + q);
+#pragma unroll
+      for (int e = 0; e < EV; ++e) s += v[q + e] * x[e];
+    }
+    return s;
+  }
+};
+
+// Partial sum of row r over this thread's columns of vec (RowPart layout).
+template <typename T, int NB>
+__device__ __forceinline__ T row_dot(const RowPart<T, NB>& m, const T* vec) {
+  constexpr int CPT = RowPart<T, NB>::CPT;
+  constexpr int EV = (CPT * sizeof(T)) % 16 == 0 ? 16 / (int)sizeof(T) : 1;
+  const int sub = threadIdx.x % RowPart<T, NB>::TPR;
+  T s = T(0);
+  T x[EV];
+#pragma unroll
+  for (int q = 0; q < CPT; q += EV) {
+    lds_vec<T, EV>(x, vec + sub * CPT + q);
+#pragma unroll
+    for (int e = 0; e < EV; ++e) s += m.v[q + e] * x[e];
+  }
+  return s;
+}
+
+// Store one value into a peer CTA's shared memory; the store completes that
+// CTA's mbarrier by sizeof(value) bytes.
+__device__ __forceinline__ void st_async_peer(uint32_t addr, float val, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
+               ::"r"(addr), "r"(__float_as_uint(val)), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void st_async_peer(uint32_t addr, double val, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];"
+               ::"r"(addr), "l"(__double_as_longlong(val)), "r"(bar) : "memory");
+}
+
+// Bounded wait of the calling thread for a row's arrival.
+__device__ __forceinline__ void thread_wait_row(uint64_t* bar, int* abort_flag, int* status) {
+  unsigned it = 0;
+  while (!mbar_try_wait(bar, 0)) {
+    if (++it > kSpinLimit) {
+      set_status(status, SLIM_ETIMEOUT);
+      atomicExch(abort_flag, 1);
+      return;
+    }
+    if ((it & 255u) == 0 && ld_acquire(abort_flag)) return;
+  }
+}
 
 template <typename T, int NB>
 __global__ void __launch_bounds__(kThreads) chol_solve_cluster_kernel(
     const T* L, int P, int Tt, const T* winv, const double* v, double* z, int* status,
     int* abort_flag) {
-  constexpr int R = solve_rows<T, NB>();
-  static_assert(R == 1 || R == 2, "one intra-super-row tile per row");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* y = reinterpret_cast<T*>(smem_raw);     // [P] forward solution
   T* zt = y + P;                              // [P] backward solution
-  const int ST = (Tt + R - 1) / R;            // super-rows
-  uint64_t* fbar = reinterpret_cast<uint64_t*>(zt + P);   // [ST] arrival of y super-rows
-  uint64_t* bbar = fbar + ST;                             // [ST] arrival of z super-rows
-  __shared__ T acc[R][NB], out[NB];
+  uint64_t* fbar = reinterpret_cast<uint64_t*>(zt + P);   // [Tt] arrival of y rows
+  uint64_t* bbar = fbar + Tt;                             // [Tt] arrival of z rows
+  __shared__ __align__(16) T acc[NB];
   __shared__ T part[kThreads];
   __shared__ int s_ok;
+  using RP = RowPart<T, NB>;
+  using TP = TPart<T, NB>;
+  constexpr int TPR = RP::TPR, CPT = RP::CPT;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, r = tid / TPR, sub = tid % TPR;
   if (tid == 0) {
-    for (int q = 0; q < ST; ++q) {
-      mbar_init(&fbar[q], 1);
-      mbar_init(&bbar[q], 1);
-      if (q % C != rank) {   // super-rows sent by other CTAs
-        const uint32_t bytes = (uint32_t)(min(R, Tt - q * R) * NB * sizeof(T));
-        mbar_expect_tx(&fbar[q], bytes);
-        mbar_expect_tx(&bbar[q], bytes);
+    for (int i = 0; i < Tt; ++i) {
+      mbar_init(&fbar[i], 1);
+      mbar_init(&bbar[i], 1);
+      if (i % C != rank) {   // rows sent by other CTAs: one arrival expecting NB values
+        mbar_expect_tx(&fbar[i], NB * sizeof(T));
+        mbar_expect_tx(&bbar[i], NB * sizeof(T));
       }
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   cl.sync();   // every CTA's barriers exist before anyone sends
   bool ok = true;
+  // The owner of row i finishes it with one barrier on the chain: every thread
+  // waits for row i-1 itself, the rows' accumulators meet in shared memory,
+  // and the lanes holding the results store them into every peer.
   // forward: y_i = W_i (v_i - sum_{j<i} L_ij y_j)
-  {
-    using RP = RowPart<T, NB>;
-    const int r = tid / RP::TPR, sub = tid % RP::TPR;
-    for (int sr = rank; ok && sr < ST; sr += C) {
-      const int i0 = sr * R, nr = min(R, Tt - i0), p0 = i0 - R;   // p0: previous super-row
-      T sacc[R];
+  for (int i = rank; ok && i < Tt; i += C) {
+    RP wp, lastp;
+    wp.load(winv + (size_t)i * NB * NB, NB);
+    if (i > 0) lastp.load(L + (size_t)i * NB * P + (size_t)(i - 1) * NB, P);
+    T s = T(0);
+    for (int j = 0; j + 1 < i; j += kSolveBatch) {   // rows < i-1, batches in flight
+      const int nj = min(kSolveBatch, i - 1 - j);
+      RP bp[kSolveBatch];
 #pragma unroll
-      for (int b = 0; b < R; ++b) sacc[b] = T(0);
-      // super-rows before the previous one: (mostly) arrived; batches of
-      // tiles for every row of the super-row, all loads in flight per batch
-      for (int j = 0; j < p0; j += kSolveBatch) {
-        const int nj = min(kSolveBatch, p0 - j);
-        RP bp[R][kSolveBatch];
-#pragma unroll
-        for (int b = 0; b < R; ++b)
-#pragma unroll
-          for (int u = 0; u < kSolveBatch; ++u)
-            if (b < nr && u < nj) bp[b][u].load(L + (size_t)(i0 + b) * NB * P + (size_t)(j + u) * NB, P);
-        if (!cluster_wait_rows(fbar, j / R, (j + nj - 1) / R + 1, C, rank, kSpinLimit, abort_flag,
-                               status, &s_ok)) {
-          ok = false;
-          break;
-        }
-#pragma unroll
-        for (int b = 0; b < R; ++b)
-#pragma unroll
-          for (int u = 0; u < kSolveBatch; ++u)
-            if (b < nr && u < nj)
-#pragma unroll
-              for (int q = 0; q < RP::CPT; ++q)
-                sacc[b] += bp[b][u].v[q] * y[(j + u) * NB + sub * RP::CPT + q];
-      }
-      if (!ok) break;
-      // the previous super-row closes the chain link
-      RP wp[R], prevp[R][R], intra[R];
-#pragma unroll
-      for (int b = 0; b < R; ++b)
-        if (b < nr) {
-          wp[b].load(winv + (size_t)(i0 + b) * NB * NB, NB);
-#pragma unroll
-          for (int c = 0; c < R; ++c)
-            if (p0 >= 0) prevp[b][c].load(L + (size_t)(i0 + b) * NB * P + (size_t)(p0 + c) * NB, P);
-          if (b > 0) intra[b].load(L + (size_t)(i0 + b) * NB * P + (size_t)i0 * NB, P);
-        }
-      if (p0 >= 0) {
-        if (!cluster_wait_rows(fbar, sr - 1, sr, C, rank, kSpinLimit, abort_flag, status, &s_ok)) {
-          ok = false;
-          break;
-        }
-#pragma unroll
-        for (int b = 0; b < R; ++b)
-          if (b < nr)
-#pragma unroll
-            for (int c = 0; c < R; ++c)
-#pragma unroll
-              for (int q = 0; q < RP::CPT; ++q)
-                sacc[b] += prevp[b][c].v[q] * y[(p0 + c) * NB + sub * RP::CPT + q];
+      for (int u = 0; u < kSolveBatch; ++u)
+        if (u < nj) bp[u].load(L + (size_t)i * NB * P + (size_t)(j + u) * NB, P);
+      if (!cluster_wait_rows(fbar, j, j + nj, C, rank, kSpinLimit, abort_flag, status, &s_ok)) {
+        ok = false;
+        break;
       }
 #pragma unroll
-      for (int b = 0; b < R; ++b) {
-#pragma unroll
-        for (int o = RP::TPR / 2; o > 0; o >>= 1) sacc[b] += __shfl_xor_sync(0xffffffffu, sacc[b], o, RP::TPR);
-        if (b < nr && sub == 0) acc[b][r] = (T)v[(i0 + b) * NB + r] - sacc[b];
-      }
-      // rows of the super-row in order (R <= 2: row i0+1 needs only y_{i0})
-#pragma unroll
-      for (int b = 0; b < R; ++b) {
-        if (b >= nr) break;
-        if (tid < NB) out[tid] = T(0);
-        __syncthreads();
-        if (b > 0) {
-          intra[b].apply(y + i0 * NB, acc[b], T(-1));
-          __syncthreads();
-        }
-        wp[b].apply(acc[b], out, T(1));
-        __syncthreads();
-        if (tid < NB) y[(i0 + b) * NB + tid] = out[tid];
-      }
-      // send the super-row to the other CTAs
-      if (tid < NB) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid < C && tid != rank) {
-        const uint32_t src = smem_u32(y + i0 * NB);
-        bulk_copy_to(map_to_rank(src, tid), src, nr * NB * sizeof(T),
-                     map_to_rank(smem_u32(&fbar[sr]), tid));
-      }
+      for (int u = 0; u < kSolveBatch; ++u)
+        if (u < nj) s += row_dot<T, NB>(bp[u], y + (j + u) * NB);
     }
-  }
-  // backward: z_i = W_i^T (y_i - sum_{j>i} L_ji^T z_j)
-  {
-    using CP = ColPart<T, NB>;
-    const int a = tid % NB, ch = tid / NB;
-    const int last = ST - 1 - ((ST - 1 - rank) % C + C) % C;   // largest super-row = rank (mod C)
-    for (int sr = last; ok && sr >= 0; sr -= C) {
-      const int i0 = sr * R, nr = min(R, Tt - i0);
-      const int n0 = i0 + R;                      // first row of the next super-row
-      const int n1 = min(Tt, n0 + R);             // end of the next super-row
-      T sacc[R];
-#pragma unroll
-      for (int b = 0; b < R; ++b) sacc[b] = T(0);
-      // super-rows after the next one: tiles j >= n1, every row of the
-      // super-row per batch
-      for (int j = Tt - 1; j >= n1; j -= kSolveBatch) {
-        const int nj = min(kSolveBatch, j - n1 + 1);   // tiles j, j-1, .., j-nj+1
-        CP bp[R][kSolveBatch];
-#pragma unroll
-        for (int b = 0; b < R; ++b)
-#pragma unroll
-          for (int u = 0; u < kSolveBatch; ++u)
-            if (b < nr && u < nj) bp[b][u].load(L + (size_t)(j - u) * NB * P + (size_t)(i0 + b) * NB, P);
-        if (!cluster_wait_rows(bbar, (j - nj + 1) / R, j / R + 1, C, rank, kSpinLimit, abort_flag,
-                               status, &s_ok)) {
-          ok = false;
-          break;
-        }
-#pragma unroll
-        for (int b = 0; b < R; ++b)
-#pragma unroll
-          for (int u = 0; u < kSolveBatch; ++u)
-            if (b < nr && u < nj)
-#pragma unroll
-              for (int q = 0; q < CP::RPC; ++q)
-                sacc[b] += bp[b][u].v[q] * zt[(j - u) * NB + ch * CP::RPC + q];
-      }
-      if (!ok) break;
-      CP wp[R], nextp[R][R], intra[R];
-#pragma unroll
-      for (int b = 0; b < R; ++b)
-        if (b < nr) {
-          wp[b].load(winv + (size_t)(i0 + b) * NB * NB, NB);
-#pragma unroll
-          for (int c = 0; c < R; ++c)
-            if (n0 + c < n1) nextp[b][c].load(L + (size_t)(n0 + c) * NB * P + (size_t)(i0 + b) * NB, P);
-          if (b + 1 < nr) intra[b].load(L + (size_t)(i0 + R - 1) * NB * P + (size_t)(i0 + b) * NB, P);
-        }
-      if (n0 < Tt) {
-        if (!cluster_wait_rows(bbar, sr + 1, sr + 2, C, rank, kSpinLimit, abort_flag, status, &s_ok)) {
-          ok = false;
-          break;
-        }
-#pragma unroll
-        for (int b = 0; b < R; ++b)
-          if (b < nr)
-#pragma unroll
-            for (int c = 0; c < R; ++c)
-              if (n0 + c < n1)
-#pragma unroll
-                for (int q = 0; q < CP::RPC; ++q)
-                  sacc[b] += nextp[b][c].v[q] * zt[(n0 + c) * NB + ch * CP::RPC + q];
-      }
-#pragma unroll
-      for (int b = 0; b < R; ++b) {
-        if (b >= nr) break;
-        part[ch * NB + a] = sacc[b];
-        __syncthreads();
-        if (tid < NB) {
-          T t = T(0);
-#pragma unroll
-          for (int c = 0; c < CP::CH; ++c) t += part[c * NB + tid];
-          acc[b][tid] = y[(i0 + b) * NB + tid] - t;
-        }
-        __syncthreads();
-      }
-      // rows of the super-row from the last (R <= 2: row i0 needs only z_{i0+1})
-#pragma unroll
-      for (int bb = R - 1; bb >= 0; --bb) {
-        if (bb >= nr) continue;
-        if (tid < NB) out[tid] = T(0);
-        __syncthreads();
-        if (bb + 1 < nr) {
-          intra[bb].apply(zt + (i0 + R - 1) * NB, acc[bb], T(-1), part);
-          __syncthreads();
-        }
-        wp[bb].apply(acc[bb], out, T(1), part);
-        __syncthreads();
-        if (tid < NB) {
-          zt[(i0 + bb) * NB + tid] = out[tid];
-          z[(i0 + bb) * NB + tid] = (double)out[tid];
-        }
-      }
-      if (tid < NB) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid < C && tid != rank) {
-        const uint32_t src = smem_u32(zt + i0 * NB);
-        bulk_copy_to(map_to_rank(src, tid), src, nr * NB * sizeof(T),
-                     map_to_rank(smem_u32(&bbar[sr]), tid));
-      }
+    if (!ok) break;
+    if (i > 0) {
+      if ((i - 1) % C != rank) thread_wait_row(&fbar[i - 1], abort_flag, status);
+      s += row_dot<T, NB>(lastp, y + (i - 1) * NB);
     }
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
+    if (sub == 0) acc[r] = (T)v[i * NB + r] - s;
+    __syncthreads();
+    T w = row_dot<T, NB>(wp, acc);
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o, TPR);
+    if (sub == 0) {
+      y[i * NB + r] = w;
+      const uint32_t la = smem_u32(y + i * NB + r), lb = smem_u32(&fbar[i]);
+      for (int d = 0; d < C; ++d)
+        if (d != rank) st_async_peer(map_to_rank(la, d), w, map_to_rank(lb, d));
+    }
+    __syncthreads();
   }
-  // wait for every copy addressed to this CTA before leaving (briefly when a
+  // backward: z_i = W_i^T (y_i - sum_{j>i} L_ji^T z_j); column sums meet in
+  // shared memory (one barrier each)
+  const int a = tid % NB, ch = tid / NB;
+  const int last = Tt - 1 - ((Tt - 1 - rank) % C + C) % C;   // largest i = rank (mod C)
+  for (int i = last; ok && i >= 0; i -= C) {
+    TP wp, nextp;
+    wp.load(winv + (size_t)i * NB * NB, NB);
+    if (i + 1 < Tt) nextp.load(L + (size_t)(i + 1) * NB * P + (size_t)i * NB, P);
+    T s = T(0);
+    for (int j = Tt - 1; j > i + 1; j -= kSolveBatch) {   // rows > i+1, batches in flight
+      const int nj = min(kSolveBatch, j - i - 1);         // tiles j, j-1, .., j-nj+1
+      TP bp[kSolveBatch];
+#pragma unroll
+      for (int u = 0; u < kSolveBatch; ++u)
+        if (u < nj) bp[u].load(L + (size_t)(j - u) * NB * P + (size_t)i * NB, P);
+      if (!cluster_wait_rows(bbar, j - nj + 1, j + 1, C, rank, kSpinLimit, abort_flag, status,
+                             &s_ok)) {
+        ok = false;
+        break;
+      }
+#pragma unroll
+      for (int u = 0; u < kSolveBatch; ++u)
+        if (u < nj) s += bp[u].dot(zt + (j - u) * NB);
+    }
+    if (!ok) break;
+    if (i + 1 < Tt) {
+      if ((i + 1) % C != rank) thread_wait_row(&bbar[i + 1], abort_flag, status);
+      s += nextp.dot(zt + (i + 1) * NB);
+    }
+    part[ch * NB + a] = s;
+    __syncthreads();
+    if (tid < NB) {
+      T t = T(0);
+#pragma unroll
+      for (int c = 0; c < TP::CH; ++c) t += part[c * NB + tid];
+      acc[tid] = y[i * NB + tid] - t;
+    }
+    __syncthreads();
+    part[ch * NB + a] = wp.dot(acc);
+    __syncthreads();
+    if (tid < NB) {
+      T w = T(0);
+#pragma unroll
+      for (int c = 0; c < TP::CH; ++c) w += part[c * NB + tid];
+      zt[i * NB + tid] = w;
+      z[i * NB + tid] = (double)w;
+      const uint32_t la = smem_u32(zt + i * NB + tid), lb = smem_u32(&bbar[i]);
+      for (int d = 0; d < C; ++d)
+        if (d != rank) st_async_peer(map_to_rank(la, d), w, map_to_rank(lb, d));
+    }
+    __syncthreads();
+  }
+  // wait for every store addressed to this CTA before leaving (briefly when a
   // wait already ran out: the rows still missing will not come)
   const unsigned drain = ok ? kSpinLimit : (kSpinLimit >> 8);
-  cluster_wait_rows(fbar, 0, ST, C, rank, drain, abort_flag, status, &s_ok);
-  cluster_wait_rows(bbar, 0, ST, C, rank, drain, abort_flag, status, &s_ok);
-  cl.sync();   // no CTA leaves while others may still read its shared memory
+  cluster_wait_rows(fbar, 0, Tt, C, rank, drain, abort_flag, status, &s_ok);
+  cluster_wait_rows(bbar, 0, Tt, C, rank, drain, abort_flag, status, &s_ok);
+  cl.sync();   // no CTA leaves while others may still store into its shared memory
 }
 
 template <typename T>
