@@ -719,9 +719,9 @@ def main():
     ap.add_argument("--ws-batch", type=int, default=8)
     ap.add_argument("--ws-lr", type=float, default=1e-3)
     ap.add_argument("--ws-verbose", action="store_true")
-    ap.add_argument("--factor-ctas-per-sm", type=int, default=0,
+    ap.add_argument("--factor-ctas-per-sm", type=int, default=2,
                     help="persistent factorisation CTAs per SM (0: library default)")
-    ap.add_argument("--lookahead", type=int, default=3,
+    ap.add_argument("--lookahead", type=int, default=6,
                     help="steps the geometry chain runs ahead in the chosen form (0: one chain)")
     ap.add_argument("--batch-steps", type=int, default=5,
                     help="timed steps of the 96-problem batched block (0: skip it)")

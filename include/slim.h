@@ -128,7 +128,7 @@ typedef struct {
  *   ctas_per_sm   resident CTAs per SM of the persistent factorisation (1..4,
  *                 0 = default: 2, or 1 with lookahead, where the D factorisations
  *                 in flight share these CTAs, num_SMs * ctas_per_sm / D each)
- *   lookahead     0: each step runs as one chain.  D = 1..3 (view blocks, 2D,
+ *   lookahead     0: each step runs as one chain.  D = 1..6 (view blocks, 2D,
  *                 rows from the projector): the matrix lambda_k I + M_k M_k^T of
  *                 Eq. (B_k) depends only on the blocks drawn, so the chain that
  *                 draws tau_j, adds its Gram rows and factors K_j runs up to D

@@ -15,7 +15,7 @@
 
 using namespace slim;
 
-constexpr int kMaxBuf = 4;   // lookahead D <= 3: D+1 factor buffers
+constexpr int kMaxBuf = 7;   // lookahead D <= 6: D+1 factor buffers
 
 struct slim_ctx {
   // configuration
@@ -840,10 +840,6 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       {(void**)&c->d_map_w, use_map ? 2 * (size_t)c->n * sizeof(double) : 0},
       {(void**)&c->d_G, g_elems * sizeof(double)},
       {&c->d_L, dense_solve && !la ? (size_t)c->P * c->P * fs : 0},
-      {&c->d_Lb[0], la ? (size_t)c->P * c->P * fs : 0},
-      {&c->d_Lb[1], la ? (size_t)c->P * c->P * fs : 0},
-      {&c->d_Lb[2], la && c->nbuf > 2 ? (size_t)c->P * c->P * fs : 0},
-      {&c->d_Lb[3], la && c->nbuf > 3 ? (size_t)c->P * c->P * fs : 0},
       {(void**)&c->d_gdone, la ? sizeof(long long) : 0},
       {(void**)&c->d_info_buf, la ? c->nbuf * sizeof(StepInfo) : 0},
       {(void**)&c->d_ext, la ? (size_t)c->nbuf * c->P * sizeof(int) : 0},
@@ -872,6 +868,8 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     if (dense_solve && !la) chk(cudaMemset(c->d_L, 0, (size_t)c->P * c->P * fs), "memset");
     chk(cudaMemset(c->d_z, 0, (size_t)c->P * sizeof(double)), "memset");
     if (la) {
+      for (int b = 0; b < c->nbuf && st == SLIM_OK; ++b)
+        chk(cudaMalloc(&c->d_Lb[b], (size_t)c->P * c->P * fs), "cudaMalloc");
       chk(cudaMemset(c->d_gdone, 0, sizeof(long long)), "memset");
       chk(cudaMemset(c->d_info_buf, 0, c->nbuf * sizeof(StepInfo)), "memset");
       // up to D factorisations run at once next to the iterate chain: together

@@ -28,7 +28,7 @@ def _problem(N=32, V=20, D=47, seed=7):
     return g, b
 
 
-@pytest.mark.parametrize("D,ramp", [(1, False), (2, True), (3, False)])
+@pytest.mark.parametrize("D,ramp", [(1, False), (2, True), (3, False), (6, False)])
 def test_trajectory_fp64(sl, D, ramp):
     g, b = _problem()
     r, lam, seed, steps = 3, 1e-2, 7, 11
@@ -116,7 +116,7 @@ def test_unsupported_combinations(sl):
     with pytest.raises(sl.SlimError):
         sl.Slim(32, 20, 47, 20, 2, 1e-2, 1, kind=sl.SLIM_BLOCKS_RAYS, lookahead=1)
     with pytest.raises(sl.SlimError):
-        sl.Slim(32, 20, 47, 47, 2, 1e-2, 1, lookahead=4)
+        sl.Slim(32, 20, 47, 47, 2, 1e-2, 1, lookahead=7)
     with pytest.raises(sl.SlimError):
         sl.SlimBatch([dict(N=24, n_views=18, det=35, ell=35, r=2, lam=1e-2, seed=1, kind=0,
                            lookahead=1)])
