@@ -279,7 +279,7 @@ def traffic_from_profiles(kernel):
     return rec["bytes"] if h.hexdigest() == rec["sha256"] else None
 
 
-def tta_block(sl, cfg, b, flush, stream, epochs, thresholds, lookahead=0):
+def tta_block(sl, cfg, b, flush, stream, epochs, thresholds, lookahead=0, ctas_per_sm=0):
     """Time to relative error thresholds vs the reference iterate."""
     import torch
     M = cfg.n_views
@@ -289,7 +289,8 @@ def tta_block(sl, cfg, b, flush, stream, epochs, thresholds, lookahead=0):
     res = {}
     x_ref = None
     for form in ("plain", "chosen"):
-        s = make_form(sl, cfg, form, cfg.seed, lookahead=lookahead if form == "chosen" else 0)
+        s = make_form(sl, cfg, form, cfg.seed, lookahead=lookahead if form == "chosen" else 0,
+                      ctas_per_sm=ctas_per_sm if form == "chosen" else 0)
         s.set_data(b if form == "plain" else b.astype(np.float32))
         if form == "chosen" and lookahead:
             per, _, snaps = timed_region(s, steps, 0, flush, stream, snapshot_every=every)
@@ -518,11 +519,11 @@ def warm_start_block(args):
             "steps_to_threshold": ws.summarize(recs, thresholds)}
 
 
-def e2e_block(sl, cfg, b, K, W, lookahead=0):
+def e2e_block(sl, cfg, b, K, W, lookahead=0, ctas_per_sm=0):
     """Same metric through the C ABI with host buffers: each step copies b from
     pinned host memory, steps, and reads x back to pinned host memory."""
     import torch
-    s = make_form(sl, cfg, "chosen", cfg.seed, lookahead=lookahead)
+    s = make_form(sl, cfg, "chosen", cfg.seed, lookahead=lookahead, ctas_per_sm=ctas_per_sm)
     bh = torch.tensor(b.astype(np.float32)).pin_memory()
     xh = torch.empty(cfg.n, dtype=torch.float32).pin_memory()
     s.set_data(bh)
@@ -625,8 +626,10 @@ def main_gpu(args):
     tta = None
     if args.tta_epochs > 0 and rank == 0:
         tta = tta_block(sl, cfg, b, flush, stream, args.tta_epochs,
-                        [0.5, 0.2, 0.1, 0.05, 0.02, 0.01], lookahead=args.lookahead)
-    e2e = (e2e_block(sl, cfg, b, args.steps, args.warmup, lookahead=args.lookahead)
+                        [0.5, 0.2, 0.1, 0.05, 0.02, 0.01], lookahead=args.lookahead,
+                        ctas_per_sm=args.factor_ctas_per_sm)
+    e2e = (e2e_block(sl, cfg, b, args.steps, args.warmup, lookahead=args.lookahead,
+                     ctas_per_sm=args.factor_ctas_per_sm)
            if rank == 0 and not args.no_e2e else None)
     csr_pass = csr_block(sl, cfg, flush, stream) if rank == 0 and not args.no_csr else None
     s3d = stream3d_block(sl, flush, stream, args.steps, args.warmup) if rank == 0 and not args.no_3d else None
