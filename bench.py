@@ -463,6 +463,79 @@ def batch_block(sl, flush, stream, K, W, count=96):
             "autotune": {"choices_tile_x_ctas": choices, "seconds": tune_s}}
 
 
+def measured_peaks():
+    """The measured peaks of this GPU model (MEASURED_PEAKS.json), or {}."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return {}
+
+
+def unet_flops(sl, n1):
+    """Multiply-add flops (x2) of one image through the network with n1 pixels
+    at full resolution: each weight is used once per output pixel (conv) or
+    per input pixel (tconv).  The training step adds the weight gradient (the
+    same contraction) and the input gradient (the same, except for the first
+    layer, whose input needs none)."""
+    px = {"enc1a": n1, "enc1b": n1, "enc2a": n1 // 4, "enc2b": n1 // 4, "enc3a": n1 // 16,
+          "enc3b": n1 // 16, "bota": n1 // 64, "botb": n1 // 64, "up3": n1 // 64, "dec3a": n1 // 16,
+          "dec3b": n1 // 16, "up2": n1 // 16, "dec2a": n1 // 4, "dec2b": n1 // 4, "up1": n1 // 4,
+          "dec1a": n1, "dec1b": n1, "out": n1}
+    per = {name: 2 * int(np.prod(shape)) * px[name] for name, shape, _ in sl.UNET_LAYERS}
+    fwd = sum(per.values())
+    return {"forward": fwd, "train": 3 * fwd - per["enc1a"]}
+
+
+def unet_block(sl, flush, stream, reps=10, batch=8):
+    """The network alone on the 256 x 256 grid with random weights: one
+    forward pass of one image, and one training step (forward, backward, Adam)
+    of `batch` images, each timed with events on the launching stream after an
+    L2 flush.  Flops are the network's own (see unet_flops); the tensor cores
+    execute 3x as many for the float32-accurate operands."""
+    import torch
+    import workloads
+    N = workloads.C2.N
+    net = sl.UNet(N, N, max_batch=batch)
+    net.set_params(sl.flatten_params(workloads.unet_init(0, sl.UNET_LAYERS)))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(batch * N * N, device="cuda", generator=g)
+    t = torch.randn(batch * N * N, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    sp = stream.cuda_stream
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        tot = 0.0
+        for i in range(reps):
+            flush.fill_(i)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / reps
+
+    with torch.cuda.stream(stream):
+        f_ms = timed(lambda: net.forward(x[:N * N], y[:N * N], sp))
+        t_ms = timed(lambda: net.train_step(x, t, 1e-4, sp))
+    net.close()
+    fl = unet_flops(sl, N * N)
+    peak = measured_peaks().get("bf16_tflops")
+    f_tf = fl["forward"] / f_ms * 1e-9
+    t_tf = batch * fl["train"] / t_ms * 1e-9
+    return {"grid": f"{N}x{N}", "forward_ms": f_ms, "forward_gflop": fl["forward"] * 1e-9,
+            "forward_tflops": f_tf, "train_batch": batch, "train_step_ms": t_ms,
+            "train_gflop": batch * fl["train"] * 1e-9, "train_tflops": t_tf,
+            "train_images_per_s": batch / t_ms * 1e3,
+            "bf16_peak_tflops": peak, "forward_frac_of_measured_bf16": f_tf / peak if peak else None,
+            "note": ("implicit-GEMM convolutions on mma.sync bfloat16 tensor cores; activations as "
+                     "3 bfloat16 terms (weight gradients 2 x 2), so the pipe executes 3x the flops "
+                     "counted here; L2 flushed before each timed call")}
+
+
 def warm_start_block(args):
     """Learned initial guess on the 256x256 workload: pairs from the method,
     training of the U-Net in the library's kernels, held-out steps to relative
@@ -499,13 +572,7 @@ def warm_start_block(args):
     thresholds = [0.5, 0.3, 0.2, 0.15, 0.1]
     recs, t_ws = ws.evaluate(net, cfg, test, s_in, args.ws_eval_epochs, thresholds, torch, log=log)
     net.close()
-    # each weight is used once per output pixel (conv) or per input pixel (tconv)
-    n1 = cfg.n
-    px = {"enc1a": n1, "enc1b": n1, "enc2a": n1 // 4, "enc2b": n1 // 4, "enc3a": n1 // 16,
-          "enc3b": n1 // 16, "bota": n1 // 64, "botb": n1 // 64, "up3": n1 // 64, "dec3a": n1 // 16,
-          "dec3b": n1 // 16, "up2": n1 // 16, "dec2a": n1 // 4, "dec2b": n1 // 4, "up1": n1 // 4,
-          "dec1a": n1, "dec1b": n1, "out": n1}
-    fwd_gflop = 2e-9 * sum(int(np.prod(shape)) * px[name] for name, shape, _ in sl.UNET_LAYERS)
+    fwd_gflop = unet_flops(sl, cfg.n)["forward"] * 1e-9
     return {"train_seeds": len(train), "test_seeds": len(test),
             "target": f"chosen-form iterate after {args.ws_target_epochs} epochs from x0=0",
             "error": "relative error to x_true (the phantom), checked every 6 steps",
@@ -636,6 +703,7 @@ def main_gpu(args):
     batch = (batch_block(sl, flush, stream, args.batch_steps, max(3, args.warmup))
              if rank == 0 and args.batch_steps > 0 else None)
     warm = warm_start_block(args) if rank == 0 and args.warm_start else None
+    unet = unet_block(sl, flush, stream) if rank == 0 and not args.no_unet else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         leg = run_cpu_leg(args)
@@ -671,7 +739,7 @@ def main_gpu(args):
         "phases_note": ("one step at a time (synchronous pass); the pipelined region overlaps "
                         "the geometry phases with the iterate chain" if args.lookahead else
                         "per step, inside the timed region"),
-        "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "batched": batch, "warm_start": warm, "tta": tta, "e2e": e2e,
+        "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "batched": batch, "unet": unet, "warm_start": warm, "tta": tta, "e2e": e2e,
         "cpu_baseline": cpu,
         "gpu_launches": kernels * args.steps, "kernels_per_step": kernels, "clocks": clocks,
     }
@@ -712,6 +780,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-csr", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--no-unet", action="store_true")
     ap.add_argument("--warm-start", action="store_true",
                     help="train and evaluate the learned initial guess (minutes of GPU time)")
     ap.add_argument("--ws-train", type=int, default=256)

@@ -324,6 +324,39 @@ slim_status slim_unet_forward(slim_unet* net, const float* x, float* y, int n, v
  * *loss (if not NULL) receives the loss; the call then synchronises. */
 slim_status slim_unet_train_step(slim_unet* net, const float* x, const float* target, int n,
                                  float lr, double* loss, void* cuda_stream);
+/* The network's layers on their own, as used by forward and train_step.
+ * Device float32 arrays in the network's layout: channel c of image i,
+ * pixel (y, x) at [c][i][y][x], i.e. c * n*H*W + i * H*W + y * W + x.
+ * Asynchronous on `cuda_stream`; no allocation.  Weights are read as
+ * bfloat16 (nearest even), which leaves the network's rounded weights
+ * unchanged; activations and gradients keep float32 accuracy (they enter the
+ * bfloat16 tensor cores as sums of bfloat16 terms) and accumulation is
+ * float32.  SLIM_EINVAL for a NULL required pointer, a size < 1, more than
+ * 65536 channels or 4 n H W >= 2^31; SLIM_ECUDA if a launch fails.
+ *
+ * 3x3 convolution, stride 1, zero padding 1: w [c_out][c_in][3][3], b [c_out]
+ * (NULL: zero), x [c_in][n][H][W], y [c_out][n][H][W] = conv(x, w) + b, then
+ * max(y, 0) when relu != 0. */
+slim_status slim_unet_conv3x3(const float* x, int n, int c_in, int H, int W, const float* w,
+                              const float* b, int c_out, int relu, float* y, void* cuda_stream);
+/* Gradients of that convolution for dy [c_out][n][H][W], the gradient at
+ * conv(x, w) + b (before any ReLU): dw [c_out][c_in][3][3] += dL/dw and
+ * db [c_out] += dL/db (accumulated; db may be NULL); dx [c_in][n][H][W] =
+ * dL/dx, overwritten (skipped when NULL). */
+slim_status slim_unet_conv3x3_grad(const float* x, const float* dy, int n, int c_in, int H, int W,
+                                   const float* w, int c_out, float* dw, float* db, float* dx,
+                                   void* cuda_stream);
+/* 2x2 transposed convolution, stride 2: w [c_in][c_out][2][2], b [c_out]
+ * (NULL: zero), x [c_in][n][H][W], y [c_out][n][2H][2W] with
+ * y[o][i][2r+u][2q+v] = sum_c w[c][o][u][v] x[c][i][r][q] + b[o]. */
+slim_status slim_unet_tconv2x2(const float* x, int n, int c_in, int H, int W, const float* w,
+                               const float* b, int c_out, float* y, void* cuda_stream);
+/* Its gradients for dy [c_out][n][2H][2W]: dw += dL/dw, db += dL/db
+ * (accumulated; db may be NULL), dx [c_in][n][H][W] = dL/dx (skipped when
+ * NULL). */
+slim_status slim_unet_tconv2x2_grad(const float* x, const float* dy, int n, int c_in, int H, int W,
+                                    const float* w, int c_out, float* dw, float* db, float* dx,
+                                    void* cuda_stream);
 /* Warm start of a 2D context: x_0 = s_out * U-Net(s_in * A^T b) with the
  * context's data b (N x N network).  If ||A x_0 - b|| >= ||b|| the network's
  * guess is worse than zero and x is set to 0 instead.  *used = 1 when x_0

@@ -4,10 +4,12 @@
 //
 // Layout: activations are channel-major over the batch, C x (n*H*W) float32
 // ("CNHW"), so every layer is one GEMM:
-//   conv3x3    Y = W col(X) + b        col = im2col of X (K = 9 C_in rows)
-//              dW += dY col(X)^T,  dX = col2im(W^T dY)
+//   conv3x3    Y = W col(X) + b        col = im2col of X (K = 9 C_in rows),
+//              dW += dY col(X)^T,  dX = Wf col(dY)   (Wf: the adjoint conv's weights)
+//              implicit GEMMs: col is gathered into shared memory, never stored
 //   tconv2x2   Y4 = W^T X (rows (o,u,v)), scattered to the 2x upsampled grid
-//              dW += X dY4^T,  dX = W dY4   (dY4 gathered from dY)
+//              dW += X dY4^T,  dX = W dY4   (dY4 gathered from dY); the
+//              scatter is the GEMM's epilogue and the gather its loaders
 //   conv1x1    Y = W X + b
 // The decoder's concatenation [upsampled; skip] is one buffer whose lower
 // channel rows are written by the encoder directly.  Weights used by the
@@ -17,6 +19,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -127,58 +130,417 @@ cudaError_t gemm(int M, int N, int K, const float* A, int lda, const float* B, i
   return cudaGetLastError();
 }
 
-// Split-K factor for the weight gradients (long reductions over pixels).
+
+// ---------------------------------------------------------------------------
+// Tensor-core GEMM (mma.sync m16n8k16, bfloat16 operands, float32
+// accumulation) with operand loaders, so that the 3x3 convolutions run as
+// implicit GEMMs: the im2col matrix is gathered tile by tile from the
+// activations into shared memory and never written out.
+//
+//   C[m][n] (+)= sum_k A(m, k) B(n, k)  (+ bias[m]) (ReLU)
+//
+// Float32 values reach the bfloat16 pipe as a sum of T bfloat16 terms,
+// x = x_0 + x_1 + ... with x_j = bf16(x - x_0 - ... - x_{j-1}) (nearest
+// even).  T = 3 carries 24 significant bits, i.e. the float32 value itself
+// (up to the last bit); T = 2 carries 16.  The weights used by the network
+// are bfloat16 values already (T = 1).  The products x_i y_j with
+// i + j < max(TA, TB) are accumulated, which drops only terms below the
+// float32 rounding of the sum (T = 3 x 1) or below 2^-16 relative (2 x 2).
+//
+// CTA tile BM x 128 x 32, 8 warps; each operand tile is stored per term as
+// rows of 32 bfloat16 (64 bytes, four 16-byte chunks, chunk c of row r at
+// c ^ ((r >> 1) & 3)) so that both the 16-byte stores of the staging and the
+// ldmatrix reads of the fragments are free of bank conflicts.  Two stages:
+// the next k-slab is loaded into registers while the current one is
+// multiplied.  With gridDim.z > 1 the k range is split and the partial sums
+// are added atomically into C.
+// ---------------------------------------------------------------------------
+constexpr int kTcBN = 128, kTcBK = 32;
+
+// C[m][n] = acc (+ bias[m]) (+ C[m][n]) (ReLU); atomically added when split.
+struct OutPlain {
+  float* C;
+  long long ldc;
+  int M, N;
+  const float* bias;
+  int relu, accumulate;
+  __device__ void store(int m, int n, float v, bool split) const {
+    float* c = C + (size_t)m * ldc + n;
+    if (split) {
+      atomicAdd(c, v);
+      return;
+    }
+    if (bias) v += bias[m];
+    if (accumulate) v += *c;
+    if (relu) v = fmaxf(v, 0.f);
+    *c = v;
+  }
+};
+
+// 2x2 stride-2 transposed conv: row m = o*4 + u*2 + v, column n = input pixel
+// (global image row R = n / W, column x); the value lands at output
+// Y[o][2R+u][2x+v] (images stacked along R) plus bias[o].  Never split.
+struct OutUp {
+  float* Y;
+  long long Pout;
+  int M, N, W;
+  const float* bias;
+  __device__ void store(int m, int n, float v, bool) const {
+    const int o = m >> 2, u = (m >> 1) & 1, vv = m & 1;
+    const int R = n / W, x = n - R * W;
+    Y[(size_t)o * Pout + (size_t)(2 * R + u) * (2 * W) + 2 * x + vv] = v + (bias ? bias[o] : 0.f);
+  }
+};
+
+// A(row, k) = p[row * ld + k]
+struct LoadRowK {
+  const float* p;
+  long long ld;
+  int rows;
+  struct Row { const float* ptr; };
+  __device__ Row row(int r) const { return {r < rows ? p + (size_t)r * ld : nullptr}; }
+  __device__ void load8(const Row& c, int k, int kend, float (&v)[8]) const {
+    if (c.ptr && k + 8 <= kend && (reinterpret_cast<uintptr_t>(c.ptr + k) & 15) == 0) {
+      const float4 a = *reinterpret_cast<const float4*>(c.ptr + k);
+      const float4 b = *reinterpret_cast<const float4*>(c.ptr + k + 4);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+      v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+      return;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = (c.ptr && k + i < kend) ? c.ptr[k + i] : 0.f;
+  }
+};
+
+// A(row, k) = p[k * ld + row]
+struct LoadKRow {
+  const float* p;
+  long long ld;
+  int rows;
+  struct Row { const float* ptr; };
+  __device__ Row row(int r) const { return {r < rows ? p + r : nullptr}; }
+  __device__ void load8(const Row& c, int k, int kend, float (&v)[8]) const {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = (c.ptr && k + i < kend) ? c.ptr[(size_t)(k + i) * ld] : 0.f;
+  }
+};
+
+// Rows are pixels p of X (C x P, n images of H x W), k = c*9 + u*3 + v:
+// A(p, k) = X[c][img, y+u-1, x+v-1], zero outside the image.
+struct LoadPixTap {
+  const float* X;
+  long long P;
+  int H, W;
+  struct Row { long long p; int y, x; };
+  __device__ Row row(int r) const {
+    if (r >= P) return {-1, 0, 0};
+    const int rem = (int)(r % ((long long)H * W));
+    return {r, rem / W, rem % W};
+  }
+  __device__ void load8(const Row& c, int k, int kend, float (&v)[8]) const {
+    int ch = k / 9, t = k - 9 * ch;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float val = 0.f;
+      if (c.p >= 0 && k + i < kend) {
+        const int du = t / 3 - 1, dv = t % 3 - 1;
+        const int yy = c.y + du, xx = c.x + dv;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+          val = X[(size_t)ch * P + c.p + (long long)du * W + dv];
+      }
+      v[i] = val;
+      if (++t == 9) { t = 0; ++ch; }
+    }
+  }
+};
+
+// Rows are taps r = c*9 + u*3 + v, k = pixel p of X:
+// A(r, p) = X[c][img, y+u-1, x+v-1], zero outside the image.
+struct LoadTapPix {
+  const float* X;
+  long long P;
+  int H, W, rows;
+  struct Row { long long base; int du, dv; };
+  __device__ Row row(int r) const {
+    if (r >= rows) return {-1, 0, 0};
+    const int ch = r / 9, t = r % 9;
+    return {(long long)ch * P, t / 3 - 1, t % 3 - 1};
+  }
+  __device__ void load8(const Row& c, int k, int kend, float (&v)[8]) const {
+    const int HW = H * W;
+    int rem = (int)(k % HW);
+    int y = rem / W, x = rem % W;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float val = 0.f;
+      if (c.base >= 0 && k + i < kend) {
+        const int yy = y + c.du, xx = x + c.dv;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+          val = X[c.base + k + i + (long long)c.du * W + c.dv];
+      }
+      v[i] = val;
+      if (++x == W) { x = 0; if (++y == H) y = 0; }
+    }
+  }
+};
+
+// Weights of the adjoint 3x3 conv read in place from W [C_out][C_in][3][3]:
+// A(c, k = o*9 + t) = W[o][c][8 - t].
+struct LoadFlipW {
+  const float* W;
+  int Ci;
+  struct Row { int c; };
+  __device__ Row row(int r) const { return {r < Ci ? r : -1}; }
+  __device__ void load8(const Row& c, int k, int kend, float (&v)[8]) const {
+    int o = k / 9, t = k - 9 * o;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      v[i] = (c.c >= 0 && k + i < kend) ? W[((size_t)o * Ci + c.c) * 9 + 8 - t] : 0.f;
+      if (++t == 9) { t = 0; ++o; }
+    }
+  }
+};
+
+// Rows are input pixels p of a 2x2 stride-2 transposed conv (global image
+// row R = p / W, column x), k = o*4 + u*2 + v: A(p, k) = dY[o][2R+u][2x+v].
+struct LoadUpPix {
+  const float* dY;
+  long long Pout;
+  int W, rows;
+  struct Row { long long base; };
+  __device__ Row row(int r) const {
+    if (r >= rows) return {-1};
+    const int R = r / W, x = r - R * W;
+    return {(long long)(2 * R) * (2 * W) + 2 * x};
+  }
+  __device__ void load8(const Row& c, int k, int kend, float (&v)[8]) const {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int kk = k + i;
+      v[i] = (c.base >= 0 && kk < kend)
+                 ? dY[(size_t)(kk >> 2) * Pout + c.base + ((kk >> 1) & 1) * (2 * W) + (kk & 1)]
+                 : 0.f;
+    }
+  }
+};
+
+// Rows are taps r = o*4 + u*2 + v, k = input pixel p (R = p / W, x):
+// A(r, p) = dY[o][2R+u][2x+v].
+struct LoadUpTapPix {
+  const float* dY;
+  long long Pout;
+  int W, rows;
+  struct Row { long long base; int u, v; };
+  __device__ Row row(int r) const {
+    if (r >= rows) return {-1, 0, 0};
+    return {(long long)(r >> 2) * Pout, (r >> 1) & 1, r & 1};
+  }
+  __device__ void load8(const Row& c, int k, int kend, float (&v)[8]) const {
+    int R = k / W, x = k - R * W;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      v[i] = (c.base >= 0 && k + i < kend)
+                 ? dY[c.base + (long long)(2 * R + c.u) * (2 * W) + 2 * x + c.v]
+                 : 0.f;
+      if (++x == W) { x = 0; ++R; }
+    }
+  }
+};
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                               uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t bf16_pair(float lo, float hi) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
+// Split 8 float32 values into T bfloat16 terms and store each term's 16
+// bytes at its swizzled place (row r, chunk kg) of the term's tile.
+template <int T>
+__device__ __forceinline__ void stage_terms(unsigned char* tile0, int tile_bytes, int r, int kg,
+                                            float (&v)[8]) {
+  const int off = r * 64 + ((kg ^ ((r >> 1) & 3)) << 4);
+#pragma unroll
+  for (int j = 0; j < T; ++j) {
+    float h[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      h[i] = __bfloat162float(__float2bfloat16_rn(v[i]));
+      if (j + 1 < T) v[i] -= h[i];
+    }
+    uint4 w;
+    w.x = bf16_pair(h[0], h[1]);
+    w.y = bf16_pair(h[2], h[3]);
+    w.z = bf16_pair(h[4], h[5]);
+    w.w = bf16_pair(h[6], h[7]);
+    *reinterpret_cast<uint4*>(tile0 + j * tile_bytes + off) = w;
+  }
+}
+
+template <class LA, class LB, class OUT, int BM, int TA, int TB>
+__global__ void __launch_bounds__(kT) tc_gemm_kernel(OUT out, LA la, LB lb, int K, int kchunk) {
+  constexpr int WMW = BM >= 64 ? 2 : 1, WNW = 8 / WMW;   // warps along M, N
+  constexpr int WTM = BM / WMW, WTN = kTcBN / WNW;        // warp tile
+  constexpr int MT = WTM / 16, NT = WTN / 8;
+  static_assert(MT >= 1 && NT % 2 == 0, "warp tile");
+  constexpr int A_BYTES = BM * 64, B_BYTES = kTcBN * 64;
+  constexpr int STAGE = A_BYTES * TA + B_BYTES * TB;
+  constexpr int TMAX = TA > TB ? TA : TB;
+  constexpr int GA = (BM * 4 + kT - 1) / kT, GB = (kTcBN * 4) / kT;   // 8-k groups per thread
+  extern __shared__ __align__(128) unsigned char tc_smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = warp % WMW, wn = warp / WMW;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * kTcBN;
+  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+  const int ra = tid % BM, rb = tid % kTcBN;
+  const typename LA::Row rowA = la.row(m0 + ra);
+  const typename LB::Row rowB = lb.row(n0 + rb);
+  float va[GA][8], vb[GB][8];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int i = 0; i < GA; ++i) {
+      const int kg = tid / BM + i * (kT / BM);
+      if (kg < 4) la.load8(rowA, k0 + kg * 8, kend, va[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < GB; ++i) lb.load8(rowB, k0 + (tid / kTcBN + i * 2) * 8, kend, vb[i]);
+  };
+  auto stage = [&](int s) {
+    unsigned char* base = tc_smem + s * STAGE;
+#pragma unroll
+    for (int i = 0; i < GA; ++i) {
+      const int kg = tid / BM + i * (kT / BM);
+      if (kg < 4) stage_terms<TA>(base, A_BYTES, ra, kg, va[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < GB; ++i)
+      stage_terms<TB>(base + TA * A_BYTES, B_BYTES, rb, tid / kTcBN + i * 2, vb[i]);
+  };
+  float acc[MT][NT][4];
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+  const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(tc_smem);
+  int cur = 0;
+  if (kbeg < kend) {
+    fetch(kbeg);
+    stage(0);
+  }
+  __syncthreads();
+  for (int k0 = kbeg; k0 < kend; k0 += kTcBK) {
+    const bool more = k0 + kTcBK < kend;
+    if (more) fetch(k0 + kTcBK);
+    const uint32_t sA = smem0 + cur * STAGE, sB = sA + TA * A_BYTES;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {   // two k16 steps per slab
+      uint32_t af[TA][MT][4], bf[TB][NT][2];
+#pragma unroll
+      for (int j = 0; j < TA; ++j)
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+          const int r = wm * WTM + mt * 16 + (lane & 15);
+          const int ch = kk * 2 + (lane >> 4);
+          ldsm_x4(af[j][mt], sA + j * A_BYTES + r * 64 + ((ch ^ ((r >> 1) & 3)) << 4));
+        }
+#pragma unroll
+      for (int j = 0; j < TB; ++j)
+#pragma unroll
+        for (int nt = 0; nt < NT; nt += 2) {
+          const int r = wn * WTN + nt * 8 + (lane & 7) + ((lane >> 4) << 3);
+          const int ch = kk * 2 + ((lane >> 3) & 1);
+          uint32_t q[4];
+          ldsm_x4(q, sB + j * B_BYTES + r * 64 + ((ch ^ ((r >> 1) & 3)) << 4));
+          bf[j][nt][0] = q[0]; bf[j][nt][1] = q[1];
+          bf[j][nt + 1][0] = q[2]; bf[j][nt + 1][1] = q[3];
+        }
+#pragma unroll
+      for (int i = 0; i < TA; ++i)
+#pragma unroll
+        for (int j = 0; j < TB; ++j) {
+          if (i + j >= TMAX) continue;
+#pragma unroll
+          for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(acc[mt][nt], af[i][mt], bf[j][nt][0], bf[j][nt][1]);
+        }
+    }
+    if (more) stage(cur ^ 1);
+    __syncthreads();
+    cur ^= 1;
+  }
+  const bool split = gridDim.z > 1;
+  const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int m = m0 + wm * WTM + mt * 16 + g + (e >> 1) * 8;
+        const int n = n0 + wn * WTN + nt * 8 + 2 * t4 + (e & 1);
+        if (m < out.M && n < out.N) out.store(m, n, acc[mt][nt][e], split);
+      }
+}
+
+template <int BM, int TA, int TB, class OUT, class LA, class LB>
+cudaError_t tc_launch_bm(const OUT& o, int K, LA la, LB lb, int splits, cudaStream_t s) {
+  constexpr int smem = 2 * (BM * 64 * TA + kTcBN * 64 * TB);
+  auto kern = tc_gemm_kernel<LA, LB, OUT, BM, TA, TB>;
+  static unsigned long long attr_set = 0;   // per device: shared-memory opt-in done
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 64 || !(attr_set >> dev & 1)) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) attr_set |= 1ULL << dev;
+  }
+  splits = std::max(1, std::min(splits, cdiv(K, kTcBK)));
+  const int kchunk = cdiv(cdiv(K, splits), kTcBK) * kTcBK;
+  splits = cdiv(K, kchunk);
+  dim3 grid(cdiv(o.N, kTcBN), cdiv(o.M, BM), splits);
+  kern<<<grid, kT, smem, s>>>(o, la, lb, K, kchunk);
+  return cudaGetLastError();
+}
+
+// M-tile: 32 or 64 rows where M is small or the 128-row grid would leave
+// most of the 152 SMs idle.
+template <int TA, int TB, class OUT, class LA, class LB>
+cudaError_t tc_launch(const OUT& o, int K, LA la, LB lb, int splits, cudaStream_t s) {
+  if (o.M <= 0 || o.N <= 0) return cudaSuccess;
+  if (o.M <= 32) return tc_launch_bm<32, TA, TB>(o, K, la, lb, splits, s);
+  if (o.M <= 64 || (long long)cdiv(o.M, 128) * cdiv(o.N, kTcBN) * splits < 2 * 152)
+    return tc_launch_bm<64, TA, TB>(o, K, la, lb, splits, s);
+  return tc_launch_bm<128, TA, TB>(o, K, la, lb, splits, s);
+}
+
+// Split-K factor for the weight gradients (reductions over all pixels).
 int wgrad_splits(int M, int N, int K) {
-  const long long tiles = (long long)cdiv(M, 64) * cdiv(N, 64);
+  const long long tiles = (long long)cdiv(M, 64) * cdiv(N, kTcBN);
   const long long want = std::max<long long>(1, 152 * 4 / std::max<long long>(tiles, 1));
   return (int)std::min<long long>(want, std::max(1, K / 1024));
 }
 
+
 // ---------------------------------------------------------------------------
 // Layout kernels
 // ---------------------------------------------------------------------------
-// col[(c*9 + u*3 + v) * P + p] = X[c][img, y+u-1, x+v-1] (zero outside)
-__global__ void im2col_kernel(const float* __restrict__ X, int C, int n, int H, int W, float* col) {
-  const long long P = (long long)n * H * W, total = 9LL * C * P;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long k = idx / P, p = idx % P;
-    const int c = (int)(k / 9), t = (int)(k % 9), u = t / 3, v = t % 3;
-    const int img = (int)(p / ((long long)H * W));
-    const int rem = (int)(p % ((long long)H * W));
-    const int y = rem / W + u - 1, x = rem % W + v - 1;
-    col[idx] = (y >= 0 && y < H && x >= 0 && x < W)
-                   ? X[(size_t)c * P + ((size_t)img * H + y) * W + x] : 0.f;
-  }
-}
-
-// dX[c][img, y, x] = sum_{u,v} dcol[(c*9+u*3+v)][img, y-u+1, x-v+1]
-__global__ void col2im_kernel(const float* __restrict__ dcol, int C, int n, int H, int W,
-                              float* dX) {
-  const long long P = (long long)n * H * W, total = (long long)C * P;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(idx / P);
-    const long long p = idx % P;
-    const int img = (int)(p / ((long long)H * W));
-    const int rem = (int)(p % ((long long)H * W));
-    const int y = rem / W, x = rem % W;
-    float s = 0.f;
-#pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      const int yy = y - u + 1;
-      if (yy < 0 || yy >= H) continue;
-#pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        const int xx = x - v + 1;
-        if (xx < 0 || xx >= W) continue;
-        s += dcol[(size_t)(c * 9 + u * 3 + v) * P + ((size_t)img * H + yy) * W + xx];
-      }
-    }
-    dX[idx] = s;
-  }
-}
-
 // 2x2 max-pool: first maximum in row-major window order (arg in 0..3).
 __global__ void maxpool_kernel(const float* __restrict__ X, int C, int n, int H, int W, float* Y,
                                unsigned char* arg) {
@@ -220,39 +582,6 @@ __global__ void maxpool_bwd_kernel(const float* __restrict__ dY, const unsigned 
   }
 }
 
-// Y[o][img, 2y+u, 2x+v] = Y4[(o*4 + u*2 + v)][img, y, x] + b[o]
-__global__ void tconv_scatter_kernel(const float* __restrict__ Y4, const float* __restrict__ b,
-                                     int O, int n, int H, int W, float* Y) {
-  const long long Pin = (long long)n * H * W, total = 4LL * O * Pin;
-  const long long Pout = 4 * Pin;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(idx / Pin);
-    const long long p = idx % Pin;
-    const int o = r / 4, u = (r % 4) / 2, v = r % 2;
-    const int img = (int)(p / ((long long)H * W));
-    const int rem = (int)(p % ((long long)H * W));
-    const int y = 2 * (rem / W) + u, x = 2 * (rem % W) + v;
-    Y[(size_t)o * Pout + ((size_t)img * 2 * H + y) * (2 * W) + x] = Y4[idx] + b[o];
-  }
-}
-
-__global__ void tconv_gather_kernel(const float* __restrict__ dY, int O, int n, int H, int W,
-                                    float* dY4) {
-  const long long Pin = (long long)n * H * W, total = 4LL * O * Pin;
-  const long long Pout = 4 * Pin;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(idx / Pin);
-    const long long p = idx % Pin;
-    const int o = r / 4, u = (r % 4) / 2, v = r % 2;
-    const int img = (int)(p / ((long long)H * W));
-    const int rem = (int)(p % ((long long)H * W));
-    const int y = 2 * (rem / W) + u, x = 2 * (rem % W) + v;
-    dY4[idx] = dY[(size_t)o * Pout + ((size_t)img * 2 * H + y) * (2 * W) + x];
-  }
-}
-
 // db[c] += sum_p dY[c][p]   (one CTA per channel)
 __global__ void rowsum_kernel(const float* __restrict__ dY, long long P, float* db) {
   const int c = blockIdx.x;
@@ -272,6 +601,63 @@ __global__ void relu_mask_kernel(float* d, const float* __restrict__ y, long lon
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x)
     if (!(y[i] > 0.f)) d[i] = 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// Layers (CNHW: channel c of image i at row c, column i*H*W + y*W + x)
+// ---------------------------------------------------------------------------
+// Y = W * col(X) + b (ReLU): M = C_out, N = pixels, K = 9 C_in.
+cudaError_t conv3x3_fwd(const float* X, int n, int Ci, int H, int W, const float* Wt,
+                        const float* b, int Co, bool relu, float* Y, cudaStream_t s) {
+  const long long P = (long long)n * H * W;
+  return tc_launch<1, 3>(OutPlain{Y, P, Co, (int)P, b, relu ? 1 : 0, 0}, 9 * Ci,
+                         LoadRowK{Wt, 9LL * Ci, Co}, LoadPixTap{X, P, H, W}, 1, s);
+}
+
+// dY is the gradient at the conv's output (before any ReLU).
+//   dW += dY col(X)^T      M = C_out, N = 9 C_in, K = pixels (split-K)
+//   db += row sums of dY
+//   dX  = Wf col(dY)       the adjoint conv, Wf[c][o*9+t] = W[o][c][8-t]:
+//                          M = C_in, N = pixels, K = 9 C_out
+cudaError_t conv3x3_bwd(const float* X, const float* dY, int n, int Ci, int H, int W,
+                        const float* Wt, int Co, float* dW, float* db, float* dX, cudaStream_t s) {
+  const long long P = (long long)n * H * W;
+  const int K9 = 9 * Ci;
+  cudaError_t e = tc_launch<2, 2>(OutPlain{dW, K9, Co, K9, nullptr, 0, 1}, (int)P,
+                                  LoadRowK{dY, P, Co}, LoadTapPix{X, P, H, W, K9},
+                                  wgrad_splits(Co, K9, (int)P), s);
+  if (e != cudaSuccess) return e;
+  if (db) rowsum_kernel<<<Co, kT, 0, s>>>(dY, P, db);
+  if ((e = cudaGetLastError()) != cudaSuccess || !dX) return e;
+  return tc_launch<1, 3>(OutPlain{dX, P, Ci, (int)P, nullptr, 0, 0}, 9 * Co, LoadFlipW{Wt, Ci},
+                         LoadPixTap{dY, P, H, W}, 1, s);
+}
+
+// 2x2 stride-2 transposed conv, W [C_in][C_out][2][2]: Y4 = W^T X with
+// M = 4 C_out, N = input pixels, K = C_in, each value written to its place
+// on the 2x grid (plus bias) by the epilogue.
+cudaError_t tconv2x2_fwd(const float* X, int n, int Ci, int H, int W, const float* Wt,
+                         const float* b, int Co, float* Y, cudaStream_t s) {
+  const long long Pin = (long long)n * H * W;
+  return tc_launch<1, 3>(OutUp{Y, 4 * Pin, 4 * Co, (int)Pin, W, b}, Ci,
+                         LoadKRow{Wt, 4LL * Co, 4 * Co}, LoadKRow{X, Pin, (int)Pin}, 1, s);
+}
+
+//   dW += X dY4^T    M = C_in, N = 4 C_out, K = input pixels (split-K)
+//   db += row sums of dY
+//   dX  = W dY4      M = C_in, N = input pixels, K = 4 C_out
+// with dY4[o*4+u*2+v][p] = dY[o][2R+u][2x+v] gathered by the loaders.
+cudaError_t tconv2x2_bwd(const float* X, const float* dY, int n, int Ci, int H, int W,
+                         const float* Wt, int Co, float* dW, float* db, float* dX, cudaStream_t s) {
+  const long long Pin = (long long)n * H * W;
+  cudaError_t e = tc_launch<2, 2>(OutPlain{dW, 4LL * Co, Ci, 4 * Co, nullptr, 0, 1}, (int)Pin,
+                                  LoadRowK{X, Pin, Ci}, LoadUpTapPix{dY, 4 * Pin, W, 4 * Co},
+                                  wgrad_splits(Ci, 4 * Co, (int)Pin), s);
+  if (e != cudaSuccess) return e;
+  if (db) rowsum_kernel<<<Co, kT, 0, s>>>(dY, 4 * Pin, db);
+  if ((e = cudaGetLastError()) != cudaSuccess || !dX) return e;
+  return tc_launch<1, 3>(OutPlain{dX, Pin, Ci, (int)Pin, nullptr, 0, 0}, 4 * Co,
+                         LoadRowK{Wt, 4LL * Co, Ci}, LoadUpPix{dY, 4 * Pin, W, (int)Pin}, 1, s);
 }
 
 // grad = 2 (y - t) / count;  loss += sum (y - t)^2
@@ -372,7 +758,6 @@ struct slim_unet {
         *gbt = nullptr, *gd3a = nullptr, *gd3 = nullptr, *gd2a = nullptr, *gd2 = nullptr,
         *gd1a = nullptr, *gd1 = nullptr, *gy = nullptr;
   unsigned char *arg1 = nullptr, *arg2 = nullptr, *arg3 = nullptr;
-  float *col = nullptr, *dcol = nullptr, *y4 = nullptr;
   double* loss = nullptr;
   std::vector<void*> allocs;
 };
@@ -395,56 +780,26 @@ struct Net {
 
   cudaError_t conv(int l, const float* X, int level, float* Y, bool relu) const {
     const LayerSpec& L = kLayers[l];
-    const long long P_ = P(level);
-    im2col_kernel<<<grid_for(9LL * L.i * P_), kT, 0, s>>>(X, L.i, n, h(level), w(level), u->col);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return gemm<false, false>(L.o, (int)P_, 9 * L.i, W_(l), 9 * L.i, u->col, (int)P_, Y, (int)P_,
-                              B_(l), relu, false, 1, s);
+    return conv3x3_fwd(X, n, L.i, h(level), w(level), W_(l), B_(l), L.o, relu, Y, s);
   }
   // dY holds the gradient at the ReLU output; on return dX (if any) holds the
   // gradient at the layer input.
   cudaError_t conv_back(int l, const float* X, int level, const float* Yout, float* dY, float* dX) const {
     const LayerSpec& L = kLayers[l];
-    const long long P_ = P(level);
-    const int K9 = 9 * L.i;
-    relu_mask_kernel<<<grid_for((long long)L.o * P_), kT, 0, s>>>(dY, Yout, (long long)L.o * P_);
-    im2col_kernel<<<grid_for((long long)K9 * P_), kT, 0, s>>>(X, L.i, n, h(level), w(level), u->col);
+    const long long count = (long long)L.o * P(level);
+    relu_mask_kernel<<<grid_for(count), kT, 0, s>>>(dY, Yout, count);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = gemm<false, true>(L.o, K9, (int)P_, dY, (int)P_, u->col, (int)P_, gW(l), K9, nullptr, false,
-                          true, wgrad_splits(L.o, K9, (int)P_), s);
-    if (e != cudaSuccess) return e;
-    rowsum_kernel<<<L.o, kT, 0, s>>>(dY, P_, gB(l));
-    if (!dX) return cudaGetLastError();
-    e = gemm<true, false>(K9, (int)P_, L.o, W_(l), K9, dY, (int)P_, u->dcol, (int)P_, nullptr, false,
-                          false, 1, s);
-    if (e != cudaSuccess) return e;
-    col2im_kernel<<<grid_for((long long)L.i * P_), kT, 0, s>>>(u->dcol, L.i, n, h(level), w(level), dX);
-    return cudaGetLastError();
+    return conv3x3_bwd(X, dY, n, L.i, h(level), w(level), W_(l), L.o, gW(l), gB(l), dX, s);
   }
   // transposed conv from level `lin` (input) to lin-1
   cudaError_t tconv(int l, const float* X, int lin, float* Y) const {
     const LayerSpec& L = kLayers[l];
-    const long long Pin = P(lin);
-    cudaError_t e = gemm<true, false>(4 * L.o, (int)Pin, L.i, W_(l), 4 * L.o, X, (int)Pin, u->y4,
-                                      (int)Pin, nullptr, false, false, 1, s);
-    if (e != cudaSuccess) return e;
-    tconv_scatter_kernel<<<grid_for(4LL * L.o * Pin), kT, 0, s>>>(u->y4, B_(l), L.o, n, h(lin), w(lin), Y);
-    return cudaGetLastError();
+    return tconv2x2_fwd(X, n, L.i, h(lin), w(lin), W_(l), B_(l), L.o, Y, s);
   }
   cudaError_t tconv_back(int l, const float* X, int lin, const float* dY, float* dX) const {
     const LayerSpec& L = kLayers[l];
-    const long long Pin = P(lin);
-    tconv_gather_kernel<<<grid_for(4LL * L.o * Pin), kT, 0, s>>>(dY, L.o, n, h(lin), w(lin), u->y4);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = gemm<false, true>(L.i, 4 * L.o, (int)Pin, X, (int)Pin, u->y4, (int)Pin, gW(l), 4 * L.o,
-                          nullptr, false, true, wgrad_splits(L.i, 4 * L.o, (int)Pin), s);
-    if (e != cudaSuccess) return e;
-    rowsum_kernel<<<L.o, kT, 0, s>>>(dY, 4 * Pin, gB(l));
-    return gemm<false, false>(L.i, (int)Pin, 4 * L.o, W_(l), 4 * L.o, u->y4, (int)Pin, dX, (int)Pin,
-                              nullptr, false, false, 1, s);
+    return tconv2x2_bwd(X, dY, n, L.i, h(lin), w(lin), W_(l), L.o, gW(l), gB(l), dX, s);
   }
   cudaError_t pool(const float* X, int level, float* Y, unsigned char* arg, int C) const {
     maxpool_kernel<<<grid_for((long long)C * P(level + 1)), kT, 0, s>>>(X, C, n, h(level), w(level), Y, arg);
@@ -548,6 +903,40 @@ slim_status slim_unet_param_count(long long* count) {
   return SLIM_OK;
 }
 
+namespace {
+bool layer_sizes_ok(int n, int ci, int H, int W, int co) {
+  return n > 0 && ci > 0 && H > 0 && W > 0 && co > 0 && ci <= 65536 && co <= 65536 &&
+         4LL * n * H * W < (1LL << 31);
+}
+slim_status layer_status(cudaError_t e) { return e == cudaSuccess ? SLIM_OK : SLIM_ECUDA; }
+}  // namespace
+
+slim_status slim_unet_conv3x3(const float* x, int n, int c_in, int H, int W, const float* w,
+                              const float* b, int c_out, int relu, float* y, void* stream) {
+  if (!x || !w || !y || !layer_sizes_ok(n, c_in, H, W, c_out)) return SLIM_EINVAL;
+  return layer_status(conv3x3_fwd(x, n, c_in, H, W, w, b, c_out, relu != 0, y, (cudaStream_t)stream));
+}
+
+slim_status slim_unet_conv3x3_grad(const float* x, const float* dy, int n, int c_in, int H, int W,
+                                   const float* w, int c_out, float* dw, float* db, float* dx,
+                                   void* stream) {
+  if (!x || !dy || !w || !dw || !layer_sizes_ok(n, c_in, H, W, c_out)) return SLIM_EINVAL;
+  return layer_status(conv3x3_bwd(x, dy, n, c_in, H, W, w, c_out, dw, db, dx, (cudaStream_t)stream));
+}
+
+slim_status slim_unet_tconv2x2(const float* x, int n, int c_in, int H, int W, const float* w,
+                               const float* b, int c_out, float* y, void* stream) {
+  if (!x || !w || !y || !layer_sizes_ok(n, c_in, H, W, c_out)) return SLIM_EINVAL;
+  return layer_status(tconv2x2_fwd(x, n, c_in, H, W, w, b, c_out, y, (cudaStream_t)stream));
+}
+
+slim_status slim_unet_tconv2x2_grad(const float* x, const float* dy, int n, int c_in, int H, int W,
+                                    const float* w, int c_out, float* dw, float* db, float* dx,
+                                    void* stream) {
+  if (!x || !dy || !w || !dw || !layer_sizes_ok(n, c_in, H, W, c_out)) return SLIM_EINVAL;
+  return layer_status(tconv2x2_bwd(x, dy, n, c_in, H, W, w, c_out, dw, db, dx, (cudaStream_t)stream));
+}
+
 slim_status slim_unet_create(int H, int W, int max_batch, slim_unet** out) {
   if (!out) return SLIM_EINVAL;
   *out = nullptr;
@@ -595,15 +984,6 @@ slim_status slim_unet_create(int H, int W, int max_batch, slim_unet** out) {
   fa(&u->gd3, 128 * P3); fa(&u->gd2a, 64 * P2); fa(&u->gd2, 64 * P2); fa(&u->gd1a, 32 * P1);
   fa(&u->gd1, 32 * P1); fa(&u->gy, P1);
   ba(&u->arg1, 32 * P2); ba(&u->arg2, 64 * P3); ba(&u->arg3, 128 * P4);
-  // im2col buffers: the largest 9 C_in x P is dec1a's (64 channels at level 1;
-  // level 2 at most 128 channels on P1/4, level 3 256 on P1/16)
-  const long long colmax = std::max({9LL * 64 * P1, 9LL * 128 * P2, 9LL * 256 * P3, 9LL * 256 * P4});
-  fa(&u->col, colmax); fa(&u->dcol, colmax);
-  fa(&u->y4, 4LL * 128 * P4 * 4);   // largest 4*o*Pin: up3 512 x P4, up2 256 x P3, up1 128 x P2
-  {
-    long long y4 = std::max({4LL * 128 * P4, 4LL * 64 * P3, 4LL * 32 * P2});
-    if (ok && y4 > 4LL * 128 * P4 * 4) ok = false;
-  }
   if (ok) {
     void* q = nullptr;
     ok = cudaMalloc(&q, sizeof(double)) == cudaSuccess;

@@ -35,7 +35,8 @@ EXPORTS = [
     "slim_batch_set_stream", "slim_batch_destroy", "slim_get_launch_log",
     "slim_unet_param_count", "slim_unet_create", "slim_unet_destroy", "slim_unet_set_params",
     "slim_unet_get_params", "slim_unet_get_grads", "slim_unet_forward", "slim_unet_train_step",
-    "slim_warm_start", "slim_backproject_data",
+    "slim_warm_start", "slim_backproject_data", "slim_unet_conv3x3", "slim_unet_conv3x3_grad",
+    "slim_unet_tconv2x2", "slim_unet_tconv2x2_grad",
 ]
 A_MATRIX_FREE, A_CSR_F32, A_CSR_BF16 = 0, 1, 2
 NOALLOC_MAX_P = 1024
@@ -123,6 +124,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "slim_unet_train_step": ([VP, VP, VP, I, C.c_float, P(D), VP], I),
         "slim_warm_start": ([VP, VP, D, D, P(I), P(D)], I),
         "slim_backproject_data": ([VP, VP], I),
+        "slim_unet_conv3x3": ([VP, I, I, I, I, VP, VP, I, I, VP, VP], I),
+        "slim_unet_conv3x3_grad": ([VP, VP, I, I, I, I, VP, I, VP, VP, VP, VP], I),
+        "slim_unet_tconv2x2": ([VP, I, I, I, I, VP, VP, I, VP, VP], I),
+        "slim_unet_tconv2x2_grad": ([VP, VP, I, I, I, I, VP, I, VP, VP, VP, VP], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -509,6 +514,46 @@ class UNet:
             self.close()
         except Exception:
             pass
+
+
+def _dptr(t):
+    """Device pointer of a contiguous float32 CUDA tensor, or NULL for None."""
+    if t is None:
+        return C.c_void_p(0)
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _layer_call(name, *args):
+    st = getattr(load(), name)(*args)
+    if st != SLIM_OK:
+        raise SlimError(st, f"{name} failed")
+
+
+def unet_conv3x3(x, n, c_in, H, W, w, b, c_out, relu, y, stream_ptr=0):
+    """y = max?(conv3x3(x, w) + b) on [channel][image][H][W] device arrays."""
+    _layer_call("slim_unet_conv3x3", _dptr(x), n, c_in, H, W, _dptr(w), _dptr(b), c_out,
+                int(bool(relu)), _dptr(y), C.c_void_p(stream_ptr))
+
+
+def unet_conv3x3_grad(x, dy, n, c_in, H, W, w, c_out, dw, db, dx, stream_ptr=0):
+    """dw += dL/dw, db += dL/db, dx = dL/dx for dy at the conv's output."""
+    _layer_call("slim_unet_conv3x3_grad", _dptr(x), _dptr(dy), n, c_in, H, W, _dptr(w), c_out,
+                _dptr(dw), _dptr(db), _dptr(dx), C.c_void_p(stream_ptr))
+
+
+def unet_tconv2x2(x, n, c_in, H, W, w, b, c_out, y, stream_ptr=0):
+    """y = tconv2x2(x, w) + b (stride 2) on [channel][image][H][W] device arrays."""
+    _layer_call("slim_unet_tconv2x2", _dptr(x), n, c_in, H, W, _dptr(w), _dptr(b), c_out,
+                _dptr(y), C.c_void_p(stream_ptr))
+
+
+def unet_tconv2x2_grad(x, dy, n, c_in, H, W, w, c_out, dw, db, dx, stream_ptr=0):
+    """dw += dL/dw, db += dL/db, dx = dL/dx for dy at the transposed conv's output."""
+    _layer_call("slim_unet_tconv2x2_grad", _dptr(x), _dptr(dy), n, c_in, H, W, _dptr(w), c_out,
+                _dptr(dw), _dptr(db), _dptr(dx), C.c_void_p(stream_ptr))
 
 
 def flatten_params(params, layers=UNET_LAYERS):

@@ -34,7 +34,7 @@ def test_layer_tables_agree(sl):
     assert sl.UNet(16, 16).nparams == U.param_count()
 
 
-@pytest.mark.parametrize("H,W,n", [(16, 16, 2), (64, 40, 1)])
+@pytest.mark.parametrize("H,W,n", [(16, 16, 2), (64, 40, 1), (24, 56, 3)])
 def test_forward_matches_oracle(sl, H, W, n):
     net, params = _net(sl, H, W, n, 5)
     x = np.random.default_rng(1).standard_normal((n, 1, H, W)).astype(np.float32)
