@@ -319,6 +319,15 @@ def tta_block(sl, cfg, b, flush, stream, epochs, thresholds, lookahead=0, ctas_p
     return out
 
 
+def l2_flush(flush, i):
+    """Evict L2 before a timed HBM stream: write a buffer twice the L2's size,
+    then read it back, so that the lines left in L2 are clean (a dirty line
+    left by the write would be written back during the timed pass and take
+    HBM bandwidth from it)."""
+    flush.fill_(i)
+    flush.sum()
+
+
 def csr_block(sl, cfg, flush, stream, reps=20):
     """Full-A passes over the stored matrix (HBM streams): y = A x through the CSR
     and x += A^T y through the CSC copy, float32 and bfloat16 values."""
@@ -339,14 +348,14 @@ def csr_block(sl, cfg, flush, stream, reps=20):
                 ("transpose", lambda: s.backproject(y, x),
                  nnz * (4 + vs) + (cfg.n + 1) * 4 + cfg.m * 4 + 2 * cfg.n * 4)):
             for i in range(3):
-                flush.fill_(i)
+                l2_flush(flush, i)
                 fn()
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             tot = 0.0
             for i in range(reps):
-                flush.fill_(i)
+                l2_flush(flush, i)
                 e0.record(stream)
                 fn()
                 e1.record(stream)
@@ -358,7 +367,9 @@ def csr_block(sl, cfg, flush, stream, reps=20):
         out[kind] = res
         s.close()
     out["note"] = ("one pass over all 180 views; bytes = index + value arrays + row/col pointers + "
-                   "vector reads/writes; L2 flushed between passes; peak = measured copy bandwidth")
+                   "vector reads/writes; L2 flushed between passes (256 MiB write, then a read of it "
+                   "so that no dirty line is written back inside the timed pass); peak = measured "
+                   "copy bandwidth")
     return out
 
 
@@ -698,12 +709,14 @@ def main_gpu(args):
     e2e = (e2e_block(sl, cfg, b, args.steps, args.warmup, lookahead=args.lookahead,
                      ctas_per_sm=args.factor_ctas_per_sm)
            if rank == 0 and not args.no_e2e else None)
-    csr_pass = csr_block(sl, cfg, flush, stream) if rank == 0 and not args.no_csr else None
+    csr_pass = (csr_block(sl, cfg, flush, stream, reps=args.csr_reps)
+                if rank == 0 and not args.no_csr else None)
     s3d = stream3d_block(sl, flush, stream, args.steps, args.warmup) if rank == 0 and not args.no_3d else None
     batch = (batch_block(sl, flush, stream, args.batch_steps, max(3, args.warmup))
              if rank == 0 and args.batch_steps > 0 else None)
     warm = warm_start_block(args) if rank == 0 and args.warm_start else None
-    unet = unet_block(sl, flush, stream) if rank == 0 and not args.no_unet else None
+    unet = (unet_block(sl, flush, stream, reps=args.unet_reps)
+            if rank == 0 and not args.no_unet else None)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         leg = run_cpu_leg(args)
@@ -746,6 +759,29 @@ def main_gpu(args):
     print(json.dumps(line))
 
 
+def main_unet(args):
+    """The network leg alone (one JSON line), e.g. for a launch list."""
+    import torch
+    from paper_1912_07962_gb300 import build as slbuild, slim as sl
+    slbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    print(json.dumps({"unet": unet_block(sl, flush, stream, reps=args.unet_reps)}))
+
+
+def main_csr(args):
+    """The stored-matrix passes alone (one JSON line), e.g. for a profile."""
+    import torch
+    from paper_1912_07962_gb300 import build as slbuild, slim as sl
+    slbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    cfg, _ = workload_of(args.workload)
+    print(json.dumps({"csr_full_pass": csr_block(sl, cfg, flush, stream, reps=args.csr_reps)}))
+
+
 def main_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -781,6 +817,12 @@ def main():
     ap.add_argument("--no-csr", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-unet", action="store_true")
+    ap.add_argument("--unet-only", action="store_true",
+                    help="time only the network (forward and training step) and print that line")
+    ap.add_argument("--unet-reps", type=int, default=10)
+    ap.add_argument("--csr-only", action="store_true",
+                    help="time only the stored-matrix passes and print that line")
+    ap.add_argument("--csr-reps", type=int, default=20)
     ap.add_argument("--warm-start", action="store_true",
                     help="train and evaluate the learned initial guess (minutes of GPU time)")
     ap.add_argument("--ws-train", type=int, default=256)
@@ -809,6 +851,10 @@ def main():
         cpu_leg(args)
     elif args.impl == "reference":
         main_reference(args)
+    elif args.unet_only:
+        main_unet(args)
+    elif args.csr_only:
+        main_csr(args)
     else:
         main_gpu(args)
 

@@ -225,12 +225,14 @@ struct LoadKRow {
   }
 };
 
-// Rows are pixels p of X (C x P, n images of H x W), k = c*9 + u*3 + v:
-// A(p, k) = X[c][img, y+u-1, x+v-1], zero outside the image.
+// Rows are pixels p of X (C x P, n images of H x W), k = t*C + c with tap
+// t = u*3 + v: A(p, k) = X[c][img, y+u-1, x+v-1], zero outside the image.
+// Tap-major k: when C is a multiple of 8 a group of 8 k shares one tap, so
+// one bounds test and one offset serve its 8 loads (stride P).
 struct LoadPixTap {
   const float* X;
   long long P;
-  int H, W;
+  int H, W, C;
   struct Row { long long p; int y, x; };
   __device__ Row row(int r) const {
     if (r >= P) return {-1, 0, 0};
@@ -238,18 +240,50 @@ struct LoadPixTap {
     return {r, rem / W, rem % W};
   }
   __device__ void load8(const Row& c, int k, int kend, float (&v)[8]) const {
-    int ch = k / 9, t = k - 9 * ch;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      float val = 0.f;
-      if (c.p >= 0 && k + i < kend) {
-        const int du = t / 3 - 1, dv = t % 3 - 1;
-        const int yy = c.y + du, xx = c.x + dv;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-          val = X[(size_t)ch * P + c.p + (long long)du * W + dv];
-      }
-      v[i] = val;
-      if (++t == 9) { t = 0; ++ch; }
+    for (int i = 0; i < 8; ++i) v[i] = 0.f;
+    if (c.p < 0) return;
+    int t = k / C, ch = k - t * C;
+    if ((C & 7) == 0 && k + 8 <= kend) {
+      const int du = t / 3 - 1, dv = t % 3 - 1;
+      const int yy = c.y + du, xx = c.x + dv;
+      if (yy < 0 || yy >= H || xx < 0 || xx >= W) return;
+      const float* src = X + (size_t)ch * P + c.p + (long long)du * W + dv;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = src[(size_t)i * P];
+      return;
+    }
+    for (int i = 0; i < 8 && k + i < kend; ++i) {
+      const int du = t / 3 - 1, dv = t % 3 - 1;
+      const int yy = c.y + du, xx = c.x + dv;
+      if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+        v[i] = X[(size_t)ch * P + c.p + (long long)du * W + dv];
+      if (++ch == C) { ch = 0; ++t; }
+    }
+  }
+};
+
+// Conv weights W [O][C][3][3] as A(o, k = t*C + c) = W[o][c][t] (tap-major k,
+// matching LoadPixTap).
+struct LoadWTap {
+  const float* Wt;
+  int C, rows;
+  struct Row { const float* ptr; };
+  __device__ Row row(int r) const { return {r < rows ? Wt + (size_t)r * C * 9 : nullptr}; }
+  __device__ void load8(const Row& c, int k, int kend, float (&v)[8]) const {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = 0.f;
+    if (!c.ptr) return;
+    int t = k / C, ch = k - t * C;
+    if ((C & 7) == 0 && k + 8 <= kend) {
+      const float* src = c.ptr + ch * 9 + t;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = src[i * 9];
+      return;
+    }
+    for (int i = 0; i < 8 && k + i < kend; ++i) {
+      v[i] = c.ptr[ch * 9 + t];
+      if (++ch == C) { ch = 0; ++t; }
     }
   }
 };
@@ -267,36 +301,55 @@ struct LoadTapPix {
     return {(long long)ch * P, t / 3 - 1, t % 3 - 1};
   }
   __device__ void load8(const Row& c, int k, int kend, float (&v)[8]) const {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = 0.f;
+    if (c.base < 0) return;
     const int HW = H * W;
     int rem = (int)(k % HW);
     int y = rem / W, x = rem % W;
+    const int yy = y + c.du;
+    if ((W & 7) == 0 && k + 8 <= kend) {
+      // the 8 pixels share image row y (k is a multiple of 8); only the
+      // first or last can fall off the row
+      if (yy < 0 || yy >= H) return;
+      const float* src = X + c.base + k + (long long)c.du * W + c.dv;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      float val = 0.f;
-      if (c.base >= 0 && k + i < kend) {
-        const int yy = y + c.du, xx = x + c.dv;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-          val = X[c.base + k + i + (long long)c.du * W + c.dv];
+      for (int i = 0; i < 8; ++i) {
+        const int xx = x + i + c.dv;
+        if (xx >= 0 && xx < W) v[i] = src[i];
       }
-      v[i] = val;
+      return;
+    }
+    for (int i = 0; i < 8 && k + i < kend; ++i) {
+      const int yy2 = y + c.du, xx = x + c.dv;
+      if (yy2 >= 0 && yy2 < H && xx >= 0 && xx < W)
+        v[i] = X[c.base + k + i + (long long)c.du * W + c.dv];
       if (++x == W) { x = 0; if (++y == H) y = 0; }
     }
   }
 };
 
-// Weights of the adjoint 3x3 conv read in place from W [C_out][C_in][3][3]:
-// A(c, k = o*9 + t) = W[o][c][8 - t].
+// Weights of the adjoint 3x3 conv read in place from W [O][C][3][3]:
+// A(c, k = t*O + o) = W[o][c][8 - t] (tap-major k, matching LoadPixTap on dY).
 struct LoadFlipW {
-  const float* W;
-  int Ci;
+  const float* Wt;
+  int C, O;
   struct Row { int c; };
-  __device__ Row row(int r) const { return {r < Ci ? r : -1}; }
+  __device__ Row row(int r) const { return {r < C ? r : -1}; }
   __device__ void load8(const Row& c, int k, int kend, float (&v)[8]) const {
-    int o = k / 9, t = k - 9 * o;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      v[i] = (c.c >= 0 && k + i < kend) ? W[((size_t)o * Ci + c.c) * 9 + 8 - t] : 0.f;
-      if (++t == 9) { t = 0; ++o; }
+    for (int i = 0; i < 8; ++i) v[i] = 0.f;
+    if (c.c < 0) return;
+    int t = k / O, o = k - t * O;
+    if ((O & 7) == 0 && k + 8 <= kend) {
+      const float* src = Wt + ((size_t)o * C + c.c) * 9 + 8 - t;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = src[(size_t)i * C * 9];
+      return;
+    }
+    for (int i = 0; i < 8 && k + i < kend; ++i) {
+      v[i] = Wt[((size_t)o * C + c.c) * 9 + 8 - t];
+      if (++o == O) { o = 0; ++t; }
     }
   }
 };
@@ -362,31 +415,27 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ uint32_t bf16_pair(float lo, float hi) {
-  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
-         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
-}
-
 // Split 8 float32 values into T bfloat16 terms and store each term's 16
-// bytes at its swizzled place (row r, chunk kg) of the term's tile.
+// bytes at its swizzled place (row r, chunk kg) of the term's tile.  One
+// cvt.rn.bf16x2 rounds two values; the residual is exact in float32.
 template <int T>
 __device__ __forceinline__ void stage_terms(unsigned char* tile0, int tile_bytes, int r, int kg,
                                             float (&v)[8]) {
   const int off = r * 64 + ((kg ^ ((r >> 1) & 3)) << 4);
 #pragma unroll
   for (int j = 0; j < T; ++j) {
-    float h[8];
+    uint32_t w[4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      h[i] = __bfloat162float(__float2bfloat16_rn(v[i]));
-      if (j + 1 < T) v[i] -= h[i];
+    for (int q = 0; q < 4; ++q) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+      w[q] = *reinterpret_cast<const uint32_t*>(&h);
+      if (j + 1 < T) {
+        const float2 f = __bfloat1622float2(h);
+        v[2 * q] -= f.x;
+        v[2 * q + 1] -= f.y;
+      }
     }
-    uint4 w;
-    w.x = bf16_pair(h[0], h[1]);
-    w.y = bf16_pair(h[2], h[3]);
-    w.z = bf16_pair(h[4], h[5]);
-    w.w = bf16_pair(h[6], h[7]);
-    *reinterpret_cast<uint4*>(tile0 + j * tile_bytes + off) = w;
+    *reinterpret_cast<uint4*>(tile0 + j * tile_bytes + off) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -582,19 +631,31 @@ __global__ void maxpool_bwd_kernel(const float* __restrict__ dY, const unsigned 
   }
 }
 
-// db[c] += sum_p dY[c][p]   (one CTA per channel)
+// db[c] += sum_p dY[c][p]: blockIdx.x = channel, blockIdx.y strides over
+// chunks of pixels; one atomic add per CTA.
 __global__ void rowsum_kernel(const float* __restrict__ dY, long long P, float* db) {
   const int c = blockIdx.x;
   float s = 0.f;
-  for (long long p = threadIdx.x; p < P; p += blockDim.x) s += dY[(size_t)c * P + p];
-  __shared__ float red[kT];
-  red[threadIdx.x] = s;
+  for (long long p = blockIdx.y * (long long)blockDim.x + threadIdx.x; p < P;
+       p += (long long)gridDim.y * blockDim.x)
+    s += dY[(size_t)c * P + p];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ float red[kT / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
-  for (int o = kT / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < kT / 32; ++w) t += red[w];
+    atomicAdd(db + c, t);
   }
-  if (threadIdx.x == 0) db[c] += red[0];
+}
+
+// Row sums of dY [C][P] added into db, with about 4 CTAs per SM in total.
+cudaError_t rowsum(const float* dY, int C, long long P, float* db, cudaStream_t s) {
+  const long long per = std::max<long long>(1, std::min<long long>(cdiv(P, kT), cdiv(4 * 152, C)));
+  rowsum_kernel<<<dim3(C, (unsigned)per), kT, 0, s>>>(dY, P, db);
+  return cudaGetLastError();
 }
 
 __global__ void relu_mask_kernel(float* d, const float* __restrict__ y, long long count) {
@@ -606,18 +667,55 @@ __global__ void relu_mask_kernel(float* d, const float* __restrict__ y, long lon
 // ---------------------------------------------------------------------------
 // Layers (CNHW: channel c of image i at row c, column i*H*W + y*W + x)
 // ---------------------------------------------------------------------------
-// Y = W * col(X) + b (ReLU): M = C_out, N = pixels, K = 9 C_in.
+// y[m][p] = max?(y[m][p] + b[m], 0) after a split-K accumulation.
+__global__ void bias_act_kernel(float* Y, const float* __restrict__ b, int relu, int M, long long P) {
+  const long long total = (long long)M * P;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    float v = Y[i];
+    if (b) v += b[i / P];
+    if (relu) v = fmaxf(v, 0.f);
+    Y[i] = v;
+  }
+}
+
+// k-splits for an output GEMM whose tile grid alone would leave SMs idle
+// (the deep levels): enough CTAs for two per SM, at least 8 k-slabs each.
+int out_splits(int M, int N, int K) {
+  const long long tiles = (long long)cdiv(M, 64) * cdiv(N, kTcBN);
+  if (tiles >= 2 * 152) return 1;
+  const long long want = cdiv(2 * 152, tiles);
+  return (int)std::max<long long>(1, std::min<long long>(want, K / (8 * kTcBK)));
+}
+
+// C [M][N] (contiguous) = op + bias, ReLU: one pass when the grid fills the
+// GPU, else zero, split-K atomics and a bias / ReLU pass.
+template <int TA, int TB, class LA, class LB>
+cudaError_t gemm_out(float* C, int M, int N, int K, LA la, LB lb, const float* bias, bool relu,
+                     cudaStream_t s) {
+  const int splits = out_splits(M, N, K);
+  if (splits == 1)
+    return tc_launch<TA, TB>(OutPlain{C, N, M, N, bias, relu ? 1 : 0, 0}, K, la, lb, 1, s);
+  cudaError_t e = cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  e = tc_launch<TA, TB>(OutPlain{C, N, M, N, nullptr, 0, 1}, K, la, lb, splits, s);
+  if (e != cudaSuccess || (!bias && !relu)) return e;
+  bias_act_kernel<<<grid_for((long long)M * N), kT, 0, s>>>(C, bias, relu ? 1 : 0, M, N);
+  return cudaGetLastError();
+}
+
+// Y = W * col(X) + b (ReLU): M = C_out, N = pixels, K = 9 C_in (tap-major).
 cudaError_t conv3x3_fwd(const float* X, int n, int Ci, int H, int W, const float* Wt,
                         const float* b, int Co, bool relu, float* Y, cudaStream_t s) {
   const long long P = (long long)n * H * W;
-  return tc_launch<1, 3>(OutPlain{Y, P, Co, (int)P, b, relu ? 1 : 0, 0}, 9 * Ci,
-                         LoadRowK{Wt, 9LL * Ci, Co}, LoadPixTap{X, P, H, W}, 1, s);
+  return gemm_out<1, 3>(Y, Co, (int)P, 9 * Ci, LoadWTap{Wt, Ci, Co}, LoadPixTap{X, P, H, W, Ci}, b,
+                        relu, s);
 }
 
 // dY is the gradient at the conv's output (before any ReLU).
 //   dW += dY col(X)^T      M = C_out, N = 9 C_in, K = pixels (split-K)
 //   db += row sums of dY
-//   dX  = Wf col(dY)       the adjoint conv, Wf[c][o*9+t] = W[o][c][8-t]:
+//   dX  = Wf col(dY)       the adjoint conv, Wf[c][t*C_out + o] = W[o][c][8-t]:
 //                          M = C_in, N = pixels, K = 9 C_out
 cudaError_t conv3x3_bwd(const float* X, const float* dY, int n, int Ci, int H, int W,
                         const float* Wt, int Co, float* dW, float* db, float* dX, cudaStream_t s) {
@@ -627,10 +725,10 @@ cudaError_t conv3x3_bwd(const float* X, const float* dY, int n, int Ci, int H, i
                                   LoadRowK{dY, P, Co}, LoadTapPix{X, P, H, W, K9},
                                   wgrad_splits(Co, K9, (int)P), s);
   if (e != cudaSuccess) return e;
-  if (db) rowsum_kernel<<<Co, kT, 0, s>>>(dY, P, db);
-  if ((e = cudaGetLastError()) != cudaSuccess || !dX) return e;
-  return tc_launch<1, 3>(OutPlain{dX, P, Ci, (int)P, nullptr, 0, 0}, 9 * Co, LoadFlipW{Wt, Ci},
-                         LoadPixTap{dY, P, H, W}, 1, s);
+  if (db && (e = rowsum(dY, Co, P, db, s)) != cudaSuccess) return e;
+  if (!dX) return cudaSuccess;
+  return gemm_out<1, 3>(dX, Ci, (int)P, 9 * Co, LoadFlipW{Wt, Ci, Co}, LoadPixTap{dY, P, H, W, Co},
+                        nullptr, false, s);
 }
 
 // 2x2 stride-2 transposed conv, W [C_in][C_out][2][2]: Y4 = W^T X with
@@ -654,8 +752,8 @@ cudaError_t tconv2x2_bwd(const float* X, const float* dY, int n, int Ci, int H, 
                                   LoadRowK{X, Pin, Ci}, LoadUpTapPix{dY, 4 * Pin, W, 4 * Co},
                                   wgrad_splits(Ci, 4 * Co, (int)Pin), s);
   if (e != cudaSuccess) return e;
-  if (db) rowsum_kernel<<<Co, kT, 0, s>>>(dY, 4 * Pin, db);
-  if ((e = cudaGetLastError()) != cudaSuccess || !dX) return e;
+  if (db && (e = rowsum(dY, Co, 4 * Pin, db, s)) != cudaSuccess) return e;
+  if (!dX) return cudaSuccess;
   return tc_launch<1, 3>(OutPlain{dX, Pin, Ci, (int)Pin, nullptr, 0, 0}, 4 * Co,
                          LoadRowK{Wt, 4LL * Co, Ci}, LoadUpPix{dY, 4 * Pin, W, (int)Pin}, 1, s);
 }
@@ -857,7 +955,7 @@ struct Net {
     // output 1x1 conv
     CKE((gemm<false, true>(1, 32, P1, U.gy, P1, U.d1, P1, gW(L_OUT), 32, nullptr, false, true,
                            wgrad_splits(1, 32, P1), s)));
-    rowsum_kernel<<<1, kT, 0, s>>>(U.gy, P(1), gB(L_OUT));
+    CKE(rowsum(U.gy, 1, P(1), gB(L_OUT), s));
     CKE((gemm<true, false>(32, P1, 1, W_(L_OUT), 32, U.gy, P1, U.gd1, P1, nullptr, false, false, 1, s)));
     // level 1 decoder
     CKE(conv_back(L_DEC1B, U.d1a, 1, U.d1, U.gd1, U.gd1a));

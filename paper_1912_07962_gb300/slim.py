@@ -228,6 +228,9 @@ class Slim:
         self._check(self._lib.slim_sync(self.h))
 
     def set_stream(self, stream_ptr):
+        """Run the context's work on the cudaStream_t `stream_ptr`.  0 selects
+        the context's own stream, not the legacy default stream, so torch's
+        default stream (handle 0) cannot be named here: use a side stream."""
         self._check(self._lib.slim_set_stream(self.h, C.c_void_p(stream_ptr)))
 
     def set_ref(self, x_ref):

@@ -18,7 +18,14 @@ from . import slim as sl
 
 
 def _stream(torch):
-    return torch.cuda.current_stream().cuda_stream
+    """Handle of torch's current stream, which must not be the default one:
+    the library reads handle 0 as "the context's own stream", whose work
+    would not be ordered with the tensors PyTorch forms around it."""
+    h = torch.cuda.current_stream().cuda_stream
+    if h == 0:
+        raise RuntimeError("run the warm-start driver under a non-default torch stream "
+                           "(with torch.cuda.stream(torch.cuda.Stream()): ...)")
+    return h
 
 
 def _solver(cfg, torch, lookahead=3):

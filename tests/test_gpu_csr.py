@@ -9,7 +9,8 @@ from _common import rel, tomo_problem
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU"),
+              pytest.mark.usefixtures("torch_side_stream")]
 
 KIND_MODE = {"f32": 1, "bf16": 2}
 
@@ -27,8 +28,13 @@ def c1():
 
 
 def _make(sl, cfg, kind, **kw):
-    return sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.det, cfg.r, cfg.lam, cfg.seed,
-                   precision=1, solver=1, a_mode=KIND_MODE[kind], **kw)
+    """Context on torch's current stream (a side stream, see conftest), so
+    that its passes are ordered with the tensors the tests fill and read."""
+    s = sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.det, cfg.r, cfg.lam, cfg.seed,
+                precision=kw.pop("precision", 1), solver=kw.pop("solver", 1),
+                a_mode=KIND_MODE[kind], **kw)
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    return s
 
 
 @pytest.mark.parametrize("kind", ["f32", "bf16"])
@@ -70,6 +76,22 @@ def test_full_passes(sl, c1, kind):
 
 
 @pytest.mark.parametrize("kind", ["f32", "bf16"])
+def test_full_forward_pass_float64(sl, c1, kind):
+    # float64 iterate over the stored float32 / bfloat16 values (the staged
+    # full pass instantiated for double): exact products, float64 sums
+    cfg = workloads.C1
+    g = c1[0]
+    S = csr.stored_matrix(g, kind)
+    s = _make(sl, cfg, kind, precision=0, solver=0)
+    xv = np.random.default_rng(4).standard_normal(g.n)
+    y = torch.zeros(g.m, dtype=torch.float64, device="cuda")
+    s.project(torch.tensor(xv, device="cuda"), y)
+    scale = np.abs(S) @ np.abs(xv) + 1e-300
+    assert np.max(np.abs(y.cpu().numpy() - S @ xv) / scale) < 1e-13
+    s.close()
+
+
+@pytest.mark.parametrize("kind", ["f32", "bf16"])
 def test_single_steps_on_the_stored_matrix(sl, c1, kind):
     cfg = workloads.C1
     g, A, _, b = c1
@@ -105,4 +127,18 @@ def test_stored_matrix_at_the_256_workload(sl):
             seg = slice(rp[r], rp[r + 1])
             assert np.array_equal(col[seg], idx)
             assert np.array_equal(val[seg].astype(np.float64), csr.round_values(w, kind))
+        # the full forward pass over all 65,340 rays (staged tiles of
+        # consecutive rays), checked on the sampled rows against the stored
+        # entries just verified
+        xv = np.random.default_rng(6).standard_normal(g.n).astype(np.float32)
+        y = torch.full((g.m,), np.nan, dtype=torch.float32, device="cuda")
+        s.project(torch.tensor(xv, device="cuda"), y)
+        yh = y.cpu().numpy().astype(np.float64)
+        assert np.isfinite(yh).all()
+        x64 = xv.astype(np.float64)
+        for r in rows:
+            seg = slice(rp[r], rp[r + 1])
+            want = np.dot(val[seg].astype(np.float64), x64[col[seg]])
+            mag = np.dot(np.abs(val[seg].astype(np.float64)), np.abs(x64[col[seg]]))
+            assert abs(yh[r] - want) <= 2e-6 * mag + 1e-30, (kind, int(r))
         s.close()

@@ -15,7 +15,8 @@ from _common import oracle_step_from, rel, tomo_problem
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU"),
+              pytest.mark.usefixtures("torch_side_stream")]
 
 TOL64 = 1e-12
 TOL32 = 1e-5
@@ -39,8 +40,13 @@ def c2():
 
 
 def _make(sl, cfg, precision=0, solver=0, **kw):
-    return sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.det, cfg.r, cfg.lam, cfg.seed,
-                   precision=precision, solver=solver, **kw)
+    """Context on torch's current stream (a side stream, see conftest), so
+    that its asynchronous passes are ordered with the tensors the tests fill
+    and read."""
+    s = sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.det, cfg.r, cfg.lam, cfg.seed,
+                precision=precision, solver=solver, **kw)
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    return s
 
 
 # ---------------------------------------------------------------- projector

@@ -9,7 +9,8 @@ import workloads
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU"),
+              pytest.mark.usefixtures("torch_side_stream")]
 
 
 def test_driver_end_to_end():
@@ -31,3 +32,12 @@ def test_driver_end_to_end():
     assert 0.0 < summary["zero"]["best"] < 0.9
     assert 0.0 <= summary["used_fraction"] <= 1.0
     net.close()
+
+
+def test_driver_refuses_the_default_stream():
+    # handle 0 would put the library's work on the context's own stream,
+    # unordered with the tensors the driver forms
+    from paper_1912_07962_gb300 import warmstart as ws
+    with torch.cuda.stream(torch.cuda.default_stream()):
+        with pytest.raises(RuntimeError):
+            ws._stream(torch)
