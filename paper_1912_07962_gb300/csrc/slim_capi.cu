@@ -558,7 +558,10 @@ cudaError_t la_enqueue_iterate(slim_ctx* c, int b, cudaStream_t s) {
   if ((e = cudaMemsetAsync(c->d_rhs, 0, (size_t)c->P * sizeof(double), s)) != cudaSuccess) return e;
   if ((e = la_launch_residual<T>(a, info, s)) != cudaSuccess) return e;
   if ((e = la_mark(c, 7, s)) != cudaSuccess) return e;
-  if ((e = chol_solve(c->planb[b], c->d_Lb[b], c->d_rhs, c->d_z, c->d_status, s)) != cudaSuccess)
+  // the right-hand side is zero above the newest block (the last one)
+  const int first_tile = (c->nslots - 1) * c->ell / c->nb;
+  if ((e = chol_solve(c->planb[b], c->d_Lb[b], c->d_rhs, c->d_z, c->d_status, s, first_tile)) !=
+      cudaSuccess)
     return e;
   if (c->solver == SLIM_SOLVE_MIXED) {
     for (int it = 0; it < c->refine_iters; ++it) {
@@ -1217,8 +1220,19 @@ slim_status slim_get_memory(slim_ctx* c, int* ids, double* G, double* z) {
         for (int j = 0; j < c->p; ++j) G[(size_t)i * c->p + j] = ext[j] >= 0 ? row[ext[j]] : 0.0;
       }
     }
-    if (z) CK(cudaMemcpy(z, c->d_z, (size_t)c->p * sizeof(double), cudaMemcpyDeviceToHost),
-              "get_memory");
+    if (z) {
+      // z is in the factored matrix's order (blocks chronological); report it
+      // in ring order like ids and G: ring slot s holds block k - d with
+      // d = (k-1-s) mod (r+1), at chronological position r - d
+      std::vector<double> zf((size_t)c->p);
+      CK(cudaMemcpy(zf.data(), c->d_z, zf.size() * sizeof(double), cudaMemcpyDeviceToHost),
+         "get_memory");
+      for (int q = 0; q < c->p; ++q) {
+        const int s = q / c->ell;
+        const long long d = ((c->h_k - 1 - s) % c->nslots + c->nslots) % c->nslots;
+        z[q] = zf[(size_t)(c->nslots - 1 - d) * c->ell + q % c->ell];
+      }
+    }
     return read_status(c);
   }
   if (ids) CK(cudaMemcpy(ids, c->d_ring_ids, (size_t)c->p * sizeof(int), cudaMemcpyDeviceToHost),

@@ -13,6 +13,7 @@
 // The solves chain diagonal blocks the same way: CTA i of the forward solve
 // subtracts L_ij y_j as each y_j is published, then applies L_ii^{-1}; the
 // backward solve runs the transposed chain from the last block.
+#include <algorithm>
 #include <type_traits>
 
 #include <cooperative_groups.h>
@@ -1042,7 +1043,7 @@ __device__ __forceinline__ void thread_wait_row(uint64_t* bar, int* abort_flag, 
 template <typename T, int NB>
 __global__ void __launch_bounds__(kThreads) chol_solve_cluster_kernel(
     const T* L, int P, int Tt, const T* winv, const double* v, double* z, int* status,
-    int* abort_flag) {
+    int* abort_flag, int i0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* y = reinterpret_cast<T*>(smem_raw);     // [P] forward solution
   T* zt = y + P;                              // [P] backward solution
@@ -1063,24 +1064,27 @@ __global__ void __launch_bounds__(kThreads) chol_solve_cluster_kernel(
       mbar_init(&fbar[i], 1);
       mbar_init(&bbar[i], 1);
       if (i % C != rank) {   // rows sent by other CTAs: one arrival expecting NB values
-        mbar_expect_tx(&fbar[i], NB * sizeof(T));
+        if (i >= i0) mbar_expect_tx(&fbar[i], NB * sizeof(T));   // y rows above i0 are not sent
         mbar_expect_tx(&bbar[i], NB * sizeof(T));
       }
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // v is zero above tile i0, hence so is y: every CTA holds those rows as zero
+  for (int q = tid; q < i0 * NB; q += kThreads) y[q] = T(0);
   cl.sync();   // every CTA's barriers exist before anyone sends
   bool ok = true;
   // The owner of row i finishes it with one barrier on the chain: every thread
   // waits for row i-1 itself, the rows' accumulators meet in shared memory,
   // and the lanes holding the results store them into every peer.
-  // forward: y_i = W_i (v_i - sum_{j<i} L_ij y_j)
-  for (int i = rank; ok && i < Tt; i += C) {
+  // forward: y_i = W_i (v_i - sum_{i0<=j<i} L_ij y_j), from the first tile
+  // i >= i0 this CTA owns
+  for (int i = i0 + ((rank - i0) % C + C) % C; ok && i < Tt; i += C) {
     RP wp, lastp;
     wp.load(winv + (size_t)i * NB * NB, NB);
-    if (i > 0) lastp.load(L + (size_t)i * NB * P + (size_t)(i - 1) * NB, P);
+    if (i > i0) lastp.load(L + (size_t)i * NB * P + (size_t)(i - 1) * NB, P);
     T s = T(0);
-    for (int j = 0; j + 1 < i; j += kSolveBatch) {   // rows < i-1, batches in flight
+    for (int j = i0; j + 1 < i; j += kSolveBatch) {   // rows i0 .. i-2, batches in flight
       const int nj = min(kSolveBatch, i - 1 - j);
       RP bp[kSolveBatch];
 #pragma unroll
@@ -1095,7 +1099,7 @@ __global__ void __launch_bounds__(kThreads) chol_solve_cluster_kernel(
         if (u < nj) s += row_dot<T, NB>(bp[u], y + (j + u) * NB);
     }
     if (!ok) break;
-    if (i > 0) {
+    if (i > i0) {
       if ((i - 1) % C != rank) thread_wait_row(&fbar[i - 1], abort_flag, status);
       s += row_dot<T, NB>(lastp, y + (i - 1) * NB);
     }
@@ -1169,7 +1173,7 @@ __global__ void __launch_bounds__(kThreads) chol_solve_cluster_kernel(
   // wait for every store addressed to this CTA before leaving (briefly when a
   // wait already ran out: the rows still missing will not come)
   const unsigned drain = ok ? kSpinLimit : (kSpinLimit >> 8);
-  cluster_wait_rows(fbar, 0, Tt, C, rank, drain, abort_flag, status, &s_ok);
+  cluster_wait_rows(fbar, i0, Tt, C, rank, drain, abort_flag, status, &s_ok);
   cluster_wait_rows(bbar, 0, Tt, C, rank, drain, abort_flag, status, &s_ok);
   cl.sync();   // no CTA leaves while others may still store into its shared memory
 }
@@ -1216,7 +1220,7 @@ int pick_solve_cluster(int P, int Tt) {
 
 template <typename T, int NB>
 cudaError_t launch_solve_cluster(const CholPlan& p, const void* L, const double* v, double* z,
-                                 int* status, cudaStream_t s) {
+                                 int* status, cudaStream_t s, int i0) {
   int* abort_flag = p.d_sync + p.T * p.T + 2 * p.T + 3;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p.cluster);
@@ -1231,7 +1235,7 @@ cudaError_t launch_solve_cluster(const CholPlan& p, const void* L, const double*
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, chol_solve_cluster_kernel<T, NB>, (const T*)L, p.P, p.T,
-                            (const T*)p.d_winv, v, z, status, abort_flag);
+                            (const T*)p.d_winv, v, z, status, abort_flag, i0);
 }
 
 template <typename T, int NB>
@@ -1358,12 +1362,13 @@ cudaError_t chol_factor(const CholPlan& p, void* L, int* status, cudaStream_t s)
 }
 
 cudaError_t chol_solve(const CholPlan& p, const void* L, const double* v, double* z, int* status,
-                       cudaStream_t s) {
+                       cudaStream_t s, int first_tile) {
   if (p.cluster) {
-    if (p.is_f32) return p.nb == 64 ? launch_solve_cluster<float, 64>(p, L, v, z, status, s)
-                                    : launch_solve_cluster<float, 32>(p, L, v, z, status, s);
-    return p.nb == 64 ? launch_solve_cluster<double, 64>(p, L, v, z, status, s)
-                      : launch_solve_cluster<double, 32>(p, L, v, z, status, s);
+    const int i0 = std::max(0, std::min(first_tile, p.T - 1));
+    if (p.is_f32) return p.nb == 64 ? launch_solve_cluster<float, 64>(p, L, v, z, status, s, i0)
+                                    : launch_solve_cluster<float, 32>(p, L, v, z, status, s, i0);
+    return p.nb == 64 ? launch_solve_cluster<double, 64>(p, L, v, z, status, s, i0)
+                      : launch_solve_cluster<double, 32>(p, L, v, z, status, s, i0);
   }
   // reset the solve flags and tickets, keep the factor's abort flag
   int* fflag = p.d_sync + p.T * p.T;

@@ -47,8 +47,10 @@ void chol_plan_destroy(CholPlan* plan);
 // Factor L (P x P row-major, lower triangle holds K on entry, L on exit) in
 // the factor precision; then solve L L^T z = v (float64 vectors of length P).
 // Errors are recorded in *status (SLIM_ENOTPD, SLIM_ETIMEOUT).
+// first_tile: v is zero in rows [0, first_tile * nb), so the forward sweep
+// starts at that tile (y is zero above it); 0 for a general v.
 cudaError_t chol_factor(const CholPlan& plan, void* L, int* status, cudaStream_t s);
 cudaError_t chol_solve(const CholPlan& plan, const void* L, const double* v, double* z,
-                       int* status, cudaStream_t s);
+                       int* status, cudaStream_t s, int first_tile = 0);
 
 }  // namespace slim

@@ -143,9 +143,11 @@ __global__ void __launch_bounds__(kCta) la_map_clear_kernel(LaArgs<T> a) {
   }
 }
 
-// Ring index q (slot s = q / ell, row q % ell) of step k -> extended row of
-// the block held there: block k - ((k-1-s) mod (r+1)), -1 if that block index
-// is < 1 or q is padding.
+// Row q of the factored matrix of step k -> extended row.  The window's
+// blocks are in chronological order, block k - (r - s) at position
+// s = q / ell (the newest, block k, last), so that the first solve's right-hand
+// side [0; ...; 0; r_k] is zero above the last block; -1 if that block index is
+// < 1 or q is padding.
 __global__ void la_ext_map_kernel(const StepInfo* info, int ell, int nslots, int eslots, int p,
                                   int P, int* ext) {
   const long long k = info->k;
@@ -153,7 +155,7 @@ __global__ void la_ext_map_kernel(const StepInfo* info, int ell, int nslots, int
     int e = -1;
     if (q < p) {
       const int s = q / ell;
-      const long long blk = k - (long long)((k - 1 - s) % nslots + nslots) % nslots;
+      const long long blk = k - (nslots - 1 - s);
       if (blk >= 1) e = eslot_of(blk, eslots) * ell + q % ell;
     }
     ext[q] = e;
@@ -180,7 +182,8 @@ __global__ void la_form_kernel(const StepInfo* info, const int* __restrict__ ext
 // Iterate chain of step k (the step held in `info`)
 // ---------------------------------------------------------------------------
 
-// r_k = A_k x - b_k from the stored taps of block k, into its ring slot.
+// r_k = A_k x - b_k from the stored taps of block k, into the last block of
+// the right-hand side (the newest block's place in the factored matrix).
 // The per-lane order of the sum is the one of the fused march-and-residual
 // kernel of the plain form, so both forms give the same residual.
 template <typename T>
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(kCta) la_residual_kernel(LaArgs<T> a, const St
     if (pb >= 0) acc += (T)rw[2 * s + 1] * a.x[pb];
   }
   acc = warp_sum(acc);
-  if (lane == 0) a.rhs[info->slot * a.ell + w] = (double)(acc - a.b[a.ring_ids[q]]);
+  if (lane == 0) a.rhs[(a.nslots - 1) * a.ell + w] = (double)(acc - a.b[a.ring_ids[q]]);
 }
 
 __global__ void la_refine_kernel(const StepInfo* info, const int* __restrict__ ext,

@@ -53,7 +53,8 @@ template <typename T> cudaError_t la_launch_sample(const LaArgs<T>& a, cudaStrea
 template <typename T> cudaError_t la_launch_taps(const LaArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t la_launch_gram(const LaArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t la_launch_map_clear(const LaArgs<T>& a, cudaStream_t s);
-// Ring index -> extended row for the step held in `info` (-1: empty or padding).
+// Row of the factored matrix (blocks in chronological order, the newest last)
+// -> extended row for the step held in `info` (-1: empty or padding).
 cudaError_t la_launch_ext_map(const StepInfo* info, int ell, int nslots, int eslots, int p, int P,
                               int* ext, cudaStream_t s);
 // L = lambda_k I + G gathered into ring order (lower triangle), precision TF.
