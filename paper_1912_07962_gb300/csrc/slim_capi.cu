@@ -258,20 +258,21 @@ cudaError_t mark(slim_ctx* c, int i) {
   return cudaEventRecord(c->ev[i], c->stream);
 }
 
-// Kernels one step launches (sample, forward, Gram, K, factor, 2 per solve,
-// 2 per refinement round, scatter).
+// Kernels one step launches (sample, forward, Gram, K, factor, the solves:
+// one cluster kernel each, else a forward and a backward kernel; 2 per
+// refinement round (residual, z += dz), scatter).
 int kernels_per_step(const slim_ctx* c) {
   if (c->dim == 3) return 6;   // sample, march, collect, slice Gram, slice solve, scatter
+  const int solves = c->solver == SLIM_SOLVE_MIXED ? 1 + c->refine_iters : 1;
+  const int refine = c->solver == SLIM_SOLVE_MIXED ? 2 * c->refine_iters : 0;
   if (c->lookahead) {
     // geometry: sample, taps, Gram, map clear, ring map, K, factor; iterate:
-    // residual, 2 per solve, 2 per refinement round, scatter
-    int solves = c->solver == SLIM_SOLVE_MIXED ? 1 + c->refine_iters : 1;
-    int refine = c->solver == SLIM_SOLVE_MIXED ? 2 * c->refine_iters : 0;
-    return 7 + 1 + 2 * solves + refine + 1;
+    // residual, the solves, refinement rounds, scatter
+    const int per_solve = c->planb[0].cluster ? 1 : 2;
+    return 7 + 1 + per_solve * solves + refine + 1;
   }
-  int solves = c->solver == SLIM_SOLVE_MIXED ? 1 + c->refine_iters : 1;
-  int refine = c->solver == SLIM_SOLVE_MIXED ? 2 * c->refine_iters : 0;
-  return 5 + 2 * solves + refine + 1;
+  const int per_solve = c->plan.cluster ? 1 : 2;
+  return 5 + per_solve * solves + refine + 1;
 }
 
 // The damped solve (lambda_k I + G) z = rhs: float64 tiled Cholesky, or a
