@@ -833,7 +833,7 @@ def main():
     ap.add_argument("--ws-batch", type=int, default=8)
     ap.add_argument("--ws-lr", type=float, default=1e-3)
     ap.add_argument("--ws-verbose", action="store_true")
-    ap.add_argument("--factor-ctas-per-sm", type=int, default=2,
+    ap.add_argument("--factor-ctas-per-sm", type=int, default=1,
                     help="persistent factorisation CTAs per SM (0: library default)")
     ap.add_argument("--lookahead", type=int, default=6,
                     help="steps the geometry chain runs ahead in the chosen form (0: one chain)")

@@ -109,9 +109,15 @@ constexpr int kPanelLd = 20;   // 16 panel columns + pad, 16-byte rows
 //   S       a tile staged as is: the GEMM's C operand, or the diagonal tile
 // The diagonal factorisation reuses Bs for the inverse and As for the
 // factored panel and the partial sums of the inverse.
+// The float32 factor with 64 x 64 tiles also runs grouped updates, whose
+// operands are two 64 x (128 + 4) tiles staged transposed.
 template <typename T>
 __host__ __device__ constexpr size_t factor_smem_bytes(int nb) {
-  return (size_t)3 * nb * gemm_ld(nb) * sizeof(T);
+  return (sizeof(T) == 4 && nb == 64)
+             ? (size_t)2 * nb * (2 * nb + 4) * sizeof(T) > (size_t)3 * nb * gemm_ld(nb) * sizeof(T)
+                   ? (size_t)2 * nb * (2 * nb + 4) * sizeof(T)
+                   : (size_t)3 * nb * gemm_ld(nb) * sizeof(T)
+             : (size_t)3 * nb * gemm_ld(nb) * sizeof(T);
 }
 
 template <typename T>
@@ -155,6 +161,24 @@ struct TileRegs {
 #pragma unroll
           for (int f = 0; f < EV; ++f) po[f] = reinterpret_cast<const T*>(&v[t][f])[e];
           *reinterpret_cast<V*>(As + (size_t)(qq * EV + e) * LD + rq * EV) = o;
+        }
+      }
+    }
+  }
+  // As[q][col0 + r] = A[r][q] with row length ld (a tile of a wider operand)
+  __device__ void store_t_ld(T* As, int ld, int col0) const {
+#pragma unroll
+    for (int t = 0; t < BPT; ++t) {
+      const int b = threadIdx.x + t * kThreads;
+      if (b < NBLKS) {
+        const int rq = b / QB, qq = b % QB;
+#pragma unroll
+        for (int e = 0; e < EV; ++e) {
+          V o;
+          T* po = reinterpret_cast<T*>(&o);
+#pragma unroll
+          for (int f = 0; f < EV; ++f) po[f] = reinterpret_cast<const T*>(&v[t][f])[e];
+          *reinterpret_cast<V*>(As + (size_t)(qq * EV + e) * ld + col0 + rq * EV) = o;
         }
       }
     }
@@ -265,6 +289,103 @@ __device__ __noinline__ void task_gemm(T* out, int ldo, const T* A, int lda, con
     st_row<T, TM>(out + (size_t)r * ldo + tx * TM, o);
   }
   __syncthreads();
+}
+
+// C -= A B^T for a 2x2 group of 64 x 64 tiles (float32): C is the 128 x 128
+// block at the group's top-left tile, A and B the 128 x 64 blocks of column
+// k at rows i and m (leading dimension P).  Thread (ty, tx) owns rows ty*8..,
+// columns tx*8..; the products are summed from zero and subtracted from C
+// once, as in the single-tile update (C is large next to the Schur complement
+// it leaves, so it must not take the rounding of every product).  Like every
+// tile read of the factorisation, C is read around L1 (tiles change under
+// other SMs).
+template <int NB>
+__device__ __noinline__ void task_gemm_group(float* C, int P, const float* A, const float* B,
+                                             float* As, float* Bs) {
+  constexpr int LD2 = 2 * NB + 4;
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  {
+    TileRegs<float, NB> r0, r1;
+    r0.load(A, P);
+    r1.load(A + (size_t)NB * P, P);
+    r0.store_t_ld(As, LD2, 0);
+    r1.store_t_ld(As, LD2, NB);
+    r0.load(B, P);
+    r1.load(B + (size_t)NB * P, P);
+    r0.store_t_ld(Bs, LD2, 0);
+    r1.store_t_ld(Bs, LD2, NB);
+  }
+  __syncthreads();
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+#pragma unroll 4
+  for (int q = 0; q < NB; ++q) {
+    const float4 a0 = *reinterpret_cast<const float4*>(As + q * LD2 + ty * 8);
+    const float4 a1 = *reinterpret_cast<const float4*>(As + q * LD2 + ty * 8 + 4);
+    const float4 b0 = *reinterpret_cast<const float4*>(Bs + q * LD2 + tx * 8);
+    const float4 b1 = *reinterpret_cast<const float4*>(Bs + q * LD2 + tx * 8 + 4);
+    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] += av[a] * bv[b];
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    float* row = C + (size_t)(ty * 8 + a) * P + tx * 8;
+    float4 c0 = __ldcg(reinterpret_cast<const float4*>(row));
+    float4 c1 = __ldcg(reinterpret_cast<const float4*>(row + 4));
+    c0.x -= acc[a][0]; c0.y -= acc[a][1]; c0.z -= acc[a][2]; c0.w -= acc[a][3];
+    c1.x -= acc[a][4]; c1.y -= acc[a][5]; c1.z -= acc[a][6]; c1.w -= acc[a][7];
+    __stcg(reinterpret_cast<float4*>(row), c0);
+    __stcg(reinterpret_cast<float4*>(row + 4), c1);
+  }
+  __syncthreads();
+}
+
+// CTA-wide bounded wait for the 8 counters of a grouped update of tiles
+// (i..i+1, m..m+1) at step k: the four operand tiles of column k final
+// (counter k+1), the four output tiles with the k earlier updates applied.
+__device__ bool cta_wait_group(const int* cnt, int Tt, int i, int m, int k, int* abort_flag,
+                               int* status, int* s_ok8) {
+  const int tid = threadIdx.x;
+  if (tid < 8) {
+    const int q = tid & 3;
+    const int* f;
+    int tg;
+    if (tid < 4) {
+      const int row = q == 0 ? i : q == 1 ? i + 1 : q == 2 ? m : m + 1;
+      f = cnt + row * Tt + k;
+      tg = k + 1;
+    } else {
+      f = cnt + (i + (q >> 1)) * Tt + m + (q & 1);
+      tg = k;
+    }
+    int ok = 1;
+    unsigned it = 0;
+    while (ld_acquire(f) < tg) {
+      if (ld_acquire(abort_flag)) { ok = 0; break; }
+      if (++it > kSpinLimit) {
+        set_status(status, SLIM_ETIMEOUT);
+        atomicExch(abort_flag, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    s_ok8[tid] = ok;
+  }
+  __syncthreads();
+  int ok = 1;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) ok &= s_ok8[q];
+  __syncthreads();
+  return ok != 0;
 }
 
 template <typename T>
@@ -687,7 +808,7 @@ __global__ void __launch_bounds__(kThreads, 2) chol_factor_kernel(T* L, int P, i
   T* As = reinterpret_cast<T*>(smem_raw);
   T* Bs = As + NB * gemm_ld(NB);
   T* S = Bs + NB * gemm_ld(NB);
-  __shared__ int s_task, s_ok3[3];
+  __shared__ int s_task, s_ok3[3], s_ok8[8];
   __shared__ CholTask s_desc;
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -717,6 +838,25 @@ __global__ void __launch_bounds__(kThreads, 2) chol_factor_kernel(T* L, int P, i
         const T* Lmk = L + (size_t)m * NB * P + (size_t)k * NB;
         task_gemm<T, NB>(tile_im, P, Lik, P, Lmk, P, tile_im, T(-1), As, Bs, S);
         cta_publish(&cnt[i * Tt + m]);
+      }
+    } else if (tk.type == kUpd4) {
+      ok = cta_wait_group(cnt, Tt, i, m, k, abort_flag, status, s_ok8);
+      if (ok) {
+        if constexpr (sizeof(T) == 4 && NB == 64) {
+          task_gemm_group<NB>(L + (size_t)i * NB * P + (size_t)m * NB, P,
+                              L + (size_t)i * NB * P + (size_t)k * NB,
+                              L + (size_t)m * NB * P + (size_t)k * NB, As, As + NB * (2 * NB + 4));
+        } else {
+          set_status(status, SLIM_EINVAL);   // the list holds no groups for this factor
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          __threadfence();
+          red_release_add(&cnt[i * Tt + m], 1);
+          red_release_add(&cnt[i * Tt + m + 1], 1);
+          red_release_add(&cnt[(i + 1) * Tt + m], 1);
+          red_release_add(&cnt[(i + 1) * Tt + m + 1], 1);
+        }
       }
     } else if (tk.type == kTrsm) {
       ok = cta_wait(&cnt[m * Tt + m], m + 1, &cnt[i * Tt + m], m, nullptr, 0, 2, abort_flag,
@@ -1272,7 +1412,7 @@ cudaError_t launch_solve(const CholPlan& p, const void* L, const double* v, doub
 
 }  // namespace
 
-std::vector<CholTask> build_chol_tasks(int T) {
+std::vector<CholTask> build_chol_tasks(int T, bool grouped) {
   // Right-looking order with a lookahead of one panel.  The critical path of
   // panel k+1 (TRSM of tile (k+1,k), its update of the diagonal tile, and the
   // diagonal factorisation) is one task placed right after panel k's, ahead of
@@ -1285,8 +1425,27 @@ std::vector<CholTask> build_chol_tasks(int T) {
     t.push_back({kPanel, (uint16_t)n1, (uint16_t)n1, (uint16_t)k});
     for (int i = n1 + 1; i < T; ++i) t.push_back({kUpd, (uint16_t)i, (uint16_t)n1, (uint16_t)k});
     for (int i = n1 + 2; i < T; ++i) t.push_back({kTrsm, (uint16_t)i, (uint16_t)n1, (uint16_t)n1});
-    for (int m = k + 2; m < T; ++m)
-      for (int i = m; i < T; ++i) t.push_back({kUpd, (uint16_t)i, (uint16_t)m, (uint16_t)k});
+    if (!grouped) {
+      for (int m = k + 2; m < T; ++m)
+        for (int i = m; i < T; ++i) t.push_back({kUpd, (uint16_t)i, (uint16_t)m, (uint16_t)k});
+      continue;
+    }
+    // columns m, m+1 together: the diagonal tile (m, m) alone, then 2x2
+    // groups of rows i, i+1 (i >= m+1, so (m+1, m+1) is a group's diagonal
+    // tile), a last odd row as two tiles; a last odd column tile by tile
+    for (int m = k + 2; m < T; m += 2) {
+      if (m + 1 >= T) {
+        for (int i = m; i < T; ++i) t.push_back({kUpd, (uint16_t)i, (uint16_t)m, (uint16_t)k});
+        continue;
+      }
+      t.push_back({kUpd, (uint16_t)m, (uint16_t)m, (uint16_t)k});
+      int i = m + 1;
+      for (; i + 1 < T; i += 2) t.push_back({kUpd4, (uint16_t)i, (uint16_t)m, (uint16_t)k});
+      if (i < T) {
+        t.push_back({kUpd, (uint16_t)i, (uint16_t)m, (uint16_t)k});
+        t.push_back({kUpd, (uint16_t)i, (uint16_t)(m + 1), (uint16_t)k});
+      }
+    }
   }
   return t;
 }
@@ -1299,7 +1458,7 @@ cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_
   plan->nb = nb;
   plan->T = P / nb;
   plan->is_f32 = is_f32;
-  std::vector<CholTask> tasks = build_chol_tasks(plan->T);
+  std::vector<CholTask> tasks = build_chol_tasks(plan->T, is_f32 && nb == 64);
   plan->ntasks = (int)tasks.size();
   size_t es = is_f32 ? sizeof(float) : sizeof(double);
   cudaError_t e;

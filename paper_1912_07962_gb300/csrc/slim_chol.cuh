@@ -18,12 +18,14 @@ namespace slim {
 struct CholTask {
   uint16_t type, i, m, k;
 };
-enum : uint16_t { kPotrf = 0, kTrsm = 1, kUpd = 2, kPanel = 3 };
+enum : uint16_t { kPotrf = 0, kTrsm = 1, kUpd = 2, kPanel = 3, kUpd4 = 4 };
 
 // Task list in a dependency-compatible order: every task depends only on
 // tasks earlier in the list, so CTAs that claim tasks through an atomic
-// ticket always make progress.
-std::vector<CholTask> build_chol_tasks(int T);
+// ticket always make progress.  With `grouped`, the trailing updates of a
+// step come as 2x2 groups of tiles (kUpd4, top-left tile (i, m)) where the
+// tiles are below the diagonal or on it.
+std::vector<CholTask> build_chol_tasks(int T, bool grouped = false);
 
 struct CholPlan {
   int P = 0;          // padded order (multiple of NB)
