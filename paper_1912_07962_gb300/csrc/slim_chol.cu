@@ -1250,10 +1250,11 @@ __global__ void __launch_bounds__(kThreads) chol_solve_cluster_kernel(
     T w = row_dot<T, NB>(wp, acc);
 #pragma unroll
     for (int o = TPR / 2; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o, TPR);
-    if (sub == 0) {
-      y[i * NB + r] = w;
+    // the TPR lanes of row r all hold w: each stores it into every TPR-th peer
+    if (sub == 0) y[i * NB + r] = w;
+    {
       const uint32_t la = smem_u32(y + i * NB + r), lb = smem_u32(&fbar[i]);
-      for (int d = 0; d < C; ++d)
+      for (int d = sub; d < C; d += TPR)
         if (d != rank) st_async_peer(map_to_rank(la, d), w, map_to_rank(lb, d));
     }
     __syncthreads();
@@ -1298,14 +1299,18 @@ __global__ void __launch_bounds__(kThreads) chol_solve_cluster_kernel(
     __syncthreads();
     part[ch * NB + a] = wp.dot(acc);
     __syncthreads();
-    if (tid < NB) {
+    {
+      // the CH threads of column a form the same sum: each stores it into
+      // every CH-th peer
       T w = T(0);
 #pragma unroll
-      for (int c = 0; c < TP::CH; ++c) w += part[c * NB + tid];
-      zt[i * NB + tid] = w;
-      z[i * NB + tid] = (double)w;
-      const uint32_t la = smem_u32(zt + i * NB + tid), lb = smem_u32(&bbar[i]);
-      for (int d = 0; d < C; ++d)
+      for (int c = 0; c < TP::CH; ++c) w += part[c * NB + a];
+      if (ch == 0) {
+        zt[i * NB + a] = w;
+        z[i * NB + a] = (double)w;
+      }
+      const uint32_t la = smem_u32(zt + i * NB + a), lb = smem_u32(&bbar[i]);
+      for (int d = ch; d < C; d += TP::CH)
         if (d != rank) st_async_peer(map_to_rank(la, d), w, map_to_rank(lb, d));
     }
     __syncthreads();
@@ -1411,44 +1416,6 @@ cudaError_t launch_solve(const CholPlan& p, const void* L, const double* v, doub
 }
 
 }  // namespace
-
-std::vector<CholTask> build_chol_tasks(int T, bool grouped) {
-  // Right-looking order with a lookahead of one panel.  The critical path of
-  // panel k+1 (TRSM of tile (k+1,k), its update of the diagonal tile, and the
-  // diagonal factorisation) is one task placed right after panel k's, ahead of
-  // panel k's remaining trailing updates.
-  std::vector<CholTask> t;
-  t.push_back({kPotrf, 0, 0, 0});
-  for (int i = 2; i < T; ++i) t.push_back({kTrsm, (uint16_t)i, 0, 0});
-  for (int k = 0; k + 1 < T; ++k) {
-    const int n1 = k + 1;
-    t.push_back({kPanel, (uint16_t)n1, (uint16_t)n1, (uint16_t)k});
-    for (int i = n1 + 1; i < T; ++i) t.push_back({kUpd, (uint16_t)i, (uint16_t)n1, (uint16_t)k});
-    for (int i = n1 + 2; i < T; ++i) t.push_back({kTrsm, (uint16_t)i, (uint16_t)n1, (uint16_t)n1});
-    if (!grouped) {
-      for (int m = k + 2; m < T; ++m)
-        for (int i = m; i < T; ++i) t.push_back({kUpd, (uint16_t)i, (uint16_t)m, (uint16_t)k});
-      continue;
-    }
-    // columns m, m+1 together: the diagonal tile (m, m) alone, then 2x2
-    // groups of rows i, i+1 (i >= m+1, so (m+1, m+1) is a group's diagonal
-    // tile), a last odd row as two tiles; a last odd column tile by tile
-    for (int m = k + 2; m < T; m += 2) {
-      if (m + 1 >= T) {
-        for (int i = m; i < T; ++i) t.push_back({kUpd, (uint16_t)i, (uint16_t)m, (uint16_t)k});
-        continue;
-      }
-      t.push_back({kUpd, (uint16_t)m, (uint16_t)m, (uint16_t)k});
-      int i = m + 1;
-      for (; i + 1 < T; i += 2) t.push_back({kUpd4, (uint16_t)i, (uint16_t)m, (uint16_t)k});
-      if (i < T) {
-        t.push_back({kUpd, (uint16_t)i, (uint16_t)m, (uint16_t)k});
-        t.push_back({kUpd, (uint16_t)i, (uint16_t)(m + 1), (uint16_t)k});
-      }
-    }
-  }
-  return t;
-}
 
 cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_sms,
                              int ctas_per_sm) {

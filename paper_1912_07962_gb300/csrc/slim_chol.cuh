@@ -6,26 +6,9 @@
 #include <vector>
 #include <cuda_runtime.h>
 
+#include "slim_chol_tasks.h"
+
 namespace slim {
-
-// One task of the right-looking tiled factorisation.
-//   kPotrf (k):      factor diagonal tile (k,k) and form its inverse
-//   kTrsm  (i,k):    L_ik = A_ik L_kk^{-T}
-//   kUpd   (i,m,k):  A_im -= L_ik L_mk^T   (update from panel k)
-//   kPanel (k+1,k):  the critical path of one panel in one task:
-//                    TRSM(k+1,k), then A_{k+1,k+1} -= L_{k+1,k} L_{k+1,k}^T,
-//                    then POTRF(k+1)
-struct CholTask {
-  uint16_t type, i, m, k;
-};
-enum : uint16_t { kPotrf = 0, kTrsm = 1, kUpd = 2, kPanel = 3, kUpd4 = 4 };
-
-// Task list in a dependency-compatible order: every task depends only on
-// tasks earlier in the list, so CTAs that claim tasks through an atomic
-// ticket always make progress.  With `grouped`, the trailing updates of a
-// step come as 2x2 groups of tiles (kUpd4, top-left tile (i, m)) where the
-// tiles are below the diagonal or on it.
-std::vector<CholTask> build_chol_tasks(int T, bool grouped = false);
 
 struct CholPlan {
   int P = 0;          // padded order (multiple of NB)
