@@ -692,6 +692,9 @@ def main_gpu(args):
               "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
               "launch_ms": launch_log["factor_launch_ms"],
               "iterate_chain_ms": launch_log["iterate_chain_ms"],
+              "aggregate_tflops": chol_flops(cfg.p) / (t_c / args.steps) / 1e12,
+              "aggregate_note": ("one factorisation per step over the region's time per step: the "
+                                 "throughput of the factorisations in flight together"),
               "launches_timed": launch_log["chains"],
               "note": (f"factorisations run up to {args.lookahead} steps ahead of the iterate "
                        "chain, overlapping one another and it; launch_ms is the mean duration "
