@@ -618,7 +618,9 @@ def e2e_block(sl, cfg, b, K, W, lookahead=0, ctas_per_sm=0):
     el = time.perf_counter() - t0
     s.close()
     return {"value": cfg.ell * K / el, "unit": "rows/s", "h2d_bytes_per_step": 4 * cfg.m,
-            "d2h_bytes_per_step": 4 * cfg.n, "seconds": el, "steps": K}
+            "d2h_bytes_per_step": 4 * cfg.n, "seconds": el, "steps": K,
+            "note": ("host clock around K steps, each copying b in from pinned host memory, "
+                     "stepping and copying x out (synchronous), no L2 flush between steps")}
 
 
 def main_gpu(args):
