@@ -60,7 +60,7 @@ typedef enum {
 
 enum { SLIM_F32 = 0, SLIM_F64 = 1 };
 enum { SLIM_PREC_FP64 = 0, SLIM_PREC_FP32 = 1 };
-enum { SLIM_SOLVE_FP64 = 0, SLIM_SOLVE_MIXED = 1 };
+enum { SLIM_SOLVE_FP64 = 0, SLIM_SOLVE_MIXED = 1, SLIM_SOLVE_LSQR = 2 };
 enum { SLIM_BLOCKS_VIEWS = 0, SLIM_BLOCKS_RAYS = 1, SLIM_BLOCKS_STREAM = 2 };
 
 /* Parallel-beam geometry (Sec. 4.3; Joseph rows defined in the library docs).
@@ -120,6 +120,11 @@ typedef struct {
  *                 SLIM_SOLVE_MIXED: float32 tiled Cholesky of the same float64
  *                 matrix, then `refine_iters` rounds of iterative refinement whose
  *                 residual (lambda_k I + G) z is computed in float64
+ *                 SLIM_SOLVE_LSQR: no Gram matrix and no factorisation: s_k of
+ *                 Eq. (slimLSstep) by LSQR for damped least squares (Sec. 4.2),
+ *                 matrix-free over the window's stored taps, float64 vectors;
+ *                 2D view blocks, rows from the projector, lookahead 0 only
+ *                 (SLIM_ENOTSUP otherwise), never captured in a graph
  *   refine_iters  refinement rounds for SLIM_SOLVE_MIXED (0..16)
  *   use_graph     1: capture one step as a CUDA graph at the first slim_step and
  *                 replay it (one graph launch per step)
@@ -137,7 +142,11 @@ typedef struct {
  *                 update of x enqueued on the context's stream and the
  *                 geometry of up to D later steps in flight on internal
  *                 streams (slim_sync waits for those too).  Uses graphs
- *                 whatever use_graph says. */
+ *                 whatever use_graph says.
+ *   lsqr_max_iter SLIM_SOLVE_LSQR: iterations per step at most (1..1000000)
+ *   lsqr_tol      SLIM_SOLVE_LSQR: stop once ||M_k^T (c - M_k s) - lambda_k s||
+ *                 <= lsqr_tol ||M_k^T c|| (LSQR's estimate; 0: lsqr_max_iter
+ *                 iterations exactly) */
 typedef struct {
   double eta;
   int ramp;
@@ -147,7 +156,15 @@ typedef struct {
   int tile;
   int ctas_per_sm;
   int lookahead;
+  int lsqr_max_iter;
+  double lsqr_tol;
 } slim_step_opts;
+
+/* SLIM_SOLVE_LSQR: the last step's LSQR iterations, its final estimate of
+ * ||M_k^T (c - M_k s) - lambda_k s|| and ||M_k^T c|| (synchronises).
+ * SLIM_ESTATE for another solver. */
+slim_status slim_get_lsqr_info(slim_ctx* ctx, int* iters, double* normal_res,
+                               double* normal_res0);
 
 /* Create a context: validates the arguments and allocates all device state
  * (x, b, the ring of r+1 blocks, G and its factor).  r is the memory of

@@ -10,6 +10,7 @@
 #include "slim_chol.cuh"
 #include "slim_kernels.cuh"
 #include "slim_lookahead.cuh"
+#include "slim_lsqr.cuh"
 #include "slim_unet.cuh"
 #include "slim_rays.cuh"
 
@@ -50,6 +51,10 @@ struct slim_ctx {
   double* d_rhs = nullptr;
   double* d_z = nullptr;
   double* d_dz = nullptr;
+  int lsqr_max_iter = 0;
+  double lsqr_tol = 0.0;
+  double* d_lsqr = nullptr;        // LSQR scratch: u [p], v, w, s, tmp [n], partial sums, stats [3]
+  unsigned* d_lsqr_bar = nullptr;  // its grid barrier
   double* d_res = nullptr;
   double* d_ref = nullptr;
   double* d_err = nullptr;
@@ -263,6 +268,7 @@ cudaError_t mark(slim_ctx* c, int i) {
 // refinement round (residual, z += dz), scatter).
 int kernels_per_step(const slim_ctx* c) {
   if (c->dim == 3) return 6;   // sample, march, collect, slice Gram, slice solve, scatter
+  if (c->solver == SLIM_SOLVE_LSQR) return 3;   // sample, forward + residual, LSQR (with x update)
   const int solves = c->solver == SLIM_SOLVE_MIXED ? 1 + c->refine_iters : 1;
   const int refine = c->solver == SLIM_SOLVE_MIXED ? 2 * c->refine_iters : 0;
   if (c->lookahead) {
@@ -336,10 +342,54 @@ cudaError_t enqueue_ray_step_t(slim_ctx* c) {
 }
 
 template <typename T>
+LsqrArgs<T> make_lsqr_args(slim_ctx* c) {
+  LsqrArgs<T> l;
+  l.info = c->d_info;
+  l.p = c->p;
+  l.taps = c->taps;
+  l.n = c->n;
+  l.ring_ids = c->d_ring_ids;
+  l.ring_pix = c->d_ring_pix;
+  l.ring_w = c->d_ring_w;
+  l.c = c->d_rhs;
+  l.eta = c->eta;
+  l.max_iter = c->lsqr_max_iter;
+  l.tol = c->lsqr_tol;
+  l.x = (T*)c->d_x;
+  l.u = c->d_lsqr;
+  l.v = l.u + c->p;
+  l.w = l.v + c->n;
+  l.s = l.w + c->n;
+  l.tmp = l.s + c->n;
+  l.part = l.tmp + c->n;
+  l.stats = l.part + lsqr_part_count(c->num_sms);
+  l.bar = c->d_lsqr_bar;
+  l.status = c->d_status;
+  return l;
+}
+
+template <typename T>
 cudaError_t enqueue_step_t(slim_ctx* c) {
   if (c->kind != SLIM_BLOCKS_VIEWS) return enqueue_ray_step_t<T>(c);
   StepArgs<T> a = make_args<T>(c);
   cudaError_t e;
+  if (c->solver == SLIM_SOLVE_LSQR) {
+    // Eq. (slimLSstep) by LSQR over the window's taps: no Gram, no factor
+    if ((e = mark(c, 0)) != cudaSuccess) return e;
+    if ((e = launch_sample<T>(a, c->stream)) != cudaSuccess) return e;
+    if ((e = mark(c, kPhSample)) != cudaSuccess) return e;
+    if ((e = launch_forward_residual<T>(a, c->stream)) != cudaSuccess) return e;
+    // the residual kernel enters the new block in the pixel map for the Gram
+    // update, which LSQR does not run: clear it for the next step
+    if ((e = cudaMemsetAsync(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int), c->stream)) !=
+        cudaSuccess)
+      return e;
+    for (int ph = kPhForward; ph <= kPhFactor; ++ph)
+      if ((e = mark(c, ph)) != cudaSuccess) return e;
+    if ((e = launch_lsqr<T>(make_lsqr_args<T>(c), c->num_sms, c->stream)) != cudaSuccess) return e;
+    if ((e = mark(c, kPhSolve)) != cudaSuccess) return e;
+    return mark(c, kPhScatter);
+  }
   if ((e = mark(c, 0)) != cudaSuccess) return e;
   if ((e = launch_sample<T>(a, c->stream)) != cudaSuccess) return e;
   if ((e = mark(c, kPhSample)) != cudaSuccess) return e;
@@ -424,7 +474,8 @@ void free_all(slim_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   void* ptrs[] = {c->d_slice_cnt, c->d_slice_rows, c->d_views, c->d_info, c->d_done, c->d_status, c->d_x, c->d_b,
                   c->d_ring_ids, c->d_ring_pix, c->d_ring_w, c->d_map_ray, c->d_map_w,
-                  c->d_G, c->d_L, c->d_rhs, c->d_z, c->d_dz, c->d_res, c->d_ref, c->d_err};
+                  c->d_G, c->d_L, c->d_rhs, c->d_z, c->d_dz, c->d_res, c->d_ref, c->d_err,
+                  c->d_lsqr, c->d_lsqr_bar};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   chol_plan_destroy(&c->plan);
@@ -757,7 +808,23 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     c->tile = step->tile;
     c->lookahead = step->lookahead;
     c->ctas_per_sm = step->ctas_per_sm ? step->ctas_per_sm : (c->lookahead ? 1 : 2);
-    if (!(c->eta > 0.0) || (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED) ||
+    c->lsqr_max_iter = step->lsqr_max_iter;
+    c->lsqr_tol = step->lsqr_tol;
+    if (c->solver == SLIM_SOLVE_LSQR) {
+      if (c->lsqr_max_iter < 1 || c->lsqr_max_iter > 1000000 || !(c->lsqr_tol >= 0.0) ||
+          !std::isfinite(c->lsqr_tol)) {
+        delete c;
+        return SLIM_EINVAL;
+      }
+      if (c->kind != SLIM_BLOCKS_VIEWS || c->dim != 2 || c->a_mode != 0 || c->lookahead != 0) {
+        delete c;
+        return SLIM_ENOTSUP;
+      }
+      c->use_graph = 0;   // a cooperative launch per step
+    }
+    if (!(c->eta > 0.0) ||
+        (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED &&
+         c->solver != SLIM_SOLVE_LSQR) ||
         c->refine_iters < 0 || c->refine_iters > 16 || (c->tile != 0 && c->tile != 32 && c->tile != 64) ||
         c->ctas_per_sm < 1 || c->ctas_per_sm > 4 || c->lookahead < 0 ||
         c->lookahead > kMaxBuf - 1) {
@@ -884,6 +951,12 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
         chk(chol_plan_create(&c->planb[b], c->P, c->nb, c->solver == SLIM_SOLVE_MIXED ? 1 : 0,
                              fgrid, 1), "chol plan");
       }
+    } else if (c->solver == SLIM_SOLVE_LSQR) {
+      const size_t cnt = (size_t)c->p + 4 * (size_t)c->n + lsqr_part_count(c->num_sms) + 3;
+      chk(cudaMalloc(&c->d_lsqr, cnt * sizeof(double)), "cudaMalloc");
+      chk(cudaMalloc(&c->d_lsqr_bar, 2 * sizeof(unsigned)), "cudaMalloc");
+      // tmp (and the rest) start at zero: the solve leaves tmp at zero
+      chk(cudaMemset(c->d_lsqr, 0, cnt * sizeof(double)), "memset");
     } else if (dense_solve)
       chk(chol_plan_create(&c->plan, c->P, c->nb, c->solver == SLIM_SOLVE_MIXED ? 1 : 0,
                            c->num_sms, c->ctas_per_sm), "chol plan");
@@ -1195,8 +1268,23 @@ slim_status slim_restore(slim_ctx* c, const void* buf, size_t len) {
   return slim_set_iter(c, h.k);
 }
 
+slim_status slim_get_lsqr_info(slim_ctx* c, int* iters, double* normal_res, double* normal_res0) {
+  if (!c) return SLIM_EINVAL;
+  if (c->solver != SLIM_SOLVE_LSQR) return fail(c, SLIM_ESTATE, "lsqr_info: not an LSQR context");
+  CK(cudaStreamSynchronize(c->stream), "lsqr_info");
+  double st[3];
+  CK(cudaMemcpy(st, c->d_lsqr + (size_t)c->p + 4 * (size_t)c->n + lsqr_part_count(c->num_sms),
+                sizeof(st), cudaMemcpyDeviceToHost), "lsqr_info");
+  if (iters) *iters = (int)st[0];
+  if (normal_res) *normal_res = st[1];
+  if (normal_res0) *normal_res0 = st[2];
+  return read_status(c);
+}
+
 slim_status slim_get_memory(slim_ctx* c, int* ids, double* G, double* z) {
   if (!c) return SLIM_EINVAL;
+  if (c->solver == SLIM_SOLVE_LSQR && (G || z))
+    return fail(c, SLIM_ENOTSUP, "get_memory: LSQR keeps no Gram matrix and no z");
   CK(cudaStreamSynchronize(c->stream), "get_memory");
   if (c->lookahead) {
     // gather the window of step h_k from the extended ring into ring order
@@ -1709,7 +1797,7 @@ extern "C" slim_status slim_batch_create(int count, const slim_geometry* geoms,
       slim_batch_destroy(b);
       return st;
     }
-    if (c->lookahead) {   // a batch captures one plain chain per problem
+    if (c->lookahead || c->solver == SLIM_SOLVE_LSQR) {   // a batch captures one plain chain per problem
       slim_destroy(c);
       slim_batch_destroy(b);
       return SLIM_ENOTSUP;
