@@ -373,6 +373,53 @@ def csr_block(sl, cfg, flush, stream, reps=20):
     return out
 
 
+def lsqr_block(sl, cfg, b, flush, stream, K, W, tol=1e-6, max_iter=5000):
+    """The step of Eq. (slimLSstep) by LSQR instead of the Woodbury form, on
+    the same workload: float64 iterate, each step timed alone with events
+    after an L2 flush; iterations per step from the library.  Algorithmic
+    bytes of one LSQR iteration: the window's tap rows read twice (pixel +
+    float64 weight, 12 B per tap slot), the gathered v and the scattered
+    M^T u (8 B per stored tap each), and the n-vectors of the two element
+    passes (v, w, s, tmp: 9 reads or writes of 8 B per pixel)."""
+    import torch
+    s = sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.ell, cfg.r, cfg.lam, cfg.seed,
+                precision=sl.SLIM_PREC_FP64, solver=sl.SLIM_SOLVE_LSQR, lsqr_max_iter=max_iter,
+                lsqr_tol=tol)
+    s.set_stream(stream.cuda_stream)
+    s.set_data(b)
+    for i in range(W):
+        flush.fill_(i)
+        s.step(1)
+    torch.cuda.synchronize()
+    ms, its = [], []
+    for i in range(K):
+        flush.fill_(i)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        its.append(s.lsqr_info()[0])
+    s.close()
+    tot_ms, tot_it = sum(ms), sum(its)
+    taps = 2 * cfg.N
+    stored = 0.85 * taps          # stored taps per ray (about 2N x 0.85 for this geometry)
+    p = (cfg.r + 1) * cfg.ell
+    byts = p * taps * 12 * 2 + p * stored * 8 * 2 + cfg.n * 8 * 9
+    gbs = byts * tot_it / (tot_ms * 1e-3) / 1e9
+    hbm = measured_peaks().get("hbm_gbs", 6797.2)
+    return {"workload": f"{cfg.name}, step by LSQR to ||M^T r - lambda s|| <= {tol:g} ||M^T c||",
+            "rows_per_s": cfg.ell * K / (tot_ms * 1e-3), "ms_per_step": tot_ms / K,
+            "iterations_per_step": tot_it / K, "iterations_min_max": [min(its), max(its)],
+            "us_per_iteration": tot_ms * 1e3 / max(tot_it, 1), "steps": K, "warmup": W,
+            "algorithmic_bytes_per_iteration": byts, "GB_s": gbs,
+            "frac_of_measured_hbm": gbs / hbm,
+            "note": ("one cooperative launch per step (two grid-wide sums per iteration); the "
+                     "window's taps and vectors are L2-resident, so the fraction is of the HBM "
+                     "copy peak for scale only")}
+
+
 def stream3d_block(sl, flush, stream, K, W, steps_per_view=46):
     """The 3D streaming form at 256^3: float32 volume, random rays from the views
     that have arrived, float64 per-slice solves, one CUDA graph per step."""
@@ -719,6 +766,8 @@ def main_gpu(args):
     s3d = stream3d_block(sl, flush, stream, args.steps, args.warmup) if rank == 0 and not args.no_3d else None
     batch = (batch_block(sl, flush, stream, args.batch_steps, max(3, args.warmup))
              if rank == 0 and args.batch_steps > 0 else None)
+    lsqr_pass = (lsqr_block(sl, cfg, b, flush, stream, args.lsqr_steps, 3)
+                 if rank == 0 and args.lsqr_steps > 0 else None)
     warm = warm_start_block(args) if rank == 0 and args.warm_start else None
     unet = (unet_block(sl, flush, stream, reps=args.unet_reps)
             if rank == 0 and not args.no_unet else None)
@@ -757,7 +806,7 @@ def main_gpu(args):
         "phases_note": ("one step at a time (synchronous pass); the pipelined region overlaps "
                         "the geometry phases with the iterate chain" if args.lookahead else
                         "per step, inside the timed region"),
-        "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "batched": batch, "unet": unet, "warm_start": warm, "tta": tta, "e2e": e2e,
+        "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "batched": batch, "lsqr": lsqr_pass, "unet": unet, "warm_start": warm, "tta": tta, "e2e": e2e,
         "cpu_baseline": cpu,
         "gpu_launches": kernels * args.steps, "kernels_per_step": kernels, "clocks": clocks,
     }
@@ -785,6 +834,20 @@ def main_csr(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     cfg, _ = workload_of(args.workload)
     print(json.dumps({"csr_full_pass": csr_block(sl, cfg, flush, stream, reps=args.csr_reps)}))
+
+
+def main_lsqr(args):
+    """The LSQR-step form alone (one JSON line), e.g. for a profile."""
+    import torch
+    from paper_1912_07962_gb300 import build as slbuild, slim as sl
+    slbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    cfg, _ = workload_of(args.workload)
+    x_true, e = workloads.tomo_inputs_2d(cfg)
+    b = make_b(sl, cfg, x_true, e)
+    print(json.dumps({"lsqr": lsqr_block(sl, cfg, b, flush, stream, args.lsqr_steps, 3)}))
 
 
 def main_reference(args):
@@ -822,6 +885,10 @@ def main():
     ap.add_argument("--no-csr", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-unet", action="store_true")
+    ap.add_argument("--lsqr-steps", type=int, default=12,
+                    help="steps of the LSQR-step form timed on the workload (0: skip)")
+    ap.add_argument("--lsqr-only", action="store_true",
+                    help="time only the LSQR-step form and print that line")
     ap.add_argument("--unet-only", action="store_true",
                     help="time only the network (forward and training step) and print that line")
     ap.add_argument("--unet-reps", type=int, default=10)
@@ -860,6 +927,8 @@ def main():
         main_unet(args)
     elif args.csr_only:
         main_csr(args)
+    elif args.lsqr_only:
+        main_lsqr(args)
     else:
         main_gpu(args)
 

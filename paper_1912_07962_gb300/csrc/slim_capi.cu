@@ -414,7 +414,8 @@ cudaError_t rebuild_t(slim_ctx* c, long long k) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(c->d_ring_ids, 0xFF, (size_t)c->p * sizeof(int), s)) != cudaSuccess)
     return e;
-  if ((e = cudaMemsetAsync(c->d_G, 0, (size_t)c->P * c->P * sizeof(double), s)) != cudaSuccess)
+  if (c->d_G && (e = cudaMemsetAsync(c->d_G, 0, (size_t)c->P * c->P * sizeof(double), s)) !=
+                    cudaSuccess)
     return e;
   if (c->d_map_ray &&
       (e = cudaMemsetAsync(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int), s)) != cudaSuccess)
@@ -438,7 +439,7 @@ cudaError_t rebuild_t(slim_ctx* c, long long k) {
     }
     if ((e = launch_sample<T>(a, s)) != cudaSuccess) return e;
     if ((e = launch_forward_residual<T>(a, s)) != cudaSuccess) return e;
-    if ((e = launch_gram_update<T>(a, s)) != cudaSuccess) return e;
+    if (c->solver != SLIM_SOLVE_LSQR && (e = launch_gram_update<T>(a, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int), s)) !=
         cudaSuccess)
       return e;
@@ -894,7 +895,8 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     chk(cudaEventCreateWithFlags(&c->ev_g1, cudaEventDisableTiming), "event");
   }
   const int ring_rows = la ? c->Pe : c->p;
-  const size_t g_elems = la ? (size_t)c->Pe * c->Pe : (size_t)c->P * c->P;
+  const bool lsqr = c->solver == SLIM_SOLVE_LSQR;   // no Gram matrix, no factor
+  const size_t g_elems = lsqr ? 0 : la ? (size_t)c->Pe * c->Pe : (size_t)c->P * c->P;
   const size_t es = elem(c->precision);
   const size_t fs = c->solver == SLIM_SOLVE_FP64 ? sizeof(double) : sizeof(float);
   struct { void** p; size_t bytes; } allocs[] = {
@@ -910,7 +912,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       {(void**)&c->d_map_ray, use_map ? 2 * (size_t)c->n * sizeof(int) : 0},
       {(void**)&c->d_map_w, use_map ? 2 * (size_t)c->n * sizeof(double) : 0},
       {(void**)&c->d_G, g_elems * sizeof(double)},
-      {&c->d_L, dense_solve && !la ? (size_t)c->P * c->P * fs : 0},
+      {&c->d_L, dense_solve && !la && !lsqr ? (size_t)c->P * c->P * fs : 0},
       {(void**)&c->d_gdone, la ? sizeof(long long) : 0},
       {(void**)&c->d_info_buf, la ? c->nbuf * sizeof(StepInfo) : 0},
       {(void**)&c->d_ext, la ? (size_t)c->nbuf * c->P * sizeof(int) : 0},
@@ -935,8 +937,8 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     chk(cudaMemset(c->d_ring_pix, 0xFF, (size_t)ring_rows * c->taps * sizeof(int)), "memset");
     chk(cudaMemset(c->d_ring_w, 0, (size_t)ring_rows * c->taps * sizeof(double)), "memset");
     if (use_map) chk(cudaMemset(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int)), "memset");
-    chk(cudaMemset(c->d_G, 0, g_elems * sizeof(double)), "memset");
-    if (dense_solve && !la) chk(cudaMemset(c->d_L, 0, (size_t)c->P * c->P * fs), "memset");
+    if (g_elems) chk(cudaMemset(c->d_G, 0, g_elems * sizeof(double)), "memset");
+    if (dense_solve && !la && !lsqr) chk(cudaMemset(c->d_L, 0, (size_t)c->P * c->P * fs), "memset");
     chk(cudaMemset(c->d_z, 0, (size_t)c->P * sizeof(double)), "memset");
     if (la) {
       for (int b = 0; b < c->nbuf && st == SLIM_OK; ++b)

@@ -10,6 +10,7 @@
 //   phase A  rows:     u' = (M v_raw)/alpha - alpha u_raw/beta, tmp += M^T u'
 //            elements: the previous iteration's s += (phi/rho) w,
 //                      w = v_raw/alpha - (theta/rho) w
+//            (the scalings by 1/alpha, 1/beta are products with reciprocals)
 //            sum ||u'||^2 -> beta'
 //   phase B  elements: v' = tmp/beta' - beta' v_raw/alpha, tmp = 0
 //            sum ||v'||^2 -> alpha'
@@ -31,7 +32,7 @@ namespace {
 
 constexpr int kLsqrThreads = 256;
 constexpr int kLsqrWarps = kLsqrThreads / 32;
-constexpr unsigned kLsqrSpin = 1u << 22;   // polls of a barrier before giving up
+constexpr unsigned kLsqrSpin = 1u << 22;   // polls of a barrier before giving up (about a second)
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
@@ -64,7 +65,6 @@ __device__ bool grid_barrier(unsigned* bar, int* status, int* s_flag) {
           ok = 0;
           break;
         }
-        __nanosleep(32);
       }
     }
     *s_flag = ok;
@@ -163,10 +163,12 @@ __global__ void __launch_bounds__(kLsqrThreads) lsqr_kernel(LsqrArgs<T> a) {
     write_stats(0, 0.0, 0.0);
     return;
   }
-  // v_raw = M^T c / beta; alpha_1 = ||v_raw||
+  // v_raw = M^T c / beta; alpha_1 = ||v_raw||  (scalings by reciprocals
+  // computed once: float64 division is slow on this GPU's FP64 pipe)
   acc = 0.0;
+  const double inv_beta1 = 1.0 / beta;
   for (long long j = gt; j < a.n; j += nthreads) {
-    const double t = __ldcg(a.tmp + j) / beta;
+    const double t = __ldcg(a.tmp + j) * inv_beta1;
     a.tmp[j] = 0.0;
     a.v[j] = t;
     acc += t * t;
@@ -187,29 +189,42 @@ __global__ void __launch_bounds__(kLsqrThreads) lsqr_kernel(LsqrArgs<T> a) {
     ++it;
     // phase A: update of s and w owed by the previous iteration (w_1 = v_1),
     // then u' = M v - alpha u and its scatter
+    const double inv_alpha = 1.0 / alpha;
+    const double inv_beta = beta > 0.0 ? 1.0 / beta : 1.0;
+    const double cs = phi / rho, cw = theta / rho;
     for (long long j = gt; j < a.n; j += nthreads) {
-      const double vj = a.v[j] / alpha;
+      const double vj = a.v[j] * inv_alpha;
       if (it == 1) {
         a.w[j] = vj;
       } else {
         const double wj = a.w[j];
-        a.s[j] += (phi / rho) * wj;
-        a.w[j] = vj - (theta / rho) * wj;
+        a.s[j] += cs * wj;
+        a.w[j] = vj - cw * wj;
       }
     }
     acc = 0.0;
     for (int q = gw; q < a.p; q += nwarps) {
-      const double uq = beta > 0.0 ? a.u[q] / beta : a.u[q];
+      const double uq = a.u[q] * inv_beta;
       double mv = 0.0;
       const bool row = a.ring_ids[q] >= 0;
       const int* rp = a.ring_pix + (size_t)q * a.taps;
       const double* rw = a.ring_w + (size_t)q * a.taps;
       if (row) {
-        for (int t = lane; t < a.taps; t += 32) {
-          const int pix = rp[t];
-          if (pix >= 0) mv += rw[t] * __ldcg(a.v + pix);   // other SMs wrote v: around L1
+        // four taps per lane per round: their loads are issued together
+        for (int t0 = lane; t0 < a.taps; t0 += 128) {
+          int pix[4];
+          double wt[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int t = t0 + 32 * e;
+            pix[e] = t < a.taps ? rp[t] : -1;
+            wt[e] = t < a.taps ? rw[t] : 0.0;
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e)   // other SMs wrote v: read around L1
+            if (pix[e] >= 0) mv += wt[e] * __ldcg(a.v + pix[e]);
         }
-        mv = warp_sum(mv) / alpha;
+        mv = warp_sum(mv) * inv_alpha;
       }
       const double un = mv - alpha * uq;
       if (lane == 0) {
@@ -223,10 +238,11 @@ __global__ void __launch_bounds__(kLsqrThreads) lsqr_kernel(LsqrArgs<T> a) {
     beta_n = sqrt(beta_n);
     // phase B: v' = M^T u'/beta' - beta' v
     acc = 0.0;
+    const double inv_beta_n = beta_n > 0.0 ? 1.0 / beta_n : 1.0;
     for (long long j = gt; j < a.n; j += nthreads) {
       const double mt = __ldcg(a.tmp + j);
       a.tmp[j] = 0.0;
-      const double t = (beta_n > 0.0 ? mt / beta_n : mt) - beta_n * (a.v[j] / alpha);
+      const double t = mt * inv_beta_n - beta_n * (a.v[j] * inv_alpha);
       a.v[j] = t;
       acc += t * t;
     }
@@ -250,8 +266,9 @@ __global__ void __launch_bounds__(kLsqrThreads) lsqr_kernel(LsqrArgs<T> a) {
     if (a.tol > 0.0 && res <= a.tol * res0) break;
   }
   // the last iteration's update of s, and x -= eta s
+  const double cs_last = phi / rho;
   for (long long j = gt; j < a.n; j += nthreads) {
-    const double sj = a.s[j] + (phi / rho) * a.w[j];
+    const double sj = a.s[j] + cs_last * a.w[j];
     a.s[j] = sj;
     a.x[j] = (T)((double)a.x[j] - a.eta * sj);
   }
@@ -269,7 +286,8 @@ cudaError_t launch_lsqr(const LsqrArgs<T>& a, int num_sms, cudaStream_t s) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lsqr_kernel<T>, kLsqrThreads, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-  const int grid = std::max(1, num_sms) * std::min(per_sm, 2);
+  // one CTA per SM: fewer arrivals at each grid barrier
+  const int grid = std::max(1, num_sms) * std::min(per_sm, 1);
   if ((e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), s)) != cudaSuccess) return e;
   LsqrArgs<T> args = a;
   void* params[] = {&args};

@@ -34,8 +34,7 @@ struct LsqrArgs {
   int* status;
 };
 
-// Cooperative launch of the whole solve and the update of x; the grid is the
-// number of CTAs that can be resident at once (at most num_sms * 2).
+// Cooperative launch of the whole solve and the update of x, one CTA per SM.
 template <typename T>
 cudaError_t launch_lsqr(const LsqrArgs<T>& a, int num_sms, cudaStream_t s);
 
