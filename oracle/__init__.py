@@ -16,6 +16,8 @@ Modules
   slim     one slimLS step, Eq. (ram)/(B_k), in Woodbury and direct form; runs
   targets  reference solutions: x_LS (Eq. LS), Tikhonov x_tik, CGLS
   theory   Sec. 3 quantities for r = 0: B_k(alpha), B, x_hat (Eq. xhat), bounds
+  lsqr     LSQR for the damped least-squares step of Eq. (slimLSstep)
+  tik      one slimTik step, Eq. (slimTik) (C_k = L^T L), direct and Woodbury form
 
 Parity status: every function is pinned by tests in `tests/test_oracle_*.py`
 against closed forms, special cases and the paper's theorems, except the
