@@ -420,6 +420,45 @@ def lsqr_block(sl, cfg, b, flush, stream, K, W, tol=1e-6, max_iter=5000):
                      "copy peak for scale only")}
 
 
+def tik_block(sl, cfg, b, flush, stream, K, W, lam_tik=1.0, lookahead=6, ctas_per_sm=1):
+    """slimTik (Eq. slimTik, C_k = diag(c)) on the same workload, against
+    slimLS in the same form and timing: float32 iterate, float64 Gram
+    M C^{-1} M^T, float32 tiled Cholesky + 2 float64-residual refinements;
+    one CUDA graph per step (lookahead 0, each step timed alone, with its
+    phases) and the pipelined form (the headline's timing: K steps in one
+    region after W warm-up steps).  c is seeded uniform in [0.5, 2];
+    beta = lam_tik^2 / A_v."""
+    c = 0.5 + 1.5 * np.random.default_rng(cfg.seed).random(cfg.n)
+    out = {"workload": f"{cfg.name}, slimTik with lam_tik = {lam_tik:g}, C_k = diag(c)",
+           "steps": K, "warmup": W}
+    for name, lt in (("slimls", 0.0), ("slimtik", lam_tik)):
+        row = {}
+        for la in (0, lookahead):
+            s = sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.ell, cfg.r, cfg.lam, cfg.seed,
+                        precision=sl.SLIM_PREC_FP32, solver=sl.SLIM_SOLVE_MIXED, refine_iters=2,
+                        use_graph=True, tik_lambda=lt, lookahead=la,
+                        ctas_per_sm=ctas_per_sm if la else 0)
+            s.set_data(b.astype(np.float32))
+            if lt > 0:
+                s.set_c_diag(c)
+            if la:
+                per, _, _ = timed_region(s, K, W, flush, stream)
+                row[f"lookahead_{la}"] = {"rows_per_s": cfg.ell * K / (sum(per) * 1e-3),
+                                          "ms_per_step": sum(per) / K}
+            else:
+                per, ph, _, _ = timed_steps(s, K, W, flush, stream)
+                row["lookahead_0"] = {"rows_per_s": cfg.ell * K / (sum(per) * 1e-3),
+                                      "ms_per_step": sum(per) / K,
+                                      "phase_ms": {k: v / K for k, v in ph.items()},
+                                      "kernels_per_step": s.kernels_per_step()}
+            s.close()
+        out[name] = row
+    for key in out["slimls"]:
+        out[f"overhead_{key}"] = (out["slimtik"][key]["ms_per_step"] /
+                                  out["slimls"][key]["ms_per_step"] - 1.0)
+    return out
+
+
 def stream3d_block(sl, flush, stream, K, W, steps_per_view=46):
     """The 3D streaming form at 256^3: float32 volume, random rays from the views
     that have arrived, float64 per-slice solves, one CUDA graph per step."""
@@ -768,6 +807,9 @@ def main_gpu(args):
              if rank == 0 and args.batch_steps > 0 else None)
     lsqr_pass = (lsqr_block(sl, cfg, b, flush, stream, args.lsqr_steps, 3)
                  if rank == 0 and args.lsqr_steps > 0 else None)
+    tik_pass = (tik_block(sl, cfg, b, flush, stream, args.tik_steps, max(3, args.warmup),
+                          lookahead=args.lookahead or 6, ctas_per_sm=args.factor_ctas_per_sm)
+                if rank == 0 and args.tik_steps > 0 else None)
     warm = warm_start_block(args) if rank == 0 and args.warm_start else None
     unet = (unet_block(sl, flush, stream, reps=args.unet_reps)
             if rank == 0 and not args.no_unet else None)
@@ -806,7 +848,7 @@ def main_gpu(args):
         "phases_note": ("one step at a time (synchronous pass); the pipelined region overlaps "
                         "the geometry phases with the iterate chain" if args.lookahead else
                         "per step, inside the timed region"),
-        "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "batched": batch, "lsqr": lsqr_pass, "unet": unet, "warm_start": warm, "tta": tta, "e2e": e2e,
+        "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "batched": batch, "lsqr": lsqr_pass, "tik": tik_pass, "unet": unet, "warm_start": warm, "tta": tta, "e2e": e2e,
         "cpu_baseline": cpu,
         "gpu_launches": kernels * args.steps, "kernels_per_step": kernels, "clocks": clocks,
     }
@@ -850,6 +892,22 @@ def main_lsqr(args):
     print(json.dumps({"lsqr": lsqr_block(sl, cfg, b, flush, stream, args.lsqr_steps, 3)}))
 
 
+def main_tik(args):
+    """slimTik against slimLS alone (one JSON line)."""
+    import torch
+    from paper_1912_07962_gb300 import build as slbuild, slim as sl
+    slbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    cfg, _ = workload_of(args.workload)
+    x_true, e = workloads.tomo_inputs_2d(cfg)
+    b = make_b(sl, cfg, x_true, e)
+    print(json.dumps({"tik": tik_block(sl, cfg, b, flush, stream, args.tik_steps,
+                                       max(3, args.warmup), lookahead=args.lookahead or 6,
+                                       ctas_per_sm=args.factor_ctas_per_sm)}))
+
+
 def main_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -889,6 +947,10 @@ def main():
                     help="steps of the LSQR-step form timed on the workload (0: skip)")
     ap.add_argument("--lsqr-only", action="store_true",
                     help="time only the LSQR-step form and print that line")
+    ap.add_argument("--tik-steps", type=int, default=30,
+                    help="steps of slimTik and slimLS timed side by side (0: skip)")
+    ap.add_argument("--tik-only", action="store_true",
+                    help="time only slimTik against slimLS and print that line")
     ap.add_argument("--unet-only", action="store_true",
                     help="time only the network (forward and training step) and print that line")
     ap.add_argument("--unet-reps", type=int, default=10)
@@ -929,6 +991,8 @@ def main():
         main_csr(args)
     elif args.lsqr_only:
         main_lsqr(args)
+    elif args.tik_only:
+        main_tik(args)
     else:
         main_gpu(args)
 

@@ -146,7 +146,22 @@ typedef struct {
  *   lsqr_max_iter SLIM_SOLVE_LSQR: iterations per step at most (1..1000000)
  *   lsqr_tol      SLIM_SOLVE_LSQR: stop once ||M_k^T (c - M_k s) - lambda_k s||
  *                 <= lsqr_tol ||M_k^T c|| (LSQR's estimate; 0: lsqr_max_iter
- *                 iterations exactly) */
+ *                 iterations exactly)
+ *   tik_lambda    slimTik (Sec. 2, Eq. slimTik): slimLS applied to the Tikhonov
+ *                 problem min ||A x - b||^2 + tik_lambda^2 ||L x||^2 (Eq. TLS1)
+ *                 with C_k = L^T L (set by slim_set_c_diag, default I) and
+ *                 M = A_v blocks:
+ *                   x_k = x_{k-1} - (mu_k C + M_k^T M_k)^{-1}
+ *                         (A_k^T (A_k x_{k-1} - b_k) + beta C x_{k-1}),
+ *                   beta = tik_lambda^2 / A_v,  mu_k = lambda_k + c_k beta.
+ *                 0 = plain slimLS.  2D view blocks, Woodbury form (FP64 or
+ *                 MIXED solver; SLIM_ENOTSUP otherwise), with or without
+ *                 lookahead (mu_k I + M_k C^{-1} M_k^T depends only on the
+ *                 blocks drawn)
+ *   tik_reading   c_k, the Tikhonov rows that the stacked M_k holds: 0 = the
+ *                 blocks of M_k, min(k, r+1) (slimLS on the stacked problem,
+ *                 whose full-memory iterates reach the Tikhonov solution);
+ *                 1 = r, as Eq. (slimTik) prints it */
 typedef struct {
   double eta;
   int ramp;
@@ -158,6 +173,8 @@ typedef struct {
   int lookahead;
   int lsqr_max_iter;
   double lsqr_tol;
+  double tik_lambda;
+  int tik_reading;
 } slim_step_opts;
 
 /* SLIM_SOLVE_LSQR: the last step's LSQR iterations, its final estimate of
@@ -189,6 +206,18 @@ slim_status slim_set_data(slim_ctx* ctx, const void* b, size_t m, int dtype, int
 
 /* x_0 (default 0), n values, copied.  Does not change the step counter. */
 slim_status slim_set_x(slim_ctx* ctx, const void* x, size_t n, int dtype, int on_device);
+
+/* C_k = diag(c) of Eq. (B_k), constant over k (C_k = L^T L with L = diag(sqrt c)
+ * in slimTik), n values > 0 and finite (host or device, SLIM_F32/SLIM_F64),
+ * copied; NULL restores C_k = I.  The step becomes
+ *   x_k = x_{k-1} - (lambda_k C + M_k^T M_k)^{-1} A_k^T r_k  (plus the slimTik
+ * terms when tik_lambda > 0), computed as (mu_k I + M_k C^{-1} M_k^T) z = rhs,
+ * x_k = (1 - eta beta/mu_k) x_{k-1} - eta C^{-1} M_k^T z.  The memory of the
+ * steps taken so far is rebuilt with the new C (with lookahead, the steps
+ * prepared ahead are prepared again).  2D view blocks, Woodbury form
+ * (SLIM_ENOTSUP otherwise); SLIM_EINVAL if a value is not positive.
+ * Synchronises. */
+slim_status slim_set_c_diag(slim_ctx* ctx, const void* c, size_t n, int dtype, int on_device);
 
 /* Copy the current iterate into the caller's buffer (synchronises; returns
  * any device-side error recorded since the last synchronising call). */

@@ -53,6 +53,9 @@ struct slim_ctx {
   double* d_dz = nullptr;
   int lsqr_max_iter = 0;
   double lsqr_tol = 0.0;
+  double tik_lambda = 0.0;         // slimTik: lam_tik of Eq. (TLS1) (0: slimLS)
+  int tik_reading = 0;             // count of Tikhonov rows: 0 blocks of M_k, 1 r
+  double* d_cinv = nullptr;        // [n] 1/c of C_k = diag(c); null: C_k = I
   double* d_lsqr = nullptr;        // LSQR scratch: u [p], v, w, s, tmp [n], partial sums, stats [3]
   unsigned* d_lsqr_bar = nullptr;  // its grid barrier
   double* d_res = nullptr;
@@ -212,6 +215,9 @@ StepArgs<T> make_args(slim_ctx* c) {
   a.csr_col = c->a_mode ? c->csr.col : nullptr;
   a.csr_val = c->a_mode ? c->csr.val : nullptr;
   a.csr_bf16 = c->csr.bf16;
+  a.tik_beta = c->tik_lambda * c->tik_lambda / c->n_views;   // M = A_v view blocks
+  a.tik_reading = c->tik_reading;
+  a.cinv = c->d_cinv;
   return a;
 }
 
@@ -275,10 +281,12 @@ int kernels_per_step(const slim_ctx* c) {
     // geometry: sample, taps, Gram, map clear, ring map, K, factor; iterate:
     // residual, the solves, refinement rounds, scatter
     const int per_solve = c->planb[0].cluster ? 1 : 2;
-    return 7 + 1 + per_solve * solves + refine + 1;
+    const int tik = c->tik_lambda > 0.0 ? 2 : 0;   // window projection, x scale
+    return 7 + 1 + per_solve * solves + refine + 1 + tik;
   }
   const int per_solve = c->plan.cluster ? 1 : 2;
-  return 5 + per_solve * solves + refine + 1;
+  const int tik = c->tik_lambda > 0.0 ? 2 : 0;   // window projection, x scale
+  return 5 + per_solve * solves + refine + 1 + tik;
 }
 
 // The damped solve (lambda_k I + G) z = rhs: float64 tiled Cholesky, or a
@@ -394,11 +402,15 @@ cudaError_t enqueue_step_t(slim_ctx* c) {
   if ((e = launch_sample<T>(a, c->stream)) != cudaSuccess) return e;
   if ((e = mark(c, kPhSample)) != cudaSuccess) return e;
   if ((e = launch_forward_residual<T>(a, c->stream)) != cudaSuccess) return e;
+  const bool tik = c->tik_lambda > 0.0;
+  // slimTik: rhs c - (beta/mu_k) M_k x_{k-1}
+  if (tik && (e = launch_tik_rhs<T>(a, c->stream)) != cudaSuccess) return e;
   if ((e = mark(c, kPhForward)) != cudaSuccess) return e;
   if ((e = launch_gram_update<T>(a, c->stream)) != cudaSuccess) return e;
   if ((e = mark(c, kPhGram)) != cudaSuccess) return e;
   if ((e = enqueue_solve(c)) != cudaSuccess) return e;
   if ((e = mark(c, kPhSolve)) != cudaSuccess) return e;
+  if (tik && (e = launch_tik_scale<T>(a, c->stream)) != cudaSuccess) return e;
   if ((e = launch_scatter<T>(a, c->stream)) != cudaSuccess) return e;
   return mark(c, kPhScatter);
 }
@@ -476,7 +488,7 @@ void free_all(slim_ctx* c) {
   void* ptrs[] = {c->d_slice_cnt, c->d_slice_rows, c->d_views, c->d_info, c->d_done, c->d_status, c->d_x, c->d_b,
                   c->d_ring_ids, c->d_ring_pix, c->d_ring_w, c->d_map_ray, c->d_map_w,
                   c->d_G, c->d_L, c->d_rhs, c->d_z, c->d_dz, c->d_res, c->d_ref, c->d_err,
-                  c->d_lsqr, c->d_lsqr_bar};
+                  c->d_lsqr, c->d_lsqr_bar, c->d_cinv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   chol_plan_destroy(&c->plan);
@@ -562,6 +574,9 @@ LaArgs<T> make_la_args(slim_ctx* c) {
   a.x = (T*)c->d_x;
   a.b = (const T*)c->d_b;
   a.status = c->d_status;
+  a.tik_beta = c->tik_lambda * c->tik_lambda / c->n_views;   // M = A_v view blocks
+  a.tik_reading = c->tik_reading;
+  a.cinv = c->d_cinv;
   return a;
 }
 
@@ -610,9 +625,12 @@ cudaError_t la_enqueue_iterate(slim_ctx* c, int b, cudaStream_t s) {
   if ((e = la_mark(c, 6, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->d_rhs, 0, (size_t)c->P * sizeof(double), s)) != cudaSuccess) return e;
   if ((e = la_launch_residual<T>(a, info, s)) != cudaSuccess) return e;
+  const bool tik = c->tik_lambda > 0.0;
+  // slimTik: rhs c - (beta/mu_k) M_k x_{k-1}
+  if (tik && (e = la_launch_tik_rhs<T>(a, ext, info, s)) != cudaSuccess) return e;
   if ((e = la_mark(c, 7, s)) != cudaSuccess) return e;
-  // the right-hand side is zero above the newest block (the last one)
-  const int first_tile = (c->nslots - 1) * c->ell / c->nb;
+  // slimLS: the right-hand side is zero above the newest block (the last one)
+  const int first_tile = tik ? 0 : (c->nslots - 1) * c->ell / c->nb;
   if ((e = chol_solve(c->planb[b], c->d_Lb[b], c->d_rhs, c->d_z, c->d_status, s, first_tile)) !=
       cudaSuccess)
     return e;
@@ -628,6 +646,7 @@ cudaError_t la_enqueue_iterate(slim_ctx* c, int b, cudaStream_t s) {
     }
   }
   if ((e = la_mark(c, 8, s)) != cudaSuccess) return e;
+  if (tik && (e = la_launch_tik_scale<T>(a, info, s)) != cudaSuccess) return e;
   if ((e = la_launch_scatter<T>(a, ext, s)) != cudaSuccess) return e;
   return la_mark(c, 9, s);
 }
@@ -811,6 +830,18 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     c->ctas_per_sm = step->ctas_per_sm ? step->ctas_per_sm : (c->lookahead ? 1 : 2);
     c->lsqr_max_iter = step->lsqr_max_iter;
     c->lsqr_tol = step->lsqr_tol;
+    c->tik_lambda = step->tik_lambda;
+    c->tik_reading = step->tik_reading;
+    if (!(c->tik_lambda >= 0.0) || !std::isfinite(c->tik_lambda) ||
+        (c->tik_reading != 0 && c->tik_reading != 1)) {
+      delete c;
+      return SLIM_EINVAL;
+    }
+    if (c->tik_lambda > 0.0 && (c->kind != SLIM_BLOCKS_VIEWS || c->dim != 2 ||
+                                c->solver == SLIM_SOLVE_LSQR)) {
+      delete c;
+      return SLIM_ENOTSUP;
+    }
     if (c->solver == SLIM_SOLVE_LSQR) {
       if (c->lsqr_max_iter < 1 || c->lsqr_max_iter > 1000000 || !(c->lsqr_tol >= 0.0) ||
           !std::isfinite(c->lsqr_tol)) {
@@ -1102,6 +1133,51 @@ slim_status slim_set_x(slim_ctx* c, const void* x, size_t n, int dtype, int on_d
      "set_x");
   CK(cudaStreamSynchronize(c->stream), "set_x");
   return SLIM_OK;
+}
+
+slim_status slim_set_c_diag(slim_ctx* c, const void* cdiag, size_t n, int dtype, int on_device) {
+  if (!c || (cdiag && ((long long)n != c->n || (dtype != SLIM_F32 && dtype != SLIM_F64))))
+    return fail(c, SLIM_EINVAL, "set_c_diag: bad arguments");
+  if (c->kind != SLIM_BLOCKS_VIEWS || c->dim != 2 || c->solver == SLIM_SOLVE_LSQR)
+    return fail(c, SLIM_ENOTSUP, "set_c_diag: 2D view blocks, Woodbury form");
+  CK(c->lookahead ? la_sync_all(c) : cudaStreamSynchronize(c->stream), "set_c_diag");
+  if (!cdiag) {
+    if (c->d_cinv) CK(cudaFree(c->d_cinv), "set_c_diag");
+    c->d_cinv = nullptr;
+  } else {
+    // read the values to the host (as float64), check C is positive definite
+    std::vector<double> h((size_t)c->n);
+    if (dtype == SLIM_F64) {
+      CK(cudaMemcpy(h.data(), cdiag, h.size() * sizeof(double),
+                    on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost), "set_c_diag");
+    } else {
+      std::vector<float> f((size_t)c->n);
+      CK(cudaMemcpy(f.data(), cdiag, f.size() * sizeof(float),
+                    on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost), "set_c_diag");
+      for (size_t i = 0; i < f.size(); ++i) h[i] = f[i];
+    }
+    for (double& v : h) {
+      if (!(v > 0.0) || !std::isfinite(v))
+        return fail(c, SLIM_EINVAL, "set_c_diag: C_k must be positive definite (c > 0, finite)");
+      v = 1.0 / v;
+    }
+    if (!c->d_cinv) CK(cudaMalloc(&c->d_cinv, h.size() * sizeof(double)), "cudaMalloc");
+    CK(cudaMemcpy(c->d_cinv, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice),
+       "set_c_diag");
+  }
+  // the captured step and the retained Gram entries used the previous C_k
+  if (c->lookahead) {
+    la_drop_graphs(c);
+    CK(la_rebuild(c, c->h_k), "set_c_diag");
+    return read_status(c);
+  }
+  drop_graph(c);
+  if (c->h_k > 0) {
+    cudaError_t e = c->precision == SLIM_PREC_FP32 ? rebuild_t<float>(c, c->h_k)
+                                                   : rebuild_t<double>(c, c->h_k);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_c_diag");
+  }
+  return read_status(c);
 }
 
 slim_status slim_get_x(slim_ctx* c, void* x, size_t n, int dtype, int on_device) {

@@ -112,7 +112,8 @@ struct StepInfo {
   long long k;      // 1-based index of the step being taken
   int slot;         // ring slot of the new block
   int view;         // sampled view (view blocks)
-  double lam_k;     // damping lambda_k
+  double lam_k;     // shift of the Gram system: lambda_k, or mu_k = lambda_k + c_k beta (slimTik)
+  double tik_c;     // slimTik: beta / mu_k; 0 otherwise
 };
 
 }  // namespace slim

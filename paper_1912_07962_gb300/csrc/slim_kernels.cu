@@ -28,10 +28,18 @@ __global__ void sample_kernel(StepArgs<T> a) {
     int slot = (int)((k - 1) % a.nslots);
     double lam_k = a.lam;
     if (a.ramp && k <= a.r + 1) lam_k = __ddiv_rn(__dmul_rn(a.lam, (double)(a.r + 1)), (double)k);
+    double tik_c = 0.0;
+    if (a.tik_beta > 0.0) {
+      // Eq. (slimTik): mu_k = lambda_k + c_k lam_tik^2 / M
+      const long long cnt = a.tik_reading ? a.r : (k < a.r + 1 ? k : a.r + 1);
+      lam_k = __dadd_rn(lam_k, __dmul_rn((double)cnt, a.tik_beta));
+      tik_c = __ddiv_rn(a.tik_beta, lam_k);
+    }
     a.info->k = k;
     a.info->slot = slot;
     a.info->view = view;
     a.info->lam_k = lam_k;
+    a.info->tik_c = tik_c;
     *a.done = k;
     s_k = k;
     s_view = view;
@@ -468,6 +476,7 @@ __global__ void __launch_bounds__(kCta) gram_update_kernel(StepArgs<T> a) {
       int pix = rp[t];
       if (pix < 0) continue;
       double wq = rw[t];
+      if (a.cinv) wq *= a.cinv[pix];   // M C^{-1} M^T (slimTik, diagonal C)
       int ia = a.map_ray[pix];
       if (ia >= 0) atomicAdd(&acc[ia], wq * a.map_w[pix]);
       int ib = a.map_ray[n + pix];
@@ -503,12 +512,42 @@ __global__ void __launch_bounds__(kCta) scatter_kernel(StepArgs<T> a) {
   for (int t = lane; t < a.taps; t += 32) {
     int pix = rp[t];
     if (pix < 0) continue;
-    if (c != T(0)) atomicAdd(&a.x[pix], c * (T)rw[t]);
+    if (c != T(0)) atomicAdd(&a.x[pix], c * (T)(a.cinv ? rw[t] * a.cinv[pix] : rw[t]));
     if (is_new && a.map_ray) {
       a.map_ray[pix] = -1;
       a.map_ray[n + pix] = -1;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// slimTik (Eq. slimTik, C_k = diag(c)).  With W = C^{-1} and beta = lam_tik^2/M
+// the step is s = (beta/mu) x + W M^T z, (mu I + M W M^T) z = c - (beta/mu) M x,
+// c = [0; ...; r_k]: the right-hand side takes the window's projection of
+// x_{k-1}, and x_k = (1 - eta beta/mu) x_{k-1} - eta W M^T z.
+// One warp per ring row.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kCta) tik_rhs_kernel(StepArgs<T> a) {
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (q >= a.p || a.ring_ids[q] < 0) return;
+  const int* rp = a.ring_pix + (size_t)q * a.taps;
+  const double* rw = a.ring_w + (size_t)q * a.taps;
+  double acc = 0.0;
+  for (int t = lane; t < a.taps; t += 32) {
+    const int pix = rp[t];
+    if (pix >= 0) acc += rw[t] * (double)a.x[pix];
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) a.rhs[q] -= a.info->tik_c * acc;
+}
+
+template <typename T>
+__global__ void tik_scale_kernel(StepArgs<T> a) {
+  const T f = (T)(1.0 - a.eta * a.info->tik_c);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n;
+       i += (long long)gridDim.x * blockDim.x)
+    a.x[i] *= f;
 }
 
 template <typename TF>
@@ -785,6 +824,19 @@ cudaError_t launch_scatter(const StepArgs<T>& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_tik_rhs(const StepArgs<T>& a, cudaStream_t s) {
+  tik_rhs_kernel<T><<<cdiv(a.p, kWarpsPerCta), kCta, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tik_scale(const StepArgs<T>& a, cudaStream_t s) {
+  const int grid = (int)std::min<long long>((a.n + 255) / 256, 152LL * 8);
+  tik_scale_kernel<T><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename TF>
 cudaError_t launch_form_k(const StepInfo* info, const double* G, TF* L, int P, cudaStream_t s) {
   long long total = (long long)P * P;
@@ -837,6 +889,8 @@ cudaError_t launch_rel_err(const T* x, const double* ref, long long n, double* o
   template cudaError_t launch_forward_residual<T>(const StepArgs<T>&, cudaStream_t);          \
   template cudaError_t launch_gram_update<T>(const StepArgs<T>&, cudaStream_t);               \
   template cudaError_t launch_scatter<T>(const StepArgs<T>&, cudaStream_t);                   \
+  template cudaError_t launch_tik_rhs<T>(const StepArgs<T>&, cudaStream_t);                   \
+  template cudaError_t launch_tik_scale<T>(const StepArgs<T>&, cudaStream_t);                 \
   template cudaError_t launch_form_k<T>(const StepInfo*, const double*, T*, int, cudaStream_t); \
   template cudaError_t launch_project<T>(const ViewGeom*, int, int, const int*, int, const T*, \
                                          T*, cudaStream_t);                                    \

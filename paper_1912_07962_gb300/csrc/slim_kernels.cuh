@@ -36,6 +36,12 @@ struct StepArgs {
   const int* csr_col;      // [nnz]
   const void* csr_val;     // [nnz]
   int csr_bf16;
+  // slimTik, Eq. (slimTik) with C_k = diag(c): beta = lam_tik^2 / M (0: slimLS),
+  // the count c_k of Tikhonov rows (0: blocks of M_k, 1: r as printed), 1/c
+  // per pixel (null: C_k = I)
+  double tik_beta;
+  int tik_reading;
+  const double* cinv;
 };
 
 // Sliced ELLPACK with slices of 32 lines (SELL-32): line l of slice s has its
@@ -84,6 +90,11 @@ template <typename T> cudaError_t launch_sample(const StepArgs<T>& a, cudaStream
 template <typename T> cudaError_t launch_forward_residual(const StepArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_gram_update(const StepArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_scatter(const StepArgs<T>& a, cudaStream_t s);
+
+// slimTik: rhs -= (beta/mu_k) M_k x over the window's rows, and
+// x *= 1 - eta beta/mu_k (before the scatter adds -eta C^{-1} M_k^T z).
+template <typename T> cudaError_t launch_tik_rhs(const StepArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_tik_scale(const StepArgs<T>& a, cudaStream_t s);
 
 // L = lambda_k I + G on the lower triangle, converted to TF (the factor precision).
 template <typename TF> cudaError_t launch_form_k(const StepInfo* info, const double* G, TF* L,

@@ -31,11 +31,19 @@ __global__ void la_sample_kernel(LaArgs<T> a) {
                                     (uint32_t)a.n_views);
     double lam_j = a.lam;
     if (a.ramp && j <= a.r + 1) lam_j = __ddiv_rn(__dmul_rn(a.lam, (double)(a.r + 1)), (double)j);
+    double tik_c = 0.0;
+    if (a.tik_beta > 0.0) {
+      // Eq. (slimTik): mu_j = lambda_j + c_j lam_tik^2 / M
+      const long long cnt = a.tik_reading ? a.r : (j < a.r + 1 ? j : a.r + 1);
+      lam_j = __dadd_rn(lam_j, __dmul_rn((double)cnt, a.tik_beta));
+      tik_c = __ddiv_rn(a.tik_beta, lam_j);
+    }
     StepInfo* inf = a.info_buf + (int)(j % a.nbuf);
     inf->k = j;
     inf->slot = (int)((j - 1) % a.nslots);
     inf->view = view;
     inf->lam_k = lam_j;
+    inf->tik_c = tik_c;
     *a.gdone = j;
     s_view = view;
     s_e = eslot_of(j, a.eslots);
@@ -105,7 +113,7 @@ __global__ void __launch_bounds__(kCta) la_gram_kernel(LaArgs<T> a) {
     for (int t = lane; t < a.taps; t += 32) {
       const int pix = rp[t];
       if (pix < 0) continue;
-      const double wv = rw[t];
+      const double wv = a.cinv ? rw[t] * a.cinv[pix] : rw[t];   // M C^{-1} M^T
       const int ia = a.map_ray[pix];
       if (ia >= 0) atomicAdd(&acc[ia], wv * a.map_w[pix]);
       const int ib = a.map_ray[n + pix];
@@ -235,8 +243,37 @@ __global__ void __launch_bounds__(kCta) la_scatter_kernel(LaArgs<T> a, const int
   const double* rw = a.ring_w + (size_t)qe * a.taps;
   for (int t = lane; t < a.taps; t += 32) {
     const int pix = rp[t];
-    if (pix >= 0) atomicAdd(&a.x[pix], c * (T)rw[t]);
+    if (pix >= 0) atomicAdd(&a.x[pix], c * (T)(a.cinv ? rw[t] * a.cinv[pix] : rw[t]));
   }
+}
+
+// slimTik (Eq. slimTik, C_k = diag(c)): rhs c - (beta/mu_k) M_k x_{k-1} over
+// the factored rows (one warp per row), then x *= 1 - eta beta/mu_k before
+// the scatter adds -eta C^{-1} M_k^T z.
+template <typename T>
+__global__ void __launch_bounds__(kCta) la_tik_rhs_kernel(LaArgs<T> a, const int* ext,
+                                                          const StepInfo* info) {
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (q >= a.p) return;
+  const int qe = ext[q];
+  if (qe < 0) return;
+  const int* rp = a.ring_pix + (size_t)qe * a.taps;
+  const double* rw = a.ring_w + (size_t)qe * a.taps;
+  double acc = 0.0;
+  for (int t = lane; t < a.taps; t += 32) {
+    const int pix = rp[t];
+    if (pix >= 0) acc += rw[t] * (double)a.x[pix];
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) a.rhs[q] -= info->tik_c * acc;
+}
+
+template <typename T>
+__global__ void la_tik_scale_kernel(LaArgs<T> a, const StepInfo* info) {
+  const T f = (T)(1.0 - a.eta * info->tik_c);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n;
+       i += (long long)gridDim.x * blockDim.x)
+    a.x[i] *= f;
 }
 
 }  // namespace
@@ -305,13 +342,30 @@ cudaError_t la_launch_scatter(const LaArgs<T>& a, const int* ext, cudaStream_t s
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t la_launch_tik_rhs(const LaArgs<T>& a, const int* ext, const StepInfo* info,
+                              cudaStream_t s) {
+  la_tik_rhs_kernel<T><<<cdiv(a.p, kWarps), kCta, 0, s>>>(a, ext, info);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t la_launch_tik_scale(const LaArgs<T>& a, const StepInfo* info, cudaStream_t s) {
+  const int grid = (int)std::min<long long>((a.n + 255) / 256, 152LL * 8);
+  la_tik_scale_kernel<T><<<grid, 256, 0, s>>>(a, info);
+  return cudaGetLastError();
+}
+
 #define SLIM_LA_INST(T)                                                                      \
   template cudaError_t la_launch_sample<T>(const LaArgs<T>&, cudaStream_t);                  \
   template cudaError_t la_launch_taps<T>(const LaArgs<T>&, cudaStream_t);                    \
   template cudaError_t la_launch_gram<T>(const LaArgs<T>&, cudaStream_t);                    \
   template cudaError_t la_launch_map_clear<T>(const LaArgs<T>&, cudaStream_t);               \
   template cudaError_t la_launch_residual<T>(const LaArgs<T>&, const StepInfo*, cudaStream_t); \
-  template cudaError_t la_launch_scatter<T>(const LaArgs<T>&, const int*, cudaStream_t);
+  template cudaError_t la_launch_scatter<T>(const LaArgs<T>&, const int*, cudaStream_t);      \
+  template cudaError_t la_launch_tik_rhs<T>(const LaArgs<T>&, const int*, const StepInfo*,     \
+                                            cudaStream_t);                                     \
+  template cudaError_t la_launch_tik_scale<T>(const LaArgs<T>&, const StepInfo*, cudaStream_t);
 SLIM_LA_INST(float)
 SLIM_LA_INST(double)
 template cudaError_t la_launch_form<float>(const StepInfo*, const int*, const double*, int, float*,

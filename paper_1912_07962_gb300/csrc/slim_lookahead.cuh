@@ -46,6 +46,9 @@ struct LaArgs {
   T* x;
   const T* b;
   int* status;
+  double tik_beta;               // slimTik: lam_tik^2 / M (0: slimLS)
+  int tik_reading;               // Tikhonov count: 0 blocks of M_k, 1 r
+  const double* cinv;            // [n] 1/c of C_k = diag(c); null: C_k = I
 };
 
 // Geometry chain (stream of its own, one step at a time).
@@ -69,5 +72,11 @@ cudaError_t la_launch_refine(const StepInfo* info, const int* ext, const double*
                              cudaStream_t s);
 template <typename T> cudaError_t la_launch_scatter(const LaArgs<T>& a, const int* ext,
                                                     cudaStream_t s);
+// slimTik: rhs -= (beta/mu_k) M_k x over the factored rows, and
+// x *= 1 - eta beta/mu_k before the scatter.
+template <typename T> cudaError_t la_launch_tik_rhs(const LaArgs<T>& a, const int* ext,
+                                                    const StepInfo* info, cudaStream_t s);
+template <typename T> cudaError_t la_launch_tik_scale(const LaArgs<T>& a, const StepInfo* info,
+                                                      cudaStream_t s);
 
 }  // namespace slim

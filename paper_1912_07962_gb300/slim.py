@@ -36,7 +36,7 @@ EXPORTS = [
     "slim_unet_param_count", "slim_unet_create", "slim_unet_destroy", "slim_unet_set_params",
     "slim_unet_get_params", "slim_unet_get_grads", "slim_unet_forward", "slim_unet_train_step",
     "slim_warm_start", "slim_backproject_data", "slim_unet_conv3x3", "slim_unet_conv3x3_grad",
-    "slim_unet_tconv2x2", "slim_unet_tconv2x2_grad", "slim_get_lsqr_info",
+    "slim_unet_tconv2x2", "slim_unet_tconv2x2_grad", "slim_get_lsqr_info", "slim_set_c_diag",
 ]
 A_MATRIX_FREE, A_CSR_F32, A_CSR_BF16 = 0, 1, 2
 NOALLOC_MAX_P = 1024
@@ -58,7 +58,7 @@ class slim_step_opts(C.Structure):
     _fields_ = [("eta", C.c_double), ("ramp", C.c_int), ("solver", C.c_int),
                 ("refine_iters", C.c_int), ("use_graph", C.c_int), ("tile", C.c_int),
                 ("ctas_per_sm", C.c_int), ("lookahead", C.c_int), ("lsqr_max_iter", C.c_int),
-                ("lsqr_tol", C.c_double)]
+                ("lsqr_tol", C.c_double), ("tik_lambda", C.c_double), ("tik_reading", C.c_int)]
 
 
 class SlimError(RuntimeError):
@@ -130,6 +130,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "slim_unet_tconv2x2": ([VP, I, I, I, I, VP, VP, I, VP, VP], I),
         "slim_unet_tconv2x2_grad": ([VP, VP, I, I, I, I, VP, I, VP, VP, VP, VP], I),
         "slim_get_lsqr_info": ([VP, P(I), P(D), P(D)], I),
+        "slim_set_c_diag": ([VP, VP, C.c_size_t, I, I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -163,7 +164,7 @@ class Slim:
                  solver=SLIM_SOLVE_FP64, refine_iters=2, eta=1.0, ramp=False, use_graph=False,
                  angles=None, a_mode=A_MATRIX_FREE, dim=2, det_v=1, kind=SLIM_BLOCKS_VIEWS,
                  steps_per_view=1, tile=0, ctas_per_sm=0, lookahead=0, lsqr_max_iter=0,
-                 lsqr_tol=0.0, _handle=None):
+                 lsqr_tol=0.0, tik_lambda=0.0, tik_reading=0, _handle=None):
         lib = load()
         self._lib = lib
         self._angles = None
@@ -182,7 +183,7 @@ class Slim:
             g.angles = self._angles.ctypes.data_as(C.POINTER(C.c_double))
         blk = slim_blocks(kind, ell, seed, steps_per_view)
         opts = slim_step_opts(eta, int(ramp), solver, refine_iters, int(use_graph), tile, ctas_per_sm,
-                              lookahead, lsqr_max_iter, lsqr_tol)
+                              lookahead, lsqr_max_iter, lsqr_tol, tik_lambda, tik_reading)
         h = C.c_void_p()
         st = lib.slim_create(C.byref(g), C.byref(blk), r, lam, C.byref(opts), C.byref(h))
         if st != SLIM_OK:
@@ -203,6 +204,15 @@ class Slim:
         it, res, res0 = C.c_int(), C.c_double(), C.c_double()
         self._check(self._lib.slim_get_lsqr_info(self.h, C.byref(it), C.byref(res), C.byref(res0)))
         return it.value, res.value, res0.value
+
+    def set_c_diag(self, c):
+        """C_k = diag(c) of Eq. (B_k) (c > 0; slimTik: L^T L with L = diag(sqrt c)).
+        None restores C_k = I.  The memory of the steps taken is rebuilt."""
+        if c is None:
+            self._check(self._lib.slim_set_c_diag(self.h, None, 0, SLIM_F64, 0))
+            return
+        p, dev, code, cnt = _ptr(c)
+        self._check(self._lib.slim_set_c_diag(self.h, p, cnt, code, dev))
 
     def close(self):
         if getattr(self, "h", None) and getattr(self, "_owned", True):
