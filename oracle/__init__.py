@@ -18,6 +18,7 @@ Modules
   theory   Sec. 3 quantities for r = 0: B_k(alpha), B, x_hat (Eq. xhat), bounds
   lsqr     LSQR for the damped least-squares step of Eq. (slimLSstep)
   tik      one slimTik step, Eq. (slimTik) (C_k = L^T L), direct and Woodbury form
+  comparators  sg (B_k = alpha_k I), olbfgs (two-loop L-BFGS), decaying damping
 
 Parity status: every function is pinned by tests in `tests/test_oracle_*.py`
 against closed forms, special cases and the paper's theorems, except the
