@@ -60,7 +60,8 @@ typedef enum {
 
 enum { SLIM_F32 = 0, SLIM_F64 = 1 };
 enum { SLIM_PREC_FP64 = 0, SLIM_PREC_FP32 = 1 };
-enum { SLIM_SOLVE_FP64 = 0, SLIM_SOLVE_MIXED = 1, SLIM_SOLVE_LSQR = 2 };
+enum { SLIM_SOLVE_FP64 = 0, SLIM_SOLVE_MIXED = 1, SLIM_SOLVE_LSQR = 2, SLIM_SOLVE_SG = 3,
+       SLIM_SOLVE_OLBFGS = 4 };
 enum { SLIM_BLOCKS_VIEWS = 0, SLIM_BLOCKS_RAYS = 1, SLIM_BLOCKS_STREAM = 2 };
 
 /* Parallel-beam geometry (Sec. 4.3; Joseph rows defined in the library docs).
@@ -125,6 +126,19 @@ typedef struct {
  *                 matrix-free over the window's stored taps, float64 vectors;
  *                 2D view blocks, rows from the projector, lookahead 0 only
  *                 (SLIM_ENOTSUP otherwise), never captured in a graph
+ *                 SLIM_SOLVE_SG: the comparator sg of Sec. 2, B_k = alpha_k I in
+ *                 Eq. (ram): x_k = x_{k-1} - eta alpha_k A_k^T r_k with the step
+ *                 size alpha_k = 1/lambda_k (lambda_k from the damping schedule)
+ *                 SLIM_SOLVE_OLBFGS: the comparator olbfgs of Sec. 4.1 (online
+ *                 L-BFGS, memory olbfgs_memory): x_k = x_{k-1} - eta alpha_k H_k g_k,
+ *                 g_k = A_k^T r_k, H_k the L-BFGS inverse of the last pairs
+ *                 (s_j = x_j - x_{j-1}, y_j = A_j^T A_j s_j) from H^0 = gamma_k I,
+ *                 gamma_k the mean of s^T y / y^T y over the stored pairs (I
+ *                 before the first); a pair with s^T y <= 0 is not stored.
+ *                 SG and OLBFGS keep no slimLS memory: r must be 0
+ *                 (SLIM_EINVAL); 2D view blocks, lookahead 0, tik_lambda 0
+ *                 (SLIM_ENOTSUP otherwise); OLBFGS is one cooperative launch
+ *                 per step, never captured in a graph
  *   refine_iters  refinement rounds for SLIM_SOLVE_MIXED (0..16)
  *   use_graph     1: capture one step as a CUDA graph at the first slim_step and
  *                 replay it (one graph launch per step)
@@ -158,6 +172,10 @@ typedef struct {
  *                 MIXED solver; SLIM_ENOTSUP otherwise), with or without
  *                 lookahead (mu_k I + M_k C^{-1} M_k^T depends only on the
  *                 blocks drawn)
+ *   decay_after   0: lambda_k as above.  K > 0: the decaying damping of Sec. 3
+ *                 (after a constant one): lambda_k = lambda k / K for k > K
+ *                 (alpha_k = alpha K / k), every solver
+ *   olbfgs_memory SLIM_SOLVE_OLBFGS: pairs kept (1..20, 0 = 10)
  *   tik_reading   c_k, the Tikhonov rows that the stacked M_k holds: 0 = the
  *                 blocks of M_k, min(k, r+1) (slimLS on the stacked problem,
  *                 whose full-memory iterates reach the Tikhonov solution);
@@ -175,6 +193,8 @@ typedef struct {
   double lsqr_tol;
   double tik_lambda;
   int tik_reading;
+  int decay_after;
+  int olbfgs_memory;
 } slim_step_opts;
 
 /* SLIM_SOLVE_LSQR: the last step's LSQR iterations, its final estimate of
@@ -255,10 +275,14 @@ slim_status slim_get_iter(const slim_ctx* ctx, long long* k);
 
 /* Jump to the state after k steps: the memory is rebuilt from the sampled
  * blocks tau_{max(1,k-r)}..tau_k and the current x is kept.  Used by
- * slim_restore and to align the device with an externally computed iterate. */
+ * slim_restore and to align the device with an externally computed iterate.
+ * SLIM_SOLVE_OLBFGS: k = 0 only (the stored pairs are dropped; SLIM_ENOTSUP
+ * otherwise, since the pairs depend on the iterates). */
 slim_status slim_set_iter(slim_ctx* ctx, long long k);
 
-/* Checkpoint: k and x.  With buf == NULL, *len receives the size needed. */
+/* Checkpoint: k and x.  With buf == NULL, *len receives the size needed.
+ * SLIM_ENOTSUP for SLIM_SOLVE_OLBFGS (its pairs are not part of it), for
+ * both calls. */
 slim_status slim_checkpoint(slim_ctx* ctx, void* buf, size_t* len);
 slim_status slim_restore(slim_ctx* ctx, const void* buf, size_t len);
 

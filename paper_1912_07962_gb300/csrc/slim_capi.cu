@@ -11,6 +11,7 @@
 #include "slim_kernels.cuh"
 #include "slim_lookahead.cuh"
 #include "slim_lsqr.cuh"
+#include "slim_olbfgs.cuh"
 #include "slim_unet.cuh"
 #include "slim_rays.cuh"
 
@@ -30,6 +31,7 @@ struct slim_ctx {
   int* d_slice_cnt = nullptr;
   int* d_slice_rows = nullptr;
   int ramp = 0, r = 0, nslots = 1, ell = 0, p = 0, P = 0, taps = 0, nb = 32;
+  int decay_after = 0;             // 1/k decay of the damping after this step (0: none)
   int tile = 0, ctas_per_sm = 2;
   double lam = 0.0, eta = 1.0;
   unsigned long long seed = 0;
@@ -56,6 +58,9 @@ struct slim_ctx {
   double tik_lambda = 0.0;         // slimTik: lam_tik of Eq. (TLS1) (0: slimLS)
   int tik_reading = 0;             // count of Tikhonov rows: 0 blocks of M_k, 1 r
   double* d_cinv = nullptr;        // [n] 1/c of C_k = diag(c); null: C_k = I
+  int olbfgs_memory = 0;           // pairs of the olbfgs comparator
+  double* d_olb = nullptr;         // its scratch: g, S, Y, u, S^T Y, Y^T Y, partial sums
+  int* d_olb_state = nullptr;      // its pair bookkeeping
   double* d_lsqr = nullptr;        // LSQR scratch: u [p], v, w, s, tmp [n], partial sums, stats [3]
   unsigned* d_lsqr_bar = nullptr;  // its grid barrier
   double* d_res = nullptr;
@@ -200,6 +205,7 @@ StepArgs<T> make_args(slim_ctx* c) {
   a.lam = c->lam;
   a.eta = c->eta;
   a.ramp = c->ramp;
+  a.decay_after = c->decay_after;
   a.ring_ids = c->d_ring_ids;
   a.ring_pix = c->d_ring_pix;
   a.ring_w = c->d_ring_w;
@@ -218,6 +224,7 @@ StepArgs<T> make_args(slim_ctx* c) {
   a.tik_beta = c->tik_lambda * c->tik_lambda / c->n_views;   // M = A_v view blocks
   a.tik_reading = c->tik_reading;
   a.cinv = c->d_cinv;
+  a.sg = c->solver == SLIM_SOLVE_SG;
   return a;
 }
 
@@ -243,6 +250,7 @@ RayArgs make_ray_args(slim_ctx* c) {
   a.seed = c->seed;
   a.lam = c->lam;
   a.ramp = c->ramp;
+  a.decay_after = c->decay_after;
   a.ring_ids = c->d_ring_ids;
   a.ring_pix = c->d_ring_pix;
   a.ring_w = c->d_ring_w;
@@ -275,6 +283,8 @@ cudaError_t mark(slim_ctx* c, int i) {
 int kernels_per_step(const slim_ctx* c) {
   if (c->dim == 3) return 6;   // sample, march, collect, slice Gram, slice solve, scatter
   if (c->solver == SLIM_SOLVE_LSQR) return 3;   // sample, forward + residual, LSQR (with x update)
+  if (c->solver == SLIM_SOLVE_SG) return 3;     // sample, forward + residual, scatter
+  if (c->solver == SLIM_SOLVE_OLBFGS) return 3; // sample, forward + residual, the olbfgs step
   const int solves = c->solver == SLIM_SOLVE_MIXED ? 1 + c->refine_iters : 1;
   const int refine = c->solver == SLIM_SOLVE_MIXED ? 2 * c->refine_iters : 0;
   if (c->lookahead) {
@@ -398,6 +408,37 @@ cudaError_t enqueue_step_t(slim_ctx* c) {
     if ((e = mark(c, kPhSolve)) != cudaSuccess) return e;
     return mark(c, kPhScatter);
   }
+  if (c->solver == SLIM_SOLVE_SG || c->solver == SLIM_SOLVE_OLBFGS) {
+    // the comparators: no Gram matrix, no factor
+    if ((e = mark(c, 0)) != cudaSuccess) return e;
+    if ((e = launch_sample<T>(a, c->stream)) != cudaSuccess) return e;
+    if ((e = mark(c, kPhSample)) != cudaSuccess) return e;
+    if ((e = launch_forward_residual<T>(a, c->stream)) != cudaSuccess) return e;
+    for (int ph = kPhForward; ph <= kPhSolve; ++ph)
+      if ((e = mark(c, ph)) != cudaSuccess) return e;
+    if (c->solver == SLIM_SOLVE_SG) {
+      if ((e = launch_scatter<T>(a, c->stream)) != cudaSuccess) return e;
+    } else {
+      OlbfgsArgs<T> o;
+      o.info = c->d_info;
+      o.ell = c->ell;
+      o.taps = c->taps;
+      o.tau = c->olbfgs_memory;
+      o.n = c->n;
+      o.ring_pix = c->d_ring_pix;
+      o.ring_w = c->d_ring_w;
+      o.rhs = c->d_rhs;
+      o.map_ray = c->d_map_ray;
+      o.eta = c->eta;
+      o.x = (T*)c->d_x;
+      o.state = c->d_olb_state;
+      o.bar = c->d_lsqr_bar;
+      o.status = c->d_status;
+      olbfgs_bind(&o, c->d_olb, c->num_sms);
+      if ((e = launch_olbfgs<T>(o, c->num_sms, c->stream)) != cudaSuccess) return e;
+    }
+    return mark(c, kPhScatter);
+  }
   if ((e = mark(c, 0)) != cudaSuccess) return e;
   if ((e = launch_sample<T>(a, c->stream)) != cudaSuccess) return e;
   if ((e = mark(c, kPhSample)) != cudaSuccess) return e;
@@ -451,7 +492,7 @@ cudaError_t rebuild_t(slim_ctx* c, long long k) {
     }
     if ((e = launch_sample<T>(a, s)) != cudaSuccess) return e;
     if ((e = launch_forward_residual<T>(a, s)) != cudaSuccess) return e;
-    if (c->solver != SLIM_SOLVE_LSQR && (e = launch_gram_update<T>(a, s)) != cudaSuccess) return e;
+    if (c->d_G && (e = launch_gram_update<T>(a, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int), s)) !=
         cudaSuccess)
       return e;
@@ -488,7 +529,7 @@ void free_all(slim_ctx* c) {
   void* ptrs[] = {c->d_slice_cnt, c->d_slice_rows, c->d_views, c->d_info, c->d_done, c->d_status, c->d_x, c->d_b,
                   c->d_ring_ids, c->d_ring_pix, c->d_ring_w, c->d_map_ray, c->d_map_w,
                   c->d_G, c->d_L, c->d_rhs, c->d_z, c->d_dz, c->d_res, c->d_ref, c->d_err,
-                  c->d_lsqr, c->d_lsqr_bar, c->d_cinv};
+                  c->d_lsqr, c->d_lsqr_bar, c->d_cinv, c->d_olb, c->d_olb_state};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   chol_plan_destroy(&c->plan);
@@ -560,6 +601,7 @@ LaArgs<T> make_la_args(slim_ctx* c) {
   a.lam = c->lam;
   a.eta = c->eta;
   a.ramp = c->ramp;
+  a.decay_after = c->decay_after;
   a.gdone = c->d_gdone;
   a.info_buf = c->d_info_buf;
   a.nbuf = c->nbuf;
@@ -832,13 +874,33 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     c->lsqr_tol = step->lsqr_tol;
     c->tik_lambda = step->tik_lambda;
     c->tik_reading = step->tik_reading;
+    c->decay_after = step->decay_after;
+    c->olbfgs_memory = step->olbfgs_memory ? step->olbfgs_memory : 10;
+    if (c->decay_after < 0 ||
+        (c->solver == SLIM_SOLVE_OLBFGS &&
+         (c->olbfgs_memory < 1 || c->olbfgs_memory > kOlbfgsMaxMem))) {
+      delete c;
+      return SLIM_EINVAL;
+    }
+    if (c->solver == SLIM_SOLVE_SG || c->solver == SLIM_SOLVE_OLBFGS) {
+      if (c->r != 0) {   // the comparators keep no slimLS memory
+        delete c;
+        return SLIM_EINVAL;
+      }
+      if (c->kind != SLIM_BLOCKS_VIEWS || c->dim != 2 || c->lookahead != 0 ||
+          c->tik_lambda != 0.0) {
+        delete c;
+        return SLIM_ENOTSUP;
+      }
+      if (c->solver == SLIM_SOLVE_OLBFGS) c->use_graph = 0;   // a cooperative launch per step
+    }
     if (!(c->tik_lambda >= 0.0) || !std::isfinite(c->tik_lambda) ||
         (c->tik_reading != 0 && c->tik_reading != 1)) {
       delete c;
       return SLIM_EINVAL;
     }
     if (c->tik_lambda > 0.0 && (c->kind != SLIM_BLOCKS_VIEWS || c->dim != 2 ||
-                                c->solver == SLIM_SOLVE_LSQR)) {
+                                (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED))) {
       delete c;
       return SLIM_ENOTSUP;
     }
@@ -856,7 +918,8 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     }
     if (!(c->eta > 0.0) ||
         (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED &&
-         c->solver != SLIM_SOLVE_LSQR) ||
+         c->solver != SLIM_SOLVE_LSQR && c->solver != SLIM_SOLVE_SG &&
+         c->solver != SLIM_SOLVE_OLBFGS) ||
         c->refine_iters < 0 || c->refine_iters > 16 || (c->tile != 0 && c->tile != 32 && c->tile != 64) ||
         c->ctas_per_sm < 1 || c->ctas_per_sm > 4 || c->lookahead < 0 ||
         c->lookahead > kMaxBuf - 1) {
@@ -926,7 +989,9 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     chk(cudaEventCreateWithFlags(&c->ev_g1, cudaEventDisableTiming), "event");
   }
   const int ring_rows = la ? c->Pe : c->p;
-  const bool lsqr = c->solver == SLIM_SOLVE_LSQR;   // no Gram matrix, no factor
+  // LSQR and the comparators: no Gram matrix, no factor
+  const bool lsqr = c->solver == SLIM_SOLVE_LSQR || c->solver == SLIM_SOLVE_SG ||
+                    c->solver == SLIM_SOLVE_OLBFGS;
   const size_t g_elems = lsqr ? 0 : la ? (size_t)c->Pe * c->Pe : (size_t)c->P * c->P;
   const size_t es = elem(c->precision);
   const size_t fs = c->solver == SLIM_SOLVE_FP64 ? sizeof(double) : sizeof(float);
@@ -984,6 +1049,16 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
         chk(chol_plan_create(&c->planb[b], c->P, c->nb, c->solver == SLIM_SOLVE_MIXED ? 1 : 0,
                              fgrid, 1), "chol plan");
       }
+    } else if (c->solver == SLIM_SOLVE_SG) {
+      // the scatter alone
+    } else if (c->solver == SLIM_SOLVE_OLBFGS) {
+      const size_t cnt = olbfgs_scratch_count(c->n, c->ell, c->olbfgs_memory, c->num_sms);
+      chk(cudaMalloc(&c->d_olb, cnt * sizeof(double)), "cudaMalloc");
+      chk(cudaMalloc(&c->d_olb_state, (2 + kOlbfgsMaxMem) * sizeof(int)), "cudaMalloc");
+      chk(cudaMalloc(&c->d_lsqr_bar, 2 * sizeof(unsigned)), "cudaMalloc");
+      // g, the spare y and the bookkeeping (no pairs) start at zero
+      chk(cudaMemset(c->d_olb, 0, cnt * sizeof(double)), "memset");
+      chk(cudaMemset(c->d_olb_state, 0, (2 + kOlbfgsMaxMem) * sizeof(int)), "memset");
     } else if (c->solver == SLIM_SOLVE_LSQR) {
       const size_t cnt = (size_t)c->p + 4 * (size_t)c->n + lsqr_part_count(c->num_sms) + 3;
       chk(cudaMalloc(&c->d_lsqr, cnt * sizeof(double)), "cudaMalloc");
@@ -1138,7 +1213,8 @@ slim_status slim_set_x(slim_ctx* c, const void* x, size_t n, int dtype, int on_d
 slim_status slim_set_c_diag(slim_ctx* c, const void* cdiag, size_t n, int dtype, int on_device) {
   if (!c || (cdiag && ((long long)n != c->n || (dtype != SLIM_F32 && dtype != SLIM_F64))))
     return fail(c, SLIM_EINVAL, "set_c_diag: bad arguments");
-  if (c->kind != SLIM_BLOCKS_VIEWS || c->dim != 2 || c->solver == SLIM_SOLVE_LSQR)
+  if (c->kind != SLIM_BLOCKS_VIEWS || c->dim != 2 ||
+      (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED))
     return fail(c, SLIM_ENOTSUP, "set_c_diag: 2D view blocks, Woodbury form");
   CK(c->lookahead ? la_sync_all(c) : cudaStreamSynchronize(c->stream), "set_c_diag");
   if (!cdiag) {
@@ -1296,6 +1372,12 @@ slim_status slim_get_iter(const slim_ctx* c, long long* k) {
 
 slim_status slim_set_iter(slim_ctx* c, long long k) {
   if (!c || k < 0) return fail(c, SLIM_EINVAL, "set_iter: bad arguments");
+  if (c->solver == SLIM_SOLVE_OLBFGS) {
+    // the pairs depend on the iterates: only a restart from step 0 (no pairs)
+    if (k != 0) return fail(c, SLIM_ENOTSUP, "set_iter: olbfgs restarts at 0 only");
+    CK(cudaStreamSynchronize(c->stream), "set_iter");
+    CK(cudaMemset(c->d_olb_state, 0, (2 + kOlbfgsMaxMem) * sizeof(int)), "set_iter");
+  }
   cudaError_t e = c->lookahead ? la_rebuild(c, k)
                  : c->precision == SLIM_PREC_FP32 ? rebuild_t<float>(c, k) : rebuild_t<double>(c, k);
   if (e != cudaSuccess) return cuda_fail(c, e, "set_iter");
@@ -1313,6 +1395,8 @@ struct CkptHeader {
 
 slim_status slim_checkpoint(slim_ctx* c, void* buf, size_t* len) {
   if (!c || !len) return SLIM_EINVAL;
+  if (c->solver == SLIM_SOLVE_OLBFGS)
+    return fail(c, SLIM_ENOTSUP, "checkpoint: the olbfgs pairs are not checkpointed");
   size_t need = sizeof(CkptHeader) + (size_t)c->n * elem(c->precision);
   if (!buf) {
     *len = need;
@@ -1335,6 +1419,8 @@ slim_status slim_checkpoint(slim_ctx* c, void* buf, size_t* len) {
 
 slim_status slim_restore(slim_ctx* c, const void* buf, size_t len) {
   if (!c || !buf || len < sizeof(CkptHeader)) return fail(c, SLIM_EINVAL, "restore: bad buffer");
+  if (c->solver == SLIM_SOLVE_OLBFGS)
+    return fail(c, SLIM_ENOTSUP, "restore: the olbfgs pairs are not checkpointed");
   CkptHeader h;
   memcpy(&h, buf, sizeof(h));
   if (memcmp(h.magic, "SLIMCKP1", 8) != 0 || h.version != 1 || h.n != c->n ||
@@ -1361,7 +1447,7 @@ slim_status slim_get_lsqr_info(slim_ctx* c, int* iters, double* normal_res, doub
 
 slim_status slim_get_memory(slim_ctx* c, int* ids, double* G, double* z) {
   if (!c) return SLIM_EINVAL;
-  if (c->solver == SLIM_SOLVE_LSQR && (G || z))
+  if (!c->d_G && (G || z))
     return fail(c, SLIM_ENOTSUP, "get_memory: LSQR keeps no Gram matrix and no z");
   CK(cudaStreamSynchronize(c->stream), "get_memory");
   if (c->lookahead) {
@@ -1875,7 +1961,7 @@ extern "C" slim_status slim_batch_create(int count, const slim_geometry* geoms,
       slim_batch_destroy(b);
       return st;
     }
-    if (c->lookahead || c->solver == SLIM_SOLVE_LSQR) {   // a batch captures one plain chain per problem
+    if (c->lookahead || c->solver >= SLIM_SOLVE_LSQR) {   // a batch captures one plain chain per problem
       slim_destroy(c);
       slim_batch_destroy(b);
       return SLIM_ENOTSUP;

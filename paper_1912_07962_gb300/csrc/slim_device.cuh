@@ -108,6 +108,17 @@ __device__ __forceinline__ double rsqrt_pivot(double d, int* status) {
 }
 
 // Per-step values computed on the device by the sampler.
+// lambda_k: the damping ramp of Sec. 4.2 (lambda (r+1)/k for k <= r+1), the
+// 1/k decay after step decay_after (lambda k / decay_after; 0: none), else
+// lambda.  Each operation rounded once.
+__device__ __forceinline__ double damping_k(double lam, long long k, int r, int ramp,
+                                            int decay_after) {
+  if (ramp && k <= r + 1) return __ddiv_rn(__dmul_rn(lam, (double)(r + 1)), (double)k);
+  if (decay_after > 0 && k > decay_after)
+    return __ddiv_rn(__dmul_rn(lam, (double)k), (double)decay_after);
+  return lam;
+}
+
 struct StepInfo {
   long long k;      // 1-based index of the step being taken
   int slot;         // ring slot of the new block

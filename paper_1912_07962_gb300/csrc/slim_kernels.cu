@@ -26,8 +26,7 @@ __global__ void sample_kernel(StepArgs<T> a) {
     int view = (int)bounded32(draw64(a.seed, kStreamBlocks, (unsigned long long)(k - 1)),
                               (uint32_t)a.n_views);
     int slot = (int)((k - 1) % a.nslots);
-    double lam_k = a.lam;
-    if (a.ramp && k <= a.r + 1) lam_k = __ddiv_rn(__dmul_rn(a.lam, (double)(a.r + 1)), (double)k);
+    double lam_k = damping_k(a.lam, k, a.r, a.ramp, a.decay_after);
     double tik_c = 0.0;
     if (a.tik_beta > 0.0) {
       // Eq. (slimTik): mu_k = lambda_k + c_k lam_tik^2 / M
@@ -505,7 +504,9 @@ __global__ void __launch_bounds__(kCta) scatter_kernel(StepArgs<T> a) {
   const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (q >= a.p || a.ring_ids[q] < 0) return;
   const bool is_new = (q / a.ell) == a.info->slot;
-  const T c = (T)(-a.eta * a.z[q]);
+  // sg: x -= eta alpha_k A_k^T r_k, alpha_k = 1/lambda_k
+  const double zq = a.sg ? a.rhs[q] * (1.0 / a.info->lam_k) : a.z[q];
+  const T c = (T)(-a.eta * zq);
   const int* rp = a.ring_pix + (size_t)q * a.taps;
   const double* rw = a.ring_w + (size_t)q * a.taps;
   const long long n = a.n;

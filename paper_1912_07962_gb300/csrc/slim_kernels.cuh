@@ -19,6 +19,7 @@ struct StepArgs {
   unsigned long long seed;
   double lam, eta;
   int ramp;
+  int decay_after;             // 1/k decay of the damping after this step (0: none)
   int* ring_ids;           // [p]        ray id per ring row, -1 if empty
   int* ring_pix;           // [p*taps]   pixel of each tap, -1 if none
   double* ring_w;          // [p*taps]   float64 tap weights
@@ -42,6 +43,8 @@ struct StepArgs {
   double tik_beta;
   int tik_reading;
   const double* cinv;
+  // sg (B_k = alpha_k I): the scatter takes z = r_k / lambda_k on the block's rows
+  int sg;
 };
 
 // Sliced ELLPACK with slices of 32 lines (SELL-32): line l of slice s has its

@@ -29,8 +29,7 @@ __global__ void la_sample_kernel(LaArgs<T> a) {
     const long long j = *a.gdone + 1;
     const int view = (int)bounded32(draw64(a.seed, kStreamBlocks, (unsigned long long)(j - 1)),
                                     (uint32_t)a.n_views);
-    double lam_j = a.lam;
-    if (a.ramp && j <= a.r + 1) lam_j = __ddiv_rn(__dmul_rn(a.lam, (double)(a.r + 1)), (double)j);
+    double lam_j = damping_k(a.lam, j, a.r, a.ramp, a.decay_after);
     double tik_c = 0.0;
     if (a.tik_beta > 0.0) {
       // Eq. (slimTik): mu_j = lambda_j + c_j lam_tik^2 / M

@@ -32,6 +32,7 @@ struct LaArgs {
   unsigned long long seed;
   double lam, eta;
   int ramp;
+  int decay_after;             // 1/k decay of the damping after this step (0: none)
   long long* gdone;              // geometry steps prepared (device counter)
   StepInfo* info_buf;            // [nbuf] per-buffer step values
   int nbuf;                      // D+1

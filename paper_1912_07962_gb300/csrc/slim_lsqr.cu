@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "slim_device.cuh"
+#include "slim_grid.cuh"
 
 namespace slim {
 
@@ -32,47 +33,6 @@ namespace {
 
 constexpr int kLsqrThreads = 256;
 constexpr int kLsqrWarps = kLsqrThreads / 32;
-constexpr unsigned kLsqrSpin = 1u << 22;   // polls of a barrier before giving up (about a second)
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Grid barrier of a cooperative launch (every CTA resident): bar[0] counts
-// arrivals, bar[1] is the generation.  False when the wait ran out (status
-// SLIM_ETIMEOUT); the CTA then leaves, and the others run out at their next
-// barrier.
-__device__ bool grid_barrier(unsigned* bar, int* status, int* s_flag) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned gen = ld_acquire_u32(bar + 1);
-    __threadfence();
-    if (atomicAdd(bar, 1u) + 1 == gridDim.x) {
-      bar[0] = 0;
-      __threadfence();
-      st_release_u32(bar + 1, gen + 1);
-    } else {
-      unsigned it = 0;
-      while (ld_acquire_u32(bar + 1) == gen) {
-        if (++it > kLsqrSpin) {
-          set_status(status, SLIM_ETIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    *s_flag = ok;
-  }
-  __syncthreads();
-  return *s_flag != 0;
-}
-
 // Sum of every thread's v over the grid, returned in every thread: CTA sums
 // in part[blockIdx.x], then each CTA's warp 0 adds part[0..grid) in a fixed
 // order.

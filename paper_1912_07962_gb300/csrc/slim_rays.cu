@@ -97,8 +97,7 @@ __global__ void sample_rays_kernel(RayArgs a) {
   if (threadIdx.x == 0) {
     const long long k = *a.done + 1;
     const int slot = (int)((k - 1) % a.nslots);
-    double lam_k = a.lam;
-    if (a.ramp && k <= a.r + 1) lam_k = __ddiv_rn(__dmul_rn(a.lam, (double)(a.r + 1)), (double)k);
+    const double lam_k = damping_k(a.lam, k, a.r, a.ramp, a.decay_after);
     long long avail = a.m;
     if (a.kind == 2) {
       long long arrived = (k - 1) / a.steps_per_view + 1;

@@ -19,6 +19,7 @@ struct RayArgs {
   unsigned long long seed;
   double lam;
   int ramp;
+  int decay_after;             // 1/k decay of the damping after this step (0: none)
   int* ring_ids;                     // [p]
   int* ring_pix;                     // [p*taps] voxel index or -1
   double* ring_w;                    // [p*taps]

@@ -21,7 +21,7 @@ STATUS_NAMES = ["SLIM_OK", "SLIM_EINVAL", "SLIM_ENOMEM", "SLIM_ECUDA", "SLIM_ENO
                 "SLIM_ETIMEOUT", "SLIM_ESTATE", "SLIM_ENOTSUP"]
 SLIM_F32, SLIM_F64 = 0, 1
 SLIM_PREC_FP64, SLIM_PREC_FP32 = 0, 1
-SLIM_SOLVE_FP64, SLIM_SOLVE_MIXED, SLIM_SOLVE_LSQR = 0, 1, 2
+SLIM_SOLVE_FP64, SLIM_SOLVE_MIXED, SLIM_SOLVE_LSQR, SLIM_SOLVE_SG, SLIM_SOLVE_OLBFGS = 0, 1, 2, 3, 4
 SLIM_BLOCKS_VIEWS, SLIM_BLOCKS_RAYS, SLIM_BLOCKS_STREAM = 0, 1, 2
 
 # every function the header declares (checked by the CPU test suite)
@@ -58,7 +58,8 @@ class slim_step_opts(C.Structure):
     _fields_ = [("eta", C.c_double), ("ramp", C.c_int), ("solver", C.c_int),
                 ("refine_iters", C.c_int), ("use_graph", C.c_int), ("tile", C.c_int),
                 ("ctas_per_sm", C.c_int), ("lookahead", C.c_int), ("lsqr_max_iter", C.c_int),
-                ("lsqr_tol", C.c_double), ("tik_lambda", C.c_double), ("tik_reading", C.c_int)]
+                ("lsqr_tol", C.c_double), ("tik_lambda", C.c_double), ("tik_reading", C.c_int),
+                ("decay_after", C.c_int), ("olbfgs_memory", C.c_int)]
 
 
 class SlimError(RuntimeError):
@@ -164,7 +165,8 @@ class Slim:
                  solver=SLIM_SOLVE_FP64, refine_iters=2, eta=1.0, ramp=False, use_graph=False,
                  angles=None, a_mode=A_MATRIX_FREE, dim=2, det_v=1, kind=SLIM_BLOCKS_VIEWS,
                  steps_per_view=1, tile=0, ctas_per_sm=0, lookahead=0, lsqr_max_iter=0,
-                 lsqr_tol=0.0, tik_lambda=0.0, tik_reading=0, _handle=None):
+                 lsqr_tol=0.0, tik_lambda=0.0, tik_reading=0, decay_after=0, olbfgs_memory=0,
+                 _handle=None):
         lib = load()
         self._lib = lib
         self._angles = None
@@ -183,7 +185,8 @@ class Slim:
             g.angles = self._angles.ctypes.data_as(C.POINTER(C.c_double))
         blk = slim_blocks(kind, ell, seed, steps_per_view)
         opts = slim_step_opts(eta, int(ramp), solver, refine_iters, int(use_graph), tile, ctas_per_sm,
-                              lookahead, lsqr_max_iter, lsqr_tol, tik_lambda, tik_reading)
+                              lookahead, lsqr_max_iter, lsqr_tol, tik_lambda, tik_reading,
+                              decay_after, olbfgs_memory)
         h = C.c_void_p()
         st = lib.slim_create(C.byref(g), C.byref(blk), r, lam, C.byref(opts), C.byref(h))
         if st != SLIM_OK:
