@@ -459,6 +459,69 @@ def tik_block(sl, cfg, b, flush, stream, K, W, lam_tik=1.0, lookahead=6, ctas_pe
     return out
 
 
+def sensitivity_block(sl, flush, stream, reps=5, K=30, W=3, memory=10):
+    """Step-size sensitivity of slimLS (r = 0), sg and olbfgs (the comparison of
+    Sec. 4.1, here on the synthetic 64x64 tomography workload): the relative
+    reconstruction error to the phantom x_true after one epoch (60 view
+    blocks) for alpha = 1e-5 .. 1e3, the step size of sg and olbfgs and the
+    damping 1/lambda of slimLS; median and 5-95th percentiles over `reps`
+    block sequences.  (Against x_LS every method sits near 1 after one epoch:
+    this problem is ill-posed and x_LS carries the amplified noise.)  Also the
+    device time of one step of each method on the 256x256 workload."""
+    import torch
+    cfg = workloads.C1
+    x_true, e = workloads.tomo_inputs_2d(cfg)
+    b = make_b(sl, cfg, x_true, e)
+    xt = torch.tensor(x_true, dtype=torch.float64, device="cuda")
+    n_true = float(torch.linalg.norm(xt))
+    alphas = [10.0 ** p for p in range(-5, 4)]
+    methods = {"slimls_r0": sl.SLIM_SOLVE_FP64, "sg": sl.SLIM_SOLVE_SG,
+               "olbfgs": sl.SLIM_SOLVE_OLBFGS}
+    out = {"workload": f"{cfg.name}: one epoch ({cfg.n_views} view blocks), r = 0, "
+                       "error to the phantom", "reps": reps, "alpha": alphas,
+           "olbfgs_memory": memory}
+    xb = torch.empty(cfg.n, dtype=torch.float64, device="cuda")
+    for name, solver in methods.items():
+        rows = []
+        for alpha in alphas:
+            errs = []
+            for rep in range(reps):
+                c = sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.ell, 0, 1.0 / alpha, 1000 + rep,
+                            solver=solver, olbfgs_memory=memory,
+                            use_graph=solver != sl.SLIM_SOLVE_OLBFGS)
+                c.set_data(b)
+                try:
+                    c.step(cfg.n_views)
+                    c.get_x(xb)
+                    err = float(torch.linalg.norm(xb - xt)) / n_true
+                except sl.SlimError:
+                    err = float("inf")
+                c.close()
+                errs.append(err if np.isfinite(err) else float("inf"))
+            with np.errstate(invalid="ignore"):   # diverged runs are inf
+                q = np.percentile(np.array(errs), [5, 50, 95])
+
+            def fin(v):   # JSON has no infinity: a diverged run reads as null
+                return float(v) if np.isfinite(v) else None
+            rows.append({"alpha": alpha, "median": fin(q[1]), "p5": fin(q[0]), "p95": fin(q[2]),
+                         "diverged": int(sum(not np.isfinite(v) for v in errs))})
+        out[name] = rows
+    # device time of one step at 256x256 (float64 iterate, each step timed alone)
+    big = workloads.C2
+    xt2, e2 = workloads.tomo_inputs_2d(big)
+    b2 = make_b(sl, big, xt2, e2)
+    cost = {}
+    for name, solver in methods.items():
+        c = sl.Slim(big.N, big.n_views, big.det, big.ell, 0, 1e3, big.seed, solver=solver,
+                    olbfgs_memory=memory, use_graph=solver != sl.SLIM_SOLVE_OLBFGS)
+        c.set_data(b2)
+        per, _, _, _ = timed_steps(c, K, W, flush, stream)
+        c.close()
+        cost[name] = {"ms_per_step": sum(per) / K, "rows_per_s": big.ell * K / (sum(per) * 1e-3)}
+    out["step_cost_256"] = cost
+    return out
+
+
 def stream3d_block(sl, flush, stream, K, W, steps_per_view=46):
     """The 3D streaming form at 256^3: float32 volume, random rays from the views
     that have arrived, float64 per-slice solves, one CUDA graph per step."""
@@ -807,6 +870,8 @@ def main_gpu(args):
              if rank == 0 and args.batch_steps > 0 else None)
     lsqr_pass = (lsqr_block(sl, cfg, b, flush, stream, args.lsqr_steps, 3)
                  if rank == 0 and args.lsqr_steps > 0 else None)
+    sens = (sensitivity_block(sl, flush, stream, reps=args.sens_reps)
+            if rank == 0 and args.sens_reps > 0 else None)
     tik_pass = (tik_block(sl, cfg, b, flush, stream, args.tik_steps, max(3, args.warmup),
                           lookahead=args.lookahead or 6, ctas_per_sm=args.factor_ctas_per_sm)
                 if rank == 0 and args.tik_steps > 0 else None)
@@ -848,7 +913,7 @@ def main_gpu(args):
         "phases_note": ("one step at a time (synchronous pass); the pipelined region overlaps "
                         "the geometry phases with the iterate chain" if args.lookahead else
                         "per step, inside the timed region"),
-        "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "batched": batch, "lsqr": lsqr_pass, "tik": tik_pass, "unet": unet, "warm_start": warm, "tta": tta, "e2e": e2e,
+        "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "batched": batch, "lsqr": lsqr_pass, "tik": tik_pass, "step_size_sensitivity": sens, "unet": unet, "warm_start": warm, "tta": tta, "e2e": e2e,
         "cpu_baseline": cpu,
         "gpu_launches": kernels * args.steps, "kernels_per_step": kernels, "clocks": clocks,
     }
@@ -890,6 +955,18 @@ def main_lsqr(args):
     x_true, e = workloads.tomo_inputs_2d(cfg)
     b = make_b(sl, cfg, x_true, e)
     print(json.dumps({"lsqr": lsqr_block(sl, cfg, b, flush, stream, args.lsqr_steps, 3)}))
+
+
+def main_sens(args):
+    """The step-size sensitivity of slimLS, sg and olbfgs alone (one JSON line)."""
+    import torch
+    from paper_1912_07962_gb300 import build as slbuild, slim as sl
+    slbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    print(json.dumps({"step_size_sensitivity": sensitivity_block(sl, flush, stream,
+                                                                 reps=max(1, args.sens_reps))}))
 
 
 def main_tik(args):
@@ -949,6 +1026,10 @@ def main():
                     help="time only the LSQR-step form and print that line")
     ap.add_argument("--tik-steps", type=int, default=30,
                     help="steps of slimTik and slimLS timed side by side (0: skip)")
+    ap.add_argument("--sens-reps", type=int, default=5,
+                    help="block sequences per step size in the sensitivity sweep (0: skip)")
+    ap.add_argument("--sens-only", action="store_true",
+                    help="run only the step-size sensitivity sweep and print that line")
     ap.add_argument("--tik-only", action="store_true",
                     help="time only slimTik against slimLS and print that line")
     ap.add_argument("--unet-only", action="store_true",
@@ -993,6 +1074,8 @@ def main():
         main_lsqr(args)
     elif args.tik_only:
         main_tik(args)
+    elif args.sens_only:
+        main_sens(args)
     else:
         main_gpu(args)
 
