@@ -28,6 +28,21 @@ Definition (float64, every operation rounded once; no fused multiply-add):
   the 2D one; along z, fz = z_v + cc, k0 = floor(fz), wz = fz - k0, and each
   in-plane tap w splits into w*(1 - wz) at slice k0 and w*wz at slice k0+1.
   Ray id = (a*Dv + v)*Du + uu; 2D ray id = a*D + d.
+
+  3D with random directions (Sec. 4.3: projection images from directions
+  uniform on the sphere): view a has a frame (d, u, v) given as data, d the
+  unit ray direction and (u, v) an orthonormal detector basis perpendicular
+  to it.  Ray (a, v, uu) passes through p0 = t_u u + t_v v (t_u = uu -
+  (Du-1)/2, t_v = v - (Dv-1)/2; componentwise t_u*u_c + t_v*v_c) in
+  coordinates centred on the volume.  March along k = argmax_c |d_c| (first on
+  ties), the other axes (i, j) in increasing order; inv = 1/d_k and ia = |inv|
+  per view (shared as data).  For slice s = 0..N-1:
+      tau = ((s - cc) - p0_k)*inv
+      fi = (p0_i + tau*d_i) + cc;  i0 = floor(fi);  wi = fi - i0   (same for j)
+      taps (i0, j0) ((1-wi)*(1-wj))*ia, (i0+1, j0) (wi*(1-wj))*ia,
+           (i0, j0+1) ((1-wi)*wj)*ia, (i0+1, j0+1) (wi*wj)*ia
+  at axis-k coordinate s, in that order; taps outside the volume or of weight
+  exactly 0 are dropped.
 """
 from __future__ import annotations
 
@@ -41,8 +56,15 @@ class Geometry:
     """Parallel-beam geometry: 2D when det_v == 1 and dim == 2, else 3D."""
 
     def __init__(self, N: int, n_views: int, det_u: int, det_v: int = 1, dim: int = 2,
-                 angles=None):
+                 angles=None, frames=None):
         self.N, self.n_views, self.det_u, self.det_v, self.dim = N, n_views, det_u, det_v, dim
+        # 3D random directions: per view (d, u, v) and the march axis, 1/d_k
+        self.frames = None if frames is None else np.asarray(frames, dtype=np.float64)
+        if self.frames is not None:
+            if dim != 3 or self.frames.shape != (n_views, 9):
+                raise ValueError("frames: 3D, one (d, u, v) row per view")
+            self.axis = [int(np.argmax(np.abs(f[:3]))) for f in self.frames]
+            self.inv = [1.0 / f[k] for f, k in zip(self.frames, self.axis)]
         if dim == 2 and det_v != 1:
             raise ValueError("2D geometry has det_v == 1")
         if angles is None:
@@ -90,8 +112,44 @@ def _inplane_taps(g: Geometry, a: int, du: int):
     return major, minor, w          # ix = major, iy = minor
 
 
+def _frame_taps(g: Geometry, ray: int):
+    """Taps of one ray of the random-direction 3D geometry (voxel, weight)."""
+    N = g.N
+    a, rem = divmod(int(ray), g.rays_per_view)
+    iv, iu = divmod(rem, g.det_u)
+    f = g.frames[a]
+    d, u, v = f[0:3], f[3:6], f[6:9]
+    tu = iu - (g.det_u - 1) / 2.0
+    tv = iv - (g.det_v - 1) / 2.0
+    p0 = [tu * u[c] + tv * v[c] for c in range(3)]
+    k = g.axis[a]
+    i, j = [c for c in range(3) if c != k]
+    inv = g.inv[a]
+    ia = abs(inv)
+    cc = (N - 1) / 2.0
+    s = np.arange(N, dtype=np.int64)
+    tau = ((s.astype(np.float64) - cc) - p0[k]) * inv
+    fi = (p0[i] + tau * d[i]) + cc
+    fj = (p0[j] + tau * d[j]) + cc
+    i0f, j0f = np.floor(fi), np.floor(fj)
+    wi, wj = fi - i0f, fj - j0f
+    i0, j0 = i0f.astype(np.int64), j0f.astype(np.int64)
+    w = np.stack([((1.0 - wi) * (1.0 - wj)) * ia, (wi * (1.0 - wj)) * ia,
+                  ((1.0 - wi) * wj) * ia, (wi * wj) * ia], axis=1).reshape(-1)
+    ci = np.stack([i0, i0 + 1, i0, i0 + 1], axis=1).reshape(-1)
+    cj = np.stack([j0, j0, j0 + 1, j0 + 1], axis=1).reshape(-1)
+    ck = np.repeat(s, 4)
+    coord = np.zeros((3, ci.size), dtype=np.int64)
+    coord[k], coord[i], coord[j] = ck, ci, cj
+    keep = ((coord >= 0) & (coord < N)).all(axis=0) & (w != 0.0)
+    idx = (coord[2] * N + coord[1]) * N + coord[0]
+    return idx[keep], w[keep]
+
+
 def ray_taps(g: Geometry, ray: int):
     """(pixel indices int64, weights float64) of one row of A."""
+    if g.frames is not None:
+        return _frame_taps(g, ray)
     if g.dim == 2:
         a, d = divmod(int(ray), g.det_u)
         ix, iy, w = _inplane_taps(g, a, d)

@@ -220,6 +220,35 @@ class Tomo3D:
 C4 = Tomo3D("streaming-256^3", N=256, n_views=360, det_u=368, det_v=256, ell=2048, r=4,
             lam=1e-3, seed=4)
 
+STREAM_FRAMES = 6
+
+
+def random_frames(n_views: int, seed: int) -> np.ndarray:
+    """View frames of the random-direction 3D geometry (Sec. 4.3: projection
+    images taken from directions uniform on the unit sphere).  Rows
+    (d, u, v), 9 float64 values each: d a normalised standard-normal 3-vector;
+    u, v an orthonormal detector basis perpendicular to d: u from the
+    coordinate axis least aligned with d by one Gram-Schmidt step, v = d x u."""
+    g = _gen(seed, STREAM_FRAMES)
+    out = np.empty((n_views, 9))
+    for a in range(n_views):
+        d = g.standard_normal(3)
+        d /= np.linalg.norm(d)
+        e = np.zeros(3)
+        e[int(np.argmin(np.abs(d)))] = 1.0
+        u = e - (e @ d) * d
+        u /= np.linalg.norm(u)
+        v = np.cross(d, u)
+        out[a] = np.concatenate([d, u, v])
+    return out
+
+
+# The 3D geometry of Sec. 4.3 (random directions) at 256^3: 360 random view
+# directions on a 368 x 368 detector (the cube's shadow is up to 443 wide; the
+# corners are clipped), l = 2048 random rays from the arrived views, r = 4.
+C4R = Tomo3D("random-directions-256^3", N=256, n_views=360, det_u=368, det_v=368, ell=2048,
+             r=4, lam=1e-3, seed=5)
+
 
 def batch_mix(count: int = 96, meta_seed: int = 3):
     """Parameters of the batched workload: per problem (N, n_views, det, ell, r, lam, seed).
