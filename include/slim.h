@@ -70,7 +70,7 @@ enum { SLIM_BLOCKS_VIEWS = 0, SLIM_BLOCKS_RAYS = 1, SLIM_BLOCKS_STREAM = 2 };
  *   n_side     N
  *   n_views    A_v projection angles
  *   det_u      D detector bins per view row, unit spacing, centred
- *   det_v      1 in 2D; in 3D the detector rows, which must equal N: row v
+ *   det_v      1 in 2D; in 3D (no frames) the detector rows, which must equal N: row v
  *              then lies in z-slice v, rays of different slices share no voxel
  *              and the Gram matrix is block diagonal by slice
  *   angles     host array [n_views] of radians, or NULL for theta_a = a*pi/A_v
@@ -81,6 +81,19 @@ enum { SLIM_BLOCKS_VIEWS = 0, SLIM_BLOCKS_RAYS = 1, SLIM_BLOCKS_STREAM = 2 };
  *                 The step then reads its rows from the stored matrix, and the
  *                 method runs on that (rounded) A: residual, Gram and scatter
  *                 all use the stored values.
+ *   frames     3D only: NULL (views rotate about z, as above), or a host
+ *              array [n_views * 9] of per-view frames (d, u, v) for views from
+ *              arbitrary directions (Sec. 4.3: directions uniform on the unit
+ *              sphere): d the unit ray direction, (u, v) an orthonormal
+ *              detector basis perpendicular to it (SLIM_EINVAL otherwise,
+ *              1e-9).  Ray (a, v, uu), id (a*Dv + v)*Du + uu, passes through
+ *              t_u u + t_v v (t_u = uu - (Du-1)/2, t_v = v - (Dv-1)/2) from the
+ *              volume's centre; Joseph's rows march it along k = argmax |d_c|
+ *              with bilinear taps in the other two axes (four per slice,
+ *              weights times |1/d_k|).  Any det_v.  Random-ray blocks only
+ *              (SLIM_BLOCKS_RAYS / _STREAM); the Gram matrix comes from
+ *              voxel lists and the damped solve is the tiled dense one
+ *              (FP64 or MIXED solver, lookahead 0)
  *   precision  SLIM_PREC_FP64: x, b, residual and scatter in float64;
  *              SLIM_PREC_FP32: x, b, residual and scatter in float32 with float32
  *              accumulation.  The Gram matrix is float64 in both. */
@@ -93,6 +106,7 @@ typedef struct {
   const double* angles;
   int a_mode;
   int precision;
+  const double* frames;
 } slim_geometry;
 
 /* Block sampling (Sec. 1: W_k i.i.d. uniform over M selectors).

@@ -12,6 +12,7 @@
 #include "slim_lookahead.cuh"
 #include "slim_lsqr.cuh"
 #include "slim_olbfgs.cuh"
+#include "slim_frames.cuh"
 #include "slim_unet.cuh"
 #include "slim_rays.cuh"
 
@@ -58,6 +59,12 @@ struct slim_ctx {
   double tik_lambda = 0.0;         // slimTik: lam_tik of Eq. (TLS1) (0: slimLS)
   int tik_reading = 0;             // count of Tikhonov rows: 0 blocks of M_k, 1 r
   double* d_cinv = nullptr;        // [n] 1/c of C_k = diag(c); null: C_k = I
+  // 3D with random view directions (frames given): general Joseph rows, Gram
+  // from voxel lists, the tiled dense solve
+  bool general3d = false;
+  std::vector<FrameGeom> h_frames;
+  FrameGeom* d_frames = nullptr;
+  int* d_vnext = nullptr;          // [ell * taps] voxel-list links of the new block
   int olbfgs_memory = 0;           // pairs of the olbfgs comparator
   double* d_olb = nullptr;         // its scratch: g, S, Y, u, S^T Y, Y^T Y, partial sums
   int* d_olb_state = nullptr;      // its pair bookkeeping
@@ -263,6 +270,7 @@ RayArgs make_ray_args(slim_ctx* c) {
   a.cap = c->cap;
   a.slice_cnt = c->d_slice_cnt;
   a.slice_rows = c->d_slice_rows;
+  a.dense = c->dim == 2 || c->general3d;
   return a;
 }
 
@@ -281,7 +289,7 @@ cudaError_t mark(slim_ctx* c, int i) {
 // one cluster kernel each, else a forward and a backward kernel; 2 per
 // refinement round (residual, z += dz), scatter).
 int kernels_per_step(const slim_ctx* c) {
-  if (c->dim == 3) return 6;   // sample, march, collect, slice Gram, slice solve, scatter
+  if (c->dim == 3 && !c->general3d) return 6;   // sample, march, collect, slice Gram, slice solve, scatter
   if (c->solver == SLIM_SOLVE_LSQR) return 3;   // sample, forward + residual, LSQR (with x update)
   if (c->solver == SLIM_SOLVE_SG) return 3;     // sample, forward + residual, scatter
   if (c->solver == SLIM_SOLVE_OLBFGS) return 3; // sample, forward + residual, the olbfgs step
@@ -341,6 +349,21 @@ cudaError_t enqueue_ray_step_t(slim_ctx* c) {
   if ((e = mark(c, 0)) != cudaSuccess) return e;
   if ((e = launch_sample_rays<T>(ra, s)) != cudaSuccess) return e;
   if ((e = mark(c, kPhSample)) != cudaSuccess) return e;
+  if (c->general3d) {
+    // random directions: march with voxel lists, Gram through them, tiled
+    // solve; the scatter clears the lists' heads
+    const FrameArgs fa{c->d_frames, c->d_map_ray, c->d_vnext};
+    a.map_ray = c->d_map_ray;
+    if ((e = launch_forward_frames<T>(ra, fa, (T*)c->d_x, (const T*)c->d_b, s)) != cudaSuccess)
+      return e;
+    if ((e = mark(c, kPhForward)) != cudaSuccess) return e;
+    if ((e = launch_gram_frames(ra, fa, s)) != cudaSuccess) return e;
+    if ((e = mark(c, kPhGram)) != cudaSuccess) return e;
+    if ((e = enqueue_solve(c)) != cudaSuccess) return e;
+    if ((e = mark(c, kPhSolve)) != cudaSuccess) return e;
+    if ((e = launch_scatter<T>(a, s)) != cudaSuccess) return e;
+    return mark(c, kPhScatter);
+  }
   if ((e = launch_forward_rays<T>(ra, (T*)c->d_x, (const T*)c->d_b, s)) != cudaSuccess) return e;
   if ((e = mark(c, kPhForward)) != cudaSuccess) return e;
   if (c->dim == 2) {
@@ -482,6 +505,18 @@ cudaError_t rebuild_t(slim_ctx* c, long long k) {
         cudaSuccess)
       return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;   // `done` is a host local
+    if (c->general3d) {
+      RayArgs ra = make_ray_args(c);
+      const FrameArgs fa{c->d_frames, c->d_map_ray, c->d_vnext};
+      if ((e = launch_sample_rays<T>(ra, s)) != cudaSuccess) return e;
+      if ((e = launch_forward_frames<T>(ra, fa, (T*)c->d_x, (const T*)c->d_b, s)) != cudaSuccess)
+        return e;
+      if ((e = launch_gram_frames(ra, fa, s)) != cudaSuccess) return e;
+      if ((e = cudaMemsetAsync(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int), s)) !=
+          cudaSuccess)
+        return e;
+      continue;
+    }
     if (c->kind != SLIM_BLOCKS_VIEWS) {
       RayArgs ra = make_ray_args(c);
       if ((e = launch_sample_rays<T>(ra, s)) != cudaSuccess) return e;
@@ -529,7 +564,8 @@ void free_all(slim_ctx* c) {
   void* ptrs[] = {c->d_slice_cnt, c->d_slice_rows, c->d_views, c->d_info, c->d_done, c->d_status, c->d_x, c->d_b,
                   c->d_ring_ids, c->d_ring_pix, c->d_ring_w, c->d_map_ray, c->d_map_w,
                   c->d_G, c->d_L, c->d_rhs, c->d_z, c->d_dz, c->d_res, c->d_ref, c->d_err,
-                  c->d_lsqr, c->d_lsqr_bar, c->d_cinv, c->d_olb, c->d_olb_state};
+                  c->d_lsqr, c->d_lsqr_bar, c->d_cinv, c->d_olb, c->d_olb_state,
+                  c->d_frames, c->d_vnext};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   chol_plan_destroy(&c->plan);
@@ -828,7 +864,24 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
   if (!geom || !blocks) return SLIM_EINVAL;
   if (geom->dim != 2 && geom->dim != 3) return SLIM_EINVAL;
   if (geom->dim == 2 && geom->det_v != 1) return SLIM_EINVAL;
-  if (geom->dim == 3 && geom->det_v != geom->n_side) return SLIM_ENOTSUP;
+  const bool frames = geom->dim == 3 && geom->frames != nullptr;
+  if (geom->dim == 2 && geom->frames) return SLIM_EINVAL;
+  if (geom->dim == 3 && !frames && geom->det_v != geom->n_side) return SLIM_ENOTSUP;
+  if (frames) {
+    // each row (d, u, v) orthonormal
+    for (int a = 0; a < geom->n_views; ++a) {
+      const double* f = geom->frames + 9 * (size_t)a;
+      for (int q = 0; q < 9; ++q)
+        if (!std::isfinite(f[q])) return SLIM_EINVAL;
+      auto dot = [&](int x, int y) { return f[x] * f[y] + f[x + 1] * f[y + 1] + f[x + 2] * f[y + 2]; };
+      if (std::fabs(dot(0, 0) - 1.0) > 1e-9 || std::fabs(dot(3, 3) - 1.0) > 1e-9 ||
+          std::fabs(dot(6, 6) - 1.0) > 1e-9 || std::fabs(dot(0, 3)) > 1e-9 ||
+          std::fabs(dot(0, 6)) > 1e-9 || std::fabs(dot(3, 6)) > 1e-9)
+        return SLIM_EINVAL;
+    }
+    if (geom->det_v < 1 || (long long)geom->det_v * geom->det_u * geom->n_views > 0x7fffffffLL)
+      return SLIM_EINVAL;
+  }
   if (geom->a_mode < 0 || geom->a_mode > 2) return SLIM_EINVAL;
   if (geom->n_side < 2 || geom->n_side > 16384 || geom->n_views < 1 || geom->det_u < 1)
     return SLIM_EINVAL;
@@ -861,6 +914,8 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
   c->lam = lambda;
   c->p = c->nslots * c->ell;
   c->taps = 2 * c->N;
+  c->general3d = frames;
+  if (frames) c->taps = 4 * c->N;   // four bilinear taps per slice
   if (step) {
     c->eta = step->eta;
     c->ramp = step->ramp;
@@ -944,9 +999,23 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
   }
   c->nb = c->tile ? c->tile : (c->solver == SLIM_SOLVE_FP64 ? 32 : 64);
   c->P = (c->p + c->nb - 1) / c->nb * c->nb;
-  const bool dense_solve = c->dim == 2;             // tiled Cholesky of the full p x p system
-  const bool use_map = c->kind == SLIM_BLOCKS_VIEWS;
-  if (c->dim == 3) {
+  // tiled Cholesky of the full p x p system (2D, and 3D with random directions)
+  const bool dense_solve = c->dim == 2 || c->general3d;
+  // pixel -> ray map of the new block (view blocks), or voxel list heads
+  const bool use_map = c->kind == SLIM_BLOCKS_VIEWS || c->general3d;
+  if (c->general3d && (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED)) {
+    delete c;
+    return SLIM_ENOTSUP;
+  }
+  if (c->general3d && gram_frames_smem(c->ell) > 200 * 1024) {
+    delete c;
+    return SLIM_ENOTSUP;
+  }
+  if (c->general3d) {
+    c->h_frames.resize(c->n_views);
+    for (int a = 0; a < c->n_views; ++a) c->h_frames[a] = make_frame_geom(geom->frames + 9 * (size_t)a);
+  }
+  if (c->dim == 3 && !c->general3d) {
     c->P = c->p;      // G stored p x p; the solve runs slice by slice
     c->S = c->N;
     c->cap = 96;
@@ -1006,7 +1075,9 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       {(void**)&c->d_ring_pix, (size_t)ring_rows * c->taps * sizeof(int)},
       {(void**)&c->d_ring_w, (size_t)ring_rows * c->taps * sizeof(double)},
       {(void**)&c->d_map_ray, use_map ? 2 * (size_t)c->n * sizeof(int) : 0},
-      {(void**)&c->d_map_w, use_map ? 2 * (size_t)c->n * sizeof(double) : 0},
+      {(void**)&c->d_map_w, c->kind == SLIM_BLOCKS_VIEWS ? 2 * (size_t)c->n * sizeof(double) : 0},
+      {(void**)&c->d_frames, c->general3d ? c->h_frames.size() * sizeof(FrameGeom) : 0},
+      {(void**)&c->d_vnext, c->general3d ? (size_t)c->ell * c->taps * sizeof(int) : 0},
       {(void**)&c->d_G, g_elems * sizeof(double)},
       {&c->d_L, dense_solve && !la && !lsqr ? (size_t)c->P * c->P * fs : 0},
       {(void**)&c->d_gdone, la ? sizeof(long long) : 0},
@@ -1025,6 +1096,9 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
   if (st == SLIM_OK) {
     chk(cudaMemcpy(c->d_views, c->h_views.data(), c->h_views.size() * sizeof(ViewGeom),
                    cudaMemcpyHostToDevice), "views");
+    if (c->general3d)
+      chk(cudaMemcpy(c->d_frames, c->h_frames.data(), c->h_frames.size() * sizeof(FrameGeom),
+                     cudaMemcpyHostToDevice), "frames");
     chk(cudaMemset(c->d_done, 0, sizeof(long long)), "memset");
     chk(cudaMemset(c->d_status, 0, sizeof(int)), "memset");
     chk(cudaMemset(c->d_x, 0, (size_t)c->n * es), "memset");
@@ -1681,6 +1755,15 @@ slim_status slim_project(slim_ctx* c, const int* ids, int count, const void* x, 
   if (!c || !x || !y) return fail(c, SLIM_EINVAL, "project: bad arguments");
   if (!ids) count = (int)c->m;
   if (count < 0) return fail(c, SLIM_EINVAL, "project: bad count");
+  if (c->general3d) {
+    if (c->precision == SLIM_PREC_FP32)
+      CK(launch_project_frames<float>(c->d_frames, c->N, c->D, c->Dv, ids, count,
+                                      (const float*)x, (float*)y, c->stream), "project");
+    else
+      CK(launch_project_frames<double>(c->d_frames, c->N, c->D, c->Dv, ids, count,
+                                       (const double*)x, (double*)y, c->stream), "project");
+    return SLIM_OK;
+  }
   if (c->dim == 3) {
     if (c->precision == SLIM_PREC_FP32)
       CK(launch_project_rays<float>(c->d_views, c->N, c->D, c->Dv, ids, count, (const float*)x,
@@ -1712,6 +1795,15 @@ slim_status slim_backproject(slim_ctx* c, const int* ids, int count, const void*
   if (!c || !x || !y) return fail(c, SLIM_EINVAL, "backproject: bad arguments");
   if (!ids) count = (int)c->m;
   if (count < 0) return fail(c, SLIM_EINVAL, "backproject: bad count");
+  if (c->general3d) {
+    if (c->precision == SLIM_PREC_FP32)
+      CK(launch_backproject_frames<float>(c->d_frames, c->N, c->D, c->Dv, ids, count,
+                                          (const float*)y, (float*)x, c->stream), "backproject");
+    else
+      CK(launch_backproject_frames<double>(c->d_frames, c->N, c->D, c->Dv, ids, count,
+                                           (const double*)y, (double*)x, c->stream), "backproject");
+    return SLIM_OK;
+  }
   if (c->dim == 3) return fail(c, SLIM_ENOTSUP, "backproject: 2D only");
   if (c->a_mode) {
     if (c->precision == SLIM_PREC_FP32)

@@ -118,10 +118,10 @@ __global__ void sample_rays_kernel(RayArgs a) {
   for (int i = threadIdx.x; i < a.ell; i += blockDim.x)
     a.ring_ids[s_slot * a.ell + i] =
         (int)bounded32(draw64(a.seed, kStreamRays, base + (unsigned long long)i), s_avail);
-  const int nr = a.dim == 3 ? a.p : a.P;
+  const int nr = a.dense ? a.P : a.p;
   for (int i = threadIdx.x; i < nr; i += blockDim.x) {
     a.rhs[i] = 0.0;
-    if (a.dim == 3) a.z[i] = 0.0;
+    if (!a.dense) a.z[i] = 0.0;
   }
 }
 

@@ -46,7 +46,7 @@ PHASES = ["sample", "forward_residual", "gram_update", "form_k", "factor", "solv
 class slim_geometry(C.Structure):
     _fields_ = [("dim", C.c_int), ("n_side", C.c_int), ("n_views", C.c_int),
                 ("det_u", C.c_int), ("det_v", C.c_int), ("angles", C.POINTER(C.c_double)),
-                ("a_mode", C.c_int), ("precision", C.c_int)]
+                ("a_mode", C.c_int), ("precision", C.c_int), ("frames", C.POINTER(C.c_double))]
 
 
 class slim_blocks(C.Structure):
@@ -166,7 +166,7 @@ class Slim:
                  angles=None, a_mode=A_MATRIX_FREE, dim=2, det_v=1, kind=SLIM_BLOCKS_VIEWS,
                  steps_per_view=1, tile=0, ctas_per_sm=0, lookahead=0, lsqr_max_iter=0,
                  lsqr_tol=0.0, tik_lambda=0.0, tik_reading=0, decay_after=0, olbfgs_memory=0,
-                 _handle=None):
+                 frames=None, _handle=None):
         lib = load()
         self._lib = lib
         self._angles = None
@@ -183,6 +183,10 @@ class Slim:
         if angles is not None:
             self._angles = np.ascontiguousarray(angles, dtype=np.float64)
             g.angles = self._angles.ctypes.data_as(C.POINTER(C.c_double))
+        self._frames = None
+        if frames is not None:       # 3D views from arbitrary directions: rows (d, u, v)
+            self._frames = np.ascontiguousarray(frames, dtype=np.float64).reshape(-1)
+            g.frames = self._frames.ctypes.data_as(C.POINTER(C.c_double))
         blk = slim_blocks(kind, ell, seed, steps_per_view)
         opts = slim_step_opts(eta, int(ramp), solver, refine_iters, int(use_graph), tile, ctas_per_sm,
                               lookahead, lsqr_max_iter, lsqr_tol, tik_lambda, tik_reading,
