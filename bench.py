@@ -566,6 +566,51 @@ def stream3d_block(sl, flush, stream, K, W, steps_per_view=46):
             "roofline": rl}
 
 
+def frames3d_block(sl, flush, stream, K, W, r_values=(0, 4), steps_per_view=46):
+    """3D with views from random directions (Sec. 4.3's geometry) at 256^3:
+    360 directions uniform on the sphere, a 368 x 368 detector, ell = 2048
+    random rays from the arrived views; float32 volume, float64 Gram from the
+    voxel lists, float32 tiled Cholesky + 2 float64 refinements (the window's
+    rays cross every slice, so the Gram matrix is dense in general), one CUDA
+    graph per step.  r = 0 is the paper's 3D setting, r = 4 the memory of the
+    streaming workload (p = 10,240)."""
+    import torch
+    cfg = workloads.C4R
+    fr = workloads.random_frames(cfg.n_views, cfg.seed)
+    x_true = workloads.phantom_3d(cfg.N, cfg.seed, cfg.n_ellipsoids, dtype=np.float32)
+    out = {"workload": f"{cfg.name}: {cfg.N}^3 volume, {cfg.n_views} random directions x "
+                       f"{cfg.det_v}x{cfg.det_u} detector (m={cfg.m}), ell={cfg.ell} random rays "
+                       f"from arrived views (one view every {steps_per_view} steps), "
+                       f"lambda={cfg.lam:g}", "steps": K, "warmup": W}
+    b = None
+    for r in r_values:
+        s = sl.Slim(cfg.N, cfg.n_views, cfg.det_u, cfg.ell, r, cfg.lam, cfg.seed,
+                    precision=sl.SLIM_PREC_FP32, solver=sl.SLIM_SOLVE_MIXED, refine_iters=2,
+                    dim=3, det_v=cfg.det_v, kind=sl.SLIM_BLOCKS_STREAM,
+                    steps_per_view=steps_per_view, use_graph=True, frames=fr)
+        if b is None:
+            xt = torch.tensor(x_true, device="cuda")
+            y = torch.zeros(cfg.m, dtype=torch.float32, device="cuda")
+            s.project(xt, y)
+            torch.cuda.synchronize()
+            e = torch.tensor(workloads.noise_direction(cfg.m, cfg.seed), dtype=torch.float32,
+                             device="cuda")
+            b = y + cfg.noise * torch.linalg.norm(y) * e / torch.linalg.norm(e)
+            torch.cuda.synchronize()
+            del xt, e, y
+        s.set_data(b)
+        per, ph, _, _ = timed_steps(s, K, W, flush, stream)
+        s.close()
+        t = sum(per) * 1e-3
+        p = (r + 1) * cfg.ell
+        phases = {k: v / K for k, v in ph.items()}
+        out[f"r{r}"] = {"p": p, "rows_per_s": cfg.ell * K / t, "ms_per_step": t / K * 1e3,
+                        "phases_ms": phases, "dominant": max(phases, key=phases.get),
+                        "factor_tflops": (p ** 3 / 3) / (phases["factor"] * 1e-3) / 1e12
+                        if phases.get("factor") else None}
+    return out
+
+
 def batch_block(sl, flush, stream, K, W, count=96):
     """Many uneven 2D problems (random-ray blocks) advancing together: one CUDA
     graph per batch step with a parallel branch per problem, tile size and CTAs
@@ -872,6 +917,8 @@ def main_gpu(args):
                  if rank == 0 and args.lsqr_steps > 0 else None)
     sens = (sensitivity_block(sl, flush, stream, reps=args.sens_reps)
             if rank == 0 and args.sens_reps > 0 else None)
+    f3d = (frames3d_block(sl, flush, stream, args.frames_steps, 3)
+           if rank == 0 and args.frames_steps > 0 else None)
     tik_pass = (tik_block(sl, cfg, b, flush, stream, args.tik_steps, max(3, args.warmup),
                           lookahead=args.lookahead or 6, ctas_per_sm=args.factor_ctas_per_sm)
                 if rank == 0 and args.tik_steps > 0 else None)
@@ -913,7 +960,7 @@ def main_gpu(args):
         "phases_note": ("one step at a time (synchronous pass); the pipelined region overlaps "
                         "the geometry phases with the iterate chain" if args.lookahead else
                         "per step, inside the timed region"),
-        "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "batched": batch, "lsqr": lsqr_pass, "tik": tik_pass, "step_size_sensitivity": sens, "unet": unet, "warm_start": warm, "tta": tta, "e2e": e2e,
+        "roofline": rl, "csr_full_pass": csr_pass, "streaming_3d": s3d, "batched": batch, "lsqr": lsqr_pass, "tik": tik_pass, "random_directions_3d": f3d, "step_size_sensitivity": sens, "unet": unet, "warm_start": warm, "tta": tta, "e2e": e2e,
         "cpu_baseline": cpu,
         "gpu_launches": kernels * args.steps, "kernels_per_step": kernels, "clocks": clocks,
     }
@@ -967,6 +1014,18 @@ def main_sens(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     print(json.dumps({"step_size_sensitivity": sensitivity_block(sl, flush, stream,
                                                                  reps=max(1, args.sens_reps))}))
+
+
+def main_frames(args):
+    """3D with random view directions alone (one JSON line)."""
+    import torch
+    from paper_1912_07962_gb300 import build as slbuild, slim as sl
+    slbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    print(json.dumps({"random_directions_3d": frames3d_block(sl, flush, stream,
+                                                             max(1, args.frames_steps), 3)}))
 
 
 def main_tik(args):
@@ -1030,6 +1089,10 @@ def main():
                     help="block sequences per step size in the sensitivity sweep (0: skip)")
     ap.add_argument("--sens-only", action="store_true",
                     help="run only the step-size sensitivity sweep and print that line")
+    ap.add_argument("--frames-steps", type=int, default=5,
+                    help="timed steps of the random-direction 3D block (0: skip)")
+    ap.add_argument("--frames-only", action="store_true",
+                    help="run only the random-direction 3D block and print that line")
     ap.add_argument("--tik-only", action="store_true",
                     help="time only slimTik against slimLS and print that line")
     ap.add_argument("--unet-only", action="store_true",
@@ -1076,6 +1139,8 @@ def main():
         main_tik(args)
     elif args.sens_only:
         main_sens(args)
+    elif args.frames_only:
+        main_frames(args)
     else:
         main_gpu(args)
 
