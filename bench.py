@@ -470,16 +470,38 @@ def sensitivity_block(sl, flush, stream, reps=5, K=30, W=3, memory=10):
     device time of one step of each method on the 256x256 workload."""
     import torch
     cfg = workloads.C1
+    out = {"workload": f"{cfg.name}: one epoch ({cfg.n_views} view blocks), r = 0, "
+                       "error to the phantom", "reps": reps, "olbfgs_memory": memory}
+    methods = {"slimls_r0": sl.SLIM_SOLVE_FP64, "sg": sl.SLIM_SOLVE_SG,
+               "olbfgs": sl.SLIM_SOLVE_OLBFGS}
+    if reps > 0:
+        out.update(_sensitivity_sweep(sl, cfg, methods, reps, memory))
+    # device time of one step at 256x256 (float64 iterate, each step timed alone)
+    big = workloads.C2
+    xt2, e2 = workloads.tomo_inputs_2d(big)
+    b2 = make_b(sl, big, xt2, e2)
+    cost = {}
+    for name, solver in methods.items():
+        c = sl.Slim(big.N, big.n_views, big.det, big.ell, 0, 1e3, big.seed, solver=solver,
+                    olbfgs_memory=memory, use_graph=solver != sl.SLIM_SOLVE_OLBFGS)
+        c.set_data(b2)
+        per, _, _, _ = timed_steps(c, K, W, flush, stream)
+        c.close()
+        cost[name] = {"ms_per_step": sum(per) / K, "rows_per_s": big.ell * K / (sum(per) * 1e-3)}
+    out["step_cost_256"] = cost
+    return out
+
+
+def _sensitivity_sweep(sl, cfg, methods, reps, memory):
+    """The error after one epoch for every method and step size (see
+    sensitivity_block)."""
+    import torch
     x_true, e = workloads.tomo_inputs_2d(cfg)
     b = make_b(sl, cfg, x_true, e)
     xt = torch.tensor(x_true, dtype=torch.float64, device="cuda")
     n_true = float(torch.linalg.norm(xt))
     alphas = [10.0 ** p for p in range(-5, 4)]
-    methods = {"slimls_r0": sl.SLIM_SOLVE_FP64, "sg": sl.SLIM_SOLVE_SG,
-               "olbfgs": sl.SLIM_SOLVE_OLBFGS}
-    out = {"workload": f"{cfg.name}: one epoch ({cfg.n_views} view blocks), r = 0, "
-                       "error to the phantom", "reps": reps, "alpha": alphas,
-           "olbfgs_memory": memory}
+    out = {"alpha": alphas}
     xb = torch.empty(cfg.n, dtype=torch.float64, device="cuda")
     for name, solver in methods.items():
         rows = []
@@ -506,19 +528,6 @@ def sensitivity_block(sl, flush, stream, reps=5, K=30, W=3, memory=10):
             rows.append({"alpha": alpha, "median": fin(q[1]), "p5": fin(q[0]), "p95": fin(q[2]),
                          "diverged": int(sum(not np.isfinite(v) for v in errs))})
         out[name] = rows
-    # device time of one step at 256x256 (float64 iterate, each step timed alone)
-    big = workloads.C2
-    xt2, e2 = workloads.tomo_inputs_2d(big)
-    b2 = make_b(sl, big, xt2, e2)
-    cost = {}
-    for name, solver in methods.items():
-        c = sl.Slim(big.N, big.n_views, big.det, big.ell, 0, 1e3, big.seed, solver=solver,
-                    olbfgs_memory=memory, use_graph=solver != sl.SLIM_SOLVE_OLBFGS)
-        c.set_data(b2)
-        per, _, _, _ = timed_steps(c, K, W, flush, stream)
-        c.close()
-        cost[name] = {"ms_per_step": sum(per) / K, "rows_per_s": big.ell * K / (sum(per) * 1e-3)}
-    out["step_cost_256"] = cost
     return out
 
 
@@ -1013,7 +1022,7 @@ def main_sens(args):
     torch.cuda.set_stream(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     print(json.dumps({"step_size_sensitivity": sensitivity_block(sl, flush, stream,
-                                                                 reps=max(1, args.sens_reps))}))
+                                                                 reps=max(0, args.sens_reps))}))
 
 
 def main_frames(args):
@@ -1086,7 +1095,8 @@ def main():
     ap.add_argument("--tik-steps", type=int, default=30,
                     help="steps of slimTik and slimLS timed side by side (0: skip)")
     ap.add_argument("--sens-reps", type=int, default=5,
-                    help="block sequences per step size in the sensitivity sweep (0: skip)")
+                    help="block sequences per step size in the sensitivity sweep (0: skip; with "
+                         "--sens-only, 0 times only the step costs)")
     ap.add_argument("--sens-only", action="store_true",
                     help="run only the step-size sensitivity sweep and print that line")
     ap.add_argument("--frames-steps", type=int, default=5,
