@@ -1007,10 +1007,6 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     delete c;
     return SLIM_ENOTSUP;
   }
-  if (c->general3d && gram_frames_smem(c->ell) > 200 * 1024) {
-    delete c;
-    return SLIM_ENOTSUP;
-  }
   if (c->general3d) {
     c->h_frames.resize(c->n_views);
     for (int a = 0; a < c->n_views; ++a) c->h_frames[a] = make_frame_geom(geom->frames + 9 * (size_t)a);

@@ -114,44 +114,54 @@ __global__ void __launch_bounds__(kCta) forward_frames_kernel(RayArgs a, FrameAr
 }
 
 // One warp per ring row q: walk q's taps through the new block's voxel lists
-// into a per-warp accumulator of ell doubles, then write row block and column
-// block `slot` of G.  A list longer than any block can make (4 ell entries at
-// one voxel) is cut and reported (SLIM_EINVAL).
+// and add each product into G[q][slot block] (float64 atomics in L2).  Without a per-warp accumulator in shared memory
+// the kernel runs at full occupancy, which its chains of dependent loads
+// (tap, list head, list entries) need.  A list longer than any block can make
+// (4 ell entries at one voxel) is cut and reported (SLIM_EINVAL).
 __global__ void __launch_bounds__(kCta) gram_frames_kernel(RayArgs a, FrameArgs f) {
-  extern __shared__ double acc_all[];   // kWarps * ell
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int q0 = blockIdx.x * kWarps;
-  const int q = q0 + wib;
-  double* acc = acc_all + (size_t)wib * a.ell;
-  for (int i = lane; i < a.ell; i += 32) acc[i] = 0.0;
-  __syncwarp();
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (q >= a.p || a.ring_ids[q] < 0) return;
   const int base = a.info->slot * a.ell;
   const double* nw = a.ring_w + (size_t)base * a.taps;   // weight of entry e of the new block
+  double* grow = a.G + (size_t)q * a.P + base;
+  // this warp is the only writer of its row's block: clear it, then add
+  for (int i = lane; i < a.ell; i += 32) grow[i] = 0.0;
+  __syncwarp();
   const int max_hops = 4 * a.ell;
-  if (q < a.p && a.ring_ids[q] >= 0) {
-    const int* rp = a.ring_pix + (size_t)q * a.taps;
-    const double* rw = a.ring_w + (size_t)q * a.taps;
-    for (int t = lane; t < a.taps; t += 32) {
-      const int vox = rp[t];
-      if (vox < 0) continue;
-      const double wq = rw[t];
-      int hops = 0;
-      for (int e = f.vhead[vox]; e >= 0; e = f.vnext[e]) {
-        if (++hops > max_hops) {
-          set_status(a.status, SLIM_EINVAL);
-          break;
-        }
-        atomicAdd(&acc[e / a.taps], wq * nw[e]);
+  const int* rp = a.ring_pix + (size_t)q * a.taps;
+  const double* rw = a.ring_w + (size_t)q * a.taps;
+  for (int t = lane; t < a.taps; t += 32) {
+    const int vox = rp[t];
+    if (vox < 0) continue;
+    const double wq = rw[t];
+    int hops = 0;
+    for (int e = f.vhead[vox]; e >= 0; e = f.vnext[e]) {
+      if (++hops > max_hops) {
+        set_status(a.status, SLIM_EINVAL);
+        break;
       }
+      atomicAdd(grow + e / a.taps, wq * nw[e]);
     }
   }
+}
+
+// G[slot block][q] = G[q][slot block] for the ring rows q outside the new
+// block (whose rows hold both halves already): 32 x 32 tiles through shared
+// memory, reads and writes coalesced.
+__global__ void __launch_bounds__(kCta) gram_frames_mirror_kernel(RayArgs a) {
+  __shared__ double tile[32][33];
+  const int base = a.info->slot * a.ell;
+  const int i0 = blockIdx.x * 32, q0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  for (int r = ty; r < 32; r += 8) {
+    const int q = q0 + r, i = i0 + tx;
+    tile[r][tx] = (q < a.p && i < a.ell) ? a.G[(size_t)q * a.P + base + i] : 0.0;
+  }
   __syncthreads();
-  const int nq = min(kWarps, a.p - q0);
-  if (q < a.p)
-    for (int i = lane; i < a.ell; i += 32) a.G[(size_t)q * a.P + base + i] = acc[i];
-  for (int idx = threadIdx.x; idx < a.ell * kWarps; idx += blockDim.x) {
-    const int i = idx / kWarps, wq = idx % kWarps;
-    if (wq < nq) a.G[(size_t)(base + i) * a.P + q0 + wq] = acc_all[(size_t)wq * a.ell + i];
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + r, q = q0 + tx;
+    if (i < a.ell && q < a.p && (q < base || q >= base + a.ell))
+      a.G[(size_t)(base + i) * a.P + q] = tile[tx][r];
   }
 }
 
@@ -213,16 +223,11 @@ cudaError_t launch_forward_frames(const RayArgs& a, const FrameArgs& f, const T*
   return cudaGetLastError();
 }
 
-size_t gram_frames_smem(int ell) { return (size_t)kWarps * ell * sizeof(double); }
-
 cudaError_t launch_gram_frames(const RayArgs& a, const FrameArgs& f, cudaStream_t s) {
-  const size_t smem = gram_frames_smem(a.ell);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(gram_frames_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  gram_frames_kernel<<<cdiv(a.p, kWarps), kCta, smem, s>>>(a, f);
+  gram_frames_kernel<<<cdiv(a.p, kWarps), kCta, 0, s>>>(a, f);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gram_frames_mirror_kernel<<<dim3(cdiv(a.ell, 32), cdiv(a.p, 32)), kCta, 0, s>>>(a);
   return cudaGetLastError();
 }
 

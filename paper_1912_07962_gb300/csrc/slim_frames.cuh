@@ -40,10 +40,8 @@ struct FrameArgs {
 // voxel.  The scatter clears the lists' heads afterwards (vhead as its map).
 template <typename T> cudaError_t launch_forward_frames(const RayArgs& a, const FrameArgs& f,
                                                         const T* x, const T* b, cudaStream_t s);
-// G[q][new] and G[new][q] for every ring row q through the voxel lists
-// (shared memory: 8 * ell doubles per CTA).
+// G[q][new] and G[new][q] for every ring row q through the voxel lists.
 cudaError_t launch_gram_frames(const RayArgs& a, const FrameArgs& f, cudaStream_t s);
-size_t gram_frames_smem(int ell);
 // y[i] = A_{ids[i]} x (ids null: ray i) and x += A_ids^T y.
 template <typename T> cudaError_t launch_project_frames(const FrameGeom* frames, int N, int Du,
                                                         int Dv, const int* ids, long long count,
