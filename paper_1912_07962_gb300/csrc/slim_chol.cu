@@ -1328,10 +1328,15 @@ size_t solve_cluster_smem(int P, int Tt) {
   return 2 * (size_t)P * sizeof(T) + 2 * (size_t)Tt * sizeof(uint64_t);   // Tt >= super-rows
 }
 
-// Largest cluster (16, else 8) that fits the solve, or 0 when none does.
+// Largest cluster (16, else 8) that fits the solve, or 0 when none does, or
+// when the lower triangle of L is over half of L2 (64 MB): the cluster's 16
+// SMs then stream L from DRAM at a fraction of its bandwidth, while the
+// chained solve (a CTA per tile row across the GPU) folds with all SMs.
 template <typename T, int NB>
 int pick_solve_cluster(int P, int Tt) {
   constexpr int kMaxSmem = 200 * 1024;   // allowance set once for every plan
+  constexpr size_t kMaxTriangle = 64u << 20;
+  if ((size_t)P * P / 2 * sizeof(T) > kMaxTriangle) return 0;
   const size_t smem = solve_cluster_smem<T>(P, Tt);
   if (smem > (size_t)kMaxSmem) return 0;
   auto kern = chol_solve_cluster_kernel<T, NB>;
