@@ -119,3 +119,31 @@ def step_lsqr(x_prev, blocks, b_new, lam_k: float, max_iter: int, tol: float = 0
     res = lsqr_damped(lambda v: M @ v, lambda u: M.T @ u, c, M.shape[1], math.sqrt(lam_k),
                       max_iter, tol)
     return x_prev - eta * res.s, r_k, res
+
+
+def step_tik_lsqr(x_prev, blocks, b_new, lam_k: float, lam_tik: float, n_blocks: int, count: int,
+                  cdiag=None, max_iter: int = 1000, tol: float = 0.0, eta: float = 1.0):
+    """One slimTik step (Eq. slimTik, C_k = diag(c), c = None: I) by LSQR.
+
+    With W = C^{-1}, beta = lam_tik^2 / M and mu = lambda_k + count beta, the
+    step s solves (mu C + M^T M) s = M^T c0 + beta C x (c0 = [0; ...; r_k]),
+    i.e. s = (beta/mu) x + W^{1/2} y with
+        y = argmin || M W^{1/2} y - (c0 - (beta/mu) M x) ||^2 + mu ||y||^2
+    (substitute s = (beta/mu) x + W^{1/2} y in the normal equations), which is
+    LSQR for damped least squares on the column-scaled window, damping
+    sqrt(mu).  Returns (x_k, r_k, LsqrResult of y)."""
+    import scipy.sparse as sp
+    M = sp.vstack([sp.csr_matrix(B) for B in blocks], format="csr")
+    A_k = sp.csr_matrix(blocks[-1])
+    ell, p, n = A_k.shape[0], M.shape[0], M.shape[1]
+    wh = np.ones(n) if cdiag is None else 1.0 / np.sqrt(np.asarray(cdiag, dtype=np.float64))
+    beta = lam_tik * lam_tik / n_blocks
+    mu = lam_k + count * beta
+    r_k = A_k @ x_prev - b_new
+    c = np.zeros(p)
+    c[p - ell:] = r_k
+    c = c - (beta / mu) * (M @ x_prev)
+    MW = M @ sp.diags(wh)
+    res = lsqr_damped(lambda v: MW @ v, lambda u: MW.T @ u, c, n, math.sqrt(mu), max_iter, tol)
+    s = (beta / mu) * x_prev + wh * res.s
+    return x_prev - eta * s, r_k, res

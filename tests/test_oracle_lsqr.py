@@ -152,3 +152,29 @@ def test_planted_mutations_break_the_pins():
     assert run("none") < 1e-9
     assert run("theta_sign") > 1e-3
     assert run("no_damping") > 1e-3
+
+
+def test_tik_lsqr_converges_to_the_slimtik_step():
+    # the column-scaled damped problem of step_tik_lsqr, solved to 1e-13, is
+    # the slimTik step (Woodbury form of the slimTik oracle, itself pinned to
+    # the direct form of Eq. slimTik)
+    from oracle import tik
+    N, V, D = 14, 10, 21
+    g = joseph.Geometry(N, V, D)
+    A = joseph.full_matrix(g)
+    b = workloads.add_noise(A @ workloads.phantom_2d(N, 5, 4), workloads.noise_direction(g.m, 5),
+                            0.01)
+    src = slim.tomo_source(g, b)
+    cdiag = 0.5 + 1.5 * np.random.default_rng(3).random(g.n)
+    x = np.random.default_rng(4).standard_normal(g.n) * 0.1
+    blocks = [src.rows(slim.view_block_ids(g, 5, k)) for k in (1, 2, 3)]
+    b_new = src.rhs(slim.view_block_ids(g, 5, 3))
+    for lam_tik, cd in ((0.8, cdiag), (0.0, cdiag), (0.6, None)):
+        xw, *_ = tik.step_woodbury(x, blocks, b_new, 5e-2, lam_tik, V, 3,
+                                   None if cd is None else np.sqrt(cd))
+        xl, _, res = lsqr.step_tik_lsqr(x, blocks, b_new, 5e-2, lam_tik, V, 3, cd, 5000, 1e-13)
+        assert np.linalg.norm(xl - xw) <= 1e-9 * np.linalg.norm(xw), lam_tik
+    # C = I and no Tikhonov rows: the plain LSQR step
+    xl, _, _ = lsqr.step_tik_lsqr(x, blocks, b_new, 5e-2, 0.0, V, 3, None, 7)
+    xp, _, _ = lsqr.step_lsqr(x, blocks, b_new, 5e-2, 7)
+    assert np.linalg.norm(xl - xp) <= 1e-12 * np.linalg.norm(xp)   # scaling by diag(1) reorders sums
