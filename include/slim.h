@@ -139,7 +139,10 @@ typedef struct {
  *                 Eq. (slimLSstep) by LSQR for damped least squares (Sec. 4.2),
  *                 matrix-free over the window's stored taps, float64 vectors;
  *                 2D view blocks, rows from the projector, lookahead 0 only
- *                 (SLIM_ENOTSUP otherwise), never captured in a graph
+ *                 (SLIM_ENOTSUP otherwise), never captured in a graph.  With
+ *                 C_k = diag(c) and/or tik_lambda it runs on the columns
+ *                 scaled by c^{-1/2} with damping sqrt(mu_k) and right-hand
+ *                 side c - (beta/mu_k) M_k x (the same step)
  *                 SLIM_SOLVE_SG: the comparator sg of Sec. 2, B_k = alpha_k I in
  *                 Eq. (ram): x_k = x_{k-1} - eta alpha_k A_k^T r_k with the step
  *                 size alpha_k = 1/lambda_k (lambda_k from the damping schedule)
@@ -183,7 +186,7 @@ typedef struct {
  *                         (A_k^T (A_k x_{k-1} - b_k) + beta C x_{k-1}),
  *                   beta = tik_lambda^2 / A_v,  mu_k = lambda_k + c_k beta.
  *                 0 = plain slimLS.  2D view blocks, Woodbury form (FP64 or
- *                 MIXED solver; SLIM_ENOTSUP otherwise), with or without
+ *                 MIXED solver) or LSQR (SLIM_ENOTSUP otherwise), with or without
  *                 lookahead (mu_k I + M_k C^{-1} M_k^T depends only on the
  *                 blocks drawn)
  *   decay_after   0: lambda_k as above.  K > 0: the decaying damping of Sec. 3
@@ -248,7 +251,7 @@ slim_status slim_set_x(slim_ctx* ctx, const void* x, size_t n, int dtype, int on
  * terms when tik_lambda > 0), computed as (mu_k I + M_k C^{-1} M_k^T) z = rhs,
  * x_k = (1 - eta beta/mu_k) x_{k-1} - eta C^{-1} M_k^T z.  The memory of the
  * steps taken so far is rebuilt with the new C (with lookahead, the steps
- * prepared ahead are prepared again).  2D view blocks, Woodbury form
+ * prepared ahead are prepared again).  2D view blocks, Woodbury or LSQR form
  * (SLIM_ENOTSUP otherwise); SLIM_EINVAL if a value is not positive.
  * Synchronises. */
 slim_status slim_set_c_diag(slim_ctx* ctx, const void* c, size_t n, int dtype, int on_device);

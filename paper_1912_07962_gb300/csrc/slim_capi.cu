@@ -59,6 +59,7 @@ struct slim_ctx {
   double tik_lambda = 0.0;         // slimTik: lam_tik of Eq. (TLS1) (0: slimLS)
   int tik_reading = 0;             // count of Tikhonov rows: 0 blocks of M_k, 1 r
   double* d_cinv = nullptr;        // [n] 1/c of C_k = diag(c); null: C_k = I
+  double* d_cinvh = nullptr;       // [n] c^{-1/2} (the LSQR form's column scaling)
   // 3D with random view directions (frames given): general Joseph rows, Gram
   // from voxel lists, the tiled dense solve
   bool general3d = false;
@@ -290,7 +291,8 @@ cudaError_t mark(slim_ctx* c, int i) {
 // refinement round (residual, z += dz), scatter).
 int kernels_per_step(const slim_ctx* c) {
   if (c->dim == 3 && !c->general3d) return 6;   // sample, march, collect, slice Gram, slice solve, scatter
-  if (c->solver == SLIM_SOLVE_LSQR) return 3;   // sample, forward + residual, LSQR (with x update)
+  if (c->solver == SLIM_SOLVE_LSQR)   // sample, forward + residual, (slimTik rhs,) LSQR with x update
+    return c->tik_lambda > 0.0 ? 4 : 3;
   if (c->solver == SLIM_SOLVE_SG) return 3;     // sample, forward + residual, scatter
   if (c->solver == SLIM_SOLVE_OLBFGS) return 3; // sample, forward + residual, the olbfgs step
   const int solves = c->solver == SLIM_SOLVE_MIXED ? 1 + c->refine_iters : 1;
@@ -406,6 +408,8 @@ LsqrArgs<T> make_lsqr_args(slim_ctx* c) {
   l.stats = l.part + lsqr_part_count(c->num_sms);
   l.bar = c->d_lsqr_bar;
   l.status = c->d_status;
+  l.wh = c->d_cinvh;
+  l.vs = l.stats + 3;
   return l;
 }
 
@@ -420,6 +424,8 @@ cudaError_t enqueue_step_t(slim_ctx* c) {
     if ((e = launch_sample<T>(a, c->stream)) != cudaSuccess) return e;
     if ((e = mark(c, kPhSample)) != cudaSuccess) return e;
     if ((e = launch_forward_residual<T>(a, c->stream)) != cudaSuccess) return e;
+    // slimTik: c - (beta/mu_k) M_k x_{k-1}
+    if (c->tik_lambda > 0.0 && (e = launch_tik_rhs<T>(a, c->stream)) != cudaSuccess) return e;
     // the residual kernel enters the new block in the pixel map for the Gram
     // update, which LSQR does not run: clear it for the next step
     if ((e = cudaMemsetAsync(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int), c->stream)) !=
@@ -565,7 +571,7 @@ void free_all(slim_ctx* c) {
                   c->d_ring_ids, c->d_ring_pix, c->d_ring_w, c->d_map_ray, c->d_map_w,
                   c->d_G, c->d_L, c->d_rhs, c->d_z, c->d_dz, c->d_res, c->d_ref, c->d_err,
                   c->d_lsqr, c->d_lsqr_bar, c->d_cinv, c->d_olb, c->d_olb_state,
-                  c->d_frames, c->d_vnext};
+                  c->d_frames, c->d_vnext, c->d_cinvh};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   chol_plan_destroy(&c->plan);
@@ -955,7 +961,8 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       return SLIM_EINVAL;
     }
     if (c->tik_lambda > 0.0 && (c->kind != SLIM_BLOCKS_VIEWS || c->dim != 2 ||
-                                (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED))) {
+                                (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED &&
+                                 c->solver != SLIM_SOLVE_LSQR))) {
       delete c;
       return SLIM_ENOTSUP;
     }
@@ -1130,7 +1137,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       chk(cudaMemset(c->d_olb, 0, cnt * sizeof(double)), "memset");
       chk(cudaMemset(c->d_olb_state, 0, (2 + kOlbfgsMaxMem) * sizeof(int)), "memset");
     } else if (c->solver == SLIM_SOLVE_LSQR) {
-      const size_t cnt = (size_t)c->p + 4 * (size_t)c->n + lsqr_part_count(c->num_sms) + 3;
+      const size_t cnt = (size_t)c->p + 5 * (size_t)c->n + lsqr_part_count(c->num_sms) + 3;
       chk(cudaMalloc(&c->d_lsqr, cnt * sizeof(double)), "cudaMalloc");
       chk(cudaMalloc(&c->d_lsqr_bar, 2 * sizeof(unsigned)), "cudaMalloc");
       // tmp (and the rest) start at zero: the solve leaves tmp at zero
@@ -1284,12 +1291,15 @@ slim_status slim_set_c_diag(slim_ctx* c, const void* cdiag, size_t n, int dtype,
   if (!c || (cdiag && ((long long)n != c->n || (dtype != SLIM_F32 && dtype != SLIM_F64))))
     return fail(c, SLIM_EINVAL, "set_c_diag: bad arguments");
   if (c->kind != SLIM_BLOCKS_VIEWS || c->dim != 2 ||
-      (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED))
-    return fail(c, SLIM_ENOTSUP, "set_c_diag: 2D view blocks, Woodbury form");
+      (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED &&
+       c->solver != SLIM_SOLVE_LSQR))
+    return fail(c, SLIM_ENOTSUP, "set_c_diag: 2D view blocks, Woodbury or LSQR form");
   CK(c->lookahead ? la_sync_all(c) : cudaStreamSynchronize(c->stream), "set_c_diag");
   if (!cdiag) {
     if (c->d_cinv) CK(cudaFree(c->d_cinv), "set_c_diag");
+    if (c->d_cinvh) CK(cudaFree(c->d_cinvh), "set_c_diag");
     c->d_cinv = nullptr;
+    c->d_cinvh = nullptr;
   } else {
     // read the values to the host (as float64), check C is positive definite
     std::vector<double> h((size_t)c->n);
@@ -1302,13 +1312,19 @@ slim_status slim_set_c_diag(slim_ctx* c, const void* cdiag, size_t n, int dtype,
                     on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost), "set_c_diag");
       for (size_t i = 0; i < f.size(); ++i) h[i] = f[i];
     }
-    for (double& v : h) {
+    std::vector<double> hh(h.size());
+    for (size_t i = 0; i < h.size(); ++i) {
+      const double v = h[i];
       if (!(v > 0.0) || !std::isfinite(v))
         return fail(c, SLIM_EINVAL, "set_c_diag: C_k must be positive definite (c > 0, finite)");
-      v = 1.0 / v;
+      h[i] = 1.0 / v;
+      hh[i] = 1.0 / std::sqrt(v);
     }
     if (!c->d_cinv) CK(cudaMalloc(&c->d_cinv, h.size() * sizeof(double)), "cudaMalloc");
+    if (!c->d_cinvh) CK(cudaMalloc(&c->d_cinvh, hh.size() * sizeof(double)), "cudaMalloc");
     CK(cudaMemcpy(c->d_cinv, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice),
+       "set_c_diag");
+    CK(cudaMemcpy(c->d_cinvh, hh.data(), hh.size() * sizeof(double), cudaMemcpyHostToDevice),
        "set_c_diag");
   }
   // the captured step and the retained Gram entries used the previous C_k

@@ -119,25 +119,35 @@ __global__ void __launch_bounds__(kLsqrThreads) lsqr_kernel(LsqrArgs<T> a) {
   double beta;
   if (!reduce(acc, &beta)) return;
   beta = sqrt(beta);
-  if (beta == 0.0) {   // c = 0: s = 0, x unchanged
+  // y = 0 (c = 0, or M^T c = 0): x unchanged, or scaled by 1 - eta beta/mu (slimTik)
+  auto finish_zero = [&]() {
+    const double keep = 1.0 - a.eta * a.info->tik_c;
+    if (keep != 1.0)
+      for (long long j = gt; j < a.n; j += nthreads) a.x[j] = (T)(keep * (double)a.x[j]);
     write_stats(0, 0.0, 0.0);
+  };
+  if (beta == 0.0) {
+    finish_zero();
     return;
   }
   // v_raw = M^T c / beta; alpha_1 = ||v_raw||  (scalings by reciprocals
   // computed once: float64 division is slow on this GPU's FP64 pipe)
   acc = 0.0;
   const double inv_beta1 = 1.0 / beta;
+  const double* vg = a.wh ? a.vs : a.v;   // the vector the rows gather: wh v (or v)
   for (long long j = gt; j < a.n; j += nthreads) {
-    const double t = __ldcg(a.tmp + j) * inv_beta1;
+    const double whj = a.wh ? a.wh[j] : 1.0;
+    const double t = whj * __ldcg(a.tmp + j) * inv_beta1;
     a.tmp[j] = 0.0;
     a.v[j] = t;
+    if (a.wh) a.vs[j] = whj * t;
     acc += t * t;
   }
   double alpha;
   if (!reduce(acc, &alpha)) return;
   alpha = sqrt(alpha);
   if (alpha == 0.0) {
-    write_stats(0, 0.0, 0.0);
+    finish_zero();
     return;
   }
   double rho_bar = alpha, phi_bar = beta;
@@ -182,7 +192,7 @@ __global__ void __launch_bounds__(kLsqrThreads) lsqr_kernel(LsqrArgs<T> a) {
           }
 #pragma unroll
           for (int e = 0; e < 4; ++e)   // other SMs wrote v: read around L1
-            if (pix[e] >= 0) mv += wt[e] * __ldcg(a.v + pix[e]);
+            if (pix[e] >= 0) mv += wt[e] * __ldcg(vg + pix[e]);
         }
         mv = warp_sum(mv) * inv_alpha;
       }
@@ -200,10 +210,12 @@ __global__ void __launch_bounds__(kLsqrThreads) lsqr_kernel(LsqrArgs<T> a) {
     acc = 0.0;
     const double inv_beta_n = beta_n > 0.0 ? 1.0 / beta_n : 1.0;
     for (long long j = gt; j < a.n; j += nthreads) {
-      const double mt = __ldcg(a.tmp + j);
+      const double whj = a.wh ? a.wh[j] : 1.0;
+      const double mt = whj * __ldcg(a.tmp + j);
       a.tmp[j] = 0.0;
       const double t = mt * inv_beta_n - beta_n * (a.v[j] * inv_alpha);
       a.v[j] = t;
+      if (a.wh) a.vs[j] = whj * t;
       acc += t * t;
     }
     double alpha_n;
@@ -225,12 +237,15 @@ __global__ void __launch_bounds__(kLsqrThreads) lsqr_kernel(LsqrArgs<T> a) {
     alpha = alpha_n;
     if (a.tol > 0.0 && res <= a.tol * res0) break;
   }
-  // the last iteration's update of s, and x -= eta s
+  // the last iteration's update of s, and x -= eta s (slimTik: x = (1 -
+  // eta beta/mu) x - eta wh s)
   const double cs_last = phi / rho;
+  const double keep = 1.0 - a.eta * a.info->tik_c;
   for (long long j = gt; j < a.n; j += nthreads) {
     const double sj = a.s[j] + cs_last * a.w[j];
     a.s[j] = sj;
-    a.x[j] = (T)((double)a.x[j] - a.eta * sj);
+    const double step = a.wh ? a.wh[j] * sj : sj;
+    a.x[j] = (T)(keep * (double)a.x[j] - a.eta * step);
   }
   write_stats(it, res, res0);
 }

@@ -32,6 +32,12 @@ struct LsqrArgs {
   unsigned* bar;            // [2] grid barrier (count, generation), zero before the first use
   double* stats;            // [3] iterations, ||M^T r - lambda s|| estimate, ||M^T c||
   int* status;
+  // slimTik with C_k = diag(c) (Eq. slimTik): LSQR runs on the window's
+  // columns scaled by wh = c^{-1/2} with damping sqrt(mu_k) (info->lam_k) and
+  // c = [0..r_k..0] - (beta/mu_k) M x; then x = (1 - eta beta/mu_k) x - eta wh s
+  // (info->tik_c = beta/mu_k).  wh null: C = I.
+  const double* wh;         // [n] c^{-1/2}, or null
+  double* vs;               // [n] wh * v (scratch, used when wh is set)
 };
 
 // Cooperative launch of the whole solve and the update of x, one CTA per SM.

@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import workloads
-from oracle import joseph, lsqr as olsqr, slim as oslim
+from oracle import joseph, lsqr as olsqr, slim as oslim, tik as otik
 
 from _common import oracle_memory, rel
 
@@ -192,3 +192,55 @@ def test_unsupported_and_invalid(sl):
     with pytest.raises(sl.SlimError):   # not an LSQR context
         wb.lsqr_info()
     wb.close()
+
+
+def _tik_problem(sl, iters, tol, seed=12, lam_tik=0.8, reading=0):
+    g, b = _problem(seed=seed)
+    src = oslim.tomo_source(g, b)
+    r, lam = 3, 1e-2
+    cdiag = 0.5 + 1.5 * np.random.default_rng(seed).random(g.n)
+    s = _ctx(sl, g, r, lam, seed, iters, tol, tik_lambda=lam_tik, tik_reading=reading)
+    s.set_data(b)
+    s.set_c_diag(cdiag)
+    return g, b, src, r, lam, cdiag, s
+
+
+@pytest.mark.parametrize("iters", [3, 8])
+def test_slimtik_fixed_iterations_match_the_oracle(sl, iters):
+    # slimTik with C_k = diag(c) by LSQR on the column-scaled window
+    g, b, src, r, lam, cdiag, s = _tik_problem(sl, iters, 0.0)
+    lam_tik = 0.8
+    x_prev = np.random.default_rng(2).standard_normal(g.n) * 0.05
+    for k in range(1, 7):
+        mem = oracle_memory(g, 12, k, r)
+        blocks = [src.rows(ids) for _, _, ids in mem]
+        xo, _, res = olsqr.step_tik_lsqr(x_prev, blocks, src.rhs(mem[-1][2]),
+                                         oslim.damping(lam, k, r, False), lam_tik, g.n_views,
+                                         otik.window_count(k, r), cdiag, iters)
+        s.set_x(x_prev)
+        s.set_iter(k - 1)
+        s.step(1)
+        assert rel(s.get_x(), xo) < 1e-11, (iters, k)
+        assert s.lsqr_info()[0] == res.iters
+        x_prev = xo
+    s.close()
+
+
+def test_slimtik_converged_is_the_woodbury_step(sl):
+    g, b, src, r, lam, cdiag, s = _tik_problem(sl, 20000, 1e-10, seed=13, lam_tik=1.1)
+    x_prev = np.zeros(g.n)
+    for k in range(1, 6):
+        mem = oracle_memory(g, 13, k, r)
+        blocks = [src.rows(ids) for _, _, ids in mem]
+        xw, *_ = otik.step_woodbury(x_prev, blocks, src.rhs(mem[-1][2]),
+                                    oslim.damping(lam, k, r, False), 1.1, g.n_views,
+                                    otik.window_count(k, r), np.sqrt(cdiag))
+        s.set_x(x_prev)
+        s.set_iter(k - 1)
+        s.step(1)
+        assert rel(s.get_x() - x_prev, xw - x_prev) < 1e-6, k
+        x_prev = xw
+    s.set_timing(True)
+    s.step(1)
+    assert s.get_timing()[1] == 4     # sample, march, slimTik right-hand side, LSQR
+    s.close()

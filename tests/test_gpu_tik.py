@@ -250,9 +250,6 @@ def test_unsupported_and_invalid(sl):
         sl.Slim(g.N, g.n_views, g.det_u, g.det_u, 2, 1e-2, 1, tik_lambda=1.0, tik_reading=2)
     with pytest.raises(sl.SlimError):   # random-ray blocks
         sl.Slim(g.N, g.n_views, g.det_u, 20, 2, 1e-2, 1, tik_lambda=1.0, kind=sl.SLIM_BLOCKS_RAYS)
-    with pytest.raises(sl.SlimError):   # LSQR form
-        sl.Slim(g.N, g.n_views, g.det_u, g.det_u, 2, 1e-2, 1, tik_lambda=1.0,
-                solver=sl.SLIM_SOLVE_LSQR, lsqr_max_iter=10)
     s = sl.Slim(g.N, g.n_views, g.det_u, g.det_u, 2, 1e-2, 1, tik_lambda=1.0)
     s.set_data(b)
     bad = np.ones(g.n)
@@ -262,8 +259,7 @@ def test_unsupported_and_invalid(sl):
     with pytest.raises(sl.SlimError):   # wrong length
         s.set_c_diag(np.ones(g.n - 1))
     s.close()
-    ls = sl.Slim(g.N, g.n_views, g.det_u, g.det_u, 2, 1e-2, 1, solver=sl.SLIM_SOLVE_LSQR,
-                 lsqr_max_iter=10)
-    with pytest.raises(sl.SlimError):   # the LSQR form takes C = I only
-        ls.set_c_diag(np.ones(g.n))
-    ls.close()
+    sg = sl.Slim(g.N, g.n_views, g.det_u, g.det_u, 0, 10.0, 1, solver=sl.SLIM_SOLVE_SG)
+    with pytest.raises(sl.SlimError):   # the comparators take C = I only
+        sg.set_c_diag(np.ones(g.n))
+    sg.close()
