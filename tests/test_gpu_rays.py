@@ -114,3 +114,24 @@ def test_streaming_3d_full_size_first_steps(sl):
         x, _, _, _ = oslim.step_woodbury(x, [src.rows(i) for i in mem], src.rhs(mem[-1]), cfg.lam)
         s.step(1)
         assert rel(s.get_x(), x) < 1e-11, k
+
+
+def test_random_rays_2d_decaying_damping(sl):
+    # the 1/k decay of the damping after step K, drawn by the random-ray sampler
+    from oracle import comparators as cmp
+    N, V, D, ell, r, lam, seed, K = 24, 18, 35, 20, 2, 3e-2, 10, 3
+    g = joseph.Geometry(N, V, D)
+    A = joseph.full_matrix(g)
+    b = workloads.add_noise(A @ workloads.phantom_2d(N, seed, 5), workloads.noise_direction(g.m, seed), 0.01)
+    src = oslim.tomo_source(g, b)
+    steps = 8
+    sched = list(oslim.random_ray_schedule(seed, ell, g.m, steps))
+    x = np.zeros(g.n)
+    for k in range(1, steps + 1):
+        blocks = [src.rows(sched[j - 1]) for j in range(max(1, k - r), k + 1)]
+        x, *_ = oslim.step_woodbury(x, blocks, src.rhs(sched[k - 1]), cmp.damping(lam, k, r, False, K))
+    s = sl.Slim(N, V, D, ell, r, lam, seed, kind=sl.SLIM_BLOCKS_RAYS, decay_after=K)
+    s.set_data(b)
+    s.step(steps)
+    assert rel(s.get_x(), x) < 1e-12
+    s.close()
