@@ -5,7 +5,7 @@ optimiser.  Nothing outside tests/, the smoke check and the bench's CPU leg
 imports this module.
 
 The paper starts its iterations from x_0 = 0 (Sec. 4); a learned x_0 is an
-extension of this build, not a method of the paper.  Architecture:
+extension beyond the paper, not one of its methods.  Architecture:
   encoder  three levels of [conv3x3 + ReLU, conv3x3 + ReLU] with 32, 64, 128
            channels, each followed by a 2x2 max-pool;
   bottom   [conv3x3 + ReLU] x 2 with 256 channels;
