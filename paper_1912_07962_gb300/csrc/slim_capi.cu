@@ -2085,6 +2085,21 @@ extern "C" slim_status slim_batch_create(int count, const slim_geometry* geoms,
     return SLIM_ECUDA;
   }
   b->own_stream = true;
+  // Share the GPU between the problems' factorisations: each problem gets
+  // persistent CTAs in proportion to its factorisation work (p^3) out of two
+  // per SM, instead of CTAs on every SM for each (any grid is correct: tasks
+  // are claimed by ticket).
+  double work = 0.0;
+  for (slim_ctx* c : b->ctx)
+    if (c->plan.grid > 0) work += (double)c->p * c->p * c->p;
+  if (work > 0.0 && b->ctx.size() > 1) {
+    const double slots = 2.0 * b->ctx[0]->num_sms;
+    for (slim_ctx* c : b->ctx)
+      if (c->plan.grid > 0) {
+        const int g = (int)std::lround(slots * (double)c->p * c->p * c->p / work);
+        c->plan.grid = std::max(2, std::min(c->plan.grid, g));
+      }
+  }
   *out = b;
   return SLIM_OK;
 }
