@@ -306,7 +306,8 @@ int kernels_per_step(const slim_ctx* c) {
   }
   const int per_solve = c->plan.cluster ? 1 : 2;
   const int tik = c->tik_lambda > 0.0 ? 2 : 0;   // window projection, x scale
-  return 5 + per_solve * solves + refine + 1 + tik;
+  const int mirror = c->general3d ? 1 : 0;       // the Gram's mirrored block
+  return 5 + per_solve * solves + refine + 1 + tik + mirror;
 }
 
 // The damped solve (lambda_k I + G) z = rhs: float64 tiled Cholesky, or a
