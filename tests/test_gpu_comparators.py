@@ -162,3 +162,15 @@ def test_kernels_and_arguments(sl):
                 olbfgs_memory=21)
     with pytest.raises(sl.SlimError):       # negative decay start
         sl.Slim(g.N, g.n_views, g.det_u, g.det_u, 2, 1e-2, 1, decay_after=-1)
+
+
+def test_olbfgs_memory_one_and_step_factor(sl):
+    g, b = _problem(seed=14)
+    lam, seed, eta = 25.0, 14, 0.5
+    xs = _oracle(g, b, seed, 10, lam, "olbfgs", memory=1, eta=eta)
+    s = sl.Slim(g.N, g.n_views, g.det_u, g.det_u, 0, lam, seed, solver=sl.SLIM_SOLVE_OLBFGS,
+                olbfgs_memory=1, eta=eta)
+    s.set_data(b)
+    s.step(10)
+    assert rel(s.get_x(), xs[-1]) < 1e-10
+    s.close()

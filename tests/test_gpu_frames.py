@@ -150,3 +150,22 @@ def test_arguments(sl):
     s.step(1)
     assert s.get_timing()[1] >= 6         # sample, march, Gram, K, factor, solves, scatter
     s.close()
+
+
+def test_rays_missing_the_volume(sl):
+    # a detector much wider than the volume's shadow: many rays cross no voxel
+    # (zero rows of A, zero Gram rows and columns)
+    N = 8
+    fr = workloads.random_frames(6, 7)
+    g = joseph.Geometry(N, 6, 30, 28, dim=3, frames=fr)
+    A, b = _data(g, 7)
+    empty = np.diff(A.indptr) == 0
+    assert empty.mean() > 0.3
+    ell, r, lam, seed, steps = 40, 2, 1e-2, 7, 8
+    sched = list(oslim.random_ray_schedule(seed, ell, g.m, steps))
+    traj = [x for _, x, _ in oslim.run(oslim.tomo_source(g, b), sched, r, lam)]
+    s = _ctx(sl, g, fr, ell, r, lam, seed)
+    s.set_data(b)
+    s.step(steps)
+    assert rel(s.get_x(), traj[-1]) < 1e-12
+    s.close()

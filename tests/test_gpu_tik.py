@@ -263,3 +263,26 @@ def test_unsupported_and_invalid(sl):
     with pytest.raises(sl.SlimError):   # the comparators take C = I only
         sg.set_c_diag(np.ones(g.n))
     sg.close()
+
+
+def test_checkpoint_and_restore(sl):
+    # a context restored from a checkpoint (x, k) with the same options and C
+    # continues the trajectory (the memory is rebuilt with C)
+    g, b = _problem(seed=16)
+    r, lam, lam_tik, seed = 2, 1e-2, 0.7, 16
+    c = _cdiag(g.n, 17)
+    a = sl.Slim(g.N, g.n_views, g.det_u, g.det_u, r, lam, seed, tik_lambda=lam_tik)
+    a.set_data(b)
+    a.set_c_diag(c)
+    a.step(5)
+    blob = a.checkpoint()
+    a.step(4)
+    want = a.get_x()
+    a.close()
+    d = sl.Slim(g.N, g.n_views, g.det_u, g.det_u, r, lam, seed, tik_lambda=lam_tik)
+    d.set_data(b)
+    d.set_c_diag(c)
+    d.restore(blob)
+    d.step(4)
+    assert rel(d.get_x(), want) < 1e-12
+    d.close()
