@@ -826,6 +826,25 @@ def e2e_block(sl, cfg, b, K, W, lookahead=0, ctas_per_sm=0):
                      "stepping and copying x out (synchronous), no L2 flush between steps")}
 
 
+def replica_seed(base: int, rank: int) -> int:
+    """Seed of rank `rank`'s replica: independent problems of the same workload."""
+    return base + 1000 * rank
+
+
+def job_throughput(local_seconds: float, units_per_rank: float, world: int, device="cpu"):
+    """Whole-job throughput of `world` replicas: the units all ranks processed
+    over the slowest rank's time (max over ranks by all-reduce when world > 1).
+    Returns (units per second, the max time)."""
+    t = float(local_seconds)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt)
+    return units_per_rank * world / t, t
+
+
 def main_gpu(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -840,7 +859,7 @@ def main_gpu(args):
     from paper_1912_07962_gb300 import slim as sl
 
     cfg, desc = workload_of(args.workload)
-    seed = cfg.seed + 1000 * rank      # independent replicas
+    seed = replica_seed(cfg.seed, rank)      # independent replicas
     x_true = workloads.phantom_2d(cfg.N, seed, cfg.n_ellipses)
     e = workloads.noise_direction(cfg.m, seed)
     b = make_b(sl, cfg, x_true, e)
@@ -876,13 +895,8 @@ def main_gpu(args):
         _, ph_c, _, _ = timed_steps(sc, 5, 0, flush, stream)
         ph_c = {k: v * args.steps / 5 for k, v in ph_c.items()}
     sc.close()
-    t_c = sum(per_c) * 1e-3
     t_p = sum(per_p) * 1e-3
-    if world > 1:
-        tt = torch.tensor([t_c], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_c = float(tt)
-    rows_c = cfg.ell * args.steps * world / t_c
+    rows_c, t_c = job_throughput(sum(per_c) * 1e-3, cfg.ell * args.steps, world, device="cuda")
     rows_p = cfg.ell * args.plain_steps / t_p
 
     if launch_log:
