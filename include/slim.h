@@ -256,6 +256,14 @@ slim_status slim_set_x(slim_ctx* ctx, const void* x, size_t n, int dtype, int on
  * Synchronises. */
 slim_status slim_set_c_diag(slim_ctx* ctx, const void* c, size_t n, int dtype, int on_device);
 
+/* Failure detection self-test: runs a grid barrier (the bounded wait of the
+ * cooperative solvers) that one of its two CTAs never reaches, on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream), and
+ * returns the status the waiting CTA recorded when its poll limit ran out
+ * (about a second): SLIM_ETIMEOUT is the expected outcome.  The kernel ends
+ * either way and the device stays usable.  Synchronises the stream. */
+slim_status slim_selftest_wait(void* cuda_stream);
+
 /* Copy the current iterate into the caller's buffer (synchronises; returns
  * any device-side error recorded since the last synchronising call). */
 slim_status slim_get_x(slim_ctx* ctx, void* x, size_t n, int dtype, int on_device);

@@ -37,6 +37,7 @@ EXPORTS = [
     "slim_unet_get_params", "slim_unet_get_grads", "slim_unet_forward", "slim_unet_train_step",
     "slim_warm_start", "slim_backproject_data", "slim_unet_conv3x3", "slim_unet_conv3x3_grad",
     "slim_unet_tconv2x2", "slim_unet_tconv2x2_grad", "slim_get_lsqr_info", "slim_set_c_diag",
+    "slim_selftest_wait",
 ]
 A_MATRIX_FREE, A_CSR_F32, A_CSR_BF16 = 0, 1, 2
 NOALLOC_MAX_P = 1024
@@ -132,6 +133,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "slim_unet_tconv2x2_grad": ([VP, VP, I, I, I, I, VP, I, VP, VP, VP, VP], I),
         "slim_get_lsqr_info": ([VP, P(I), P(D), P(D)], I),
         "slim_set_c_diag": ([VP, VP, C.c_size_t, I, I], I),
+        "slim_selftest_wait": ([VP], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -356,6 +358,11 @@ class Slim:
         cnt = ray_ids.numel() if ray_ids is not None else 0
         self._check(self._lib.slim_backproject(self.h, ids, cnt, C.c_void_p(y.data_ptr()),
                                                C.c_void_p(x.data_ptr())))
+
+
+def selftest_wait(stream_ptr=0):
+    """Status of a bounded device wait made to run out (SLIM_ETIMEOUT expected)."""
+    return load().slim_selftest_wait(C.c_void_p(stream_ptr))
 
 
 def damped_solve(G, lam, rhs, z, stream_ptr=0):
