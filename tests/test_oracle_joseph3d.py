@@ -9,6 +9,9 @@ from directions uniform on the sphere).
 * The reversed direction (-d, same u, v) is the same line: bit-identical taps.
 * A ray through the centre stays inside the volume: its weights sum to
   N / |d_k| (each slice's bilinear weights sum to 1/|d_k|).
+* Exchanging two axes of the frames (d, u, v) and of the volume gives the
+  same rows with the voxel indices exchanged (the march axis and the
+  interpolation axes are bookkept by value, not by position).
 * The frames of the input generator are orthonormal and uniform on the sphere
   in the mean.
 """
@@ -79,3 +82,22 @@ def test_frames_are_orthonormal_and_uniform():
     # uniform on the sphere: mean 0, E[d d^T] = I/3 (4000 samples: 4 sigma bounds)
     assert np.abs(d.mean(axis=0)).max() < 4 * math.sqrt(1 / 3 / 4000)
     assert np.abs(d.T @ d / 4000 - np.eye(3) / 3).max() < 0.03
+
+
+def test_exchanging_two_axes_permutes_the_voxels():
+    N, V, Du, Dv = 7, 8, 11, 10
+    fr = workloads.random_frames(V, 13)
+    for a, b in ((0, 1), (0, 2), (1, 2)):
+        sw = fr.copy()
+        for base in (0, 3, 6):       # exchange components a and b of d, u and v
+            sw[:, [base + a, base + b]] = sw[:, [base + b, base + a]]
+        g1 = joseph.Geometry(N, V, Du, Dv, dim=3, frames=fr)
+        g2 = joseph.Geometry(N, V, Du, Dv, dim=3, frames=sw)
+        # voxel (x, y, z) of g1 is voxel (x, y, z) with coordinates a, b exchanged in g2
+        idx = np.arange(N ** 3)
+        c = np.stack([idx % N, (idx // N) % N, idx // (N * N)])
+        c[[a, b]] = c[[b, a]]
+        perm = (c[2] * N + c[1]) * N + c[0]
+        A1 = joseph.full_matrix(g1).toarray()
+        A2 = joseph.full_matrix(g2).toarray()
+        assert np.abs(A1 - A2[:, perm]).max() <= 1e-14 * np.abs(A1).max(), (a, b)
