@@ -169,3 +169,25 @@ def test_rays_missing_the_volume(sl):
     s.step(steps)
     assert rel(s.get_x(), traj[-1]) < 1e-12
     s.close()
+
+
+def test_projection_at_full_size_on_sampled_rays(sl):
+    # the bench's geometry (256^3, 360 directions, 368 x 368 detector): A x on
+    # 300 sampled rays against the oracle's rows, one by one
+    cfg = workloads.C4R
+    fr = workloads.random_frames(cfg.n_views, cfg.seed)
+    g = joseph.Geometry(cfg.N, cfg.n_views, cfg.det_u, cfg.det_v, dim=3, frames=fr)
+    rng = np.random.default_rng(17)
+    ids = np.sort(rng.choice(g.m, 300, replace=False)).astype(np.int32)
+    x = rng.standard_normal(g.n)
+    s = sl.Slim(cfg.N, cfg.n_views, cfg.det_u, cfg.ell, cfg.r, cfg.lam, cfg.seed, dim=3,
+                det_v=cfg.det_v, kind=sl.SLIM_BLOCKS_STREAM, steps_per_view=46, frames=fr)
+    xt = torch.tensor(x, device="cuda")
+    yt = torch.zeros(len(ids), dtype=torch.float64, device="cuda")
+    s.project(xt, yt, torch.tensor(ids, device="cuda"))
+    got = yt.cpu().numpy()
+    for i, ray in enumerate(ids):
+        idx, w = joseph.ray_taps(g, int(ray))
+        want = float(w @ x[idx])
+        assert abs(got[i] - want) <= 1e-12 * max(1.0, float(np.abs(w).sum())), int(ray)
+    s.close()
