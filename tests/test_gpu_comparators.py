@@ -174,3 +174,20 @@ def test_olbfgs_memory_one_and_step_factor(sl):
     s.step(10)
     assert rel(s.get_x(), xs[-1]) < 1e-10
     s.close()
+
+
+@pytest.mark.parametrize("method", ["sg", "olbfgs"])
+def test_at_256(sl, method):
+    # the 256x256 workload of the bench's step costs, six steps
+    cfg = workloads.C2
+    g = joseph.Geometry(cfg.N, cfg.n_views, cfg.det)
+    x_true, e = workloads.tomo_inputs_2d(cfg)
+    b = workloads.add_noise(joseph.full_matrix(g) @ x_true, e, cfg.noise)
+    lam = 1e3
+    xs = _oracle(g, b, cfg.seed, 6, lam, method, memory=10)
+    s = sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.det, 0, lam, cfg.seed,
+                solver=sl.SLIM_SOLVE_SG if method == "sg" else sl.SLIM_SOLVE_OLBFGS)
+    s.set_data(b)
+    s.step(6)
+    assert rel(s.get_x(), xs[-1]) < 1e-11
+    s.close()
