@@ -136,6 +136,7 @@ def make_b(sl, cfg, x_true, e):
     s = sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.ell, cfg.r, cfg.lam, cfg.seed)
     xt = torch.tensor(x_true, dtype=torch.float64, device="cuda")
     y = torch.zeros(cfg.m, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()   # inputs filled on torch's stream; the context has its own
     s.project(xt, y)
     torch.cuda.synchronize()
     clean = y.cpu().numpy()
@@ -542,6 +543,7 @@ def stream3d_block(sl, flush, stream, K, W, steps_per_view=46):
                 steps_per_view=steps_per_view, use_graph=True)
     xt = torch.tensor(x_true, device="cuda")
     y = torch.zeros(cfg.m, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()   # inputs filled on torch's stream; the context has its own
     s.project(xt, y)
     torch.cuda.synchronize()
     e = torch.tensor(workloads.noise_direction(cfg.m, cfg.seed), dtype=torch.float32, device="cuda")
@@ -600,6 +602,7 @@ def frames3d_block(sl, flush, stream, K, W, r_values=(0, 4), steps_per_view=46):
         if b is None:
             xt = torch.tensor(x_true, device="cuda")
             y = torch.zeros(cfg.m, dtype=torch.float32, device="cuda")
+            torch.cuda.synchronize()   # inputs filled on torch's stream; the context has its own
             s.project(xt, y)
             torch.cuda.synchronize()
             e = torch.tensor(workloads.noise_direction(cfg.m, cfg.seed), dtype=torch.float32,
@@ -641,6 +644,7 @@ def batch_block(sl, flush, stream, K, W, count=96):
         xt = torch.tensor(workloads.phantom_2d(c.N, c.seed, c.n_ellipses), dtype=torch.float32,
                           device="cuda")
         y = torch.zeros(c.m, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()   # inputs filled on torch's stream; the context has its own
         pb.project(xt, y)
         torch.cuda.synchronize()     # y comes from the problem's stream, b is formed on torch's
         e = torch.tensor(workloads.noise_direction(c.m, c.seed), dtype=torch.float32, device="cuda")

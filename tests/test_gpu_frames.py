@@ -56,17 +56,24 @@ def test_projections_match_the_oracle_rows(sl):
     s = _ctx(sl, g, fr, 16, 1, 1e-2, 1)
     xt = torch.tensor(x, device="cuda")
     yt = torch.zeros(g.m, dtype=torch.float64, device="cuda")
-    s.project(xt, yt)
+    torch.cuda.synchronize()   # inputs filled on torch's stream; the projections
+    s.project(xt, yt)          # run on the context's own stream
+    s.sync()
     want = A @ x
     assert np.abs(yt.cpu().numpy() - want).max() <= 1e-13 * np.abs(want).max()
     bt = torch.zeros(g.n, dtype=torch.float64, device="cuda")
-    s.backproject(torch.tensor(y, device="cuda"), bt)
+    yd = torch.tensor(y, device="cuda")
+    torch.cuda.synchronize()
+    s.backproject(yd, bt)
+    s.sync()
     want = A.T @ y
     assert np.abs(bt.cpu().numpy() - want).max() <= 1e-13 * np.abs(want).max()
     # a subset of rays by id
     ids = torch.tensor([0, 5, g.m - 1, 77, 5], dtype=torch.int32, device="cuda")
     ys = torch.zeros(5, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
     s.project(xt, ys, ids)
+    s.sync()
     assert np.abs(ys.cpu().numpy() - (A @ x)[[0, 5, g.m - 1, 77, 5]]).max() <= 1e-13 * np.abs(
         A @ x).max()
     s.close()
@@ -184,7 +191,10 @@ def test_projection_at_full_size_on_sampled_rays(sl):
                 det_v=cfg.det_v, kind=sl.SLIM_BLOCKS_STREAM, steps_per_view=46, frames=fr)
     xt = torch.tensor(x, device="cuda")
     yt = torch.zeros(len(ids), dtype=torch.float64, device="cuda")
-    s.project(xt, yt, torch.tensor(ids, device="cuda"))
+    idt = torch.tensor(ids, device="cuda")
+    torch.cuda.synchronize()   # inputs filled on torch's stream; the projection
+    s.project(xt, yt, idt)     # runs on the context's own stream
+    s.sync()
     got = yt.cpu().numpy()
     for i, ray in enumerate(ids):
         idx, w = joseph.ray_taps(g, int(ray))
