@@ -161,7 +161,19 @@ def _ptr(a):
 
 
 class Slim:
-    """One slimLS problem on the GPU (owns a slim_ctx)."""
+    """One slimLS problem on the GPU (owns a slim_ctx).
+
+    The arguments map onto slim_geometry, slim_blocks and slim_step_opts of
+    include/slim.h, which documents each one.  Beyond the Woodbury step:
+      solver        SLIM_SOLVE_LSQR (the step by LSQR; lsqr_max_iter, lsqr_tol),
+                    SLIM_SOLVE_SG and SLIM_SOLVE_OLBFGS (the comparators, r = 0;
+                    olbfgs_memory), step size alpha_k = 1/lambda_k
+      tik_lambda    slimTik's Tikhonov parameter (0: slimLS); tik_reading 0/1 the
+                    count of Tikhonov rows (blocks of M_k, or r as printed);
+                    C_k = diag(c) through set_c_diag
+      decay_after   the 1/k decay of the damping after that step (0: none)
+      frames        3D views from arbitrary directions: rows (d, u, v) per view
+    """
 
     def __init__(self, N, n_views, det, ell, r, lam, seed, precision=SLIM_PREC_FP64,
                  solver=SLIM_SOLVE_FP64, refine_iters=2, eta=1.0, ramp=False, use_graph=False,
