@@ -112,7 +112,8 @@ typedef struct {
 /* Block sampling (Sec. 1: W_k i.i.d. uniform over M selectors).
  *   kind   SLIM_BLOCKS_VIEWS (2D): one view per block, M = n_views, drawn
  *          uniformly with replacement; ell must equal det_u.  Step k draws view
- *          bounded(draw(seed, 2, k-1), A_v).
+ *          bounded(draw(seed, 2, k-1), A_v) (with `cyclic`, the random cyclic
+ *          order below instead).
  *          SLIM_BLOCKS_RAYS: ell rays, each uniform over all m rays.
  *          SLIM_BLOCKS_STREAM (streaming data, Sec. 4.3): views arrive in angle
  *          order, view v from step steps_per_view*v + 1; each of the ell rays is
@@ -120,12 +121,30 @@ typedef struct {
  *          k is bounded(draw(seed, 3, (k-1)*ell + i), available rays).
  *   ell    rows per block
  *   seed   generator seed
- *   steps_per_view  SLIM_BLOCKS_STREAM only */
+ *   steps_per_view  SLIM_BLOCKS_STREAM only
+ *   with_replacement  1 (every configuration here): draws are independent, so
+ *          a view may recur within an epoch and a ray within a random-ray
+ *          block (Sec. 1's i.i.d. W_k).  0: without replacement -- view
+ *          blocks then follow the random cyclic order (as cyclic = 1), and
+ *          the ell rays of a random-ray block are distinct: Floyd's algorithm
+ *          (Bentley and Floyd 1987) over the available rays, draw i of step k
+ *          bounded(draw(seed, 3, (k-1)*ell + i), n_avail - ell + i + 1), the
+ *          ids in the algorithm's insertion order (ell <= 2048 and ell <= the
+ *          rays of one view for SLIM_BLOCKS_STREAM, of all views for
+ *          SLIM_BLOCKS_RAYS; SLIM_ENOTSUP / SLIM_EINVAL otherwise)
+ *   cyclic SLIM_BLOCKS_VIEWS only (SLIM_ENOTSUP otherwise): 1 = random cyclic
+ *          order (the walnut experiment of Sec. 4.3): epoch e = (k-1) / A_v
+ *          visits every view once, in the order of the Fisher-Yates shuffle
+ *          of 0..A_v-1 whose swap i (i = A_v-1 down to 1) exchanges entries i
+ *          and bounded(draw(seed, 7, e*A_v + A_v-1-i), i+1); step k takes
+ *          entry (k-1) mod A_v.  A_v <= 4096 (SLIM_ENOTSUP otherwise). */
 typedef struct {
   int kind;
   int ell;
   unsigned long long seed;
   int steps_per_view;
+  int with_replacement;
+  int cyclic;
 } slim_blocks;
 
 /* Step options.
@@ -283,6 +302,14 @@ slim_status slim_get_timing(slim_ctx* ctx, double* phase_ms, int nphase, int* ke
 
 /* Wait for queued work and return the device status. */
 slim_status slim_sync(slim_ctx* ctx);
+
+/* Make `cuda_stream` (a cudaStream_t; NULL = the context's stream) wait,
+ * without blocking the host, for all work the context has queued so far on
+ * every stream it uses -- with lookahead, the geometry chains and
+ * factorisations prepared ahead of the iterate included.  Work queued on
+ * cuda_stream afterwards starts once the context is idle.  Used to end a
+ * timed region at the point where the steps' whole pipeline has finished. */
+slim_status slim_join_stream(slim_ctx* ctx, void* cuda_stream);
 
 /* Reference iterate for slim_run's error metric ||x - x_ref|| / ||x_ref||
  * (host or device array of n values).  NULL clears it. */
@@ -472,15 +499,22 @@ slim_status slim_backproject_data(slim_ctx* ctx, float* x);
  * caching allocator), or a latency-critical loop that must not call
  * cudaMalloc/cudaFree, which synchronise the device.
  *
- * Same arguments, arithmetic (float64 tiled Cholesky and triangular solves)
- * and results as slim_damped_solve, for p <= SLIM_NOALLOC_MAX_P; larger p is
- * rejected with SLIM_EINVAL (use slim_damped_solve).  The caller passes G,
- * rhs and z as device arrays.  All scratch lives in one static device array of
- * about 8.7 MB that every GPU which loads the library keeps until the process
- * exits.  The first call on a device resolves that array's address for the
- * current device (a one-time set-up).  Calls share the array: calls that
- * overlap on the GPU (different streams or host threads at the same time)
- * race and give wrong results.  Each call synchronises `cuda_stream`. */
+ * Same arguments as slim_damped_solve and the same computation: the float64
+ * tiled Cholesky with the same task list and grid, then the same
+ * triangular-solve kernels, so the results agree to rounding (the order of
+ * the floating-point sums is the same; only the scheduling of the persistent
+ * factorisation's CTAs varies between runs, as it does for the allocating
+ * solve).  p <= SLIM_NOALLOC_MAX_P; larger p is rejected with SLIM_EINVAL
+ * (use slim_damped_solve).  The caller passes G, rhs and z as device arrays.
+ * All scratch lives in one static device array of about 9 MB that every GPU
+ * which loads the library keeps until the process exits.  The first call on a
+ * device does a one-time set-up with that device current: it resolves the
+ * array's address and copies the factorisation's task lists into it with
+ * synchronous copies, so make that first call before capturing any stream.
+ * Calls share the array and each overwrites what the previous one left
+ * there: calls that overlap on the GPU (different streams or host threads at
+ * the same time) race and give wrong results.  Each call synchronises
+ * `cuda_stream`. */
 slim_status slim_damped_solve_noalloc(const double* G, int p, double lambda, const double* rhs,
                                       double* z, void* cuda_stream);
 

@@ -129,29 +129,36 @@ def run(source: RowSource, blocks: Iterable, r: int, lam: float, x0=None, eta: f
 # --------------------------------------------------------------------------
 # Block schedules (the sampling of W_k, Sec. 1)
 # --------------------------------------------------------------------------
-def view_block_ids(g: joseph.Geometry, seed: int, k: int) -> np.ndarray:
-    """Row ids of the block drawn at step k: one view, uniform with replacement."""
-    return g.view_rays(rng.view_block(seed, k, g.n_views))
+def view_block_ids(g: joseph.Geometry, seed: int, k: int, cyclic: bool = False) -> np.ndarray:
+    """Row ids of the block drawn at step k: one view, uniform with replacement
+    (Sec. 1), or the view of step k in the random cyclic order (Sec. 4.3)."""
+    view = (rng.cyclic_block(seed, k, g.n_views) if cyclic
+            else rng.view_block(seed, k, g.n_views))
+    return g.view_rays(view)
 
 
-def view_schedule(g: joseph.Geometry, seed: int, steps: int, k0: int = 1):
+def view_schedule(g: joseph.Geometry, seed: int, steps: int, k0: int = 1, cyclic: bool = False):
     for k in range(k0, k0 + steps):
-        yield view_block_ids(g, seed, k)
+        yield view_block_ids(g, seed, k, cyclic)
 
 
-def random_ray_schedule(seed: int, ell: int, n_avail: int, steps: int, k0: int = 1):
+def random_ray_schedule(seed: int, ell: int, n_avail: int, steps: int, k0: int = 1,
+                        distinct: bool = False):
+    """Random-ray blocks: ell ids drawn independently, or ell distinct ids (Floyd)."""
+    draw = rng.distinct_rays if distinct else rng.random_rays
     for k in range(k0, k0 + steps):
-        yield np.array(rng.random_rays(seed, k, ell, n_avail), dtype=np.int64)
+        yield np.array(draw(seed, k, ell, n_avail), dtype=np.int64)
 
 
 def streaming_ray_schedule(seed: int, ell: int, n_views: int, rays_per_view: int,
-                           steps_per_view: int, steps: int, k0: int = 1):
+                           steps_per_view: int, steps: int, k0: int = 1, distinct: bool = False):
     """Streaming data (Sec. 4.3, 3D streaming): views arrive in angle order, view v
     from step steps_per_view * v + 1 on; step k draws ell rays uniformly from the
-    views that have arrived."""
+    views that have arrived (independently, or ell distinct ones by Floyd)."""
+    draw = rng.distinct_rays if distinct else rng.random_rays
     for k in range(k0, k0 + steps):
         arrived = min(n_views, (k - 1) // steps_per_view + 1)
-        yield np.array(rng.random_rays(seed, k, ell, arrived * rays_per_view), dtype=np.int64)
+        yield np.array(draw(seed, k, ell, arrived * rays_per_view), dtype=np.int64)
 
 
 def contiguous_block_ids(i: int, ell: int) -> np.ndarray:

@@ -59,6 +59,10 @@ struct slim_ctx {
   double tik_lambda = 0.0;         // slimTik: lam_tik of Eq. (TLS1) (0: slimLS)
   int tik_reading = 0;             // count of Tikhonov rows: 0 blocks of M_k, 1 r
   double* d_cinv = nullptr;        // [n] 1/c of C_k = diag(c); null: C_k = I
+  int cyclic = 0;                  // view blocks in the random cyclic order
+  int distinct = 0;                // random-ray blocks of distinct rays (Floyd)
+  int* d_perm = nullptr;           // [n_views] the current epoch's permutation (cyclic)
+  long long* d_perm_epoch = nullptr;
   double* d_cinvh = nullptr;       // [n] c^{-1/2} (the LSQR form's column scaling)
   // 3D with random view directions (frames given): general Joseph rows, Gram
   // from voxel lists, the tiled dense solve
@@ -233,6 +237,9 @@ StepArgs<T> make_args(slim_ctx* c) {
   a.tik_reading = c->tik_reading;
   a.cinv = c->d_cinv;
   a.sg = c->solver == SLIM_SOLVE_SG;
+  a.cyclic = c->cyclic;
+  a.perm = c->d_perm;
+  a.perm_epoch = c->d_perm_epoch;
   return a;
 }
 
@@ -272,6 +279,7 @@ RayArgs make_ray_args(slim_ctx* c) {
   a.slice_cnt = c->d_slice_cnt;
   a.slice_rows = c->d_slice_rows;
   a.dense = c->dim == 2 || c->general3d;
+  a.distinct = c->distinct;
   return a;
 }
 
@@ -572,7 +580,7 @@ void free_all(slim_ctx* c) {
                   c->d_ring_ids, c->d_ring_pix, c->d_ring_w, c->d_map_ray, c->d_map_w,
                   c->d_G, c->d_L, c->d_rhs, c->d_z, c->d_dz, c->d_res, c->d_ref, c->d_err,
                   c->d_lsqr, c->d_lsqr_bar, c->d_cinv, c->d_olb, c->d_olb_state,
-                  c->d_frames, c->d_vnext, c->d_cinvh};
+                  c->d_frames, c->d_vnext, c->d_cinvh, c->d_perm, c->d_perm_epoch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   chol_plan_destroy(&c->plan);
@@ -662,6 +670,9 @@ LaArgs<T> make_la_args(slim_ctx* c) {
   a.tik_beta = c->tik_lambda * c->tik_lambda / c->n_views;   // M = A_v view blocks
   a.tik_reading = c->tik_reading;
   a.cinv = c->d_cinv;
+  a.cyclic = c->cyclic;
+  a.perm = c->d_perm;
+  a.perm_epoch = c->d_perm_epoch;
   return a;
 }
 
@@ -900,6 +911,24 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
   if (geom->dim == 3 && blocks->kind == SLIM_BLOCKS_VIEWS) return SLIM_ENOTSUP;
   if (blocks->kind == SLIM_BLOCKS_STREAM && blocks->steps_per_view < 1) return SLIM_EINVAL;
   if (blocks->ell < 1) return SLIM_EINVAL;
+  if ((blocks->with_replacement != 0 && blocks->with_replacement != 1) ||
+      (blocks->cyclic != 0 && blocks->cyclic != 1))
+    return SLIM_EINVAL;
+  if (blocks->kind == SLIM_BLOCKS_VIEWS) {
+    // a view block without replacement within the epoch is the random cyclic order
+    if ((blocks->cyclic || !blocks->with_replacement) && geom->n_views > kMaxCyclicViews)
+      return SLIM_ENOTSUP;
+  } else {
+    if (blocks->cyclic) return SLIM_ENOTSUP;   // random-ray blocks have no epoch order
+    if (!blocks->with_replacement) {
+      const long long first = blocks->kind == SLIM_BLOCKS_STREAM
+                                  ? (long long)geom->det_u * (geom->dim == 3 ? geom->det_v : 1)
+                                  : (long long)geom->n_views * geom->det_u *
+                                        (geom->dim == 3 ? geom->det_v : 1);
+      if (blocks->ell > kMaxDistinctRays) return SLIM_ENOTSUP;
+      if (blocks->ell > first) return SLIM_EINVAL;   // not enough rays to draw distinct ones
+    }
+  }
   if (r < 0 || !(lambda > 0.0) || !std::isfinite(lambda)) return SLIM_EINVAL;
   slim_ctx* c = new (std::nothrow) slim_ctx();
   if (!c) return SLIM_ENOMEM;
@@ -910,6 +939,8 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
   c->dim = geom->dim;
   c->kind = blocks->kind;
   c->steps_per_view = blocks->kind == SLIM_BLOCKS_STREAM ? blocks->steps_per_view : 1;
+  c->cyclic = blocks->kind == SLIM_BLOCKS_VIEWS && (blocks->cyclic || !blocks->with_replacement);
+  c->distinct = blocks->kind != SLIM_BLOCKS_VIEWS && !blocks->with_replacement;
   c->n = c->dim == 3 ? (long long)c->N * c->N * c->N : (long long)c->N * c->N;
   c->m = (long long)c->n_views * c->D * c->Dv;
   c->precision = geom->precision;
@@ -1094,6 +1125,8 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       {(void**)&c->d_dz, (size_t)c->P * sizeof(double)},
       {(void**)&c->d_res, (size_t)c->P * sizeof(double)},
       {(void**)&c->d_err, 2 * sizeof(double)},
+      {(void**)&c->d_perm, c->cyclic ? (size_t)c->n_views * sizeof(int) : 0},
+      {(void**)&c->d_perm_epoch, c->cyclic ? sizeof(long long) : 0},
   };
   for (auto& al : allocs)
     if (st == SLIM_OK && al.bytes > 0) chk(cudaMalloc(al.p, al.bytes), "cudaMalloc");
@@ -1114,6 +1147,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     if (g_elems) chk(cudaMemset(c->d_G, 0, g_elems * sizeof(double)), "memset");
     if (dense_solve && !la && !lsqr) chk(cudaMemset(c->d_L, 0, (size_t)c->P * c->P * fs), "memset");
     chk(cudaMemset(c->d_z, 0, (size_t)c->P * sizeof(double)), "memset");
+    if (c->cyclic) chk(cudaMemset(c->d_perm_epoch, 0xFF, sizeof(long long)), "memset");   // -1
     if (la) {
       for (int b = 0; b < c->nbuf && st == SLIM_OK; ++b)
         chk(cudaMalloc(&c->d_Lb[b], (size_t)c->P * c->P * fs), "cudaMalloc");
@@ -1387,6 +1421,25 @@ slim_status slim_sync(slim_ctx* c) {
   if (c->lookahead) CK(la_sync_all(c), "sync");
   CK(cudaStreamSynchronize(c->stream), "sync");
   return read_status(c);
+}
+
+slim_status slim_join_stream(slim_ctx* c, void* stream) {
+  if (!c) return SLIM_EINVAL;
+  cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+  if (c->lookahead && c->gs) {
+    // the last record of each event marks the newest work on its stream
+    CK(cudaStreamWaitEvent(s, c->ev_g1, 0), "join");
+    for (int b = 0; b < c->nbuf; ++b) {
+      CK(cudaStreamWaitEvent(s, c->ev_g2[b], 0), "join");
+      CK(cudaStreamWaitEvent(s, c->ev_x[b], 0), "join");
+    }
+  }
+  if (s != c->stream) {
+    if (!c->ev_user) CK(cudaEventCreateWithFlags(&c->ev_user, cudaEventDisableTiming), "join");
+    CK(cudaEventRecord(c->ev_user, c->stream), "join");
+    CK(cudaStreamWaitEvent(s, c->ev_user, 0), "join");
+  }
+  return SLIM_OK;
 }
 
 slim_status slim_set_ref(slim_ctx* c, const void* x_ref, size_t n, int dtype, int on_device) {

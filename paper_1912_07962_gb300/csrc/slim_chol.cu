@@ -1422,27 +1422,14 @@ cudaError_t launch_solve(const CholPlan& p, const void* L, const double* v, doub
 
 }  // namespace
 
-cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_sms,
-                             int ctas_per_sm) {
+cudaError_t chol_plan_configure(CholPlan* plan, int P, int nb, int is_f32, int num_sms,
+                                int ctas_per_sm) {
   *plan = CholPlan{};
   if (P % nb) return cudaErrorInvalidValue;
   plan->P = P;
   plan->nb = nb;
   plan->T = P / nb;
   plan->is_f32 = is_f32;
-  std::vector<CholTask> tasks = build_chol_tasks(plan->T, is_f32 && nb == 64);
-  plan->ntasks = (int)tasks.size();
-  size_t es = is_f32 ? sizeof(float) : sizeof(double);
-  cudaError_t e;
-  if ((e = cudaMalloc(&plan->d_tasks, tasks.size() * sizeof(CholTask))) != cudaSuccess) return e;
-  if ((e = cudaMemcpy(plan->d_tasks, tasks.data(), tasks.size() * sizeof(CholTask),
-                      cudaMemcpyHostToDevice)) != cudaSuccess)
-    return e;
-  size_t nsync = (size_t)plan->T * plan->T + 2 * plan->T + 4;
-  if ((e = cudaMalloc(&plan->d_sync, nsync * sizeof(int))) != cudaSuccess) return e;
-  if ((e = cudaMemset(plan->d_sync, 0, nsync * sizeof(int))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&plan->d_winv, (size_t)plan->T * nb * nb * es)) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&plan->d_y, 2 * (size_t)P * es)) != cudaSuccess) return e;
   plan->grid = ctas_per_sm * num_sms;
   if (is_f32)
     plan->cluster = nb == 64 ? pick_solve_cluster<float, 64>(P, plan->T)
@@ -1451,6 +1438,7 @@ cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_
     plan->cluster = nb == 64 ? pick_solve_cluster<double, 64>(P, plan->T)
                              : pick_solve_cluster<double, 32>(P, plan->T);
   // opt in to the shared memory the factor kernel needs
+  cudaError_t e;
   if (is_f32) {
     if (nb == 64)
       e = cudaFuncSetAttribute(chol_factor_kernel<float, 64>,
@@ -1473,6 +1461,24 @@ cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_
   return e;
 }
 
+cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_sms,
+                             int ctas_per_sm) {
+  cudaError_t e = chol_plan_configure(plan, P, nb, is_f32, num_sms, ctas_per_sm);
+  if (e != cudaSuccess) return e;
+  std::vector<CholTask> tasks = build_chol_tasks(plan->T, is_f32 && nb == 64);
+  plan->ntasks = (int)tasks.size();
+  size_t es = is_f32 ? sizeof(float) : sizeof(double);
+  if ((e = cudaMalloc(&plan->d_tasks, tasks.size() * sizeof(CholTask))) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(plan->d_tasks, tasks.data(), tasks.size() * sizeof(CholTask),
+                      cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
+  size_t nsync = chol_sync_words(plan->T);
+  if ((e = cudaMalloc(&plan->d_sync, nsync * sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMemset(plan->d_sync, 0, nsync * sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&plan->d_winv, (size_t)plan->T * nb * nb * es)) != cudaSuccess) return e;
+  return cudaMalloc(&plan->d_y, 2 * (size_t)P * es);
+}
+
 void chol_plan_destroy(CholPlan* plan) {
   cudaFree(plan->d_tasks);
   cudaFree(plan->d_sync);
@@ -1483,8 +1489,7 @@ void chol_plan_destroy(CholPlan* plan) {
 
 cudaError_t chol_factor(const CholPlan& p, void* L, int* status, cudaStream_t s) {
   // counters and tickets start at zero for every factorisation
-  size_t nsync = (size_t)p.T * p.T + 2 * p.T + 4;
-  cudaError_t e = cudaMemsetAsync(p.d_sync, 0, nsync * sizeof(int), s);
+  cudaError_t e = cudaMemsetAsync(p.d_sync, 0, chol_sync_words(p.T) * sizeof(int), s);
   if (e != cudaSuccess) return e;
   if (p.is_f32) return p.nb == 64 ? launch_factor<float, 64>(p, L, status, s)
                                   : launch_factor<float, 32>(p, L, status, s);

@@ -24,6 +24,18 @@ struct CholPlan {
   int cluster = 0;               // CTAs of the cluster that runs both solves (0: chained CTAs)
 };
 
+// Words of the plan's synchronisation array (d_sync): tile counters, solve
+// flags, tickets and the abort flag.
+inline size_t chol_sync_words(int T) { return (size_t)T * T + 2 * (size_t)T + 4; }
+
+// Shape the plan for order P (multiple of nb) without allocating anything:
+// tiles, factorisation grid, the solve's cluster size and the factor kernel's
+// shared-memory opt-in.  The caller then provides d_tasks (the list of
+// build_chol_tasks(T, is_f32 && nb == 64)) and ntasks, d_sync
+// (chol_sync_words(T) ints), d_winv (T * nb * nb values) and d_y (2P values).
+cudaError_t chol_plan_configure(CholPlan* plan, int P, int nb, int is_f32, int num_sms,
+                                int ctas_per_sm = 2);
+
 // Allocate / free the plan for order P (multiple of nb).
 cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_sms,
                              int ctas_per_sm = 2);

@@ -34,6 +34,92 @@ __host__ __device__ inline uint32_t bounded32(uint64_t u, uint32_t k) {
 }
 
 // ---------------------------------------------------------------------------
+// Sampling without replacement.
+//
+// Random cyclic order of view blocks (the walnut experiment of Sec. 4.3 visits
+// its blocks in a random cyclic order): epoch e = (k-1) / V of the steps visits
+// every view once, in the order of the Fisher-Yates (Durstenfeld) shuffle of
+// 0..V-1 in which swap i, for i = V-1 down to 1, exchanges entries i and
+// bounded(draw(seed, 7, e*V + V-1-i), i+1).  Step k takes entry (k-1) mod V.
+// ---------------------------------------------------------------------------
+constexpr int kStreamCyclic = 7;
+constexpr int kMaxCyclicViews = 4096;
+
+// View of step k in the random cyclic order.  Every thread of the block calls
+// it with the same arguments (its branches are uniform).  The permutation of
+// the current epoch is cached in perm[V] with its epoch in *perm_epoch (-1:
+// none), and recomputed in s_perm (kMaxCyclicViews shared ints) when the
+// epoch changes.  A block-wide barrier follows any recomputation.
+__device__ inline int cyclic_view(uint64_t seed, long long k, int V, int* perm,
+                                  long long* perm_epoch, int* s_perm) {
+  const long long e = (k - 1) / V;
+  const int pos = (int)((k - 1) % V);
+  if (*perm_epoch == e) return perm[pos];
+  for (int i = threadIdx.x; i < V; i += blockDim.x) s_perm[i] = i;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint64_t base = (uint64_t)e * (uint64_t)V;
+    for (int i = V - 1; i >= 1; --i) {
+      const int j = (int)bounded32(draw64(seed, kStreamCyclic, base + (uint64_t)(V - 1 - i)),
+                                   (uint32_t)(i + 1));
+      const int t = s_perm[i];
+      s_perm[i] = s_perm[j];
+      s_perm[j] = t;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < V; i += blockDim.x) perm[i] = s_perm[i];
+  const int view = s_perm[pos];
+  __syncthreads();   // every thread has read *perm_epoch and s_perm
+  if (threadIdx.x == 0) *perm_epoch = e;
+  return view;
+}
+
+// Distinct rays in a random-ray block: Floyd's algorithm (Bentley and Floyd,
+// "A sample of brilliance", CACM 1987) for ell distinct ids of [0, n): for
+// i = 0 .. ell-1, with j = n - ell + i and t = bounded(draw(seed, 3,
+// (k-1)*ell + i), j+1), insert t unless it is already in the sample, else
+// insert j.  The ids are kept in insertion order.
+constexpr int kMaxDistinctRays = 2048;
+constexpr int kDistinctTable = 2 * kMaxDistinctRays;   // open-addressing set, power of two
+
+// Fills ids[0..ell) for step k.  Every thread of the block calls it; s_t
+// (kMaxDistinctRays ints) and s_tab (kDistinctTable ints) are shared memory.
+// ell <= kMaxDistinctRays and ell <= n are the caller's to check.
+__device__ inline void floyd_rays(uint64_t seed, long long k, int ell, uint32_t n, int* ids,
+                                  int* s_t, int* s_tab) {
+  const uint64_t base = (uint64_t)(k - 1) * (uint64_t)ell;
+  for (int i = threadIdx.x; i < ell; i += blockDim.x) {
+    const uint32_t j = n - (uint32_t)ell + (uint32_t)i;
+    s_t[i] = (int)bounded32(draw64(seed, kStreamRays, base + (uint64_t)i), j + 1u);
+  }
+  for (int i = threadIdx.x; i < kDistinctTable; i += blockDim.x) s_tab[i] = -1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < ell; ++i) {
+      const int j = (int)(n - (uint32_t)ell + (uint32_t)i);
+      int v = s_t[i];
+      // look v up; j itself can never be in the set yet (every earlier entry is < j)
+      uint32_t h = ((uint32_t)v * 0x9E3779B1u) & (kDistinctTable - 1);
+      bool found = false;
+      while (s_tab[h] != -1) {
+        if (s_tab[h] == v) { found = true; break; }
+        h = (h + 1) & (kDistinctTable - 1);
+      }
+      if (found) {
+        v = j;
+        h = ((uint32_t)v * 0x9E3779B1u) & (kDistinctTable - 1);
+        while (s_tab[h] != -1) h = (h + 1) & (kDistinctTable - 1);
+      }
+      s_tab[h] = v;
+      s_t[i] = v;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ell; i += blockDim.x) ids[i] = s_t[i];
+}
+
+// ---------------------------------------------------------------------------
 // Joseph geometry.  Per view: co = cos(theta), si = sin(theta) from the host
 // table; row-stepping iff |co| >= |si|; rc = 1/co (row) or 1/si (column);
 // ia = |rc| is the path length per step.  For step s (row iy or column ix):

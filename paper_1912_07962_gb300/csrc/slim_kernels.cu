@@ -21,10 +21,15 @@ template <typename T>
 __global__ void sample_kernel(StepArgs<T> a) {
   __shared__ long long s_k;
   __shared__ int s_view, s_slot;
+  __shared__ int s_perm[kMaxCyclicViews];
+  const long long k0 = *a.done + 1;
+  const int cview = a.cyclic ? cyclic_view(a.seed, k0, a.n_views, a.perm, a.perm_epoch, s_perm) : 0;
+  __syncthreads();   // every thread has read the step counter
   if (threadIdx.x == 0) {
-    long long k = *a.done + 1;
-    int view = (int)bounded32(draw64(a.seed, kStreamBlocks, (unsigned long long)(k - 1)),
-                              (uint32_t)a.n_views);
+    long long k = k0;
+    int view = a.cyclic ? cview
+                        : (int)bounded32(draw64(a.seed, kStreamBlocks, (unsigned long long)(k - 1)),
+                                         (uint32_t)a.n_views);
     int slot = (int)((k - 1) % a.nslots);
     double lam_k = damping_k(a.lam, k, a.r, a.ramp, a.decay_after);
     double tik_c = 0.0;

@@ -45,6 +45,11 @@ struct StepArgs {
   const double* cinv;
   // sg (B_k = alpha_k I): the scatter takes z = r_k / lambda_k on the block's rows
   int sg;
+  // view blocks in the random cyclic order (a permutation of the views per
+  // epoch) instead of i.i.d. draws; the current epoch's permutation and its epoch
+  int cyclic;
+  int* perm;               // [n_views]
+  long long* perm_epoch;   // -1 before the first
 };
 
 // Sliced ELLPACK with slices of 32 lines (SELL-32): line l of slice s has its

@@ -25,10 +25,16 @@ __device__ __forceinline__ int eslot_of(long long block, int eslots) {
 template <typename T>
 __global__ void la_sample_kernel(LaArgs<T> a) {
   __shared__ int s_view, s_e;
+  __shared__ int s_perm[kMaxCyclicViews];
+  const long long j0 = *a.gdone + 1;
+  const int cview = a.cyclic ? cyclic_view(a.seed, j0, a.n_views, a.perm, a.perm_epoch, s_perm) : 0;
+  __syncthreads();   // every thread has read the step counter
   if (threadIdx.x == 0) {
-    const long long j = *a.gdone + 1;
-    const int view = (int)bounded32(draw64(a.seed, kStreamBlocks, (unsigned long long)(j - 1)),
-                                    (uint32_t)a.n_views);
+    const long long j = j0;
+    const int view = a.cyclic ? cview
+                              : (int)bounded32(draw64(a.seed, kStreamBlocks,
+                                                      (unsigned long long)(j - 1)),
+                                               (uint32_t)a.n_views);
     double lam_j = damping_k(a.lam, j, a.r, a.ramp, a.decay_after);
     double tik_c = 0.0;
     if (a.tik_beta > 0.0) {

@@ -50,6 +50,9 @@ struct LaArgs {
   double tik_beta;               // slimTik: lam_tik^2 / M (0: slimLS)
   int tik_reading;               // Tikhonov count: 0 blocks of M_k, 1 r
   const double* cinv;            // [n] 1/c of C_k = diag(c); null: C_k = I
+  int cyclic;                    // random cyclic order of the views (see StepArgs)
+  int* perm;                     // [n_views]
+  long long* perm_epoch;
 };
 
 // Geometry chain (stream of its own, one step at a time).

@@ -1,7 +1,9 @@
 // Damped Gram solve that allocates nothing: the same float64 tiled Cholesky
-// and triangular solves as slim_damped_solve, with all scratch memory in one
-// file-scope device array of fixed size.
+// (same task list, same grid) and the same triangular-solve kernels as
+// slim_damped_solve, with all scratch memory in one file-scope device array
+// of fixed size.
 #include <mutex>
+#include <vector>
 
 #include "../../include/slim.h"
 #include "slim_chol.cuh"
@@ -14,12 +16,22 @@ constexpr int kNb = 32;                                  // tile size of the flo
 constexpr int kMaxP = SLIM_NOALLOC_MAX_P;                // largest order accepted
 constexpr int kMaxT = kMaxP / kNb;
 constexpr int kMaxDevices = 64;
+constexpr int kCtasPerSm = 2;                            // as chol_plan_create's default
 
 constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
-constexpr size_t task_count(int T) {
-  // POTRF + TRSM + update tasks of the tiled factorisation of T x T tiles
+// An upper bound on the tasks of the T x T factorisation: one POTRF, TRSM and
+// single-tile update task per tile operation (the list the factor runs fuses
+// some of them into panel tasks, so it is never longer).
+constexpr size_t task_bound(int T) {
   size_t n = 0;
   for (int k = 0; k < T; ++k) n += 1 + (size_t)(T - k - 1) + (size_t)(T - k - 1) * (T - k) / 2;
+  return n;
+}
+// Start of the list for T tiles inside the task region: the lists for
+// T = 1 .. kMaxT are stored one after another.
+constexpr size_t task_offset(int T) {
+  size_t n = 0;
+  for (int t = 1; t < T; ++t) n += task_bound(t);
   return n;
 }
 
@@ -30,11 +42,12 @@ constexpr size_t kOffY = kOffWinv + align256((size_t)kMaxT * kNb * kNb * sizeof(
 constexpr size_t kOffV = kOffY + align256(2 * (size_t)kMaxP * sizeof(double));
 constexpr size_t kOffZ = kOffV + align256((size_t)kMaxP * sizeof(double));
 constexpr size_t kOffTasks = kOffZ + align256((size_t)kMaxP * sizeof(double));
-constexpr size_t kOffSync = kOffTasks + align256(task_count(kMaxT) * sizeof(CholTask));
+constexpr size_t kOffSync =
+    kOffTasks + align256(task_offset(kMaxT + 1) * sizeof(CholTask));
 constexpr size_t kOffStatus = kOffSync + align256(((size_t)kMaxT * kMaxT + 2 * kMaxT + 4) * sizeof(int));
 constexpr size_t kScratchBytes = kOffStatus + 256;
 
-// The scratch itself (about 8.7 MB).  Host code must not use this name as an
+// The scratch itself (about 9 MB).  Host code must not use this name as an
 // address: it takes the device address from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -42,11 +55,15 @@ struct DeviceSetup {
   bool ready = false;
   unsigned char* base = nullptr;   // device address of g_noalloc_scratch on that device
   int num_sms = 0;
+  int ntasks[kMaxT + 1] = {};      // length of the stored list for T tiles
 };
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mu;
 
-// Once per device, with that device current: resolve the scratch address.
+// Once per device, with that device current: resolve the scratch address and
+// store the factorisation's task lists for every T up to kMaxT there (built
+// by the same host routine as the allocating solve's, so the order is the
+// one its counter protocol was checked on).  The copies are synchronous.
 slim_status setup_device(int dev, DeviceSetup* out) {
   if (dev < 0 || dev >= kMaxDevices) return SLIM_ENOTSUP;
   std::lock_guard<std::mutex> lock(g_setup_mu);
@@ -62,29 +79,23 @@ slim_status setup_device(int dev, DeviceSetup* out) {
       cudaGetLastError();
       return SLIM_ECUDA;
     }
-    s.base = static_cast<unsigned char*>(ptr);
+    unsigned char* base = static_cast<unsigned char*>(ptr);
+    for (int T = 1; T <= kMaxT; ++T) {
+      const std::vector<CholTask> tasks = build_chol_tasks(T, false);
+      if (tasks.size() > task_bound(T)) return SLIM_EINVAL;   // cannot happen; keeps the bound honest
+      if (cudaMemcpy(base + kOffTasks + task_offset(T) * sizeof(CholTask), tasks.data(),
+                     tasks.size() * sizeof(CholTask), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return SLIM_ECUDA;
+      }
+      s.ntasks[T] = (int)tasks.size();
+    }
+    s.base = base;
     s.num_sms = sms;
     s.ready = true;
   }
   *out = s;
   return SLIM_OK;
-}
-
-// The task list of the T x T tiled factorisation, in the dependency-compatible
-// order the factor kernel expects (lookahead of one panel).
-__global__ void gen_tasks_kernel(CholTask* t, int T) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int n = 0;
-  t[n++] = {kPotrf, 0, 0, 0};
-  for (int i = 1; i < T; ++i) t[n++] = {kTrsm, (uint16_t)i, 0, 0};
-  for (int k = 0; k + 1 < T; ++k) {
-    const int n1 = k + 1;
-    for (int i = n1; i < T; ++i) t[n++] = {kUpd, (uint16_t)i, (uint16_t)n1, (uint16_t)k};
-    t[n++] = {kPotrf, (uint16_t)n1, (uint16_t)n1, (uint16_t)n1};
-    for (int i = n1 + 1; i < T; ++i) t[n++] = {kTrsm, (uint16_t)i, (uint16_t)n1, (uint16_t)n1};
-    for (int m = k + 2; m < T; ++m)
-      for (int i = m; i < T; ++i) t[n++] = {kUpd, (uint16_t)i, (uint16_t)m, (uint16_t)k};
-  }
 }
 
 // L = lambda I + G on the p x p block, identity on the padding.
@@ -116,28 +127,25 @@ extern "C" slim_status slim_damped_solve_noalloc(const double* G, int p, double 
   if (st != SLIM_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int P = (p + kNb - 1) / kNb * kNb;
-  const int T = P / kNb;
+  CholPlan plan;
+  if (chol_plan_configure(&plan, P, kNb, 0, ds.num_sms, kCtasPerSm) != cudaSuccess) {
+    cudaGetLastError();
+    return SLIM_ECUDA;
+  }
+  const int T = plan.T;
   double* L = reinterpret_cast<double*>(ds.base + kOffL);
   double* v = reinterpret_cast<double*>(ds.base + kOffV);
   double* out = reinterpret_cast<double*>(ds.base + kOffZ);
   int* status = reinterpret_cast<int*>(ds.base + kOffStatus);
-  CholPlan plan;
-  plan.P = P;
-  plan.T = T;
-  plan.nb = kNb;
-  plan.is_f32 = 0;
-  plan.ntasks = (int)task_count(T);
-  plan.d_tasks = reinterpret_cast<CholTask*>(ds.base + kOffTasks);
+  plan.ntasks = ds.ntasks[T];
+  plan.d_tasks = reinterpret_cast<CholTask*>(ds.base + kOffTasks + task_offset(T) * sizeof(CholTask));
   plan.d_sync = reinterpret_cast<int*>(ds.base + kOffSync);
   plan.d_winv = ds.base + kOffWinv;
   plan.d_y = ds.base + kOffY;
-  plan.grid = 2 * ds.num_sms;
 
+  // the previous call's status, counters and right-hand side are stale: the
+  // factorisation and the solves clear their counters and flags themselves
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
-  if (e == cudaSuccess) {
-    gen_tasks_kernel<<<1, 1, 0, s>>>(plan.d_tasks, T);
-    e = cudaGetLastError();
-  }
   if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, (size_t)P * sizeof(double), s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(v, rhs, (size_t)p * sizeof(double), cudaMemcpyDeviceToDevice, s);

@@ -114,10 +114,15 @@ __global__ void sample_rays_kernel(RayArgs a) {
     s_avail = (unsigned int)avail;
   }
   __syncthreads();
-  const unsigned long long base = (unsigned long long)(s_k - 1) * (unsigned long long)a.ell;
-  for (int i = threadIdx.x; i < a.ell; i += blockDim.x)
-    a.ring_ids[s_slot * a.ell + i] =
-        (int)bounded32(draw64(a.seed, kStreamRays, base + (unsigned long long)i), s_avail);
+  if (a.distinct) {
+    __shared__ int s_t[kMaxDistinctRays], s_tab[kDistinctTable];
+    floyd_rays(a.seed, s_k, a.ell, s_avail, a.ring_ids + s_slot * a.ell, s_t, s_tab);
+  } else {
+    const unsigned long long base = (unsigned long long)(s_k - 1) * (unsigned long long)a.ell;
+    for (int i = threadIdx.x; i < a.ell; i += blockDim.x)
+      a.ring_ids[s_slot * a.ell + i] =
+          (int)bounded32(draw64(a.seed, kStreamRays, base + (unsigned long long)i), s_avail);
+  }
   const int nr = a.dense ? a.P : a.p;
   for (int i = threadIdx.x; i < nr; i += blockDim.x) {
     a.rhs[i] = 0.0;

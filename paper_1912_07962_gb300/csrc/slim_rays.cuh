@@ -34,6 +34,7 @@ struct RayArgs {
   int* slice_cnt;                    // [S]
   int* slice_rows;                   // [S*cap]
   int dense;                         // 1: the tiled solve over P rows (2D, 3D random directions)
+  int distinct;                      // 1: the ell rays of a block are distinct (Floyd)
 };
 
 template <typename T> cudaError_t launch_sample_rays(const RayArgs& a, cudaStream_t s);

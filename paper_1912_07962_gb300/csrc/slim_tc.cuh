@@ -1,0 +1,77 @@
+// Float32-accurate matrix products on the Blackwell tensor cores (tcgen05),
+// and the triangular inverse built on them.
+//
+// A float32 operand x enters as three bfloat16 terms x0 = bf16(x),
+// x1 = bf16(x - x0), x2 = bf16(x - x0 - x1), which carry its 24 significant
+// bits.  A product a b is accumulated as the six term products a_i b_j with
+// i + j <= 2 (the dropped ones are below 2^-24 relative), each a tcgen05.mma
+// of kind f16 (bfloat16 inputs, float32 accumulator in tensor memory).
+#pragma once
+#include <cstdint>
+#include <vector>
+#include <cuda_runtime.h>
+
+namespace slim {
+
+// One product of a batched launch: C = alpha op(A) op(B) + beta C, op(A) M x K,
+// op(B) K x N, float32 in global memory.
+struct TcProblem {
+  const float* A;
+  long long lda;     // a_km = 0: op(A)[m][k] = A[m*lda + k]; 1: A[k*lda + m]
+  const float* B;
+  long long ldb;     // b_kn = 0: op(B)[k][n] = B[n*ldb + k]; 1: B[k*ldb + n]
+  float* C;
+  long long ldc;     // c_nm = 0: C[m*ldc + n]; 1: C[n*ldc + m]
+  int M, N, K;       // K a multiple of 64
+  int a_km, b_kn, c_nm;
+  int k_from_n;      // op(B)[k][n] = 0 for k < n: an output tile's K loop starts at its first column
+  int k_to_m;        // op(A)[m][k] = 0 for k > m: an output tile's K loop ends after its last row
+  float alpha, beta; // beta = 0: C is not read
+};
+
+constexpr int kTcBM = 128;   // output rows per CTA (the MMA's M)
+constexpr int kTcBN = 64;    // output columns per CTA (the MMA's N)
+constexpr int kTcBK = 64;    // K per pipeline stage (128-byte bfloat16 rows)
+
+// Launch the products probs[0..nprob) (a device array) with a grid covering
+// max_m x max_n outputs; CTAs beyond a problem's own M x N return at once.
+// A bounded wait that runs out records SLIM_ETIMEOUT in *status.
+cudaError_t tc_gemm(const TcProblem* d_probs, int nprob, int max_m, int max_n, int* status,
+                    cudaStream_t s);
+// Dynamic shared memory of one CTA (opted in by tc_prepare, once per process).
+size_t tc_smem_bytes();
+cudaError_t tc_prepare();
+
+// Inverse of a lower-triangular factor L (P x P row-major float32, P = T nb,
+// nb = 64) whose diagonal tiles' inverses W_j are given (T tiles of 64 x 64,
+// row-major, zero above the diagonal): X = L^{-1} in the lower triangle of the
+// P x P buffer X (diagonal included) and X^T in its strict upper triangle.
+// The recursion splits the tile range [a, b) at m = (a + b) / 2:
+//   X11 = inv(L11), X22 = inv(L22),  X21 = -X22 (L21 X11),
+// all blocks of one recursion depth in one batched launch per product; the
+// intermediate L21 X11 is held, transposed, in X's upper triangle.
+struct TriInvPlan {
+  int P = 0, T = 0;
+  std::vector<int> level_first;       // problems of depth d: [level_first[d], level_first[d+1])
+  std::vector<int> level_max_m, level_max_n;
+  TcProblem* d_probs = nullptr;       // 2 per split: (L21 X11) and (-X22 T1)
+  int nprob = 0;
+};
+// Plan for order P; L, W and X are bound now (the plan's problems point at them).
+cudaError_t tri_inverse_plan(TriInvPlan* plan, int P, const float* L, const float* W, float* X);
+void tri_inverse_plan_destroy(TriInvPlan* plan);
+cudaError_t tri_inverse(const TriInvPlan& plan, const float* W, float* X, int* status,
+                        cudaStream_t s);
+
+// Matrix-vector products with the triangular inverse held as above (lower: X,
+// strict upper: X^T), rows and columns in [0, p):
+//   y[i]  = sum_{j = lo..i} X[i][j] v[j]        for i in [lo, p)   (trinv_lower)
+//   z[j] (+)= sum_{i = max(j, lo)..p-1} X[i][j] y[i]   for j in [0, p)   (trinv_upper)
+// lo: v is zero below index lo (the right-hand side's first nonzero row), so y
+// is zero there too.  float32 products, float64 sums across the row.
+cudaError_t trinv_lower(const float* X, int P, int p, int lo, const double* v, double* y,
+                        cudaStream_t s);
+cudaError_t trinv_upper(const float* X, int P, int p, int lo, const double* y, double* z,
+                        int accumulate, cudaStream_t s);
+
+}  // namespace slim

@@ -37,7 +37,7 @@ EXPORTS = [
     "slim_unet_get_params", "slim_unet_get_grads", "slim_unet_forward", "slim_unet_train_step",
     "slim_warm_start", "slim_backproject_data", "slim_unet_conv3x3", "slim_unet_conv3x3_grad",
     "slim_unet_tconv2x2", "slim_unet_tconv2x2_grad", "slim_get_lsqr_info", "slim_set_c_diag",
-    "slim_selftest_wait",
+    "slim_selftest_wait", "slim_join_stream",
 ]
 A_MATRIX_FREE, A_CSR_F32, A_CSR_BF16 = 0, 1, 2
 NOALLOC_MAX_P = 1024
@@ -52,7 +52,7 @@ class slim_geometry(C.Structure):
 
 class slim_blocks(C.Structure):
     _fields_ = [("kind", C.c_int), ("ell", C.c_int), ("seed", C.c_ulonglong),
-                ("steps_per_view", C.c_int)]
+                ("steps_per_view", C.c_int), ("with_replacement", C.c_int), ("cyclic", C.c_int)]
 
 
 class slim_step_opts(C.Structure):
@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "slim_get_x": ([VP, VP, SZ, I, I], I),
         "slim_step": ([VP, I], I),
         "slim_sync": ([VP], I),
+        "slim_join_stream": ([VP, VP], I),
         "slim_set_ref": ([VP, VP, SZ, I, I], I),
         "slim_run": ([VP, LL, D, I, P(LL), P(D), P(D)], I),
         "slim_get_iter": ([VP, P(LL)], I),
@@ -172,6 +173,8 @@ class Slim:
                     count of Tikhonov rows (blocks of M_k, or r as printed);
                     C_k = diag(c) through set_c_diag
       decay_after   the 1/k decay of the damping after that step (0: none)
+      with_replacement, cyclic  block sampling: False / True selects the random
+                    cyclic order of the views, or distinct rays in random-ray blocks
       frames        3D views from arbitrary directions: rows (d, u, v) per view
     """
 
@@ -180,7 +183,7 @@ class Slim:
                  angles=None, a_mode=A_MATRIX_FREE, dim=2, det_v=1, kind=SLIM_BLOCKS_VIEWS,
                  steps_per_view=1, tile=0, ctas_per_sm=0, lookahead=0, lsqr_max_iter=0,
                  lsqr_tol=0.0, tik_lambda=0.0, tik_reading=0, decay_after=0, olbfgs_memory=0,
-                 frames=None, _handle=None):
+                 frames=None, with_replacement=True, cyclic=False, _handle=None):
         lib = load()
         self._lib = lib
         self._angles = None
@@ -201,7 +204,7 @@ class Slim:
         if frames is not None:       # 3D views from arbitrary directions: rows (d, u, v)
             self._frames = np.ascontiguousarray(frames, dtype=np.float64).reshape(-1)
             g.frames = self._frames.ctypes.data_as(C.POINTER(C.c_double))
-        blk = slim_blocks(kind, ell, seed, steps_per_view)
+        blk = slim_blocks(kind, ell, seed, steps_per_view, int(with_replacement), int(cyclic))
         opts = slim_step_opts(eta, int(ramp), solver, refine_iters, int(use_graph), tile, ctas_per_sm,
                               lookahead, lsqr_max_iter, lsqr_tol, tik_lambda, tik_reading,
                               decay_after, olbfgs_memory)
@@ -266,6 +269,11 @@ class Slim:
 
     def sync(self):
         self._check(self._lib.slim_sync(self.h))
+
+    def join(self, stream_ptr):
+        """Make the cudaStream_t `stream_ptr` wait (on the device) for everything
+        the context has queued on all its streams, work prepared ahead included."""
+        self._check(self._lib.slim_join_stream(self.h, C.c_void_p(stream_ptr)))
 
     def set_stream(self, stream_ptr):
         """Run the context's work on the cudaStream_t `stream_ptr`.  0 selects
@@ -411,7 +419,8 @@ def problem_structs(specs):
     S = (slim_step_opts * n)()
     for i, sp in enumerate(specs):
         G[i] = slim_geometry(2, sp["N"], sp["n_views"], sp["det"], 1, None, 0, sp.get("precision", 0))
-        B[i] = slim_blocks(sp.get("kind", SLIM_BLOCKS_RAYS), sp["ell"], sp["seed"], 1)
+        B[i] = slim_blocks(sp.get("kind", SLIM_BLOCKS_RAYS), sp["ell"], sp["seed"], 1,
+                           int(sp.get("with_replacement", True)), int(sp.get("cyclic", False)))
         R[i] = sp["r"]
         L[i] = sp["lam"]
         S[i] = slim_step_opts(1.0, 0, sp.get("solver", 0), sp.get("refine_iters", 2), 0,

@@ -14,15 +14,15 @@ def tomo_problem(cfg):
     return g, A, x_true, b
 
 
-def oracle_memory(g, seed, k, r):
+def oracle_memory(g, seed, k, r, cyclic=False):
     """Row-id blocks of S_k (oldest first) and their ring slots, as the oracle draws them."""
     ks = list(range(max(1, k - r), k + 1))
-    return [(kk, (kk - 1) % (r + 1), oslim.view_block_ids(g, seed, kk)) for kk in ks]
+    return [(kk, (kk - 1) % (r + 1), oslim.view_block_ids(g, seed, kk, cyclic)) for kk in ks]
 
 
-def oracle_step_from(g, src, seed, k, r, lam, x_prev, ramp=False, eta=1.0):
+def oracle_step_from(g, src, seed, k, r, lam, x_prev, ramp=False, eta=1.0, cyclic=False):
     """x_k from x_{k-1} with the memory of step k (Woodbury form, float64)."""
-    mem = oracle_memory(g, seed, k, r)
+    mem = oracle_memory(g, seed, k, r, cyclic)
     blocks = [src.rows(ids) for _, _, ids in mem]
     lam_k = oslim.damping(lam, k, r, ramp)
     x, r_k, s, z = oslim.step_woodbury(x_prev, blocks, src.rhs(mem[-1][2]), lam_k, eta)

@@ -269,23 +269,20 @@ def test_bench_configuration_c2_graph_sampled_steps(sl, c2):
     assert worst < TOL32
 
 
-def _kappa_tol(g, mem, lam, x_prev, x_k):
-    """max(1e-12, 0.1 * kappa(lambda I + G) * u * ||s|| / ||x_k||): two backward-stable
-    float64 solves of the damped Gram system may differ by up to about kappa * u in
-    z, hence in s = M^T z; the tolerance sits a decade below that first-order bound."""
+def _kappa(g, mem, lam):
+    """kappa(lambda I + G) of the window, reported beside the error."""
     import scipy.linalg as sla
     M = joseph.rows(g, np.concatenate([ids for _, _, ids in mem]))
     K = (M @ M.T).toarray() + lam * np.eye(M.shape[0])
     p = K.shape[0]
     lo = sla.eigvalsh(K, subset_by_index=[0, 0])[0]
     hi = sla.eigvalsh(K, subset_by_index=[p - 1, p - 1])[0]
-    u = 2.0 ** -53
-    s_rel = np.linalg.norm(x_k - x_prev) / np.linalg.norm(x_k)
-    return max(TOL64, 0.1 * (hi / lo) * u * s_rel), hi / lo
+    return hi / lo
 
 
 def test_plain_fp64_c2_single_steps(sl, c2):
-    # the 256x256 workload: kappa(lambda I + G) = 1.5e6 once the memory is full
+    # the 256x256 workload: kappa(lambda I + G) = 1.5e6 once the memory is full;
+    # the float64 bar of 1e-12 holds as it is (the step s is small next to x)
     cfg = workloads.C2
     g, A, _, b = c2
     src = oslim.tomo_source(g, b)
@@ -298,6 +295,6 @@ def test_plain_fp64_c2_single_steps(sl, c2):
             s.set_x(x_prev)
             s.set_iter(k - 1)
             s.step(1)
-            tol, kappa = _kappa_tol(g, mem, cfg.lam, x_prev, xo)
-            assert rel(s.get_x(), xo) < tol, (k, kappa, tol)
+            e = rel(s.get_x(), xo)
+            assert e < TOL64, (k, e, _kappa(g, mem, cfg.lam))
         x_prev = xo

@@ -78,3 +78,59 @@ def test_random_rays_in_range_and_distinct_streams():
     assert len(rays) == 64 and all(0 <= v < 1000 for v in rays)
     assert rays != rng.random_rays(5, 4, 64, 1000)
     assert rays == [rng.bounded(rng.draw(5, rng.STREAM_RAYS, 2 * 64 + i), 1000) for i in range(64)]
+
+
+# ------------------------------------------------------------ sampling without replacement
+def test_cyclic_order_visits_every_block_once_per_epoch():
+    for V, seed in ((1, 3), (2, 4), (7, 5), (60, 1), (180, 2)):
+        for epoch in range(4):
+            seen = [rng.cyclic_block(seed, epoch * V + i, V) for i in range(1, V + 1)]
+            assert sorted(seen) == list(range(V)), (V, seed, epoch)
+
+
+def test_cyclic_epochs_differ():
+    V = 60
+    perms = {tuple(rng.cyclic_permutation(9, e, V)) for e in range(20)}
+    assert len(perms) == 20
+
+
+def test_cyclic_permutation_is_uniform():
+    # Fisher-Yates draws each of the M! orders with probability 1/M!; a swap
+    # index drawn from [0, i) instead of [0, i] (Sattolo's cycles) reaches only
+    # (M-1)! of them, and any bias in the swaps shows in the counts
+    import itertools
+    V, E = 4, 24000
+    counts = dict.fromkeys(itertools.permutations(range(V)), 0)
+    for e in range(E):
+        counts[tuple(rng.cyclic_permutation(21, e, V))] += 1
+    exp = E / len(counts)
+    chi2 = sum((c - exp) ** 2 / exp for c in counts.values())
+    assert min(counts.values()) > 0
+    assert chi2 < 60.0, chi2          # 23 degrees of freedom: p < 1e-4 above 55
+
+
+def test_floyd_rays_are_distinct_and_in_range():
+    for n, ell, seed in ((5, 4, 1), (10, 10, 2), (1000, 37, 3), (65340, 363, 4)):
+        for k in range(1, 40):
+            ids = rng.distinct_rays(seed, k, ell, n)
+            assert len(ids) == ell and len(set(ids)) == ell
+            assert all(0 <= v < n for v in ids)
+    assert sorted(rng.distinct_rays(5, 3, 10, 10)) == list(range(10))
+
+
+def test_floyd_sample_is_uniform_over_subsets():
+    # Floyd's algorithm gives every ell-subset of the n ids probability 1 / C(n, ell)
+    import itertools
+    n, ell, K = 6, 3, 20000
+    counts = {frozenset(c): 0 for c in itertools.combinations(range(n), ell)}
+    for k in range(1, K + 1):
+        counts[frozenset(rng.distinct_rays(17, k, ell, n))] += 1
+    exp = K / len(counts)
+    chi2 = sum((c - exp) ** 2 / exp for c in counts.values())
+    assert chi2 < 50.0, chi2          # 19 degrees of freedom: p < 1e-4 above 47
+
+
+def test_floyd_rejects_blocks_larger_than_the_rays():
+    import pytest
+    with pytest.raises(ValueError):
+        rng.distinct_rays(1, 1, 11, 10)
