@@ -144,6 +144,9 @@ def make_b(sl, cfg, x_true, e):
     return workloads.add_noise(clean, e, cfg.noise)
 
 
+CHOSEN_SOLVER = "mixed"   # set from --solver
+
+
 def make_form(sl, cfg, form, seed, lookahead=0, ctas_per_sm=0, decay_after=0):
     """chosen: float32 projector/residual/scatter, float64 Gram, float32 factor
     refined twice against the float64 Gram; chosen_fp64_factor: the same with
@@ -151,10 +154,12 @@ def make_form(sl, cfg, form, seed, lookahead=0, ctas_per_sm=0, decay_after=0):
     plain: float64 everywhere, one kernel per phase, no graph."""
     if form in ("chosen", "chosen_fp64_factor"):
         mixed = form == "chosen"
+        solver = ((sl.SLIM_SOLVE_MIXED_TC if CHOSEN_SOLVER == "mixed_tc" and lookahead
+                   else sl.SLIM_SOLVE_MIXED) if mixed else sl.SLIM_SOLVE_FP64)
+        refine = (3 if solver == sl.SLIM_SOLVE_MIXED_TC else 2) if mixed else 0
         return sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.ell, cfg.r, cfg.lam, seed,
-                       precision=sl.SLIM_PREC_FP32,
-                       solver=sl.SLIM_SOLVE_MIXED if mixed else sl.SLIM_SOLVE_FP64,
-                       refine_iters=2 if mixed else 0, use_graph=True, lookahead=lookahead,
+                       precision=sl.SLIM_PREC_FP32, solver=solver,
+                       refine_iters=refine, use_graph=True, lookahead=lookahead,
                        ctas_per_sm=ctas_per_sm, decay_after=decay_after)
     return sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.ell, cfg.r, cfg.lam, seed,
                    precision=sl.SLIM_PREC_FP64, solver=sl.SLIM_SOLVE_FP64, use_graph=False,
@@ -839,7 +844,12 @@ def warm_start_block(args):
     recs, t_ws = ws.evaluate(net, cfg, test, s_in, args.ws_eval_epochs, thresholds, torch, log=log)
     net.close()
     fwd_gflop = unet_flops(sl, cfg.n)["forward"] * 1e-9
+    summ = ws.summarize(recs, thresholds)
     return {"train_seeds": len(train), "test_seeds": len(test),
+            "seeds": (f"train {train[0]}..{train[-1]}, held out {test[0]}..{test[-1]}"),
+            "gain": {"warm_x0_err_median": summ["warm"]["err0"],
+                     "zero_start_best_err_median": summ["zero"]["best"],
+                     "warm_x0_beats_zero_start_best": summ["warm"]["err0"] < summ["zero"]["best"]},
             "target": f"chosen-form iterate after {args.ws_target_epochs} epochs from x0=0",
             "error": "relative error to x_true (the phantom), checked every 6 steps",
             "budget": f"{args.ws_eval_epochs} epochs per start",
@@ -849,7 +859,7 @@ def warm_start_block(args):
             "input_scale": s_in, "forward_ms": fwd_ms, "forward_gflop": fwd_gflop,
             "forward_tflops": fwd_gflop / fwd_ms,
             "warm_start_call_ms_median": t_ws * 1e3,
-            "steps_to_threshold": ws.summarize(recs, thresholds)}
+            "steps_to_threshold": summ}
 
 
 def e2e_block(sl, cfg, b, K, W, lookahead=0, ctas_per_sm=0):
@@ -1020,7 +1030,7 @@ def main_gpu(args):
     tik_pass = (tik_block(sl, cfg, b, flush, stream, args.tik_steps, max(3, args.warmup),
                           lookahead=args.lookahead or 6, ctas_per_sm=args.factor_ctas_per_sm)
                 if rank == 0 and args.tik_steps > 0 else None)
-    warm = warm_start_block(args) if rank == 0 and args.warm_start else None
+    warm = warm_start_block(args) if rank == 0 and not args.no_warm_start else None
     unet = (unet_block(sl, flush, stream, reps=args.unet_reps)
             if rank == 0 and not args.no_unet else None)
     cpu = None
@@ -1178,6 +1188,9 @@ def main():
     ap.add_argument("--tta-decay-after", type=int, default=180,
                     help="also run time-to-accuracy with the 1/k damping decay after this step "
                          "(0: skip)")
+    ap.add_argument("--solver", default="mixed", choices=["mixed", "mixed_tc"],
+                    help="chosen form's solve: through the float32 factor (mixed) or through "
+                         "its tensor-core inverse (mixed_tc, pipelined only)")
     ap.add_argument("--no-fp64-factor", action="store_true",
                     help="skip the pipelined chosen form with the float64 factor")
     ap.add_argument("--no-cpu", action="store_true")
@@ -1208,12 +1221,14 @@ def main():
     ap.add_argument("--csr-only", action="store_true",
                     help="time only the stored-matrix passes and print that line")
     ap.add_argument("--csr-reps", type=int, default=20)
-    ap.add_argument("--warm-start", action="store_true",
-                    help="train and evaluate the learned initial guess (minutes of GPU time)")
-    ap.add_argument("--ws-train", type=int, default=256)
-    ap.add_argument("--ws-test", type=int, default=20)
-    ap.add_argument("--ws-target-epochs", type=int, default=2)
-    ap.add_argument("--ws-eval-epochs", type=int, default=4)
+    ap.add_argument("--no-warm-start", action="store_true",
+                    help="skip the learned initial guess (by default a reduced protocol runs: "
+                         "the --ws-* defaults; the full one is --ws-train 2000 --ws-test 200 "
+                         "--ws-target-epochs 2 --ws-eval-epochs 2 --ws-net-epochs 10)")
+    ap.add_argument("--ws-train", type=int, default=96)
+    ap.add_argument("--ws-test", type=int, default=12)
+    ap.add_argument("--ws-target-epochs", type=int, default=1)
+    ap.add_argument("--ws-eval-epochs", type=int, default=2)
     ap.add_argument("--ws-net-epochs", type=int, default=8)
     ap.add_argument("--ws-batch", type=int, default=8)
     ap.add_argument("--ws-lr", type=float, default=1e-3)
@@ -1229,6 +1244,8 @@ def main():
     ap.add_argument("--cpu-warmup", type=int, default=6)
     ap.add_argument("--cpu-leg", action="store_true")
     args = ap.parse_args()
+    global CHOSEN_SOLVER
+    CHOSEN_SOLVER = args.solver
     args.r_warm = workload_of(args.workload)[0].r + 1
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

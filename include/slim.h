@@ -61,7 +61,7 @@ typedef enum {
 enum { SLIM_F32 = 0, SLIM_F64 = 1 };
 enum { SLIM_PREC_FP64 = 0, SLIM_PREC_FP32 = 1 };
 enum { SLIM_SOLVE_FP64 = 0, SLIM_SOLVE_MIXED = 1, SLIM_SOLVE_LSQR = 2, SLIM_SOLVE_SG = 3,
-       SLIM_SOLVE_OLBFGS = 4 };
+       SLIM_SOLVE_OLBFGS = 4, SLIM_SOLVE_MIXED_TC = 5 };
 enum { SLIM_BLOCKS_VIEWS = 0, SLIM_BLOCKS_RAYS = 1, SLIM_BLOCKS_STREAM = 2 };
 
 /* Parallel-beam geometry (Sec. 4.3; Joseph rows defined in the library docs).
@@ -154,6 +154,18 @@ typedef struct {
  *                 SLIM_SOLVE_MIXED: float32 tiled Cholesky of the same float64
  *                 matrix, then `refine_iters` rounds of iterative refinement whose
  *                 residual (lambda_k I + G) z is computed in float64
+ *                 SLIM_SOLVE_MIXED_TC: a float32 factor with the same float64
+ *                 refinement, built on the tcgen05 tensor cores with
+ *                 float32-accurate split-bfloat16 products (as slim_tc_matmul):
+ *                 the geometry chain factors panel by panel (a one-CTA
+ *                 diagonal tile, then the panel and the trailing update as
+ *                 tensor-core products) and forms X = L^{-1} (recursive
+ *                 blocking, X21 = -X22 L21 X11) while it runs ahead; every
+ *                 solve of the iterate chain is z = X^T (X v), two
+ *                 matrix-vector products instead of two chains of triangular
+ *                 sweeps.
+ *                 lookahead >= 1 and tile 0 or 64 only (SLIM_ENOTSUP
+ *                 otherwise)
  *                 SLIM_SOLVE_LSQR: no Gram matrix and no factorisation: s_k of
  *                 Eq. (slimLSstep) by LSQR for damped least squares (Sec. 4.2),
  *                 matrix-free over the window's stored taps, float64 vectors;
@@ -183,7 +195,7 @@ typedef struct {
  *   ctas_per_sm   resident CTAs per SM of the persistent factorisation (1..4,
  *                 0 = default: 2, or 1 with lookahead, where the D factorisations
  *                 in flight share these CTAs, num_SMs * ctas_per_sm / D each)
- *   lookahead     0: each step runs as one chain.  D = 1..6 (view blocks, 2D,
+ *   lookahead     0: each step runs as one chain.  D = 1..10 (view blocks, 2D,
  *                 rows from the projector): the matrix lambda_k I + M_k M_k^T of
  *                 Eq. (B_k) depends only on the blocks drawn, so the chain that
  *                 draws tau_j, adds its Gram rows and factors K_j runs up to D
@@ -370,6 +382,37 @@ slim_status slim_backproject(slim_ctx* ctx, const int* ray_ids, int count, const
  * Returns SLIM_ENOTPD on a non-positive pivot. */
 slim_status slim_damped_solve(const double* G, int p, double lambda, const double* rhs,
                               double* z, void* cuda_stream);
+
+/* The two building blocks of the mixed-precision solve's triangular inverse,
+ * on their own (they serve the damped solve of Eq. (B_k); the paper itself
+ * solves with LSQR or a factorisation and names no kernel).
+ *
+ * slim_tc_matmul: C = alpha op(A) op(B) + beta C on the tcgen05 tensor
+ * cores, op(A) M x K, op(B) K x N, float32 device arrays.  Every float32
+ * operand enters as three bfloat16 terms (x0 = bf16(x), x1 = bf16(x - x0),
+ * x2 = bf16(x - x0 - x1)) and the six term products a_i b_j with i + j <= 2
+ * accumulate in float32, so the result has float32 accuracy.  Layout flags:
+ * a_km = 0: op(A)[m][k] = A[m*lda + k], 1: A[k*lda + m]; b_kn = 0:
+ * op(B)[k][n] = B[n*ldb + k], 1: B[k*ldb + n]; c_nm = 0: C[m*ldc + n], 1:
+ * C[n*ldc + m].  a_lower = 1: op(A) is lower triangular (op(A)[m][k] for
+ * k > m is read as zero, whatever A holds there); b_lower = 1: op(B) is
+ * lower triangular (op(B)[k][n] for k < n read as zero).  K a multiple of 64;
+ * K-contiguous operands (a_km = 0, b_kn = 0) 16-byte aligned with lda / ldb
+ * multiples of 4 (SLIM_EINVAL otherwise).  beta = 0: C is not read.
+ * Allocates a few bytes of device memory and synchronises `cuda_stream`.
+ *
+ * slim_chol_inverse: the float32 tiled Cholesky factor L of lambda I + G
+ * (G: p x p float64 device array, lower triangle read) and X = L^{-1},
+ * computed by recursive blocking (X21 = -X22 L21 X11) on the tensor-core
+ * product above: X (p x p float32 device array, row-major) receives L^{-1} in
+ * its lower triangle and diagonal and (L^{-1})^T in its strict upper
+ * triangle.  SLIM_ENOTPD on a non-positive pivot.  Allocates its work space
+ * and synchronises `cuda_stream`. */
+slim_status slim_tc_matmul(int M, int N, int K, const float* A, long long lda, int a_km,
+                           const float* B, long long ldb, int b_kn, float* C, long long ldc,
+                           int c_nm, float alpha, float beta, int a_lower, int b_lower,
+                           void* cuda_stream);
+slim_status slim_chol_inverse(const double* G, int p, double lambda, float* X, void* cuda_stream);
 
 /* Launch log of the pipelined form (lookahead > 0, timing on): every
  * factorisation launch and every iterate chain is bracketed by events without

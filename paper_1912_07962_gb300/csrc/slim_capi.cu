@@ -15,10 +15,11 @@
 #include "slim_frames.cuh"
 #include "slim_unet.cuh"
 #include "slim_rays.cuh"
+#include "slim_tc.cuh"
 
 using namespace slim;
 
-constexpr int kMaxBuf = 7;   // lookahead D <= 6: D+1 factor buffers
+constexpr int kMaxBuf = 11;   // lookahead D <= 10: D+1 factor buffers
 
 struct slim_ctx {
   // configuration
@@ -97,6 +98,13 @@ struct slim_ctx {
   int* d_ext = nullptr;              // [nbuf * P] ring index -> extended row
   void* d_Lb[kMaxBuf] = {};
   CholPlan planb[kMaxBuf];
+  // SLIM_SOLVE_MIXED_TC: X = L^{-1} per buffer (X^T in its upper triangle)
+  void* d_Xb[kMaxBuf] = {};
+  TriInvPlan tplan[kMaxBuf];
+  TcCholPlan cplan[kMaxBuf];         // launch-per-panel tensor-core factorisation
+  double* d_ty = nullptr;            // [P] intermediate of the products with X
+  unsigned* d_coop_bar = nullptr;    // grid barrier of the cooperative iterate chain
+  int coop_grid = 0;                 // its CTAs (0: the chain runs kernel by kernel)
   cudaStream_t xs = nullptr, gs = nullptr, fs[kMaxBuf] = {};
   cudaGraphExec_t g1_exec[kMaxBuf] = {}, g2_exec[kMaxBuf] = {}, gx_exec[kMaxBuf] = {};
   cudaEvent_t ev_user = nullptr, ev_g1 = nullptr, ev_g2[kMaxBuf] = {}, ev_x[kMaxBuf] = {};
@@ -294,6 +302,12 @@ cudaError_t mark(slim_ctx* c, int i) {
   return cudaEventRecord(c->ev[i], c->stream);
 }
 
+// Float32 factor with float64-residual refinement (solved through the
+// factor, or through its tensor-core inverse).
+inline bool is_mixed(const slim_ctx* c) {
+  return c->solver == SLIM_SOLVE_MIXED || c->solver == SLIM_SOLVE_MIXED_TC;
+}
+
 // Kernels one step launches (sample, forward, Gram, K, factor, the solves:
 // one cluster kernel each, else a forward and a backward kernel; 2 per
 // refinement round (residual, z += dz), scatter).
@@ -303,8 +317,21 @@ int kernels_per_step(const slim_ctx* c) {
     return c->tik_lambda > 0.0 ? 4 : 3;
   if (c->solver == SLIM_SOLVE_SG) return 3;     // sample, forward + residual, scatter
   if (c->solver == SLIM_SOLVE_OLBFGS) return 3; // sample, forward + residual, the olbfgs step
-  const int solves = c->solver == SLIM_SOLVE_MIXED ? 1 + c->refine_iters : 1;
-  const int refine = c->solver == SLIM_SOLVE_MIXED ? 2 * c->refine_iters : 0;
+  const int solves = is_mixed(c) ? 1 + c->refine_iters : 1;
+  const int refine = is_mixed(c) ? 2 * c->refine_iters : 0;
+  if (c->lookahead && c->solver == SLIM_SOLVE_MIXED_TC) {
+    // geometry: sample, taps, Gram, map clear, ring map, K; the factor (per
+    // panel: diagonal tile, panel product, trailing product; the last panel
+    // its diagonal tile only), the inverse (diagonal tiles, one product per
+    // recursion depth and side, mirror); iterate: residual, 2 products per
+    // solve, a residual per refinement round, scatter -- or all of the
+    // iterate chain in one cooperative kernel
+    const int factor = 3 * c->cplan[0].T - 2;
+    const int inv = 2 + (int)c->tplan[0].level_first.size() - 1;
+    const int tik = c->tik_lambda > 0.0 ? 2 : 0;
+    const int iterate = c->coop_grid ? 1 : 1 + 2 * solves + c->refine_iters + 1 + tik;
+    return 6 + factor + inv + iterate;
+  }
   if (c->lookahead) {
     // geometry: sample, taps, Gram, map clear, ring map, K, factor; iterate:
     // residual, the solves, refinement rounds, scatter
@@ -597,6 +624,9 @@ void free_all(slim_ctx* c) {
     if (c->gx_exec[b]) cudaGraphExecDestroy(c->gx_exec[b]);
     if (c->d_Lb[b]) cudaFree(c->d_Lb[b]);
     chol_plan_destroy(&c->planb[b]);
+    if (c->d_Xb[b]) cudaFree(c->d_Xb[b]);
+    tri_inverse_plan_destroy(&c->tplan[b]);
+    tc_chol_plan_destroy(&c->cplan[b]);
     if (c->ev_g2[b]) cudaEventDestroy(c->ev_g2[b]);
     if (c->ev_x[b]) cudaEventDestroy(c->ev_x[b]);
     if (c->fs[b]) cudaStreamDestroy(c->fs[b]);
@@ -608,6 +638,8 @@ void free_all(slim_ctx* c) {
   if (c->xs) cudaStreamDestroy(c->xs);
   if (c->gs) cudaStreamDestroy(c->gs);
   if (c->d_gdone) cudaFree(c->d_gdone);
+  if (c->d_ty) cudaFree(c->d_ty);
+  if (c->d_coop_bar) cudaFree(c->d_coop_bar);
   if (c->d_info_buf) cudaFree(c->d_info_buf);
   if (c->d_ext) cudaFree(c->d_ext);
 }
@@ -697,7 +729,7 @@ cudaError_t la_enqueue_geometry(slim_ctx* c, int b, cudaStream_t s) {
   if ((e = la_launch_ext_map(info, c->ell, c->nslots, c->eslots, c->p, c->P, ext, s)) !=
       cudaSuccess)
     return e;
-  if (c->solver == SLIM_SOLVE_MIXED)
+  if (is_mixed(c))
     e = la_launch_form<float>(info, ext, c->d_G, c->Pe, (float*)c->d_Lb[b], c->P, s);
   else
     e = la_launch_form<double>(info, ext, c->d_G, c->Pe, (double*)c->d_Lb[b], c->P, s);
@@ -708,7 +740,15 @@ cudaError_t la_enqueue_geometry(slim_ctx* c, int b, cudaStream_t s) {
 cudaError_t la_enqueue_factor(slim_ctx* c, int b, cudaStream_t s) {
   cudaError_t e;
   if ((e = la_mark(c, 4, s)) != cudaSuccess) return e;
-  if ((e = chol_factor(c->planb[b], c->d_Lb[b], c->d_status, s)) != cudaSuccess) return e;
+  if (c->solver == SLIM_SOLVE_MIXED_TC)
+    e = tc_cholesky(c->cplan[b], (float*)c->d_Lb[b], (float*)c->planb[b].d_winv, c->d_status, s);
+  else
+    e = chol_factor(c->planb[b], c->d_Lb[b], c->d_status, s);
+  if (e != cudaSuccess) return e;
+  if (c->solver == SLIM_SOLVE_MIXED_TC &&
+      (e = tri_inverse(c->tplan[b], (const float*)c->planb[b].d_winv, (float*)c->d_Xb[b],
+                       c->d_status, s)) != cudaSuccess)
+    return e;
   return la_mark(c, 5, s);
 }
 
@@ -727,9 +767,23 @@ cudaError_t la_enqueue_iterate(slim_ctx* c, int b, cudaStream_t s) {
   if ((e = la_mark(c, 7, s)) != cudaSuccess) return e;
   // slimLS: the right-hand side is zero above the newest block (the last one)
   const int first_tile = tik ? 0 : (c->nslots - 1) * c->ell / c->nb;
-  if ((e = chol_solve(c->planb[b], c->d_Lb[b], c->d_rhs, c->d_z, c->d_status, s, first_tile)) !=
-      cudaSuccess)
+  if (c->solver == SLIM_SOLVE_MIXED_TC) {
+    // z = X^T X rhs with X = L^{-1}: two matrix-vector products per solve
+    const float* X = (const float*)c->d_Xb[b];
+    const int lo = tik ? 0 : (c->nslots - 1) * c->ell;
+    if ((e = trinv_lower(X, c->P, c->p, lo, c->d_rhs, c->d_ty, s)) != cudaSuccess) return e;
+    if ((e = trinv_upper(X, c->P, c->p, lo, c->d_ty, c->d_z, 0, s)) != cudaSuccess) return e;
+    for (int it = 0; it < c->refine_iters; ++it) {
+      if ((e = la_launch_refine(info, ext, c->d_G, c->Pe, c->d_z, c->d_rhs, c->d_res, c->P, s)) !=
+          cudaSuccess)
+        return e;
+      if ((e = trinv_lower(X, c->P, c->p, 0, c->d_res, c->d_ty, s)) != cudaSuccess) return e;
+      if ((e = trinv_upper(X, c->P, c->p, 0, c->d_ty, c->d_z, 1, s)) != cudaSuccess) return e;
+    }
+  } else if ((e = chol_solve(c->planb[b], c->d_Lb[b], c->d_rhs, c->d_z, c->d_status, s,
+                             first_tile)) != cudaSuccess) {
     return e;
+  }
   if (c->solver == SLIM_SOLVE_MIXED) {
     for (int it = 0; it < c->refine_iters; ++it) {
       if ((e = la_launch_refine(info, ext, c->d_G, c->Pe, c->d_z, c->d_rhs, c->d_res, c->P, s)) !=
@@ -830,7 +884,28 @@ cudaError_t la_step(slim_ctx* c, int nsteps) {
     if ((e = cudaStreamWaitEvent(c->xs, c->ev_g2[b], 0)) != cudaSuccess) return e;
     const int lx = (int)(c->log_nx % slim_ctx::kLog);
     if (log && (e = cudaEventRecord(c->log_x[2 * lx], c->xs)) != cudaSuccess) return e;
-    if ((e = cudaGraphLaunch(c->gx_exec[b], c->xs)) != cudaSuccess) return e;
+    if (c->coop_grid) {
+      // the tensor-core form's chain as one cooperative launch (its phases
+      // are one interval: the timing reports it all as the solve phase)
+      if (c->timing && ((e = cudaEventRecord(c->la_ev[6], c->xs)) != cudaSuccess ||
+                        (e = cudaEventRecord(c->la_ev[7], c->xs)) != cudaSuccess))
+        return e;
+      const bool f32 = c->precision == SLIM_PREC_FP32;
+      const int* ext = c->d_ext + (size_t)b * c->P;
+      const StepInfo* info = c->d_info_buf + b;
+      e = f32 ? iterate_tc<float>(make_la_args<float>(c), info, ext, (const float*)c->d_Xb[b],
+                                  c->d_ty, c->d_res, c->d_coop_bar, c->refine_iters,
+                                  c->coop_grid, c->xs)
+              : iterate_tc<double>(make_la_args<double>(c), info, ext, (const float*)c->d_Xb[b],
+                                   c->d_ty, c->d_res, c->d_coop_bar, c->refine_iters,
+                                   c->coop_grid, c->xs);
+      if (e != cudaSuccess) return e;
+      if (c->timing && ((e = cudaEventRecord(c->la_ev[8], c->xs)) != cudaSuccess ||
+                        (e = cudaEventRecord(c->la_ev[9], c->xs)) != cudaSuccess))
+        return e;
+    } else if ((e = cudaGraphLaunch(c->gx_exec[b], c->xs)) != cudaSuccess) {
+      return e;
+    }
     if (log) {
       if ((e = cudaEventRecord(c->log_x[2 * lx + 1], c->xs)) != cudaSuccess) return e;
       ++c->log_nx;
@@ -993,7 +1068,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       return SLIM_EINVAL;
     }
     if (c->tik_lambda > 0.0 && (c->kind != SLIM_BLOCKS_VIEWS || c->dim != 2 ||
-                                (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED &&
+                                (c->solver != SLIM_SOLVE_FP64 && !is_mixed(c) &&
                                  c->solver != SLIM_SOLVE_LSQR))) {
       delete c;
       return SLIM_ENOTSUP;
@@ -1011,7 +1086,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       c->use_graph = 0;   // a cooperative launch per step
     }
     if (!(c->eta > 0.0) ||
-        (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED &&
+        (c->solver != SLIM_SOLVE_FP64 && !is_mixed(c) &&
          c->solver != SLIM_SOLVE_LSQR && c->solver != SLIM_SOLVE_SG &&
          c->solver != SLIM_SOLVE_OLBFGS) ||
         c->refine_iters < 0 || c->refine_iters > 16 || (c->tile != 0 && c->tile != 32 && c->tile != 64) ||
@@ -1021,6 +1096,13 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       return SLIM_EINVAL;
     }
     if (c->lookahead && (c->kind != SLIM_BLOCKS_VIEWS || c->dim != 2 || c->a_mode != 0)) {
+      delete c;
+      return SLIM_ENOTSUP;
+    }
+    // the tensor-core inverse runs in the geometry chain of the pipelined
+    // form, on the 64-wide tiles of the float32 factor
+    if (c->solver == SLIM_SOLVE_MIXED_TC &&
+        (c->lookahead == 0 || (c->tile != 0 && c->tile != 64) || c->p > 8192)) {
       delete c;
       return SLIM_ENOTSUP;
     }
@@ -1158,8 +1240,30 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       const int fgrid = std::max(16, c->num_sms * c->ctas_per_sm / c->lookahead);
       for (int b = 0; b < c->nbuf; ++b) {
         chk(cudaMemset(c->d_Lb[b], 0, (size_t)c->P * c->P * fs), "memset");
-        chk(chol_plan_create(&c->planb[b], c->P, c->nb, c->solver == SLIM_SOLVE_MIXED ? 1 : 0,
+        chk(chol_plan_create(&c->planb[b], c->P, c->nb, is_mixed(c) ? 1 : 0,
                              fgrid, 1), "chol plan");
+      }
+      if (c->solver == SLIM_SOLVE_MIXED_TC && st == SLIM_OK) {
+        chk(tc_prepare(), "tensor-core product");
+        chk(chol_potrf_tile_prepare(), "diagonal tiles");
+        for (int b = 0; b < c->nbuf && st == SLIM_OK; ++b)
+          chk(tc_chol_plan(&c->cplan[b], c->P, (float*)c->d_Lb[b],
+                           (const float*)c->planb[b].d_winv), "factor plan");
+        chk(cudaMalloc(&c->d_ty, (size_t)c->P * sizeof(double)), "cudaMalloc");
+        if (c->tik_lambda == 0.0 && st == SLIM_OK) {
+          chk(cudaMalloc(&c->d_coop_bar, 2 * sizeof(unsigned)), "cudaMalloc");
+          chk(c->precision == SLIM_PREC_FP32
+                  ? iterate_tc_prepare<float>(c->P, c->num_sms, &c->coop_grid)
+                  : iterate_tc_prepare<double>(c->P, c->num_sms, &c->coop_grid),
+              "cooperative iterate chain");
+        }
+        for (int b = 0; b < c->nbuf && st == SLIM_OK; ++b) {
+          chk(cudaMalloc(&c->d_Xb[b], (size_t)c->P * c->P * sizeof(float)), "cudaMalloc");
+          chk(cudaMemset(c->d_Xb[b], 0, (size_t)c->P * c->P * sizeof(float)), "memset");
+          chk(tri_inverse_plan(&c->tplan[b], c->P, (const float*)c->d_Lb[b],
+                               (const float*)c->planb[b].d_winv, (float*)c->d_Xb[b]),
+              "inverse plan");
+        }
       }
     } else if (c->solver == SLIM_SOLVE_SG) {
       // the scatter alone
@@ -1178,7 +1282,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       // tmp (and the rest) start at zero: the solve leaves tmp at zero
       chk(cudaMemset(c->d_lsqr, 0, cnt * sizeof(double)), "memset");
     } else if (dense_solve)
-      chk(chol_plan_create(&c->plan, c->P, c->nb, c->solver == SLIM_SOLVE_MIXED ? 1 : 0,
+      chk(chol_plan_create(&c->plan, c->P, c->nb, is_mixed(c) ? 1 : 0,
                            c->num_sms, c->ctas_per_sm), "chol plan");
     else
       chk(prepare_slice_solve(c->cap), "slice solve");
@@ -1326,8 +1430,7 @@ slim_status slim_set_c_diag(slim_ctx* c, const void* cdiag, size_t n, int dtype,
   if (!c || (cdiag && ((long long)n != c->n || (dtype != SLIM_F32 && dtype != SLIM_F64))))
     return fail(c, SLIM_EINVAL, "set_c_diag: bad arguments");
   if (c->kind != SLIM_BLOCKS_VIEWS || c->dim != 2 ||
-      (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED &&
-       c->solver != SLIM_SOLVE_LSQR))
+      (c->solver != SLIM_SOLVE_FP64 && !is_mixed(c) && c->solver != SLIM_SOLVE_LSQR))
     return fail(c, SLIM_ENOTSUP, "set_c_diag: 2D view blocks, Woodbury or LSQR form");
   CK(c->lookahead ? la_sync_all(c) : cudaStreamSynchronize(c->stream), "set_c_diag");
   if (!cdiag) {

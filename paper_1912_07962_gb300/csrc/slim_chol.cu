@@ -893,6 +893,18 @@ __global__ void __launch_bounds__(kThreads, 2) chol_factor_kernel(T* L, int P, i
   }
 }
 
+// One diagonal tile on its own (the launch-per-panel factorisation): factor
+// tile (j, j) of L in place and write its inverse to winv[j].
+__global__ void __launch_bounds__(kThreads) chol_potrf_tile_kernel(float* L, int P, int j,
+                                                                    float* winv, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* As = reinterpret_cast<float*>(smem_raw);
+  float* Bs = As + 64 * gemm_ld(64);
+  float* S = Bs + 64 * gemm_ld(64);
+  task_potrf<float, 64>(L + (size_t)j * 64 * P + (size_t)j * 64, P, winv + (size_t)j * 64 * 64,
+                        As, Bs, S, status);
+}
+
 // Row-split GEMV pieces: thread (r = tid/TPR, sub = tid%TPR) owns columns
 // sub*CPT .. sub*CPT+CPT-1 of row r.  Tiles are loaded into registers before
 // the wait for the vector they multiply, hiding the L2 latency of the tile.
@@ -1421,6 +1433,16 @@ cudaError_t launch_solve(const CholPlan& p, const void* L, const double* v, doub
 }
 
 }  // namespace
+
+cudaError_t chol_potrf_tile_prepare() {
+  return cudaFuncSetAttribute(chol_potrf_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)factor_smem<float, 64>());
+}
+
+cudaError_t chol_potrf_tile(float* L, int P, int j, float* winv, int* status, cudaStream_t s) {
+  chol_potrf_tile_kernel<<<1, kThreads, factor_smem<float, 64>(), s>>>(L, P, j, winv, status);
+  return cudaGetLastError();
+}
 
 cudaError_t chol_plan_configure(CholPlan* plan, int P, int nb, int is_f32, int num_sms,
                                 int ctas_per_sm) {

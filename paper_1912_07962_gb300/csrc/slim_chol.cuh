@@ -36,6 +36,14 @@ inline size_t chol_sync_words(int T) { return (size_t)T * T + 2 * (size_t)T + 4;
 cudaError_t chol_plan_configure(CholPlan* plan, int P, int nb, int is_f32, int num_sms,
                                 int ctas_per_sm = 2);
 
+// Factor diagonal tile (j, j) of the float32 matrix L (P x P row-major, tiles
+// of 64, its trailing updates applied) in place, L_jj with zeros above the
+// diagonal, and write L_jj^{-1} to winv + j * 64 * 64.  One CTA; non-positive
+// pivots record SLIM_ENOTPD in *status.  chol_potrf_tile_prepare opts in to
+// its shared memory (once per process).
+cudaError_t chol_potrf_tile_prepare();
+cudaError_t chol_potrf_tile(float* L, int P, int j, float* winv, int* status, cudaStream_t s);
+
 // Allocate / free the plan for order P (multiple of nb).
 cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_sms,
                              int ctas_per_sm = 2);

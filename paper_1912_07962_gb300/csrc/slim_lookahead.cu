@@ -217,22 +217,46 @@ __global__ void __launch_bounds__(kCta) la_residual_kernel(LaArgs<T> a, const St
   if (lane == 0) a.rhs[(a.nslots - 1) * a.ell + w] = (double)(acc - a.b[a.ring_ids[q]]);
 }
 
-__global__ void la_refine_kernel(const StepInfo* info, const int* __restrict__ ext,
-                                 const double* __restrict__ G, int Pe, const double* z,
-                                 const double* rhs, double* res, int P) {
-  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+// res = rhs - lambda_k z - G z over the factored rows (G gathered through the
+// extended-row map).  Eight rows per CTA, one warp each; the map and z are
+// staged in shared memory once per CTA, so the rows of G are the only global
+// stream, gathered four entries per lane at a time.
+__global__ void __launch_bounds__(kCta) la_refine_kernel(const StepInfo* info,
+                                                         const int* __restrict__ ext,
+                                                         const double* __restrict__ G, int Pe,
+                                                         const double* z, const double* rhs,
+                                                         double* res, int P) {
+  extern __shared__ double s_z[];                         // P doubles, then P ints
+  int* s_ext = reinterpret_cast<int*>(s_z + P);
+  for (int j = threadIdx.x; j < P; j += blockDim.x) {
+    s_z[j] = z[j];
+    s_ext[j] = ext[j];
+  }
+  __syncthreads();
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * kWarps + wib;
   if (row >= P) return;
-  const int ei = ext[row];
+  const int ei = s_ext[row];
   double s = 0.0;
   if (ei >= 0) {
     const double* g = G + (size_t)ei * Pe;
-    for (int j = lane; j < P; j += 32) {
-      const int ej = ext[j];
-      if (ej >= 0) s += g[ej] * z[j];
+    for (int base = 0; base < P; base += 128) {
+      double gv[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int j = base + 32 * t + lane;
+        const int ej = j < P ? s_ext[j] : -1;
+        gv[t] = ej >= 0 ? __ldg(g + ej) : 0.0;
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int j = base + 32 * t + lane;
+        if (j < P) s += gv[t] * s_z[j];
+      }
     }
   }
   s = warp_sum(s);
-  if (lane == 0) res[row] = rhs[row] - info->lam_k * z[row] - s;
+  if (lane == 0) res[row] = rhs[row] - info->lam_k * s_z[row] - s;
 }
 
 // x -= eta M_k^T z over the rows of the window (atomic scatter-add).
@@ -337,7 +361,13 @@ cudaError_t la_launch_residual(const LaArgs<T>& a, const StepInfo* info, cudaStr
 cudaError_t la_launch_refine(const StepInfo* info, const int* ext, const double* G, int Pe,
                              const double* z, const double* rhs, double* res, int P,
                              cudaStream_t s) {
-  la_refine_kernel<<<cdiv(P, kWarps), kCta, 0, s>>>(info, ext, G, Pe, z, rhs, res, P);
+  const size_t smem = (size_t)P * (sizeof(double) + sizeof(int));
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(la_refine_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  la_refine_kernel<<<cdiv(P, kWarps), kCta, smem, s>>>(info, ext, G, Pe, z, rhs, res, P);
   return cudaGetLastError();
 }
 

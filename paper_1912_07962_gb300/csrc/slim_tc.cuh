@@ -11,6 +11,8 @@
 #include <vector>
 #include <cuda_runtime.h>
 
+#include "slim_lookahead.cuh"
+
 namespace slim {
 
 // One product of a batched launch: C = alpha op(A) op(B) + beta C, op(A) M x K,
@@ -24,9 +26,13 @@ struct TcProblem {
   long long ldc;     // c_nm = 0: C[m*ldc + n]; 1: C[n*ldc + m]
   int M, N, K;       // K a multiple of 64
   int a_km, b_kn, c_nm;
-  int k_from_n;      // op(B)[k][n] = 0 for k < n: an output tile's K loop starts at its first column
-  int k_to_m;        // op(A)[m][k] = 0 for k > m: an output tile's K loop ends after its last row
+  int k_from_n;      // op(B) lower triangular (op(B)[k][n] = 0 for k < n; whatever the storage
+                     // holds there is read as zero): an output tile's K loop starts at its first column
+  int k_to_m;        // op(A) lower triangular (op(A)[m][k] = 0 for k > m, likewise masked): an
+                     // output tile's K loop ends after its last row
   float alpha, beta; // beta = 0: C is not read
+  int c_lower;       // 1: only output tiles that reach the lower triangle (some n <= m) are
+                     // computed; tiles wholly above the diagonal are left alone
 };
 
 constexpr int kTcBM = 128;   // output rows per CTA (the MMA's M)
@@ -63,6 +69,23 @@ void tri_inverse_plan_destroy(TriInvPlan* plan);
 cudaError_t tri_inverse(const TriInvPlan& plan, const float* W, float* X, int* status,
                         cudaStream_t s);
 
+// Right-looking blocked Cholesky of the float32 matrix L (P x P row-major, its
+// lower triangle, P = 64 T) with one launch per step of each 64-wide panel j:
+//   diagonal tile:  L_jj = chol(A_jj), W_j = L_jj^{-1}     (one CTA, SIMT)
+//   panel:          L_ij = A_ij W_j^T for all i > j      (one tensor-core product, in place)
+//   trailing:       A_il -= L_ij L_lj^T for all i >= l > j (one tensor-core product, the
+//                   tiles that reach the lower triangle)
+// The factor replaces L's lower triangle; W goes to winv (T tiles of 64 x 64).
+// Entries above the diagonal of L's tiles are work space.
+struct TcCholPlan {
+  int P = 0, T = 0;
+  TcProblem* d_probs = nullptr;       // 2 per panel: the panel's TRSM and its trailing update
+};
+cudaError_t tc_chol_plan(TcCholPlan* plan, int P, float* L, const float* winv);
+void tc_chol_plan_destroy(TcCholPlan* plan);
+cudaError_t tc_cholesky(const TcCholPlan& plan, float* L, float* winv, int* status,
+                        cudaStream_t s);
+
 // Matrix-vector products with the triangular inverse held as above (lower: X,
 // strict upper: X^T), rows and columns in [0, p):
 //   y[i]  = sum_{j = lo..i} X[i][j] v[j]        for i in [lo, p)   (trinv_lower)
@@ -73,5 +96,22 @@ cudaError_t trinv_lower(const float* X, int P, int p, int lo, const double* v, d
                         cudaStream_t s);
 cudaError_t trinv_upper(const float* X, int P, int p, int lo, const double* y, double* z,
                         int accumulate, cudaStream_t s);
+
+// The iterate chain of the pipelined tensor-core form for step `info` (plain
+// slimLS: no slimTik terms; C_k may be diagonal) as one cooperative launch of
+// `grid` CTAs: r_k into rhs, z = X^T X rhs, `refine` rounds of
+// res = rhs - lambda_k z - G z (float64) and z += X^T X res, then
+// x -= eta M_k^T z.  y and res are work vectors of P doubles; bar two
+// unsigned ints (zeroed here).  A grid barrier that runs out records
+// SLIM_ETIMEOUT.  iterate_tc_prepare opts in to the shared memory for order P
+// and gives the grid (at most kIterTcCtas CTAs, one per SM of a GB300, all co-resident).
+constexpr int kIterTcCtas = 152;
+size_t iterate_tc_smem(int P);
+template <typename T>
+cudaError_t iterate_tc_prepare(int P, int num_sms, int* grid);
+template <typename T>
+cudaError_t iterate_tc(const LaArgs<T>& a, const StepInfo* info, const int* ext, const float* X,
+                       double* y, double* res, unsigned* bar, int refine, int grid,
+                       cudaStream_t s);
 
 }  // namespace slim

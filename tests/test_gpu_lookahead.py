@@ -7,7 +7,7 @@ import pytest
 import workloads
 from oracle import joseph, slim as oslim
 
-from _common import oracle_memory, rel
+from _common import oracle_memory, oracle_step_from, rel
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu,
@@ -116,7 +116,42 @@ def test_unsupported_combinations(sl):
     with pytest.raises(sl.SlimError):
         sl.Slim(32, 20, 47, 20, 2, 1e-2, 1, kind=sl.SLIM_BLOCKS_RAYS, lookahead=1)
     with pytest.raises(sl.SlimError):
-        sl.Slim(32, 20, 47, 47, 2, 1e-2, 1, lookahead=7)
+        sl.Slim(32, 20, 47, 47, 2, 1e-2, 1, lookahead=11)
     with pytest.raises(sl.SlimError):
         sl.SlimBatch([dict(N=24, n_views=18, det=35, ell=35, r=2, lam=1e-2, seed=1, kind=0,
                            lookahead=1)])
+
+
+@pytest.mark.parametrize("D,r,N,V,det", [(1, 5, 40, 30, 57), (3, 2, 24, 18, 35), (6, 3, 64, 30, 91)])
+def test_tensor_core_inverse_solves(sl, D, r, N, V, det):
+    # the solves through X = L^{-1} (tensor-core inverse in the geometry
+    # chain): the same iterates as the float64 oracle at the float32 bar,
+    # on ragged orders (p = 342, 105, 364) and wrapping buffers
+    g, b = _problem(N=N, V=V, D=det, seed=9)
+    lam, seed = 1e-2, 9
+    steps = r + 1 + D + 3
+    sched = list(oslim.view_schedule(g, seed, steps))
+    traj = [x for _, x, _ in oslim.run(oslim.tomo_source(g, b), sched, r, lam)]
+    s = sl.Slim(g.N, g.n_views, g.det_u, g.det_u, r, lam, seed, precision=sl.SLIM_PREC_FP32,
+                solver=sl.SLIM_SOLVE_MIXED_TC, refine_iters=2, lookahead=D)
+    s.set_data(b)
+    src = oslim.tomo_source(g, b)
+    for k in range(1, steps + 1):
+        x_prev = traj[k - 2] if k > 1 else np.zeros(g.n)
+        s.set_x(x_prev)                  # the oracle's x_{k-1}, rounded to float32
+        s.step(1)
+        xp = x_prev.astype(np.float32).astype(np.float64)
+        xo32, _ = oracle_step_from(g, src, seed, k, r, lam, xp)
+        assert rel(s.get_x(), xo32) < 1e-5, (D, k)
+    s.close()
+
+
+def test_tensor_core_inverse_argument_checks(sl):
+    with pytest.raises(sl.SlimError) as ei:      # needs the pipelined form
+        sl.Slim(32, 20, 47, 47, 2, 1e-2, 1, precision=sl.SLIM_PREC_FP32,
+                solver=sl.SLIM_SOLVE_MIXED_TC)
+    assert ei.value.code == sl.SLIM_ENOTSUP
+    with pytest.raises(sl.SlimError) as ei:      # 64-wide tiles only
+        sl.Slim(32, 20, 47, 47, 2, 1e-2, 1, precision=sl.SLIM_PREC_FP32,
+                solver=sl.SLIM_SOLVE_MIXED_TC, lookahead=2, tile=32)
+    assert ei.value.code == sl.SLIM_ENOTSUP

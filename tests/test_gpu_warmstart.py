@@ -41,3 +41,32 @@ def test_driver_refuses_the_default_stream():
     with torch.cuda.stream(torch.cuda.default_stream()):
         with pytest.raises(RuntimeError):
             ws._stream(torch)
+
+
+def test_trained_network_beats_the_zero_start():
+    # What the learned initial guess gains: trained in the library's kernels on
+    # pairs the method produces (160 seeds of the 64 x 64 workload, targets the
+    # chosen form's iterate after 2 epochs), evaluated on 10 held-out seeds.
+    # The network's x_0 alone must be closer to the phantom than the best
+    # iterate the method reaches from x_0 = 0 within 3 epochs (medians), and
+    # the warm-started run must do at least as well as the zero start.
+    from paper_1912_07962_gb300 import build, slim as sl, warmstart as ws
+    build.build()
+    cfg = workloads.C1
+    train = list(workloads.WARM_TRAIN_SEEDS)[:160]
+    test = list(workloads.WARM_TEST_SEEDS)[:10]
+    X, Y, worst = ws.make_pairs(cfg, train, 2, torch, check_every=40)
+    assert worst < 1e-4
+    s_in = ws.input_scale(X)
+    net = sl.UNet(cfg.N, cfg.N, max_batch=8)
+    net.set_params(sl.flatten_params(workloads.unet_init(0, sl.UNET_LAYERS)))
+    losses, _ = ws.train(net, X, Y, s_in, 25, 8, 1e-3, torch)
+    assert losses[-1] < 0.5 * losses[0]
+    recs, _ = ws.evaluate(net, cfg, test, s_in, 3, [0.5, 0.3], torch, every=6)
+    net.close()
+    warm0 = float(np.median([r["warm"]["err0"] for r in recs]))
+    zero_best = float(np.median([r["zero"]["best"] for r in recs]))
+    warm_best = float(np.median([r["warm"]["best"] for r in recs]))
+    assert all(r["used"] for r in recs)           # the residual check kept every guess
+    assert warm0 < zero_best, (warm0, zero_best)
+    assert warm_best <= zero_best, (warm_best, zero_best)
