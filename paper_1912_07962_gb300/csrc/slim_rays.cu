@@ -328,6 +328,88 @@ __global__ void __launch_bounds__(kCta) project_rays_kernel(const ViewGeom* view
   if (lane == 0) y[w] = acc;
 }
 
+// Full-view forward projection in the per-slice geometry (views rotating
+// about z, det_v = N): ray (a, v, u) lies in slice v and its in-plane taps do
+// not depend on v.  A CTA takes kFvRays consecutive bins of one view, marches
+// their taps once (the float64 Joseph steps every kernel uses, so the same
+// weights) into shared memory, and applies them to all N slices: one march
+// serves N x kFvRays rays.  The taps are laid out so that lanes run along the
+// image's contiguous axis: across the bins for row-stepping views (adjacent
+// bins meet adjacent pixels of one row), along the steps for column-stepping
+// views (adjacent steps are adjacent pixels of one row).
+constexpr int kFvRays = 16;
+
+__host__ __device__ inline size_t fullview_smem(int N, int elem) {
+  return (size_t)N * kFvRays * (2 * sizeof(int) + 2 * (size_t)elem);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) project_fullview_kernel(const ViewGeom* views, int N,
+                                                               int Du, const T* x, T* y) {
+  extern __shared__ __align__(16) unsigned char fv_smem[];
+  int2* s_pix = reinterpret_cast<int2*>(fv_smem);                       // [N * kFvRays]
+  T* s_w = reinterpret_cast<T*>(s_pix + (size_t)N * kFvRays);           // [N * kFvRays * 2]
+  const int tiles = (Du + kFvRays - 1) / kFvRays;
+  const int a = blockIdx.x / tiles, u0 = (blockIdx.x % tiles) * kFvRays;
+  const ViewGeom v = views[a];
+  const bool rows = v.row_step != 0;
+  // tap slot of (step s, ray r)
+  auto slot = [&](int s, int r) { return rows ? s * kFvRays + r : r * N + s; };
+  const double cc = 0.5 * (double)(N - 1);
+  for (int e = threadIdx.x; e < N * kFvRays; e += blockDim.x) {
+    const int s = e / kFvRays, r = e % kFvRays, u = u0 + r;
+    int2 px = make_int2(-1, -1);
+    T wa = T(0), wb = T(0);
+    if (u < Du) {
+      const double t = (double)u - 0.5 * (double)(Du - 1);
+      const Tap2 tp = joseph_step(v, t, cc, s);
+      px.x = tp.wa != 0.0 ? inplane_pixel(v.row_step, N, s, tp.minor0) : -1;
+      px.y = tp.wb != 0.0 ? inplane_pixel(v.row_step, N, s, tp.minor0 + 1) : -1;
+      wa = (T)tp.wa;
+      wb = (T)tp.wb;
+    }
+    const int q = slot(s, r);
+    s_pix[q] = px;
+    s_w[2 * q] = wa;
+    s_w[2 * q + 1] = wb;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const long long NN = (long long)N * N;
+  if (rows) {
+    // half-warps over the 16 bins, the two halves over even and odd steps
+    const int r = lane & 15, ph = lane >> 4, u = u0 + r;
+    for (int sl = warp; sl < N; sl += nw) {
+      const T* xs = x + sl * NN;
+      T acc = T(0);
+      for (int s = ph; s < N; s += 2) {
+        const int q = s * kFvRays + r;
+        const int2 px = s_pix[q];
+        if (px.x >= 0) acc += s_w[2 * q] * xs[px.x];
+        if (px.y >= 0) acc += s_w[2 * q + 1] * xs[px.y];
+      }
+      acc += __shfl_down_sync(0xffffffffu, acc, 16);
+      if (ph == 0 && u < Du) y[((long long)a * N + sl) * Du + u] = acc;
+    }
+  } else {
+    // a warp per (slice, bin), lanes over the steps
+    for (int w = warp; w < N * kFvRays; w += nw) {
+      const int sl = w / kFvRays, r = w % kFvRays, u = u0 + r;
+      if (u >= Du) continue;
+      const T* xs = x + sl * NN;
+      T acc = T(0);
+      for (int s = lane; s < N; s += 32) {
+        const int q = r * N + s;
+        const int2 px = s_pix[q];
+        if (px.x >= 0) acc += s_w[2 * q] * xs[px.x];
+        if (px.y >= 0) acc += s_w[2 * q + 1] * xs[px.y];
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) y[((long long)a * N + sl) * Du + u] = acc;
+    }
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -374,6 +456,17 @@ template <typename T>
 cudaError_t launch_project_rays(const ViewGeom* views, int N, int Du, int Dv, const int* ids,
                                 long long count, const T* x, T* y, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
+  const size_t fv = fullview_smem(N, sizeof(T));
+  if (!ids && Dv == N && fv <= 200 * 1024 && count % ((long long)Du * Dv) == 0) {
+    // every ray of every view in order: the taps of a bin serve all N slices
+    cudaError_t e = cudaFuncSetAttribute(project_fullview_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fv);
+    if (e != cudaSuccess) return e;
+    const long long views_n = count / ((long long)Du * Dv);
+    const long long grid = views_n * ((Du + kFvRays - 1) / kFvRays);
+    project_fullview_kernel<T><<<(unsigned)grid, 256, fv, s>>>(views, N, Du, x, y);
+    return cudaGetLastError();
+  }
   project_rays_kernel<T><<<cdiv(count, kWarpsPerCta), kCta, 0, s>>>(views, N, Du, Dv, ids, count,
                                                                     x, y);
   return cudaGetLastError();

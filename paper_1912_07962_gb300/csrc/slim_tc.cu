@@ -182,67 +182,75 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int c) {
 // k < r0 + r (a triangular operand whose other triangle holds other data).
 // R * 64 / 256 values per thread, in runs of 8 consecutive k (one 16-byte
 // chunk per term each), loaded, split and stored one run at a time.
+// A thread's share of one operand stage: R * 64 / 256 values of op(X) in
+// runs of 8 consecutive k (one 16-byte chunk per bfloat16 term each).
+//   K-contiguous rows (km = 0): eight lanes per 64-float row, two float4
+//     each, so a warp reads four whole rows per pass (R / 32 passes);
+//   K-strided rows (X[k][m], km = 1): consecutive lanes take consecutive rows
+//     m, so every load reads a contiguous run of one k row.
+// All of the stage's loads are issued first (load_operand), then the values
+// are masked, split and stored (store_operand): one memory round trip per
+// stage instead of one per run.
 template <int R>
-__device__ __forceinline__ void stage_operand(unsigned char* dst, const float* X, long long ld,
-                                              int km, int r0, int rows, int k0, int tri) {
-  const int tid = threadIdx.x;
-  if (km == 0) {
-    // K-contiguous rows: eight lanes per 64-float row, each two float4 (one
-    // 16-byte chunk per term), so a warp reads four whole rows per pass
-    const int sub = tid & 7, rr = tid >> 3;
-#pragma unroll
-    for (int pass = 0; pass < R / 32; ++pass) {
-      const int row = rr + 32 * pass, rg = r0 + row, kc = k0 + 8 * sub;
-      float x8[8];
-      if (rg < rows) {
-        const float4* src = reinterpret_cast<const float4*>(X + (long long)rg * ld + kc);
-        const float4 q0 = __ldg(src), q1 = __ldg(src + 1);
-        x8[0] = q0.x; x8[1] = q0.y; x8[2] = q0.z; x8[3] = q0.w;
-        x8[4] = q1.x; x8[5] = q1.y; x8[6] = q1.z; x8[7] = q1.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) x8[e] = 0.f;
-      }
-      if (tri) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-          if (tri == 1 ? kc + e > rg : kc + e < rg) x8[e] = 0.f;
-      }
-      uint4 t0, t1, t2;
-      split8(x8, t0, t1, t2);
-      const uint32_t off = sw128_off(row, sub);
-      *reinterpret_cast<uint4*>(dst + off) = t0;
-      *reinterpret_cast<uint4*>(dst + R * 128 + off) = t1;
-      *reinterpret_cast<uint4*>(dst + 2 * R * 128 + off) = t2;
-    }
-    return;
-  }
-  // K-strided rows (X[k][m]): consecutive lanes take consecutive rows m, so
-  // every load instruction reads a contiguous run of one k row
-  constexpr int kPer = R * kTcBK / kThreads;          // k values per thread: 32 (R=128) or 16
-  const int row = tid % R, kb = (tid / R) * kPer;
-  const int rg = r0 + row;
-  const bool live = rg < rows;
-#pragma unroll
-  for (int c = 0; c < kPer / 8; ++c) {
-    const int kc = k0 + kb + 8 * c;          // first k of this run
-    float x8[8];
-    if (live) {
-      const float* src = X + (long long)kc * ld + rg;
-#pragma unroll
-      for (int e = 0; e < 8; ++e) x8[e] = __ldg(src + (long long)e * ld);
+struct StageMap {
+  static constexpr int kPer = R * kTcBK / kThreads;   // 32 (R = 128) or 16 (R = 64)
+  __device__ __forceinline__ static void at(int km, int c, int& row, int& kc) {
+    const int tid = threadIdx.x;
+    if (km == 0) {
+      row = (tid >> 3) + 32 * c;
+      kc = 8 * (tid & 7);
     } else {
-#pragma unroll
-      for (int e = 0; e < 8; ++e) x8[e] = 0.f;
+      row = tid % R;
+      kc = (tid / R) * kPer + 8 * c;
     }
-    if (tri) {
+  }
+};
+
+template <int R>
+__device__ __forceinline__ void load_operand(float (&v)[StageMap<R>::kPer], const float* X,
+                                             long long ld, int km, int r0, int rows, int k0) {
+  constexpr int kRuns = StageMap<R>::kPer / 8;
 #pragma unroll
-      for (int e = 0; e < 8; ++e)
-        if (tri == 1 ? kc + e > rg : kc + e < rg) x8[e] = 0.f;
+  for (int c = 0; c < kRuns; ++c) {
+    int row, kc;
+    StageMap<R>::at(km, c, row, kc);
+    const int rg = r0 + row;
+    if (rg >= rows) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[8 * c + e] = 0.f;
+    } else if (km == 0) {
+      const float4* src = reinterpret_cast<const float4*>(X + (long long)rg * ld + k0 + kc);
+      const float4 q0 = __ldg(src), q1 = __ldg(src + 1);
+      v[8 * c + 0] = q0.x; v[8 * c + 1] = q0.y; v[8 * c + 2] = q0.z; v[8 * c + 3] = q0.w;
+      v[8 * c + 4] = q1.x; v[8 * c + 5] = q1.y; v[8 * c + 6] = q1.z; v[8 * c + 7] = q1.w;
+    } else {
+      const float* src = X + (long long)(k0 + kc) * ld + rg;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[8 * c + e] = __ldg(src + (long long)e * ld);
+    }
+  }
+}
+
+// tri = 1 reads op(X)[r][k] as zero for k > r0 + r, tri = 2 for k < r0 + r
+// (a triangular operand whose other triangle holds other data).
+template <int R>
+__device__ __forceinline__ void store_operand(unsigned char* dst, const float (&v)[StageMap<R>::kPer],
+                                              int km, int r0, int k0, int tri) {
+  constexpr int kRuns = StageMap<R>::kPer / 8;
+#pragma unroll
+  for (int c = 0; c < kRuns; ++c) {
+    int row, kc;
+    StageMap<R>::at(km, c, row, kc);
+    const int rg = r0 + row;
+    float x8[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = k0 + kc + e;
+      x8[e] = (tri == 1 && k > rg) || (tri == 2 && k < rg) ? 0.f : v[8 * c + e];
     }
     uint4 t0, t1, t2;
     split8(x8, t0, t1, t2);
-    const uint32_t off = sw128_off(row, kb / 8 + c);
+    const uint32_t off = sw128_off(row, kc / 8);
     *reinterpret_cast<uint4*>(dst + off) = t0;
     *reinterpret_cast<uint4*>(dst + R * 128 + off) = t1;
     *reinterpret_cast<uint4*>(dst + 2 * R * 128 + off) = t2;
@@ -288,8 +296,13 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const TcProblem* p
       if (!mbar_wait(smem_u32(&s_bar[st]), (uint32_t)((c / kStages - 1) & 1))) s_fail = 1;
     }
     const int k0 = kbeg + c * kTcBK;
-    stage_operand<kTcBM>(sa, pb.A, pb.lda, pb.a_km, m0, pb.M, k0, pb.k_to_m ? 1 : 0);
-    stage_operand<kTcBN>(sb, pb.B, pb.ldb, pb.b_kn, n0, pb.N, k0, pb.k_from_n ? 2 : 0);
+    {
+      float va[StageMap<kTcBM>::kPer], vb[StageMap<kTcBN>::kPer];
+      load_operand<kTcBM>(va, pb.A, pb.lda, pb.a_km, m0, pb.M, k0);
+      load_operand<kTcBN>(vb, pb.B, pb.ldb, pb.b_kn, n0, pb.N, k0);
+      store_operand<kTcBM>(sa, va, pb.a_km, m0, k0, pb.k_to_m ? 1 : 0);
+      store_operand<kTcBN>(sb, vb, pb.b_kn, n0, k0, pb.k_from_n ? 2 : 0);
+    }
     fence_proxy_async();
     __syncthreads();
     if (s_fail) break;   // uniform after the barrier
