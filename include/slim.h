@@ -287,6 +287,25 @@ slim_status slim_set_x(slim_ctx* ctx, const void* x, size_t n, int dtype, int on
  * Synchronises. */
 slim_status slim_set_c_diag(slim_ctx* ctx, const void* c, size_t n, int dtype, int on_device);
 
+/* slimTik (Eq. slimTik) with C_k = L^T L for a lower-bidiagonal L on the
+ * image vector: (L x)_i = d0_i x_i + d1_i x_{i-1} (d1_0 unused), e.g. the
+ * first difference along the image rows plus a multiple of the identity.  L
+ * must be invertible (every d0_i nonzero and finite; SLIM_EINVAL otherwise).
+ * The Woodbury form keeps a p x p system with W = C^{-1} = L^{-1} L^{-T}:
+ *   (mu_k I + M_k W M_k^T) z = c - (beta/mu_k) M_k x_{k-1},
+ *   x_k = (1 - eta beta/mu_k) x_{k-1} - eta W M_k^T z
+ * (with tik_lambda = 0: slimLS with this C_k, beta = 0).  Each step applies W
+ * to the new block's ell rows and to M_k^T z; W v is two first-order
+ * recurrences (L^T t = v backward, L u = t forward), each a chunked affine
+ * scan in one thread block.  d0, d1: n values each (host, or device with
+ * on_device = 1), copied; d1 may be NULL (L diagonal); d0 = NULL restores
+ * C_k = I.  Replaces a diagonal C_k of slim_set_c_diag (and is replaced by
+ * one).  2D view blocks, rows from the projector, FP64 or MIXED solver,
+ * lookahead 0 (SLIM_ENOTSUP otherwise).  The memory of the steps taken so far
+ * is rebuilt.  Synchronises. */
+slim_status slim_set_tik_bidiag(slim_ctx* ctx, const double* d0, const double* d1, size_t n,
+                                int on_device);
+
 /* Failure detection self-test: runs a grid barrier (the bounded wait of the
  * cooperative solvers) that one of its two CTAs never reaches, on
  * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream), and

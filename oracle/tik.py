@@ -25,7 +25,8 @@ telescope to the Tikhonov solution.  Both readings are offered
 Two forms of the step s_k (x_k = x_{k-1} - eta s_k):
 
   direct     the n x n system above as written, any invertible L (small n);
-  Woodbury   L = diag(l), P = L^T L, W = P^{-1} = diag(1/l^2):
+  Woodbury   L = diag(l), P = L^T L, W = P^{-1} = diag(1/l^2) (step_woodbury;
+             step_woodbury_general takes any invertible L, with W dense):
                  (mu_k I_p + M_k W M_k^T) z = c - (beta/mu_k) M_k x_{k-1},
                  s_k = (beta/mu_k) x_{k-1} + W M_k^T z,
              c = [0; ...; 0; r_k] (r_k = A_k x_{k-1} - b_k in the rows of the
@@ -106,6 +107,35 @@ def step_woodbury(x_prev, blocks, b_new, lam_k: float, lam_tik: float, n_blocks:
     K = mu * np.eye(p) + (MW @ M.T).toarray()
     z = sla.cho_solve(sla.cho_factor(K, lower=True), c - (beta / mu) * (M @ x_prev))
     s = (beta / mu) * x_prev + MW.T @ z
+    return x_prev - eta * s, r_k, s, z
+
+
+def bidiagonal(d0, d1) -> sp.csr_matrix:
+    """L with (L x)_i = d0_i x_i + d1_i x_{i-1} (d1_0 unused): lower bidiagonal."""
+    d0 = np.asarray(d0, dtype=np.float64)
+    d1 = np.asarray(d1, dtype=np.float64)
+    return sp.diags([d0, d1[1:]], [0, -1], format="csr")
+
+
+def step_woodbury_general(x_prev, blocks, b_new, lam_k: float, lam_tik: float, n_blocks: int,
+                          count: int, L, eta: float = 1.0):
+    """The Woodbury form with any invertible L, W = (L^T L)^{-1} formed densely
+    (small n): (mu I + M W M^T) z = c - (beta/mu) M x, s = (beta/mu) x + W M^T z.
+    Returns (x_k, r_k, s_k, z)."""
+    M, A_k = _stack(blocks)
+    L = L.toarray() if sp.issparse(L) else np.asarray(L, dtype=np.float64)
+    n = L.shape[0]
+    W = sla.cho_solve(sla.cho_factor(L.T @ L, lower=True), np.eye(n))
+    beta = lam_tik * lam_tik / n_blocks
+    mu = shift(lam_k, lam_tik, n_blocks, count)
+    ell, p = A_k.shape[0], M.shape[0]
+    r_k = A_k @ x_prev - b_new
+    c = np.zeros(p)
+    c[p - ell:] = r_k
+    Md = M.toarray()
+    K = mu * np.eye(p) + Md @ W @ Md.T
+    z = sla.cho_solve(sla.cho_factor(K, lower=True), c - (beta / mu) * (Md @ x_prev))
+    s = (beta / mu) * x_prev + W @ (Md.T @ z)
     return x_prev - eta * s, r_k, s, z
 
 

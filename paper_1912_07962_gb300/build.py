@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libslim.so")
 SOURCES = [
     "slim_capi.cu", "slim_kernels.cu", "slim_chol.cu", "slim_noalloc.cu", "slim_rays.cu",
     "slim_lookahead.cu", "slim_unet.cu", "slim_lsqr.cu", "slim_olbfgs.cu", "slim_frames.cu", "slim_selftest.cu",
-    "slim_tc.cu",
+    "slim_tc.cu", "slim_tikl.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -16,6 +16,7 @@
 #include "slim_unet.cuh"
 #include "slim_rays.cuh"
 #include "slim_tc.cuh"
+#include "slim_tikl.cuh"
 
 using namespace slim;
 
@@ -60,6 +61,12 @@ struct slim_ctx {
   double tik_lambda = 0.0;         // slimTik: lam_tik of Eq. (TLS1) (0: slimLS)
   int tik_reading = 0;             // count of Tikhonov rows: 0 blocks of M_k, 1 r
   double* d_cinv = nullptr;        // [n] 1/c of C_k = diag(c); null: C_k = I
+  // slimTik with a lower-bidiagonal L (slim_set_tik_bidiag); null: C_k = I or diagonal
+  double* d_tl_d0inv = nullptr;    // [n] 1 / d0
+  double* d_tl_d1 = nullptr;       // [n]
+  double* d_tl_U = nullptr;        // [ell * n] W a_i^T of the new block's rows
+  double* d_tl_UT = nullptr;       // [n * ell]
+  double* d_tl_v = nullptr;        // [n]
   int cyclic = 0;                  // view blocks in the random cyclic order
   int distinct = 0;                // random-ray blocks of distinct rays (Floyd)
   int* d_perm = nullptr;           // [n_views] the current epoch's permutation (cyclic)
@@ -342,7 +349,10 @@ int kernels_per_step(const slim_ctx* c) {
   const int per_solve = c->plan.cluster ? 1 : 2;
   const int tik = c->tik_lambda > 0.0 ? 2 : 0;   // window projection, x scale
   const int mirror = c->general3d ? 1 : 0;       // the Gram's mirrored block
-  return 5 + per_solve * solves + refine + 1 + tik + mirror;
+  // bidiagonal L: the Gram is rows W a_i, a transpose and the products (3);
+  // the update M^T z, W v and the axpy (3) instead of the scatter
+  const int tikl = c->d_tl_d0inv ? 4 : 0;
+  return 5 + per_solve * solves + refine + 1 + tik + mirror + tikl;
 }
 
 // The damped solve (lambda_k I + G) z = rhs: float64 tiled Cholesky, or a
@@ -449,6 +459,10 @@ LsqrArgs<T> make_lsqr_args(slim_ctx* c) {
   return l;
 }
 
+TiklArgs make_tikl_args(const slim_ctx* c) {
+  return TiklArgs{c->d_tl_d0inv, c->d_tl_d1, c->d_tl_U, c->d_tl_UT, c->d_tl_v};
+}
+
 template <typename T>
 cudaError_t enqueue_step_t(slim_ctx* c) {
   if (c->kind != SLIM_BLOCKS_VIEWS) return enqueue_ray_step_t<T>(c);
@@ -512,12 +526,25 @@ cudaError_t enqueue_step_t(slim_ctx* c) {
   // slimTik: rhs c - (beta/mu_k) M_k x_{k-1}
   if (tik && (e = launch_tik_rhs<T>(a, c->stream)) != cudaSuccess) return e;
   if ((e = mark(c, kPhForward)) != cudaSuccess) return e;
-  if ((e = launch_gram_update<T>(a, c->stream)) != cudaSuccess) return e;
+  const bool tikl = c->d_tl_d0inv != nullptr;
+  if (tikl) {
+    // G = M W M^T with W = (L^T L)^{-1}: rows W a_i^T of the new block first
+    if ((e = launch_tikl_gram<T>(a, make_tikl_args(c), c->stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int), c->stream)) !=
+        cudaSuccess)
+      return e;
+  } else if ((e = launch_gram_update<T>(a, c->stream)) != cudaSuccess) {
+    return e;
+  }
   if ((e = mark(c, kPhGram)) != cudaSuccess) return e;
   if ((e = enqueue_solve(c)) != cudaSuccess) return e;
   if ((e = mark(c, kPhSolve)) != cudaSuccess) return e;
   if (tik && (e = launch_tik_scale<T>(a, c->stream)) != cudaSuccess) return e;
-  if ((e = launch_scatter<T>(a, c->stream)) != cudaSuccess) return e;
+  if (tikl)
+    e = launch_tikl_update<T>(a, make_tikl_args(c), c->stream);
+  else
+    e = launch_scatter<T>(a, c->stream);
+  if (e != cudaSuccess) return e;
   return mark(c, kPhScatter);
 }
 
@@ -569,7 +596,11 @@ cudaError_t rebuild_t(slim_ctx* c, long long k) {
     }
     if ((e = launch_sample<T>(a, s)) != cudaSuccess) return e;
     if ((e = launch_forward_residual<T>(a, s)) != cudaSuccess) return e;
-    if (c->d_G && (e = launch_gram_update<T>(a, s)) != cudaSuccess) return e;
+    if (c->d_G && c->d_tl_d0inv) {
+      if ((e = launch_tikl_gram<T>(a, make_tikl_args(c), s)) != cudaSuccess) return e;
+    } else if (c->d_G && (e = launch_gram_update<T>(a, s)) != cudaSuccess) {
+      return e;
+    }
     if ((e = cudaMemsetAsync(c->d_map_ray, 0xFF, 2 * (size_t)c->n * sizeof(int), s)) !=
         cudaSuccess)
       return e;
@@ -607,7 +638,8 @@ void free_all(slim_ctx* c) {
                   c->d_ring_ids, c->d_ring_pix, c->d_ring_w, c->d_map_ray, c->d_map_w,
                   c->d_G, c->d_L, c->d_rhs, c->d_z, c->d_dz, c->d_res, c->d_ref, c->d_err,
                   c->d_lsqr, c->d_lsqr_bar, c->d_cinv, c->d_olb, c->d_olb_state,
-                  c->d_frames, c->d_vnext, c->d_cinvh, c->d_perm, c->d_perm_epoch};
+                  c->d_frames, c->d_vnext, c->d_cinvh, c->d_perm, c->d_perm_epoch,
+                  c->d_tl_d0inv, c->d_tl_d1, c->d_tl_U, c->d_tl_UT, c->d_tl_v};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   chol_plan_destroy(&c->plan);
@@ -1426,6 +1458,60 @@ slim_status slim_set_x(slim_ctx* c, const void* x, size_t n, int dtype, int on_d
   return SLIM_OK;
 }
 
+slim_status slim_set_tik_bidiag(slim_ctx* c, const double* d0, const double* d1, size_t n,
+                                int on_device) {
+  if (!c || (d0 && (long long)n != c->n)) return fail(c, SLIM_EINVAL, "set_tik_bidiag: bad arguments");
+  if (c->kind != SLIM_BLOCKS_VIEWS || c->dim != 2 || c->lookahead != 0 || c->a_mode != 0 ||
+      (c->solver != SLIM_SOLVE_FP64 && c->solver != SLIM_SOLVE_MIXED))
+    return fail(c, SLIM_ENOTSUP,
+                "set_tik_bidiag: 2D view blocks, rows from the projector, Woodbury form "
+                "(FP64 or MIXED solver), lookahead 0");
+  CK(cudaStreamSynchronize(c->stream), "set_tik_bidiag");
+  const size_t nn = (size_t)c->n;
+  std::vector<double> h0, h1;
+  if (d0) {   // read and check the new L before anything changes
+    h0.resize(nn);
+    h1.assign(nn, 0.0);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    CK(cudaMemcpy(h0.data(), d0, nn * sizeof(double), kind), "set_tik_bidiag");
+    if (d1) CK(cudaMemcpy(h1.data(), d1, nn * sizeof(double), kind), "set_tik_bidiag");
+    for (size_t i = 0; i < nn; ++i) {
+      if (!(h0[i] != 0.0) || !std::isfinite(h0[i]) || !std::isfinite(h1[i]))
+        return fail(c, SLIM_EINVAL, "set_tik_bidiag: L must be invertible (d0 != 0, finite)");
+      h0[i] = 1.0 / h0[i];
+    }
+    h1[0] = 0.0;
+  }
+  double** bufs[] = {&c->d_tl_d0inv, &c->d_tl_d1, &c->d_tl_U, &c->d_tl_UT, &c->d_tl_v};
+  for (double** b : bufs) {
+    if (*b) CK(cudaFree(*b), "set_tik_bidiag");
+    *b = nullptr;
+  }
+  if (d0) {
+    // a diagonal C_k set before is replaced
+    if (c->d_cinv) CK(cudaFree(c->d_cinv), "set_tik_bidiag");
+    if (c->d_cinvh) CK(cudaFree(c->d_cinvh), "set_tik_bidiag");
+    c->d_cinv = c->d_cinvh = nullptr;
+    CK(cudaMalloc(&c->d_tl_d0inv, nn * sizeof(double)), "cudaMalloc");
+    CK(cudaMalloc(&c->d_tl_d1, nn * sizeof(double)), "cudaMalloc");
+    CK(cudaMalloc(&c->d_tl_U, (size_t)c->ell * nn * sizeof(double)), "cudaMalloc");
+    CK(cudaMalloc(&c->d_tl_UT, (size_t)c->ell * nn * sizeof(double)), "cudaMalloc");
+    CK(cudaMalloc(&c->d_tl_v, nn * sizeof(double)), "cudaMalloc");
+    CK(cudaMemcpy(c->d_tl_d0inv, h0.data(), nn * sizeof(double), cudaMemcpyHostToDevice),
+       "set_tik_bidiag");
+    CK(cudaMemcpy(c->d_tl_d1, h1.data(), nn * sizeof(double), cudaMemcpyHostToDevice),
+       "set_tik_bidiag");
+  }
+  // the captured step and the retained Gram entries used the previous C_k
+  drop_graph(c);
+  if (c->h_k > 0) {
+    cudaError_t e = c->precision == SLIM_PREC_FP32 ? rebuild_t<float>(c, c->h_k)
+                                                   : rebuild_t<double>(c, c->h_k);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_tik_bidiag");
+  }
+  return read_status(c);
+}
+
 slim_status slim_set_c_diag(slim_ctx* c, const void* cdiag, size_t n, int dtype, int on_device) {
   if (!c || (cdiag && ((long long)n != c->n || (dtype != SLIM_F32 && dtype != SLIM_F64))))
     return fail(c, SLIM_EINVAL, "set_c_diag: bad arguments");
@@ -1433,6 +1519,13 @@ slim_status slim_set_c_diag(slim_ctx* c, const void* cdiag, size_t n, int dtype,
       (c->solver != SLIM_SOLVE_FP64 && !is_mixed(c) && c->solver != SLIM_SOLVE_LSQR))
     return fail(c, SLIM_ENOTSUP, "set_c_diag: 2D view blocks, Woodbury or LSQR form");
   CK(c->lookahead ? la_sync_all(c) : cudaStreamSynchronize(c->stream), "set_c_diag");
+  {   // a bidiagonal L set before is replaced
+    double** bufs[] = {&c->d_tl_d0inv, &c->d_tl_d1, &c->d_tl_U, &c->d_tl_UT, &c->d_tl_v};
+    for (double** b : bufs) {
+      if (*b) CK(cudaFree(*b), "set_c_diag");
+      *b = nullptr;
+    }
+  }
   if (!cdiag) {
     if (c->d_cinv) CK(cudaFree(c->d_cinv), "set_c_diag");
     if (c->d_cinvh) CK(cudaFree(c->d_cinvh), "set_c_diag");

@@ -39,6 +39,7 @@ EXPORTS = [
     "slim_warm_start", "slim_backproject_data", "slim_unet_conv3x3", "slim_unet_conv3x3_grad",
     "slim_unet_tconv2x2", "slim_unet_tconv2x2_grad", "slim_get_lsqr_info", "slim_set_c_diag",
     "slim_selftest_wait", "slim_join_stream", "slim_tc_matmul", "slim_chol_inverse",
+    "slim_set_tik_bidiag",
 ]
 A_MATRIX_FREE, A_CSR_F32, A_CSR_BF16 = 0, 1, 2
 NOALLOC_MAX_P = 1024
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "slim_tc_matmul": ([I, I, I, VP, LL, I, VP, LL, I, VP, LL, I, C.c_float, C.c_float, I, I,
                             VP], I),
         "slim_chol_inverse": ([VP, I, D, VP, VP], I),
+        "slim_set_tik_bidiag": ([VP, VP, VP, SZ, I], I),
         "slim_set_ref": ([VP, VP, SZ, I, I], I),
         "slim_run": ([VP, LL, D, I, P(LL), P(D), P(D)], I),
         "slim_get_iter": ([VP, P(LL)], I),
@@ -232,6 +234,18 @@ class Slim:
         it, res, res0 = C.c_int(), C.c_double(), C.c_double()
         self._check(self._lib.slim_get_lsqr_info(self.h, C.byref(it), C.byref(res), C.byref(res0)))
         return it.value, res.value, res0.value
+
+    def set_tik_bidiag(self, d0, d1=None):
+        """C_k = L^T L with L lower bidiagonal on the image vector, (L x)_i =
+        d0_i x_i + d1_i x_{i-1}; None restores C_k = I (host arrays, copied)."""
+        if d0 is None:
+            self._check(self._lib.slim_set_tik_bidiag(self.h, None, None, 0, 0))
+            return
+        a0 = np.ascontiguousarray(d0, dtype=np.float64)
+        a1 = None if d1 is None else np.ascontiguousarray(d1, dtype=np.float64)
+        self._check(self._lib.slim_set_tik_bidiag(
+            self.h, a0.ctypes.data_as(C.c_void_p),
+            None if a1 is None else a1.ctypes.data_as(C.c_void_p), a0.size, 0))
 
     def set_c_diag(self, c):
         """C_k = diag(c) of Eq. (B_k) (c > 0; slimTik: L^T L with L = diag(sqrt c)).

@@ -213,3 +213,42 @@ def test_planted_mutations_break_the_pins(monkeypatch):
     # the count fixed at r+1 in the growing window
     monkeypatch.setattr(tik, "window_count", lambda k, r, reading="window": r + 1)
     assert worst() > 1e-4
+
+
+def _bidiag(n, N, seed):
+    # the first difference along the image rows plus a multiple of the identity
+    rs = np.random.default_rng(seed)
+    d0 = 1.0 + 0.5 * rs.random(n)
+    d1 = -0.8 * (0.5 + 0.5 * rs.random(n))
+    d1[::N] = 0.0                      # no coupling across image rows
+    return d0, d1
+
+
+def test_bidiagonal_matrix_is_the_stated_operator():
+    g, A, b = _tiny_tomo()
+    d0, d1 = _bidiag(g.n, g.N, 1)
+    L = tik.bidiagonal(d0, d1).toarray()
+    x = np.random.default_rng(2).standard_normal(g.n)
+    want = d0 * x + d1 * np.concatenate([[0.0], x[:-1]])
+    assert np.allclose(L @ x, want, rtol=0, atol=1e-15)
+    assert np.allclose(np.triu(L, 1), 0) and np.allclose(np.tril(L, -2), 0)
+
+
+@pytest.mark.parametrize("lam_tik", [0.0, 0.7])
+def test_general_woodbury_equals_direct(lam_tik):
+    # the Woodbury algebra with W = (L^T L)^{-1} for a non-diagonal L, step by
+    # step against Eq. (slimTik) as written
+    g, A, b = _tiny_tomo()
+    src = slim.tomo_source(g, b)
+    r, lam = 2, 1e-2
+    L = tik.bidiagonal(*_bidiag(g.n, g.N, 3))
+    x = np.random.default_rng(5).standard_normal(g.n) * 0.1
+    mem = []
+    for k, ids in enumerate(slim.view_schedule(g, 4, 7), start=1):
+        mem = (mem + [src.rows(ids)])[-(r + 1):]
+        cnt = tik.window_count(k, r)
+        xd, *_ = tik.step_direct(x, mem, src.rhs(ids), lam, lam_tik, g.n_views, cnt, L, 0.9)
+        xw, *_ = tik.step_woodbury_general(x, mem, src.rhs(ids), lam, lam_tik, g.n_views, cnt, L,
+                                          0.9)
+        assert np.linalg.norm(xw - xd) <= 1e-10 * np.linalg.norm(xd), k
+        x = xd
