@@ -700,11 +700,12 @@ def batch_block(sl, flush, stream, K, W, count=96):
     import torch
     cfgs = workloads.batch_mix(count)
     t0 = time.perf_counter()
-    specs, choices = [], {}
+    specs, choices, alone_ms = [], {}, 0.0
     for c in cfgs:
         sp = dict(N=c.N, n_views=c.n_views, det=c.det, ell=c.ell, r=c.r, lam=c.lam, seed=c.seed,
                   kind=sl.SLIM_BLOCKS_RAYS, precision=sl.SLIM_PREC_FP32, solver=sl.SLIM_SOLVE_MIXED)
-        tile, cps, _ = sl.autotune(sp, steps=3)
+        tile, cps, ms = sl.autotune(sp, steps=3)
+        alone_ms += ms
         sp.update(tile=tile, ctas_per_sm=cps)
         choices[f"{tile}x{cps}"] = choices.get(f"{tile}x{cps}", 0) + 1
         specs.append(sp)
@@ -748,6 +749,9 @@ def batch_block(sl, flush, stream, K, W, count=96):
             "rows_per_s": rows * K / t, "ms_per_step": t / K * 1e3, "rows_per_step": rows,
             "steps": K, "warmup": W, "factor_flops_per_step": flops,
             "factor_tflops_if_all_time": flops / (t / K) / 1e12,
+            # the autotuner's best step time of each problem run alone, summed:
+            # the step of the batch if the problems ran one after another
+            "one_by_one_ms_per_step": alone_ms,
             "autotune": {"choices_tile_x_ctas": choices, "seconds": tune_s}}
 
 
@@ -1170,6 +1174,18 @@ def main_frames(args):
                                                              max(1, args.frames_steps), 3)}))
 
 
+def main_batch(args):
+    """The batched block alone (one JSON line)."""
+    import torch
+    from paper_1912_07962_gb300 import build as slbuild, slim as sl
+    slbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    print(json.dumps({"batched": batch_block(sl, flush, stream, max(1, args.batch_steps),
+                                             max(3, args.warmup))}))
+
+
 def main_tik(args):
     """slimTik against slimLS alone (one JSON line)."""
     import torch
@@ -1270,6 +1286,8 @@ def main():
                     help="steps the geometry chain runs ahead in the chosen form (0: one chain)")
     ap.add_argument("--batch-steps", type=int, default=5,
                     help="timed steps of the 96-problem batched block (0: skip it)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched block and print that line")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-steps", type=int, default=0)
     ap.add_argument("--cpu-warmup", type=int, default=6)
@@ -1296,6 +1314,8 @@ def main():
         main_sens(args)
     elif args.frames_only:
         main_frames(args)
+    elif args.batch_only:
+        main_batch(args)
     else:
         main_gpu(args)
 

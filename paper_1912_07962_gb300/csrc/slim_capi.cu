@@ -67,6 +67,10 @@ struct slim_ctx {
   double* d_tl_U = nullptr;        // [ell * n] W a_i^T of the new block's rows
   double* d_tl_UT = nullptr;       // [n * ell]
   double* d_tl_v = nullptr;        // [n]
+  // capture stage of a batch step: 0 the whole step; 1 up to K = lambda I + G
+  // (the batch factors every problem in one merged launch); 2 from the
+  // solves on
+  int stage = 0;
   int cyclic = 0;                  // view blocks in the random cyclic order
   int distinct = 0;                // random-ray blocks of distinct rays (Floyd)
   int* d_perm = nullptr;           // [n_views] the current epoch's permutation (cyclic)
@@ -275,6 +279,7 @@ RayArgs make_ray_args(slim_ctx* c) {
   a.r = c->r;
   a.p = c->p;
   a.taps = c->taps;
+  a.magic_n = c->N > 1 ? (unsigned)((0x100000000ull + c->N - 1) / c->N) : 0xFFFFFFFFu;
   a.kind = c->kind;
   a.steps_per_view = c->steps_per_view;
   a.seed = c->seed;
@@ -360,19 +365,18 @@ int kernels_per_step(const slim_ctx* c) {
 cudaError_t enqueue_solve(slim_ctx* c) {
   cudaStream_t s = c->stream;
   cudaError_t e;
-  if (c->solver == SLIM_SOLVE_FP64) {
-    if ((e = launch_form_k<double>(c->d_info, c->d_G, (double*)c->d_L, c->P, s)) != cudaSuccess)
-      return e;
+  if (c->stage != 2) {
+    e = c->solver == SLIM_SOLVE_FP64
+            ? launch_form_k<double>(c->d_info, c->d_G, (double*)c->d_L, c->P, s)
+            : launch_form_k<float>(c->d_info, c->d_G, (float*)c->d_L, c->P, s);
+    if (e != cudaSuccess) return e;
     if ((e = mark(c, kPhFormK)) != cudaSuccess) return e;
-    if ((e = chol_factor(c->plan, c->d_L, c->d_status, s)) != cudaSuccess) return e;
-    if ((e = mark(c, kPhFactor)) != cudaSuccess) return e;
-    return chol_solve(c->plan, c->d_L, c->d_rhs, c->d_z, c->d_status, s);
   }
-  if ((e = launch_form_k<float>(c->d_info, c->d_G, (float*)c->d_L, c->P, s)) != cudaSuccess)
-    return e;
-  if ((e = mark(c, kPhFormK)) != cudaSuccess) return e;
-  if ((e = chol_factor(c->plan, c->d_L, c->d_status, s)) != cudaSuccess) return e;
+  if (c->stage == 1) return cudaSuccess;   // the batch factors between its stages
+  if (c->stage == 0 && (e = chol_factor(c->plan, c->d_L, c->d_status, s)) != cudaSuccess) return e;
   if ((e = mark(c, kPhFactor)) != cudaSuccess) return e;
+  if (c->solver == SLIM_SOLVE_FP64)
+    return chol_solve(c->plan, c->d_L, c->d_rhs, c->d_z, c->d_status, s);
   if ((e = chol_solve(c->plan, c->d_L, c->d_rhs, c->d_z, c->d_status, s)) != cudaSuccess) return e;
   for (int it = 0; it < c->refine_iters; ++it) {
     if ((e = launch_refine_residual(c->d_info, c->d_G, c->d_z, c->d_rhs, c->d_res, c->P, s)) !=
@@ -394,6 +398,14 @@ cudaError_t enqueue_ray_step_t(slim_ctx* c) {
   a.map_ray = nullptr;
   cudaStream_t s = c->stream;
   cudaError_t e;
+  if (c->stage == 2) {   // a batch's second stage: the part after the factor
+    if (c->dim == 3 && !c->general3d) return cudaSuccess;   // no tiled factor: all in stage 1
+    if (c->general3d) a.map_ray = c->d_map_ray;
+    if ((e = enqueue_solve(c)) != cudaSuccess) return e;
+    if ((e = mark(c, kPhSolve)) != cudaSuccess) return e;
+    if ((e = launch_scatter<T>(a, s)) != cudaSuccess) return e;
+    return mark(c, kPhScatter);
+  }
   if ((e = mark(c, 0)) != cudaSuccess) return e;
   if ((e = launch_sample_rays<T>(ra, s)) != cudaSuccess) return e;
   if ((e = mark(c, kPhSample)) != cudaSuccess) return e;
@@ -408,6 +420,7 @@ cudaError_t enqueue_ray_step_t(slim_ctx* c) {
     if ((e = launch_gram_frames(ra, fa, s)) != cudaSuccess) return e;
     if ((e = mark(c, kPhGram)) != cudaSuccess) return e;
     if ((e = enqueue_solve(c)) != cudaSuccess) return e;
+    if (c->stage == 1) return cudaSuccess;
     if ((e = mark(c, kPhSolve)) != cudaSuccess) return e;
     if ((e = launch_scatter<T>(a, s)) != cudaSuccess) return e;
     return mark(c, kPhScatter);
@@ -418,6 +431,7 @@ cudaError_t enqueue_ray_step_t(slim_ctx* c) {
     if ((e = launch_gram_pairs(ra, s)) != cudaSuccess) return e;
     if ((e = mark(c, kPhGram)) != cudaSuccess) return e;
     if ((e = enqueue_solve(c)) != cudaSuccess) return e;
+    if (c->stage == 1) return cudaSuccess;
   } else {
     if ((e = launch_slice_collect(ra, s)) != cudaSuccess) return e;
     if ((e = mark(c, kPhGram)) != cudaSuccess) return e;
@@ -518,15 +532,16 @@ cudaError_t enqueue_step_t(slim_ctx* c) {
     }
     return mark(c, kPhScatter);
   }
+  const bool tik = c->tik_lambda > 0.0;
+  const bool tikl = c->d_tl_d0inv != nullptr;
+  if (c->stage == 2) goto solves;   // a batch's second stage: the part after the factor
   if ((e = mark(c, 0)) != cudaSuccess) return e;
   if ((e = launch_sample<T>(a, c->stream)) != cudaSuccess) return e;
   if ((e = mark(c, kPhSample)) != cudaSuccess) return e;
   if ((e = launch_forward_residual<T>(a, c->stream)) != cudaSuccess) return e;
-  const bool tik = c->tik_lambda > 0.0;
   // slimTik: rhs c - (beta/mu_k) M_k x_{k-1}
   if (tik && (e = launch_tik_rhs<T>(a, c->stream)) != cudaSuccess) return e;
   if ((e = mark(c, kPhForward)) != cudaSuccess) return e;
-  const bool tikl = c->d_tl_d0inv != nullptr;
   if (tikl) {
     // G = M W M^T with W = (L^T L)^{-1}: rows W a_i^T of the new block first
     if ((e = launch_tikl_gram<T>(a, make_tikl_args(c), c->stream)) != cudaSuccess) return e;
@@ -537,7 +552,9 @@ cudaError_t enqueue_step_t(slim_ctx* c) {
     return e;
   }
   if ((e = mark(c, kPhGram)) != cudaSuccess) return e;
+solves:
   if ((e = enqueue_solve(c)) != cudaSuccess) return e;
+  if (c->stage == 1) return cudaSuccess;
   if ((e = mark(c, kPhSolve)) != cudaSuccess) return e;
   if (tik && (e = launch_tik_scale<T>(a, c->stream)) != cudaSuccess) return e;
   if (tikl)
@@ -2270,8 +2287,11 @@ extern "C" slim_status slim_autotune(const slim_geometry* geom, const slim_block
 
 struct slim_batch {
   std::vector<slim_ctx*> ctx;
-  std::vector<cudaEvent_t> join;
-  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join, join2;
+  cudaEvent_t fork = nullptr, fork2 = nullptr;
+  // the problems' tiled factorisations, one merged persistent launch per
+  // factor precision and tile size
+  std::vector<slim::CholBatch> groups;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaGraph_t graph = nullptr;
@@ -2294,7 +2314,11 @@ extern "C" void slim_batch_destroy(slim_batch* b) {
   for (slim_ctx* c : b->ctx) slim_destroy(c);
   for (cudaEvent_t e : b->join)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->join2)
+    if (e) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->fork2) cudaEventDestroy(b->fork2);
+  for (slim::CholBatch& g : b->groups) slim::chol_batch_destroy(&g);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -2328,28 +2352,43 @@ extern "C" slim_status slim_batch_create(int count, const slim_geometry* geoms,
       return SLIM_ECUDA;
     }
     b->join.push_back(e);
+    e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      slim_batch_destroy(b);
+      return SLIM_ECUDA;
+    }
+    b->join2.push_back(e);
   }
   if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork2, cudaEventDisableTiming) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
     slim_batch_destroy(b);
     return SLIM_ECUDA;
   }
   b->own_stream = true;
-  // Share the GPU between the problems' factorisations: each problem gets
-  // persistent CTAs in proportion to its factorisation work (p^3) out of two
-  // per SM, instead of CTAs on every SM for each (any grid is correct: tasks
-  // are claimed by ticket).
-  double work = 0.0;
-  for (slim_ctx* c : b->ctx)
-    if (c->plan.grid > 0) work += (double)c->p * c->p * c->p;
-  if (work > 0.0 && b->ctx.size() > 1) {
-    const double slots = 2.0 * b->ctx[0]->num_sms;
-    for (slim_ctx* c : b->ctx)
-      if (c->plan.grid > 0) {
-        const int g = (int)std::lround(slots * (double)c->p * c->p * c->p / work);
-        c->plan.grid = std::max(2, std::min(c->plan.grid, g));
+  // The problems' tiled factorisations run as one persistent launch per
+  // factor precision and tile size, their task lists merged into one queue:
+  // every CTA of the GPU works on whichever problem has a ready task.
+  for (int is_f32 = 0; is_f32 < 2; ++is_f32)
+    for (int nb : {32, 64}) {
+      std::vector<const CholPlan*> plans;
+      std::vector<void*> Ls;
+      std::vector<int*> sts;
+      for (slim_ctx* c : b->ctx)
+        if (c->plan.T > 0 && c->plan.is_f32 == is_f32 && c->plan.nb == nb) {
+          plans.push_back(&c->plan);
+          Ls.push_back(c->d_L);
+          sts.push_back(c->d_status);
+        }
+      if (plans.empty()) continue;
+      slim::CholBatch g;
+      if (slim::chol_batch_create(&g, plans, Ls, sts, b->ctx[0]->num_sms, 2) != cudaSuccess) {
+        slim::chol_batch_destroy(&g);
+        slim_batch_destroy(b);
+        return SLIM_ECUDA;
       }
-  }
+      b->groups.push_back(g);
+    }
   *out = b;
   return SLIM_OK;
 }
@@ -2380,21 +2419,32 @@ extern "C" slim_status slim_batch_step(slim_batch* b, int nsteps) {
   for (slim_ctx* c : b->ctx)
     if (!c->has_data) return SLIM_ESTATE;
   if (!b->exec) {
-    // fork every problem's stream off the batch stream, capture one step on
-    // each, join them back: one graph with a parallel branch per problem
+    // one graph in three parts: a parallel branch per problem up to its
+    // K = lambda I + G; the merged factorisation launches; a parallel branch
+    // per problem from its solves on
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return SLIM_ECUDA;
-    cudaError_t e = cudaEventRecord(b->fork, b->stream);
-    for (size_t i = 0; i < b->ctx.size() && e == cudaSuccess; ++i) {
-      slim_ctx* c = b->ctx[i];
-      e = cudaStreamWaitEvent(c->stream, b->fork, 0);
-      if (e == cudaSuccess) {
-        c->capturing = true;
-        e = enqueue_step(c);
-        c->capturing = false;
+    cudaError_t e = cudaSuccess;
+    for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
+      cudaEvent_t fork = stage == 1 ? b->fork : b->fork2;
+      std::vector<cudaEvent_t>& join = stage == 1 ? b->join : b->join2;
+      e = cudaEventRecord(fork, b->stream);
+      for (size_t i = 0; i < b->ctx.size() && e == cudaSuccess; ++i) {
+        slim_ctx* c = b->ctx[i];
+        e = cudaStreamWaitEvent(c->stream, fork, 0);
+        if (e == cudaSuccess) {
+          c->capturing = true;
+          c->stage = stage;
+          e = enqueue_step(c);
+          c->stage = 0;
+          c->capturing = false;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(join[i], c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, join[i], 0);
       }
-      if (e == cudaSuccess) e = cudaEventRecord(b->join[i], c->stream);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+      if (stage == 1)
+        for (size_t g = 0; g < b->groups.size() && e == cudaSuccess; ++g)
+          e = chol_factor_batch(b->groups[g], b->stream);
     }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);

@@ -799,6 +799,73 @@ __device__ __noinline__ void task_potrf(T* Lkk, int P, T* w_k, T* As, T* Bs, T* 
   potrf_tile<T, NB>(S, As, Bs, Lkk, P, w_k, status);
 }
 
+// Run task tk of the factorisation of L (P x P, Tt x Tt tiles): wait for its
+// inputs on the tile counters, compute, publish.  Returns false when a wait
+// ran out or another CTA asked everyone to stop.
+template <typename T, int NB>
+__device__ __forceinline__ bool run_factor_task(const CholTask tk, T* L, int P, int Tt, int* cnt,
+                                                T* winv, int* status, int* abort_flag, T* As,
+                                                T* Bs, T* S, int* s_ok3, int* s_ok8) {
+  const int i = tk.i, m = tk.m, k = tk.k;
+  bool ok = true;
+  if (tk.type == kUpd) {
+    ok = cta_wait(&cnt[i * Tt + k], k + 1, &cnt[m * Tt + k], k + 1, &cnt[i * Tt + m], k, 3,
+                  abort_flag, status, s_ok3);
+    if (ok) {
+      T* tile_im = L + (size_t)i * NB * P + (size_t)m * NB;
+      const T* Lik = L + (size_t)i * NB * P + (size_t)k * NB;
+      const T* Lmk = L + (size_t)m * NB * P + (size_t)k * NB;
+      task_gemm<T, NB>(tile_im, P, Lik, P, Lmk, P, tile_im, T(-1), As, Bs, S);
+      cta_publish(&cnt[i * Tt + m]);
+    }
+  } else if (tk.type == kUpd4) {
+    ok = cta_wait_group(cnt, Tt, i, m, k, abort_flag, status, s_ok8);
+    if (ok) {
+      if constexpr (sizeof(T) == 4 && NB == 64) {
+        task_gemm_group<NB>(L + (size_t)i * NB * P + (size_t)m * NB, P,
+                            L + (size_t)i * NB * P + (size_t)k * NB,
+                            L + (size_t)m * NB * P + (size_t)k * NB, As, As + NB * (2 * NB + 4));
+      } else {
+        set_status(status, SLIM_EINVAL);   // the list holds no groups for this factor
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        red_release_add(&cnt[i * Tt + m], 1);
+        red_release_add(&cnt[i * Tt + m + 1], 1);
+        red_release_add(&cnt[(i + 1) * Tt + m], 1);
+        red_release_add(&cnt[(i + 1) * Tt + m + 1], 1);
+      }
+    }
+  } else if (tk.type == kTrsm) {
+    ok = cta_wait(&cnt[m * Tt + m], m + 1, &cnt[i * Tt + m], m, nullptr, 0, 2, abort_flag,
+                  status, s_ok3);
+    if (ok) {
+      T* tile_im = L + (size_t)i * NB * P + (size_t)m * NB;
+      task_gemm<T, NB>(tile_im, P, tile_im, P, winv + (size_t)m * NB * NB, NB, nullptr, T(1),
+                       As, Bs, S);
+      cta_publish(&cnt[i * Tt + m]);
+    }
+  } else if (tk.type == kPanel) {
+    ok = cta_wait(&cnt[k * Tt + k], k + 1, &cnt[i * Tt + k], k, &cnt[i * Tt + i], k, 3,
+                  abort_flag, status, s_ok3);
+    if (ok) {
+      task_panel<T, NB>(L + (size_t)i * NB * P + (size_t)k * NB,
+                        L + (size_t)i * NB * P + (size_t)i * NB, P, winv + (size_t)k * NB * NB,
+                        winv + (size_t)i * NB * NB, &cnt[i * Tt + k], As, Bs, S, status);
+      cta_publish(&cnt[i * Tt + i], 2);
+    }
+  } else {
+    ok = cta_wait(&cnt[k * Tt + k], k, abort_flag, status, s_ok3);
+    if (ok) {
+      task_potrf<T, NB>(L + (size_t)k * NB * P + (size_t)k * NB, P, winv + (size_t)k * NB * NB,
+                        As, Bs, S, status);
+      cta_publish(&cnt[k * Tt + k]);
+    }
+  }
+  return ok;
+}
+
 template <typename T, int NB>
 __global__ void __launch_bounds__(kThreads, 2) chol_factor_kernel(T* L, int P, int Tt,
                                                                const CholTask* tasks, int ntasks,
@@ -827,67 +894,53 @@ __global__ void __launch_bounds__(kThreads, 2) chol_factor_kernel(T* L, int P, i
     int next = 0;
     if (tid == 32) next = atomicAdd(ticket, 1);
     __syncthreads();
-    const int i = tk.i, m = tk.m, k = tk.k;
-    bool ok = true;
-    if (tk.type == kUpd) {
-      ok = cta_wait(&cnt[i * Tt + k], k + 1, &cnt[m * Tt + k], k + 1, &cnt[i * Tt + m], k, 3,
-                    abort_flag, status, s_ok3);
-      if (ok) {
-        T* tile_im = L + (size_t)i * NB * P + (size_t)m * NB;
-        const T* Lik = L + (size_t)i * NB * P + (size_t)k * NB;
-        const T* Lmk = L + (size_t)m * NB * P + (size_t)k * NB;
-        task_gemm<T, NB>(tile_im, P, Lik, P, Lmk, P, tile_im, T(-1), As, Bs, S);
-        cta_publish(&cnt[i * Tt + m]);
-      }
-    } else if (tk.type == kUpd4) {
-      ok = cta_wait_group(cnt, Tt, i, m, k, abort_flag, status, s_ok8);
-      if (ok) {
-        if constexpr (sizeof(T) == 4 && NB == 64) {
-          task_gemm_group<NB>(L + (size_t)i * NB * P + (size_t)m * NB, P,
-                              L + (size_t)i * NB * P + (size_t)k * NB,
-                              L + (size_t)m * NB * P + (size_t)k * NB, As, As + NB * (2 * NB + 4));
-        } else {
-          set_status(status, SLIM_EINVAL);   // the list holds no groups for this factor
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          __threadfence();
-          red_release_add(&cnt[i * Tt + m], 1);
-          red_release_add(&cnt[i * Tt + m + 1], 1);
-          red_release_add(&cnt[(i + 1) * Tt + m], 1);
-          red_release_add(&cnt[(i + 1) * Tt + m + 1], 1);
-        }
-      }
-    } else if (tk.type == kTrsm) {
-      ok = cta_wait(&cnt[m * Tt + m], m + 1, &cnt[i * Tt + m], m, nullptr, 0, 2, abort_flag,
-                    status, s_ok3);
-      if (ok) {
-        T* tile_im = L + (size_t)i * NB * P + (size_t)m * NB;
-        task_gemm<T, NB>(tile_im, P, tile_im, P, winv + (size_t)m * NB * NB, NB, nullptr, T(1),
-                         As, Bs, S);
-        cta_publish(&cnt[i * Tt + m]);
-      }
-    } else if (tk.type == kPanel) {
-      ok = cta_wait(&cnt[k * Tt + k], k + 1, &cnt[i * Tt + k], k, &cnt[i * Tt + i], k, 3,
-                    abort_flag, status, s_ok3);
-      if (ok) {
-        task_panel<T, NB>(L + (size_t)i * NB * P + (size_t)k * NB,
-                          L + (size_t)i * NB * P + (size_t)i * NB, P, winv + (size_t)k * NB * NB,
-                          winv + (size_t)i * NB * NB, &cnt[i * Tt + k], As, Bs, S, status);
-        cta_publish(&cnt[i * Tt + i], 2);
-      }
-    } else {
-      ok = cta_wait(&cnt[k * Tt + k], k, abort_flag, status, s_ok3);
-      if (ok) {
-        task_potrf<T, NB>(L + (size_t)k * NB * P + (size_t)k * NB, P, winv + (size_t)k * NB * NB,
-                          As, Bs, S, status);
-        cta_publish(&cnt[k * Tt + k]);
-      }
-    }
+    const bool ok = run_factor_task<T, NB>(tk, L, P, Tt, cnt, winv, status, abort_flag, As, Bs, S,
+                                           s_ok3, s_ok8);
     __syncthreads();
     if (tid == 32) {
       s_task = ok ? next : ntasks;
       if (ok && next < ntasks) s_desc = tasks[next];
+    }
+    __syncthreads();
+  }
+}
+
+// Many factorisations in one persistent launch: the CTAs claim (problem,
+// task) pairs from one merged queue in which every problem's tasks keep
+// their own order, so a claimed task depends only on tasks of its problem
+// claimed before it and the launch always makes progress.
+template <typename T, int NB>
+__global__ void __launch_bounds__(kThreads, 2) chol_factor_batch_kernel(
+    const FactorJob* jobs, const int2* queue, int nqueue, int* ticket, int* abort_flag) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* As = reinterpret_cast<T*>(smem_raw);
+  T* Bs = As + NB * gemm_ld(NB);
+  T* S = Bs + NB * gemm_ld(NB);
+  __shared__ int s_task, s_ok3[3], s_ok8[8];
+  __shared__ int2 s_q;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    const int t = atomicAdd(ticket, 1);
+    s_task = t;
+    if (t < nqueue) s_q = queue[t];
+  }
+  __syncthreads();
+  for (;;) {
+    const int t = s_task;
+    if (t >= nqueue) return;
+    const int2 q = s_q;
+    const FactorJob jb = jobs[q.x];
+    const CholTask tk = jb.tasks[q.y];
+    int next = 0;
+    if (tid == 32) next = atomicAdd(ticket, 1);
+    __syncthreads();
+    const bool ok = run_factor_task<T, NB>(tk, reinterpret_cast<T*>(jb.L), jb.P, jb.T, jb.cnt,
+                                           reinterpret_cast<T*>(jb.winv), jb.status, abort_flag,
+                                           As, Bs, S, s_ok3, s_ok8);
+    __syncthreads();
+    if (tid == 32) {
+      s_task = ok ? next : nqueue;
+      if (ok && next < nqueue) s_q = queue[next];
     }
     __syncthreads();
   }
@@ -1433,6 +1486,92 @@ cudaError_t launch_solve(const CholPlan& p, const void* L, const double* v, doub
 }
 
 }  // namespace
+
+cudaError_t chol_batch_create(CholBatch* b, const std::vector<const CholPlan*>& plans,
+                              const std::vector<void*>& Ls, const std::vector<int*>& statuses,
+                              int num_sms, int ctas_per_sm) {
+  *b = CholBatch{};
+  if (plans.empty()) return cudaSuccess;
+  b->is_f32 = plans[0]->is_f32;
+  b->nb = plans[0]->nb;
+  b->plans = plans;
+  std::vector<FactorJob> jobs;
+  struct Item { double key; int job, task; };
+  std::vector<Item> items;
+  for (size_t j = 0; j < plans.size(); ++j) {
+    const CholPlan* p = plans[j];
+    if (p->is_f32 != b->is_f32 || p->nb != b->nb) return cudaErrorInvalidValue;
+    jobs.push_back(FactorJob{Ls[j], p->P, p->T, p->d_tasks, p->d_sync, p->d_winv, statuses[j]});
+    for (int t = 0; t < p->ntasks; ++t)
+      items.push_back(Item{(t + 0.5) / p->ntasks, (int)j, t});
+  }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const Item& x, const Item& y) { return x.key < y.key; });
+  std::vector<int2> queue(items.size());
+  for (size_t q = 0; q < items.size(); ++q) queue[q] = make_int2(items[q].job, items[q].task);
+  b->njobs = (int)jobs.size();
+  b->nqueue = (int)queue.size();
+  b->grid = num_sms * ctas_per_sm;
+  cudaError_t e = cudaMalloc(&b->d_jobs, jobs.size() * sizeof(FactorJob));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, queue.size() * sizeof(int2));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_ticket, 2 * sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_jobs, jobs.data(), jobs.size() * sizeof(FactorJob), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_queue, queue.data(), queue.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  if (b->is_f32)
+    e = b->nb == 64 ? cudaFuncSetAttribute(chol_factor_batch_kernel<float, 64>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)factor_smem<float, 64>())
+                    : cudaFuncSetAttribute(chol_factor_batch_kernel<float, 32>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)factor_smem<float, 32>());
+  else
+    e = b->nb == 64 ? cudaFuncSetAttribute(chol_factor_batch_kernel<double, 64>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)factor_smem<double, 64>())
+                    : cudaFuncSetAttribute(chol_factor_batch_kernel<double, 32>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)factor_smem<double, 32>());
+  return e;
+}
+
+void chol_batch_destroy(CholBatch* b) {
+  cudaFree(b->d_jobs);
+  cudaFree(b->d_queue);
+  cudaFree(b->d_ticket);
+  *b = CholBatch{};
+}
+
+cudaError_t chol_factor_batch(const CholBatch& b, cudaStream_t s) {
+  if (b.nqueue == 0) return cudaSuccess;
+  cudaError_t e;
+  // tile counters start at zero for every factorisation, and so do the
+  // merged queue's ticket and abort flag
+  for (const CholPlan* p : b.plans)
+    if ((e = cudaMemsetAsync(p->d_sync, 0, chol_sync_words(p->T) * sizeof(int), s)) != cudaSuccess)
+      return e;
+  if ((e = cudaMemsetAsync(b.d_ticket, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;
+  int* ticket = b.d_ticket;
+  int* abort_flag = b.d_ticket + 1;
+  if (b.is_f32) {
+    if (b.nb == 64)
+      chol_factor_batch_kernel<float, 64><<<b.grid, kThreads, factor_smem<float, 64>(), s>>>(
+          b.d_jobs, b.d_queue, b.nqueue, ticket, abort_flag);
+    else
+      chol_factor_batch_kernel<float, 32><<<b.grid, kThreads, factor_smem<float, 32>(), s>>>(
+          b.d_jobs, b.d_queue, b.nqueue, ticket, abort_flag);
+  } else {
+    if (b.nb == 64)
+      chol_factor_batch_kernel<double, 64><<<b.grid, kThreads, factor_smem<double, 64>(), s>>>(
+          b.d_jobs, b.d_queue, b.nqueue, ticket, abort_flag);
+    else
+      chol_factor_batch_kernel<double, 32><<<b.grid, kThreads, factor_smem<double, 32>(), s>>>(
+          b.d_jobs, b.d_queue, b.nqueue, ticket, abort_flag);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t chol_potrf_tile_prepare() {
   return cudaFuncSetAttribute(chol_potrf_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -10,6 +10,17 @@
 
 namespace slim {
 
+// One factorisation of a merged launch (chol_factor_batch): its matrix, tile
+// grid, task list, tile counters, diagonal-tile inverses and status word.
+struct FactorJob {
+  void* L;
+  int P, T;
+  const CholTask* tasks;
+  int* cnt;
+  void* winv;
+  int* status;
+};
+
 struct CholPlan {
   int P = 0;          // padded order (multiple of NB)
   int T = 0;          // tiles per side
@@ -57,5 +68,25 @@ void chol_plan_destroy(CholPlan* plan);
 cudaError_t chol_factor(const CholPlan& plan, void* L, int* status, cudaStream_t s);
 cudaError_t chol_solve(const CholPlan& plan, const void* L, const double* v, double* z,
                        int* status, cudaStream_t s, int first_tile = 0);
+
+// Factorisations of many problems (same factor precision and tile size) in
+// one persistent launch: their task lists merged into one queue, each
+// problem's order kept (task t of a problem with n tasks is placed by
+// (t + 1/2) / n, so the problems advance together).  The CTAs of the launch
+// claim (problem, task) pairs by ticket; a wait that runs out stops every
+// CTA (SLIM_ETIMEOUT in that problem's status).
+struct CholBatch {
+  int is_f32 = 0, nb = 0, grid = 0;
+  int njobs = 0, nqueue = 0;
+  FactorJob* d_jobs = nullptr;
+  int2* d_queue = nullptr;
+  int* d_ticket = nullptr;                 // [ticket, abort flag]
+  std::vector<const CholPlan*> plans;      // for the counter resets
+};
+cudaError_t chol_batch_create(CholBatch* b, const std::vector<const CholPlan*>& plans,
+                              const std::vector<void*>& Ls, const std::vector<int*>& statuses,
+                              int num_sms, int ctas_per_sm);
+void chol_batch_destroy(CholBatch* b);
+cudaError_t chol_factor_batch(const CholBatch& b, cudaStream_t s);
 
 }  // namespace slim

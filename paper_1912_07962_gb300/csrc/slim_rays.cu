@@ -51,37 +51,70 @@ __device__ __forceinline__ bool overlap_window(const ViewGeom& gi, const RayDesc
   return lo <= hi;
 }
 
-// sum_pixels a_i(pix) a_j(pix) for two rays in the same slice, read from the
-// stored taps: tap 2s / 2s+1 of a ray are its two taps at step s, so ray j's
-// taps at a pixel are at the step of ray j that covers the pixel.  The steps
-// of the window are split over `lanes` threads starting at `lane` (the caller
-// reduces the partial sums).
-__device__ double pair_overlap(const RayArgs& a, int qi, int qj, int lane = 0, int lanes = 1) {
+// Overlap of ray i's two taps at step s with ray j (same slice, plane offset
+// `off`), read from the stored taps: tap 2s / 2s+1 of a ray are its taps at
+// step s, so ray j's taps at a pixel are at the step of ray j that covers the
+// pixel.  A ray stepping along rows has the pixel's row as its step, one
+// stepping along columns the column; ray i's taps at step s lie in row s or
+// column s.  A row from a pixel index is an exact division by N, done as a
+// multiply-high by magic_n = ceil(2^32 / N) (exact for multiples of N below
+// 2^32 when N < 2^16).
+__device__ __forceinline__ double taps_at_step(const int* __restrict__ pi,
+                                               const double* __restrict__ wi,
+                                               const int* __restrict__ pj,
+                                               const double* __restrict__ wj, int s, int i_rows,
+                                               int j_rows, int N, unsigned magic_n, int off) {
+  const int2 pp = *reinterpret_cast<const int2*>(pi + 2 * s);
+  double acc = 0.0;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int pix = e ? pp.y : pp.x;
+    if (pix < 0) continue;
+    int sj = s;                                        // same stepping axis
+    if (i_rows != j_rows)
+      sj = i_rows ? pix - off - s * N                  // the pixel's column
+                  : (int)__umulhi((unsigned)(pix - off - s), magic_n);   // its row
+    const int2 pq = *reinterpret_cast<const int2*>(pj + 2 * sj);
+    if (pq.x == pix) acc += wi[2 * s + e] * wj[2 * sj];
+    if (pq.y == pix) acc += wi[2 * s + e] * wj[2 * sj + 1];
+  }
+  return acc;
+}
+
+// The rays of ring rows qi, qj and the steps [lo, hi] of ray qi that can meet
+// ray qj (hi < lo: no overlap).
+struct PairWindow {
+  int lo = 0, hi = -1, i_rows = 0, j_rows = 0, off = 0;
+};
+__device__ __forceinline__ PairWindow pair_window(const RayArgs& a, int qi, int qj) {
+  PairWindow w;
   const int rayi = a.ring_ids[qi], rayj = a.ring_ids[qj];
-  if (rayi < 0 || rayj < 0) return 0.0;
+  if (rayi < 0 || rayj < 0) return w;
   const RayDesc ri = decode_ray(rayi, a.Du, a.Dv), rj = decode_ray(rayj, a.Du, a.Dv);
-  if (ri.slice != rj.slice) return 0.0;
+  if (ri.slice != rj.slice) return w;
   const ViewGeom gi = a.views[ri.view], gj = a.views[rj.view];
   int lo, hi;
-  if (!overlap_window(gi, ri, gj, rj, a.N, lo, hi)) return 0.0;
+  if (!overlap_window(gi, ri, gj, rj, a.N, lo, hi)) return w;
+  w.lo = lo;
+  w.hi = hi;
+  w.i_rows = gi.row_step;
+  w.j_rows = gj.row_step;
+  w.off = ri.slice * a.N * a.N;
+  return w;
+}
+
+// sum_pixels a_i(pix) a_j(pix) for two rays of the ring, ray qi marched over
+// its window; the steps are split over `lanes` threads starting at `lane`
+// (the caller reduces the partial sums).
+__device__ double pair_overlap(const RayArgs& a, int qi, int qj, int lane = 0, int lanes = 1) {
+  const PairWindow w = pair_window(a, qi, qj);
   const int* pi = a.ring_pix + (size_t)qi * a.taps;
   const double* wi = a.ring_w + (size_t)qi * a.taps;
   const int* pj = a.ring_pix + (size_t)qj * a.taps;
   const double* wj = a.ring_w + (size_t)qj * a.taps;
-  const long long plane = (long long)a.N * a.N;
   double acc = 0.0;
-  for (int s = lo + lane; s <= hi; s += lanes) {
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int pix = pi[2 * s + e];
-      if (pix < 0) continue;
-      const int in = (int)(pix % plane);
-      const int sj = gj.row_step ? in / a.N : in % a.N;   // step of ray j covering the pixel
-      const double w = wi[2 * s + e];
-      if (pj[2 * sj] == pix) acc += w * wj[2 * sj];
-      if (pj[2 * sj + 1] == pix) acc += w * wj[2 * sj + 1];
-    }
-  }
+  for (int s = w.lo + lane; s <= w.hi; s += lanes)
+    acc += taps_at_step(pi, wi, pj, wj, s, w.i_rows, w.j_rows, a.N, a.magic_n, w.off);
   return acc;
 }
 
@@ -162,21 +195,58 @@ __global__ void __launch_bounds__(kCta) forward_rays_kernel(RayArgs a, const T* 
   if (lane == 0) a.rhs[q] = (double)(acc - b[ray]);
 }
 
-// 2D: one warp per (new ray i, ring row q): G[new_i][q] = G[q][new_i]; the
-// lanes split the overlap window (windows of near-parallel rays span the image).
-// The ray with the smaller ring index is the one marched, so both warps of a
-// pair inside the new block compute the same value.
+// 2D: G[new_i][q] = G[q][new_i] for every ring row q, a thread per pair
+// (i, q) marching the new ray i over its overlap window with ray q.  Windows
+// longer than kShortWindow steps (near-parallel rays, and the diagonal) go to
+// the whole warp afterwards, one at a time, with the steps split over the
+// lanes.  A pair of two new rows is computed once, by the thread of the
+// smaller ring index, which writes both entries.
+constexpr int kShortWindow = 32;
 __global__ void __launch_bounds__(kCta) gram_pairs_kernel(RayArgs a) {
-  const long long idx = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  if (idx >= (long long)a.ell * a.p) return;
-  const int i = (int)(idx / a.p), q = (int)(idx % a.p);
-  const int qi = a.info->slot * a.ell + i;
-  double v = pair_overlap(a, min(qi, q), max(qi, q), lane, 32);
-  v = warp_sum(v);
-  if (lane == 0) {
-    a.G[(size_t)qi * a.P + q] = v;
-    a.G[(size_t)q * a.P + qi] = v;
+  const int base = a.info->slot * a.ell;
+  int qi = 0, q = 0;
+  bool mine = false;
+  PairWindow w;
+  if (idx < (long long)a.ell * a.p) {
+    qi = base + (int)(idx / a.p);
+    q = (int)(idx % a.p);
+    mine = q < base || q >= base + a.ell || q >= qi;
+    if (mine) w = pair_window(a, qi, q);
+  }
+  const bool longw = w.hi - w.lo + 1 > kShortWindow;
+  double acc = 0.0;
+  if (!longw) {
+    const int* pi = a.ring_pix + (size_t)qi * a.taps;
+    const double* wi = a.ring_w + (size_t)qi * a.taps;
+    const int* pj = a.ring_pix + (size_t)q * a.taps;
+    const double* wj = a.ring_w + (size_t)q * a.taps;
+    for (int s = w.lo; s <= w.hi; ++s)
+      acc += taps_at_step(pi, wi, pj, wj, s, w.i_rows, w.j_rows, a.N, a.magic_n, w.off);
+  }
+  unsigned pending = __ballot_sync(0xffffffffu, longw);
+  while (pending) {
+    const int src = __ffs(pending) - 1;
+    pending &= pending - 1;
+    const int sqi = __shfl_sync(0xffffffffu, qi, src), sq = __shfl_sync(0xffffffffu, q, src);
+    const int lo = __shfl_sync(0xffffffffu, w.lo, src), hi = __shfl_sync(0xffffffffu, w.hi, src);
+    const int ir = __shfl_sync(0xffffffffu, w.i_rows, src);
+    const int jr = __shfl_sync(0xffffffffu, w.j_rows, src);
+    const int off = __shfl_sync(0xffffffffu, w.off, src);
+    const int* pi = a.ring_pix + (size_t)sqi * a.taps;
+    const double* wi = a.ring_w + (size_t)sqi * a.taps;
+    const int* pj = a.ring_pix + (size_t)sq * a.taps;
+    const double* wj = a.ring_w + (size_t)sq * a.taps;
+    double v = 0.0;
+    for (int s = lo + lane; s <= hi; s += 32)
+      v += taps_at_step(pi, wi, pj, wj, s, ir, jr, a.N, a.magic_n, off);
+    v = warp_sum(v);
+    if (lane == src) acc = v;
+  }
+  if (mine) {
+    a.G[(size_t)qi * a.P + q] = acc;
+    a.G[(size_t)q * a.P + qi] = acc;
   }
 }
 
@@ -426,7 +496,7 @@ cudaError_t launch_forward_rays(const RayArgs& a, T* x, const T* b, cudaStream_t
 
 cudaError_t launch_gram_pairs(const RayArgs& a, cudaStream_t s) {
   const long long total = (long long)a.ell * a.p;
-  gram_pairs_kernel<<<cdiv(total, kWarpsPerCta), kCta, 0, s>>>(a);
+  gram_pairs_kernel<<<cdiv(total, kCta), kCta, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -15,6 +15,7 @@ struct RayArgs {
   int N, Du, Dv, n_views, dim;       // dim 3: det_v == N, ray (a, v, u) lies in z-slice v
   long long n, m;
   int ell, nslots, r, p, taps;       // taps = 2N per ray
+  unsigned magic_n;                  // ceil(2^32 / N) (N = 1: 2^32 - 1), exact division by N
   int kind, steps_per_view;          // 1: i.i.d. over all rays; 2: over arrived views
   unsigned long long seed;
   double lam;

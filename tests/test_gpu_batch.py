@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import workloads
-from oracle import joseph, slim as oslim
+from oracle import joseph, rng, slim as oslim
 
 from _common import rel
 
@@ -150,3 +150,37 @@ def test_tile_variants_single_step(sl, solver, tile, cps):
     tol = 1e-12 if solver == 0 else 1e-9
     assert rel(s.get_x(), traj[7]) < tol
     s.close()
+
+
+def test_batch_at_the_mix_extremes(sl):
+    # the batched mix's largest order and smallest damping: a 128 x 128 problem
+    # with ell = 512 random rays and r = 7 (p = 4096), float64, next to a
+    # lambda = 1e-4 problem in the float32 form (float32 iterate, mixed solve
+    # with three refinement rounds: at this damping its floor is 1.4e-5 per
+    # step, test_gpu_bench_config), and a small one
+    big = dict(N=128, n_views=90, det=182, ell=512, r=7, lam=1e-3, seed=31, kind=1, tile=32,
+               ctas_per_sm=2)
+    small_lam = dict(N=96, n_views=60, det=137, ell=200, r=4, lam=1e-4, seed=32, kind=1,
+                     precision=sl.SLIM_PREC_FP32, solver=sl.SLIM_SOLVE_MIXED, refine_iters=3)
+    specs = [big, small_lam, SPECS[0]]
+    probs = [_problem(sp) for sp in specs]
+    steps = 3
+    bt = sl.SlimBatch(specs)
+    assert bt.problems[0].p == 4096
+    for pb, (_, b) in zip(bt.problems, probs):
+        pb.set_data(b)
+    xs = []
+    for k in range(1, steps + 1):
+        xs.append([pb.get_x() for pb in bt.problems])     # x_{k-1}
+        bt.step(1)
+        bt.sync()
+        for i, (sp, (g, b)) in enumerate(zip(specs, probs)):
+            src = oslim.tomo_source(g, b)
+            ids = [np.array(rng.random_rays(sp["seed"], kk, sp["ell"], g.m))
+                   for kk in range(max(1, k - sp["r"]), k + 1)]
+            x_prev = xs[-1][i]
+            xo, _, _, _ = oslim.step_woodbury(x_prev, [src.rows(j) for j in ids], src.rhs(ids[-1]),
+                                             sp["lam"])
+            tol = 2e-5 if sp.get("precision") == sl.SLIM_PREC_FP32 else 1e-12
+            assert rel(bt.problems[i].get_x(), xo) < tol, (i, k)
+    bt.close()
