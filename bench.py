@@ -156,7 +156,8 @@ def make_form(sl, cfg, form, seed, lookahead=0, ctas_per_sm=0, decay_after=0):
     plain: float64 everywhere, one kernel per phase, no graph."""
     if form in ("chosen", "chosen_fp64_factor"):
         mixed = form == "chosen"
-        solver = ((sl.SLIM_SOLVE_MIXED_TC if CHOSEN_SOLVER == "mixed_tc" and lookahead
+        inverse = {"mixed_tc": sl.SLIM_SOLVE_MIXED_TC, "mixed_inv": sl.SLIM_SOLVE_MIXED_INV}
+        solver = ((inverse[CHOSEN_SOLVER] if CHOSEN_SOLVER in inverse and lookahead
                    else sl.SLIM_SOLVE_MIXED) if mixed else sl.SLIM_SOLVE_FP64)
         refine = (3 if solver == sl.SLIM_SOLVE_MIXED_TC else 2) if mixed else 0
         return sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.ell, cfg.r, cfg.lam, seed,
@@ -1235,9 +1236,10 @@ def main():
     ap.add_argument("--tta-decay-after", type=int, default=180,
                     help="also run time-to-accuracy with the 1/k damping decay after this step "
                          "(0: skip)")
-    ap.add_argument("--solver", default="mixed", choices=["mixed", "mixed_tc"],
-                    help="chosen form's solve: through the float32 factor (mixed) or through "
-                         "its tensor-core inverse (mixed_tc, pipelined only)")
+    ap.add_argument("--solver", default="mixed", choices=["mixed", "mixed_tc", "mixed_inv"],
+                    help="chosen form's solve: through the float32 factor (mixed), through the "
+                         "inverse of a tensor-core factor (mixed_tc), or through the tensor-core "
+                         "inverse of the tiled factor (mixed_inv); the last two pipelined only")
     ap.add_argument("--no-fp64-factor", action="store_true",
                     help="skip the pipelined chosen form with the float64 factor")
     ap.add_argument("--no-cpu", action="store_true")

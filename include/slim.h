@@ -61,7 +61,7 @@ typedef enum {
 enum { SLIM_F32 = 0, SLIM_F64 = 1 };
 enum { SLIM_PREC_FP64 = 0, SLIM_PREC_FP32 = 1 };
 enum { SLIM_SOLVE_FP64 = 0, SLIM_SOLVE_MIXED = 1, SLIM_SOLVE_LSQR = 2, SLIM_SOLVE_SG = 3,
-       SLIM_SOLVE_OLBFGS = 4, SLIM_SOLVE_MIXED_TC = 5 };
+       SLIM_SOLVE_OLBFGS = 4, SLIM_SOLVE_MIXED_TC = 5, SLIM_SOLVE_MIXED_INV = 6 };
 enum { SLIM_BLOCKS_VIEWS = 0, SLIM_BLOCKS_RAYS = 1, SLIM_BLOCKS_STREAM = 2 };
 
 /* Parallel-beam geometry (Sec. 4.3; Joseph rows defined in the library docs).
@@ -166,6 +166,10 @@ typedef struct {
  *                 sweeps.
  *                 lookahead >= 1 and tile 0 or 64 only (SLIM_ENOTSUP
  *                 otherwise)
+ *                 SLIM_SOLVE_MIXED_INV: as SLIM_SOLVE_MIXED_TC, with the
+ *                 factor from the persistent tiled factorisation of
+ *                 SLIM_SOLVE_MIXED (one launch) and only X = L^{-1} formed by
+ *                 tensor-core products; same limits
  *                 SLIM_SOLVE_LSQR: no Gram matrix and no factorisation: s_k of
  *                 Eq. (slimLSstep) by LSQR for damped least squares (Sec. 4.2),
  *                 matrix-free over the window's stored taps, float64 vectors;
@@ -187,14 +191,17 @@ typedef struct {
  *                 (SLIM_EINVAL); 2D view blocks, lookahead 0, tik_lambda 0
  *                 (SLIM_ENOTSUP otherwise); OLBFGS is one cooperative launch
  *                 per step, never captured in a graph
- *   refine_iters  refinement rounds for SLIM_SOLVE_MIXED (0..16)
+ *   refine_iters  refinement rounds for the SLIM_SOLVE_MIXED* solvers (0..16)
  *   use_graph     1: capture one step as a CUDA graph at the first slim_step and
  *                 replay it (one graph launch per step)
  *   tile          tile size of the tiled Cholesky: 32 or 64, 0 = default (64 for
  *                 the float32 factor, 32 for float64)
  *   ctas_per_sm   resident CTAs per SM of the persistent factorisation (1..4,
- *                 0 = default: 2, or 1 with lookahead, where the D factorisations
- *                 in flight share these CTAs, num_SMs * ctas_per_sm / D each)
+ *                 0 = default 1): 1 gives each CTA the whole register file, 2..4
+ *                 cap it at 128 registers a thread.  With lookahead the D
+ *                 factorisations in flight share num_SMs * ctas_per_sm CTAs at
+ *                 128 registers a thread (num_SMs * ctas_per_sm / D each), which
+ *                 leaves room on the SMs for the iterate chain
  *   lookahead     0: each step runs as one chain.  D = 1..10 (view blocks, 2D,
  *                 rows from the projector): the matrix lambda_k I + M_k M_k^T of
  *                 Eq. (B_k) depends only on the blocks drawn, so the chain that

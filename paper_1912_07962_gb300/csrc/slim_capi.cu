@@ -35,7 +35,7 @@ struct slim_ctx {
   int* d_slice_rows = nullptr;
   int ramp = 0, r = 0, nslots = 1, ell = 0, p = 0, P = 0, taps = 0, nb = 32;
   int decay_after = 0;             // 1/k decay of the damping after this step (0: none)
-  int tile = 0, ctas_per_sm = 2;
+  int tile = 0, ctas_per_sm = 1;
   double lam = 0.0, eta = 1.0;
   unsigned long long seed = 0;
   std::vector<ViewGeom> h_views;
@@ -316,8 +316,13 @@ cudaError_t mark(slim_ctx* c, int i) {
 
 // Float32 factor with float64-residual refinement (solved through the
 // factor, or through its tensor-core inverse).
+// the pipelined forms whose iterate chain solves through X = L^{-1}
+inline bool uses_inverse(const slim_ctx* c) {
+  return c->solver == SLIM_SOLVE_MIXED_TC || c->solver == SLIM_SOLVE_MIXED_INV;
+}
+
 inline bool is_mixed(const slim_ctx* c) {
-  return c->solver == SLIM_SOLVE_MIXED || c->solver == SLIM_SOLVE_MIXED_TC;
+  return c->solver == SLIM_SOLVE_MIXED || uses_inverse(c);
 }
 
 // Kernels one step launches (sample, forward, Gram, K, factor, the solves:
@@ -331,14 +336,14 @@ int kernels_per_step(const slim_ctx* c) {
   if (c->solver == SLIM_SOLVE_OLBFGS) return 3; // sample, forward + residual, the olbfgs step
   const int solves = is_mixed(c) ? 1 + c->refine_iters : 1;
   const int refine = is_mixed(c) ? 2 * c->refine_iters : 0;
-  if (c->lookahead && c->solver == SLIM_SOLVE_MIXED_TC) {
+  if (c->lookahead && uses_inverse(c)) {
     // geometry: sample, taps, Gram, map clear, ring map, K; the factor (per
     // panel: diagonal tile, panel product, trailing product; the last panel
-    // its diagonal tile only), the inverse (diagonal tiles, one product per
-    // recursion depth and side, mirror); iterate: residual, 2 products per
-    // solve, a residual per refinement round, scatter -- or all of the
-    // iterate chain in one cooperative kernel
-    const int factor = 3 * c->cplan[0].T - 2;
+    // its diagonal tile only -- or one persistent launch), the inverse
+    // (diagonal tiles, one product per recursion depth and side, mirror);
+    // iterate: residual, 2 products per solve, a residual per refinement
+    // round, scatter -- or all of the iterate chain in one cooperative kernel
+    const int factor = c->solver == SLIM_SOLVE_MIXED_TC ? 3 * c->cplan[0].T - 2 : 1;
     const int inv = 2 + (int)c->tplan[0].level_first.size() - 1;
     const int tik = c->tik_lambda > 0.0 ? 2 : 0;
     const int iterate = c->coop_grid ? 1 : 1 + 2 * solves + c->refine_iters + 1 + tik;
@@ -794,7 +799,7 @@ cudaError_t la_enqueue_factor(slim_ctx* c, int b, cudaStream_t s) {
   else
     e = chol_factor(c->planb[b], c->d_Lb[b], c->d_status, s);
   if (e != cudaSuccess) return e;
-  if (c->solver == SLIM_SOLVE_MIXED_TC &&
+  if (uses_inverse(c) &&
       (e = tri_inverse(c->tplan[b], (const float*)c->planb[b].d_winv, (float*)c->d_Xb[b],
                        c->d_status, s)) != cudaSuccess)
     return e;
@@ -816,7 +821,7 @@ cudaError_t la_enqueue_iterate(slim_ctx* c, int b, cudaStream_t s) {
   if ((e = la_mark(c, 7, s)) != cudaSuccess) return e;
   // slimLS: the right-hand side is zero above the newest block (the last one)
   const int first_tile = tik ? 0 : (c->nslots - 1) * c->ell / c->nb;
-  if (c->solver == SLIM_SOLVE_MIXED_TC) {
+  if (uses_inverse(c)) {
     // z = X^T X rhs with X = L^{-1}: two matrix-vector products per solve
     const float* X = (const float*)c->d_Xb[b];
     const int lo = tik ? 0 : (c->nslots - 1) * c->ell;
@@ -1086,7 +1091,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     c->use_graph = step->use_graph;
     c->tile = step->tile;
     c->lookahead = step->lookahead;
-    c->ctas_per_sm = step->ctas_per_sm ? step->ctas_per_sm : (c->lookahead ? 1 : 2);
+    c->ctas_per_sm = step->ctas_per_sm ? step->ctas_per_sm : 1;
     c->lsqr_max_iter = step->lsqr_max_iter;
     c->lsqr_tol = step->lsqr_tol;
     c->tik_lambda = step->tik_lambda;
@@ -1150,7 +1155,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     }
     // the tensor-core inverse runs in the geometry chain of the pipelined
     // form, on the 64-wide tiles of the float32 factor
-    if (c->solver == SLIM_SOLVE_MIXED_TC &&
+    if (uses_inverse(c) &&
         (c->lookahead == 0 || (c->tile != 0 && c->tile != 64) || c->p > 8192)) {
       delete c;
       return SLIM_ENOTSUP;
@@ -1290,14 +1295,16 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       for (int b = 0; b < c->nbuf; ++b) {
         chk(cudaMemset(c->d_Lb[b], 0, (size_t)c->P * c->P * fs), "memset");
         chk(chol_plan_create(&c->planb[b], c->P, c->nb, is_mixed(c) ? 1 : 0,
-                             fgrid, 1), "chol plan");
+                             fgrid, 1, 0), "chol plan");
       }
-      if (c->solver == SLIM_SOLVE_MIXED_TC && st == SLIM_OK) {
+      if (uses_inverse(c) && st == SLIM_OK) {
         chk(tc_prepare(), "tensor-core product");
-        chk(chol_potrf_tile_prepare(), "diagonal tiles");
-        for (int b = 0; b < c->nbuf && st == SLIM_OK; ++b)
-          chk(tc_chol_plan(&c->cplan[b], c->P, (float*)c->d_Lb[b],
-                           (const float*)c->planb[b].d_winv), "factor plan");
+        if (c->solver == SLIM_SOLVE_MIXED_TC) {
+          chk(chol_potrf_tile_prepare(), "diagonal tiles");
+          for (int b = 0; b < c->nbuf && st == SLIM_OK; ++b)
+            chk(tc_chol_plan(&c->cplan[b], c->P, (float*)c->d_Lb[b],
+                             (const float*)c->planb[b].d_winv), "factor plan");
+        }
         chk(cudaMalloc(&c->d_ty, (size_t)c->P * sizeof(double)), "cudaMalloc");
         if (c->tik_lambda == 0.0 && st == SLIM_OK) {
           chk(cudaMalloc(&c->d_coop_bar, 2 * sizeof(unsigned)), "cudaMalloc");
@@ -2132,7 +2139,7 @@ extern "C" slim_status slim_damped_solve(const double* G, int p, double lambda, 
   double *L = nullptr, *v = nullptr, *out = nullptr;
   int* status = nullptr;
   slim_status st = SLIM_OK;
-  cudaError_t e = chol_plan_create(&plan, P, nb, 0, sms);
+  cudaError_t e = chol_plan_create(&plan, P, nb, 0, sms, 1);
   if (e == cudaSuccess) e = cudaMalloc(&L, (size_t)P * P * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&v, (size_t)P * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&out, (size_t)P * sizeof(double));
@@ -2382,6 +2389,7 @@ extern "C" slim_status slim_batch_create(int count, const slim_geometry* geoms,
         }
       if (plans.empty()) continue;
       slim::CholBatch g;
+      // throughput-bound: two CTAs per SM at 128 registers keep more tasks in flight
       if (slim::chol_batch_create(&g, plans, Ls, sts, b->ctx[0]->num_sms, 2) != cudaSuccess) {
         slim::chol_batch_destroy(&g);
         slim_batch_destroy(b);

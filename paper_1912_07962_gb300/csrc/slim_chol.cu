@@ -736,6 +736,211 @@ __device__ void potrf_smem(T* S, T* Wt, T* Pn, T* Tmp, T* Lg, int ld, T* Wg, int
   __syncthreads();
 }
 
+// float32, NB = 64: the tile factorisation laid out for latency.  The 64
+// pivots of a tile are a chain that no blocking shortens, so the chain runs
+// in one warp with the 16 x 16 diagonal block in registers, and everything
+// else runs on the other warps in its shadow.
+constexpr int kLd64 = 68;       // gemm_ld(64)
+constexpr int kLtLd = 17;       // transposed diagonal factor, 16 x 17
+
+// One warp: the 16 x 16 diagonal block at (c0, c0) of S, minus the product of
+// the previous panel's rows with themselves when `upd` (Pn rows c0..c0+15,
+// 16 columns), factored in registers and inverted.  Lane l (and its mirror
+// l + 16) holds row l.  Pivot c: the diagonal element comes from lane c, each
+// lane scales its own column-c entry and the scaled column reaches the other
+// rows by shuffles; entries above the diagonal carry values that are never
+// read.  The inverse X = D^{-1} is formed column by column (lane l: column l)
+// right-looking, X_ql = -(sum_{i<q} L_qi X_il) / L_qq.  L_D goes to S, X to
+// Wt (block (c0, c0)).  Non-positive pivots set SLIM_ENOTPD and are replaced
+// by 1.
+__device__ __forceinline__ void diag16_f32(float* S, float* Wt, const float* Pn, bool upd, int c0,
+                                        float* Lt, int* status) {
+  const int lane = threadIdx.x & 31, l = lane & 15;
+  float* srow = S + (c0 + l) * kLd64 + c0;
+  float a[16];
+#pragma unroll
+  for (int q = 0; q < 16; q += 4) {
+    const float4 v = *reinterpret_cast<const float4*>(srow + q);
+    a[q] = v.x; a[q + 1] = v.y; a[q + 2] = v.z; a[q + 3] = v.w;
+  }
+  if (upd) {
+    float pr[16];
+    const float* prow = Pn + (c0 + l) * kPanelLd;
+#pragma unroll
+    for (int q = 0; q < 16; q += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(prow + q);
+      pr[q] = v.x; pr[q + 1] = v.y; pr[q + 2] = v.z; pr[q + 3] = v.w;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float* pj = Pn + (c0 + j) * kPanelLd;
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < 16; q += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(pj + q);
+        acc += pr[q] * v.x;
+        acc += pr[q + 1] * v.y;
+        acc += pr[q + 2] * v.z;
+        acc += pr[q + 3] * v.w;
+      }
+      a[j] -= acc;
+    }
+  }
+  bool bad = false;
+  float my_rs = 1.f;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const float d = __shfl_sync(0xffffffffu, a[c], c);
+    const bool ok = d > 0.f;
+    bad |= !ok;
+    const float dd = ok ? d : 1.f;
+    const float rs = rsqrtf(dd);
+    if (l == c) my_rs = rs;
+    const float lc = (l == c ? dd : a[c]) * rs;
+    a[c] = lc;
+#pragma unroll
+    for (int j = c + 1; j < 16; ++j) a[j] -= lc * __shfl_sync(0xffffffffu, lc, j);
+  }
+  if (bad && lane == 0) set_status(status, SLIM_ENOTPD);
+  if (lane < 16) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j <= l) srow[j] = a[j];
+      Lt[j * kLtLd + l] = j <= l ? a[j] : 0.f;   // Lt[q][i] = L_iq
+    }
+  }
+  __syncwarp();
+  float rsv[16], sacc[16], x[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    rsv[i] = __shfl_sync(0xffffffffu, my_rs, i);
+    sacc[i] = 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    x[q] = q == l ? rsv[q] : (q > l ? -rsv[q] * sacc[q] : 0.f);
+#pragma unroll
+    for (int i = q + 1; i < 16; ++i) sacc[i] += Lt[q * kLtLd + i] * x[q];
+  }
+  if (lane < 16) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) Wt[(c0 + i) * kLd64 + c0 + l] = x[i];
+  }
+  __syncwarp();
+}
+
+// Factor the 64 x 64 tile in S (lower triangle) into L_kk (to S, then Lg) and
+// its inverse W (Wt, then Wg), blocked by 16 columns, two barriers per block:
+//   B(pb), all warps: the panel below block pb, L_P = S_P X_pb^T, into Pn;
+//          and W's row-block pb, W_pb,j = -X_pb T_pb,j (j < pb).
+//   C(pb), warp 0: the next diagonal block, updated by the panel, factored
+//          and inverted (X_pb+1);  warps 1-7 meanwhile: the rest of the
+//          trailing update S -= L_P L_P^T, the panel copied into S, and
+//          T_pb+1,j = sum_{k=j..pb} L_pb+1,k W_k,j for the next row-block of W.
+// Shared scratch: Pn (64 x 20), Tmp (3 blocks of 16 x 16), Lt (16 x 17).
+__device__ __noinline__ void potrf_la_f32(float* S, float* Wt, float* Pn, float* Tmp, float* Lt, float* Lg,
+                             int ld, float* Wg, int* status) {
+  constexpr int LD = kLd64, LP = kPanelLd;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int idx = tid; idx < 64 * 64; idx += kThreads) {
+    const int i = idx / 64, c = idx % 64;
+    if (i / 16 < c / 16) Wt[i * LD + c] = 0.f;
+  }
+  if (warp == 0) diag16_f32(S, Wt, Pn, false, 0, Lt, status);
+  __syncthreads();
+  for (int pb = 0; pb < 4; ++pb) {
+    const int c0 = 16 * pb;
+    const int rows = 48 - c0;
+    // B(pb)
+    for (int idx = tid; idx < rows * 16; idx += kThreads) {
+      const int r = c0 + 16 + idx / 16, c = idx % 16;
+      const float* sr = S + r * LD + c0;
+      const float* xc = Wt + (c0 + c) * LD + c0;   // row c of X_pb, zeros above the diagonal
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < 16; q += 4) {
+        const float4 u = *reinterpret_cast<const float4*>(sr + q);
+        const float4 v = *reinterpret_cast<const float4*>(xc + q);
+        acc += u.x * v.x;
+        acc += u.y * v.y;
+        acc += u.z * v.z;
+        acc += u.w * v.w;
+      }
+      Pn[r * LP + c] = acc;
+    }
+    for (int idx = tid; idx < pb * 256; idx += kThreads) {
+      const int j = idx / 256, e = idx % 256, rr = e / 16, cc = e % 16;
+      const float* xr = Wt + (c0 + rr) * LD + c0;
+      const float* t = Tmp + j * 256 + cc;
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc += xr[q] * t[q * 16];
+      Wt[(c0 + rr) * LD + 16 * j + cc] = -acc;
+    }
+    __syncthreads();
+    if (pb == 3) break;
+    // C(pb)
+    const int n0 = c0 + 16;   // first row / column of the trailing matrix
+    if (warp == 0) {
+      diag16_f32(S, Wt, Pn, true, n0, Lt, status);
+    } else {
+      const int t = tid - 32, nt = kThreads - 32;
+      // trailing blocks (bi, bj), pb+1 <= bj <= bi <= 3, except (pb+1, pb+1)
+      const int nb = 3 - pb;                  // block rows of the trailing matrix
+      const int nblk = nb * (nb + 1) / 2 - 1;
+      for (int idx = t; idx < nblk * 256; idx += nt) {
+        int b = idx / 256 + 1;                // triangle index, 0 is (pb+1, pb+1)
+        int bi = 0;
+        while (b > bi) b -= ++bi;
+        const int r = n0 + 16 * bi + (idx % 256) / 16, c = n0 + 16 * b + idx % 16;
+        const float* pr = Pn + r * LP;
+        const float* pc = Pn + c * LP;
+        float acc = 0.f;
+#pragma unroll
+        for (int q = 0; q < 16; q += 4) {
+          const float4 u = *reinterpret_cast<const float4*>(pr + q);
+          const float4 v = *reinterpret_cast<const float4*>(pc + q);
+          acc += u.x * v.x;
+          acc += u.y * v.y;
+          acc += u.z * v.z;
+          acc += u.w * v.w;
+        }
+        S[r * LD + c] -= acc;
+      }
+      for (int idx = t; idx < rows * 16; idx += nt) {
+        const int r = n0 + idx / 16, q = idx % 16;
+        S[r * LD + c0 + q] = Pn[r * LP + q];
+      }
+      // T_{pb+1, j} for j <= pb; L_{pb+1, pb} is still in Pn
+      for (int idx = t; idx < (pb + 1) * 256; idx += nt) {
+        const int j = idx / 256, rr = (idx % 256) / 16, cc = idx % 16;
+        const int r = n0 + rr;
+        float acc = 0.f;
+        for (int k = j; k <= pb; ++k) {
+          const float* lr = k < pb ? S + r * LD + 16 * k : Pn + r * LP;
+          const float* wc = Wt + 16 * k * LD + 16 * j + cc;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) acc += lr[q] * wc[q * LD];
+        }
+        Tmp[j * 256 + rr * 16 + cc] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < 64 * 16; idx += kThreads) {
+    const int r = idx / 16, c = (idx % 16) * 4;
+    float lo[4], wo[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      lo[e] = (c + e <= r) ? S[r * LD + c + e] : 0.f;
+      wo[e] = Wt[r * LD + c + e];
+    }
+    st_vec16(Lg + (size_t)r * ld + c, lo);
+    st_vec16(Wg + (size_t)r * 64 + c, wo);
+  }
+  __syncthreads();
+}
+
 // Factor the diagonal tile staged in S (float32: blocked by 16 columns;
 // float64: CTA-wide elimination, where the narrow float64 pipe makes one
 // warp's serial 16 x 16 factorisations slow).
@@ -743,6 +948,8 @@ template <typename T, int NB>
 __device__ __forceinline__ void potrf_tile(T* S, T* As, T* Bs, T* Lg, int ld, T* Wg, int* status) {
   if constexpr (sizeof(T) == 8)
     potrf_elim<T, NB>(S, gemm_ld(NB), Lg, ld, Wg, As, Bs, status);
+  else if constexpr (NB == 64)
+    potrf_la_f32(S, Bs, As, As + 64 * kPanelLd, As + 64 * kPanelLd + 3 * 256, Lg, ld, Wg, status);
   else
     potrf_smem<T, NB>(S, Bs, As, As + NB * kPanelLd, Lg, ld, Wg, status);
 }
@@ -866,8 +1073,14 @@ __device__ __forceinline__ bool run_factor_task(const CholTask tk, T* L, int P, 
   return ok;
 }
 
-template <typename T, int NB>
-__global__ void __launch_bounds__(kThreads, 2) chol_factor_kernel(T* L, int P, int Tt,
+// R: the register cap per thread.  255 when one CTA has the SM to itself:
+// below that the task code keeps values across its non-inlined calls in
+// memory, and the chain of diagonal tiles runs about 1.5x slower; 128 lets two
+// CTAs, or a factorisation CTA and other kernels, share an SM.
+constexpr int kRegsWide = 255, kRegsShared = 128;
+
+template <typename T, int NB, int R>
+__global__ void __maxnreg__(R) chol_factor_kernel(T* L, int P, int Tt,
                                                                const CholTask* tasks, int ntasks,
                                                                int* cnt, int* ticket, T* winv,
                                                                int* status, int* abort_flag) {
@@ -909,8 +1122,8 @@ __global__ void __launch_bounds__(kThreads, 2) chol_factor_kernel(T* L, int P, i
 // task) pairs from one merged queue in which every problem's tasks keep
 // their own order, so a claimed task depends only on tasks of its problem
 // claimed before it and the launch always makes progress.
-template <typename T, int NB>
-__global__ void __launch_bounds__(kThreads, 2) chol_factor_batch_kernel(
+template <typename T, int NB, int R>
+__global__ void __maxnreg__(R) chol_factor_batch_kernel(
     const FactorJob* jobs, const int2* queue, int nqueue, int* ticket, int* abort_flag) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* As = reinterpret_cast<T*>(smem_raw);
@@ -1461,9 +1674,41 @@ cudaError_t launch_factor(const CholPlan& p, void* L, int* status, cudaStream_t 
   int* cnt = p.d_sync;
   int* ticket = p.d_sync + p.T * p.T + 2 * p.T;
   int* abort_flag = ticket + 3;
-  chol_factor_kernel<T, NB><<<p.grid, kThreads, factor_smem<T, NB>(), s>>>(
-      (T*)L, p.P, p.T, p.d_tasks, p.ntasks, cnt, ticket, (T*)p.d_winv, status, abort_flag);
+  if (p.wide)
+    chol_factor_kernel<T, NB, kRegsWide><<<p.grid, kThreads, factor_smem<T, NB>(), s>>>(
+        (T*)L, p.P, p.T, p.d_tasks, p.ntasks, cnt, ticket, (T*)p.d_winv, status, abort_flag);
+  else
+    chol_factor_kernel<T, NB, kRegsShared><<<p.grid, kThreads, factor_smem<T, NB>(), s>>>(
+        (T*)L, p.P, p.T, p.d_tasks, p.ntasks, cnt, ticket, (T*)p.d_winv, status, abort_flag);
   return cudaGetLastError();
+}
+
+// opt in to the factor kernels' shared memory
+template <typename T, int NB>
+cudaError_t factor_smem_optin() {
+  const int bytes = (int)factor_smem<T, NB>();
+  cudaError_t e = cudaFuncSetAttribute(chol_factor_kernel<T, NB, kRegsWide>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(chol_factor_kernel<T, NB, kRegsShared>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(chol_factor_batch_kernel<T, NB, kRegsWide>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(chol_factor_batch_kernel<T, NB, kRegsShared>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
+template <typename T, int NB>
+void launch_factor_batch(const CholBatch& b, int* ticket, int* abort_flag, cudaStream_t s) {
+  if (b.wide)
+    chol_factor_batch_kernel<T, NB, kRegsWide><<<b.grid, kThreads, factor_smem<T, NB>(), s>>>(
+        b.d_jobs, b.d_queue, b.nqueue, ticket, abort_flag);
+  else
+    chol_factor_batch_kernel<T, NB, kRegsShared><<<b.grid, kThreads, factor_smem<T, NB>(), s>>>(
+        b.d_jobs, b.d_queue, b.nqueue, ticket, abort_flag);
 }
 
 template <typename T, int NB>
@@ -1511,7 +1756,8 @@ cudaError_t chol_batch_create(CholBatch* b, const std::vector<const CholPlan*>& 
   for (size_t q = 0; q < items.size(); ++q) queue[q] = make_int2(items[q].job, items[q].task);
   b->njobs = (int)jobs.size();
   b->nqueue = (int)queue.size();
-  b->grid = num_sms * ctas_per_sm;
+  b->wide = ctas_per_sm <= 1;
+  b->grid = num_sms * (b->wide ? 1 : ctas_per_sm);
   cudaError_t e = cudaMalloc(&b->d_jobs, jobs.size() * sizeof(FactorJob));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, queue.size() * sizeof(int2));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_ticket, 2 * sizeof(int));
@@ -1520,21 +1766,8 @@ cudaError_t chol_batch_create(CholBatch* b, const std::vector<const CholPlan*>& 
   if (e == cudaSuccess)
     e = cudaMemcpy(b->d_queue, queue.data(), queue.size() * sizeof(int2), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
-  if (b->is_f32)
-    e = b->nb == 64 ? cudaFuncSetAttribute(chol_factor_batch_kernel<float, 64>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)factor_smem<float, 64>())
-                    : cudaFuncSetAttribute(chol_factor_batch_kernel<float, 32>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)factor_smem<float, 32>());
-  else
-    e = b->nb == 64 ? cudaFuncSetAttribute(chol_factor_batch_kernel<double, 64>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)factor_smem<double, 64>())
-                    : cudaFuncSetAttribute(chol_factor_batch_kernel<double, 32>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)factor_smem<double, 32>());
-  return e;
+  if (b->is_f32) return b->nb == 64 ? factor_smem_optin<float, 64>() : factor_smem_optin<float, 32>();
+  return b->nb == 64 ? factor_smem_optin<double, 64>() : factor_smem_optin<double, 32>();
 }
 
 void chol_batch_destroy(CholBatch* b) {
@@ -1556,19 +1789,11 @@ cudaError_t chol_factor_batch(const CholBatch& b, cudaStream_t s) {
   int* ticket = b.d_ticket;
   int* abort_flag = b.d_ticket + 1;
   if (b.is_f32) {
-    if (b.nb == 64)
-      chol_factor_batch_kernel<float, 64><<<b.grid, kThreads, factor_smem<float, 64>(), s>>>(
-          b.d_jobs, b.d_queue, b.nqueue, ticket, abort_flag);
-    else
-      chol_factor_batch_kernel<float, 32><<<b.grid, kThreads, factor_smem<float, 32>(), s>>>(
-          b.d_jobs, b.d_queue, b.nqueue, ticket, abort_flag);
+    if (b.nb == 64) launch_factor_batch<float, 64>(b, ticket, abort_flag, s);
+    else launch_factor_batch<float, 32>(b, ticket, abort_flag, s);
   } else {
-    if (b.nb == 64)
-      chol_factor_batch_kernel<double, 64><<<b.grid, kThreads, factor_smem<double, 64>(), s>>>(
-          b.d_jobs, b.d_queue, b.nqueue, ticket, abort_flag);
-    else
-      chol_factor_batch_kernel<double, 32><<<b.grid, kThreads, factor_smem<double, 32>(), s>>>(
-          b.d_jobs, b.d_queue, b.nqueue, ticket, abort_flag);
+    if (b.nb == 64) launch_factor_batch<double, 64>(b, ticket, abort_flag, s);
+    else launch_factor_batch<double, 32>(b, ticket, abort_flag, s);
   }
   return cudaGetLastError();
 }
@@ -1584,47 +1809,28 @@ cudaError_t chol_potrf_tile(float* L, int P, int j, float* winv, int* status, cu
 }
 
 cudaError_t chol_plan_configure(CholPlan* plan, int P, int nb, int is_f32, int num_sms,
-                                int ctas_per_sm) {
+                                int ctas_per_sm, int wide) {
   *plan = CholPlan{};
   if (P % nb) return cudaErrorInvalidValue;
   plan->P = P;
   plan->nb = nb;
   plan->T = P / nb;
   plan->is_f32 = is_f32;
-  plan->grid = ctas_per_sm * num_sms;
+  plan->wide = wide < 0 ? (ctas_per_sm <= 1) : (wide != 0);
+  plan->grid = (plan->wide ? 1 : ctas_per_sm) * num_sms;
   if (is_f32)
     plan->cluster = nb == 64 ? pick_solve_cluster<float, 64>(P, plan->T)
                              : pick_solve_cluster<float, 32>(P, plan->T);
   else
     plan->cluster = nb == 64 ? pick_solve_cluster<double, 64>(P, plan->T)
                              : pick_solve_cluster<double, 32>(P, plan->T);
-  // opt in to the shared memory the factor kernel needs
-  cudaError_t e;
-  if (is_f32) {
-    if (nb == 64)
-      e = cudaFuncSetAttribute(chol_factor_kernel<float, 64>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)factor_smem<float, 64>());
-    else
-      e = cudaFuncSetAttribute(chol_factor_kernel<float, 32>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)factor_smem<float, 32>());
-  } else {
-    if (nb == 64)
-      e = cudaFuncSetAttribute(chol_factor_kernel<double, 64>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)factor_smem<double, 64>());
-    else
-      e = cudaFuncSetAttribute(chol_factor_kernel<double, 32>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)factor_smem<double, 32>());
-  }
-  return e;
+  if (is_f32) return nb == 64 ? factor_smem_optin<float, 64>() : factor_smem_optin<float, 32>();
+  return nb == 64 ? factor_smem_optin<double, 64>() : factor_smem_optin<double, 32>();
 }
 
 cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_sms,
-                             int ctas_per_sm) {
-  cudaError_t e = chol_plan_configure(plan, P, nb, is_f32, num_sms, ctas_per_sm);
+                             int ctas_per_sm, int wide) {
+  cudaError_t e = chol_plan_configure(plan, P, nb, is_f32, num_sms, ctas_per_sm, wide);
   if (e != cudaSuccess) return e;
   std::vector<CholTask> tasks = build_chol_tasks(plan->T, is_f32 && nb == 64);
   plan->ntasks = (int)tasks.size();

@@ -32,6 +32,8 @@ struct CholPlan {
   void* d_winv = nullptr;        // T inverse diagonal tiles, NB*NB each (factor precision)
   void* d_y = nullptr;           // forward-solve intermediate, P values (factor precision)
   int grid = 0;                  // persistent CTAs for the factorisation
+  int wide = 0;                  // 1: the factorisation CTAs use the whole register file
+                                 // (one per SM); 0: 128 registers a thread (SMs shared)
   int cluster = 0;               // CTAs of the cluster that runs both solves (0: chained CTAs)
 };
 
@@ -41,11 +43,13 @@ inline size_t chol_sync_words(int T) { return (size_t)T * T + 2 * (size_t)T + 4;
 
 // Shape the plan for order P (multiple of nb) without allocating anything:
 // tiles, factorisation grid, the solve's cluster size and the factor kernel's
-// shared-memory opt-in.  The caller then provides d_tasks (the list of
+// shared-memory opt-in.  wide = 1: one factorisation CTA per SM with the whole
+// register file (grid = num_sms); 0: ctas_per_sm CTAs per SM at 128 registers
+// a thread; -1: wide when ctas_per_sm is 1.  The caller then provides d_tasks (the list of
 // build_chol_tasks(T, is_f32 && nb == 64)) and ntasks, d_sync
 // (chol_sync_words(T) ints), d_winv (T * nb * nb values) and d_y (2P values).
 cudaError_t chol_plan_configure(CholPlan* plan, int P, int nb, int is_f32, int num_sms,
-                                int ctas_per_sm = 2);
+                                int ctas_per_sm = 2, int wide = -1);
 
 // Factor diagonal tile (j, j) of the float32 matrix L (P x P row-major, tiles
 // of 64, its trailing updates applied) in place, L_jj with zeros above the
@@ -57,7 +61,7 @@ cudaError_t chol_potrf_tile(float* L, int P, int j, float* winv, int* status, cu
 
 // Allocate / free the plan for order P (multiple of nb).
 cudaError_t chol_plan_create(CholPlan* plan, int P, int nb, int is_f32, int num_sms,
-                             int ctas_per_sm = 2);
+                             int ctas_per_sm = 2, int wide = -1);
 void chol_plan_destroy(CholPlan* plan);
 
 // Factor L (P x P row-major, lower triangle holds K on entry, L on exit) in
@@ -74,9 +78,10 @@ cudaError_t chol_solve(const CholPlan& plan, const void* L, const double* v, dou
 // problem's order kept (task t of a problem with n tasks is placed by
 // (t + 1/2) / n, so the problems advance together).  The CTAs of the launch
 // claim (problem, task) pairs by ticket; a wait that runs out stops every
-// CTA (SLIM_ETIMEOUT in that problem's status).
+// CTA (SLIM_ETIMEOUT in that problem's status).  ctas_per_sm 1: one CTA per
+// SM with the whole register file, as a wide plan.
 struct CholBatch {
-  int is_f32 = 0, nb = 0, grid = 0;
+  int is_f32 = 0, nb = 0, grid = 0, wide = 0;
   int njobs = 0, nqueue = 0;
   FactorJob* d_jobs = nullptr;
   int2* d_queue = nullptr;

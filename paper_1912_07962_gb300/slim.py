@@ -23,6 +23,7 @@ SLIM_F32, SLIM_F64 = 0, 1
 SLIM_PREC_FP64, SLIM_PREC_FP32 = 0, 1
 SLIM_SOLVE_FP64, SLIM_SOLVE_MIXED, SLIM_SOLVE_LSQR, SLIM_SOLVE_SG, SLIM_SOLVE_OLBFGS = 0, 1, 2, 3, 4
 SLIM_SOLVE_MIXED_TC = 5
+SLIM_SOLVE_MIXED_INV = 6
 SLIM_BLOCKS_VIEWS, SLIM_BLOCKS_RAYS, SLIM_BLOCKS_STREAM = 0, 1, 2
 
 # every function the header declares (checked by the CPU test suite)

@@ -47,13 +47,19 @@ def c2():
     return tomo_problem(workloads.C2)
 
 
+# the float32-factor forms: tiled factor and triangular sweeps; tensor-core
+# factor and inverse; tiled factor and tensor-core inverse
+SOLVERS = {"mixed": "SLIM_SOLVE_MIXED", "mixed_tc": "SLIM_SOLVE_MIXED_TC",
+           "mixed_inv": "SLIM_SOLVE_MIXED_INV"}
+
+
 def _context(sl, cfg, form, refine_iters=2, **kw):
     """The bench's chosen form (`mixed`) or the same pipeline with the float64
     factor (`fp64`), on torch's current stream."""
     common = dict(lookahead=LOOKAHEAD, ctas_per_sm=1, use_graph=True)
     common.update(kw)
-    if form in ("mixed", "mixed_tc"):
-        solver = sl.SLIM_SOLVE_MIXED if form == "mixed" else sl.SLIM_SOLVE_MIXED_TC
+    if form in SOLVERS:
+        solver = getattr(sl, SOLVERS[form])
         s = sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.det, cfg.r, cfg.lam, cfg.seed,
                     precision=sl.SLIM_PREC_FP32, solver=solver, refine_iters=refine_iters,
                     **common)
@@ -95,7 +101,7 @@ def _run_sampled(s, g, b, cfg, steps, check, tol, mem_at=()):
 # (24 MMA accumulations per entry of a 64-wide trailing update), a little
 # coarser than chains of rounded FMAs: its form refines three times
 @pytest.mark.parametrize("form,tol,refine", [("mixed", 1e-5, 2), ("mixed_tc", 1e-5, 3),
-                                             ("fp64", 1e-12, 0)])
+                                             ("mixed_inv", 1e-5, 2), ("fp64", 1e-12, 0)])
 def test_bench_configuration_at_full_size(sl, c2, form, tol, refine):
     cfg = workloads.C2
     g, _, _, b = c2
@@ -121,7 +127,7 @@ def _lambda_1e4_problem():
     return cfg, g, b, ev[-1] / ev[0]
 
 
-@pytest.mark.parametrize("form", ["mixed", "mixed_tc"])
+@pytest.mark.parametrize("form", ["mixed", "mixed_tc", "mixed_inv"])
 def test_mixed_solver_at_lambda_1e4(sl, form):
     # The solver alone at kappa(lambda I + G) = 1.1e7 (kappa * u32 = 0.66 against
     # 0.09 at the 256 x 256 workload): float64 iterate, residual and scatter,
@@ -130,11 +136,11 @@ def test_mixed_solver_at_lambda_1e4(sl, form):
     # tensor-core factor's three rounds leave 1.1e-6)
     cfg, g, b, kappa = _lambda_1e4_problem()
     assert kappa > 5e6, kappa
-    solver = sl.SLIM_SOLVE_MIXED if form == "mixed" else sl.SLIM_SOLVE_MIXED_TC
+    solver = getattr(sl, SOLVERS[form])
     # the tensor-core factor contracts a little more slowly here: five rounds
     s = sl.Slim(cfg.N, cfg.n_views, cfg.det, cfg.det, cfg.r, cfg.lam, cfg.seed,
                 precision=sl.SLIM_PREC_FP64, solver=solver,
-                refine_iters=3 if form == "mixed" else 5,
+                refine_iters=5 if form == "mixed_tc" else 3,
                 lookahead=LOOKAHEAD, ctas_per_sm=1, use_graph=True)
     s.set_stream(torch.cuda.current_stream().cuda_stream)
     s.set_data(b)
@@ -143,7 +149,7 @@ def test_mixed_solver_at_lambda_1e4(sl, form):
     s.close()
 
 
-@pytest.mark.parametrize("form", ["mixed", "mixed_tc"])
+@pytest.mark.parametrize("form", ["mixed", "mixed_tc", "mixed_inv"])
 def test_float32_form_at_lambda_1e4(sl, form):
     # The float32 form at lambda = 1e-4: its float32 residual and scatter
     # (float32 weights, float32 accumulation) are rounded at u32 of their

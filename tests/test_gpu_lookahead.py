@@ -122,8 +122,9 @@ def test_unsupported_combinations(sl):
                            lookahead=1)])
 
 
+@pytest.mark.parametrize("solver", ["SLIM_SOLVE_MIXED_TC", "SLIM_SOLVE_MIXED_INV"])
 @pytest.mark.parametrize("D,r,N,V,det", [(1, 5, 40, 30, 57), (3, 2, 24, 18, 35), (6, 3, 64, 30, 91)])
-def test_tensor_core_inverse_solves(sl, D, r, N, V, det):
+def test_tensor_core_inverse_solves(sl, D, r, N, V, det, solver):
     # the solves through X = L^{-1} (tensor-core inverse in the geometry
     # chain): the same iterates as the float64 oracle at the float32 bar,
     # on ragged orders (p = 342, 105, 364) and wrapping buffers
@@ -133,7 +134,7 @@ def test_tensor_core_inverse_solves(sl, D, r, N, V, det):
     sched = list(oslim.view_schedule(g, seed, steps))
     traj = [x for _, x, _ in oslim.run(oslim.tomo_source(g, b), sched, r, lam)]
     s = sl.Slim(g.N, g.n_views, g.det_u, g.det_u, r, lam, seed, precision=sl.SLIM_PREC_FP32,
-                solver=sl.SLIM_SOLVE_MIXED_TC, refine_iters=2, lookahead=D)
+                solver=getattr(sl, solver), refine_iters=2, lookahead=D)
     s.set_data(b)
     src = oslim.tomo_source(g, b)
     for k in range(1, steps + 1):
@@ -146,12 +147,13 @@ def test_tensor_core_inverse_solves(sl, D, r, N, V, det):
     s.close()
 
 
-def test_tensor_core_inverse_argument_checks(sl):
+@pytest.mark.parametrize("solver", ["SLIM_SOLVE_MIXED_TC", "SLIM_SOLVE_MIXED_INV"])
+def test_tensor_core_inverse_argument_checks(sl, solver):
     with pytest.raises(sl.SlimError) as ei:      # needs the pipelined form
         sl.Slim(32, 20, 47, 47, 2, 1e-2, 1, precision=sl.SLIM_PREC_FP32,
-                solver=sl.SLIM_SOLVE_MIXED_TC)
+                solver=getattr(sl, solver))
     assert ei.value.code == sl.SLIM_ENOTSUP
     with pytest.raises(sl.SlimError) as ei:      # 64-wide tiles only
         sl.Slim(32, 20, 47, 47, 2, 1e-2, 1, precision=sl.SLIM_PREC_FP32,
-                solver=sl.SLIM_SOLVE_MIXED_TC, lookahead=2, tile=32)
+                solver=getattr(sl, solver), lookahead=2, tile=32)
     assert ei.value.code == sl.SLIM_ENOTSUP
