@@ -694,10 +694,12 @@ def frames3d_block(sl, flush, stream, K, W, r_values=(0, 4), steps_per_view=46):
     return out
 
 
-def batch_block(sl, flush, stream, K, W, count=96):
+def batch_block(sl, flush, stream, K, W, count=96, tune=True):
     """Many uneven 2D problems (random-ray blocks) advancing together: one CUDA
-    graph per batch step with a parallel branch per problem, tile size and CTAs
-    per SM chosen by the autotuner per size class."""
+    graph per batch step with a parallel branch per problem and the problems'
+    factorisations in one merged launch; tile size and CTAs per SM chosen by
+    the autotuner per size class (tune=False: 64-wide tiles, 1 CTA per SM, no
+    tuning runs)."""
     import torch
     cfgs = workloads.batch_mix(count)
     t0 = time.perf_counter()
@@ -705,7 +707,7 @@ def batch_block(sl, flush, stream, K, W, count=96):
     for c in cfgs:
         sp = dict(N=c.N, n_views=c.n_views, det=c.det, ell=c.ell, r=c.r, lam=c.lam, seed=c.seed,
                   kind=sl.SLIM_BLOCKS_RAYS, precision=sl.SLIM_PREC_FP32, solver=sl.SLIM_SOLVE_MIXED)
-        tile, cps, ms = sl.autotune(sp, steps=3)
+        tile, cps, ms = sl.autotune(sp, steps=3) if tune else (64, 1, 0.0)
         alone_ms += ms
         sp.update(tile=tile, ctas_per_sm=cps)
         choices[f"{tile}x{cps}"] = choices.get(f"{tile}x{cps}", 0) + 1
@@ -752,7 +754,7 @@ def batch_block(sl, flush, stream, K, W, count=96):
             "factor_tflops_if_all_time": flops / (t / K) / 1e12,
             # the autotuner's best step time of each problem run alone, summed:
             # the step of the batch if the problems ran one after another
-            "one_by_one_ms_per_step": alone_ms,
+            "one_by_one_ms_per_step": alone_ms if tune else None,
             "autotune": {"choices_tile_x_ctas": choices, "seconds": tune_s}}
 
 
@@ -1175,6 +1177,76 @@ def main_frames(args):
                                                              max(1, args.frames_steps), 3)}))
 
 
+def tc_block(sl, flush, stream, reps=5):
+    """The float32-accurate tensor-core product (slim_tc_matmul: three bfloat16
+    terms per operand, six term products on tcgen05) and the tensor-core
+    factor + inverse (slim_chol_inverse), each through the C ABI with device
+    operands, timed with events on the caller's stream after two warm-up calls
+    (each call also allocates its few bytes of descriptors and synchronises)."""
+    import torch
+    peak = float(measured_peaks().get("bf16_tflops", 1900.0))
+    out = {"matmul": [], "chol_inverse": []}
+    g = torch.Generator(device="cuda").manual_seed(11)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for n in (4096, 8192):
+        A = torch.randn(n, n, device="cuda", generator=g)
+        B = torch.randn(n, n, device="cuda", generator=g)
+        Cm = torch.empty(n, n, device="cuda")
+        torch.cuda.synchronize()
+        for _ in range(2):
+            sl.tc_matmul(n, n, n, A, n, 0, B, n, 0, Cm, n, 0, stream_ptr=stream.cuda_stream)
+        ms = []
+        for i in range(reps):
+            flush.fill_(i)
+            ev[0].record(stream)
+            sl.tc_matmul(n, n, n, A, n, 0, B, n, 0, Cm, n, 0, stream_ptr=stream.cuda_stream)
+            ev[1].record(stream)
+            ev[1].synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        t = min(ms)
+        # accuracy on a sampled block against float64
+        ref = (A[:256].double() @ B[:256].double().T)
+        err = float(torch.linalg.norm(Cm[:256, :256].double() - ref[:, :256]) / torch.linalg.norm(ref[:, :256]))
+        eff = 2.0 * n ** 3 / (t * 1e-3) / 1e12
+        out["matmul"].append({"M=N=K": n, "ms": t, "float32_tflops": eff,
+                              "tensor_tflops": 6 * eff, "tensor_frac_of_bf16_peak": 6 * eff / peak,
+                              "rel_error_vs_float64": err})
+        del A, B, Cm
+    for p in (2178, 4104):
+        M = torch.randn(p, p + 16, device="cuda", generator=g, dtype=torch.float64) / (p ** 0.5)
+        G = M @ M.T
+        X = torch.empty(p, p, device="cuda")
+        torch.cuda.synchronize()
+        for _ in range(2):
+            sl.chol_inverse(G, 1e-3, X, stream_ptr=stream.cuda_stream)
+        ms = []
+        for i in range(reps):
+            flush.fill_(i)
+            ev[0].record(stream)
+            sl.chol_inverse(G, 1e-3, X, stream_ptr=stream.cuda_stream)
+            ev[1].record(stream)
+            ev[1].synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        t = min(ms)
+        out["chol_inverse"].append({"p": p, "ms": t,
+                                    "float32_tflops": (2.0 * p ** 3 / 3.0) / (t * 1e-3) / 1e12})
+    out["peak"] = {"bf16_tflops": peak, "source": "MEASURED_PEAKS.json (cuBLAS bf16, burst)"}
+    out["note"] = ("float32_tflops counts the float32 product's 2MNK (factor + inverse: p^3/3 + p^3/3); "
+                   "tensor_tflops the six bfloat16 term products the tensor cores execute")
+    return out
+
+
+def main_tc(args):
+    """The tensor-core product and inverse alone (one JSON line)."""
+    import torch
+    from paper_1912_07962_gb300 import build as slbuild, slim as sl
+    slbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    print(json.dumps({"tensor_core": tc_block(sl, flush, stream)}))
+
+
 def main_batch(args):
     """The batched block alone (one JSON line)."""
     import torch
@@ -1184,7 +1256,8 @@ def main_batch(args):
     torch.cuda.set_stream(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     print(json.dumps({"batched": batch_block(sl, flush, stream, max(1, args.batch_steps),
-                                             max(3, args.warmup))}))
+                                             max(3, args.warmup),
+                                             tune=not args.batch_no_tune)}))
 
 
 def main_tik(args):
@@ -1290,6 +1363,10 @@ def main():
                     help="timed steps of the 96-problem batched block (0: skip it)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched block and print that line")
+    ap.add_argument("--tc-only", action="store_true",
+                    help="time only the tensor-core product and factor inverse and print that line")
+    ap.add_argument("--batch-no-tune", action="store_true",
+                    help="batched block without the autotuner (64-wide tiles, 1 CTA per SM)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-steps", type=int, default=0)
     ap.add_argument("--cpu-warmup", type=int, default=6)
@@ -1318,6 +1395,8 @@ def main():
         main_frames(args)
     elif args.batch_only:
         main_batch(args)
+    elif args.tc_only:
+        main_tc(args)
     else:
         main_gpu(args)
 

@@ -197,8 +197,9 @@ typedef struct {
  *   tile          tile size of the tiled Cholesky: 32 or 64, 0 = default (64 for
  *                 the float32 factor, 32 for float64)
  *   ctas_per_sm   resident CTAs per SM of the persistent factorisation (1..4,
- *                 0 = default 1): 1 gives each CTA the whole register file, 2..4
- *                 cap it at 128 registers a thread.  With lookahead the D
+ *                 0 = chosen by the library: 1 for float32 factors of up to 96
+ *                 tiles a side, else 2): 1 gives each CTA the whole register
+ *                 file, 2..4 cap it at 128 registers a thread.  With lookahead the D
  *                 factorisations in flight share num_SMs * ctas_per_sm CTAs at
  *                 128 registers a thread (num_SMs * ctas_per_sm / D each), which
  *                 leaves room on the SMs for the iterate chain

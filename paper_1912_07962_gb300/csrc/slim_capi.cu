@@ -36,6 +36,7 @@ struct slim_ctx {
   int ramp = 0, r = 0, nslots = 1, ell = 0, p = 0, P = 0, taps = 0, nb = 32;
   int decay_after = 0;             // 1/k decay of the damping after this step (0: none)
   int tile = 0, ctas_per_sm = 1;
+  int cps_auto = 1;   // ctas_per_sm left to the library (0 in the step options)
   double lam = 0.0, eta = 1.0;
   unsigned long long seed = 0;
   std::vector<ViewGeom> h_views;
@@ -316,6 +317,18 @@ cudaError_t mark(slim_ctx* c, int i) {
 
 // Float32 factor with float64-residual refinement (solved through the
 // factor, or through its tensor-core inverse).
+// CTAs per SM of the plain form's persistent factorisation.  Left to the
+// library: one CTA per SM with the whole register file for float32 factors of
+// up to 96 tiles a side (latency-bound: the chain of diagonal tiles decides);
+// two at 128 registers for float64 factors and larger ones, which are bound by
+// their arithmetic and gain from more tasks in flight (measured: p = 2178
+// float64 5.6 ms against 6.0; p = 10240 float32 14.8 ms against 18.6; p = 2178
+// float32 0.66 ms against 1.02).
+inline int plan_ctas_per_sm(const slim_ctx* c) {
+  if (!c->cps_auto) return c->ctas_per_sm;
+  return (c->solver == SLIM_SOLVE_FP64 || c->P / c->nb > 96) ? 2 : 1;
+}
+
 // the pipelined forms whose iterate chain solves through X = L^{-1}
 inline bool uses_inverse(const slim_ctx* c) {
   return c->solver == SLIM_SOLVE_MIXED_TC || c->solver == SLIM_SOLVE_MIXED_INV;
@@ -1091,6 +1104,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     c->use_graph = step->use_graph;
     c->tile = step->tile;
     c->lookahead = step->lookahead;
+    c->cps_auto = step->ctas_per_sm == 0;
     c->ctas_per_sm = step->ctas_per_sm ? step->ctas_per_sm : 1;
     c->lsqr_max_iter = step->lsqr_max_iter;
     c->lsqr_tol = step->lsqr_tol;
@@ -1339,7 +1353,7 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
       chk(cudaMemset(c->d_lsqr, 0, cnt * sizeof(double)), "memset");
     } else if (dense_solve)
       chk(chol_plan_create(&c->plan, c->P, c->nb, is_mixed(c) ? 1 : 0,
-                           c->num_sms, c->ctas_per_sm), "chol plan");
+                           c->num_sms, plan_ctas_per_sm(c)), "chol plan");
     else
       chk(prepare_slice_solve(c->cap), "slice solve");
     if (st == SLIM_OK && c->a_mode != 0)
@@ -2139,7 +2153,7 @@ extern "C" slim_status slim_damped_solve(const double* G, int p, double lambda, 
   double *L = nullptr, *v = nullptr, *out = nullptr;
   int* status = nullptr;
   slim_status st = SLIM_OK;
-  cudaError_t e = chol_plan_create(&plan, P, nb, 0, sms, 1);
+  cudaError_t e = chol_plan_create(&plan, P, nb, 0, sms, 2);
   if (e == cudaSuccess) e = cudaMalloc(&L, (size_t)P * P * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&v, (size_t)P * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&out, (size_t)P * sizeof(double));

@@ -16,7 +16,7 @@ constexpr int kNb = 32;                                  // tile size of the flo
 constexpr int kMaxP = SLIM_NOALLOC_MAX_P;                // largest order accepted
 constexpr int kMaxT = kMaxP / kNb;
 constexpr int kMaxDevices = 64;
-constexpr int kCtasPerSm = 1;                            // as slim_damped_solve's plan
+constexpr int kCtasPerSm = 2;                            // as slim_damped_solve's plan
 
 constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 // An upper bound on the tasks of the T x T factorisation: one POTRF, TRSM and
