@@ -707,10 +707,13 @@ def batch_block(sl, flush, stream, K, W, count=96, tune=True):
     for c in cfgs:
         sp = dict(N=c.N, n_views=c.n_views, det=c.det, ell=c.ell, r=c.r, lam=c.lam, seed=c.seed,
                   kind=sl.SLIM_BLOCKS_RAYS, precision=sl.SLIM_PREC_FP32, solver=sl.SLIM_SOLVE_MIXED)
-        tile, cps, ms = sl.autotune(sp, steps=3) if tune else (64, 1, 0.0)
-        alone_ms += ms
-        sp.update(tile=tile, ctas_per_sm=cps)
-        choices[f"{tile}x{cps}"] = choices.get(f"{tile}x{cps}", 0) + 1
+        opt = (sl.autotune_opts(sp, steps=3) if tune else
+               dict(tile=64, ctas_per_sm=1, ray_lanes=32, pair_window=32, ms=0.0))
+        alone_ms += opt["ms"]
+        sp.update(tile=opt["tile"], ctas_per_sm=opt["ctas_per_sm"], ray_lanes=opt["ray_lanes"],
+                  pair_window=opt["pair_window"])
+        key = f"{opt['tile']}x{opt['ctas_per_sm']} lanes {opt['ray_lanes']} window {opt['pair_window']}"
+        choices[key] = choices.get(key, 0) + 1
         specs.append(sp)
     tune_s = time.perf_counter() - t0
     bt = sl.SlimBatch(specs)
@@ -755,7 +758,9 @@ def batch_block(sl, flush, stream, K, W, count=96, tune=True):
             # the autotuner's best step time of each problem run alone, summed:
             # the step of the batch if the problems ran one after another
             "one_by_one_ms_per_step": alone_ms if tune else None,
-            "autotune": {"choices_tile_x_ctas": choices, "seconds": tune_s}}
+            "autotune": {"choices": choices, "seconds": tune_s,
+                         "searched": "tile 32/64 x CTAs per SM 1/2/3, then threads per ray 8/16/32 x "
+                                     "pair window 16/32/64"}}
 
 
 def measured_peaks():

@@ -235,7 +235,15 @@ typedef struct {
  *   tik_reading   c_k, the Tikhonov rows that the stacked M_k holds: 0 = the
  *                 blocks of M_k, min(k, r+1) (slimLS on the stacked problem,
  *                 whose full-memory iterates reach the Tikhonov solution);
- *                 1 = r, as Eq. (slimTik) prints it */
+ *                 1 = r, as Eq. (slimTik) prints it
+ *   ray_lanes     random-ray blocks: threads per ray of the ray march with
+ *                 the residual and of the scatter, 8, 16 or 32 (0 = 32); a
+ *                 warp then serves 32 / ray_lanes rays (SLIM_EINVAL otherwise)
+ *   pair_window   2D random-ray blocks: the pair-overlap Gram gives each pair
+ *                 of rays one thread, and pairs whose overlap window is longer
+ *                 than pair_window steps (near-parallel rays) the whole warp;
+ *                 8..256 (0 = 32; SLIM_EINVAL otherwise)
+ *                 (both change only the order of floating-point sums) */
 typedef struct {
   double eta;
   int ramp;
@@ -251,6 +259,8 @@ typedef struct {
   int tik_reading;
   int decay_after;
   int olbfgs_memory;
+  int ray_lanes;
+  int pair_window;
 } slim_step_opts;
 
 /* SLIM_SOLVE_LSQR: the last step's LSQR iterations, its final estimate of
@@ -451,8 +461,10 @@ slim_status slim_get_launch_log(slim_ctx* ctx, double* factor_ms, double* iterat
 
 /* Autotuner: time the factorisation tile size and CTAs per SM for a problem's
  * size class (geometry, blocks, r, lambda as for slim_create; `base` gives the
- * other step options) over `steps` steps each, and return the fastest options
- * in *best (and its time per step in *best_ms).  A size class is the
+ * other step options) over `steps` steps each, then, for 2D random-ray blocks,
+ * the threads per ray (ray_lanes 8, 16, 32) and the pair Gram's cut-off
+ * (pair_window 16, 32, 64) with the chosen factorisation options, and return
+ * the fastest options in *best (and its time per step in *best_ms).  A size class is the
  * dimension, block kind, precisions and the Gram order p = (r+1) ell rounded
  * up to a multiple of 512.  Results are cached per size class for the life of
  * the process; with the environment variable

@@ -84,6 +84,8 @@ struct slim_ctx {
   FrameGeom* d_frames = nullptr;
   int* d_vnext = nullptr;          // [ell * taps] voxel-list links of the new block
   int olbfgs_memory = 0;           // pairs of the olbfgs comparator
+  int ray_lanes = 32;              // threads per ray: random-ray march and scatter
+  int pair_window = 32;            // pair Gram: longer windows go to the whole warp
   double* d_olb = nullptr;         // its scratch: g, S, Y, u, S^T Y, Y^T Y, partial sums
   int* d_olb_state = nullptr;      // its pair bookkeeping
   double* d_lsqr = nullptr;        // LSQR scratch: u [p], v, w, s, tmp [n], partial sums, stats [3]
@@ -257,6 +259,7 @@ StepArgs<T> make_args(slim_ctx* c) {
   a.tik_reading = c->tik_reading;
   a.cinv = c->d_cinv;
   a.sg = c->solver == SLIM_SOLVE_SG;
+  a.lanes = c->kind == SLIM_BLOCKS_VIEWS ? 32 : c->ray_lanes;
   a.cyclic = c->cyclic;
   a.perm = c->d_perm;
   a.perm_epoch = c->d_perm_epoch;
@@ -281,6 +284,8 @@ RayArgs make_ray_args(slim_ctx* c) {
   a.p = c->p;
   a.taps = c->taps;
   a.magic_n = c->N > 1 ? (unsigned)((0x100000000ull + c->N - 1) / c->N) : 0xFFFFFFFFu;
+  a.lanes = c->ray_lanes;
+  a.short_window = c->pair_window;
   a.kind = c->kind;
   a.steps_per_view = c->steps_per_view;
   a.seed = c->seed;
@@ -1112,7 +1117,11 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     c->tik_reading = step->tik_reading;
     c->decay_after = step->decay_after;
     c->olbfgs_memory = step->olbfgs_memory ? step->olbfgs_memory : 10;
+    c->ray_lanes = step->ray_lanes ? step->ray_lanes : 32;
+    c->pair_window = step->pair_window ? step->pair_window : 32;
     if (c->decay_after < 0 ||
+        (c->ray_lanes != 8 && c->ray_lanes != 16 && c->ray_lanes != 32) ||
+        c->pair_window < 8 || c->pair_window > 256 ||
         (c->solver == SLIM_SOLVE_OLBFGS &&
          (c->olbfgs_memory < 1 || c->olbfgs_memory > kOlbfgsMaxMem))) {
       delete c;
@@ -2212,25 +2221,62 @@ struct TuneKey {
 struct TuneVal {
   int tile, ctas;
   double ms;
+  int lanes = 0, window = 0;   // random-ray mapping (0: the defaults)
 };
 std::map<TuneKey, TuneVal> g_tune;
 std::mutex g_tune_mu;
 
+// One entry per line: the key's five fields, tile, CTAs per SM, ms, threads
+// per ray, pair window (lines of another layout are skipped).
 void load_tune_file() {
   const char* path = std::getenv("SLIM_AUTOTUNE_CACHE");
   if (!path) return;
   std::ifstream f(path);
-  TuneKey k;
-  TuneVal v;
-  while (f >> k.dim >> k.kind >> k.precision >> k.solver >> k.pclass >> v.tile >> v.ctas >> v.ms)
-    g_tune[k] = v;
+  std::string line;
+  while (std::getline(f, line)) {
+    std::istringstream is(line);
+    TuneKey k;
+    TuneVal v;
+    std::string extra;
+    if ((is >> k.dim >> k.kind >> k.precision >> k.solver >> k.pclass >> v.tile >> v.ctas >> v.ms >>
+         v.lanes >> v.window) &&
+        !(is >> extra))
+      g_tune[k] = v;
+  }
 }
 
 void save_tune_entry(const TuneKey& k, const TuneVal& v) {
   const char* path = std::getenv("SLIM_AUTOTUNE_CACHE");
   if (!path) return;
   std::ofstream f(path, std::ios::app);
-  f << k.str() << ' ' << v.tile << ' ' << v.ctas << ' ' << v.ms << '\n';
+  f << k.str() << ' ' << v.tile << ' ' << v.ctas << ' ' << v.ms << ' ' << v.lanes << ' '
+    << v.window << '\n';
+}
+
+// Mean step time of a temporary context with options o (1e30 on failure):
+// r + 1 untimed steps, then `steps` timed on the context's stream.
+double time_options(const slim_geometry* geom, const slim_blocks* blocks, int r, double lambda,
+                    const slim_step_opts& o, int steps, const std::vector<double>& b) {
+  slim_ctx* c = nullptr;
+  if (slim_create(geom, blocks, r, lambda, &o, &c) != SLIM_OK) return 1e30;
+  double ms = 1e30;
+  if (slim_set_data(c, b.data(), b.size(), SLIM_F64, 0) == SLIM_OK &&
+      slim_step(c, r + 1) == SLIM_OK && slim_sync(c) == SLIM_OK) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, c->stream);
+    slim_step(c, steps);
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float f = 0.f;
+    cudaEventElapsedTime(&f, e0, e1);
+    if (slim_sync(c) == SLIM_OK) ms = f / steps;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  slim_destroy(c);
+  return ms;
 }
 
 }  // namespace
@@ -2258,6 +2304,8 @@ extern "C" slim_status slim_autotune(const slim_geometry* geom, const slim_block
     if (it != g_tune.end()) {
       best->tile = it->second.tile;
       best->ctas_per_sm = it->second.ctas;
+      best->ray_lanes = it->second.lanes;
+      best->pair_window = it->second.window;
       if (best_ms) *best_ms = it->second.ms;
       return SLIM_OK;
     }
@@ -2272,29 +2320,33 @@ extern "C" slim_status slim_autotune(const slim_geometry* geom, const slim_block
       o.tile = t;
       o.ctas_per_sm = cps;
       o.use_graph = 1;
-      slim_ctx* c = nullptr;
-      if (slim_create(geom, blocks, r, lambda, &o, &c) != SLIM_OK) continue;
-      double ms = 1e30;
-      if (slim_set_data(c, b.data(), b.size(), SLIM_F64, 0) == SLIM_OK &&
-          slim_step(c, r + 1) == SLIM_OK && slim_sync(c) == SLIM_OK) {
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        cudaEventRecord(e0, c->stream);
-        slim_step(c, steps);
-        cudaEventRecord(e1, c->stream);
-        cudaEventSynchronize(e1);
-        float f = 0.f;
-        cudaEventElapsedTime(&f, e0, e1);
-        if (slim_sync(c) == SLIM_OK) ms = f / steps;
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-      }
-      slim_destroy(c);
-      if (ms < bestv.ms) bestv = TuneVal{t, cps, ms};
+      const double ms = time_options(geom, blocks, r, lambda, o, steps, b);
+      if (ms < bestv.ms)
+        bestv = TuneVal{t, cps, ms, b0.ray_lanes ? b0.ray_lanes : 32,
+                        b0.pair_window ? b0.pair_window : 32};
     }
   }
   if (bestv.tile == 0) return SLIM_ECUDA;
+  // 2D random-ray blocks: threads per ray of the march and scatter, and the
+  // pair Gram's cut-off, with the factorisation options just chosen
+  if (blocks->kind != SLIM_BLOCKS_VIEWS) {
+    for (int lanes : {8, 16, 32}) {
+      for (int window : {16, 32, 64}) {
+        slim_step_opts o = b0;
+        o.tile = bestv.tile;
+        o.ctas_per_sm = bestv.ctas;
+        o.use_graph = 1;
+        o.ray_lanes = lanes;
+        o.pair_window = window;
+        const double ms = time_options(geom, blocks, r, lambda, o, steps, b);
+        if (ms < bestv.ms) {
+          bestv.ms = ms;
+          bestv.lanes = lanes;
+          bestv.window = window;
+        }
+      }
+    }
+  }
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[key] = bestv;
@@ -2302,6 +2354,8 @@ extern "C" slim_status slim_autotune(const slim_geometry* geom, const slim_block
   }
   best->tile = bestv.tile;
   best->ctas_per_sm = bestv.ctas;
+  best->ray_lanes = bestv.lanes;
+  best->pair_window = bestv.window;
   if (best_ms) *best_ms = bestv.ms;
   return SLIM_OK;
 }

@@ -506,7 +506,9 @@ __global__ void __launch_bounds__(kCta) gram_update_kernel(StepArgs<T> a) {
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kCta) scatter_kernel(StepArgs<T> a) {
-  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  // a group of a.lanes threads per ring row (no group reductions: early exit is safe)
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = gt / a.lanes, lane = gt % a.lanes;
   if (q >= a.p || a.ring_ids[q] < 0) return;
   const bool is_new = (q / a.ell) == a.info->slot;
   // sg: x -= eta alpha_k A_k^T r_k, alpha_k = 1/lambda_k
@@ -515,7 +517,7 @@ __global__ void __launch_bounds__(kCta) scatter_kernel(StepArgs<T> a) {
   const int* rp = a.ring_pix + (size_t)q * a.taps;
   const double* rw = a.ring_w + (size_t)q * a.taps;
   const long long n = a.n;
-  for (int t = lane; t < a.taps; t += 32) {
+  for (int t = lane; t < a.taps; t += a.lanes) {
     int pix = rp[t];
     if (pix < 0) continue;
     if (c != T(0)) atomicAdd(&a.x[pix], c * (T)(a.cinv ? rw[t] * a.cinv[pix] : rw[t]));
@@ -826,7 +828,7 @@ cudaError_t launch_gram_update(const StepArgs<T>& a, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_scatter(const StepArgs<T>& a, cudaStream_t s) {
-  scatter_kernel<T><<<cdiv(a.p, kWarpsPerCta), kCta, 0, s>>>(a);
+  scatter_kernel<T><<<cdiv((long long)a.p * a.lanes, kCta), kCta, 0, s>>>(a);
   return cudaGetLastError();
 }
 

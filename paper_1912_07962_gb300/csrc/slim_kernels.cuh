@@ -45,6 +45,8 @@ struct StepArgs {
   const double* cinv;
   // sg (B_k = alpha_k I): the scatter takes z = r_k / lambda_k on the block's rows
   int sg;
+  // threads per ring row in the scatter: 8, 16 or 32 (32 for view blocks)
+  int lanes;
   // view blocks in the random cyclic order (a permutation of the views per
   // epoch) instead of i.i.d. draws; the current epoch's permutation and its epoch
   int cyclic;

@@ -169,39 +169,44 @@ __global__ void sample_rays_kernel(RayArgs a) {
 template <typename T>
 __global__ void __launch_bounds__(kCta) forward_rays_kernel(RayArgs a, const T* __restrict__ x,
                                                             const T* __restrict__ b) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (w >= a.ell) return;
-  const int q = a.info->slot * a.ell + w;
-  const int ray = a.ring_ids[q];
-  const RayDesc rd = decode_ray(ray, a.Du, a.Dv);
-  const ViewGeom v = a.views[rd.view];
-  const double cc = 0.5 * (double)(a.N - 1);
-  const long long off = (long long)rd.slice * a.N * a.N;
-  int* rp = a.ring_pix + (size_t)q * a.taps;
-  double* rw = a.ring_w + (size_t)q * a.taps;
+  // a group of a.lanes threads per ray (a warp holds 32 / a.lanes rays); every
+  // lane of the warp takes part in the group reductions
+  const int L = a.lanes;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = gt / L, lane = gt % L;
+  const bool active = w < a.ell;
+  const int q = active ? a.info->slot * a.ell + w : 0;
   T acc = T(0);
-  for (int s = lane; s < a.N; s += 32) {
-    const Tap2 tp = joseph_step(v, rd.t, cc, s);
-    const int pa = tp.wa != 0.0 ? inplane_pixel(v.row_step, a.N, s, tp.minor0) : -1;
-    const int pb = tp.wb != 0.0 ? inplane_pixel(v.row_step, a.N, s, tp.minor0 + 1) : -1;
-    rp[2 * s] = pa >= 0 ? (int)(off + pa) : -1;
-    rp[2 * s + 1] = pb >= 0 ? (int)(off + pb) : -1;
-    rw[2 * s] = pa >= 0 ? tp.wa : 0.0;
-    rw[2 * s + 1] = pb >= 0 ? tp.wb : 0.0;
-    if (pa >= 0) acc += (T)tp.wa * x[off + pa];
-    if (pb >= 0) acc += (T)tp.wb * x[off + pb];
+  if (active) {
+    const int ray = a.ring_ids[q];
+    const RayDesc rd = decode_ray(ray, a.Du, a.Dv);
+    const ViewGeom v = a.views[rd.view];
+    const double cc = 0.5 * (double)(a.N - 1);
+    const long long off = (long long)rd.slice * a.N * a.N;
+    int* rp = a.ring_pix + (size_t)q * a.taps;
+    double* rw = a.ring_w + (size_t)q * a.taps;
+    for (int s = lane; s < a.N; s += L) {
+      const Tap2 tp = joseph_step(v, rd.t, cc, s);
+      const int pa = tp.wa != 0.0 ? inplane_pixel(v.row_step, a.N, s, tp.minor0) : -1;
+      const int pb = tp.wb != 0.0 ? inplane_pixel(v.row_step, a.N, s, tp.minor0 + 1) : -1;
+      rp[2 * s] = pa >= 0 ? (int)(off + pa) : -1;
+      rp[2 * s + 1] = pb >= 0 ? (int)(off + pb) : -1;
+      rw[2 * s] = pa >= 0 ? tp.wa : 0.0;
+      rw[2 * s + 1] = pb >= 0 ? tp.wb : 0.0;
+      if (pa >= 0) acc += (T)tp.wa * x[off + pa];
+      if (pb >= 0) acc += (T)tp.wb * x[off + pb];
+    }
   }
-  acc = warp_sum(acc);
-  if (lane == 0) a.rhs[q] = (double)(acc - b[ray]);
+  for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
+  if (active && lane == 0) a.rhs[q] = (double)(acc - b[a.ring_ids[q]]);
 }
 
 // 2D: G[new_i][q] = G[q][new_i] for every ring row q, a thread per pair
 // (i, q) marching the new ray i over its overlap window with ray q.  Windows
-// longer than kShortWindow steps (near-parallel rays, and the diagonal) go to
-// the whole warp afterwards, one at a time, with the steps split over the
+// longer than a.short_window steps (near-parallel rays, and the diagonal) go
+// to the whole warp afterwards, one at a time, with the steps split over the
 // lanes.  A pair of two new rows is computed once, by the thread of the
 // smaller ring index, which writes both entries.
-constexpr int kShortWindow = 32;
 __global__ void __launch_bounds__(kCta) gram_pairs_kernel(RayArgs a) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -215,7 +220,7 @@ __global__ void __launch_bounds__(kCta) gram_pairs_kernel(RayArgs a) {
     mine = q < base || q >= base + a.ell || q >= qi;
     if (mine) w = pair_window(a, qi, q);
   }
-  const bool longw = w.hi - w.lo + 1 > kShortWindow;
+  const bool longw = w.hi - w.lo + 1 > a.short_window;
   double acc = 0.0;
   if (!longw) {
     const int* pi = a.ring_pix + (size_t)qi * a.taps;
@@ -490,7 +495,7 @@ cudaError_t launch_sample_rays(const RayArgs& a, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_forward_rays(const RayArgs& a, T* x, const T* b, cudaStream_t s) {
-  forward_rays_kernel<T><<<cdiv(a.ell, kWarpsPerCta), kCta, 0, s>>>(a, x, b);
+  forward_rays_kernel<T><<<cdiv((long long)a.ell * a.lanes, kCta), kCta, 0, s>>>(a, x, b);
   return cudaGetLastError();
 }
 

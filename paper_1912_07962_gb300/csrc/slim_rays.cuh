@@ -16,6 +16,8 @@ struct RayArgs {
   long long n, m;
   int ell, nslots, r, p, taps;       // taps = 2N per ray
   unsigned magic_n;                  // ceil(2^32 / N) (N = 1: 2^32 - 1), exact division by N
+  int lanes;                         // threads per ray of the march: 8, 16 or 32
+  int short_window;                  // pair Gram: windows of more steps go to the whole warp
   int kind, steps_per_view;          // 1: i.i.d. over all rays; 2: over arrived views
   unsigned long long seed;
   double lam;

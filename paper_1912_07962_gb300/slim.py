@@ -63,7 +63,8 @@ class slim_step_opts(C.Structure):
                 ("refine_iters", C.c_int), ("use_graph", C.c_int), ("tile", C.c_int),
                 ("ctas_per_sm", C.c_int), ("lookahead", C.c_int), ("lsqr_max_iter", C.c_int),
                 ("lsqr_tol", C.c_double), ("tik_lambda", C.c_double), ("tik_reading", C.c_int),
-                ("decay_after", C.c_int), ("olbfgs_memory", C.c_int)]
+                ("decay_after", C.c_int), ("olbfgs_memory", C.c_int), ("ray_lanes", C.c_int),
+                ("pair_window", C.c_int)]
 
 
 class SlimError(RuntimeError):
@@ -190,7 +191,8 @@ class Slim:
                  angles=None, a_mode=A_MATRIX_FREE, dim=2, det_v=1, kind=SLIM_BLOCKS_VIEWS,
                  steps_per_view=1, tile=0, ctas_per_sm=0, lookahead=0, lsqr_max_iter=0,
                  lsqr_tol=0.0, tik_lambda=0.0, tik_reading=0, decay_after=0, olbfgs_memory=0,
-                 frames=None, with_replacement=True, cyclic=False, _handle=None):
+                 frames=None, with_replacement=True, cyclic=False, ray_lanes=0, pair_window=0,
+                 _handle=None):
         lib = load()
         self._lib = lib
         self._angles = None
@@ -214,7 +216,7 @@ class Slim:
         blk = slim_blocks(kind, ell, seed, steps_per_view, int(with_replacement), int(cyclic))
         opts = slim_step_opts(eta, int(ramp), solver, refine_iters, int(use_graph), tile, ctas_per_sm,
                               lookahead, lsqr_max_iter, lsqr_tol, tik_lambda, tik_reading,
-                              decay_after, olbfgs_memory)
+                              decay_after, olbfgs_memory, ray_lanes, pair_window)
         h = C.c_void_p()
         st = lib.slim_create(C.byref(g), C.byref(blk), r, lam, C.byref(opts), C.byref(h))
         if st != SLIM_OK:
@@ -453,7 +455,7 @@ def damped_solve_noalloc(G, lam, rhs, z, stream_ptr=0):
 def problem_structs(specs):
     """ctypes arrays (geometry, blocks, r, lambda, step options) for a list of
     dicts with keys N, n_views, det, ell, r, lam, seed and optional precision,
-    solver, kind, use_graph, tile, ctas_per_sm, refine_iters."""
+    solver, kind, use_graph, tile, ctas_per_sm, refine_iters, ray_lanes, pair_window."""
     n = len(specs)
     G = (slim_geometry * n)()
     B = (slim_blocks * n)()
@@ -468,7 +470,24 @@ def problem_structs(specs):
         L[i] = sp["lam"]
         S[i] = slim_step_opts(1.0, 0, sp.get("solver", 0), sp.get("refine_iters", 2), 0,
                               sp.get("tile", 0), sp.get("ctas_per_sm", 0), sp.get("lookahead", 0))
+        S[i].ray_lanes = sp.get("ray_lanes", 0)
+        S[i].pair_window = sp.get("pair_window", 0)
     return G, B, R, L, S
+
+
+def autotune_opts(spec, steps=3):
+    """The autotuner's choice for a problem spec (dict as in problem_structs):
+    a dict of tile, ctas_per_sm, ray_lanes, pair_window and the step time ms."""
+    lib = load()
+    G, B, R, L, S = problem_structs([spec])
+    best = slim_step_opts()
+    ms = C.c_double()
+    st = lib.slim_autotune(C.byref(G[0]), C.byref(B[0]), R[0], L[0], C.byref(S[0]), steps,
+                           C.byref(best), C.byref(ms))
+    if st != SLIM_OK:
+        raise SlimError(st, "slim_autotune failed")
+    return {"tile": best.tile, "ctas_per_sm": best.ctas_per_sm, "ray_lanes": best.ray_lanes,
+            "pair_window": best.pair_window, "ms": ms.value}
 
 
 def autotune(spec, steps=3):

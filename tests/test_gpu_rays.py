@@ -135,3 +135,73 @@ def test_random_rays_2d_decaying_damping(sl):
     s.step(steps)
     assert rel(s.get_x(), x) < 1e-12
     s.close()
+
+
+# The mapping the autotuner chooses for random-ray blocks: threads per ray of
+# the march and scatter, and the pair Gram's cut-off between a thread per pair
+# and the whole warp.  Only the order of floating-point sums changes.
+@pytest.mark.parametrize("lanes,window", [(8, 16), (16, 64), (32, 8), (8, 256)])
+def test_random_rays_2d_thread_mappings(sl, lanes, window):
+    N, V, D, ell, r, lam, seed = 40, 24, 57, 37, 3, 2e-2, 12
+    g = joseph.Geometry(N, V, D)
+    A = joseph.full_matrix(g)
+    b = workloads.add_noise(A @ workloads.phantom_2d(N, seed, 5), workloads.noise_direction(g.m, seed), 0.01)
+    steps = 8
+    sched = list(oslim.random_ray_schedule(seed, ell, g.m, steps))
+    traj = [x for _, x, _ in oslim.run(oslim.tomo_source(g, b), sched, r, lam)]
+    s = sl.Slim(N, V, D, ell, r, lam, seed, kind=sl.SLIM_BLOCKS_RAYS, ray_lanes=lanes,
+                pair_window=window)
+    s.set_data(b)
+    for k, xo in enumerate(traj, start=1):
+        s.step(1)
+        assert rel(s.get_x(), xo) < 1e-12, (lanes, window, k)
+        if k == steps:
+            ids, G, _ = s.get_memory()
+            assert np.array_equal(ids, _ring_ids(sched, k, r, ell))
+            M = joseph.rows(g, ids)
+            Go = (M @ M.T).toarray()
+            assert np.max(np.abs(G - Go)) <= 1e-13 * np.max(np.abs(Go))
+    s.close()
+
+
+@pytest.mark.parametrize("lanes", [8, 16])
+def test_streaming_3d_thread_mappings(sl, lanes):
+    g, b, c = _small3d()
+    steps = 7
+    sched = list(oslim.streaming_ray_schedule(c["seed"], c["ell"], c["V"], c["Du"] * c["N"],
+                                              c["spv"], steps))
+    traj = [x for _, x, _ in oslim.run(oslim.tomo_source(g, b), sched, c["r"], c["lam"])]
+    s = sl.Slim(c["N"], c["V"], c["Du"], c["ell"], c["r"], c["lam"], c["seed"], dim=3, det_v=c["N"],
+                kind=sl.SLIM_BLOCKS_STREAM, steps_per_view=c["spv"], ray_lanes=lanes)
+    s.set_data(b)
+    for k, xo in enumerate(traj, start=1):
+        s.step(1)
+        assert rel(s.get_x(), xo) < 1e-12, (lanes, k)
+    s.close()
+
+
+def test_thread_mapping_argument_checks(sl):
+    for kw in (dict(ray_lanes=12), dict(ray_lanes=64), dict(pair_window=4), dict(pair_window=300)):
+        with pytest.raises(sl.SlimError) as ei:
+            sl.Slim(24, 18, 35, 20, 2, 1e-2, 1, kind=sl.SLIM_BLOCKS_RAYS, **kw)
+        assert ei.value.code == sl.SLIM_EINVAL, kw
+
+
+def test_autotuner_picks_a_ray_mapping(sl):
+    spec = dict(N=48, n_views=30, det=69, ell=64, r=2, lam=1e-2, seed=31, kind=sl.SLIM_BLOCKS_RAYS,
+                precision=sl.SLIM_PREC_FP32, solver=sl.SLIM_SOLVE_MIXED)
+    best = sl.autotune_opts(spec, steps=2)
+    assert best["tile"] in (32, 64) and best["ctas_per_sm"] in (1, 2, 3)
+    assert best["ray_lanes"] in (8, 16, 32) and best["pair_window"] in (16, 32, 64)
+    assert 0.0 < best["ms"] < 1e3
+    again = sl.autotune_opts(spec, steps=2)          # the size class is cached
+    assert again == best
+    # the chosen options run
+    s = sl.Slim(spec["N"], spec["n_views"], spec["det"], spec["ell"], spec["r"], spec["lam"],
+                spec["seed"], precision=spec["precision"], solver=spec["solver"], kind=spec["kind"],
+                tile=best["tile"], ctas_per_sm=best["ctas_per_sm"], ray_lanes=best["ray_lanes"],
+                pair_window=best["pair_window"])
+    s.set_data(np.zeros(spec["n_views"] * spec["det"], dtype=np.float32))
+    s.step(4)
+    s.sync()
+    s.close()
