@@ -837,7 +837,8 @@ def unet_block(sl, flush, stream, reps=10, batch=8):
             "train_gflop": batch * fl["train"] * 1e-9, "train_tflops": t_tf,
             "train_images_per_s": batch / t_ms * 1e3,
             "bf16_peak_tflops": peak, "forward_frac_of_measured_bf16": f_tf / peak if peak else None,
-            "note": ("implicit-GEMM convolutions on mma.sync bfloat16 tensor cores; activations as "
+            "note": ("implicit-GEMM convolutions on the tcgen05 tensor cores (bfloat16 operands, "
+                     "float32 accumulators in tensor memory); activations as "
                      "3 bfloat16 terms (weight gradients 2 x 2), so the pipe executes 3x the flops "
                      "counted here; L2 flushed before each timed call")}
 

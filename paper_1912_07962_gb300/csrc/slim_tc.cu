@@ -20,6 +20,7 @@
 #include "slim_grid.cuh"
 #include "slim_lookahead.cuh"
 #include "slim_tc.cuh"
+#include "slim_tcgen05.cuh"
 
 namespace slim {
 
@@ -33,108 +34,27 @@ constexpr int kStageBytes = 3 * kTermA + 3 * kTermB;  // 72 KB
 constexpr int kTmemCols = kTcBN;                     // float32 accumulator: one column per n
 constexpr unsigned kSpinLimit = 1u << 24;            // mbarrier polls before giving up
 
-// ----------------------------------------------------------------------------
-// PTX wrappers
-// ----------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-// Bounded wait for the phase with the given parity; false if it ran out.
+// PTX wrappers (slim_tcgen05.cuh), with this kernel's instruction shape
+using t5::desc_sw128;
+using t5::fence_barrier_init;
+using t5::fence_proxy_async;
+using t5::mbar_init;
+using t5::mma_commit;
+using t5::smem_u32;
+using t5::tmem_alloc;
+using t5::tmem_dealloc;
+using t5::tmem_ld8;
+__device__ __forceinline__ void tc_fence_before() { t5::fence_before(); }
+__device__ __forceinline__ void tc_fence_after() { t5::fence_after(); }
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (unsigned it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
+  return t5::mbar_wait(bar, parity, kSpinLimit);
 }
-
-__device__ __forceinline__ void fence_barrier_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// Make this thread's generic-proxy shared-memory stores visible to the
-// tensor cores (async proxy).
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Tensor-memory allocation (one warp, all lanes).
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major tile in the 128-byte swizzle:
-// rows of 128 bytes, eight-row atoms of 1024 bytes one after another (stride
-// byte offset 1024), start address 1024-aligned (base offset 0).
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);          // start address, bits 0-13
-  d |= (uint64_t)1 << 16;                           // leading byte offset (unused here), bits 16-29
-  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset, bits 32-45
-  d |= (uint64_t)1 << 46;                           // descriptor version, bits 46-47
-  d |= (uint64_t)2 << 61;                           // layout: 128-byte swizzle, bits 61-63
-  return d;
-}
-
-// Instruction descriptor: kind f16 with bfloat16 A and B, float32 D, both
-// operands K-major, M = 128, N = kTcBN.
-constexpr uint32_t kIdesc = (1u << 4)                        // D float32
-                            | (1u << 7)                      // A bfloat16
-                            | (1u << 10)                     // B bfloat16
-                            | ((uint32_t)(kTcBN >> 3) << 17) // N / 8
-                            | ((uint32_t)(kTcBM >> 4) << 24);// M / 16
-
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) { return desc_sw128(addr); }
+// Instruction descriptor: M = 128, N = kTcBN
+constexpr uint32_t kIdesc = t5::idesc_bf16(kTcBM, kTcBN);
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                          uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   bar)
-               : "memory");
-}
-
-// 8 consecutive float32 accumulator columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+  t5::mma_bf16(tmem_d, adesc, bdesc, kIdesc, accumulate);
 }
 
 // ----------------------------------------------------------------------------
@@ -169,11 +89,7 @@ __device__ __forceinline__ void split8(const float (&x)[8], uint4& t0, uint4& t1
   t2 = make_uint4(w2[0], w2[1], w2[2], w2[3]);
 }
 
-// Byte offset of 16-byte chunk c (k = 8c .. 8c+7) of row `row` in a K-major
-// 128-byte-swizzled term tile.
-__device__ __forceinline__ uint32_t sw128_off(int row, int c) {
-  return (uint32_t)(row * 128 + ((c ^ (row & 7)) << 4));
-}
+using t5::sw128_off;
 
 // Stage rows [0, R) x k [k0, k0 + 64) of op(X) into the three term tiles at
 // `dst` (term t at dst + t * R * 128).  op(X)[r][k] is X[(r0 + r) * ld + k]

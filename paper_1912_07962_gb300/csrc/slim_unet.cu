@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "../../include/slim.h"
+#include "slim_tcgen05.cuh"
 #include "slim_unet.cuh"
 
 namespace {
@@ -132,30 +133,23 @@ cudaError_t gemm(int M, int N, int K, const float* A, int lda, const float* B, i
 
 
 // ---------------------------------------------------------------------------
-// Tensor-core GEMM (mma.sync m16n8k16, bfloat16 operands, float32
-// accumulation) with operand loaders, so that the 3x3 convolutions run as
+// Tensor-core GEMM with operand loaders, so that the 3x3 convolutions run as
 // implicit GEMMs: the im2col matrix is gathered tile by tile from the
 // activations into shared memory and never written out.
 //
 //   C[m][n] (+)= sum_k A(m, k) B(n, k)  (+ bias[m]) (ReLU)
 //
-// Float32 values reach the bfloat16 pipe as a sum of T bfloat16 terms,
-// x = x_0 + x_1 + ... with x_j = bf16(x - x_0 - ... - x_{j-1}) (nearest
-// even).  T = 3 carries 24 significant bits, i.e. the float32 value itself
-// (up to the last bit); T = 2 carries 16.  The weights used by the network
-// are bfloat16 values already (T = 1).  The products x_i y_j with
+// Float32 values reach the bfloat16 tensor cores as a sum of T bfloat16
+// terms, x = x_0 + x_1 + ... with x_j = bf16(x - x_0 - ... - x_{j-1})
+// (nearest even).  T = 3 carries 24 significant bits, i.e. the float32 value
+// itself (up to the last bit); T = 2 carries 16.  The weights used by the
+// network are bfloat16 values already (T = 1).  The products x_i y_j with
 // i + j < max(TA, TB) are accumulated, which drops only terms below the
 // float32 rounding of the sum (T = 3 x 1) or below 2^-16 relative (2 x 2).
-//
-// CTA tile BM x 128 x 32, 8 warps; each operand tile is stored per term as
-// rows of 32 bfloat16 (64 bytes, four 16-byte chunks, chunk c of row r at
-// c ^ ((r >> 1) & 3)) so that both the 16-byte stores of the staging and the
-// ldmatrix reads of the fragments are free of bank conflicts.  Two stages:
-// the next k-slab is loaded into registers while the current one is
-// multiplied.  With gridDim.z > 1 the k range is split and the partial sums
-// are added atomically into C.
+// A loader gives 8 consecutive k of one row at a time; with gridDim.z > 1
+// the k range is split and the partial sums are added atomically into C.
+// The kernel itself (tcgen05, tensor memory) is t5_gemm_kernel below.
 // ---------------------------------------------------------------------------
-constexpr int kTcBN = 128, kTcBK = 32;
 
 // C[m][n] = acc (+ bias[m]) (+ C[m][n]) (ReLU); atomically added when split.
 struct OutPlain {
@@ -400,28 +394,33 @@ struct LoadUpTapPix {
   }
 };
 
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(addr));
-}
+// ---------------------------------------------------------------------------
+// The same GEMM on the tcgen05 tensor cores.  The MMA's M is the GEMM's n
+// (pixels, 128 per CTA) and its N the GEMM's m (channels, BN = 32..256 per
+// CTA), so one tile covers all output channels of up to 128 pixels and the
+// float32 accumulator lives in BN columns of tensor memory.  K runs in
+// slices of 64 (128-byte rows of bfloat16): the 256 threads gather a slice
+// of both operands through the loaders, split it into bfloat16 terms and
+// store each term tile in the 128-byte-swizzled K-major layout; one thread
+// issues the term products a_i b_j (i + j < max(TA, TB)) of its four K = 16
+// steps and commits them to the slice's mbarrier, while the threads gather
+// the next slice into the other stage.  The epilogue reads the accumulator
+// (warp w: lanes 32 (w % 4) .. +31, half w / 4 of the columns) and writes
+// through the output policy; consecutive lanes are consecutive pixels.
+// Every mbarrier wait is bounded: one that runs out records 1 in
+// g_t5_timeout and the CTA skips to the end.
+// ---------------------------------------------------------------------------
+constexpr int kT5N = 128;            // pixels per CTA (the MMA's M)
+constexpr int kT5K = 64;             // K per slice
+constexpr unsigned kT5Spin = 1u << 24;
+__device__ int g_t5_timeout = 0;
 
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                               uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// Split 8 float32 values into T bfloat16 terms and store each term's 16
-// bytes at its swizzled place (row r, chunk kg) of the term's tile.  One
-// cvt.rn.bf16x2 rounds two values; the residual is exact in float32.
+// Split 8 float32 values into T bfloat16 terms at chunk kg of row r of a
+// 128-byte-swizzled K-major tile (term j at tile0 + j * tile_bytes).
 template <int T>
-__device__ __forceinline__ void stage_terms(unsigned char* tile0, int tile_bytes, int r, int kg,
-                                            float (&v)[8]) {
-  const int off = r * 64 + ((kg ^ ((r >> 1) & 3)) << 4);
+__device__ __forceinline__ void stage_terms128(unsigned char* tile0, int tile_bytes, int r, int kg,
+                                               float (&v)[8]) {
+  const uint32_t off = slim::t5::sw128_off(r, kg);
 #pragma unroll
   for (int j = 0; j < T; ++j) {
     uint32_t w[4];
@@ -439,150 +438,194 @@ __device__ __forceinline__ void stage_terms(unsigned char* tile0, int tile_bytes
   }
 }
 
-template <class LA, class LB, class OUT, int BM, int TA, int TB>
-__global__ void __launch_bounds__(kT) tc_gemm_kernel(OUT out, LA la, LB lb, int K, int kchunk) {
-  constexpr int WMW = BM >= 64 ? 2 : 1, WNW = 8 / WMW;   // warps along M, N
-  constexpr int WTM = BM / WMW, WTN = kTcBN / WNW;        // warp tile
-  constexpr int MT = WTM / 16, NT = WTN / 8;
-  static_assert(MT >= 1 && NT % 2 == 0, "warp tile");
-  constexpr int A_BYTES = BM * 64, B_BYTES = kTcBN * 64;
-  constexpr int STAGE = A_BYTES * TA + B_BYTES * TB;
-  constexpr int TMAX = TA > TB ? TA : TB;
-  constexpr int GA = (BM * 4 + kT - 1) / kT, GB = (kTcBN * 4) / kT;   // 8-k groups per thread
-  extern __shared__ __align__(128) unsigned char tc_smem[];
+template <int BN, int TA, int TB>
+struct T5Shape {
+  static constexpr int kTermN = kT5N * 128;            // bytes of one pixel-side term tile
+  static constexpr int kTermM = BN * 128;              // of one channel-side term tile
+  static constexpr int kStage = TB * kTermN + TA * kTermM;
+  static constexpr int kSmem = 2 * kStage + 1024;      // two stages, 1024-byte alignment slack
+  static constexpr int kCallsN = kT5N * 8 / kT;        // 8-value gathers per thread and slice
+  static constexpr int kCallsM = (BN * 8 + kT - 1) / kT;
+};
+
+template <class LA, class LB, class OUT, int BN, int TA, int TB>
+__global__ void __launch_bounds__(kT, 1) t5_gemm_kernel(OUT out, LA la, LB lb, int K, int kchunk) {
+  using S = T5Shape<BN, TA, TB>;
+  namespace t5 = slim::t5;
+  extern __shared__ unsigned char t5_raw[];
+  __shared__ uint64_t s_bar[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(t5_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wm = warp % WMW, wn = warp / WMW;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * kTcBN;
+  const int m0 = blockIdx.y * BN;
   const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
-  const int ra = tid % BM, rb = tid % kTcBN;
-  const typename LA::Row rowA = la.row(m0 + ra);
-  const typename LB::Row rowB = lb.row(n0 + rb);
-  float va[GA][8], vb[GB][8];
-  auto fetch = [&](int k0) {
-#pragma unroll
-    for (int i = 0; i < GA; ++i) {
-      const int kg = tid / BM + i * (kT / BM);
-      if (kg < 4) la.load8(rowA, k0 + kg * 8, kend, va[i]);
-    }
-#pragma unroll
-    for (int i = 0; i < GB; ++i) lb.load8(rowB, k0 + (tid / kTcBN + i * 2) * 8, kend, vb[i]);
-  };
-  auto stage = [&](int s) {
-    unsigned char* base = tc_smem + s * STAGE;
-#pragma unroll
-    for (int i = 0; i < GA; ++i) {
-      const int kg = tid / BM + i * (kT / BM);
-      if (kg < 4) stage_terms<TA>(base, A_BYTES, ra, kg, va[i]);
-    }
-#pragma unroll
-    for (int i = 0; i < GB; ++i)
-      stage_terms<TB>(base + TA * A_BYTES, B_BYTES, rb, tid / kTcBN + i * 2, vb[i]);
-  };
-  float acc[MT][NT][4];
-#pragma unroll
-  for (int i = 0; i < MT; ++i)
-#pragma unroll
-    for (int j = 0; j < NT; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-  const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(tc_smem);
-  int cur = 0;
-  if (kbeg < kend) {
-    fetch(kbeg);
-    stage(0);
+  const int nslice = kend > kbeg ? (kend - kbeg + kT5K - 1) / kT5K : 0;
+  const int ntiles = (out.N + kT5N - 1) / kT5N;
+  constexpr int TMAX = TA > TB ? TA : TB;
+  constexpr uint32_t kIdesc = t5::idesc_bf16(kT5N, BN);
+
+  if (tid == 0) {
+    t5::mbar_init(t5::smem_u32(&s_bar[0]), 1);
+    t5::mbar_init(t5::smem_u32(&s_bar[1]), 1);
+    s_fail = 0;
+    t5::fence_barrier_init();
   }
+  if (warp == 0) t5::tmem_alloc(t5::smem_u32(&s_tmem), BN);
+  t5::fence_before();
   __syncthreads();
-  for (int k0 = kbeg; k0 < kend; k0 += kTcBK) {
-    const bool more = k0 + kTcBK < kend;
-    if (more) fetch(k0 + kTcBK);
-    const uint32_t sA = smem0 + cur * STAGE, sB = sA + TA * A_BYTES;
+  t5::fence_after();
+  const uint32_t tmem = s_tmem;
+
+  // this thread's rows: pixel row tid % 128 (chunks tid / 128 + 2 i), and
+  // channel rows idx % BN for idx = tid + 256 i (chunk idx / BN)
+  const int rn = tid % kT5N;
+  typename LA::Row rowM[S::kCallsM];
 #pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {   // two k16 steps per slab
-      uint32_t af[TA][MT][4], bf[TB][NT][2];
-#pragma unroll
-      for (int j = 0; j < TA; ++j)
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-          const int r = wm * WTM + mt * 16 + (lane & 15);
-          const int ch = kk * 2 + (lane >> 4);
-          ldsm_x4(af[j][mt], sA + j * A_BYTES + r * 64 + ((ch ^ ((r >> 1) & 3)) << 4));
-        }
-#pragma unroll
-      for (int j = 0; j < TB; ++j)
-#pragma unroll
-        for (int nt = 0; nt < NT; nt += 2) {
-          const int r = wn * WTN + nt * 8 + (lane & 7) + ((lane >> 4) << 3);
-          const int ch = kk * 2 + ((lane >> 3) & 1);
-          uint32_t q[4];
-          ldsm_x4(q, sB + j * B_BYTES + r * 64 + ((ch ^ ((r >> 1) & 3)) << 4));
-          bf[j][nt][0] = q[0]; bf[j][nt][1] = q[1];
-          bf[j][nt + 1][0] = q[2]; bf[j][nt + 1][1] = q[3];
-        }
-#pragma unroll
-      for (int i = 0; i < TA; ++i)
-#pragma unroll
-        for (int j = 0; j < TB; ++j) {
-          if (i + j >= TMAX) continue;
-#pragma unroll
-          for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(acc[mt][nt], af[i][mt], bf[j][nt][0], bf[j][nt][1]);
-        }
-    }
-    if (more) stage(cur ^ 1);
-    __syncthreads();
-    cur ^= 1;
+  for (int i = 0; i < S::kCallsM; ++i) {
+    const int idx = tid + i * kT;
+    rowM[i] = la.row(idx < BN * 8 ? m0 + idx % BN : m0 + BN);   // past the tile: unused
   }
-  const bool split = gridDim.z > 1;
-  const int g = lane >> 2, t4 = lane & 3;
+
+  // pixel tiles blockIdx.x, + gridDim.x, ...; slices are numbered across the
+  // tiles (cg) for the stages' mbarrier phases
+  int cg = 0;
+  for (int tile = blockIdx.x; tile < ntiles && !s_fail; tile += gridDim.x) {
+    const int n0 = tile * kT5N;
+    const typename LB::Row rowN = lb.row(n0 + rn);
+    bool started = false;   // thread 0: an MMA has written this tile's accumulator
+    for (int c = 0; c < nslice; ++c, ++cg) {
+      const int st = cg & 1;
+      unsigned char* sn = smem + st * S::kStage;
+      unsigned char* sm = sn + TB * S::kTermN;
+      if (cg >= 2 &&
+          !t5::mbar_wait(t5::smem_u32(&s_bar[st]), (uint32_t)(((cg >> 1) - 1) & 1), kT5Spin))
+        s_fail = 1;
+      const int k0 = kbeg + c * kT5K;
+      {
+        float vn[S::kCallsN][8], vm[S::kCallsM][8];
 #pragma unroll
-  for (int mt = 0; mt < MT; ++mt)
+        for (int i = 0; i < S::kCallsN; ++i) lb.load8(rowN, k0 + (tid / kT5N + 2 * i) * 8, kend, vn[i]);
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
+        for (int i = 0; i < S::kCallsM; ++i) {
+          const int idx = tid + i * kT;
+          if (idx < BN * 8) la.load8(rowM[i], k0 + (idx / BN) * 8, kend, vm[i]);
+        }
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int m = m0 + wm * WTM + mt * 16 + g + (e >> 1) * 8;
-        const int n = n0 + wn * WTN + nt * 8 + 2 * t4 + (e & 1);
-        if (m < out.M && n < out.N) out.store(m, n, acc[mt][nt][e], split);
+        for (int i = 0; i < S::kCallsN; ++i)
+          stage_terms128<TB>(sn, S::kTermN, rn, tid / kT5N + 2 * i, vn[i]);
+#pragma unroll
+        for (int i = 0; i < S::kCallsM; ++i) {
+          const int idx = tid + i * kT;
+          if (idx < BN * 8) stage_terms128<TA>(sm, S::kTermM, idx % BN, idx / BN, vm[i]);
+        }
       }
+      t5::fence_proxy_async();
+      __syncthreads();
+      if (s_fail) break;   // uniform after the barrier
+      if (tid == 0) {
+        t5::fence_after();
+        const uint32_t an = t5::smem_u32(sn), bm = t5::smem_u32(sm);
+#pragma unroll
+        for (int kk = 0; kk < kT5K / 16; ++kk) {
+#pragma unroll
+          for (int i = TB - 1; i >= 0; --i)       // smallest terms first
+#pragma unroll
+            for (int j = TA - 1; j >= 0; --j) {
+              if (i + j >= TMAX) continue;
+              const uint64_t ad = t5::desc_sw128(an + i * S::kTermN) + (uint64_t)(kk * 2);
+              const uint64_t bd = t5::desc_sw128(bm + j * S::kTermM) + (uint64_t)(kk * 2);
+              t5::mma_bf16(tmem, ad, bd, kIdesc, started ? 1u : 0u);   // the first one overwrites
+              started = true;
+            }
+        }
+        t5::mma_commit(t5::smem_u32(&s_bar[st]));
+      }
+    }
+    if (s_fail) break;
+    if (nslice > 0) {   // this tile's last slice (commits complete in order)
+      const int cl = cg - 1;
+      if (!t5::mbar_wait(t5::smem_u32(&s_bar[cl & 1]), (uint32_t)((cl >> 1) & 1), kT5Spin))
+        s_fail = 1;
+    }
+    t5::fence_after();
+    __syncthreads();
+    if (s_fail) break;
+    const int q = warp & 3, h = warp >> 2;
+    const int n = n0 + 32 * q + lane;
+    const bool split = gridDim.z > 1;
+#pragma unroll 1
+    for (int g = 0; g < BN / 16; ++g) {
+      const int col = h * (BN / 2) + 8 * g;
+      float v[8];
+      if (nslice > 0) {
+        t5::tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = 0.f;
+      }
+      if (n < out.N) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int m = m0 + col + e;
+          if (m < out.M) out.store(m, n, v[e], split);
+        }
+      }
+    }
+    // the next tile's MMAs overwrite the accumulator after every warp has read it
+    t5::fence_before();
+    __syncthreads();
+  }
+  if (s_fail && tid == 0) atomicExch(&g_t5_timeout, 1);
+  t5::fence_before();
+  __syncthreads();
+  if (warp == 0) t5::tmem_dealloc(tmem, BN);
 }
 
-template <int BM, int TA, int TB, class OUT, class LA, class LB>
-cudaError_t tc_launch_bm(const OUT& o, int K, LA la, LB lb, int splits, cudaStream_t s) {
-  constexpr int smem = 2 * (BM * 64 * TA + kTcBN * 64 * TB);
-  auto kern = tc_gemm_kernel<LA, LB, OUT, BM, TA, TB>;
+template <int BN, int TA, int TB, class OUT, class LA, class LB>
+cudaError_t t5_launch_bn(const OUT& o, int K, LA la, LB lb, int splits, cudaStream_t s) {
+  using S = T5Shape<BN, TA, TB>;
+  auto kern = t5_gemm_kernel<LA, LB, OUT, BN, TA, TB>;
   static unsigned long long attr_set = 0;   // per device: shared-memory opt-in done
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 64 || !(attr_set >> dev & 1)) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmem);
     if (e != cudaSuccess) return e;
     if (dev < 64) attr_set |= 1ULL << dev;
   }
-  splits = std::max(1, std::min(splits, cdiv(K, kTcBK)));
-  const int kchunk = cdiv(cdiv(K, splits), kTcBK) * kTcBK;
+  splits = std::max(1, std::min(splits, cdiv(K, kT5K)));
+  const int kchunk = cdiv(cdiv(K, splits), kT5K) * kT5K;
   splits = cdiv(K, kchunk);
-  dim3 grid(cdiv(o.N, kTcBN), cdiv(o.M, BM), splits);
-  kern<<<grid, kT, smem, s>>>(o, la, lb, K, kchunk);
+  // one pixel tile per CTA (measured faster than fewer CTAs looping over
+  // tiles, with one or two CTAs per SM); the kernel loops when the grid is
+  // capped
+  const int ntiles = cdiv(o.N, kT5N);
+  dim3 grid((unsigned)std::min(ntiles, 65535), cdiv(o.M, BN), splits);
+  kern<<<grid, kT, S::kSmem, s>>>(o, la, lb, K, kchunk);
   return cudaGetLastError();
 }
 
-// M-tile: 32 or 64 rows where M is small or the 128-row grid would leave
-// most of the 152 SMs idle.
+// Channel tile: all of M up to 256 (the smallest of 32, 64, 128, 256 that holds it).
+inline int t5_bn(int M) { return M <= 32 ? 32 : M <= 64 ? 64 : M <= 128 ? 128 : 256; }
+
 template <int TA, int TB, class OUT, class LA, class LB>
 cudaError_t tc_launch(const OUT& o, int K, LA la, LB lb, int splits, cudaStream_t s) {
   if (o.M <= 0 || o.N <= 0) return cudaSuccess;
-  if (o.M <= 32) return tc_launch_bm<32, TA, TB>(o, K, la, lb, splits, s);
-  if (o.M <= 64 || (long long)cdiv(o.M, 128) * cdiv(o.N, kTcBN) * splits < 2 * 152)
-    return tc_launch_bm<64, TA, TB>(o, K, la, lb, splits, s);
-  return tc_launch_bm<128, TA, TB>(o, K, la, lb, splits, s);
+  switch (t5_bn(o.M)) {
+    case 32: return t5_launch_bn<32, TA, TB>(o, K, la, lb, splits, s);
+    case 64: return t5_launch_bn<64, TA, TB>(o, K, la, lb, splits, s);
+    case 128: return t5_launch_bn<128, TA, TB>(o, K, la, lb, splits, s);
+    default: return t5_launch_bn<256, TA, TB>(o, K, la, lb, splits, s);
+  }
 }
 
 // Split-K factor for the weight gradients (reductions over all pixels).
 int wgrad_splits(int M, int N, int K) {
-  const long long tiles = (long long)cdiv(M, 64) * cdiv(N, kTcBN);
-  const long long want = std::max<long long>(1, 152 * 4 / std::max<long long>(tiles, 1));
+  const long long tiles = (long long)cdiv(M, t5_bn(M)) * cdiv(N, kT5N);
+  const long long want = std::max<long long>(1, 152 * 2 / std::max<long long>(tiles, 1));
   return (int)std::min<long long>(want, std::max(1, K / 1024));
 }
 
@@ -682,10 +725,10 @@ __global__ void bias_act_kernel(float* Y, const float* __restrict__ b, int relu,
 // k-splits for an output GEMM whose tile grid alone would leave SMs idle
 // (the deep levels): enough CTAs for two per SM, at least 8 k-slabs each.
 int out_splits(int M, int N, int K) {
-  const long long tiles = (long long)cdiv(M, 64) * cdiv(N, kTcBN);
-  if (tiles >= 2 * 152) return 1;
-  const long long want = cdiv(2 * 152, tiles);
-  return (int)std::max<long long>(1, std::min<long long>(want, K / (8 * kTcBK)));
+  const long long tiles = (long long)cdiv(M, t5_bn(M)) * cdiv(N, kT5N);
+  if (tiles >= 152) return 1;
+  const long long want = cdiv(152, tiles);
+  return (int)std::max<long long>(1, std::min<long long>(want, K / (4 * kT5K)));
 }
 
 // C [M][N] (contiguous) = op + bias, ReLU: one pass when the grid fills the
