@@ -218,9 +218,10 @@ __global__ void __launch_bounds__(kCta) la_residual_kernel(LaArgs<T> a, const St
 }
 
 // res = rhs - lambda_k z - G z over the factored rows (G gathered through the
-// extended-row map).  Eight rows per CTA, one warp each; the map and z are
-// staged in shared memory once per CTA, so the rows of G are the only global
-// stream, gathered four entries per lane at a time.
+// extended-row map).  Sixteen rows per CTA, two per warp walked together so
+// that each lane keeps eight gathers of G in flight; the map and z are staged
+// in shared memory once per CTA, so the rows of G are the only global stream.
+constexpr int kRefineRowsPerWarp = 2;
 __global__ void __launch_bounds__(kCta) la_refine_kernel(const StepInfo* info,
                                                          const int* __restrict__ ext,
                                                          const double* __restrict__ G, int Pe,
@@ -234,29 +235,41 @@ __global__ void __launch_bounds__(kCta) la_refine_kernel(const StepInfo* info,
   }
   __syncthreads();
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = blockIdx.x * kWarps + wib;
-  if (row >= P) return;
-  const int ei = s_ext[row];
-  double s = 0.0;
-  if (ei >= 0) {
-    const double* g = G + (size_t)ei * Pe;
-    for (int base = 0; base < P; base += 128) {
-      double gv[4];
+  const int row0 = (blockIdx.x * kWarps + wib) * kRefineRowsPerWarp;
+  if (row0 >= P) return;
+  const double* g[kRefineRowsPerWarp];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int j = base + 32 * t + lane;
-        const int ej = j < P ? s_ext[j] : -1;
-        gv[t] = ej >= 0 ? __ldg(g + ej) : 0.0;
-      }
+  for (int u = 0; u < kRefineRowsPerWarp; ++u) {
+    const int row = row0 + u;
+    const int ei = row < P ? s_ext[row] : -1;
+    g[u] = ei >= 0 ? G + (size_t)ei * Pe : nullptr;
+  }
+  double s[kRefineRowsPerWarp] = {};
+  for (int base = 0; base < P; base += 128) {
+    double gv[kRefineRowsPerWarp][4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int j = base + 32 * t + lane;
-        if (j < P) s += gv[t] * s_z[j];
+    for (int t = 0; t < 4; ++t) {
+      const int j = base + 32 * t + lane;
+      const int ej = j < P ? s_ext[j] : -1;
+#pragma unroll
+      for (int u = 0; u < kRefineRowsPerWarp; ++u)
+        gv[u][t] = (ej >= 0 && g[u]) ? __ldg(g[u] + ej) : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int j = base + 32 * t + lane;
+      if (j < P) {
+#pragma unroll
+        for (int u = 0; u < kRefineRowsPerWarp; ++u) s[u] += gv[u][t] * s_z[j];
       }
     }
   }
-  s = warp_sum(s);
-  if (lane == 0) res[row] = rhs[row] - info->lam_k * s_z[row] - s;
+#pragma unroll
+  for (int u = 0; u < kRefineRowsPerWarp; ++u) {
+    const double t = warp_sum(s[u]);
+    const int row = row0 + u;
+    if (lane == 0 && row < P) res[row] = rhs[row] - info->lam_k * s_z[row] - t;
+  }
 }
 
 // x -= eta M_k^T z over the rows of the window (atomic scatter-add).
@@ -367,7 +380,8 @@ cudaError_t la_launch_refine(const StepInfo* info, const int* ext, const double*
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  la_refine_kernel<<<cdiv(P, kWarps), kCta, smem, s>>>(info, ext, G, Pe, z, rhs, res, P);
+  la_refine_kernel<<<cdiv(P, kWarps * kRefineRowsPerWarp), kCta, smem, s>>>(info, ext, G, Pe, z,
+                                                                            rhs, res, P);
   return cudaGetLastError();
 }
 
