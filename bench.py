@@ -1357,7 +1357,7 @@ def main():
     ap.add_argument("--ws-test", type=int, default=12)
     ap.add_argument("--ws-target-epochs", type=int, default=1)
     ap.add_argument("--ws-eval-epochs", type=int, default=2)
-    ap.add_argument("--ws-net-epochs", type=int, default=8)
+    ap.add_argument("--ws-net-epochs", type=int, default=16)
     ap.add_argument("--ws-batch", type=int, default=8)
     ap.add_argument("--ws-lr", type=float, default=1e-3)
     ap.add_argument("--ws-verbose", action="store_true")
@@ -1369,6 +1369,8 @@ def main():
                     help="timed steps of the 96-problem batched block (0: skip it)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched block and print that line")
+    ap.add_argument("--ws-only", action="store_true",
+                    help="run only the learned initial guess block (the --ws-* options) and print that line")
     ap.add_argument("--tc-only", action="store_true",
                     help="time only the tensor-core product and factor inverse and print that line")
     ap.add_argument("--batch-no-tune", action="store_true",
@@ -1403,6 +1405,12 @@ def main():
         main_batch(args)
     elif args.tc_only:
         main_tc(args)
+    elif args.ws_only:
+        import torch
+        from paper_1912_07962_gb300 import build as slbuild
+        slbuild.build()
+        with torch.cuda.stream(torch.cuda.Stream()):
+            print(json.dumps({"warm_start": warm_start_block(args)}))
     else:
         main_gpu(args)
 
