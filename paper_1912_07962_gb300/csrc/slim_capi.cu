@@ -1214,13 +1214,26 @@ slim_status slim_create(const slim_geometry* geom, const slim_blocks* blocks, in
     c->S = c->N;
     c->cap = 96;
   }
-  // geometry tables: host libm cos/sin, row-stepping iff |cos| >= |sin|
+  // geometry tables: host libm cos/sin, row-stepping iff |cos| >= |sin|.
+  // A component below 1e-15 in magnitude is the rounding residue of an
+  // axis-aligned view (cos(pi/2) evaluates to 6.1e-17): it is taken as 0 and
+  // the other as +-1.  Kept, it shifts every interpolation position by a
+  // fraction of an ulp, and where t + (N - 1) / 2 is an integer two
+  // neighbouring rays then round into the same interpolated pixel of a step
+  // (one with a weight of 1e-16), which the block's pixel -> ray map cannot hold.
   c->h_views.resize(c->n_views);
   for (int a = 0; a < c->n_views; ++a) {
     double th = geom->angles ? geom->angles[a] : a * M_PI / c->n_views;
     ViewGeom v;
     v.co = std::cos(th);
     v.si = std::sin(th);
+    if (std::fabs(v.co) < 1e-15) {
+      v.co = 0.0;
+      v.si = std::copysign(1.0, v.si);
+    } else if (std::fabs(v.si) < 1e-15) {
+      v.si = 0.0;
+      v.co = std::copysign(1.0, v.co);
+    }
     v.row_step = std::fabs(v.co) >= std::fabs(v.si) ? 1 : 0;
     v.rc = 1.0 / (v.row_step ? v.co : v.si);
     v.ia = std::fabs(v.rc);

@@ -2,12 +2,12 @@
 // inverse of a Cholesky factor built on them, and the matrix-vector products
 // that apply that inverse (declarations and the arithmetic in slim_tc.cuh).
 //
-// One CTA computes a 128 x 64 tile of C.  For each 64-wide slice of K its
+// One CTA computes a 128 x 128 tile of C.  For each 64-wide slice of K its
 // 256 threads load the float32 operand tiles (either storage order), split
 // every value into three bfloat16 terms and store each term tile in the
 // K-major, 128-byte-swizzled shared-memory layout the MMA reads.  One thread
 // then issues the six term products of each 16-wide K step as tcgen05.mma
-// (M = 128, N = 64, K = 16, float32 accumulation in tensor memory) and
+// (M = 128, N = 128, K = 16, float32 accumulation in tensor memory) and
 // commits them to an mbarrier of that stage; with two stages the loads of
 // slice s+1 overlap the MMAs of slice s.  After the last slice the eight
 // warps read the accumulator from tensor memory (each warp its 32-lane
@@ -30,8 +30,9 @@ constexpr int kThreads = 256;
 constexpr int kStages = 2;
 constexpr int kTermA = kTcBM * kTcBK * 2;            // bytes of one bfloat16 term tile of A
 constexpr int kTermB = kTcBN * kTcBK * 2;            // of B
-constexpr int kStageBytes = 3 * kTermA + 3 * kTermB;  // 72 KB
+constexpr int kStageBytes = 3 * kTermA + 3 * kTermB;  // 96 KB
 constexpr int kTmemCols = kTcBN;                     // float32 accumulator: one column per n
+constexpr int kHalfN = kTcBN / 2;                     // accumulator columns per epilogue warp
 constexpr unsigned kSpinLimit = 1u << 24;            // mbarrier polls before giving up
 
 // PTX wrappers (slim_tcgen05.cuh), with this kernel's instruction shape
@@ -173,7 +174,7 @@ __device__ __forceinline__ void store_operand(unsigned char* dst, const float (&
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const TcProblem* probs, int* status) {
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const TcProblem* probs, int* status) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t s_bar[kStages];
   __shared__ uint32_t s_tmem;
@@ -250,8 +251,8 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const TcProblem* p
   if (s_fail) {
     if (tid == 0) set_status(status, SLIM_ETIMEOUT);
   } else {
-    // epilogue: warp w reads lanes 32 (w % 4) .. +31 and columns 32 (w / 4) .. +31,
-    // 8 columns at a time
+    // epilogue: warp w reads lanes 32 (w % 4) .. +31 and half w / 4 of the
+    // columns, 8 columns at a time
     const int q = warp & 3, h = warp >> 2;
     const int row = 32 * q + lane;
     if (pb.c_nm == 0) {
@@ -260,24 +261,26 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const TcProblem* p
       constexpr int kCsLd = kTcBN + 4;
       float* Cs = reinterpret_cast<float*>(smem);
 #pragma unroll 1
-      for (int g = 0; g < 4; ++g) {
+      for (int g = 0; g < kTcBN / 16; ++g) {
         float acc[8];
         if (nchunk > 0) {
-          tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h + 8 * g), acc);
+          tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kHalfN * h + 8 * g), acc);
         } else {
 #pragma unroll
           for (int i = 0; i < 8; ++i) acc[i] = 0.f;
         }
-        float4* dst = reinterpret_cast<float4*>(Cs + row * kCsLd + 32 * h + 8 * g);
+        float4* dst = reinterpret_cast<float4*>(Cs + row * kCsLd + kHalfN * h + 8 * g);
         dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
         dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
       }
       __syncthreads();
       const bool vec = (pb.ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(pb.C) & 15) == 0;
-      const int c4 = tid & 15, rr = tid >> 4;
+      // a row of C is kTcBN / 4 16-byte pieces: kTcBN / 4 threads per row
+      constexpr int kPieces = kTcBN / 4, kRowsPerPass = kThreads / kPieces;
+      const int c4 = tid % kPieces, rr = tid / kPieces;
 #pragma unroll 2
-      for (int pass = 0; pass < kTcBM / 16; ++pass) {
-        const int r = rr + 16 * pass, m = m0 + r, n = n0 + 4 * c4;
+      for (int pass = 0; pass < kTcBM / kRowsPerPass; ++pass) {
+        const int r = rr + kRowsPerPass * pass, m = m0 + r, n = n0 + 4 * c4;
         if (m >= pb.M || n >= pb.N) continue;
         const float4 a = *reinterpret_cast<const float4*>(Cs + r * kCsLd + 4 * c4);
         float* cp = pb.C + (long long)m * pb.ldc + n;
@@ -302,16 +305,16 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const TcProblem* p
       // column n is one contiguous 128-byte run per warp
       const int m = m0 + row;
 #pragma unroll 1
-      for (int g = 0; g < 4; ++g) {
+      for (int g = 0; g < kTcBN / 16; ++g) {
         float acc[8];
         if (nchunk > 0) {
-          tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h + 8 * g), acc);
+          tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kHalfN * h + 8 * g), acc);
         } else {
 #pragma unroll
           for (int i = 0; i < 8; ++i) acc[i] = 0.f;
         }
         if (m >= pb.M) continue;
-        const int nb = n0 + 32 * h + 8 * g;
+        const int nb = n0 + kHalfN * h + 8 * g;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int n = nb + j;

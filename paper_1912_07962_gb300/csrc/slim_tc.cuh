@@ -36,7 +36,7 @@ struct TcProblem {
 };
 
 constexpr int kTcBM = 128;   // output rows per CTA (the MMA's M)
-constexpr int kTcBN = 64;    // output columns per CTA (the MMA's N)
+constexpr int kTcBN = 128;   // output columns per CTA (the MMA's N)
 constexpr int kTcBK = 64;    // K per pipeline stage (128-byte bfloat16 rows)
 
 // Launch the products probs[0..nprob) (a device array) with a grid covering

@@ -3,7 +3,7 @@ against float64 numpy, through the C ABI.
 
 slim_tc_matmul: element-wise |C - C_ref| <= 1e-5 * (|op(A)| |op(B)|) (float32
 accumulation over K <= 320; a product of the leading bfloat16 terms alone
-would miss by about 4e-3).  Layout flags, ragged M and N (tiles of 128 x 64),
+would miss by about 4e-3).  Layout flags, ragged M and N (tiles of 128 x 128),
 the triangular masks with garbage in the masked triangle, alpha and beta.
 
 slim_chol_inverse: X = L^{-1} of the float32 factor of lambda I + G; its
