@@ -2,12 +2,13 @@
 // inverse of a Cholesky factor built on them, and the matrix-vector products
 // that apply that inverse (declarations and the arithmetic in slim_tc.cuh).
 //
-// One CTA computes a 128 x 128 tile of C.  For each 64-wide slice of K its
+// One CTA computes a 128 x BN tile of C (BN = 128, or 64 for products too
+// small to fill the GPU with the wide tile).  For each 64-wide slice of K its
 // 256 threads load the float32 operand tiles (either storage order), split
 // every value into three bfloat16 terms and store each term tile in the
 // K-major, 128-byte-swizzled shared-memory layout the MMA reads.  One thread
 // then issues the six term products of each 16-wide K step as tcgen05.mma
-// (M = 128, N = 128, K = 16, float32 accumulation in tensor memory) and
+// (M = 128, N = BN, K = 16, float32 accumulation in tensor memory) and
 // commits them to an mbarrier of that stage; with two stages the loads of
 // slice s+1 overlap the MMAs of slice s.  After the last slice the eight
 // warps read the accumulator from tensor memory (each warp its 32-lane
@@ -29,11 +30,17 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kStages = 2;
 constexpr int kTermA = kTcBM * kTcBK * 2;            // bytes of one bfloat16 term tile of A
-constexpr int kTermB = kTcBN * kTcBK * 2;            // of B
-constexpr int kStageBytes = 3 * kTermA + 3 * kTermB;  // 96 KB
-constexpr int kTmemCols = kTcBN;                     // float32 accumulator: one column per n
-constexpr int kHalfN = kTcBN / 2;                     // accumulator columns per epilogue warp
 constexpr unsigned kSpinLimit = 1u << 24;            // mbarrier polls before giving up
+
+// The shape of a 128 x BN output tile.
+template <int BN>
+struct TcTile {
+  static constexpr int kTermB = BN * kTcBK * 2;                 // bytes of one term tile of B
+  static constexpr int kStageBytes = 3 * kTermA + 3 * kTermB;   // 72 KB (BN 64), 96 KB (128)
+  static constexpr int kTmemCols = BN;                          // float32 accumulator: a column per n
+  static constexpr int kHalfN = BN / 2;                         // accumulator columns per epilogue warp
+  static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024;
+};
 
 // PTX wrappers (slim_tcgen05.cuh), with this kernel's instruction shape
 using t5::desc_sw128;
@@ -51,10 +58,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return t5::mbar_wait(bar, parity, kSpinLimit);
 }
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) { return desc_sw128(addr); }
-// Instruction descriptor: M = 128, N = kTcBN
-constexpr uint32_t kIdesc = t5::idesc_bf16(kTcBM, kTcBN);
+// Instruction descriptor: M = 128, N = BN
+template <int BN>
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                          uint32_t accumulate) {
+  constexpr uint32_t kIdesc = t5::idesc_bf16(kTcBM, BN);
   t5::mma_bf16(tmem_d, adesc, bdesc, kIdesc, accumulate);
 }
 
@@ -174,13 +182,17 @@ __device__ __forceinline__ void store_operand(unsigned char* dst, const float (&
   }
 }
 
+template <int BN>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const TcProblem* probs, int* status) {
+  using Tile = TcTile<BN>;
+  constexpr int kStageBytes = Tile::kStageBytes, kTermB = Tile::kTermB;
+  constexpr int kTmemCols = Tile::kTmemCols, kHalfN = Tile::kHalfN;
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t s_bar[kStages];
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
   const TcProblem pb = probs[blockIdx.z];
-  const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * kTcBN;
+  const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
   if (m0 >= pb.M || n0 >= pb.N) return;   // uniform: the whole CTA leaves
   if (pb.c_lower && n0 >= m0 + kTcBM) return;   // wholly above the diagonal
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -214,11 +226,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const TcProblem* p
     }
     const int k0 = kbeg + c * kTcBK;
     {
-      float va[StageMap<kTcBM>::kPer], vb[StageMap<kTcBN>::kPer];
+      float va[StageMap<kTcBM>::kPer], vb[StageMap<BN>::kPer];
       load_operand<kTcBM>(va, pb.A, pb.lda, pb.a_km, m0, pb.M, k0);
-      load_operand<kTcBN>(vb, pb.B, pb.ldb, pb.b_kn, n0, pb.N, k0);
+      load_operand<BN>(vb, pb.B, pb.ldb, pb.b_kn, n0, pb.N, k0);
       store_operand<kTcBM>(sa, va, pb.a_km, m0, k0, pb.k_to_m ? 1 : 0);
-      store_operand<kTcBN>(sb, vb, pb.b_kn, n0, k0, pb.k_from_n ? 2 : 0);
+      store_operand<BN>(sb, vb, pb.b_kn, n0, k0, pb.k_from_n ? 2 : 0);
     }
     fence_proxy_async();
     __syncthreads();
@@ -235,7 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const TcProblem* p
         for (int q = 0; q < 6; ++q) {
           const uint64_t ad = smem_desc_sw128(a0 + ta[q] * kTermA) + (uint64_t)(kk * 2);
           const uint64_t bd = smem_desc_sw128(b0 + tb[q] * kTermB) + (uint64_t)(kk * 2);
-          mma_bf16(tmem, ad, bd, (c > 0 || kk > 0 || q > 0) ? 1u : 0u);
+          mma_bf16<BN>(tmem, ad, bd, (c > 0 || kk > 0 || q > 0) ? 1u : 0u);
         }
       }
       mma_commit(smem_u32(&s_bar[st]));
@@ -258,10 +270,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const TcProblem* p
     if (pb.c_nm == 0) {
       // through shared memory (the operand stages are free once the last
       // commit has arrived), then whole rows of C in 16-byte stores
-      constexpr int kCsLd = kTcBN + 4;
+      constexpr int kCsLd = BN + 4;
       float* Cs = reinterpret_cast<float*>(smem);
 #pragma unroll 1
-      for (int g = 0; g < kTcBN / 16; ++g) {
+      for (int g = 0; g < BN / 16; ++g) {
         float acc[8];
         if (nchunk > 0) {
           tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kHalfN * h + 8 * g), acc);
@@ -275,8 +287,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const TcProblem* p
       }
       __syncthreads();
       const bool vec = (pb.ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(pb.C) & 15) == 0;
-      // a row of C is kTcBN / 4 16-byte pieces: kTcBN / 4 threads per row
-      constexpr int kPieces = kTcBN / 4, kRowsPerPass = kThreads / kPieces;
+      // a row of C is BN / 4 16-byte pieces: BN / 4 threads per row
+      constexpr int kPieces = BN / 4, kRowsPerPass = kThreads / kPieces;
       const int c4 = tid % kPieces, rr = tid / kPieces;
 #pragma unroll 2
       for (int pass = 0; pass < kTcBM / kRowsPerPass; ++pass) {
@@ -305,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const TcProblem* p
       // column n is one contiguous 128-byte run per warp
       const int m = m0 + row;
 #pragma unroll 1
-      for (int g = 0; g < kTcBN / 16; ++g) {
+      for (int g = 0; g < BN / 16; ++g) {
         float acc[8];
         if (nchunk > 0) {
           tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kHalfN * h + 8 * g), acc);
@@ -582,18 +594,38 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
 
-size_t tc_smem_bytes() { return (size_t)kStages * kStageBytes + 1024; }
+size_t tc_smem_bytes() { return TcTile<kTcBN>::kSmem; }
 
 cudaError_t tc_prepare() {
-  return cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tc_smem_bytes());
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<kTcBN>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)TcTile<kTcBN>::kSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(tc_gemm_kernel<kTcBNNarrow>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)TcTile<kTcBNNarrow>::kSmem);
 }
 
+// Either tile runs one CTA per SM (two stages of 72 or 96 KB).  The wide
+// tile splits each operand once per 128 x 128 outputs instead of 128 x 64; it
+// is taken when its tiles fill every SM at least once, else the narrow tile,
+// which has twice as many.
 cudaError_t tc_gemm(const TcProblem* d_probs, int nprob, int max_m, int max_n, int* status,
                     cudaStream_t s) {
   if (nprob <= 0 || max_m <= 0 || max_n <= 0) return cudaSuccess;
-  dim3 grid(cdiv(max_n, kTcBN), cdiv(max_m, kTcBM), nprob);
-  tc_gemm_kernel<<<grid, kThreads, tc_smem_bytes(), s>>>(d_probs, status);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const long long wide_tiles = (long long)nprob * cdiv(max_m, kTcBM) * cdiv(max_n, kTcBN);
+  if (wide_tiles >= sms) {
+    dim3 grid(cdiv(max_n, kTcBN), cdiv(max_m, kTcBM), nprob);
+    tc_gemm_kernel<kTcBN><<<grid, kThreads, TcTile<kTcBN>::kSmem, s>>>(d_probs, status);
+  } else {
+    dim3 grid(cdiv(max_n, kTcBNNarrow), cdiv(max_m, kTcBM), nprob);
+    tc_gemm_kernel<kTcBNNarrow><<<grid, kThreads, TcTile<kTcBNNarrow>::kSmem, s>>>(d_probs,
+                                                                                status);
+  }
   return cudaGetLastError();
 }
 

@@ -36,7 +36,8 @@ struct TcProblem {
 };
 
 constexpr int kTcBM = 128;   // output rows per CTA (the MMA's M)
-constexpr int kTcBN = 128;   // output columns per CTA (the MMA's N)
+constexpr int kTcBN = 128;   // output columns per CTA (the MMA's N), wide tile
+constexpr int kTcBNNarrow = 64;   // narrow tile, for products with few wide tiles
 constexpr int kTcBK = 64;    // K per pipeline stage (128-byte bfloat16 rows)
 
 // Launch the products probs[0..nprob) (a device array) with a grid covering
@@ -44,7 +45,8 @@ constexpr int kTcBK = 64;    // K per pipeline stage (128-byte bfloat16 rows)
 // A bounded wait that runs out records SLIM_ETIMEOUT in *status.
 cudaError_t tc_gemm(const TcProblem* d_probs, int nprob, int max_m, int max_n, int* status,
                     cudaStream_t s);
-// Dynamic shared memory of one CTA (opted in by tc_prepare, once per process).
+// Dynamic shared memory of one wide-tile CTA (both tile widths are opted in by
+// tc_prepare, once per process).
 size_t tc_smem_bytes();
 cudaError_t tc_prepare();
 

@@ -3,8 +3,10 @@ against float64 numpy, through the C ABI.
 
 slim_tc_matmul: element-wise |C - C_ref| <= 1e-5 * (|op(A)| |op(B)|) (float32
 accumulation over K <= 320; a product of the leading bfloat16 terms alone
-would miss by about 4e-3).  Layout flags, ragged M and N (tiles of 128 x 128),
-the triangular masks with garbage in the masked triangle, alpha and beta.
+would miss by about 4e-3).  Layout flags, ragged M and N, the triangular
+masks with garbage in the masked triangle, alpha and beta, on both tile
+widths: 128 x 64 for products of fewer 128 x 128 tiles than the GPU has SMs,
+128 x 128 from there on (the last two cases, 160 and 165 wide tiles).
 
 slim_chol_inverse: X = L^{-1} of the float32 factor of lambda I + G; its
 strict upper triangle is exactly the transpose of the lower; the error to the
@@ -41,6 +43,8 @@ def _dev(a):
     (300, 70, 192, 1, 1, 0, -1.0, 0.5, 0, 0),      # alpha, beta
     (192, 192, 192, 0, 1, 0, 1.0, 0.0, 1, 0),      # lower-triangular A (masked)
     (192, 130, 192, 0, 1, 1, -1.0, 0.0, 0, 1),     # lower-triangular B (masked)
+    (2000, 1250, 64, 0, 1, 0, 1.0, 0.5, 0, 0),     # wide tiles, ragged
+    (1900, 1300, 128, 1, 0, 1, -1.0, 0.0, 1, 1),   # wide tiles, both masks, C transposed
 ])
 def test_tc_matmul(sl, M, N, K, a_km, b_kn, c_nm, alpha, beta, a_lower, b_lower):
     rs = np.random.default_rng(M + 7 * N + 13 * K)
