@@ -348,6 +348,238 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const TcProblem* p
 }
 
 // ----------------------------------------------------------------------------
+// Pre-split operands and the product that streams them
+// ----------------------------------------------------------------------------
+constexpr int kPlaneTileBytes = 3 * kTermA;   // the three term tiles of 128 rows x 64 k: 48 KB
+using t5::bulk_g2s;
+using t5::mbar_arrive;
+using t5::mbar_arrive_expect_tx;
+
+// One CTA per 128 x 64 tile of op(X): the staging code of tc_gemm_kernel,
+// writing the term tiles to global memory instead of shared memory.
+__global__ void __launch_bounds__(kThreads) tc_split_kernel(const TcSplitJob* jobs) {
+  const TcSplitJob j = jobs[blockIdx.y];
+  const int KT = j.K / kTcBK, RT = (j.rows + kTcBM - 1) / kTcBM;
+  const int t = blockIdx.x;
+  if (t >= RT * KT) return;
+  const int rt = t / KT, kt = t - rt * KT;
+  // tiles wholly in the zero triangle: no product reads them
+  if (j.tri == 1 && kt * kTcBK > rt * kTcBM + kTcBM - 1) return;
+  if (j.tri == 2 && kt * kTcBK + kTcBK - 1 < rt * kTcBM) return;
+  float v[StageMap<kTcBM>::kPer];
+  load_operand<kTcBM>(v, j.X, j.ld, j.km, rt * kTcBM, j.rows, kt * kTcBK);
+  store_operand<kTcBM>(j.planes + (size_t)t * kPlaneTileBytes, v, j.km, rt * kTcBM, kt * kTcBK,
+                       j.tri);
+}
+
+// Stage ring of the streaming product: A's three term tiles (48 KB) and B's
+// (BN rows each); two stages of 96 KB for BN = 128, three of 72 KB for 64.
+template <int BN>
+struct PlaneTile {
+  static constexpr int kTermB = BN * 128;
+  static constexpr int kStageBytes = kPlaneTileBytes + 3 * kTermB;
+  static constexpr int kStages = BN == 128 ? 2 : 3;
+  static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024;
+};
+constexpr int kPlaneThreads = 128;   // warp 0 lane 0 loads, warp 1 lane 0 issues; 4 warps store
+
+// C tile (m0, n0) of 128 x BN.  The producer thread waits for a stage to be
+// free (the MMAs that read it have committed to its `empty` barrier), arms
+// its `full` barrier with the stage's byte count and issues the bulk copies;
+// the MMA thread waits for `full`, issues the 24 term products of the slice
+// and commits to `empty`, and after the last slice to `done`.  Every wait is
+// bounded; after one runs out the CTA still waits (bounded) for its copies
+// and products in flight before it frees tensor memory.
+template <int BN>
+__global__ void __launch_bounds__(kPlaneThreads, 1)
+    tc_gemm_planes_kernel(const TcProblem* probs, int* status) {
+  using Tile = PlaneTile<BN>;
+  constexpr int S = Tile::kStages, kStageBytes = Tile::kStageBytes, kTermB = Tile::kTermB;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t s_full[S], s_empty[S], s_done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail, s_issued;
+  const TcProblem pb = probs[blockIdx.z];
+  const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
+  if (m0 >= pb.M || n0 >= pb.N) return;
+  if (pb.c_lower && n0 >= m0 + kTcBM) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+
+  int kbeg = 0, kend = pb.K;
+  if (pb.k_from_n) kbeg = n0;
+  if (pb.k_to_m) kend = min(kend, m0 + kTcBM);
+  const int nchunk = kend > kbeg ? (kend - kbeg) / kTcBK : 0;
+  const int KT = pb.K / kTcBK, kt0 = kbeg / kTcBK;
+
+  if (tid == 0) {
+    for (int st = 0; st < S; ++st) {
+      mbar_init(smem_u32(&s_full[st]), 1);
+      mbar_init(smem_u32(&s_empty[st]), 1);
+    }
+    mbar_init(smem_u32(&s_done), 1);
+    s_fail = 0;
+    s_issued = 0;
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0 && lane == 0) {
+    const unsigned char* a_src = pb.a_planes + (size_t)(m0 / kTcBM) * KT * kPlaneTileBytes;
+    const unsigned char* b_src = pb.b_planes + (size_t)(n0 / kTcBM) * KT * kPlaneTileBytes +
+                                 (BN == 64 ? (size_t)((n0 / 64) & 1) * kTermB : 0);
+    int c = 0;
+    for (; c < nchunk; ++c) {
+      const int st = c % S;
+      if (c >= S && !mbar_wait(smem_u32(&s_empty[st]), (uint32_t)((c / S - 1) & 1))) {
+        s_fail = 1;
+        break;
+      }
+      const uint32_t sa = smem_u32(smem + st * kStageBytes), sb = sa + kPlaneTileBytes;
+      const uint32_t full = smem_u32(&s_full[st]);
+      const size_t kofs = (size_t)(kt0 + c) * kPlaneTileBytes;
+      mbar_arrive_expect_tx(full, (uint32_t)kStageBytes);
+      bulk_g2s(sa, a_src + kofs, kPlaneTileBytes, full);
+      if (BN == kTcBM) {
+        bulk_g2s(sb, b_src + kofs, kPlaneTileBytes, full);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+          bulk_g2s(sb + t * kTermB, b_src + kofs + (size_t)t * kTermA, kTermB, full);
+      }
+    }
+    s_issued = c;
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t kIdescN = t5::idesc_bf16(kTcBM, BN);
+    for (int c = 0; c < nchunk; ++c) {
+      const int st = c % S;
+      if (!mbar_wait(smem_u32(&s_full[st]), (uint32_t)((c / S) & 1))) {
+        s_fail = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(smem + st * kStageBytes), b0 = a0 + kPlaneTileBytes;
+#pragma unroll
+      for (int kk = 0; kk < kTcBK / 16; ++kk) {
+        // six term products a_i b_j, i + j <= 2, smallest first
+        const int ta[6] = {2, 1, 0, 1, 0, 0};
+        const int tb[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const uint64_t ad = smem_desc_sw128(a0 + ta[q] * kTermA) + (uint64_t)(kk * 2);
+          const uint64_t bd = smem_desc_sw128(b0 + tb[q] * kTermB) + (uint64_t)(kk * 2);
+          t5::mma_bf16(tmem, ad, bd, kIdescN, (c > 0 || kk > 0 || q > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(smem_u32(&s_empty[st]));
+    }
+    // `done` completes once every product issued above has (at once if none was)
+    if (nchunk > 0) {
+      mma_commit(smem_u32(&s_done));
+    } else {
+      mbar_arrive(smem_u32(&s_done));
+    }
+  }
+  __syncwarp();
+  if (!mbar_wait(smem_u32(&s_done), 0u)) s_fail = 1;
+  tc_fence_after();
+  __syncthreads();
+  if (s_fail) {
+    if (tid == 0) {
+      // copies still in flight land before the CTA leaves
+      const int issued = s_issued;
+      for (int c = issued - S > 0 ? issued - S : 0; c < issued; ++c)
+        mbar_wait(smem_u32(&s_full[c % S]), (uint32_t)((c / S) & 1));
+      set_status(status, SLIM_ETIMEOUT);
+    }
+  } else {
+    // epilogue: warp w holds accumulator lanes (rows) 32 w .. 32 w + 31
+    const int row = 32 * warp + lane;
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    if (pb.c_nm == 0) {
+      // through shared memory (the stages are free: every product has completed),
+      // then whole rows of C in 16-byte stores
+      constexpr int kCsLd = BN + 4;
+      float* Cs = reinterpret_cast<float*>(smem);
+#pragma unroll 1
+      for (int g = 0; g < BN / 8; ++g) {
+        float acc[8];
+        if (nchunk > 0) {
+          tmem_ld8(trow + (uint32_t)(8 * g), acc);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+        }
+        float4* dst = reinterpret_cast<float4*>(Cs + row * kCsLd + 8 * g);
+        dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+      }
+      __syncthreads();
+      const bool vec = (pb.ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(pb.C) & 15) == 0;
+      constexpr int kPieces = BN / 4, kRowsPerPass = kPlaneThreads / kPieces;
+      const int c4 = tid % kPieces, rr = tid / kPieces;
+#pragma unroll 4
+      for (int pass = 0; pass < kTcBM / kRowsPerPass; ++pass) {
+        const int r = rr + kRowsPerPass * pass, m = m0 + r, n = n0 + 4 * c4;
+        if (m >= pb.M || n >= pb.N) continue;
+        const float4 a = *reinterpret_cast<const float4*>(Cs + r * kCsLd + 4 * c4);
+        float* cp = pb.C + (long long)m * pb.ldc + n;
+        if (vec && n + 3 < pb.N) {
+          float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (pb.beta != 0.f) o = *reinterpret_cast<const float4*>(cp);
+          o.x = pb.alpha * a.x + pb.beta * o.x;
+          o.y = pb.alpha * a.y + pb.beta * o.y;
+          o.z = pb.alpha * a.z + pb.beta * o.z;
+          o.w = pb.alpha * a.w + pb.beta * o.w;
+          *reinterpret_cast<float4*>(cp) = o;
+        } else {
+          const float av[4] = {a.x, a.y, a.z, a.w};
+          for (int e = 0; e < 4 && n + e < pb.N; ++e) {
+            const float old = pb.beta != 0.f ? cp[e] : 0.f;
+            cp[e] = pb.alpha * av[e] + pb.beta * old;
+          }
+        }
+      }
+    } else {
+      // C stored transposed: consecutive lanes hold consecutive m, so each
+      // column n is one contiguous 128-byte run per warp
+      const int m = m0 + row;
+#pragma unroll 1
+      for (int g = 0; g < BN / 8; ++g) {
+        float acc[8];
+        if (nchunk > 0) {
+          tmem_ld8(trow + (uint32_t)(8 * g), acc);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+        }
+        if (m >= pb.M) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int n = n0 + 8 * g + j;
+          if (n < pb.N) {
+            float* cp = pb.C + (long long)n * pb.ldc + m;
+            const float old = pb.beta != 0.f ? *cp : 0.f;
+            *cp = pb.alpha * acc[j] + pb.beta * old;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, BN);
+  }
+}
+
+// ----------------------------------------------------------------------------
 // Triangular inverse helpers
 // ----------------------------------------------------------------------------
 // X's diagonal tiles from the factor's tile inverses (zeros above the diagonal).
@@ -597,13 +829,17 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 size_t tc_smem_bytes() { return TcTile<kTcBN>::kSmem; }
 
 cudaError_t tc_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<kTcBN>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)TcTile<kTcBN>::kSmem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tc_gemm_kernel<kTcBNNarrow>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)TcTile<kTcBNNarrow>::kSmem);
+  const void* fn[4] = {(const void*)tc_gemm_kernel<kTcBN>, (const void*)tc_gemm_kernel<kTcBNNarrow>,
+                       (const void*)tc_gemm_planes_kernel<kTcBN>,
+                       (const void*)tc_gemm_planes_kernel<kTcBNNarrow>};
+  const size_t bytes[4] = {TcTile<kTcBN>::kSmem, TcTile<kTcBNNarrow>::kSmem,
+                           PlaneTile<kTcBN>::kSmem, PlaneTile<kTcBNNarrow>::kSmem};
+  for (int i = 0; i < 4; ++i) {
+    cudaError_t e = cudaFuncSetAttribute(fn[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes[i]);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Either tile runs one CTA per SM (two stages of 72 or 96 KB).  The wide
@@ -625,6 +861,60 @@ cudaError_t tc_gemm(const TcProblem* d_probs, int nprob, int max_m, int max_n, i
     dim3 grid(cdiv(max_n, kTcBNNarrow), cdiv(max_m, kTcBM), nprob);
     tc_gemm_kernel<kTcBNNarrow><<<grid, kThreads, TcTile<kTcBNNarrow>::kSmem, s>>>(d_probs,
                                                                                 status);
+  }
+  return cudaGetLastError();
+}
+
+size_t tc_plane_bytes(int rows, int K) {
+  return (size_t)cdiv(rows, kTcBM) * (size_t)(K / kTcBK) * kPlaneTileBytes;
+}
+
+TcSplitJob tc_split_job_a(const TcProblem& p, unsigned char* a) {
+  TcSplitJob j{};
+  j.X = p.A;
+  j.ld = p.lda;
+  j.km = p.a_km;
+  j.rows = p.M;
+  j.K = p.K;
+  j.tri = p.k_to_m ? 1 : 0;
+  j.planes = a;
+  return j;
+}
+
+TcSplitJob tc_split_job_b(const TcProblem& p, unsigned char* b) {
+  TcSplitJob j{};
+  j.X = p.B;
+  j.ld = p.ldb;
+  j.km = p.b_kn;   // op(B)^T[n][k] = B[n*ldb + k] (b_kn = 0) or B[k*ldb + n]
+  j.rows = p.N;
+  j.K = p.K;
+  j.tri = p.k_from_n ? 2 : 0;
+  j.planes = b;
+  return j;
+}
+
+cudaError_t tc_split(const TcSplitJob* d_jobs, int njobs, int max_tiles, cudaStream_t s) {
+  if (njobs <= 0 || max_tiles <= 0) return cudaSuccess;
+  tc_split_kernel<<<dim3(max_tiles, njobs), kThreads, 0, s>>>(d_jobs);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_gemm_planes(const TcProblem* d_probs, int nprob, int max_m, int max_n,
+                           int* status, cudaStream_t s) {
+  if (nprob <= 0 || max_m <= 0 || max_n <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const long long wide_tiles = (long long)nprob * cdiv(max_m, kTcBM) * cdiv(max_n, kTcBN);
+  if (wide_tiles >= sms) {
+    dim3 grid(cdiv(max_n, kTcBN), cdiv(max_m, kTcBM), nprob);
+    tc_gemm_planes_kernel<kTcBN>
+        <<<grid, kPlaneThreads, PlaneTile<kTcBN>::kSmem, s>>>(d_probs, status);
+  } else {
+    dim3 grid(cdiv(max_n, kTcBNNarrow), cdiv(max_m, kTcBM), nprob);
+    tc_gemm_planes_kernel<kTcBNNarrow>
+        <<<grid, kPlaneThreads, PlaneTile<kTcBNNarrow>::kSmem, s>>>(d_probs, status);
   }
   return cudaGetLastError();
 }
@@ -715,7 +1005,41 @@ cudaError_t tri_inverse_plan(TriInvPlan* plan, int P, const float* L, const floa
   plan->level_first.push_back((int)probs.size());
   plan->nprob = (int)probs.size();
   if (probs.empty()) return cudaSuccess;
-  cudaError_t e = cudaMalloc(&plan->d_probs, probs.size() * sizeof(TcProblem));
+  // plane offsets: each launch's operands from the start of the scratch
+  std::vector<TcSplitJob> jobs;
+  std::vector<std::pair<size_t, size_t>> offs(probs.size());
+  size_t scratch = 0;
+  for (size_t l = 0; l + 1 < plan->level_first.size(); ++l) {
+    plan->job_first.push_back((int)jobs.size());
+    int max_tiles = 0;
+    size_t at = 0;
+    for (int i = plan->level_first[l]; i < plan->level_first[l + 1]; ++i) {
+      const TcProblem& q = probs[i];
+      offs[i].first = at;
+      at += tc_plane_bytes(q.M, q.K);
+      offs[i].second = at;
+      at += tc_plane_bytes(q.N, q.K);
+      max_tiles = std::max(max_tiles, std::max(cdiv(q.M, kTcBM), cdiv(q.N, kTcBM)) * (q.K / kTcBK));
+      jobs.push_back(tc_split_job_a(q, nullptr));
+      jobs.push_back(tc_split_job_b(q, nullptr));
+    }
+    plan->job_max_tiles.push_back(max_tiles);
+    scratch = std::max(scratch, at);
+  }
+  plan->job_first.push_back((int)jobs.size());
+  cudaError_t e = cudaMalloc(&plan->d_planes, scratch);
+  if (e != cudaSuccess) return e;
+  for (size_t i = 0; i < probs.size(); ++i) {
+    probs[i].a_planes = plan->d_planes + offs[i].first;
+    probs[i].b_planes = plan->d_planes + offs[i].second;
+    jobs[2 * i].planes = plan->d_planes + offs[i].first;
+    jobs[2 * i + 1].planes = plan->d_planes + offs[i].second;
+  }
+  e = cudaMalloc(&plan->d_jobs, jobs.size() * sizeof(TcSplitJob));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(plan->d_jobs, jobs.data(), jobs.size() * sizeof(TcSplitJob),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_probs, probs.size() * sizeof(TcProblem));
   if (e != cudaSuccess) return e;
   return cudaMemcpy(plan->d_probs, probs.data(), probs.size() * sizeof(TcProblem),
                     cudaMemcpyHostToDevice);
@@ -723,6 +1047,8 @@ cudaError_t tri_inverse_plan(TriInvPlan* plan, int P, const float* L, const floa
 
 void tri_inverse_plan_destroy(TriInvPlan* plan) {
   if (plan->d_probs) cudaFree(plan->d_probs);
+  if (plan->d_jobs) cudaFree(plan->d_jobs);
+  if (plan->d_planes) cudaFree(plan->d_planes);
   *plan = TriInvPlan{};
 }
 
@@ -730,10 +1056,14 @@ cudaError_t tri_inverse(const TriInvPlan& plan, const float* W, float* X, int* s
                         cudaStream_t s) {
   trinv_diag_kernel<<<plan.T, 256, 0, s>>>(W, X, plan.P, plan.T);
   cudaError_t e = cudaGetLastError();
-  // each entry of level_first opens one batched launch (product 1, product 2, ...)
+  // each entry of level_first opens one batched launch (product 1, product 2, ...),
+  // its operands split into planes just before it
   for (size_t l = 0; e == cudaSuccess && l + 1 < plan.level_first.size(); ++l) {
     const int f = plan.level_first[l], n = plan.level_first[l + 1] - f;
-    e = tc_gemm(plan.d_probs + f, n, plan.level_max_m[l], plan.level_max_n[l], status, s);
+    const int jf = plan.job_first[l], jn = plan.job_first[l + 1] - jf;
+    e = tc_split(plan.d_jobs + jf, jn, plan.job_max_tiles[l], s);
+    if (e == cudaSuccess)
+      e = tc_gemm_planes(plan.d_probs + f, n, plan.level_max_m[l], plan.level_max_n[l], status, s);
   }
   if (e != cudaSuccess) return e;
   const int tb = plan.P / 32;
@@ -907,20 +1237,33 @@ extern "C" slim_status slim_tc_matmul(int M, int N, int K, const float* A, long 
   pb.M = M; pb.N = N; pb.K = K;
   pb.k_to_m = a_lower; pb.k_from_n = b_lower;
   pb.alpha = alpha; pb.beta = beta;
-  TcProblem* d_pb = nullptr;
-  int* d_st = nullptr;
+  // one allocation from the stream-ordered pool: the problem, the status word,
+  // the split jobs and both operands' planes
+  static_assert(sizeof(TcProblem) <= 256 && 2 * sizeof(TcSplitJob) <= 512, "workspace layout");
+  const size_t a_bytes = tc_plane_bytes(M, K), b_bytes = tc_plane_bytes(N, K);
+  const size_t o_st = 256, o_jobs = 512, o_a = 1024, o_b = o_a + a_bytes;
+  unsigned char* ws = nullptr;
   cudaError_t e = tc_prepare();
-  if (e == cudaSuccess) e = cudaMalloc(&d_pb, sizeof(pb));
-  if (e == cudaSuccess) e = cudaMalloc(&d_st, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_pb, &pb, sizeof(pb), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&ws), o_b + b_bytes, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  pb.a_planes = ws + o_a;
+  pb.b_planes = ws + o_b;
+  const TcSplitJob jobs[2] = {tc_split_job_a(pb, ws + o_a), tc_split_job_b(pb, ws + o_b)};
+  TcProblem* d_pb = reinterpret_cast<TcProblem*>(ws);
+  int* d_st = reinterpret_cast<int*>(ws + o_st);
+  TcSplitJob* d_jobs = reinterpret_cast<TcSplitJob*>(ws + o_jobs);
+  e = cudaMemcpyAsync(d_pb, &pb, sizeof(pb), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_jobs, jobs, sizeof(jobs), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_st, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = tc_gemm(d_pb, 1, M, N, d_st, s);
+  const int max_tiles = cdiv(std::max(M, N), kTcBM) * (K / kTcBK);
+  if (e == cudaSuccess) e = tc_split(d_jobs, 2, max_tiles, s);
+  if (e == cudaSuccess) e = tc_gemm_planes(d_pb, 1, M, N, d_st, s);
   int hs = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, d_st, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t ef = cudaFreeAsync(ws, s);
+  if (e == cudaSuccess) e = ef;
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   slim_status st = from_cuda(e);
-  cudaFree(d_pb);
-  cudaFree(d_st);
   return st != SLIM_OK ? st : (hs ? (slim_status)hs : SLIM_OK);
 }
 

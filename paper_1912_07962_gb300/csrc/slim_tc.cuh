@@ -33,6 +33,10 @@ struct TcProblem {
   float alpha, beta; // beta = 0: C is not read
   int c_lower;       // 1: only output tiles that reach the lower triangle (some n <= m) are
                      // computed; tiles wholly above the diagonal are left alone
+  // tc_gemm_planes only: op(A) and op(B)^T split in advance by tc_split (A and
+  // B are then not read; the masks were applied by the split)
+  const unsigned char* a_planes;
+  const unsigned char* b_planes;
 };
 
 constexpr int kTcBM = 128;   // output rows per CTA (the MMA's M)
@@ -45,6 +49,34 @@ constexpr int kTcBK = 64;    // K per pipeline stage (128-byte bfloat16 rows)
 // A bounded wait that runs out records SLIM_ETIMEOUT in *status.
 cudaError_t tc_gemm(const TcProblem* d_probs, int nprob, int max_m, int max_n, int* status,
                     cudaStream_t s);
+// The same products from operands split in advance.  An operand op(X),
+// rows x K, is stored as "planes": 128-row x 64-k tiles, each of its three
+// bfloat16 term tiles the exact 16 KB image of the 128-byte-swizzled K-major
+// shared-memory layout the MMA reads, the three terms of a tile consecutive
+// (48 KB).  Tile (rt, kt) starts at byte (rt * (K / 64) + kt) * 49152; rows
+// at or beyond `rows` are zero.  Each CTA then streams its tiles with bulk
+// copies (cp.async.bulk into a ring of shared-memory stages, one producer
+// thread, one MMA thread), so splitting costs one pass over each operand
+// instead of one per tile of C.
+struct TcSplitJob {
+  const float* X;
+  long long ld;      // km = 0: op(X)[r][k] = X[r*ld + k] (16-byte aligned rows); 1: X[k*ld + r]
+  int km;
+  int rows, K;       // K a multiple of 64
+  int tri;           // 1: op(X)[r][k] read as zero for k > r; 2: for k < r (the tiles wholly
+                     // in the zero triangle are not written: the products never read them)
+  unsigned char* planes;
+};
+size_t tc_plane_bytes(int rows, int K);
+// The split jobs of op(A) and op(B)^T of problem p, planes at a and b.
+TcSplitJob tc_split_job_a(const TcProblem& p, unsigned char* a);
+TcSplitJob tc_split_job_b(const TcProblem& p, unsigned char* b);
+// Split jobs[0..njobs) (a device array); max_tiles = the largest
+// ceil(rows / 128) * (K / 64) among them.
+cudaError_t tc_split(const TcSplitJob* d_jobs, int njobs, int max_tiles, cudaStream_t s);
+cudaError_t tc_gemm_planes(const TcProblem* d_probs, int nprob, int max_m, int max_n,
+                           int* status, cudaStream_t s);
+
 // Dynamic shared memory of one wide-tile CTA (both tile widths are opted in by
 // tc_prepare, once per process).
 size_t tc_smem_bytes();
@@ -64,6 +96,10 @@ struct TriInvPlan {
   std::vector<int> level_max_m, level_max_n;
   TcProblem* d_probs = nullptr;       // 2 per split: (L21 X11) and (-X22 T1)
   int nprob = 0;
+  // the operands of each batched launch, split into planes just before it
+  std::vector<int> job_first, job_max_tiles;   // jobs of launch l: [job_first[l], job_first[l+1])
+  TcSplitJob* d_jobs = nullptr;
+  unsigned char* d_planes = nullptr;           // scratch, shared by the launches in turn
 };
 // Plan for order P; L, W and X are bound now (the plan's problems point at them).
 cudaError_t tri_inverse_plan(TriInvPlan* plan, int P, const float* L, const float* W, float* X);
