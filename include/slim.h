@@ -436,7 +436,11 @@ slim_status slim_damped_solve(const double* G, int p, double lambda, const doubl
  * lower triangular (op(B)[k][n] for k < n read as zero).  K a multiple of 64;
  * K-contiguous operands (a_km = 0, b_kn = 0) 16-byte aligned with lda / ldb
  * multiples of 4 (SLIM_EINVAL otherwise).  beta = 0: C is not read.
- * Allocates a few bytes of device memory and synchronises `cuda_stream`.
+ * Each operand is first split into its three bfloat16 terms in a work space
+ * of 6 (M + 128) K + 6 (N + 128) K bytes at most, drawn from a stream-ordered
+ * memory pool of the library's own that keeps freed memory reserved for later
+ * calls (the largest work space so far stays allocated until the process
+ * ends).  Synchronises `cuda_stream`.
  *
  * slim_chol_inverse: the float32 tiled Cholesky factor L of lambda I + G
  * (G: p x p float64 device array, lower triangle read) and X = L^{-1},

@@ -14,6 +14,9 @@
 // warps read the accumulator from tensor memory (each warp its 32-lane
 // quarter and half of the columns) and write alpha acc + beta C.
 #include <algorithm>
+#include <cstdint>
+#include <map>
+#include <mutex>
 #include <cuda_bf16.h>
 
 #include "slim_chol.cuh"
@@ -373,12 +376,13 @@ __global__ void __launch_bounds__(kThreads) tc_split_kernel(const TcSplitJob* jo
 }
 
 // Stage ring of the streaming product: A's three term tiles (48 KB) and B's
-// (BN rows each); two stages of 96 KB for BN = 128, three of 72 KB for 64.
+// (BN rows each); two stages, of 96 KB for BN = 128 and 72 KB for 64 (the
+// narrow tile's 145 KB leave room on the SM for a factorisation CTA).
 template <int BN>
 struct PlaneTile {
   static constexpr int kTermB = BN * 128;
   static constexpr int kStageBytes = kPlaneTileBytes + 3 * kTermB;
-  static constexpr int kStages = BN == 128 ? 2 : 3;
+  static constexpr int kStages = 2;
   static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024;
 };
 constexpr int kPlaneThreads = 128;   // warp 0 lane 0 loads, warp 1 lane 0 issues; 4 warps store
@@ -1218,6 +1222,42 @@ slim_status from_cuda(cudaError_t e) {
 
 using namespace slim;
 
+namespace {
+// The product's work space comes from a stream-ordered pool of the library's
+// own, one per device, whose release threshold is the maximum: memory freed
+// at the end of a call stays mapped for the next one instead of going back to
+// the driver at each synchronisation.
+cudaError_t workspace_pool(cudaMemPool_t* pool) {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) {
+    *pool = it->second;
+    return cudaSuccess;
+  }
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t p = nullptr;
+  e = cudaMemPoolCreate(&p, &props);
+  if (e != cudaSuccess) return e;
+  uint64_t keep = UINT64_MAX;
+  e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+  if (e != cudaSuccess) {
+    cudaMemPoolDestroy(p);
+    return e;
+  }
+  pools[dev] = p;
+  *pool = p;
+  return cudaSuccess;
+}
+}  // namespace
+
 extern "C" slim_status slim_tc_matmul(int M, int N, int K, const float* A, long long lda,
                                       int a_km, const float* B, long long ldb, int b_kn, float* C,
                                       long long ldc, int c_nm, float alpha, float beta,
@@ -1237,14 +1277,17 @@ extern "C" slim_status slim_tc_matmul(int M, int N, int K, const float* A, long 
   pb.M = M; pb.N = N; pb.K = K;
   pb.k_to_m = a_lower; pb.k_from_n = b_lower;
   pb.alpha = alpha; pb.beta = beta;
-  // one allocation from the stream-ordered pool: the problem, the status word,
-  // the split jobs and both operands' planes
+  // one allocation from the library's stream-ordered pool: the problem, the
+  // status word, the split jobs and both operands' planes
   static_assert(sizeof(TcProblem) <= 256 && 2 * sizeof(TcSplitJob) <= 512, "workspace layout");
   const size_t a_bytes = tc_plane_bytes(M, K), b_bytes = tc_plane_bytes(N, K);
   const size_t o_st = 256, o_jobs = 512, o_a = 1024, o_b = o_a + a_bytes;
   unsigned char* ws = nullptr;
+  cudaMemPool_t pool = nullptr;
   cudaError_t e = tc_prepare();
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&ws), o_b + b_bytes, s);
+  if (e == cudaSuccess) e = workspace_pool(&pool);
+  if (e == cudaSuccess)
+    e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&ws), o_b + b_bytes, pool, s);
   if (e != cudaSuccess) return from_cuda(e);
   pb.a_planes = ws + o_a;
   pb.b_planes = ws + o_b;
