@@ -146,14 +146,29 @@ def make_b(sl, cfg, x_true, e):
     return workloads.add_noise(clean, e, cfg.noise)
 
 
-CHOSEN_SOLVER = "mixed"   # set from --solver
+CHOSEN_SOLVER = "mixed_inv"   # set from --solver
+# slimTik runs the triangular-sweep solve (the inverse forms take no slimTik
+# terms), pipelined as that solve is fastest: six steps ahead, one
+# factorisation CTA per SM
+SWEEP_LOOKAHEAD, SWEEP_CTAS = 6, 1
+
+FORM_OF_SOLVER = {
+    "mixed_inv": ("float32 tiled Cholesky, its inverse L^-1 formed on the tcgen05 tensor cores "
+                  "(float32-accurate split-bfloat16 products), the solves as products with L^-1, "
+                  "2 float64-residual refinements"),
+    "mixed": "float32 tiled Cholesky + triangular sweeps, 2 float64-residual refinements",
+    "mixed_tc": ("float32 Cholesky and its inverse on the tcgen05 tensor cores, the solves as "
+                 "products with L^-1, 3 float64-residual refinements"),
+}
 
 
 def make_form(sl, cfg, form, seed, lookahead=0, ctas_per_sm=0, decay_after=0):
     """chosen: float32 projector/residual/scatter, float64 Gram, float32 factor
-    refined twice against the float64 Gram; chosen_fp64_factor: the same with
-    the float64 factor and solves the scope names (no refinement needed);
-    plain: float64 everywhere, one kernel per phase, no graph."""
+    (solved through its tensor-core inverse, or as --solver says when
+    pipelined) refined against the float64 Gram; chosen_fp64_factor: the same
+    pipeline with the float64 factor and solves the scope names (no
+    refinement needed); plain: float64 everywhere, one kernel per phase, no
+    graph."""
     if form in ("chosen", "chosen_fp64_factor"):
         mixed = form == "chosen"
         inverse = {"mixed_tc": sl.SLIM_SOLVE_MIXED_TC, "mixed_inv": sl.SLIM_SOLVE_MIXED_INV}
@@ -1064,7 +1079,7 @@ def main_gpu(args):
     f3d = (frames3d_block(sl, flush, stream, args.frames_steps, 3)
            if rank == 0 and args.frames_steps > 0 else None)
     tik_pass = (tik_block(sl, cfg, b, flush, stream, args.tik_steps, max(3, args.warmup),
-                          lookahead=args.lookahead or 6, ctas_per_sm=args.factor_ctas_per_sm)
+                          lookahead=SWEEP_LOOKAHEAD, ctas_per_sm=SWEEP_CTAS)
                 if rank == 0 and args.tik_steps > 0 else None)
     warm = warm_start_block(args) if rank == 0 and not args.no_warm_start else None
     unet = (unet_block(sl, flush, stream, reps=args.unet_reps)
@@ -1093,11 +1108,11 @@ def main_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": desc, "form": "chosen: float32 projector/residual/scatter, "
-                   "float64 Gram, float32 tiled Cholesky + 2 float64-residual refinements, "
+                   "float64 Gram, " + FORM_OF_SOLVER[CHOSEN_SOLVER] + ", "
                    + (f"geometry and factorisation pipelined {args.lookahead} steps ahead of "
                       "the iterate chain (CUDA graphs on three kinds of stream)"
                       if args.lookahead else "one CUDA graph per step"),
-                   "lookahead": args.lookahead,
+                   "lookahead": args.lookahead, "factor_ctas_per_sm": args.factor_ctas_per_sm,
                    "timing": ("one region of K back-to-back steps after a synchronisation, ended "
                               "once every stream of the context has joined the caller's: K "
                               "iterate chains and K factorisations (pipelined steady state; the "
@@ -1278,8 +1293,8 @@ def main_tik(args):
     x_true, e = workloads.tomo_inputs_2d(cfg)
     b = make_b(sl, cfg, x_true, e)
     print(json.dumps({"tik": tik_block(sl, cfg, b, flush, stream, args.tik_steps,
-                                       max(3, args.warmup), lookahead=args.lookahead or 6,
-                                       ctas_per_sm=args.factor_ctas_per_sm)}))
+                                       max(3, args.warmup), lookahead=SWEEP_LOOKAHEAD,
+                                       ctas_per_sm=SWEEP_CTAS)}))
 
 
 def main_reference(args):
@@ -1315,10 +1330,11 @@ def main():
     ap.add_argument("--tta-decay-after", type=int, default=180,
                     help="also run time-to-accuracy with the 1/k damping decay after this step "
                          "(0: skip)")
-    ap.add_argument("--solver", default="mixed", choices=["mixed", "mixed_tc", "mixed_inv"],
-                    help="chosen form's solve: through the float32 factor (mixed), through the "
-                         "inverse of a tensor-core factor (mixed_tc), or through the tensor-core "
-                         "inverse of the tiled factor (mixed_inv); the last two pipelined only")
+    ap.add_argument("--solver", default="mixed_inv", choices=["mixed", "mixed_tc", "mixed_inv"],
+                    help="chosen form's solve: through the tensor-core inverse of the tiled "
+                         "float32 factor (mixed_inv, the default), through the float32 factor's "
+                         "triangular sweeps (mixed), or through the inverse of a tensor-core "
+                         "factor (mixed_tc); the inverse forms are pipelined only")
     ap.add_argument("--no-fp64-factor", action="store_true",
                     help="skip the pipelined chosen form with the float64 factor")
     ap.add_argument("--no-cpu", action="store_true")
@@ -1361,10 +1377,12 @@ def main():
     ap.add_argument("--ws-batch", type=int, default=8)
     ap.add_argument("--ws-lr", type=float, default=1e-3)
     ap.add_argument("--ws-verbose", action="store_true")
-    ap.add_argument("--factor-ctas-per-sm", type=int, default=1,
-                    help="persistent factorisation CTAs per SM (0: library default)")
-    ap.add_argument("--lookahead", type=int, default=6,
-                    help="steps the geometry chain runs ahead in the chosen form (0: one chain)")
+    ap.add_argument("--factor-ctas-per-sm", type=int, default=None,
+                    help="persistent factorisation CTAs per SM shared by the factorisations in "
+                         "flight (0: library default; default 2 for mixed_inv, else 1)")
+    ap.add_argument("--lookahead", type=int, default=None,
+                    help="steps the geometry chain runs ahead in the chosen form (0: one chain; "
+                         "default 8 for mixed_inv, else 6)")
     ap.add_argument("--batch-steps", type=int, default=5,
                     help="timed steps of the 96-problem batched block (0: skip it)")
     ap.add_argument("--batch-only", action="store_true",
@@ -1382,6 +1400,13 @@ def main():
     args = ap.parse_args()
     global CHOSEN_SOLVER
     CHOSEN_SOLVER = args.solver
+    # measured best per solve: the inverse form's short iterate chain leaves the
+    # step to the factorisations in flight, which gain from a longer lookahead
+    # and a second CTA per SM; the triangular sweeps' chain does not
+    if args.lookahead is None:
+        args.lookahead = 8 if args.solver == "mixed_inv" else 6
+    if args.factor_ctas_per_sm is None:
+        args.factor_ctas_per_sm = 2 if args.solver == "mixed_inv" else 1
     args.r_warm = workload_of(args.workload)[0].r + 1
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

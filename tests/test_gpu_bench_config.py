@@ -2,17 +2,20 @@
 the float64 oracle (Eq. ram / Eq. B_k).
 
 The headline runs the 256 x 256 workload (p = 2178) pipelined: the geometry
-chain six steps ahead of the iterate chain, the extended ring of r+1+D slots,
-D+1 factor buffers, the window factored in chronological order with the
-short first forward sweep, one persistent-factorisation CTA per SM shared by
-the factorisations in flight, CUDA graphs.  These tests run exactly that
-context for more than r+1+D steps, so that the extended ring and the factor
-buffers wrap, and compare sampled steps element-wise with the oracle's step
-taken from the GPU's own previous iterate:
+chain eight steps ahead of the iterate chain, the extended ring of r+1+D
+slots, D+1 factor buffers, the window factored in chronological order by the
+persistent tiled factorisation (two CTAs per SM shared by the factorisations
+in flight), its inverse L^{-1} formed on the tensor cores, the iterate chain
+solving through L^{-1}, CUDA graphs.  These tests run exactly that context
+(and the other forms, six steps ahead with one CTA per SM) for more than
+r+1+D steps, so that the extended ring and the factor buffers wrap, and
+compare sampled steps element-wise with the oracle's step taken from the
+GPU's own previous iterate:
 
-  float32 form (float32 factor + 2 float64-residual refinements): 1e-5
-  the tensor-core factor and inverse L^{-1}, 3 refinements:        1e-5
-  float64 form (float64 factor, same pipeline):                     1e-12
+  float32 factor + tensor-core inverse, 2 refinements (the headline): 1e-5
+  float32 factor + triangular sweeps, 2 float64-residual refinements:  1e-5
+  the tensor-core factor and inverse L^{-1}, 3 refinements:            1e-5
+  float64 form (float64 factor, same pipeline):                         1e-12
 
 They also compare the memory (ring ids, exact) and the Gram matrix of the
 window (1e-13 of its largest entry) with the oracle's, and run the mixed
@@ -54,7 +57,7 @@ SOLVERS = {"mixed": "SLIM_SOLVE_MIXED", "mixed_tc": "SLIM_SOLVE_MIXED_TC",
 
 
 def _context(sl, cfg, form, refine_iters=2, **kw):
-    """The bench's chosen form (`mixed`) or the same pipeline with the float64
+    """A float32-factor form of SOLVERS or the same pipeline with the float64
     factor (`fp64`), on torch's current stream."""
     common = dict(lookahead=LOOKAHEAD, ctas_per_sm=1, use_graph=True)
     common.update(kw)
@@ -110,6 +113,24 @@ def test_bench_configuration_at_full_size(sl, c2, form, tol, refine):
     steps = cfg.r + 1 + LOOKAHEAD + 4            # the extended ring (12 slots) wraps
     check = {1, 2, 6, 7, 12, 13, 14, 15, 16}
     _run_sampled(s, g, b, cfg, steps, check, tol, mem_at=(7, 13, 16))
+    assert s.get_iter() == steps
+    s.close()
+
+
+# the headline's launch configuration: eight steps ahead, two factorisation
+# CTAs per SM
+HEADLINE_LOOKAHEAD, HEADLINE_CTAS = 8, 2
+
+
+def test_headline_configuration_at_full_size(sl, c2):
+    cfg = workloads.C2
+    g, _, _, b = c2
+    s = _context(sl, cfg, "mixed_inv", refine_iters=2, lookahead=HEADLINE_LOOKAHEAD,
+                 ctas_per_sm=HEADLINE_CTAS)
+    s.set_data(b.astype(np.float32))
+    steps = cfg.r + 1 + HEADLINE_LOOKAHEAD + 4   # the extended ring (14 slots) and the 9
+    check = {1, 2, 6, 8, 9, 10, 14, 15, 16, 17, 18}   # factor buffers wrap
+    _run_sampled(s, g, b, cfg, steps, check, 1e-5, mem_at=(9, 15, 18))
     assert s.get_iter() == steps
     s.close()
 
