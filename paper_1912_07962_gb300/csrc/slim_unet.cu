@@ -631,6 +631,316 @@ int wgrad_splits(int M, int N, int K) {
 
 
 // ---------------------------------------------------------------------------
+// Convolutions from activations split in advance.  A 3x3 convolution reads
+// every activation nine times (once per tap) from the tiles of every output
+// channel block; splitting it into bfloat16 terms inside each CTA repeats
+// that work and keeps the gathers in registers.  Instead the activation
+// X [C][P] is split once into three planes, term j at planes + j P C, each
+// pixel's C terms contiguous ([P][C], C a multiple of 8): the 64 k of a
+// slice (one tap, 64 channels, or two taps of 32) of one pixel are then
+// 16-byte runs that cp.async copies straight into the 128-byte-swizzled
+// K-major tile, zero-filled outside the image.  The weight operand A(m, k)
+// (one bfloat16 term) is laid out once per call as rows of K bfloat16
+// (arrange_rows_kernel), so its 16-byte runs are copied the same way.  The
+// copies of the next kStages - 1 slices are in flight while the tensor cores
+// work on this one.  The split is the same rounding as stage_terms128<3>
+// (and <1> for the weights), so the products are those of t5_gemm_kernel.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) split_planes_kernel(const float* __restrict__ X, int C,
+                                                           long long P,
+                                                           __nv_bfloat16* __restrict__ planes) {
+  __shared__ float tile[32][33];
+  const long long p0 = (long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int c = c0 + ty + 8 * i;
+    const long long p = p0 + tx;
+    tile[ty + 8 * i][tx] = (c < C && p < P) ? X[(size_t)c * P + p] : 0.f;
+  }
+  __syncthreads();
+  const size_t plane = (size_t)P * C;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long long p = p0 + ty + 8 * i;
+    const int c = c0 + tx;
+    if (p >= P || c >= C) continue;
+    float v = tile[tx][ty + 8 * i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const __nv_bfloat16 t = __float2bfloat16_rn(v);
+      planes[j * plane + (size_t)p * C + c] = t;
+      v -= __bfloat162float(t);
+    }
+  }
+}
+
+cudaError_t split_planes(const float* X, int C, long long P, __nv_bfloat16* planes,
+                         cudaStream_t s) {
+  split_planes_kernel<<<dim3((unsigned)cdiv(P, 32), (unsigned)cdiv(C, 32)), 256, 0, s>>>(X, C, P,
+                                                                                        planes);
+  return cudaGetLastError();
+}
+
+// A(m, k) of a loader as bfloat16 rows of K (K a multiple of 8), one thread
+// per 8 consecutive k.
+template <class LA>
+__global__ void __launch_bounds__(256) arrange_rows_kernel(LA la, int M, int K,
+                                                           __nv_bfloat16* __restrict__ out) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int kc = K / 8;
+  if (q >= (long long)M * kc) return;
+  const int m = (int)(q / kc), k = (int)(q - (long long)m * kc) * 8;
+  float v[8];
+  la.load8(la.row(m), k, K, v);
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    w[i] = *reinterpret_cast<const uint32_t*>(&h);
+  }
+  *reinterpret_cast<uint4*>(out + (size_t)m * K + k) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+template <class LA>
+cudaError_t arrange_rows(LA la, int M, int K, __nv_bfloat16* out, cudaStream_t s) {
+  const long long n = (long long)M * (K / 8);
+  arrange_rows_kernel<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(la, M, K, out);
+  return cudaGetLastError();
+}
+
+// The pixel operand of a 3x3 convolution from the planes: row = pixel p,
+// k = t C + c, A(p, k) = X[c][img, y+u-1, x+v-1] with t = 3u + v.
+struct PixPlanes {
+  const __nv_bfloat16* planes;
+  long long P;
+  int H, W, C;
+};
+
+template <int BN>
+struct T5ConvShape {
+  static constexpr int kTermN = kT5N * 128;                 // one pixel-side term tile
+  static constexpr int kTermM = BN * 128;                   // the weights' one term
+  static constexpr int kStage = 3 * kTermN + kTermM;
+  static constexpr int kFit = (227 * 1024 - 1024 - 256) / kStage;
+  static constexpr int kStages = kFit > 4 ? 4 : kFit;     // 4, 4, 3, 2 for BN = 32 .. 256
+  static constexpr int kSmem = kStages * kStage + 1024;
+  static constexpr int kChunksM = (BN * 8 + kT - 1) / kT;    // 16-byte weight chunks per thread
+  static constexpr int kChunksN = kT5N * 8 / kT;            // 16-byte pixel chunks per thread
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// wa: A as bfloat16 rows of K (arrange_rows), out.M rows.
+template <class OUT, int BN>
+__global__ void __launch_bounds__(kT, 1)
+    t5_conv_kernel(OUT out, const __nv_bfloat16* __restrict__ wa, PixPlanes xb, int K,
+                   int kchunk) {
+  using S = T5ConvShape<BN>;
+  constexpr int NS = S::kStages;
+  namespace t5 = slim::t5;
+  extern __shared__ unsigned char t5_raw[];
+  __shared__ uint64_t s_bar[NS];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(t5_raw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * BN;
+  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+  const int nslice = kend > kbeg ? (kend - kbeg + kT5K - 1) / kT5K : 0;
+  const int ntiles = (out.N + kT5N - 1) / kT5N;
+  constexpr uint32_t kIdesc = t5::idesc_bf16(kT5N, BN);
+  const size_t plane = (size_t)xb.P * xb.C;
+  const int HW = xb.H * xb.W;
+
+  if (tid == 0) {
+    for (int i = 0; i < NS; ++i) t5::mbar_init(t5::smem_u32(&s_bar[i]), 1);
+    s_fail = 0;
+    t5::fence_barrier_init();
+  }
+  if (warp == 0) t5::tmem_alloc(t5::smem_u32(&s_tmem), BN);
+  t5::fence_before();
+  __syncthreads();
+  t5::fence_after();
+  const uint32_t tmem = s_tmem;
+
+
+  int cg = 0;   // slices across the CTA's tiles: stage cg % NS, phase cg / NS
+  for (int tile = blockIdx.x; tile < ntiles && !s_fail; tile += gridDim.x) {
+    const int n0 = tile * kT5N;
+    // this thread's pixel chunks q = tid + 256 i: row q / 8, chunk q % 8 (a warp
+    // covers four pixels' 128-byte runs)
+    long long pix[S::kChunksN];
+    int py[S::kChunksN], px[S::kChunksN];
+#pragma unroll
+    for (int i = 0; i < S::kChunksN; ++i) {
+      const long long p = n0 + ((tid + i * kT) >> 3);
+      pix[i] = p < xb.P ? p : -1;
+      const int rem = p < xb.P ? (int)(p % HW) : 0;
+      py[i] = rem / xb.W;
+      px[i] = rem - py[i] * xb.W;
+    }
+    // issue the copies of slice c (pixel terms and weights) into stage st
+    auto issue = [&](int c, int st) {
+      unsigned char* sn = smem + st * S::kStage;
+#pragma unroll
+      for (int i = 0; i < S::kChunksM; ++i) {
+        const int q = tid + i * kT, row = q >> 3, g = q & 7;
+        if (row >= BN) break;
+        const int m = m0 + row, k = kbeg + c * kT5K + 8 * g;
+        const bool in = m < out.M && k < kend;
+        cp_async16(t5::smem_u32(sn + 3 * S::kTermN) + t5::sw128_off(row, g),
+                   in ? wa + (size_t)m * K + k : wa, in ? 16u : 0u);
+      }
+#pragma unroll
+      for (int i = 0; i < S::kChunksN; ++i) {
+        const int q = tid + i * kT, row = q >> 3, g = q & 7;
+        const int k = kbeg + c * kT5K + 8 * g;
+        const __nv_bfloat16* src = xb.planes;
+        uint32_t bytes = 0;
+        if (pix[i] >= 0 && k < kend) {
+          const int t = k / xb.C, ch = k - t * xb.C;
+          const int du = t / 3 - 1, dv = t % 3 - 1;
+          const int yy = py[i] + du, xx = px[i] + dv;
+          if (yy >= 0 && yy < xb.H && xx >= 0 && xx < xb.W) {
+            src = xb.planes + (size_t)(pix[i] + (long long)du * xb.W + dv) * xb.C + ch;
+            bytes = 16;
+          }
+        }
+        const uint32_t dst = t5::smem_u32(sn) + t5::sw128_off(row, g);
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          cp_async16(dst + j * S::kTermN, src + (bytes ? j * plane : 0), bytes);
+      }
+    };
+#pragma unroll 1
+    for (int c = 0; c < NS - 1; ++c) {
+      if (c < nslice) issue(c, (cg + c) % NS);
+      cp_async_commit();
+    }
+    bool started = false;
+    for (int c = 0; c < nslice; ++c, ++cg) {
+      const int st = cg % NS;
+      const int cpre = c + NS - 1;
+      if (cpre < nslice) {
+        // the prefetch reuses the stage of slice cg - 1: its products must be done
+        if (cg >= 1 && !t5::mbar_wait(t5::smem_u32(&s_bar[(cg - 1) % NS]),
+                                      (uint32_t)(((cg - 1) / NS) & 1), kT5Spin))
+          s_fail = 1;
+        if (!s_fail) issue(cpre, (cg + NS - 1) % NS);
+      }
+      cp_async_commit();
+      unsigned char* sm = smem + st * S::kStage + 3 * S::kTermN;
+      cp_async_wait<NS - 1>();   // this thread's copies of slice c have landed
+      t5::fence_proxy_async();
+      __syncthreads();
+      if (s_fail) break;   // uniform after the barrier
+      if (tid == 0) {
+        t5::fence_after();
+        const uint32_t an = t5::smem_u32(smem + st * S::kStage), bm = t5::smem_u32(sm);
+#pragma unroll
+        for (int kk = 0; kk < kT5K / 16; ++kk) {
+#pragma unroll
+          for (int i = 2; i >= 0; --i) {   // smallest terms first, as t5_gemm_kernel<.., 1, 3>
+            const uint64_t ad = t5::desc_sw128(an + i * S::kTermN) + (uint64_t)(kk * 2);
+            const uint64_t bd = t5::desc_sw128(bm) + (uint64_t)(kk * 2);
+            t5::mma_bf16(tmem, ad, bd, kIdesc, started ? 1u : 0u);
+            started = true;
+          }
+        }
+        t5::mma_commit(t5::smem_u32(&s_bar[st]));
+      }
+    }
+    if (s_fail) break;
+    if (nslice > 0) {
+      const int cl = cg - 1;
+      if (!t5::mbar_wait(t5::smem_u32(&s_bar[cl % NS]), (uint32_t)((cl / NS) & 1), kT5Spin))
+        s_fail = 1;
+    }
+    t5::fence_after();
+    __syncthreads();
+    if (s_fail) break;
+    const int q = warp & 3, h = warp >> 2;
+    const int n = n0 + 32 * q + lane;
+    const bool split = gridDim.z > 1;
+#pragma unroll 1
+    for (int g = 0; g < BN / 16; ++g) {
+      const int col = h * (BN / 2) + 8 * g;
+      float v[8];
+      if (nslice > 0) {
+        t5::tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = 0.f;
+      }
+      if (n < out.N) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int m = m0 + col + e;
+          if (m < out.M) out.store(m, n, v[e], split);
+        }
+      }
+    }
+    t5::fence_before();
+    __syncthreads();
+  }
+  cp_async_wait_all();   // no copy is left in flight into the CTA's shared memory
+  if (s_fail && tid == 0) atomicExch(&g_t5_timeout, 1);
+  t5::fence_before();
+  __syncthreads();
+  if (warp == 0) t5::tmem_dealloc(tmem, BN);
+}
+
+template <int BN, class OUT>
+cudaError_t t5_conv_launch_bn(const OUT& o, int K, const __nv_bfloat16* wa, const PixPlanes& xb,
+                              int splits, cudaStream_t s) {
+  using S = T5ConvShape<BN>;
+  auto kern = t5_conv_kernel<OUT, BN>;
+  static unsigned long long attr_set = 0;   // per device: shared-memory opt-in done
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 64 || !(attr_set >> dev & 1)) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmem);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) attr_set |= 1ULL << dev;
+  }
+  splits = std::max(1, std::min(splits, cdiv(K, kT5K)));
+  const int kchunk = cdiv(cdiv(K, splits), kT5K) * kT5K;
+  splits = cdiv(K, kchunk);
+  const int ntiles = cdiv(o.N, kT5N);
+  dim3 grid((unsigned)std::min(ntiles, 65535), cdiv(o.M, BN), splits);
+  kern<<<grid, kT, S::kSmem, s>>>(o, wa, xb, K, kchunk);
+  return cudaGetLastError();
+}
+
+template <class OUT>
+cudaError_t conv_launch(const OUT& o, int K, const __nv_bfloat16* wa, const PixPlanes& xb,
+                        int splits, cudaStream_t s) {
+  if (o.M <= 0 || o.N <= 0) return cudaSuccess;
+  switch (t5_bn(o.M)) {
+    case 32: return t5_conv_launch_bn<32>(o, K, wa, xb, splits, s);
+    case 64: return t5_conv_launch_bn<64>(o, K, wa, xb, splits, s);
+    case 128: return t5_conv_launch_bn<128>(o, K, wa, xb, splits, s);
+    default: return t5_conv_launch_bn<256>(o, K, wa, xb, splits, s);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Layout kernels
 // ---------------------------------------------------------------------------
 // 2x2 max-pool: first maximum in row-major window order (arg in 0..3).
@@ -747,10 +1057,44 @@ cudaError_t gemm_out(float* C, int M, int N, int K, LA la, LB lb, const float* b
   return cudaGetLastError();
 }
 
+// gemm_out with both operands copied asynchronously (t5_conv_kernel): the
+// weight operand laid out at wa (M x K bfloat16), the pixel operand's planes.
+template <class LA>
+cudaError_t conv_out(float* C, int M, int N, int K, LA la, __nv_bfloat16* wa, const PixPlanes& xb,
+                     const float* bias, bool relu, cudaStream_t s) {
+  cudaError_t e = arrange_rows(la, M, K, wa, s);
+  if (e != cudaSuccess) return e;
+  const int splits = out_splits(M, N, K);
+  if (splits == 1)
+    return conv_launch(OutPlain{C, N, M, N, bias, relu ? 1 : 0, 0}, K, wa, xb, 1, s);
+  e = cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  e = conv_launch(OutPlain{C, N, M, N, nullptr, 0, 1}, K, wa, xb, splits, s);
+  if (e != cudaSuccess || (!bias && !relu)) return e;
+  bias_act_kernel<<<grid_for((long long)M * N), kT, 0, s>>>(C, bias, relu ? 1 : 0, M, N);
+  return cudaGetLastError();
+}
+
+// Bytes of the planes of a C x P activation; 0 when C is not a multiple of 8
+// (those convolutions gather and split in the CTA).
+size_t planes_bytes(int C, long long P) { return C % 8 ? 0 : 3 * (size_t)C * P * sizeof(__nv_bfloat16); }
+// Bytes of the laid-out weight operand of a 3x3 convolution (either direction).
+size_t conv_weight_bytes(int Ci, int Co) { return 9 * (size_t)Ci * Co * sizeof(__nv_bfloat16); }
+
 // Y = W * col(X) + b (ReLU): M = C_out, N = pixels, K = 9 C_in (tap-major).
+// With scratch for the planes (planes_bytes(C_in, P)) and the weights
+// (conv_weight_bytes) both operands are laid out once and copied
+// asynchronously.
 cudaError_t conv3x3_fwd(const float* X, int n, int Ci, int H, int W, const float* Wt,
-                        const float* b, int Co, bool relu, float* Y, cudaStream_t s) {
+                        const float* b, int Co, bool relu, float* Y, cudaStream_t s,
+                        __nv_bfloat16* planes = nullptr, __nv_bfloat16* wa = nullptr) {
   const long long P = (long long)n * H * W;
+  if (planes && wa && Ci % 8 == 0) {
+    cudaError_t e = split_planes(X, Ci, P, planes, s);
+    if (e != cudaSuccess) return e;
+    return conv_out(Y, Co, (int)P, 9 * Ci, LoadWTap{Wt, Ci, Co}, wa,
+                    PixPlanes{planes, P, H, W, Ci}, b, relu, s);
+  }
   return gemm_out<1, 3>(Y, Co, (int)P, 9 * Ci, LoadWTap{Wt, Ci, Co}, LoadPixTap{X, P, H, W, Ci}, b,
                         relu, s);
 }
@@ -761,7 +1105,8 @@ cudaError_t conv3x3_fwd(const float* X, int n, int Ci, int H, int W, const float
 //   dX  = Wf col(dY)       the adjoint conv, Wf[c][t*C_out + o] = W[o][c][8-t]:
 //                          M = C_in, N = pixels, K = 9 C_out
 cudaError_t conv3x3_bwd(const float* X, const float* dY, int n, int Ci, int H, int W,
-                        const float* Wt, int Co, float* dW, float* db, float* dX, cudaStream_t s) {
+                        const float* Wt, int Co, float* dW, float* db, float* dX, cudaStream_t s,
+                        __nv_bfloat16* planes = nullptr, __nv_bfloat16* wa = nullptr) {
   const long long P = (long long)n * H * W;
   const int K9 = 9 * Ci;
   cudaError_t e = tc_launch<2, 2>(OutPlain{dW, K9, Co, K9, nullptr, 0, 1}, (int)P,
@@ -770,6 +1115,11 @@ cudaError_t conv3x3_bwd(const float* X, const float* dY, int n, int Ci, int H, i
   if (e != cudaSuccess) return e;
   if (db && (e = rowsum(dY, Co, P, db, s)) != cudaSuccess) return e;
   if (!dX) return cudaSuccess;
+  if (planes && wa && Co % 8 == 0) {
+    if ((e = split_planes(dY, Co, P, planes, s)) != cudaSuccess) return e;
+    return conv_out(dX, Ci, (int)P, 9 * Co, LoadFlipW{Wt, Ci, Co}, wa,
+                    PixPlanes{planes, P, H, W, Co}, nullptr, false, s);
+  }
   return gemm_out<1, 3>(dX, Ci, (int)P, 9 * Co, LoadFlipW{Wt, Ci, Co}, LoadPixTap{dY, P, H, W, Co},
                         nullptr, false, s);
 }
@@ -899,6 +1249,8 @@ struct slim_unet {
         *gbt = nullptr, *gd3a = nullptr, *gd3 = nullptr, *gd2a = nullptr, *gd2 = nullptr,
         *gd1a = nullptr, *gd1 = nullptr, *gy = nullptr;
   unsigned char *arg1 = nullptr, *arg2 = nullptr, *arg3 = nullptr;
+  __nv_bfloat16* planes = nullptr;   // a convolution input (or output gradient) split into terms
+  __nv_bfloat16* wa = nullptr;       // a convolution's weight operand laid out as rows of K
   double* loss = nullptr;
   std::vector<void*> allocs;
 };
@@ -921,7 +1273,8 @@ struct Net {
 
   cudaError_t conv(int l, const float* X, int level, float* Y, bool relu) const {
     const LayerSpec& L = kLayers[l];
-    return conv3x3_fwd(X, n, L.i, h(level), w(level), W_(l), B_(l), L.o, relu, Y, s);
+    return conv3x3_fwd(X, n, L.i, h(level), w(level), W_(l), B_(l), L.o, relu, Y, s, u->planes,
+                       u->wa);
   }
   // dY holds the gradient at the ReLU output; on return dX (if any) holds the
   // gradient at the layer input.
@@ -931,7 +1284,8 @@ struct Net {
     relu_mask_kernel<<<grid_for(count), kT, 0, s>>>(dY, Yout, count);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return conv3x3_bwd(X, dY, n, L.i, h(level), w(level), W_(l), L.o, gW(l), gB(l), dX, s);
+    return conv3x3_bwd(X, dY, n, L.i, h(level), w(level), W_(l), L.o, gW(l), gB(l), dX, s,
+                       u->planes, u->wa);
   }
   // transposed conv from level `lin` (input) to lin-1
   cudaError_t tconv(int l, const float* X, int lin, float* Y) const {
@@ -1052,17 +1406,46 @@ bool layer_sizes_ok(int n, int ci, int H, int W, int co) {
 slim_status layer_status(cudaError_t e) { return e == cudaSuccess ? SLIM_OK : SLIM_ECUDA; }
 }  // namespace
 
+namespace {
+// Planes and weight-layout scratch of the standalone layer calls, one block
+// from the stream-ordered pool (none when the planes do not apply).
+struct PlanesScratch {
+  __nv_bfloat16* p = nullptr;
+  __nv_bfloat16* w = nullptr;
+  cudaStream_t s;
+  PlanesScratch(size_t planes, size_t weights, cudaStream_t st) : s(st) {
+    if (!planes) return;
+    const size_t off = (planes + 255) / 256 * 256;
+    unsigned char* q = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&q), off + weights, s) != cudaSuccess) {
+      cudaGetLastError();
+      return;   // the convolution then gathers and splits in the CTA
+    }
+    p = reinterpret_cast<__nv_bfloat16*>(q);
+    w = reinterpret_cast<__nv_bfloat16*>(q + off);
+  }
+  ~PlanesScratch() {
+    if (p) cudaFreeAsync(p, s);
+  }
+};
+}  // namespace
+
 slim_status slim_unet_conv3x3(const float* x, int n, int c_in, int H, int W, const float* w,
                               const float* b, int c_out, int relu, float* y, void* stream) {
   if (!x || !w || !y || !layer_sizes_ok(n, c_in, H, W, c_out)) return SLIM_EINVAL;
-  return layer_status(conv3x3_fwd(x, n, c_in, H, W, w, b, c_out, relu != 0, y, (cudaStream_t)stream));
+  cudaStream_t s = (cudaStream_t)stream;
+  PlanesScratch ps(planes_bytes(c_in, (long long)n * H * W), conv_weight_bytes(c_in, c_out), s);
+  return layer_status(conv3x3_fwd(x, n, c_in, H, W, w, b, c_out, relu != 0, y, s, ps.p, ps.w));
 }
 
 slim_status slim_unet_conv3x3_grad(const float* x, const float* dy, int n, int c_in, int H, int W,
                                    const float* w, int c_out, float* dw, float* db, float* dx,
                                    void* stream) {
   if (!x || !dy || !w || !dw || !layer_sizes_ok(n, c_in, H, W, c_out)) return SLIM_EINVAL;
-  return layer_status(conv3x3_bwd(x, dy, n, c_in, H, W, w, c_out, dw, db, dx, (cudaStream_t)stream));
+  cudaStream_t s = (cudaStream_t)stream;
+  PlanesScratch ps(dx ? planes_bytes(c_out, (long long)n * H * W) : 0, conv_weight_bytes(c_in, c_out),
+                   s);
+  return layer_status(conv3x3_bwd(x, dy, n, c_in, H, W, w, c_out, dw, db, dx, s, ps.p, ps.w));
 }
 
 slim_status slim_unet_tconv2x2(const float* x, int n, int c_in, int H, int W, const float* w,
@@ -1125,6 +1508,21 @@ slim_status slim_unet_create(int H, int W, int max_batch, slim_unet** out) {
   fa(&u->gd3, 128 * P3); fa(&u->gd2a, 64 * P2); fa(&u->gd2, 64 * P2); fa(&u->gd1a, 32 * P1);
   fa(&u->gd1, 32 * P1); fa(&u->gy, P1);
   ba(&u->arg1, 32 * P2); ba(&u->arg2, 64 * P3); ba(&u->arg3, 128 * P4);
+  {
+    // the widest 3x3-convolution input (or output gradient) of each level: 64
+    // channels at level 1 (dec1a), 128 at 2 (dec2a), 256 at 3 (dec3a) and 4 (botb)
+    const size_t need = std::max(std::max(planes_bytes(64, P1), planes_bytes(128, P2)),
+                                 std::max(planes_bytes(256, P3), planes_bytes(256, P4)));
+    unsigned char* q = nullptr;
+    ba(&q, (long long)need);
+    u->planes = reinterpret_cast<__nv_bfloat16*>(q);
+    size_t wneed = 0;
+    for (int l = 0; l < kNumLayers; ++l)
+      if (kLayers[l].kind == kConv) wneed = std::max(wneed, conv_weight_bytes(kLayers[l].i, kLayers[l].o));
+    q = nullptr;
+    ba(&q, (long long)wneed);
+    u->wa = reinterpret_cast<__nv_bfloat16*>(q);
+  }
   if (ok) {
     void* q = nullptr;
     ok = cudaMalloc(&q, sizeof(double)) == cudaSuccess;
