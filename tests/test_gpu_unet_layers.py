@@ -47,7 +47,13 @@ def _check(got, want, mag, rel, what):
 # (n, c_in, H, W, c_out): ragged in every dimension; one channel in (K = 9);
 # the deepest layer's K = 2304 on a 6 x 10 grid; a level-1-like case whose
 # weight gradient is split four ways
-CONV_CASES = [(3, 37, 20, 27, 70), (1, 1, 8, 8, 32), (1, 256, 6, 10, 256), (2, 32, 48, 48, 64)]
+# channel counts that are multiples of 8 take the convolution from pre-split
+# planes (forward: c_in; input gradient: c_out), the others the gathering
+# kernel; (2, 24, 13, 21, 40) has both on the planes path with ragged output
+# channels (40 of a 64-wide tile, 24 of 32) and K = 216 / 360, which end in
+# part-filled 64-wide slices
+CONV_CASES = [(3, 37, 20, 27, 70), (1, 1, 8, 8, 32), (1, 256, 6, 10, 256), (2, 32, 48, 48, 64),
+              (2, 24, 13, 21, 40)]
 
 
 @pytest.mark.parametrize("n,ci,H,W,co", CONV_CASES)
