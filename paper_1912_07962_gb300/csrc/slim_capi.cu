@@ -358,11 +358,12 @@ int kernels_per_step(const slim_ctx* c) {
     // geometry: sample, taps, Gram, map clear, ring map, K; the factor (per
     // panel: diagonal tile, panel product, trailing product; the last panel
     // its diagonal tile only -- or one persistent launch), the inverse
-    // (diagonal tiles, one product per recursion depth and side, mirror);
+    // (diagonal tiles; per recursion depth and side a split pass of the
+    // operands and one product; mirror);
     // iterate: residual, 2 products per solve, a residual per refinement
     // round, scatter -- or all of the iterate chain in one cooperative kernel
     const int factor = c->solver == SLIM_SOLVE_MIXED_TC ? 3 * c->cplan[0].T - 2 : 1;
-    const int inv = 2 + (int)c->tplan[0].level_first.size() - 1;
+    const int inv = 2 + 2 * ((int)c->tplan[0].level_first.size() - 1);
     const int tik = c->tik_lambda > 0.0 ? 2 : 0;
     const int iterate = c->coop_grid ? 1 : 1 + 2 * solves + c->refine_iters + 1 + tik;
     return 6 + factor + inv + iterate;

@@ -147,6 +147,25 @@ def test_tensor_core_inverse_solves(sl, D, r, N, V, det, solver):
     s.close()
 
 
+def _inverse_depths(T):
+    # recursion depths of the triangular inverse over T tiles (a range of n
+    # tiles splits into floor(n/2) and ceil(n/2) until single tiles remain)
+    return 0 if T <= 1 else 1 + _inverse_depths((T + 1) // 2)
+
+
+@pytest.mark.parametrize("N,V,det,r", [(32, 20, 47, 2), (64, 30, 91, 3), (256, 180, 363, 5)])
+def test_inverse_form_kernels_per_step(sl, N, V, det, r):
+    # the launches one step of the pipelined inverse form makes: the geometry
+    # chain's six kernels, one persistent factorisation, the inverse (diagonal
+    # tiles, a split pass and a product per side at every recursion depth,
+    # the mirror) and the cooperative iterate chain
+    s = sl.Slim(N, V, det, det, r, 1e-2, 1, precision=sl.SLIM_PREC_FP32,
+                solver=sl.SLIM_SOLVE_MIXED_INV, lookahead=2)
+    T = (s.p + 63) // 64
+    assert s.kernels_per_step() == 6 + 1 + (2 + 4 * _inverse_depths(T)) + 1
+    s.close()
+
+
 @pytest.mark.parametrize("solver", ["SLIM_SOLVE_MIXED_TC", "SLIM_SOLVE_MIXED_INV"])
 def test_tensor_core_inverse_argument_checks(sl, solver):
     with pytest.raises(sl.SlimError) as ei:      # needs the pipelined form
