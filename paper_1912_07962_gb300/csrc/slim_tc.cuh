@@ -88,8 +88,9 @@ cudaError_t tc_prepare();
 // P x P buffer X (diagonal included) and X^T in its strict upper triangle.
 // The recursion splits the tile range [a, b) at m = (a + b) / 2:
 //   X11 = inv(L11), X22 = inv(L22),  X21 = -X22 (L21 X11),
-// all blocks of one recursion depth in one batched launch per product; the
-// intermediate L21 X11 is held, transposed, in X's upper triangle.
+// all blocks of one recursion depth in one batched launch per product (a
+// split pass of its operands, then tc_gemm_planes); the intermediate L21 X11
+// is held, transposed, in X's upper triangle.
 struct TriInvPlan {
   int P = 0, T = 0;
   std::vector<int> level_first;       // problems of depth d: [level_first[d], level_first[d+1])
