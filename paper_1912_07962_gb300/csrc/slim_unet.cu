@@ -709,24 +709,66 @@ cudaError_t arrange_rows(LA la, int M, int K, __nv_bfloat16* out, cudaStream_t s
   return cudaGetLastError();
 }
 
-// The pixel operand of a 3x3 convolution from the planes: row = pixel p,
-// k = t C + c, A(p, k) = X[c][img, y+u-1, x+v-1] with t = 3u + v.
-struct PixPlanes {
+constexpr int kConvChunksN = kT5N * 8 / kT;   // 16-byte chunks of the 128-row side per thread
+
+// Operand source of t5_conv_kernel.  A source places one 64-wide K slice
+// of both operands as 16-byte copies: the GEMM's N side (the MMA's 128 rows,
+// kTB bfloat16 terms) and its M side (BN rows, kTA terms).  off_n / off_m
+// give the element offset of term 0 of a chunk of 8 consecutive k, or -1
+// where the chunk is zero; term j lies stride_n (stride_m) elements further.
+// (Weight gradients through row-shifted two-term planes of X were measured
+// too: the same bytes move either way, and the training step did not gain.)
+
+// 3x3 convolution: N rows are pixels p, k = t C + c with tap t = 3u + v,
+// B(p, k) = X[c][img, y+u-1, x+v-1] from planes [3][P][C] (C a multiple of
+// 8); A(m, k) the weights as bfloat16 rows of K.
+struct ConvSrc {
+  static constexpr int kTA = 1, kTB = 3;
+  const __nv_bfloat16* wa;
   const __nv_bfloat16* planes;
   long long P;
-  int H, W, C;
+  int H, W, C, M, K;
+  struct State {
+    long long pix[kConvChunksN];
+    int py[kConvChunksN], px[kConvChunksN];
+  };
+  __device__ void tile(State& st, int n0, int tid) const {
+    const int HW = H * W;
+#pragma unroll
+    for (int i = 0; i < kConvChunksN; ++i) {
+      const long long p = n0 + ((tid + i * kT) >> 3);
+      st.pix[i] = p < P ? p : -1;
+      const int rem = p < P ? (int)(p % HW) : 0;
+      st.py[i] = rem / W;
+      st.px[i] = rem - st.py[i] * W;
+    }
+  }
+  __device__ long long off_n(const State& st, int i, int k, int kend) const {
+    if (st.pix[i] < 0 || k >= kend) return -1;
+    const int t = k / C, ch = k - t * C;
+    const int du = t / 3 - 1, dv = t % 3 - 1;
+    const int yy = st.py[i] + du, xx = st.px[i] + dv;
+    if (yy < 0 || yy >= H || xx < 0 || xx >= W) return -1;
+    return (st.pix[i] + (long long)du * W + dv) * C + ch;
+  }
+  __device__ long long off_m(int m, int k, int kend) const {
+    return m < M && k < kend ? (long long)m * K + k : -1;
+  }
+  __device__ const __nv_bfloat16* base_n() const { return planes; }
+  __device__ const __nv_bfloat16* base_m() const { return wa; }
+  __device__ size_t stride_n() const { return (size_t)P * C; }
+  __device__ size_t stride_m() const { return 0; }
 };
 
-template <int BN>
+template <int BN, int TA, int TB>
 struct T5ConvShape {
-  static constexpr int kTermN = kT5N * 128;                 // one pixel-side term tile
-  static constexpr int kTermM = BN * 128;                   // the weights' one term
-  static constexpr int kStage = 3 * kTermN + kTermM;
+  static constexpr int kTermN = kT5N * 128;                 // one 128-row term tile
+  static constexpr int kTermM = BN * 128;                   // one BN-row term tile
+  static constexpr int kStage = TB * kTermN + TA * kTermM;
   static constexpr int kFit = (227 * 1024 - 1024 - 256) / kStage;
-  static constexpr int kStages = kFit > 4 ? 4 : kFit;     // 4, 4, 3, 2 for BN = 32 .. 256
+  static constexpr int kStages = kFit > 4 ? 4 : kFit;
   static constexpr int kSmem = kStages * kStage + 1024;
-  static constexpr int kChunksM = (BN * 8 + kT - 1) / kT;    // 16-byte weight chunks per thread
-  static constexpr int kChunksN = kT5N * 8 / kT;            // 16-byte pixel chunks per thread
+  static constexpr int kChunksM = (BN * 8 + kT - 1) / kT;    // 16-byte M-side chunks per thread
 };
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
@@ -744,12 +786,10 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// wa: A as bfloat16 rows of K (arrange_rows), out.M rows.
-template <class OUT, int BN>
-__global__ void __launch_bounds__(kT, 1)
-    t5_conv_kernel(OUT out, const __nv_bfloat16* __restrict__ wa, PixPlanes xb, int K,
-                   int kchunk) {
-  using S = T5ConvShape<BN>;
+template <class OUT, class SRC, int BN>
+__global__ void __launch_bounds__(kT, 1) t5_conv_kernel(OUT out, SRC src, int K, int kchunk) {
+  constexpr int TA = SRC::kTA, TB = SRC::kTB, TMAX = TA > TB ? TA : TB;
+  using S = T5ConvShape<BN, TA, TB>;
   constexpr int NS = S::kStages;
   namespace t5 = slim::t5;
   extern __shared__ unsigned char t5_raw[];
@@ -764,8 +804,6 @@ __global__ void __launch_bounds__(kT, 1)
   const int nslice = kend > kbeg ? (kend - kbeg + kT5K - 1) / kT5K : 0;
   const int ntiles = (out.N + kT5N - 1) / kT5N;
   constexpr uint32_t kIdesc = t5::idesc_bf16(kT5N, BN);
-  const size_t plane = (size_t)xb.P * xb.C;
-  const int HW = xb.H * xb.W;
 
   if (tid == 0) {
     for (int i = 0; i < NS; ++i) t5::mbar_init(t5::smem_u32(&s_bar[i]), 1);
@@ -778,53 +816,35 @@ __global__ void __launch_bounds__(kT, 1)
   t5::fence_after();
   const uint32_t tmem = s_tmem;
 
-
   int cg = 0;   // slices across the CTA's tiles: stage cg % NS, phase cg / NS
   for (int tile = blockIdx.x; tile < ntiles && !s_fail; tile += gridDim.x) {
     const int n0 = tile * kT5N;
-    // this thread's pixel chunks q = tid + 256 i: row q / 8, chunk q % 8 (a warp
-    // covers four pixels' 128-byte runs)
-    long long pix[S::kChunksN];
-    int py[S::kChunksN], px[S::kChunksN];
-#pragma unroll
-    for (int i = 0; i < S::kChunksN; ++i) {
-      const long long p = n0 + ((tid + i * kT) >> 3);
-      pix[i] = p < xb.P ? p : -1;
-      const int rem = p < xb.P ? (int)(p % HW) : 0;
-      py[i] = rem / xb.W;
-      px[i] = rem - py[i] * xb.W;
-    }
-    // issue the copies of slice c (pixel terms and weights) into stage st
-    auto issue = [&](int c, int st) {
-      unsigned char* sn = smem + st * S::kStage;
+    typename SRC::State st;
+    src.tile(st, n0, tid);
+    // this thread's copies of slice c into stage sg: chunk q = tid + 256 i is
+    // row q / 8, k-chunk q % 8 (a warp covers four rows' 128-byte runs)
+    auto issue = [&](int c, int sg) {
+      const uint32_t sn = t5::smem_u32(smem + sg * S::kStage), sm = sn + TB * S::kTermN;
 #pragma unroll
       for (int i = 0; i < S::kChunksM; ++i) {
         const int q = tid + i * kT, row = q >> 3, g = q & 7;
         if (row >= BN) break;
-        const int m = m0 + row, k = kbeg + c * kT5K + 8 * g;
-        const bool in = m < out.M && k < kend;
-        cp_async16(t5::smem_u32(sn + 3 * S::kTermN) + t5::sw128_off(row, g),
-                   in ? wa + (size_t)m * K + k : wa, in ? 16u : 0u);
+        const long long o = src.off_m(m0 + row, kbeg + c * kT5K + 8 * g, kend);
+        const __nv_bfloat16* b = src.base_m() + (o >= 0 ? o : 0);
+#pragma unroll
+        for (int j = 0; j < TA; ++j)
+          cp_async16(sm + j * S::kTermM + t5::sw128_off(row, g), o >= 0 ? b + j * src.stride_m() : b,
+                     o >= 0 ? 16u : 0u);
       }
 #pragma unroll
-      for (int i = 0; i < S::kChunksN; ++i) {
+      for (int i = 0; i < kConvChunksN; ++i) {
         const int q = tid + i * kT, row = q >> 3, g = q & 7;
-        const int k = kbeg + c * kT5K + 8 * g;
-        const __nv_bfloat16* src = xb.planes;
-        uint32_t bytes = 0;
-        if (pix[i] >= 0 && k < kend) {
-          const int t = k / xb.C, ch = k - t * xb.C;
-          const int du = t / 3 - 1, dv = t % 3 - 1;
-          const int yy = py[i] + du, xx = px[i] + dv;
-          if (yy >= 0 && yy < xb.H && xx >= 0 && xx < xb.W) {
-            src = xb.planes + (size_t)(pix[i] + (long long)du * xb.W + dv) * xb.C + ch;
-            bytes = 16;
-          }
-        }
-        const uint32_t dst = t5::smem_u32(sn) + t5::sw128_off(row, g);
+        const long long o = src.off_n(st, i, kbeg + c * kT5K + 8 * g, kend);
+        const __nv_bfloat16* b = src.base_n() + (o >= 0 ? o : 0);
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
-          cp_async16(dst + j * S::kTermN, src + (bytes ? j * plane : 0), bytes);
+        for (int j = 0; j < TB; ++j)
+          cp_async16(sn + j * S::kTermN + t5::sw128_off(row, g), o >= 0 ? b + j * src.stride_n() : b,
+                     o >= 0 ? 16u : 0u);
       }
     };
 #pragma unroll 1
@@ -834,35 +854,37 @@ __global__ void __launch_bounds__(kT, 1)
     }
     bool started = false;
     for (int c = 0; c < nslice; ++c, ++cg) {
-      const int st = cg % NS;
-      const int cpre = c + NS - 1;
-      if (cpre < nslice) {
-        // the prefetch reuses the stage of slice cg - 1: its products must be done
+      const int sg = cg % NS;
+      // the prefetch of slice c + NS - 1 reuses the stage of slice cg - 1:
+      // its products must be done
+      if (c + NS - 1 < nslice) {
         if (cg >= 1 && !t5::mbar_wait(t5::smem_u32(&s_bar[(cg - 1) % NS]),
                                       (uint32_t)(((cg - 1) / NS) & 1), kT5Spin))
           s_fail = 1;
-        if (!s_fail) issue(cpre, (cg + NS - 1) % NS);
+        if (!s_fail) issue(c + NS - 1, (cg + NS - 1) % NS);
       }
       cp_async_commit();
-      unsigned char* sm = smem + st * S::kStage + 3 * S::kTermN;
       cp_async_wait<NS - 1>();   // this thread's copies of slice c have landed
       t5::fence_proxy_async();
       __syncthreads();
       if (s_fail) break;   // uniform after the barrier
       if (tid == 0) {
         t5::fence_after();
-        const uint32_t an = t5::smem_u32(smem + st * S::kStage), bm = t5::smem_u32(sm);
+        const uint32_t an = t5::smem_u32(smem + sg * S::kStage), bm = an + TB * S::kTermN;
 #pragma unroll
         for (int kk = 0; kk < kT5K / 16; ++kk) {
 #pragma unroll
-          for (int i = 2; i >= 0; --i) {   // smallest terms first, as t5_gemm_kernel<.., 1, 3>
-            const uint64_t ad = t5::desc_sw128(an + i * S::kTermN) + (uint64_t)(kk * 2);
-            const uint64_t bd = t5::desc_sw128(bm) + (uint64_t)(kk * 2);
-            t5::mma_bf16(tmem, ad, bd, kIdesc, started ? 1u : 0u);
-            started = true;
-          }
+          for (int i = TB - 1; i >= 0; --i)   // smallest terms first, as t5_gemm_kernel
+#pragma unroll
+            for (int j = TA - 1; j >= 0; --j) {
+              if (i + j >= TMAX) continue;
+              const uint64_t ad = t5::desc_sw128(an + i * S::kTermN) + (uint64_t)(kk * 2);
+              const uint64_t bd = t5::desc_sw128(bm + j * S::kTermM) + (uint64_t)(kk * 2);
+              t5::mma_bf16(tmem, ad, bd, kIdesc, started ? 1u : 0u);
+              started = true;
+            }
         }
-        t5::mma_commit(t5::smem_u32(&s_bar[st]));
+        t5::mma_commit(t5::smem_u32(&s_bar[sg]));
       }
     }
     if (s_fail) break;
@@ -905,11 +927,10 @@ __global__ void __launch_bounds__(kT, 1)
   if (warp == 0) t5::tmem_dealloc(tmem, BN);
 }
 
-template <int BN, class OUT>
-cudaError_t t5_conv_launch_bn(const OUT& o, int K, const __nv_bfloat16* wa, const PixPlanes& xb,
-                              int splits, cudaStream_t s) {
-  using S = T5ConvShape<BN>;
-  auto kern = t5_conv_kernel<OUT, BN>;
+template <int BN, class OUT, class SRC>
+cudaError_t t5_conv_launch_bn(const OUT& o, int K, const SRC& src, int splits, cudaStream_t s) {
+  using S = T5ConvShape<BN, SRC::kTA, SRC::kTB>;
+  auto kern = t5_conv_kernel<OUT, SRC, BN>;
   static unsigned long long attr_set = 0;   // per device: shared-memory opt-in done
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -924,19 +945,18 @@ cudaError_t t5_conv_launch_bn(const OUT& o, int K, const __nv_bfloat16* wa, cons
   splits = cdiv(K, kchunk);
   const int ntiles = cdiv(o.N, kT5N);
   dim3 grid((unsigned)std::min(ntiles, 65535), cdiv(o.M, BN), splits);
-  kern<<<grid, kT, S::kSmem, s>>>(o, wa, xb, K, kchunk);
+  kern<<<grid, kT, S::kSmem, s>>>(o, src, K, kchunk);
   return cudaGetLastError();
 }
 
-template <class OUT>
-cudaError_t conv_launch(const OUT& o, int K, const __nv_bfloat16* wa, const PixPlanes& xb,
-                        int splits, cudaStream_t s) {
+template <class OUT, class SRC>
+cudaError_t conv_launch(const OUT& o, int K, const SRC& src, int splits, cudaStream_t s) {
   if (o.M <= 0 || o.N <= 0) return cudaSuccess;
   switch (t5_bn(o.M)) {
-    case 32: return t5_conv_launch_bn<32>(o, K, wa, xb, splits, s);
-    case 64: return t5_conv_launch_bn<64>(o, K, wa, xb, splits, s);
-    case 128: return t5_conv_launch_bn<128>(o, K, wa, xb, splits, s);
-    default: return t5_conv_launch_bn<256>(o, K, wa, xb, splits, s);
+    case 32: return t5_conv_launch_bn<32>(o, K, src, splits, s);
+    case 64: return t5_conv_launch_bn<64>(o, K, src, splits, s);
+    case 128: return t5_conv_launch_bn<128>(o, K, src, splits, s);
+    default: return t5_conv_launch_bn<256>(o, K, src, splits, s);
   }
 }
 
@@ -1058,18 +1078,21 @@ cudaError_t gemm_out(float* C, int M, int N, int K, LA la, LB lb, const float* b
 }
 
 // gemm_out with both operands copied asynchronously (t5_conv_kernel): the
-// weight operand laid out at wa (M x K bfloat16), the pixel operand's planes.
+// weight operand laid out at wa (M x K bfloat16), the pixel operand from the
+// planes of the gathered tensor (C_g channels, [3][P][C_g]).
 template <class LA>
-cudaError_t conv_out(float* C, int M, int N, int K, LA la, __nv_bfloat16* wa, const PixPlanes& xb,
+cudaError_t conv_out(float* C, int M, int N, int K, LA la, __nv_bfloat16* wa,
+                     const __nv_bfloat16* planes, long long P, int H, int W, int Cg,
                      const float* bias, bool relu, cudaStream_t s) {
   cudaError_t e = arrange_rows(la, M, K, wa, s);
   if (e != cudaSuccess) return e;
+  const ConvSrc src{wa, planes, P, H, W, Cg, M, K};
   const int splits = out_splits(M, N, K);
   if (splits == 1)
-    return conv_launch(OutPlain{C, N, M, N, bias, relu ? 1 : 0, 0}, K, wa, xb, 1, s);
+    return conv_launch(OutPlain{C, N, M, N, bias, relu ? 1 : 0, 0}, K, src, 1, s);
   e = cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(float), s);
   if (e != cudaSuccess) return e;
-  e = conv_launch(OutPlain{C, N, M, N, nullptr, 0, 1}, K, wa, xb, splits, s);
+  e = conv_launch(OutPlain{C, N, M, N, nullptr, 0, 1}, K, src, splits, s);
   if (e != cudaSuccess || (!bias && !relu)) return e;
   bias_act_kernel<<<grid_for((long long)M * N), kT, 0, s>>>(C, bias, relu ? 1 : 0, M, N);
   return cudaGetLastError();
@@ -1092,8 +1115,8 @@ cudaError_t conv3x3_fwd(const float* X, int n, int Ci, int H, int W, const float
   if (planes && wa && Ci % 8 == 0) {
     cudaError_t e = split_planes(X, Ci, P, planes, s);
     if (e != cudaSuccess) return e;
-    return conv_out(Y, Co, (int)P, 9 * Ci, LoadWTap{Wt, Ci, Co}, wa,
-                    PixPlanes{planes, P, H, W, Ci}, b, relu, s);
+    return conv_out(Y, Co, (int)P, 9 * Ci, LoadWTap{Wt, Ci, Co}, wa, planes, P, H, W, Ci, b, relu,
+                    s);
   }
   return gemm_out<1, 3>(Y, Co, (int)P, 9 * Ci, LoadWTap{Wt, Ci, Co}, LoadPixTap{X, P, H, W, Ci}, b,
                         relu, s);
@@ -1117,8 +1140,8 @@ cudaError_t conv3x3_bwd(const float* X, const float* dY, int n, int Ci, int H, i
   if (!dX) return cudaSuccess;
   if (planes && wa && Co % 8 == 0) {
     if ((e = split_planes(dY, Co, P, planes, s)) != cudaSuccess) return e;
-    return conv_out(dX, Ci, (int)P, 9 * Co, LoadFlipW{Wt, Ci, Co}, wa,
-                    PixPlanes{planes, P, H, W, Co}, nullptr, false, s);
+    return conv_out(dX, Ci, (int)P, 9 * Co, LoadFlipW{Wt, Ci, Co}, wa, planes, P, H, W, Co, nullptr,
+                    false, s);
   }
   return gemm_out<1, 3>(dX, Ci, (int)P, 9 * Co, LoadFlipW{Wt, Ci, Co}, LoadPixTap{dY, P, H, W, Co},
                         nullptr, false, s);
@@ -1509,10 +1532,18 @@ slim_status slim_unet_create(int H, int W, int max_batch, slim_unet** out) {
   fa(&u->gd1, 32 * P1); fa(&u->gy, P1);
   ba(&u->arg1, 32 * P2); ba(&u->arg2, 64 * P3); ba(&u->arg3, 128 * P4);
   {
-    // the widest 3x3-convolution input (or output gradient) of each level: 64
-    // channels at level 1 (dec1a), 128 at 2 (dec2a), 256 at 3 (dec3a) and 4 (botb)
-    const size_t need = std::max(std::max(planes_bytes(64, P1), planes_bytes(128, P2)),
-                                 std::max(planes_bytes(256, P3), planes_bytes(256, P4)));
+    // the largest planes any 3x3 convolution needs (its input forward, its
+    // output gradient backward) at the level it runs on (kLayers order; 0:
+    // not a 3x3 convolution)
+    static const int kLevel[] = {1, 1, 2, 2, 3, 3, 4, 4, 0, 3, 3, 0, 2, 2, 0, 1, 1, 0};
+    static_assert(sizeof(kLevel) / sizeof(kLevel[0]) == kNumLayers, "one level per layer");
+    const long long Pl[5] = {0, P1, P2, P3, P4};
+    size_t need = 0;
+    for (int l = 0; l < kNumLayers; ++l) {
+      if (!kLevel[l]) continue;
+      const LayerSpec& L = kLayers[l];
+      need = std::max(need, std::max(planes_bytes(L.i, Pl[kLevel[l]]), planes_bytes(L.o, Pl[kLevel[l]])));
+    }
     unsigned char* q = nullptr;
     ba(&q, (long long)need);
     u->planes = reinterpret_cast<__nv_bfloat16*>(q);
