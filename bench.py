@@ -1318,7 +1318,9 @@ def main_reference(args):
     }))
 
 
-def main():
+def parse_args(argv=None):
+    """The bench's options, with the chosen form's lookahead and factorisation
+    CTAs per SM resolved from its solver when not given."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)
@@ -1397,9 +1399,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=0)
     ap.add_argument("--cpu-warmup", type=int, default=6)
     ap.add_argument("--cpu-leg", action="store_true")
-    args = ap.parse_args()
-    global CHOSEN_SOLVER
-    CHOSEN_SOLVER = args.solver
+    args = ap.parse_args(argv)
     # measured best per solve: the inverse form's short iterate chain leaves the
     # step to the factorisations in flight, which gain from a longer lookahead
     # and a second CTA per SM; the triangular sweeps' chain does not
@@ -1410,6 +1410,13 @@ def main():
     args.r_warm = workload_of(args.workload)[0].r + 1
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    return args
+
+
+def main():
+    args = parse_args()
+    global CHOSEN_SOLVER
+    CHOSEN_SOLVER = args.solver
     if args.cpu_leg:
         cpu_leg(args)
     elif args.impl == "reference":
